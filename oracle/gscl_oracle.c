@@ -1,0 +1,253 @@
+/*
+ * gscl_oracle.c -- plain FP64 CPU oracle for the two iteration spaces of the
+ * generic stencil library: do_all and do_reduce (Section 3).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline / reference leg may load this code.  The CUDA
+ * library never includes, links or calls it, and it shares no code with it.
+ *
+ * What it computes (Section 3, definitions of "stencil operator",
+ * "stencil computation", do_all and do_reduce):
+ *
+ *   A grid is a dense d-dimensional array G(i0, .., i_{d-1}) (d = 2 or 3;
+ *   a 2D grid is a 3D grid with nz = 1 and no z halo).  Around the interior
+ *   each grid carries a halo of width h[axis]: the cells a stencil operator
+ *   may read at a fixed offset from the core element (Section 3, "stencil
+ *   shape ... defines the halo").
+ *
+ *   A stencil operator is given as a list of terms
+ *        t = (dx, dy, dz, in, coef, out, w)
+ *   and, at a core element p, computes
+ *        value(p)  = sum over terms with out == VALUE of  w * X_t(p) * C_t(p)
+ *        out_m(p)  = sum over terms with out == m      of  w * X_t(p) * C_t(p)
+ *   where X_t(p) = In_in(p + (dx,dy,dz)), or value(p) when in == VALUE
+ *   (offset 0: the operator's own return value, which is how two operators
+ *   are fused into one scan, Section 5.2), and C_t(p) = In_coef(p) or 1 when
+ *   coef == NONE.  Terms are summed in the order given, each product formed
+ *   as (w * X) * C, with no fused multiply-add (the file is compiled with
+ *   -ffp-contract=off).  Outputs are written only at the core element.
+ *
+ *   do_all applies the operator at every core element of an iteration range
+ *   [lo, hi) (interior coordinates), in lexicographic (k, j, i) order; the
+ *   paper guarantees no order, so the operator must not read an output grid
+ *   at a non-zero offset, and the oracle requires output arrays distinct from
+ *   input arrays.
+ *
+ *   do_reduce is do_all whose per-element return values are reduced to one
+ *   value by a commutative operator (Section 3).  Here the returned value is
+ *   value(p) (or In_0(p) when the operator is empty), reduced in lexicographic
+ *   order by one of
+ *        SUM    : Neumaier's compensated sum (Neumaier 1974),
+ *        MAXABS : max |v| (NaN if any v is NaN),
+ *        L2     : sqrt of the Neumaier-compensated sum of v*v.
+ *
+ * Layout (the oracle's own, unrelated to the library's): each grid is a
+ * dense C-order array of (nz+2hz) x (ny+2hy) x (nx+2hx) doubles, x fastest;
+ * element (i,j,k) of the interior, with -h <= i < n+h, is at
+ *        ((k+hz)*(ny+2hy) + (j+hy))*(nx+2hx) + (i+hx).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stddef.h>
+
+/* ORC_MUTANT (tests only, never set in a normal build) plants one known
+ * mistake so the test suite can show that its pins detect it. */
+#ifndef ORC_MUTANT
+#define ORC_MUTANT 0
+#endif
+
+#define ORC_VALUE 254 /* in == ORC_VALUE: the operator's value; out == ORC_VALUE: term of the value */
+#define ORC_NONE 255  /* coef == ORC_NONE: no coefficient grid */
+
+enum { ORC_OK = 0, ORC_BAD_ARG = 1, ORC_BAD_RANGE = 2 };
+enum { ORC_SUM = 0, ORC_MAXABS = 1, ORC_L2 = 2 };
+
+typedef struct {
+  int32_t dx, dy, dz;
+  int32_t in, coef, out;
+  double w;
+} orc_term;
+
+typedef struct {
+  int64_t nx, ny, nz;  /* interior extent, shared by every grid of one call */
+} orc_extent;
+
+typedef struct {
+  const double *data;  /* dense array with halo, layout above */
+  int32_t hx, hy, hz;  /* this grid's halo */
+} orc_grid;
+
+typedef struct {
+  double *data;
+  int32_t hx, hy, hz;
+} orc_out_grid;
+
+static int64_t orc_index(const orc_extent *e, int32_t hx, int32_t hy, int32_t hz,
+                         int64_t i, int64_t j, int64_t k) {
+  int64_t X = e->nx + 2 * (int64_t)hx;
+  int64_t Y = e->ny + 2 * (int64_t)hy;
+#if ORC_MUTANT == 5
+  if (Y == X) return ((k + hz) * Y + (i + hx)) * X + (j + hy); /* x and y exchanged */
+#endif
+  return ((k + hz) * Y + (j + hy)) * X + (i + hx);
+}
+
+/* Reads element (i,j,k) of input grid g; the caller has checked it lies
+ * inside the grid's interior plus halo. */
+static double orc_read(const orc_extent *e, const orc_grid *g, int64_t i, int64_t j, int64_t k) {
+  return g->data[orc_index(e, g->hx, g->hy, g->hz, i, j, k)];
+}
+
+/* Every read p + offset of every core element in [lo, hi) must fall inside
+ * [-h, n+h) of the grid it reads; coefficient reads are at offset 0. */
+static int orc_check(const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                     int n_terms, const orc_term *terms, const int64_t lo[3], const int64_t hi[3]) {
+  const int64_t n[3] = {e->nx, e->ny, e->nz};
+  for (int a = 0; a < 3; ++a) {
+    if (lo[a] < 0 || hi[a] > n[a] || lo[a] > hi[a]) return ORC_BAD_RANGE;
+  }
+  for (int t = 0; t < n_terms; ++t) {
+    const orc_term *tm = &terms[t];
+    if (tm->out != ORC_VALUE && (tm->out < 0 || tm->out >= n_out)) return ORC_BAD_ARG;
+    if (tm->coef != ORC_NONE && (tm->coef < 0 || tm->coef >= n_in)) return ORC_BAD_ARG;
+    if (tm->in == ORC_VALUE) {
+      if (tm->dx || tm->dy || tm->dz || tm->out == ORC_VALUE) return ORC_BAD_ARG;
+      continue;
+    }
+    if (tm->in < 0 || tm->in >= n_in) return ORC_BAD_ARG;
+    const orc_grid *g = &in[tm->in];
+    const int32_t h[3] = {g->hx, g->hy, g->hz};
+    const int32_t d[3] = {tm->dx, tm->dy, tm->dz};
+    for (int a = 0; a < 3; ++a) {
+      if (lo[a] >= hi[a]) continue;
+      if (lo[a] + d[a] < -(int64_t)h[a] || hi[a] - 1 + d[a] > n[a] - 1 + h[a]) return ORC_BAD_RANGE;
+    }
+  }
+  return ORC_OK;
+}
+
+/* The operator at one core element.  abs_mode evaluates the "absolute
+ * stencil" S(p) = sum |w| |X| |C| instead (with the value's own absolute
+ * stencil standing in for |value|), which the tests use to scale
+ * per-element tolerances. */
+static double orc_term_sum(const orc_extent *e, const orc_grid *in, int n_terms, const orc_term *terms,
+                           int target, double value, int abs_mode, int64_t i, int64_t j, int64_t k) {
+  double acc = 0.0;
+  for (int t = 0; t < n_terms; ++t) {
+    const orc_term *tm = &terms[t];
+    if (tm->out != target) continue;
+#if ORC_MUTANT == 3
+    if (t == n_terms - 1) continue; /* last term dropped */
+#endif
+#if ORC_MUTANT == 1
+    double x = (tm->in == ORC_VALUE) ? value : orc_read(e, &in[tm->in], i - tm->dx, j + tm->dy, k + tm->dz);
+#elif ORC_MUTANT == 7
+    double x = (tm->in == ORC_VALUE) ? 0.0 : orc_read(e, &in[tm->in], i + tm->dx, j + tm->dy, k + tm->dz);
+#else
+    double x = (tm->in == ORC_VALUE) ? value : orc_read(e, &in[tm->in], i + tm->dx, j + tm->dy, k + tm->dz);
+#endif
+#if ORC_MUTANT == 2
+    int64_t cdx = tm->dx > in[tm->coef == ORC_NONE ? 0 : tm->coef].hx ? 0 : tm->dx;
+    double c = (tm->coef == ORC_NONE) ? 1.0 : orc_read(e, &in[tm->coef], i + (cdx >= 0 ? cdx : 0), j, k);
+#else
+    double c = (tm->coef == ORC_NONE) ? 1.0 : orc_read(e, &in[tm->coef], i, j, k);
+#endif
+    double w = tm->w;
+    if (abs_mode) { x = fabs(x); c = fabs(c); w = fabs(w); }
+    acc = acc + (w * x) * c;
+  }
+  return acc;
+}
+
+/* do_all over [lo, hi).  value_out (optional) receives value(p) for every
+ * core element, dense in (k, j, i) order over the range. */
+int orc_do_all(const orc_extent *e, int n_in, const orc_grid *in, int n_out, const orc_out_grid *out,
+               int n_terms, const orc_term *terms, const int64_t lo[3], const int64_t hi[3],
+               int abs_mode, double *value_out) {
+  int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
+  if (rc) return rc;
+  int64_t q = 0;
+  for (int64_t k = lo[2]; k < hi[2]; ++k)
+    for (int64_t j = lo[1]; j < hi[1]; ++j)
+      for (int64_t i = lo[0]; i < hi[0]; ++i) {
+        double v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, abs_mode, i, j, k);
+        for (int m = 0; m < n_out; ++m) {
+          double r = orc_term_sum(e, in, n_terms, terms, m, v, abs_mode, i, j, k);
+          out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r;
+        }
+        if (value_out) value_out[q++] = v;
+      }
+  return ORC_OK;
+}
+
+/* Neumaier's improvement of Kahan summation: the running compensation c
+ * collects the rounding error of every addition, taken from whichever
+ * operand is larger in magnitude. */
+typedef struct { double s, c; } orc_neumaier;
+
+static void orc_neumaier_add(orc_neumaier *a, double x) {
+#if ORC_MUTANT == 4
+  a->s += x; /* plain recursive sum */
+  return;
+#endif
+  double t = a->s + x;
+  if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+  else a->c += (x - t) + a->s;
+  a->s = t;
+}
+
+/* do_reduce over [lo, hi): writes the reduced value to *result.  With
+ * n_terms == 0 the per-element value is In_0(p) and no output is written;
+ * otherwise the operator runs as in orc_do_all (outputs included) and its
+ * value is reduced. */
+int orc_do_reduce(int op, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                  const orc_out_grid *out, int n_terms, const orc_term *terms,
+                  const int64_t lo[3], const int64_t hi[3], double *result) {
+  if (op != ORC_SUM && op != ORC_MAXABS && op != ORC_L2) return ORC_BAD_ARG;
+  if (n_terms == 0) {
+    if (n_in < 1 || n_out != 0) return ORC_BAD_ARG;
+    orc_term id = {0, 0, 0, 0, ORC_NONE, ORC_VALUE, 1.0};
+    int rc = orc_check(e, n_in, in, 0, 1, &id, lo, hi);
+    if (rc) return rc;
+  } else {
+    int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
+    if (rc) return rc;
+  }
+  orc_neumaier acc = {0.0, 0.0};
+  double mx = 0.0;
+  int saw_nan = 0;
+  for (int64_t k = lo[2]; k < hi[2]; ++k)
+    for (int64_t j = lo[1]; j < hi[1]; ++j)
+      for (int64_t i = lo[0]; i < hi[0]; ++i) {
+        double v;
+        if (n_terms == 0) {
+          v = orc_read(e, &in[0], i, j, k);
+        } else {
+          v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, 0, i, j, k);
+          for (int m = 0; m < n_out; ++m) {
+            double r = orc_term_sum(e, in, n_terms, terms, m, v, 0, i, j, k);
+            out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r;
+          }
+        }
+        if (op == ORC_SUM) {
+          orc_neumaier_add(&acc, v);
+        } else if (op == ORC_L2) {
+#if ORC_MUTANT == 8
+          orc_neumaier_add(&acc, fabs(v)); /* norm 1 instead of norm 2 */
+#else
+          orc_neumaier_add(&acc, v * v);
+#endif
+        } else {
+#if ORC_MUTANT == 6
+          if (0) saw_nan = 1;
+#else
+          if (isnan(v)) saw_nan = 1;
+#endif
+          else if (fabs(v) > mx) mx = fabs(v);
+        }
+      }
+  if (op == ORC_SUM) *result = acc.s + acc.c;
+  else if (op == ORC_L2) *result = sqrt(acc.s + acc.c);
+  else *result = saw_nan ? NAN : mx;
+  return ORC_OK;
+}

@@ -1,0 +1,181 @@
+"""ctypes front end of the FP64 CPU oracle (``gscl_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline / reference leg are the only callers.  Nothing in the CUDA
+library imports this module, and this module imports nothing from it.
+
+The oracle's grids are plain numpy float64 arrays of shape
+``(nz + 2hz, ny + 2hy, nx + 2hx)`` (x fastest) paired with their halo widths;
+2D grids use ``nz = 1, hz = 0``.  Stencil operators are lists of terms
+``(dx, dy, dz, in, coef, out, w)`` with the meaning given in the C file's
+header (Section 3 of the paper: an operator reads fixed offsets of several
+grids around the core element and writes the core element of its outputs;
+it may also return a value, which ``do_reduce`` reduces).
+
+Parity status: every function here is pinned by tests under ``tests/``
+(closed forms, invariants, brute force); none is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+VALUE = 254  # term input/output code: the operator's returned value
+NONE = 255   # coefficient code: no coefficient grid
+
+SUM, MAXABS, L2 = 0, 1, 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gscl_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+
+
+def build(force: bool = False, mutant: int = 0) -> str:
+    """Compiles the oracle with plain gcc: -O2, no FMA contraction, no fast-math.
+
+    ``mutant`` > 0 builds a copy with one planted mistake (tests only)."""
+    path = _LIB if mutant == 0 else os.path.join(_LIB_DIR, f"liboracle_mutant{mutant}.so")
+    if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        tmp = path + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                               f"-DORC_MUTANT={int(mutant)}", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, path)
+    return path
+
+
+class _Term(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_int32), ("dy", ctypes.c_int32), ("dz", ctypes.c_int32),
+                ("in_", ctypes.c_int32), ("coef", ctypes.c_int32), ("out", ctypes.c_int32),
+                ("w", ctypes.c_double)]
+
+
+class _Extent(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64)]
+
+
+class _Grid(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("hx", ctypes.c_int32), ("hy", ctypes.c_int32),
+                ("hz", ctypes.c_int32)]
+
+
+_lib = None
+_lib_path = None
+
+
+def use_library(path=None):
+    """Selects which compiled oracle the calls below use (None: the normal build)."""
+    global _lib, _lib_path
+    _lib, _lib_path = None, path
+
+
+def _get_lib():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_lib_path or build())
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        lib.orc_do_all.argtypes = [ctypes.POINTER(_Extent), ctypes.c_int, ctypes.POINTER(_Grid),
+                                   ctypes.c_int, ctypes.POINTER(_Grid), ctypes.c_int,
+                                   ctypes.POINTER(_Term), i64p, i64p, ctypes.c_int,
+                                   ctypes.POINTER(ctypes.c_double)]
+        lib.orc_do_all.restype = ctypes.c_int
+        lib.orc_do_reduce.argtypes = [ctypes.c_int, ctypes.POINTER(_Extent), ctypes.c_int,
+                                      ctypes.POINTER(_Grid), ctypes.c_int, ctypes.POINTER(_Grid),
+                                      ctypes.c_int, ctypes.POINTER(_Term), i64p, i64p,
+                                      ctypes.POINTER(ctypes.c_double)]
+        lib.orc_do_reduce.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+@dataclass
+class Grid:
+    """A dense FP64 grid with halo: ``a[k + hz, j + hy, i + hx]`` is element (i, j, k)."""
+    a: np.ndarray
+    halo: tuple
+
+    @property
+    def n(self):
+        hx, hy, hz = self.halo
+        z, y, x = self.a.shape
+        return (x - 2 * hx, y - 2 * hy, z - 2 * hz)
+
+    def interior(self):
+        hx, hy, hz = self.halo
+        nx, ny, nz = self.n
+        return self.a[hz:hz + nz, hy:hy + ny, hx:hx + nx]
+
+    def copy(self):
+        return Grid(self.a.copy(), tuple(self.halo))
+
+
+def zeros(n, halo) -> Grid:
+    nx, ny, nz = n
+    hx, hy, hz = halo
+    return Grid(np.zeros((nz + 2 * hz, ny + 2 * hy, nx + 2 * hx), dtype=np.float64), tuple(halo))
+
+
+def _marshal(terms, ins, outs, lo, hi):
+    if not ins:
+        raise ValueError("at least one input grid")
+    n = ins[0].n
+    for g in list(ins) + list(outs):
+        if g.n != n:
+            raise ValueError("all grids of one call share the interior extent")
+        if g.a.dtype != np.float64 or not g.a.flags.c_contiguous:
+            raise ValueError("oracle grids are C-contiguous float64")
+    in_ids = {id(g.a) for g in ins}
+    for g in outs:
+        if id(g.a) in in_ids:
+            raise ValueError("the oracle requires output arrays distinct from inputs")
+    ext = _Extent(*n)
+    gin = (_Grid * len(ins))(*[_Grid(g.a.ctypes.data, *g.halo) for g in ins])
+    gout = (_Grid * max(1, len(outs)))(*[_Grid(g.a.ctypes.data, *g.halo) for g in outs])
+    tt = (_Term * max(1, len(terms)))(*[_Term(int(t[0]), int(t[1]), int(t[2]), int(t[3]),
+                                              int(t[4]), int(t[5]), float(t[6])) for t in terms])
+    if lo is None:
+        lo = (0, 0, 0)
+    if hi is None:
+        hi = n
+    clo = (ctypes.c_int64 * 3)(*lo)
+    chi = (ctypes.c_int64 * 3)(*hi)
+    return ext, gin, gout, tt, clo, chi
+
+
+def do_all(terms, ins, outs, lo=None, hi=None, abs_mode=False, want_value=False):
+    """Applies the operator at every core element of ``[lo, hi)`` (Section 3, do_all).
+
+    Writes each output grid's core elements in place; with ``want_value``
+    returns the operator's value at every core element as an array of shape
+    ``(hi_z - lo_z, hi_y - lo_y, hi_x - lo_x)``.  ``abs_mode`` computes the
+    absolute stencil S(p) instead (tolerance scaling for the tests).
+    """
+    ext, gin, gout, tt, clo, chi = _marshal(terms, ins, outs, lo, hi)
+    shape = tuple(int(chi[a] - clo[a]) for a in (2, 1, 0))
+    val = np.zeros(shape, dtype=np.float64) if want_value else None
+    vptr = val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_value else None
+    rc = _get_lib().orc_do_all(ctypes.byref(ext), len(ins), gin, len(outs), gout, len(terms), tt,
+                               clo, chi, int(bool(abs_mode)), vptr)
+    if rc != 0:
+        raise ValueError(f"oracle do_all rejected the call (code {rc})")
+    return val
+
+
+def do_reduce(op, terms, ins, outs=(), lo=None, hi=None) -> float:
+    """Reduces the operator's per-element value over ``[lo, hi)`` (Section 3, do_reduce).
+
+    ``terms`` empty means the value is ``ins[0]`` itself.  Outputs, if the
+    operator has any, are written as in ``do_all`` (a fused operator).
+    """
+    ext, gin, gout, tt, clo, chi = _marshal(terms, ins, outs, lo, hi)
+    res = ctypes.c_double(0.0)
+    rc = _get_lib().orc_do_reduce(int(op), ctypes.byref(ext), len(ins), gin, len(outs), gout,
+                                  len(terms), tt, clo, chi, ctypes.byref(res))
+    if rc != 0:
+        raise ValueError(f"oracle do_reduce rejected the call (code {rc})")
+    return float(res.value)

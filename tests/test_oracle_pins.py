@@ -1,0 +1,409 @@
+"""Pins of the FP64 CPU oracle against facts that do not come from the oracle itself:
+closed forms, telescoping invariants, exact (math.fsum) sums, a library sparse
+solve, brute-force dense matrices assembled independently, and the operator
+printed in Fig. 1b (tests/golden/fig1b_operator.txt)."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from oracle import drivers as D
+from oracle import oracle as O
+
+EPS = np.finfo(np.float64).eps
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def grid_from(fun, n, halo):
+    """Grid whose every cell (halo included) holds fun(i, j, k) in interior coordinates."""
+    g = O.zeros(n, halo)
+    hx, hy, hz = halo
+    nx, ny, nz = n
+    k, j, i = np.meshgrid(np.arange(-hz, nz + hz), np.arange(-hy, ny + hy), np.arange(-hx, nx + hx),
+                          indexing="ij")
+    g.a[...] = fun(i.astype(np.float64), j.astype(np.float64), k.astype(np.float64))
+    return g
+
+
+def laplacian_terms(dim):
+    """Sum of axial neighbours minus 2*dim times the centre, written per axis."""
+    t = []
+    for ax in range(dim):
+        for s in (1, -1):
+            o = [0, 0, 0]
+            o[ax] = s
+            t.append((o[0], o[1], o[2], 0, O.NONE, 0, 1.0))
+    t.append((0, 0, 0, 0, O.NONE, 0, -2.0 * dim))
+    return t
+
+
+# ------------------------------------------------------------------ closed forms
+@pytest.mark.parametrize("coef", [(1, 2, -1, 3, -2, 5, 7), (-2, 1, 2, 0, 1, -1, -3)])
+def test_quadratic_laplacian_3d_exact(coef):
+    a, b, c, d, e, f, g0 = coef
+    n, h = (9, 7, 6), (1, 1, 1)
+    u = grid_from(lambda i, j, k: a * i * i + b * j * j + c * k * k + d * i + e * j + f * k + g0, n, h)
+    out = O.zeros(n, h)
+    O.do_all(laplacian_terms(3), [u], [out])
+    assert np.all(out.interior() == 2.0 * (a + b + c))
+
+
+def test_quadratic_laplacian_2d_exact():
+    n, h = (11, 5, 1), (1, 1, 0)
+    u = grid_from(lambda i, j, k: 2 * i * i - j * j + 3 * i - 4 * j + 1, n, h)
+    out = O.zeros(n, h)
+    O.do_all(laplacian_terms(2), [u], [out])
+    assert np.all(out.interior() == 2.0 * (2 - 1))
+
+
+def sine_mode(n, p):
+    def fun(i, j, k):
+        v = np.sin(p[0] * math.pi * (i + 1) / (n[0] + 1)) * np.sin(p[1] * math.pi * (j + 1) / (n[1] + 1))
+        if n[2] > 1:
+            v = v * np.sin(p[2] * math.pi * (k + 1) / (n[2] + 1))
+        return v
+    h = (1, 1, 1) if n[2] > 1 else (1, 1, 0)
+    g = grid_from(fun, n, h)
+    # the eigenmode vanishes on the halo up to the rounding of sin(m pi); make it exact
+    inner = g.interior().copy()
+    g.a[...] = 0.0
+    g.interior()[...] = inner
+    return g
+
+
+@pytest.mark.parametrize("p", [(1, 1, 1), (2, 3, 1), (5, 1, 4)])
+def test_heat_sine_eigenmode_factor(p):
+    n = (12, 10, 9)
+    lam = 1.0 / 8.0
+    u = sine_mode(n, p)
+    factor = 1.0 + 2.0 * lam * sum(math.cos(p[d] * math.pi / (n[d] + 1)) - 1.0 for d in range(3))
+    sweeps = 7
+    last, _ = D.heat_run(u, None, lam, sweeps)
+    expect = u.interior() * factor ** sweeps
+    assert np.max(np.abs(last.interior() - expect)) <= 1e-13 * np.max(np.abs(u.interior()))
+
+
+@pytest.mark.parametrize("p", [(1, 1, 1), (3, 2, 1)])
+def test_jacobi2d_sine_eigenmode_factor(p):
+    n = (14, 9, 1)
+    u = sine_mode(n, p)
+    mu = 0.5 * (math.cos(p[0] * math.pi / (n[0] + 1)) + math.cos(p[1] * math.pi / (n[1] + 1)))
+    last, prev, _ = D.jacobi2d_run(u, 5)
+    assert np.max(np.abs(last.interior() - u.interior() * mu ** 5)) <= 1e-14
+    assert np.max(np.abs(prev.interior() - u.interior() * mu ** 4)) <= 1e-14
+
+
+def test_poisson_jacobi_sine_eigenmode_factor():
+    n = (8, 8, 8)
+    u = sine_mode(n, (1, 2, 3))
+    f = O.zeros(n, (1, 1, 1))
+    out = O.zeros(n, (1, 1, 1))
+    O.do_all(D.poisson_jacobi_terms(), [u, f], [out])
+    mu = sum(math.cos(q * math.pi / 9) for q in (1, 2, 3)) / 3.0
+    assert np.max(np.abs(out.interior() - mu * u.interior())) <= 1e-15
+
+
+def test_laplace2d_discrete_harmonic_fixed_point():
+    """u = sin(pi x) cosh(beta (y - 1/2)) / cosh(beta / 2) with cosh(beta h) = 2 - cos(pi h)
+    solves the 5-point equation exactly and equals sin(pi x) on both y edges."""
+    m = 40
+    hgrid = 1.0 / (m + 1)
+    beta = math.acosh(2.0 - math.cos(math.pi * hgrid)) / hgrid
+
+    def fun(i, j, k):
+        x, y = (i + 1) * hgrid, (j + 1) * hgrid
+        return np.sin(math.pi * x) * np.cosh(beta * (y - 0.5)) / math.cosh(beta / 2)
+
+    u = grid_from(fun, (m, m, 1), (1, 1, 0))
+    last, prev, res = D.jacobi2d_run(u, 1)
+    assert np.max(np.abs(last.interior() - u.interior())) <= 1e-14
+    assert res <= 1e-14
+
+
+# ------------------------------------------------------------- biharmonic, advection
+def climate_grids(n, q_fun, kappa_fun, w_fun, t_val):
+    h = (2, 2, 1)
+    q = [grid_from(q_fun, n, h) for _ in range(3)]
+    kappa = grid_from(kappa_fun, n, h)
+    w = grid_from(w_fun, n, h)
+    t = [grid_from(lambda i, j, k: np.full_like(i, t_val), n, h) for _ in range(3)]
+    return q, kappa, w, t
+
+
+@pytest.mark.parametrize("q_fun,expect", [
+    (lambda i, j, k: i ** 4, lambda i, j, k: -24.0),
+    (lambda i, j, k: j ** 4 - i ** 4, lambda i, j, k: 0.0),
+    (lambda i, j, k: i * i * j * j, lambda i, j, k: -8.0),
+    (lambda i, j, k: 3 * i ** 3 - 2 * i * i * j + i * j * j + 5 * j ** 3 + 2 * i - 7, lambda i, j, k: 0.0),
+])
+def test_biharmonic_polynomials_exact(q_fun, expect):
+    n = (9, 8, 4)
+    q, kappa, w, t = climate_grids(n, q_fun, lambda i, j, k: np.ones_like(i), lambda i, j, k: 0 * i, 0.0)
+    out = D.climate_run(q, kappa, w, t, 1)
+    ref = grid_from(lambda i, j, k: q_fun(i, j, k) + expect(i, j, k), n, (2, 2, 1))
+    for m in range(3):
+        assert np.all(out[m].interior() == ref.interior())
+
+
+def test_coefficient_read_at_core_element():
+    """kappa enters at the core element: with q = i^4 and kappa = 1 + i the update is -24 (1 + i)."""
+    n = (9, 6, 3)
+    q, kappa, w, t = climate_grids(n, lambda i, j, k: i ** 4, lambda i, j, k: 1.0 + i,
+                                   lambda i, j, k: 0 * i, 0.0)
+    out = D.climate_run(q, kappa, w, t, 1)
+    ref = grid_from(lambda i, j, k: i ** 4 - 24.0 * (1.0 + i), n, (2, 2, 1))
+    assert np.all(out[1].interior() == ref.interior())
+
+
+def test_vertical_advection_and_tendency_exact():
+    """Centred difference of k^2 is 4k, halved by 2 dz: q' = k^2 - 2k w + t."""
+    n = (5, 4, 7)
+    q, kappa, w, t = climate_grids(n, lambda i, j, k: k * k, lambda i, j, k: 0 * i,
+                                   lambda i, j, k: 1.0 + 0 * i, 3.0)
+    out = D.climate_run(q, kappa, w, t, 1)
+    ref = grid_from(lambda i, j, k: k * k - 2.0 * k + 3.0, n, (2, 2, 1))
+    assert np.all(out[2].interior() == ref.interior())
+
+
+# ---------------------------------------------------------------------- invariants
+def test_flux_invariant_telescoping():
+    """sum over the interior of (sum6 - 6u) equals the sum over the six faces of
+    (halo value - adjacent interior value)."""
+    rng = np.random.default_rng(7)
+    n, h = (10, 7, 6), (1, 1, 1)
+    u = O.zeros(n, h)
+    u.a[...] = rng.integers(-50, 50, size=u.a.shape).astype(np.float64)
+    f = O.zeros(n, h)
+    got = O.do_reduce(O.SUM, D.residual_terms(), [u, f])
+    a = u.a
+    I = a[1:-1, 1:-1, 1:-1]
+    flux = (a[1:-1, 1:-1, 0].sum() - I[:, :, 0].sum() + a[1:-1, 1:-1, -1].sum() - I[:, :, -1].sum()
+            + a[1:-1, 0, 1:-1].sum() - I[:, 0, :].sum() + a[1:-1, -1, 1:-1].sum() - I[:, -1, :].sum()
+            + a[0, 1:-1, 1:-1].sum() - I[0, :, :].sum() + a[-1, 1:-1, 1:-1].sum() - I[-1, :, :].sum())
+    assert got == flux
+
+
+def test_fused_sweep_and_residual_equal_two_passes():
+    """Section 5.2: the fused operator and two separate scans are algorithmically equivalent."""
+    rng = np.random.default_rng(3)
+    n, h = (8, 9, 7), (1, 1, 1)
+    u = O.zeros(n, h)
+    f = O.zeros(n, h)
+    u.a[...] = rng.uniform(-1, 1, u.a.shape)
+    f.a[...] = rng.uniform(-1, 1, f.a.shape)
+    fused_out, plain_out = O.zeros(n, h), O.zeros(n, h)
+    r_fused = O.do_reduce(O.L2, D.heat_terms(0.125), [u, f], [fused_out])
+    O.do_all(D.heat_terms(0.125), [u, f], [plain_out])
+    r_two = O.do_reduce(O.L2, D.residual_terms(), [u, f])
+    assert np.array_equal(fused_out.a[1:-1, 1:-1, 1:-1], plain_out.a[1:-1, 1:-1, 1:-1])
+    assert r_fused == r_two
+
+
+def test_heat_first_residual_is_norm_of_rhs():
+    rng = np.random.default_rng(11)
+    n, h = (6, 5, 7), (1, 1, 1)
+    u0 = O.zeros(n, h)
+    f = O.zeros(n, h)
+    f.interior()[...] = rng.uniform(-1, 1, (7, 5, 6))
+    _, res = D.heat_run(u0, f, 0.125, 20, every=10)
+    assert len(res) == 2
+    exact = math.sqrt(math.fsum((f.interior() ** 2).ravel()))
+    assert abs(res[0] - exact) <= 4 * EPS * exact
+
+
+# -------------------------------------------------------------------- brute force
+def dense_operator(terms, ins, n_out):
+    """Dense matrices (one per output) acting on the concatenation of all flattened
+    input arrays, assembled row by row by enumerating each term's offset."""
+    n = ins[0].n
+    sizes = [g.a.size for g in ins]
+    base = np.concatenate([[0], np.cumsum(sizes)])
+    rows = n[0] * n[1] * n[2]
+    value = np.zeros((rows, base[-1]))
+    outs = [np.zeros((rows, base[-1])) for _ in range(n_out)]
+    r = 0
+    for k in range(n[2]):
+        for j in range(n[1]):
+            for i in range(n[0]):
+                for phase in ("value", "out"):
+                    for (dx, dy, dz, a, c, m, w) in terms:
+                        if (phase == "value") != (m == O.VALUE):
+                            continue
+                        coef = 1.0
+                        if c != O.NONE:
+                            gc = ins[c]
+                            coef = gc.a[k + gc.halo[2], j + gc.halo[1], i + gc.halo[0]]
+                        target = value if m == O.VALUE else outs[m]
+                        if a == O.VALUE:
+                            target[r] += w * coef * value[r]
+                        else:
+                            g = ins[a]
+                            col = np.ravel_multi_index((k + dz + g.halo[2], j + dy + g.halo[1],
+                                                        i + dx + g.halo[0]), g.a.shape)
+                            target[r, base[a] + col] += w * coef
+                r += 1
+    return value, outs
+
+
+def random_terms(rng, n_in, n_out, halos, count):
+    terms = []
+    for t in range(count):
+        a = int(rng.integers(0, n_in))
+        hx, hy, hz = halos[a]
+        o = [int(rng.integers(-hx, hx + 1)), int(rng.integers(-hy, hy + 1)), int(rng.integers(-hz, hz + 1))]
+        c = int(rng.integers(0, n_in)) if rng.random() < 0.3 else O.NONE
+        m = O.VALUE if rng.random() < 0.25 else int(rng.integers(0, n_out))
+        terms.append((o[0], o[1], o[2], a, c, m, float(rng.uniform(-2, 2))))
+    terms.append((0, 0, 0, O.VALUE, O.NONE, 0, 0.75))
+    return terms
+
+
+@pytest.mark.parametrize("n,halos,seed", [
+    ((8, 8, 8), [(1, 1, 1), (2, 2, 1), (0, 0, 0)], 1),
+    ((7, 5, 6), [(2, 1, 2), (1, 1, 1), (1, 0, 1)], 2),
+    ((8, 8, 1), [(1, 1, 0), (2, 2, 0), (0, 0, 0)], 3),
+])
+def test_bruteforce_dense_matrix(n, halos, seed):
+    rng = np.random.default_rng(seed)
+    ins = [O.zeros(n, h) for h in halos]
+    for g in ins:
+        g.a[...] = rng.uniform(-1, 1, g.a.shape)
+    n_out = 2
+    terms = random_terms(rng, len(ins), n_out, halos, 14)
+    outs = [O.zeros(n, (1, 1, 0)) for _ in range(n_out)]
+    val = O.do_all(terms, ins, outs, want_value=True)
+    Vm, Om = dense_operator(terms, ins, n_out)
+    x = np.concatenate([g.a.ravel() for g in ins])
+    scale = np.abs(np.concatenate([g.a.ravel() for g in ins])).max() * sum(abs(t[6]) for t in terms) * 4
+    assert np.max(np.abs(val.ravel() - Vm @ x)) <= 1e-13 * scale
+    for m in range(n_out):
+        assert np.max(np.abs(outs[m].interior().ravel() - Om[m] @ x)) <= 1e-13 * scale
+
+
+# ------------------------------------------------------------- paper's operator
+def load_fig1b():
+    rows = []
+    with open(os.path.join(GOLDEN, "fig1b_operator.txt")) as fh:
+        for line in fh:
+            line = line.split("#")[0].strip()
+            if line:
+                dx, dy, dz, num, den = line.split()
+                rows.append(((int(dx), int(dy), int(dz)), float(num) / float(den)))
+    return rows
+
+
+def test_fig1b_spike_response_matches_printed_operator():
+    """A single 1 at p0 makes out(p0 - o) = w_o for each printed offset o and 0 elsewhere."""
+    golden = load_fig1b()
+    assert len(golden) == 7
+    n, h = (7, 6, 5), (1, 1, 1)
+    p0 = (3, 2, 2)
+    u = O.zeros(n, h)
+    u.a[p0[2] + 1, p0[1] + 1, p0[0] + 1] = 1.0
+    out = O.zeros(n, h)
+    O.do_all(D.fig1b_terms(), [u], [out])
+    expect = np.zeros((n[2], n[1], n[0]))
+    for (dx, dy, dz), w in golden:
+        expect[p0[2] - dz, p0[1] - dy, p0[0] - dx] = w
+    assert np.array_equal(out.interior(), expect)
+
+
+def test_fig1b_on_quadratic():
+    """Fig. 1b is -1/36 times the 7-point Laplacian, so on a quadratic it gives -2(a+b+c)/36."""
+    n, h = (6, 6, 6), (1, 1, 1)
+    u = grid_from(lambda i, j, k: 3 * i * i + j * j - 2 * k * k + i, n, h)
+    out = O.zeros(n, h)
+    O.do_all(D.fig1b_terms(), [u], [out])
+    S = O.zeros(n, h)
+    O.do_all(D.fig1b_terms(), [u], [S], abs_mode=True)
+    assert np.all(np.abs(out.interior() + 2.0 * (3 + 1 - 2) / 36.0) <= 8 * EPS * S.interior())
+
+
+# --------------------------------------------------------------------- reductions
+def test_sum_is_compensated_against_exact_fsum():
+    rng = np.random.default_rng(5)
+    n, h = (17, 9, 5), (1, 1, 1)
+    g = O.zeros(n, h)
+    big = rng.choice([1e16, -1e16, 1e8, -1e8], size=g.interior().shape)
+    g.interior()[...] = big + rng.uniform(-1, 1, big.shape)
+    exact = math.fsum(g.interior().ravel())
+    got = O.do_reduce(O.SUM, [], [g])
+    bound = 2 * EPS * abs(exact) + g.interior().size * EPS * EPS * np.abs(g.interior()).sum()
+    assert abs(got - exact) <= bound
+    naive = float(np.cumsum(g.interior().ravel())[-1])
+    assert abs(naive - exact) > abs(got - exact)
+
+
+def test_neumaier_catches_large_then_small():
+    n, h = (4, 1, 1), (0, 0, 0)
+    g = O.zeros(n, h)
+    g.a[0, 0, :] = [1.0, 1e100, 1.0, -1e100]
+    assert O.do_reduce(O.SUM, [], [g]) == 2.0
+
+
+def test_maxabs_and_nan_propagation():
+    rng = np.random.default_rng(9)
+    n, h = (13, 4, 3), (1, 1, 1)
+    g = O.zeros(n, h)
+    g.a[...] = 1e9  # halo must not count
+    g.interior()[...] = rng.uniform(-5, 5, (3, 4, 13))
+    assert O.do_reduce(O.MAXABS, [], [g]) == np.max(np.abs(g.interior()))
+    g.interior()[1, 2, 3] = np.nan
+    for op in (O.SUM, O.MAXABS, O.L2):
+        assert math.isnan(O.do_reduce(op, [], [g]))
+
+
+def test_l2_against_fsum_and_subrange():
+    rng = np.random.default_rng(13)
+    n, h = (11, 10, 9), (1, 1, 1)
+    g = O.zeros(n, h)
+    g.a[...] = rng.uniform(-3, 3, g.a.shape)
+    lo, hi = (2, 1, 3), (9, 10, 7)
+    sub = g.a[1 + lo[2]:1 + hi[2], 1 + lo[1]:1 + hi[1], 1 + lo[0]:1 + hi[0]]
+    exact = math.sqrt(math.fsum((sub * sub).ravel()))
+    got = O.do_reduce(O.L2, [], [g], lo=lo, hi=hi)
+    assert abs(got - exact) <= 4 * EPS * exact
+    assert O.do_reduce(O.SUM, [], [g], lo=lo, hi=hi) == pytest.approx(math.fsum(sub.ravel()), rel=1e-14)
+
+
+def test_empty_range_reductions():
+    g = O.zeros((4, 4, 4), (1, 1, 1))
+    assert O.do_reduce(O.SUM, [], [g], lo=(2, 0, 0), hi=(2, 4, 4)) == 0.0
+    assert O.do_reduce(O.MAXABS, [], [g], lo=(0, 0, 3), hi=(4, 4, 3)) == 0.0
+
+
+# ------------------------------------------------------------------ checks, solve
+def test_rejects_reads_outside_halo_and_bad_ranges():
+    g = O.zeros((5, 5, 5), (1, 1, 1))
+    o = O.zeros((5, 5, 5), (1, 1, 1))
+    with pytest.raises(ValueError):
+        O.do_all([(2, 0, 0, 0, O.NONE, 0, 1.0)], [g], [o])
+    with pytest.raises(ValueError):
+        O.do_all([(0, 0, 0, 0, O.NONE, 0, 1.0)], [g], [o], lo=(0, 0, 0), hi=(6, 5, 5))
+    with pytest.raises(ValueError):
+        O.do_all([(0, 0, 0, 0, O.NONE, 0, 1.0)], [g], [g])
+    # a sub-range leaves room: offset 2 is fine when the range stops one short of the edge
+    O.do_all([(2, 0, 0, 0, O.NONE, 0, 1.0)], [g], [o], lo=(0, 0, 0), hi=(4, 5, 5))
+
+
+def poisson_matrix(n):
+    """7-point -Laplacian with zero Dirichlet halo, assembled with scipy.sparse kron."""
+    T = sp.diags([-np.ones(n - 1), 2 * np.ones(n), -np.ones(n - 1)], [-1, 0, 1])
+    I = sp.identity(n)
+    return (sp.kron(sp.kron(I, I), T) + sp.kron(sp.kron(I, T), I) + sp.kron(sp.kron(T, I), I)).tocsc()
+
+
+def test_poisson_jacobi_solution_matches_sparse_direct_solve():
+    n = 6
+    rng = np.random.default_rng(17)
+    f = O.zeros((n, n, n), (1, 1, 1))
+    f.interior()[...] = rng.uniform(-1, 1, (n, n, n))
+    u, sweeps = D.poisson_jacobi_solve(f, 1e-12, 20000)
+    exact = spla.spsolve(poisson_matrix(n), f.interior().ravel())
+    assert sweeps < 20000
+    assert np.max(np.abs(u.interior().ravel() - exact)) <= 1e-10 * np.max(np.abs(exact))
+    r, fn = D.poisson_residual(u, f)
+    assert r <= 1e-12 * fn
