@@ -1,0 +1,254 @@
+/*
+ * gscl.h -- C ABI of the B300 generic stencil library (libgscl.so).
+ *
+ * The library implements the two iteration spaces on the hot path of the
+ * generic stencil library of Bianco and Varetto, "A Generic Library for
+ * Stencil Computations" (arXiv 1207.1746):
+ *
+ *   do_all     apply a stencil operator at every core element of an
+ *              iteration range, in no guaranteed order (Section 3);
+ *   do_reduce  the same, reducing the operator's per-element return value
+ *              with a commutative operator (Section 3, and the fused
+ *              diffusion + convergence loop of Section 5.2);
+ *
+ * plus the grids they run on (Section 3: a regular grid is a d-dimensional
+ * array; its stencil shape fixes the halo an operator may read) and the
+ * ping-pong swap of Section 5.2.  Every computation runs in hand-written
+ * sm_103a CUDA kernels; there is no host fallback.
+ *
+ * Conventions shared by every entry point:
+ *  - Return value: a gscl_status.  GSCL_OK means the arguments were valid and
+ *    the work was enqueued on the given stream; device-side failures surface
+ *    at the next gscl_sync() (or another synchronising call) on that stream.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy
+ *    default stream).  All work is asynchronous unless a function says
+ *    otherwise.  The calling thread's current CUDA device must be the device
+ *    that owns the grids.
+ *  - Memory: the library never allocates grid storage.  Device buffers are
+ *    owned by the caller (for example a PyTorch tensor) and borrowed by the
+ *    handles that wrap them; the caller keeps them alive until the handle is
+ *    destroyed and all work on them has completed.
+ *  - Handles are opaque 64-bit ids; a destroyed or never-created id is
+ *    rejected with GSCL_ERR_STATE (a call on a stale handle is an error, not
+ *    undefined behaviour; compare Fig. 2b, where an iteration space outside a
+ *    valid context is an error).
+ *  - Thread safety: calls may come from several host threads; the handle
+ *    registry is locked internally.  Concurrent kernels that write the same
+ *    grid race, as any CUDA work does.
+ */
+#ifndef GSCL_H
+#define GSCL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum gscl_status {
+  GSCL_OK = 0,
+  GSCL_ERR_INVALID = 1,     /* malformed argument: NULL pointer, bad count or code, misaligned buffer */
+  GSCL_ERR_RANGE = 2,       /* iteration range outside the interior, or a read outside a grid's halo */
+  GSCL_ERR_ALIAS = 3,       /* an output is read at a non-zero offset, or bound twice */
+  GSCL_ERR_DTYPE = 4,       /* the grids of one call do not share one storage dtype */
+  GSCL_ERR_SHAPE = 5,       /* the grids of one call do not share one interior extent / layout */
+  GSCL_ERR_OOM = 6,         /* a caller-supplied buffer or workspace is too small */
+  GSCL_ERR_CUDA = 7,        /* a CUDA runtime or driver call failed */
+  GSCL_ERR_STATE = 8,       /* destroyed or unknown handle */
+  GSCL_ERR_TIMEOUT = 9,     /* a bounded device-side wait gave up (reported by gscl_sync) */
+  GSCL_ERR_UNSUPPORTED = 10 /* valid request outside what this build implements (e.g. too many terms) */
+} gscl_status;
+
+typedef enum gscl_dtype {
+  GSCL_F64 = 0,  /* FP64 storage, FP64 arithmetic */
+  GSCL_F32 = 1,  /* FP32 storage, FP32 arithmetic */
+  GSCL_BF16 = 2  /* BF16 storage, FP32 arithmetic, round-to-nearest-even stores */
+} gscl_dtype;
+
+typedef enum gscl_reduce_op {
+  GSCL_SUM = 0,    /* sum of the values, FP64 with compensation */
+  GSCL_MAXABS = 1, /* max |value| (NaN if any value is NaN); 0 for an empty range */
+  GSCL_L2 = 2      /* sqrt(sum of value^2), FP64 with compensation */
+} gscl_reduce_op;
+
+typedef uint64_t gscl_grid; /* 0 is never a valid handle */
+
+/* Term input / output codes beside ordinary grid indices. */
+#define GSCL_VALUE 254 /* in: the operator's returned value at the core element; out: a term of that value */
+#define GSCL_NONE 255  /* coef: no coefficient grid */
+#define GSCL_MAX_TERMS 64
+#define GSCL_MAX_IN 8
+#define GSCL_MAX_OUT 3
+#define GSCL_MAX_HALO 4
+
+/*
+ * One term of a stencil operator (Section 3: an operator reads elements of
+ * several grids at fixed offsets from the core element and may write the
+ * core element of its output grids; it may also return a value):
+ *
+ *   out == m (0 <= m < n_out):  out_m(p)  += w * X * C
+ *   out == GSCL_VALUE:          value(p)  += w * X * C
+ *
+ * with X = in_grid[in](p + (dx,dy,dz)), or X = value(p) when in == GSCL_VALUE
+ * (then the offset must be 0 and out must be an output index), and
+ * C = in_grid[coef](p) (coefficient read at the core element) or 1 when
+ * coef == GSCL_NONE.  value(p) is formed from its terms before any output,
+ * so a term of an output may use it: that is how two operators share one
+ * scan (the paper's fuse(), Section 5.2).  Terms may be given in any order;
+ * the sum over an output's terms is evaluated in an unspecified order with
+ * fused multiply-adds in the grids' arithmetic type.
+ */
+typedef struct gscl_term {
+  int8_t dx, dy, dz;
+  uint8_t in, coef, out;
+  uint16_t reserved; /* must be 0 */
+  double w;
+} gscl_term;
+
+typedef struct gscl_stencil {
+  int32_t n_terms;          /* 1 .. GSCL_MAX_TERMS */
+  int32_t reserved;         /* must be 0 */
+  const gscl_term *terms;   /* host memory, read during the call only */
+} gscl_stencil;
+
+/* Iteration range in interior coordinates, half-open [lo, hi) per axis
+ * (x, y, z).  For a 2D grid the z range must be [0, 1). */
+typedef struct gscl_range {
+  int64_t lo[3], hi[3];
+} gscl_range;
+
+/* Layout facts of a grid handle. */
+typedef struct gscl_grid_desc {
+  int32_t ndim;
+  int32_t dtype;
+  int64_t n[3];            /* interior points per axis x, y, z (z = 1 in 2D) */
+  int32_t halo[3];         /* halo per axis (z halo 0 in 2D) */
+  int32_t elem_bytes;
+  int64_t pitch_elems;     /* row pitch */
+  int64_t offset_elems;    /* leading pad so interior element (0,0,0) is 128-byte aligned */
+  int64_t plane_elems;     /* pitch * (n[1] + 2 halo[1]) */
+  int64_t bytes;           /* storage size */
+  void *dev_buf;           /* borrowed device buffer */
+} gscl_grid_desc;
+
+/*
+ * Storage layout of a grid (x fastest; a 2D grid has nz = 1, hz = 0):
+ *   element (i, j, k), -h <= index < n + h per axis, is at element
+ *   offset_elems + ((k + hz) * (ny + 2hy) + (j + hy)) * pitch_elems + (i + hx)
+ * of the buffer.  pitch_elems is a multiple of 128 bytes and offset_elems
+ * makes interior element (0,0,0) 128-byte aligned, so tiles of interior
+ * rows can be moved with TMA and 16-byte vectors.
+ *
+ * gscl_grid_layout computes the layout without creating anything.  Every
+ * output pointer is required.  Errors: GSCL_ERR_INVALID for ndim not 2 or
+ * 3, n < 1, halo < 0 or > GSCL_MAX_HALO, a non-zero z halo or nz != 1 in
+ * 2D, an unknown dtype.
+ */
+gscl_status gscl_grid_layout(int32_t ndim, const int64_t n[3], const int32_t halo[3], int32_t dtype,
+                             int64_t *pitch_elems, int64_t *offset_elems, int64_t *bytes);
+
+/*
+ * Wraps a caller-owned device buffer of at least the layout's `bytes` as a
+ * grid.  The buffer must be 128-byte aligned (GSCL_ERR_INVALID otherwise);
+ * buf_bytes smaller than the layout gives GSCL_ERR_OOM.  The handle borrows
+ * the buffer: destroying the handle does not free it.  Contents are not
+ * touched.
+ */
+gscl_status gscl_grid_create(int32_t ndim, const int64_t n[3], const int32_t halo[3], int32_t dtype,
+                             void *dev_buf, int64_t buf_bytes, gscl_grid *out);
+
+/* Releases a handle (not its buffer).  GSCL_ERR_STATE for an unknown handle. */
+gscl_status gscl_grid_destroy(gscl_grid g);
+
+/* Fills *out with the handle's layout and current buffer (which gscl_swap
+ * and multi-sweep gscl_do_all may exchange between handles). */
+gscl_status gscl_grid_info(gscl_grid g, gscl_grid_desc *out);
+
+/*
+ * Copies between a dense host array and the grid, halo included.  The host
+ * array has (nz + 2hz) x (ny + 2hy) x (nx + 2hx) elements of the grid's dtype,
+ * x fastest.  Asynchronous on `stream` (pinned host memory makes it truly
+ * so); the host array must stay valid until the stream reaches the copy.
+ */
+gscl_status gscl_grid_copy_from_host(gscl_grid g, const void *host, void *stream);
+gscl_status gscl_grid_copy_to_host(gscl_grid g, void *host, void *stream);
+
+/*
+ * Exchanges the storage of two grids of identical layout (Section 5.2,
+ * swap_grids): O(1), no data moves, halos travel with their storage.  The
+ * handle values stay where they are; what each names is exchanged.
+ * GSCL_ERR_SHAPE if the layouts differ.  Not stream-ordered: the caller
+ * swaps between enqueued sweeps, as with any pointer exchange.
+ */
+gscl_status gscl_swap(gscl_grid *a, gscl_grid *b);
+
+/*
+ * do_all (Section 3): applies the operator at every core element of `range`
+ * (NULL = the whole interior) reading grids in[0..n_in) and writing
+ * out[0..n_out) at the core elements only.  Halos are never written.
+ *
+ *  - All grids share ndim, interior extent and dtype (GSCL_ERR_SHAPE /
+ *    GSCL_ERR_DTYPE); halos may differ per grid, and every read p + offset
+ *    must stay inside the read grid's halo for every p in the range
+ *    (GSCL_ERR_RANGE).
+ *  - do_all promises no order (Section 3), so an output grid that is also an
+ *    input may be read only at offset 0 (GSCL_ERR_ALIAS otherwise), and no
+ *    grid may be an output twice.
+ *  - 1 <= n_in <= GSCL_MAX_IN, 1 <= n_out <= GSCL_MAX_OUT,
+ *    n_terms <= GSCL_MAX_TERMS (GSCL_ERR_UNSUPPORTED beyond).
+ *  - sweeps >= 1.  sweeps > 1 repeats the operator with in[0] and out[0] as
+ *    a ping-pong pair (identical layouts, GSCL_ERR_SHAPE otherwise; they
+ *    must hold identical halos, which travel with their storage): sweep s
+ *    reads the previous sweep's result in place of in[0].  On return out[0]
+ *    names the result of the last sweep and in[0] an earlier iterate (the
+ *    two handles may have exchanged storage, as by gscl_swap).
+ *  - An empty range enqueues nothing.
+ */
+gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                        int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream);
+
+/* Bytes of device workspace one gscl_do_reduce call needs (a constant). */
+int64_t gscl_reduce_workspace_bytes(void);
+
+/*
+ * do_reduce (Section 3): runs the operator like gscl_do_all (outputs, if
+ * n_out > 0, are written exactly as do_all writes them: the fused operator
+ * of Section 5.2) and reduces its returned value over the range with `op`.
+ * op == NULL reduces in[0] itself (n_out must be 0); otherwise the operator
+ * needs at least one term with out == GSCL_VALUE.
+ *
+ *  - result: one double.  result_on_host = 0: a device pointer, written
+ *    asynchronously.  result_on_host = 1: a host pointer; the call copies the
+ *    value back and synchronises `stream` before returning.
+ *  - workspace: device memory of gscl_reduce_workspace_bytes() bytes, zero
+ *    before its first use; every call leaves it ready for the next.  Calls
+ *    that may overlap on the GPU (different streams) need separate
+ *    workspaces.  GSCL_ERR_OOM if workspace_bytes is too small.
+ *  - Accumulation is FP64 for every dtype: SUM and L2 are compensated across
+ *    z-steps, threads and CTAs, and combined in a fixed order, so a given
+ *    launch configuration gives bit-identical results run to run.  An empty
+ *    range gives 0.
+ */
+gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                           const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
+                           int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
+ * Waits for `stream` and reports device-side failures of the library's
+ * kernels enqueued on this device since the last gscl_sync: GSCL_ERR_TIMEOUT
+ * if a bounded wait inside a kernel gave up, GSCL_ERR_CUDA for a CUDA error.
+ * Clears the device-side flag.
+ */
+gscl_status gscl_sync(void *stream);
+
+/* Static English description of a status code. */
+const char *gscl_status_str(gscl_status s);
+
+/* Detail of the most recent failing call on this host thread ("" if none). */
+const char *gscl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GSCL_H */

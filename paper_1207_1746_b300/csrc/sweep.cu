@@ -1,0 +1,358 @@
+// Host side of do_all / do_reduce: validation of the operator against the
+// grids (Section 3's rules: reads only at fixed offsets inside the stencil
+// shape's halo, writes only at the core element, no order promised),
+// launch planning and the C ABI entry points.
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "sweep_kernel.cuh"
+
+namespace gscl {
+
+namespace {
+
+struct Bound {
+  const gscl_stencil *op = nullptr;
+  std::vector<Grid> in, out;
+  std::vector<gscl_grid> in_h, out_h;
+  int64_t lo[3], hi[3];
+  bool empty = false;
+};
+
+bool overlaps(const Grid &a, const Grid &b) { return a.buf < b.buf + b.bytes && b.buf < a.buf + a.bytes; }
+
+// Validates handles, shapes, dtypes, the range, every term and aliasing.
+gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                 int32_t n_out, const gscl_range *range, Bound *b) {
+  if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
+  if (n_out < 0 || n_out > kMaxOut) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut);
+  if (!in || (n_out > 0 && !out)) return fail(GSCL_ERR_INVALID, "grid arrays are required");
+  b->op = op;
+  b->in.resize(n_in);
+  b->out.resize(n_out);
+  for (int a = 0; a < n_in; ++a) {
+    if (gscl_status s = lookup(in[a], &b->in[a])) return s;
+    b->in_h.push_back(in[a]);
+  }
+  for (int m = 0; m < n_out; ++m) {
+    if (gscl_status s = lookup(out[m], &b->out[m])) return s;
+    b->out_h.push_back(out[m]);
+  }
+  const Grid &g0 = b->in[0];
+  int dev = -1;
+  cudaGetDevice(&dev);
+  auto check_same = [&](const Grid &g) -> gscl_status {
+    if (g.device != dev) return fail(GSCL_ERR_INVALID, "grid lives on device %d, current device is %d", g.device, dev);
+    if (g.dtype != g0.dtype) return fail(GSCL_ERR_DTYPE, "grids of one call must share a dtype");
+    if (g.ndim != g0.ndim || g.n[0] != g0.n[0] || g.n[1] != g0.n[1] || g.n[2] != g0.n[2])
+      return fail(GSCL_ERR_SHAPE, "grids of one call must share ndim and interior extent");
+    return GSCL_OK;
+  };
+  for (auto &g : b->in)
+    if (gscl_status s = check_same(g)) return s;
+  for (auto &g : b->out)
+    if (gscl_status s = check_same(g)) return s;
+  for (int a = 0; a < 3; ++a) {
+    b->lo[a] = range ? range->lo[a] : 0;
+    b->hi[a] = range ? range->hi[a] : g0.n[a];
+    if (b->lo[a] < 0 || b->hi[a] > g0.n[a] || b->lo[a] > b->hi[a])
+      return fail(GSCL_ERR_RANGE, "range [%lld, %lld) on axis %d outside the interior [0, %lld)", (long long)b->lo[a],
+                  (long long)b->hi[a], a, (long long)g0.n[a]);
+    if (b->lo[a] == b->hi[a]) b->empty = true;
+  }
+  for (int m = 0; m < n_out; ++m)
+    for (int m2 = 0; m2 < m; ++m2)
+      if (overlaps(b->out[m], b->out[m2])) return fail(GSCL_ERR_ALIAS, "outputs %d and %d share storage", m2, m);
+  if (!op) {
+    if (!need_value) return fail(GSCL_ERR_INVALID, "do_all needs an operator");
+    if (n_out != 0) return fail(GSCL_ERR_INVALID, "reducing in[0] itself writes no output");
+    return GSCL_OK;
+  }
+  if (op->reserved != 0) return fail(GSCL_ERR_INVALID, "stencil reserved field must be 0");
+  if (op->n_terms < 1 || op->n_terms > kMaxTerms)
+    return fail(GSCL_ERR_UNSUPPORTED, "n_terms = %d outside [1, %d]", op->n_terms, kMaxTerms);
+  if (!op->terms) return fail(GSCL_ERR_INVALID, "terms is NULL");
+  bool has_value = false;
+  for (int t = 0; t < op->n_terms; ++t) {
+    const gscl_term &tm = op->terms[t];
+    if (tm.reserved != 0) return fail(GSCL_ERR_INVALID, "term %d: reserved field must be 0", t);
+    if (tm.out != GSCL_VALUE && tm.out >= n_out)
+      return fail(GSCL_ERR_INVALID, "term %d writes output %d of %d", t, tm.out, n_out);
+    if (tm.out == GSCL_VALUE) has_value = true;
+    if (tm.coef != GSCL_NONE && tm.coef >= n_in)
+      return fail(GSCL_ERR_INVALID, "term %d: coefficient grid %d of %d", t, tm.coef, n_in);
+    if (tm.in == GSCL_VALUE) {
+      if (tm.dx || tm.dy || tm.dz) return fail(GSCL_ERR_INVALID, "term %d reads the value at a non-zero offset", t);
+      if (tm.out == GSCL_VALUE) return fail(GSCL_ERR_INVALID, "term %d: the value cannot feed itself", t);
+      continue;
+    }
+    if (tm.in >= n_in) return fail(GSCL_ERR_INVALID, "term %d reads input %d of %d", t, tm.in, n_in);
+    const Grid &g = b->in[tm.in];
+    const int d[3] = {tm.dx, tm.dy, tm.dz};
+    for (int a = 0; a < 3; ++a) {
+      if (abs(d[a]) > GSCL_MAX_HALO) return fail(GSCL_ERR_RANGE, "term %d: offset %d beyond the maximum halo", t, d[a]);
+      if (b->empty) continue;
+      if (b->lo[a] + d[a] < -(int64_t)g.halo[a] || b->hi[a] - 1 + d[a] > g.n[a] - 1 + g.halo[a])
+        return fail(GSCL_ERR_RANGE, "term %d reads input %d at offset %d on axis %d, outside its halo %d", t, tm.in,
+                    d[a], a, g.halo[a]);
+    }
+  }
+  if (need_value && !has_value) return fail(GSCL_ERR_INVALID, "do_reduce needs a term with out == GSCL_VALUE");
+  // an output may also be an input only if every read of it is at offset 0
+  for (int m = 0; m < n_out; ++m)
+    for (int a = 0; a < n_in; ++a) {
+      if (!overlaps(b->out[m], b->in[a])) continue;
+      for (int t = 0; t < op->n_terms; ++t) {
+        const gscl_term &tm = op->terms[t];
+        if (tm.in == a && (tm.dx || tm.dy || tm.dz))
+          return fail(GSCL_ERR_ALIAS, "output %d is input %d, read at a non-zero offset by term %d", m, a, t);
+      }
+    }
+  return GSCL_OK;
+}
+
+struct Plan {
+  SweepParams P;
+  int threads = 0;
+  int ctas = 0;
+  size_t smem = 0;
+};
+
+// Columns per thread: TX = 32 * VX.
+int vx_for(int dtype) { return dtype == GSCL_F64 ? 2 : 4; }
+
+gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
+  SweepParams &P = pl->P;
+  memset(&P, 0, sizeof P);
+  const Grid &g0 = b.in[0];
+  const int n_in = (int)b.in.size(), n_out = (int)b.out.size();
+  const int elem = g0.elem;
+  const int VX = vx_for(g0.dtype);
+  const int TX = 32 * VX;
+  std::vector<gscl_term> terms;
+  if (b.op) {
+    terms.assign(b.op->terms, b.op->terms + b.op->n_terms);
+  } else {
+    gscl_term id = {0, 0, 0, 0, GSCL_NONE, GSCL_VALUE, 0, 1.0};
+    terms.push_back(id);
+  }
+  int rx = 0, ry = 0, rz = 0;  // radii over every grid read
+  for (auto &t : terms) {
+    if (t.in == GSCL_VALUE) continue;
+    rx = std::max(rx, abs((int)t.dx));
+    ry = std::max(ry, abs((int)t.dy));
+    rz = std::max(rz, abs((int)t.dz));
+  }
+  const int vec = 16 / elem;  // TMA x coordinates stay multiples of 16 bytes
+  const int AX = (rx + vec - 1) / vec * vec;
+  const int BW = TX + 2 * AX;
+  const int nz_range = (int)(b.hi[2] - b.lo[2]);
+  const int smem_cap = max_smem_per_block();
+  int TY = 8, PF = nz_range > 1 ? 2 : 0;
+  size_t smem = 0;
+  int R = 0, SE = 0, BH = 0;
+  for (;;) {
+    BH = TY + 2 * ry;
+    const int slot_bytes = (BW * BH * elem + 127) / 128 * 128;
+    SE = slot_bytes / elem;
+    R = 2 * rz + 1 + PF;
+    smem = kBarBytes + (size_t)n_in * R * slot_bytes;
+    if (smem <= (size_t)smem_cap && R <= kMaxRing) break;
+    if (PF > 1) --PF;
+    else if (TY > 2) TY /= 2;
+    else return fail(GSCL_ERR_UNSUPPORTED, "operator needs %zu bytes of shared memory per CTA", smem);
+  }
+  if (BW > 256 || BH > 256) return fail(GSCL_ERR_UNSUPPORTED, "tile box too large for TMA");
+  int nt = 0;
+  auto push = [&](const gscl_term &t) {
+    DevTerm &d = P.terms[nt++];
+    d.in = t.in == GSCL_VALUE ? -1 : (int16_t)t.in;
+    d.coef = t.coef == GSCL_NONE ? -1 : (int16_t)t.coef;
+    d.dz = t.dz;
+    d.toff = (ry + t.dy) * BW + AX + t.dx;
+    d.wf = (float)t.w;
+    d.wd = t.w;
+  };
+  for (auto &t : terms)
+    if (t.out == GSCL_VALUE) push(t);
+  P.n_value_terms = nt;
+  for (int m = 0; m < n_out; ++m) {
+    P.out_begin[m] = nt;
+    for (auto &t : terms)
+      if (t.out == m) push(t);
+  }
+  P.out_begin[n_out] = nt;
+  P.n_in = n_in;
+  P.n_out = n_out;
+  for (int m = 0; m < n_out; ++m) {
+    const Grid &g = b.out[m];
+    P.out[m].base = g.elem_ptr(0, 0, 0);
+    P.out[m].pitch = g.pitch;
+    P.out[m].plane = g.plane;
+  }
+  for (int a = 0; a < n_in; ++a) {
+    const Grid &g = b.in[a];
+    if (gscl_status s = encode_tensor_map_3d(&P.tmap[a], g, (uint32_t)BW, (uint32_t)BH)) return s;
+    P.cx_add[a] = (int32_t)(g.halo[0] + g.off);
+    P.cy_add[a] = g.halo[1];
+    P.cz_add[a] = g.halo[2];
+  }
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = b.lo[a];
+    P.hi[a] = b.hi[a];
+  }
+  P.x_base = b.lo[0] / TX * TX;
+  P.y_base = b.lo[1];
+  P.tiles_x = (int32_t)((b.hi[0] - P.x_base + TX - 1) / TX);
+  P.tiles_y = (int32_t)((b.hi[1] - b.lo[1] + TY - 1) / TY);
+  // z chunks: enough CTAs to fill every SM a few times over, while keeping
+  // the re-read halo planes of each chunk a small share
+  const int threads = 32 * TY;
+  int per_sm = std::min(2048 / threads, (int)(228 * 1024 / (smem + 1024)));
+  per_sm = std::max(per_sm, 1);
+  const long long target = (long long)sm_count() * per_sm * 2;
+  const long long txy = (long long)P.tiles_x * P.tiles_y;
+  long long zchunks = std::max(1LL, std::min((long long)nz_range, (target + txy - 1) / txy));
+  int zc_len = (int)((nz_range + zchunks - 1) / zchunks);
+  zc_len = std::max(zc_len, std::min(nz_range, 4 * rz + 4));
+  zchunks = (nz_range + zc_len - 1) / zc_len;
+  P.zchunks = (int32_t)zchunks;
+  P.zc_len = zc_len;
+  P.R = R;
+  P.rz = rz;
+  P.BW = BW;
+  P.BH = BH;
+  P.AX = AX;
+  P.RY = ry;
+  P.slot_elems = SE;
+  P.center = ry * BW + AX;
+  P.tx_bytes = (uint32_t)(n_in * BW * BH * elem);
+  P.err = device_error_word();
+  if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
+  const long long n_tiles = txy * zchunks;
+  pl->threads = threads;
+  pl->smem = smem;
+  pl->ctas = (int)std::min<long long>(n_tiles, reduce ? kMaxReduceCtas : 0x7fffffffLL);
+  return GSCL_OK;
+}
+
+template <typename T, int VX, int RED>
+gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
+  auto kern = sweep_kernel<T, VX, RED>;
+  static std::mutex mu;
+  static size_t attr_set = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (pl.smem > attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      attr_set = pl.smem;
+    }
+  }
+  kern<<<pl.ctas, pl.threads, pl.smem, stream>>>(pl.P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+  return GSCL_OK;
+}
+
+template <typename T, int VX>
+gscl_status launch_red(const Plan &pl, int red, cudaStream_t stream) {
+  switch (red) {
+    case RED_NONE: return launch_t<T, VX, RED_NONE>(pl, stream);
+    case RED_SUM: return launch_t<T, VX, RED_SUM>(pl, stream);
+    case RED_MAXABS: return launch_t<T, VX, RED_MAXABS>(pl, stream);
+    case RED_L2: return launch_t<T, VX, RED_L2>(pl, stream);
+  }
+  return fail(GSCL_ERR_INVALID, "unknown reduction");
+}
+
+gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream) {
+  switch (dtype) {
+    case GSCL_F64: return launch_red<double, 2>(pl, red, stream);
+    case GSCL_F32: return launch_red<float, 4>(pl, red, stream);
+    case GSCL_BF16: return launch_red<__nv_bfloat16, 4>(pl, red, stream);
+  }
+  return fail(GSCL_ERR_DTYPE, "unknown dtype");
+}
+
+}  // namespace
+}  // namespace gscl
+
+using namespace gscl;
+
+extern "C" {
+
+int64_t gscl_reduce_workspace_bytes(void) { return kWorkspaceBytes; }
+
+gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                        int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream) {
+  if (sweeps < 1) return fail(GSCL_ERR_INVALID, "sweeps must be >= 1");
+  if (n_out < 1) return fail(GSCL_ERR_INVALID, "do_all needs at least one output");
+  Bound b;
+  if (gscl_status s = bind(op, false, in, n_in, out, n_out, range, &b)) return s;
+  if (b.empty) return GSCL_OK;
+  if (sweeps > 1) {
+    const Grid &a = b.in[0], &c = b.out[0];
+    if (a.halo[0] != c.halo[0] || a.halo[1] != c.halo[1] || a.halo[2] != c.halo[2])
+      return fail(GSCL_ERR_SHAPE, "multi-sweep ping-pong needs in[0] and out[0] of identical layout");
+    if (overlaps(a, c)) return fail(GSCL_ERR_ALIAS, "multi-sweep ping-pong needs distinct in[0] and out[0]");
+  }
+  Grid src = b.in[0], dst = b.out[0];
+  for (int s = 0; s < sweeps; ++s) {
+    b.in[0] = src;
+    b.out[0] = dst;
+    for (size_t a = 1; a < b.in.size(); ++a)  // another input naming the ping-pong grid follows it
+      if (b.in_h[a] == b.in_h[0]) b.in[a] = src;
+    Plan pl;
+    if (gscl_status st = make_plan(b, false, &pl)) return st;
+    if (gscl_status st = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream)) return st;
+    std::swap(src, dst);
+  }
+  if (sweeps > 1 && sweeps % 2 == 0) return swap_storage(in[0], out[0]);
+  return GSCL_OK;
+}
+
+gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                           const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
+                           int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream) {
+  int red;
+  switch (reduce_op) {
+    case GSCL_SUM: red = RED_SUM; break;
+    case GSCL_MAXABS: red = RED_MAXABS; break;
+    case GSCL_L2: red = RED_L2; break;
+    default: return fail(GSCL_ERR_INVALID, "unknown reduce op %d", reduce_op);
+  }
+  if (!result) return fail(GSCL_ERR_INVALID, "result is NULL");
+  if (!workspace) return fail(GSCL_ERR_INVALID, "workspace is NULL");
+  if (((uintptr_t)workspace) % 16) return fail(GSCL_ERR_INVALID, "workspace must be 16-byte aligned");
+  if (workspace_bytes < kWorkspaceBytes)
+    return fail(GSCL_ERR_OOM, "workspace has %lld bytes, needs %lld", (long long)workspace_bytes,
+                (long long)kWorkspaceBytes);
+  Bound b;
+  if (gscl_status s = bind(op, true, in, n_in, out, n_out, range, &b)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *dev_result = result_on_host ? reinterpret_cast<double *>((char *)workspace + 8) : result;
+  if (b.empty) {
+    cudaError_t e = cudaMemsetAsync(dev_result, 0, sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  } else {
+    Plan pl;
+    if (gscl_status s = make_plan(b, true, &pl)) return s;
+    pl.P.workspace = (unsigned char *)workspace;
+    pl.P.result = dev_result;
+    if (gscl_status s = launch(pl, b.in[0].dtype, red, st)) return s;
+  }
+  if (result_on_host) {
+    cudaError_t e = cudaMemcpyAsync(result, dev_result, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  }
+  return GSCL_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,420 @@
+// Device side of the do_all / do_reduce sweep (Section 3 iteration spaces).
+//
+// One kernel serves every dtype, operator and grid shape.  A CTA owns an
+// xy tile of TX x TY core elements (TX = 32 * VX, one warp per tile row,
+// lane l of a warp computing x = l, l + 32, ..., so every shared-memory read
+// of a term is 32 consecutive elements: conflict-free) and streams along z
+// through a chunk of planes (2.5D blocking).  For every input grid it keeps
+// a ring of R plane boxes of (TX + 2 AX) x (TY + 2 RY) elements in shared
+// memory, filled by TMA (cp.async.bulk.tensor) from HBM ahead of use and
+// completed on one mbarrier per ring slot; R = 2 rz + 1 + prefetch.  Each
+// input is therefore read from HBM once per sweep (plus the halo overlap
+// between tiles, which L2 absorbs), outputs are written once with coalesced
+// stores, and the operator's returned value is reduced in registers without
+// touching memory (fused sweep + reduce).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "gscl_internal.h"
+
+namespace gscl {
+
+constexpr int kMaxTerms = GSCL_MAX_TERMS;
+constexpr int kMaxIn = GSCL_MAX_IN;
+constexpr int kMaxOut = GSCL_MAX_OUT;
+constexpr int kBarBytes = 256;                   // up to 32 ring-slot mbarriers
+constexpr int kMaxRing = kBarBytes / 8;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
+constexpr int kMaxReduceCtas = 65536;
+constexpr int64_t kWorkspaceBytes = 256 + 16LL * kMaxReduceCtas;
+
+enum RedKind { RED_NONE = 0, RED_SUM = 1, RED_MAXABS = 2, RED_L2 = 3 };
+
+// A term as the kernel sees it: ring indices instead of grid ids, and the
+// read offset pre-folded into an element offset inside one ring slot.
+struct DevTerm {
+  int16_t in;    // input ring, or -1: the operator's value
+  int16_t coef;  // input ring of the coefficient, or -1
+  int16_t dz;
+  int16_t pad;
+  int32_t toff;  // (RY + dy) * BW + AX + dx
+  float wf;
+  double wd;
+};
+
+struct OutDesc {
+  char *base;     // address of interior element (0,0,0)
+  int64_t pitch;  // elements
+  int64_t plane;  // elements
+};
+
+struct SweepParams {
+  CUtensorMap tmap[kMaxIn];
+  DevTerm terms[kMaxTerms];
+  OutDesc out[kMaxOut];
+  int64_t lo[3], hi[3];
+  int64_t x_base, y_base;
+  int32_t tiles_x, tiles_y, zchunks, zc_len;
+  int32_t n_in, n_out, n_value_terms;
+  int32_t out_begin[kMaxOut + 1];
+  int32_t R, rz;
+  int32_t BW, BH, AX, RY;
+  int32_t slot_elems;
+  int32_t center;     // RY * BW + AX
+  uint32_t tx_bytes;  // bytes one plane delivers over all inputs
+  int32_t cx_add[kMaxIn], cy_add[kMaxIn], cz_add[kMaxIn];
+  unsigned char *workspace;  // reduce: ticket at +0, partials at +256
+  double *result;            // reduce: where the last CTA writes the value
+  int *err;                  // device error word
+};
+
+template <typename T> struct Arith;
+template <> struct Arith<double> { using A = double; };
+template <> struct Arith<float> { using A = float; };
+template <> struct Arith<__nv_bfloat16> { using A = float; };
+
+__device__ __forceinline__ double to_arith(double x) { return x; }
+__device__ __forceinline__ float to_arith(float x) { return x; }
+__device__ __forceinline__ float to_arith(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename T> __device__ __forceinline__ T from_arith(typename Arith<T>::A x);
+template <> __device__ __forceinline__ double from_arith<double>(double x) { return x; }
+template <> __device__ __forceinline__ float from_arith<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_arith<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+__device__ __forceinline__ double term_weight(const DevTerm &t, double) { return t.wd; }
+__device__ __forceinline__ float term_weight(const DevTerm &t, float) { return t.wf; }
+
+// ------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for the phase with the given parity to complete; gives up after
+// kWaitCycles and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// --------------------------------------------------------------- reduction
+// FP64 accumulation of the per-element values.  Within one z-step a thread
+// first adds its VX values in plain FP64, then folds that group sum into a
+// Kahan-compensated running sum (s, c) whose true value is s - c; threads
+// and CTAs are merged with Knuth's error-free TwoSum so the compensation
+// survives the tree.
+struct Compensated {
+  double s = 0.0, c = 0.0;
+  __device__ __forceinline__ void add(double x) {
+    const double y = x - c;
+    const double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+};
+
+// (s, c) += (s2, c2) for values s - c and s2 - c2.
+__device__ __forceinline__ void combine_pair(double &s, double &c, double s2, double c2) {
+  const double t = s + s2;
+  const double bp = t - s;
+  const double err = (s - (t - bp)) + (s2 - bp);  // t + err == s + s2 exactly
+  s = t;
+  c = (c + c2) - err;
+}
+
+__device__ __forceinline__ double max_abs_bits(double a, double b) {
+  return __longlong_as_double(
+      (long long)max((unsigned long long)__double_as_longlong(a), (unsigned long long)__double_as_longlong(b)));
+}
+
+// |v| as the bits of a double: for non-negative doubles the unsigned order of
+// the bits is the numeric order, and every NaN sorts above +inf.
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ unsigned long long abs_bits(float v) { return abs_bits((double)v); }
+
+// ---------------------------------------------------------------- one term
+template <typename T, int VX>
+__device__ __forceinline__ void add_term(const DevTerm &tm, const T *ring, int smod, int R, int SE, int thr, int center,
+                                         const typename Arith<T>::A (&v)[VX], typename Arith<T>::A (&acc)[VX]) {
+  using A = typename Arith<T>::A;
+  const A w = term_weight(tm, A(0));
+  A x[VX];
+  if (tm.in < 0) {
+#pragma unroll
+    for (int e = 0; e < VX; ++e) x[e] = v[e];
+  } else {
+    int slot = smod + tm.dz;
+    slot = slot >= R ? slot - R : (slot < 0 ? slot + R : slot);
+    const T *p = ring + (tm.in * R + slot) * SE + tm.toff + thr;
+#pragma unroll
+    for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
+  }
+  if (tm.coef >= 0) {
+    const T *cp = ring + (tm.coef * R + smod) * SE + center + thr;
+#pragma unroll
+    for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
+  }
+#pragma unroll
+  for (int e = 0; e < VX; ++e) acc[e] = fma(w, x[e], acc[e]);
+}
+
+// ---------------------------------------------------------------- kernel
+template <typename T, int VX, int RED>
+__global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ SweepParams P) {
+  using A = typename Arith<T>::A;
+  constexpr int TX = 32 * VX;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+  T *ring = reinterpret_cast<T *>(smem + kBarBytes);
+  __shared__ int s_abort;
+  __shared__ bool s_last;
+  __shared__ double s_red[2 * 16];
+
+  const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
+  const int TY = blockDim.x >> 5;
+  const int R = P.R, rz = P.rz, SE = P.slot_elems;
+  const int thr = wy * P.BW + lane;
+
+  if (tid == 0) {
+    for (int r = 0; r < R; ++r) mbar_init(&bars[r], 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+
+  Compensated acc;
+  unsigned long long maxbits = 0;
+  uint32_t seq = 0;         // planes issued by this CTA (identical in every thread)
+  uint32_t issued_end = 0;  // thread 0: planes actually issued
+  uint32_t waited_end = 0;  // planes this thread has waited for
+  bool ok = true;
+
+  const long long n_tiles = (long long)P.tiles_x * P.tiles_y * P.zchunks;
+  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    const int txi = (int)(tile % P.tiles_x);
+    const long long rest = tile / P.tiles_x;
+    const int tyi = (int)(rest % P.tiles_y);
+    const int zci = (int)(rest / P.tiles_y);
+    const int64_t x0 = P.x_base + (int64_t)txi * TX;
+    const int64_t y0 = P.y_base + (int64_t)tyi * TY;
+    const int64_t zb = P.lo[2] + (int64_t)zci * P.zc_len;
+    const int64_t ze = min(zb + (int64_t)P.zc_len, P.hi[2]);
+    const int zlen = (int)(ze - zb);
+    const int total = zlen + 2 * rz;
+    const uint32_t g0 = seq;
+    seq += total;
+
+    // plane q of this tile (z = zb - rz + q) goes to ring slot (g0 + q) % R
+    auto issue = [&](int q) {
+      const uint32_t g = g0 + q;
+      const int slot = (int)(g % (uint32_t)R);
+      uint64_t *bar = &bars[slot];
+      mbar_arrive_expect_tx(bar, P.tx_bytes);
+      const int zp = (int)(zb - rz + q);
+      for (int a = 0; a < P.n_in; ++a)
+        tma_load_3d(ring + (a * R + slot) * SE, &P.tmap[a], bar, (int)(x0 - P.AX) + P.cx_add[a],
+                    (int)(y0 - P.RY) + P.cy_add[a], zp + P.cz_add[a]);
+      issued_end = g + 1;
+    };
+    auto wait = [&](int q) {
+      const uint32_t g = g0 + q;
+      if (!mbar_wait_bounded(&bars[g % (uint32_t)R], (g / (uint32_t)R) & 1u)) return false;
+      waited_end = g + 1;
+      return true;
+    };
+
+    if (tid == 0) {
+      const int np = min(R, total);
+      for (int q = 0; q < np; ++q) issue(q);
+    }
+
+    const int64_t y = y0 + wy;
+    const bool yok = (y >= P.lo[1]) && (y < P.hi[1]);
+    bool xok[VX];
+#pragma unroll
+    for (int e = 0; e < VX; ++e) {
+      const int64_t x = x0 + lane + 32 * e;
+      xok[e] = (x >= P.lo[0]) && (x < P.hi[0]);
+    }
+    int smod = (int)((g0 + (uint32_t)rz) % (uint32_t)R);
+
+    for (int s = 0; s < zlen; ++s) {
+      if (ok) {
+        if (s == 0) {
+          for (int d = 0; d <= 2 * rz && ok; ++d) ok = wait(d);
+        } else {
+          ok = wait(s + 2 * rz);
+        }
+        if (!ok) {
+          s_abort = 1;
+          atomicOr(P.err, 1);
+        }
+      }
+      if (ok) {
+        const int64_t z = zb + s;
+        A v[VX];
+#pragma unroll
+        for (int e = 0; e < VX; ++e) v[e] = A(0);
+        for (int t = 0; t < P.n_value_terms; ++t) add_term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, v);
+        for (int m = 0; m < P.n_out; ++m) {
+          A o[VX];
+#pragma unroll
+          for (int e = 0; e < VX; ++e) o[e] = A(0);
+          for (int t = P.out_begin[m]; t < P.out_begin[m + 1]; ++t)
+            add_term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, o);
+          if (yok) {
+            T *dst = reinterpret_cast<T *>(P.out[m].base) + z * P.out[m].plane + y * P.out[m].pitch + x0 + lane;
+#pragma unroll
+            for (int e = 0; e < VX; ++e)
+              if (xok[e]) dst[32 * e] = from_arith<T>(o[e]);
+          }
+        }
+        if (RED != RED_NONE && yok) {
+          if (RED == RED_MAXABS) {
+#pragma unroll
+            for (int e = 0; e < VX; ++e)
+              if (xok[e]) maxbits = max(maxbits, abs_bits(v[e]));
+          } else {
+            double gsum = 0.0;
+#pragma unroll
+            for (int e = 0; e < VX; ++e) {
+              if (xok[e]) {
+                const double d = (double)v[e];
+                gsum = (RED == RED_L2) ? fma(d, d, gsum) : gsum + d;
+              }
+            }
+            acc.add(gsum);
+          }
+        }
+      }
+      smod = smod + 1 == R ? 0 : smod + 1;
+      __syncthreads();
+      if (s_abort) break;
+      if (tid == 0 && s + R < total) issue(s + R);
+    }
+    if (s_abort) break;
+  }
+
+  if (s_abort) {
+    // a wait gave up: let every copy this CTA issued land before exiting
+    if (tid == 0)
+      for (uint32_t g = waited_end; g < issued_end; ++g)
+        mbar_wait_bounded(&bars[g % (uint32_t)R], (g / (uint32_t)R) & 1u);
+    __syncthreads();
+    return;
+  }
+
+  if (RED == RED_NONE) return;
+
+  // ---- block reduction (fixed shuffle tree), then the last CTA folds all
+  double s = 0.0, c = 0.0;
+  if (RED == RED_MAXABS) {
+    s = __longlong_as_double((long long)maxbits);
+  } else {
+    s = acc.s;
+    c = acc.c;
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
+    else combine_pair(s, c, s2, c2);
+  }
+  if (lane == 0) {
+    s_red[2 * wy] = s;
+    s_red[2 * wy + 1] = c;
+  }
+  __syncthreads();
+  unsigned int *ticket = reinterpret_cast<unsigned int *>(P.workspace);
+  double *partials = reinterpret_cast<double *>(P.workspace + 256);
+  if (tid == 0) {
+    double bs = s_red[0], bc = s_red[1];
+    for (int w = 1; w < TY; ++w) {
+      if (RED == RED_MAXABS) bs = max_abs_bits(bs, s_red[2 * w]);
+      else combine_pair(bs, bc, s_red[2 * w], s_red[2 * w + 1]);
+    }
+    partials[2 * blockIdx.x] = bs;
+    partials[2 * blockIdx.x + 1] = bc;
+    __threadfence();
+    const unsigned int prev = atomicAdd(ticket, 1u);
+    s_last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  // last CTA: thread i folds a fixed contiguous chunk of partials, then the
+  // fixed shuffle tree and thread 0 fold the threads in order.
+  const int G = gridDim.x;
+  const int chunk = (G + blockDim.x - 1) / blockDim.x;
+  s = 0.0;
+  c = 0.0;
+  for (int b = tid * chunk; b < min(G, (tid + 1) * chunk); ++b) {
+    const double ps = __ldcg(&partials[2 * b]);
+    const double pc = __ldcg(&partials[2 * b + 1]);
+    if (RED == RED_MAXABS) s = max_abs_bits(s, ps);
+    else combine_pair(s, c, ps, pc);
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
+    else combine_pair(s, c, s2, c2);
+  }
+  __syncthreads();
+  if (lane == 0) {
+    s_red[2 * wy] = s;
+    s_red[2 * wy + 1] = c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double bs = s_red[0], bc = s_red[1];
+    for (int w = 1; w < TY; ++w) {
+      if (RED == RED_MAXABS) bs = max_abs_bits(bs, s_red[2 * w]);
+      else combine_pair(bs, bc, s_red[2 * w], s_red[2 * w + 1]);
+    }
+    double r;
+    if (RED == RED_MAXABS) r = bs;
+    else if (RED == RED_L2) r = sqrt(bs - bc);
+    else r = bs - bc;
+    *P.result = r;
+    *ticket = 0u;  // ready for the next call
+  }
+}
+
+}  // namespace gscl
