@@ -1,0 +1,295 @@
+"""ctypes binding of libgscl.so (include/gscl.h): argument marshalling only.
+
+Every sweep and reduction runs in the library's CUDA kernels; PyTorch only
+supplies device memory (grid buffers, reduction workspaces) and streams.
+There is no fallback: if the library is missing or a call fails, an
+exception is raised.
+
+Terms are tuples ``(dx, dy, dz, in, coef, out, w)`` (Section 3: an operator
+reads fixed offsets of its input grids around the core element, writes the
+core element of its outputs and may return a value); ``VALUE`` as ``in``
+reads the operator's value, as ``out`` adds to it; ``NONE`` as ``coef``
+means no coefficient grid.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+VALUE = 254
+NONE = 255
+F64, F32, BF16 = 0, 1, 2
+SUM, MAXABS, L2 = 0, 1, 2
+
+_DTYPES = {
+    "f64": (F64, torch.float64, 8),
+    "f32": (F32, torch.float32, 4),
+    "bf16": (BF16, torch.bfloat16, 2),
+}
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gscl.h")
+
+
+class Term(ctypes.Structure):
+    _fields_ = [("dx", ctypes.c_int8), ("dy", ctypes.c_int8), ("dz", ctypes.c_int8),
+                ("in_", ctypes.c_uint8), ("coef", ctypes.c_uint8), ("out", ctypes.c_uint8),
+                ("reserved", ctypes.c_uint16), ("w", ctypes.c_double)]
+
+
+class StencilC(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("terms", ctypes.POINTER(Term))]
+
+
+class RangeC(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_int64 * 3), ("hi", ctypes.c_int64 * 3)]
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32), ("n", ctypes.c_int64 * 3),
+                ("halo", ctypes.c_int32 * 3), ("elem_bytes", ctypes.c_int32),
+                ("pitch_elems", ctypes.c_int64), ("offset_elems", ctypes.c_int64),
+                ("plane_elems", ctypes.c_int64), ("bytes", ctypes.c_int64), ("dev_buf", ctypes.c_void_p)]
+
+
+class GsclError(RuntimeError):
+    def __init__(self, status, detail):
+        self.status = status
+        super().__init__(f"gscl status {status}: {detail}")
+
+
+_lib = None
+
+
+def declared_symbols():
+    """Names of the functions include/gscl.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(gscl_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """Loads libgscl.so (building it first if its sources are newer)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    P, i32, i64, vp = ctypes.POINTER, ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+    u64 = ctypes.c_uint64
+    sig = {
+        "gscl_grid_layout": [i32, P(i64), P(i32), i32, P(i64), P(i64), P(i64)],
+        "gscl_grid_create": [i32, P(i64), P(i32), i32, vp, i64, P(u64)],
+        "gscl_grid_destroy": [u64],
+        "gscl_grid_info": [u64, P(GridDesc)],
+        "gscl_grid_copy_from_host": [u64, vp, vp],
+        "gscl_grid_copy_to_host": [u64, vp, vp],
+        "gscl_swap": [P(u64), P(u64)],
+        "gscl_do_all": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), i32, vp],
+        "gscl_do_reduce": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double), i32,
+                           vp, i64, vp],
+        "gscl_sync": [vp],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.gscl_reduce_workspace_bytes.argtypes = []
+    L.gscl_reduce_workspace_bytes.restype = ctypes.c_int64
+    L.gscl_status_str.argtypes = [ctypes.c_int]
+    L.gscl_status_str.restype = ctypes.c_char_p
+    L.gscl_last_error.argtypes = []
+    L.gscl_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def check(status):
+    if status != 0:
+        L = lib()
+        raise GsclError(status, f"{L.gscl_status_str(status).decode()}: {L.gscl_last_error().decode()}")
+
+
+def stream_ptr(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Stencil:
+    """A stencil operator marshalled once for repeated calls."""
+
+    def __init__(self, terms):
+        self.terms = [tuple(t) for t in terms]
+        arr = (Term * max(1, len(self.terms)))()
+        for i, (dx, dy, dz, a, c, m, w) in enumerate(self.terms):
+            arr[i] = Term(int(dx), int(dy), int(dz), int(a), int(c), int(m), 0, float(w))
+        self._arr = arr
+        self.c = StencilC(len(self.terms), 0, ctypes.cast(arr, ctypes.POINTER(Term)))
+
+
+def as_stencil(op):
+    if op is None or isinstance(op, Stencil):
+        return op
+    return Stencil(op)
+
+
+def layout(n, halo, dtype="f64", ndim=3):
+    p, o, b = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    check(lib().gscl_grid_layout(ndim, (ctypes.c_int64 * 3)(*n), (ctypes.c_int32 * 3)(*halo),
+                                 _DTYPES[dtype][0], ctypes.byref(p), ctypes.byref(o), ctypes.byref(b)))
+    return p.value, o.value, b.value
+
+
+class Grid:
+    """A device grid: a torch-allocated buffer wrapped by a library handle.
+
+    ``n = (nx, ny, nz)`` interior points, ``halo = (hx, hy, hz)``; a 2D grid has
+    ``nz = 1, hz = 0`` and ``ndim = 2``."""
+
+    def __init__(self, n, halo, dtype="f64", ndim=None, device=None):
+        n = tuple(int(v) for v in n)
+        halo = tuple(int(v) for v in halo)
+        if ndim is None:
+            ndim = 2 if (n[2] == 1 and halo[2] == 0) else 3
+        self.n, self.halo, self.dtype, self.ndim = n, halo, dtype, ndim
+        self.pitch, self.off, self.bytes = layout(n, halo, dtype, ndim)
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.buf = torch.empty(self.bytes, dtype=torch.uint8, device=dev)
+        h = ctypes.c_uint64()
+        check(lib().gscl_grid_create(ndim, (ctypes.c_int64 * 3)(*n), (ctypes.c_int32 * 3)(*halo),
+                                     _DTYPES[dtype][0], ctypes.c_void_p(self.buf.data_ptr()), self.bytes,
+                                     ctypes.byref(h)))
+        self.handle = h.value
+
+    def __del__(self):
+        h = getattr(self, "handle", 0)
+        if h and _lib is not None:
+            _lib.gscl_grid_destroy(h)
+            self.handle = 0
+
+    @property
+    def padded_shape(self):
+        nx, ny, nz = self.n
+        hx, hy, hz = self.halo
+        return (nz + 2 * hz, ny + 2 * hy, nx + 2 * hx)
+
+    @property
+    def torch_dtype(self):
+        return _DTYPES[self.dtype][1]
+
+    def info(self):
+        d = GridDesc()
+        check(lib().gscl_grid_info(self.handle, ctypes.byref(d)))
+        return d
+
+    def view(self):
+        """Strided torch view (halo included) of the storage this handle names now."""
+        Z, Y, X = self.padded_shape
+        t = self.buf.view(self.torch_dtype)
+        return t.as_strided((Z, Y, X), (self.pitch * Y, self.pitch, 1), self.off)
+
+    def interior(self):
+        nx, ny, nz = self.n
+        hx, hy, hz = self.halo
+        return self.view()[hz:hz + nz, hy:hy + ny, hx:hx + nx]
+
+    def upload(self, host, stream=None):
+        """Copies a dense host array (halo included) through gscl_grid_copy_from_host."""
+        t = host if isinstance(host, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(host))
+        t = t.to(self.torch_dtype).contiguous()
+        if tuple(t.shape) != self.padded_shape:
+            raise ValueError(f"host array shape {tuple(t.shape)} != {self.padded_shape}")
+        check(lib().gscl_grid_copy_from_host(self.handle, ctypes.c_void_p(t.data_ptr()), stream_ptr(stream)))
+        (stream or torch.cuda.current_stream()).synchronize()
+        return self
+
+    def download(self, stream=None) -> torch.Tensor:
+        """Dense host copy (halo included) through gscl_grid_copy_to_host."""
+        t = torch.empty(self.padded_shape, dtype=self.torch_dtype)
+        check(lib().gscl_grid_copy_to_host(self.handle, ctypes.c_void_p(t.data_ptr()), stream_ptr(stream)))
+        (stream or torch.cuda.current_stream()).synchronize()
+        return t
+
+
+def _resync(grids):
+    """After the library exchanged storage between handles, make each Python
+    Grid hold the torch buffer its handle now names."""
+    by_ptr = {g.buf.data_ptr(): g.buf for g in grids}
+    want = [(g, g.info().dev_buf) for g in grids]
+    for g, ptr in want:
+        if ptr != g.buf.data_ptr():
+            g.buf = by_ptr[ptr]
+
+
+def swap(a: Grid, b: Grid):
+    """Section 5.2's swap_grids: exchanges the storage the two handles name."""
+    ha, hb = ctypes.c_uint64(a.handle), ctypes.c_uint64(b.handle)
+    check(lib().gscl_swap(ctypes.byref(ha), ctypes.byref(hb)))
+    a.buf, b.buf = b.buf, a.buf
+
+
+def _range(rng):
+    if rng is None:
+        return None
+    lo, hi = rng
+    return ctypes.byref(RangeC((ctypes.c_int64 * 3)(*lo), (ctypes.c_int64 * 3)(*hi)))
+
+
+def _handles(grids):
+    return (ctypes.c_uint64 * max(1, len(grids)))(*[g.handle for g in grids])
+
+
+def do_all(op, ins, outs, rng=None, sweeps=1, stream=None):
+    """gscl_do_all: applies the operator over the range (Section 3, do_all)."""
+    st = as_stencil(op)
+    check(lib().gscl_do_all(ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
+                            _range(rng), int(sweeps), stream_ptr(stream)))
+    if sweeps > 1:
+        _resync([ins[0], outs[0]])
+
+
+_workspaces = {}
+
+
+def workspace(stream=None):
+    """A zeroed reduction workspace per (device, stream)."""
+    s = stream or torch.cuda.current_stream()
+    key = (s.device.index, s.cuda_stream)
+    ws = _workspaces.get(key)
+    if ws is None:
+        ws = torch.zeros(lib().gscl_reduce_workspace_bytes(), dtype=torch.uint8, device=s.device)
+        _workspaces[key] = ws
+    return ws
+
+
+def do_reduce(reduce_op, op, ins, outs=(), rng=None, result=None, stream=None):
+    """gscl_do_reduce: reduces the operator's returned value (Section 3, do_reduce).
+
+    ``result`` None: returns the value as a Python float (the call syncs).
+    ``result`` a one-element float64 CUDA tensor (or a slice of one): written
+    asynchronously, and the call returns None."""
+    st = as_stencil(op)
+    ws = workspace(stream)
+    on_host = result is None
+    if on_host:
+        host = ctypes.c_double(0.0)
+        rptr = ctypes.pointer(host)
+    else:
+        if result.dtype != torch.float64 or not result.is_cuda:
+            raise ValueError("result must be a float64 CUDA tensor")
+        rptr = ctypes.cast(ctypes.c_void_p(result.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    check(lib().gscl_do_reduce(int(reduce_op), ctypes.byref(st.c) if st is not None else None, _handles(ins),
+                               len(ins), _handles(outs), len(outs), _range(rng), rptr, int(on_host),
+                               ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream_ptr(stream)))
+    return host.value if on_host else None
+
+
+def sync(stream=None):
+    """gscl_sync: waits for the stream and reports device-side timeouts."""
+    check(lib().gscl_sync(stream_ptr(stream)))

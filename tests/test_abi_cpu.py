@@ -1,0 +1,165 @@
+"""CPU-only checks of the C ABI: the library loads, exports every symbol the
+header declares, and its host-side layout and validation logic behave as
+documented.  No call here touches a GPU."""
+import ctypes
+
+import pytest
+
+from paper_1207_1746_b300 import binding as B
+
+
+@pytest.fixture(scope="module")
+def L():
+    return B.lib()
+
+
+def test_exports_every_declared_symbol(L):
+    names = B.declared_symbols()
+    assert "gscl_do_all" in names and "gscl_do_reduce" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+@pytest.mark.parametrize("dtype,elem", [("f64", 8), ("f32", 4), ("bf16", 2)])
+@pytest.mark.parametrize("n,halo,ndim", [((256, 256, 256), (1, 1, 1), 3), ((17, 13, 11), (2, 2, 1), 3),
+                                         ((256, 256, 1), (1, 1, 0), 2), ((1, 1, 1), (0, 0, 0), 3),
+                                         ((33, 7, 5), (4, 3, 2), 3)])
+def test_layout_alignment(dtype, elem, n, halo, ndim):
+    pitch, off, nbytes = B.layout(n, halo, dtype, ndim)
+    assert (pitch * elem) % 128 == 0
+    assert ((off + halo[0]) * elem) % 128 == 0
+    assert pitch >= off + n[0] + 2 * halo[0]
+    assert pitch - (off + n[0] + 2 * halo[0]) < 128 // elem
+    assert nbytes == pitch * (n[1] + 2 * halo[1]) * (n[2] + 2 * halo[2]) * elem
+
+
+@pytest.mark.parametrize("args", [
+    (4, (8, 8, 8), (1, 1, 1), "f64"),
+    (3, (0, 8, 8), (1, 1, 1), "f64"),
+    (3, (8, 8, 8), (5, 1, 1), "f64"),
+    (2, (8, 8, 2), (1, 1, 0), "f64"),
+    (2, (8, 8, 1), (1, 1, 1), "f64"),
+])
+def test_layout_rejects_bad_shapes(args):
+    ndim, n, halo, dtype = args
+    with pytest.raises(B.GsclError) as e:
+        B.layout(n, halo, dtype, ndim)
+    assert e.value.status == 1
+
+
+class FakeGrid:
+    """A handle over a fake (never dereferenced) aligned address: enough to
+    exercise host-side validation without a GPU."""
+    _next = 1 << 20
+
+    def __init__(self, n, halo, dtype="f64", ndim=3):
+        _, _, nbytes = B.layout(n, halo, dtype, ndim)
+        FakeGrid._next += (nbytes + 4095) // 4096 * 4096 + 4096
+        h = ctypes.c_uint64()
+        B.check(B.lib().gscl_grid_create(ndim, (ctypes.c_int64 * 3)(*n), (ctypes.c_int32 * 3)(*halo),
+                                         B._DTYPES[dtype][0], ctypes.c_void_p(FakeGrid._next), nbytes,
+                                         ctypes.byref(h)))
+        self.handle = h.value
+
+
+def do_all_status(terms, ins, outs, rng=None, sweeps=1):
+    st = B.Stencil(terms)
+    return B.lib().gscl_do_all(ctypes.byref(st.c), B._handles(ins), len(ins), B._handles(outs), len(outs),
+                               B._range(rng), sweeps, None)
+
+
+def test_handles_create_destroy_stale(L):
+    g = FakeGrid((8, 8, 8), (1, 1, 1))
+    d = B.GridDesc()
+    assert L.gscl_grid_info(g.handle, ctypes.byref(d)) == 0
+    assert d.n[0] == 8 and d.halo[2] == 1
+    assert L.gscl_grid_destroy(g.handle) == 0
+    assert L.gscl_grid_destroy(g.handle) == 8          # GSCL_ERR_STATE
+    assert L.gscl_grid_info(g.handle, ctypes.byref(d)) == 8
+    g2 = FakeGrid((8, 8, 8), (1, 1, 1))                 # reuses the slot, new generation
+    assert g2.handle != g.handle
+    assert L.gscl_grid_info(g.handle, ctypes.byref(d)) == 8
+    assert L.gscl_grid_info(0, ctypes.byref(d)) == 8
+
+
+def test_create_rejects_misaligned_and_small_buffers(L):
+    n, halo = (8, 8, 8), (1, 1, 1)
+    _, _, nbytes = B.layout(n, halo)
+    h = ctypes.c_uint64()
+    args = (3, (ctypes.c_int64 * 3)(*n), (ctypes.c_int32 * 3)(*halo), 0)
+    assert L.gscl_grid_create(*args, ctypes.c_void_p(0x10040), nbytes, ctypes.byref(h)) == 1
+    assert L.gscl_grid_create(*args, ctypes.c_void_p(0x10000), nbytes - 1, ctypes.byref(h)) == 6
+
+
+def test_swap_exchanges_storage_and_checks_layout(L):
+    a, b = FakeGrid((8, 8, 8), (1, 1, 1)), FakeGrid((8, 8, 8), (1, 1, 1))
+    c = FakeGrid((8, 8, 9), (1, 1, 1))
+    da, db = B.GridDesc(), B.GridDesc()
+    L.gscl_grid_info(a.handle, ctypes.byref(da))
+    L.gscl_grid_info(b.handle, ctypes.byref(db))
+    pa, pb = da.dev_buf, db.dev_buf
+    ha, hb, hc = ctypes.c_uint64(a.handle), ctypes.c_uint64(b.handle), ctypes.c_uint64(c.handle)
+    assert L.gscl_swap(ctypes.byref(ha), ctypes.byref(hb)) == 0
+    L.gscl_grid_info(a.handle, ctypes.byref(da))
+    assert da.dev_buf == pb
+    assert L.gscl_swap(ctypes.byref(ha), ctypes.byref(hb)) == 0
+    L.gscl_grid_info(a.handle, ctypes.byref(da))
+    assert da.dev_buf == pa                             # swap twice == identity
+    assert L.gscl_swap(ctypes.byref(ha), ctypes.byref(hc)) == 5   # GSCL_ERR_SHAPE
+
+
+def test_do_all_validation_errors():
+    u, v = FakeGrid((16, 8, 8), (1, 1, 1)), FakeGrid((16, 8, 8), (1, 1, 1))
+    w2 = FakeGrid((16, 8, 8), (2, 2, 1))
+    f32 = FakeGrid((16, 8, 8), (1, 1, 1), "f32")
+    other = FakeGrid((16, 8, 7), (1, 1, 1))
+    ok_terms = [(1, 0, 0, 0, B.NONE, 0, 1.0)]
+    # read beyond the halo
+    assert do_all_status([(2, 0, 0, 0, B.NONE, 0, 1.0)], [u], [v]) == 2
+    # ... allowed when read from a grid with a wider halo
+    assert do_all_status([(2, 0, 0, 0, B.NONE, 0, 1.0)], [w2], [v]) != 2
+    # range outside the interior
+    assert do_all_status(ok_terms, [u], [v], rng=((0, 0, 0), (17, 8, 8))) == 2
+    # output read at a non-zero offset (do_all promises no order)
+    assert do_all_status(ok_terms, [u], [u]) == 3
+    # the same output twice
+    assert do_all_status([(0, 0, 0, 0, B.NONE, 0, 1.0), (0, 0, 0, 0, B.NONE, 1, 1.0)], [u], [v, v]) == 3
+    # dtype and shape mismatch
+    assert do_all_status(ok_terms, [u], [f32]) == 4
+    assert do_all_status(ok_terms, [u], [other]) == 5
+    # bad codes
+    assert do_all_status([(0, 0, 0, 3, B.NONE, 0, 1.0)], [u], [v]) == 1
+    assert do_all_status([(0, 0, 0, 0, B.NONE, 2, 1.0)], [u], [v]) == 1
+    assert do_all_status([(1, 0, 0, B.VALUE, B.NONE, 0, 1.0)], [u], [v]) == 1
+    assert do_all_status([(0, 0, 0, 0, 5, 0, 1.0)], [u], [v]) == 1
+    assert do_all_status(ok_terms, [u], [v], sweeps=0) == 1
+    # too many terms
+    assert do_all_status([(0, 0, 0, 0, B.NONE, 0, 1.0)] * 65, [u], [v]) == 10
+    # stale handle
+    B.lib().gscl_grid_destroy(v.handle)
+    assert do_all_status(ok_terms, [u], [v]) == 8
+    # an empty range is accepted and enqueues nothing (no GPU needed)
+    assert do_all_status(ok_terms, [u], [w2], rng=((0, 0, 3), (16, 8, 3))) == 0
+
+
+def test_reduce_validation_errors():
+    u = FakeGrid((16, 8, 8), (1, 1, 1))
+    L = B.lib()
+    res = ctypes.c_double()
+    st = B.Stencil([(0, 0, 0, 0, B.NONE, 0, 1.0)])  # no value term
+    ws = ctypes.c_void_p(1 << 30)
+
+    def args(op, wsb):
+        return (op, ctypes.byref(st.c), B._handles([u]), 1, B._handles([u]), 1, None,
+                ctypes.byref(res), 1, ws, wsb, None)
+
+    assert L.gscl_do_reduce(*args(7, 1 << 22)) == 1
+    assert L.gscl_do_reduce(*args(0, 16)) == 6
+    assert L.gscl_do_reduce(*args(0, 1 << 22)) == 1
+    assert L.gscl_reduce_workspace_bytes() >= 256
+
+
+def test_status_strings(L):
+    for s in range(11):
+        assert L.gscl_status_str(s)
+    assert b"unknown" in L.gscl_status_str(99)

@@ -1,0 +1,282 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bit-exact where the arithmetic is exact (integer data, dyadic weights: every
+partial sum is representable, so any summation order and FMA give the same
+bits), element-wise tolerances otherwise: |gpu - oracle| <= tol * S(p) with
+S(p) the absolute stencil, tol = 1e-13 for FP64 and 2e-6 for FP32 storage."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import TOL, as_storage, assert_within, run_pair
+from oracle import drivers as D
+from oracle import oracle as O
+from paper_1207_1746_b300 import binding as B
+from paper_1207_1746_b300 import inputs as I
+from paper_1207_1746_b300 import stencils as S
+
+pytestmark = pytest.mark.gpu
+VALUE, NONE = B.VALUE, B.NONE
+
+
+def int_field(rng, shape, lim):
+    return rng.integers(-lim, lim + 1, size=shape).astype(np.float64)
+
+
+def dyadic_terms(rng, n_in, n_out, halos, count, with_value=True, dims=3):
+    weights = [1.0, -1.0, 2.0, -2.0, 0.5, -0.5, 0.25, -0.125]
+    terms = []
+    for _ in range(count):
+        a = int(rng.integers(0, n_in))
+        hx, hy, hz = halos[a]
+        o = [int(rng.integers(-hx, hx + 1)), int(rng.integers(-hy, hy + 1)),
+             int(rng.integers(-hz, hz + 1)) if dims == 3 else 0]
+        c = int(rng.integers(0, n_in)) if rng.random() < 0.3 else NONE
+        m = VALUE if (with_value and rng.random() < 0.3) else int(rng.integers(0, n_out))
+        terms.append((o[0], o[1], o[2], a, c, m, float(rng.choice(weights))))
+    if with_value:
+        terms.append((0, 0, 0, 0, NONE, VALUE, 1.0))
+        terms.append((0, 0, 0, VALUE, NONE, n_out - 1, -0.5))
+    return terms
+
+
+SHAPES = [
+    ((17, 13, 11), [(1, 1, 1), (2, 2, 1), (0, 0, 0)], [(1, 1, 1), (0, 0, 0)]),
+    ((150, 37, 21), [(2, 1, 2), (1, 1, 1), (1, 0, 1)], [(1, 1, 1), (2, 2, 2)]),
+    ((5, 3, 2), [(1, 1, 1), (1, 1, 1), (0, 0, 0)], [(0, 0, 0), (1, 1, 1)]),
+    ((200, 70, 1), [(1, 1, 0), (2, 2, 0), (0, 0, 0)], [(1, 1, 0), (0, 0, 0)]),
+]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("shape_id", range(len(SHAPES)))
+def test_bitexact_random_operator(dtype, shape_id):
+    n, in_halos, out_halos = SHAPES[shape_id]
+    rng = np.random.default_rng(100 + shape_id)
+    dims = 2 if n[2] == 1 else 3
+    arrays = [int_field(rng, I.padded_shape(n, h), 64) for h in in_halos]
+    arrays[2] = int_field(rng, I.padded_shape(n, in_halos[2]), 8)  # coefficient-sized
+    terms = dyadic_terms(rng, 3, 2, in_halos, 14, dims=dims)
+    got, ref, _, _, _ = run_pair(terms, arrays, in_halos, n, out_halos, dtype)
+    for g, r in zip(got, ref):
+        if dtype == "bf16":
+            r = as_storage(r, "bf16")
+        assert np.array_equal(g, r, equal_nan=True)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_bitexact_subrange_and_ragged_edges(dtype):
+    n = (300, 41, 19)
+    halos = [(2, 2, 2), (1, 1, 1)]
+    rng = np.random.default_rng(7)
+    arrays = [int_field(rng, I.padded_shape(n, h), 50) for h in halos]
+    terms = dyadic_terms(rng, 2, 1, halos, 10)
+    for lo, hi in [((3, 1, 2), (141, 40, 17)), ((129, 0, 0), (130, 41, 19)), ((0, 5, 18), (300, 6, 19))]:
+        got, ref, _, _, _ = run_pair(terms, arrays, halos, n, [(1, 1, 1)], dtype, rng=(lo, hi))
+        assert np.array_equal(got[0], ref[0], equal_nan=True)
+
+
+def test_spike_gives_reflected_fig1b_pattern():
+    n, h = (40, 20, 12), (1, 1, 1)
+    a = np.zeros(I.padded_shape(n, h))
+    p0 = (33, 7, 5)
+    a[p0[2] + 1, p0[1] + 1, p0[0] + 1] = 36.0
+    got, ref, _, _, _ = run_pair(S.fig1b(), [a], [h], n, [h], "f64")
+    inner = got[0][1:-1, 1:-1, 1:-1]
+    assert np.array_equal(got[0], ref[0], equal_nan=True)
+    nz = {tuple(int(v) for v in idx): inner[idx] for idx in zip(*np.nonzero(inner))}
+    expect = {(p0[2], p0[1], p0[0]): 6.0}
+    for dx, dy, dz in S.X6:
+        expect[(p0[2] - dz, p0[1] - dy, p0[0] - dx)] = -1.0
+    assert nz == expect
+
+
+@pytest.mark.parametrize("op", [B.SUM, B.MAXABS, B.L2])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_bitexact_reductions_on_integer_data(op, dtype):
+    n = (131, 29, 17)
+    halos = [(1, 1, 1), (1, 1, 1)]
+    rng = np.random.default_rng(11 + op)
+    arrays = [int_field(rng, I.padded_shape(n, h), 40) for h in halos]
+    terms = dyadic_terms(rng, 2, 1, halos, 9)
+    got, ref, gv, ov, _ = run_pair(terms, arrays, halos, n, [(0, 0, 0)], dtype, reduce_op=op)
+    assert np.array_equal(got[0], ref[0], equal_nan=True)
+    assert gv == ov
+    # identity reduction of in[0] over a sub-range
+    _, _, gv, ov, _ = run_pair(None, arrays[:1], halos[:1], n, [], dtype, rng=((5, 2, 1), (120, 29, 16)),
+                               reduce_op=op)
+    assert gv == ov
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_heat_fused_tolerance_random_data(dtype):
+    n, h = (97, 45, 33), (1, 1, 1)
+    u = I.random_interior(5, n, h, -1.0, 1.0)
+    f = I.random_interior(6, n, h, -1.0, 1.0)
+    lam = 0.125
+    got, ref, gv, ov, Sab = run_pair(S.heat7_fused(lam), [u, f], [h, h], n, [h], dtype, reduce_op=B.L2)
+    assert_within(got[0], ref[0], Sab[0], TOL[dtype])
+    assert abs(gv - ov) <= TOL[dtype] * ov
+    # the plain 8-term sweep computes the same update within the same bound
+    got2, _, _, _, Sab2 = run_pair(S.heat7(lam), [u, f], [h, h], n, [h], dtype)
+    assert_within(got2[0], ref[0], Sab[0] + Sab2[0], TOL[dtype])
+
+
+@pytest.mark.parametrize("op", [B.SUM, B.L2])
+def test_reduction_tolerance_random_data(op):
+    n, h = (64, 64, 64), (1, 1, 1)
+    a = I.random_interior(9, n, h, -1.0, 1.0)
+    a += 1e6 * (np.indices(a.shape).sum(axis=0) % 2 - 0.5)  # large cancelling alternation
+    _, _, gv, ov, _ = run_pair(None, [a], [h], n, [], "f64", reduce_op=op)
+    inner = a[1:-1, 1:-1, 1:-1]
+    absum = np.abs(inner).sum() if op == B.SUM else (inner ** 2).sum()
+    # compensated at every level above groups of 2 values: a few ulps of sum |x|
+    bound = 8 * np.finfo(np.float64).eps * absum
+    if op == B.SUM:
+        assert abs(gv - ov) <= bound
+    else:
+        assert abs(gv * gv - ov * ov) <= bound
+
+
+def test_reduction_nan_and_empty_range():
+    n, h = (40, 9, 5), (1, 1, 1)
+    a = I.random_interior(3, n, h, -1.0, 1.0)
+    a[3, 4, 17] = np.nan
+    for op in (B.SUM, B.MAXABS, B.L2):
+        _, _, gv, _, _ = run_pair(None, [a], [h], n, [], "f64", reduce_op=op)
+        assert math.isnan(gv)
+        _, _, gv, ov, _ = run_pair(None, [a], [h], n, [], "f64", rng=((0, 0, 2), (40, 9, 2)), reduce_op=op)
+        assert gv == 0.0 == ov
+
+
+def test_reduction_is_deterministic():
+    n, h = (128, 128, 64), (1, 1, 1)
+    a = I.random_interior(21, n, h, -1.0, 1.0)
+    g = B.Grid(n, h).upload(a)
+    vals = {B.do_reduce(B.SUM, None, [g]) for _ in range(4)}
+    assert len(vals) == 1
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_multisweep_equals_single_sweeps_and_swaps(dtype):
+    n, h = (70, 33, 26), (1, 1, 1)
+    u0 = I.random_interior(31, n, h, -1.0, 1.0, halo_value=0.25)
+    f = I.random_interior(32, n, h, -1.0, 1.0)
+    op = B.Stencil(S.heat7(0.125))
+    F = B.Grid(n, h, dtype).upload(f)
+    for k in (1, 2, 5):
+        a, b = B.Grid(n, h, dtype).upload(u0), B.Grid(n, h, dtype).upload(u0)
+        B.do_all(op, [a, F], [b], sweeps=k)
+        multi = b.download()
+        c, d = B.Grid(n, h, dtype).upload(u0), B.Grid(n, h, dtype).upload(u0)
+        for _ in range(k):
+            B.do_all(op, [c, F], [d])
+            B.swap(c, d)
+        assert torch.equal(multi, c.download())
+
+
+def test_laplace2d_100_sweeps_full_size():
+    """The 2D Laplace workload at its full size (256 x 256, 100 sweeps)."""
+    u0 = I.laplace2d(101, 256)
+    n, h = (256, 256, 1), (1, 1, 0)
+    a, b = B.Grid(n, h).upload(u0), B.Grid(n, h).upload(u0)
+    B.do_all(S.jacobi5_2d(), [a], [b], sweeps=99)       # b = u_99
+    B.do_all(S.jacobi5_2d(), [b], [a])                  # a = u_100
+    res = B.do_reduce(B.MAXABS, S.difference(), [a, b])
+    ou, op, ores = D.jacobi2d_run(O.Grid(u0.copy(), h), 100)
+    scale = np.max(np.abs(ou.a))
+    assert np.max(np.abs(a.download().numpy() - ou.a)) <= 1e-13 * scale
+    assert np.max(np.abs(b.download().numpy() - op.a)) <= 1e-13 * scale
+    assert abs(res - ores) <= 1e-13 * scale
+
+
+def run_heat(u0, f, n, dtype, lam, sweeps, every):
+    """Heat/damped-Jacobi loop: every `every` sweeps a fused do_reduce returns the
+    residual of the iterate it reads; plain multi-sweep do_all in between."""
+    h = (1, 1, 1)
+    u, v = B.Grid(n, h, dtype).upload(u0), B.Grid(n, h, dtype).upload(u0)
+    F = B.Grid(n, h, dtype).upload(f)
+    fused, plain = B.Stencil(S.heat7_fused(lam)), B.Stencil(S.heat7(lam))
+    res = torch.zeros(sweeps // every, dtype=torch.float64, device="cuda")
+    for m in range(sweeps // every):
+        B.do_reduce(B.L2, fused, [u, F], [v], result=res[m:m + 1])
+        B.swap(u, v)
+        B.do_all(plain, [u, F], [v], sweeps=every - 1)
+        B.swap(u, v)
+    B.sync()
+    return u.download().double().numpy(), res.cpu().numpy()
+
+
+def test_heat3d_multisweep_small_with_residuals():
+    n, h = (32, 32, 32), (1, 1, 1)
+    u0, f = I.heat3d(202, 32)
+    lam = 0.125
+    res = run_heat(u0, f, n, "f64", lam, 40, 10)
+    ou, ores = D.heat_run(O.Grid(u0.copy(), h), O.Grid(f.copy(), h), lam, 40, every=10)
+    assert np.max(np.abs(res[0] - ou.a)) <= 1e-13 * np.max(np.abs(ou.a))
+    assert np.allclose(res[1], ores, rtol=1e-13, atol=0)
+    r32 = run_heat(u0, f, n, "f32", lam, 40, 10)
+    assert np.max(np.abs(r32[0] - ou.a)) <= 1e-5 * np.max(np.abs(ou.a))
+    assert np.allclose(r32[1], ores, rtol=1e-5, atol=0)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_heat3d_full_size_one_fused_sweep_after_nine(dtype):
+    """256^3 at the benchmark's launch configuration: nine sweeps, then the
+    fused sweep + residual checked point by point against the oracle run from
+    the GPU's own ninth iterate."""
+    n, h = (256, 256, 256), (1, 1, 1)
+    u0, f = I.heat3d(202, 256)
+    lam = 0.125
+    u, v = B.Grid(n, h, dtype).upload(u0), B.Grid(n, h, dtype).upload(u0)
+    F = B.Grid(n, h, dtype).upload(f)
+    r0 = B.do_reduce(B.L2, S.heat7_fused(lam), [u, F], [v])
+    B.swap(u, v)
+    B.do_all(S.heat7(lam), [u, F], [v], sweeps=8)
+    B.swap(u, v)
+    r9 = B.do_reduce(B.L2, S.heat7_fused(lam), [u, F], [v])
+    u9 = u.download().double().numpy()
+    u10 = v.download().double().numpy()
+    fo = O.Grid(as_storage(f, dtype), h)
+    exact_f = math.sqrt(math.fsum((fo.a ** 2).ravel()))
+    assert abs(r0 - exact_f) <= TOL[dtype] * exact_f
+    out, Sab = O.zeros(n, h), O.zeros(n, h)
+    ores = O.do_reduce(O.L2, D.heat_terms(lam), [O.Grid(u9, h), fo], [out])
+    O.do_all(D.heat_terms(lam), [O.Grid(u9, h), fo], [Sab], abs_mode=True)
+    assert abs(r9 - ores) <= TOL[dtype] * ores
+    m = (slice(1, -1),) * 3
+    assert np.all(np.abs(u10[m] - out.a[m]) <= TOL[dtype] * Sab.a[m])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_climate_multigrid_operator(dtype):
+    n, h = (72, 40, 12), (2, 2, 1)
+    fields = I.climate(303, n, h)
+    arrays = [fields[k] for k in I.CLIMATE_FIELDS]
+    got, ref, _, _, Sab = run_pair(S.climate(), arrays, [h] * 8, n, [h] * 3, dtype)
+    for g, r, s in zip(got, ref, Sab):
+        assert_within(g, r, s, TOL[dtype])
+
+
+def test_climate_full_size_one_sweep():
+    n, h = (256, 256, 80), (2, 2, 1)
+    fields = I.climate(303, n, h)
+    arrays = [fields[k] for k in I.CLIMATE_FIELDS]
+    got, ref, _, _, Sab = run_pair(S.climate(), arrays, [h] * 8, n, [h] * 3, "f64")
+    for g, r, s in zip(got, ref, Sab):
+        assert_within(g, r, s, TOL["f64"])
+
+
+def test_degenerate_single_point_and_zero_halo():
+    n, h = (1, 1, 1), (0, 0, 0)
+    a = np.array([[[3.0]]])
+    got, ref, gv, ov, _ = run_pair([(0, 0, 0, 0, NONE, 0, 2.0), (0, 0, 0, 0, NONE, VALUE, -1.0)], [a], [h], n,
+                                   [h], "f64", reduce_op=B.SUM)
+    assert got[0][0, 0, 0] == 6.0 == ref[0][0, 0, 0]
+    assert gv == -3.0 == ov
+
+
+def test_sync_reports_clean_status():
+    B.sync()
