@@ -1,0 +1,421 @@
+"""Benchmark of the stencil hot path on the 3D heat workload.
+
+Workload (one "step"): the 3D 7-point damped-Jacobi / heat solve on a 256^3
+interior (1-cell zero halo, RHS f uniform in [-1, 1) from seed 202,
+lam = dt*alpha = 1/8), 200 sweeps with ping-pong grids, and every 10 sweeps a
+fused sweep + do_reduce returning the L2 residual of the iterate it reads
+(20 residuals per step).  Primary arithmetic FP64; the FP32-storage variant
+runs in the same invocation and is reported under "variants".
+
+Metric: grid-point updates per second (whole job, all ranks), device-timed
+with CUDA events on the launching stream; the working set (three 137 MB FP64
+grids) is larger than the 126 MB L2.  "e2e" repeats the step through the
+C ABI from pinned host buffers: the H2D copy of u0 and f and the D2H copy of
+the final grid and residuals are inside its timed region.
+
+--impl reference times the FP64 CPU oracle (the plain C loop nest) on a
+bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SIDE = 256
+LAM = 0.125
+SWEEPS = 200
+EVERY = 10
+SEED = 202
+TERMS_PLAIN = 8                # FMAs per point of the plain sweep (one per stencil input)
+BYTES_PER_PT = {"f64": 24, "f32": 12}  # u read, f read, u' written
+
+
+def load_json(path):
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def measured_peaks():
+    return load_json(os.path.join(ROOT, "MEASURED_PEAKS.json"))
+
+
+def profile_traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary (a line
+    'traffic <key> <bytes>' in profiles/sweep_kernel_heat3d_256.md), else None."""
+    path = os.path.join(ROOT, "profiles", "sweep_kernel_heat3d_256.md")
+    try:
+        for line in open(path):
+            parts = line.strip().strip("`").split()
+            if len(parts) == 3 and parts[0] == "traffic" and parts[1] == kernel_key:
+                return float(parts[2])
+    except OSError:
+        pass
+    return None
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a timed region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, val in zip(names, p[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_gpu(dtype, steps, warmup, dist, n=N_SIDE, sweeps=SWEEPS, clocks=None):
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    h = (1, 1, 1)
+    shape = (n, n, n)
+    u0, f = I.heat3d(SEED, n)
+    u, v = B.Grid(shape, h, dtype).upload(u0), B.Grid(shape, h, dtype).upload(u0)
+    F = B.Grid(shape, h, dtype).upload(f)
+    fused, plain = B.Stencil(S.heat7_fused(LAM)), B.Stencil(S.heat7(LAM))
+    groups = sweeps // EVERY
+    res = torch.zeros(groups, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    ev = []
+
+    def step(timed):
+        for m in range(groups):
+            if timed:
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                e[0].record(stream)
+            B.do_reduce(B.L2, fused, [u, F], [v], result=res[m:m + 1])
+            if timed:
+                e[1].record(stream)
+            B.swap(u, v)
+            if timed:
+                e[2].record(stream)
+            B.do_all(plain, [u, F], [v], sweeps=EVERY - 1)
+            if timed:
+                e[3].record(stream)
+                ev.append(e)
+            B.swap(u, v)
+
+    for _ in range(warmup):
+        step(False)
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx = clocks if clocks is not None else _Null()
+    with ctx:
+        t0.record(stream)
+        for _ in range(steps):
+            step(True)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    dist.barrier()
+    B.sync()
+    ms = t0.elapsed_time(t1)
+    fused_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / len(ev)
+    plain_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / (len(ev) * (EVERY - 1))
+    residuals = res.cpu().tolist()
+    return {"ms_total": ms, "ms_per_step": ms / steps, "fused_launch_ms": fused_ms, "plain_launch_ms": plain_ms,
+            "launches": steps * sweeps, "points": n ** 3, "residuals": residuals}
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def run_e2e(dtype, steps, warmup, n=N_SIDE, sweeps=SWEEPS):
+    """The same step through the C ABI from pinned host memory: H2D of u0 and f
+    (gscl_grid_copy_from_host) and D2H of the final grid and the residual
+    vector are inside the timed region."""
+    import numpy as np
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+    import ctypes
+
+    h = (1, 1, 1)
+    shape = (n, n, n)
+    u0, f = I.heat3d(SEED, n)
+    tdt = {"f64": torch.float64, "f32": torch.float32}[dtype]
+    hu0 = torch.from_numpy(u0).to(tdt).pin_memory()
+    hf = torch.from_numpy(f).to(tdt).pin_memory()
+    hout = torch.empty_like(hu0).pin_memory()
+    groups = sweeps // EVERY
+    hres = torch.empty(groups, dtype=torch.float64).pin_memory()
+    u, v, F = B.Grid(shape, h, dtype), B.Grid(shape, h, dtype), B.Grid(shape, h, dtype)
+    fused, plain = B.Stencil(S.heat7_fused(LAM)), B.Stencil(S.heat7(LAM))
+    res = torch.zeros(groups, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = B.stream_ptr(stream)
+    L = B.lib()
+
+    def step():
+        B.check(L.gscl_grid_copy_from_host(u.handle, ctypes.c_void_p(hu0.data_ptr()), sp))
+        B.check(L.gscl_grid_copy_from_host(v.handle, ctypes.c_void_p(hu0.data_ptr()), sp))
+        B.check(L.gscl_grid_copy_from_host(F.handle, ctypes.c_void_p(hf.data_ptr()), sp))
+        for m in range(groups):
+            B.do_reduce(B.L2, fused, [u, F], [v], result=res[m:m + 1])
+            B.swap(u, v)
+            B.do_all(plain, [u, F], [v], sweeps=EVERY - 1)
+            B.swap(u, v)
+        B.check(L.gscl_grid_copy_to_host(u.handle, ctypes.c_void_p(hout.data_ptr()), sp))
+        hres.copy_(res, non_blocking=True)
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for _ in range(steps):
+        step()
+    t1.record(stream)
+    torch.cuda.synchronize()
+    B.sync()
+    ms = t0.elapsed_time(t1) / steps
+    ok = bool(np.all(np.isfinite(hres.numpy())))
+    return {"ms_per_step": ms, "h2d": 3 * hu0.numel() * hu0.element_size(),
+            "d2h": hout.numel() * hout.element_size() + hres.numel() * 8, "finite": ok}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_sample(n=N_SIDE, sweeps=10):
+    """The FP64 oracle as it stands on a bounded sample: one fused sweep +
+    residual and sweeps-1 plain sweeps of the same 256^3 workload."""
+    from oracle import drivers as D
+    from oracle import oracle as O
+    from paper_1207_1746_b300 import inputs as I
+
+    h = (1, 1, 1)
+    u0, f = I.heat3d(SEED, n)
+    a, b, F = O.Grid(u0.copy(), h), O.Grid(u0.copy(), h), O.Grid(f, h)
+    terms = D.heat_terms(LAM)
+    t = time.perf_counter()
+    for s in range(sweeps):
+        if s % EVERY == 0:
+            O.do_reduce(O.L2, terms, [a, F], [b])
+        else:
+            O.do_all(terms, [a, F], [b])
+        a, b = b, a
+    sec = time.perf_counter() - t
+    return {"value": sweeps * n ** 3 / sec / 1e9, "sec": sec, "sweeps": sweeps}
+
+
+# ------------------------------------------------------------------ roofline
+def roofline_fp64(plain_ms, points, peaks, sm_mhz):
+    """FP64 sweeps are bound by the FP64 pipe: 8 FMAs (16 FLOP) per point."""
+    flops = 2.0 * TERMS_PLAIN * points
+    achieved = flops / (plain_ms * 1e-3) / 1e12
+    peak = 148 * 2 * 2 * 2032e6 / 1e12  # SMs x DFMA/clk/SM x FLOP/FMA x max SM clock
+    traffic = profile_traffic("f64_plain")
+    return {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": "derived: 148 SMs x 2 DFMA/clk/SM x 2 FLOP x 2032 MHz",
+            "hbm_gbs": round(BYTES_PER_PT["f64"] * points / (plain_ms * 1e-3) / 1e9, 1),
+            "hbm_frac_of_measured": round(BYTES_PER_PT["f64"] * points / (plain_ms * 1e-3) / 1e9
+                                          / peaks.get("hbm_gbs", 6400.0), 4)}
+
+
+def roofline_hbm(dtype, plain_ms, points, peaks):
+    nbytes = BYTES_PER_PT[dtype] * points
+    achieved = nbytes / (plain_ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs")
+    src = "measured" if peak else "fallback"
+    peak = peak or 6400.0
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profile_traffic(f"{dtype}_plain"),
+            "peak_source": src}
+
+
+# ------------------------------------------------------------------ main
+class _Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group(backend)
+            self.pg = td
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, x):
+        if self.pg is None:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gscl", choices=["gscl", "reference"])
+    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--sweeps", type=int, default=SWEEPS)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
+    args = ap.parse_args()
+    if args.sweeps % EVERY:
+        ap.error("--sweeps must be a multiple of 10")
+    dist = _Dist()
+    workload = (f"heat3d_7pt_{args.n}^3: 3D 7-point damped Jacobi/heat, {args.sweeps} sweeps, "
+                f"ping-pong grids + RHS, lam=1/8, fused L2 residual every {EVERY} sweeps")
+    config = {"workload": workload, "grid": [args.n] * 3, "halo": 1, "sweeps_per_step": args.sweeps,
+              "residual_every": EVERY, "l2": "working set (3 grids) larger than the 126 MB L2, no flush",
+              "parallelism": f"replicas{args.gpus}" if args.gpus > 1 else "single"}
+
+    if args.impl == "reference":
+        dist.init("gloo")
+        if dist.rank != 0:
+            return
+        # a bounded sample per step: one fused and one plain sweep of the 256^3 grid
+        t_all = []
+        for i in range(args.warmup + args.steps):
+            r = oracle_sample(args.n, 2)
+            if i >= args.warmup:
+                t_all.append(r["sec"])
+        sec = sum(t_all) / len(t_all)
+        value = 2 * args.n ** 3 / sec / 1e9
+        line = {"impl": "reference", "metric": "GPoint-updates/s", "value": round(value, 6),
+                "unit": "GPoint-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "cpu_baseline": {"value": round(value, 6), "unit": "GPoint-updates/s", "cores": 1, "kind": "oracle",
+                                 "sample": "per step: 1 fused + 1 plain sweep of the 256^3 grid (of 200)"},
+                "e2e": {"value": round(value, 6), "unit": "GPoint-updates/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    torch.cuda.set_device(dist.local)
+    dist.init("nccl")
+    peaks = measured_peaks()
+    gpu_uuid = torch.cuda.get_device_properties(dist.local).uuid
+    sampler = ClockSampler(f"GPU-{gpu_uuid}")
+    main_run = run_gpu("f64", args.steps, args.warmup, dist, args.n, args.sweeps, clocks=sampler)
+    t_max = dist.max(main_run["ms_total"])
+    updates = dist.world * args.steps * args.sweeps * args.n ** 3
+    value = updates / (t_max * 1e-3) / 1e9
+    clocks = sampler.summary()
+    roof = roofline_fp64(main_run["plain_launch_ms"], args.n ** 3, peaks, clocks.get("sm_mhz"))
+
+    variants = {}
+    if not args.no_variants:
+        r32 = run_gpu("f32", args.steps, args.warmup, dist, args.n, args.sweeps)
+        t32 = dist.max(r32["ms_total"])
+        variants["f32"] = {
+            "dtype": "f32", "value": round(updates / (t32 * 1e-3) / 1e9, 3), "unit": "GPoint-updates/s",
+            "ms_per_step": round(t32 / args.steps, 3),
+            "roofline": roofline_hbm("f32", r32["plain_launch_ms"], args.n ** 3, peaks),
+            "fused_launch_ms": round(r32["fused_launch_ms"], 4), "plain_launch_ms": round(r32["plain_launch_ms"], 4),
+            "final_residual": r32["residuals"][-1]}
+
+    e2e = None
+    if not args.no_e2e:
+        e = run_e2e("f64", max(2, args.steps // 2), 1, args.n, args.sweeps)
+        e_ms = dist.max(e["ms_per_step"])
+        e2e = {"value": round(dist.world * args.sweeps * args.n ** 3 / (e_ms * 1e-3) / 1e9, 3),
+               "unit": "GPoint-updates/s", "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"],
+               "ms_per_step": round(e_ms, 3)}
+
+    cpu = None
+    if dist.rank == 0 and not args.no_cpu:
+        c = oracle_sample(args.n, EVERY)
+        cpu = {"value": round(c["value"], 6), "unit": "GPoint-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{c['sweeps']} sweeps (1 fused + 9 plain) of the 256^3 FP64 grid, {c['sec']:.1f} s"}
+
+    if dist.rank == 0:
+        line = {"metric": "GPoint-updates/s", "value": round(value, 3), "unit": "GPoint-updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+                "roofline": roof, "cpu_baseline": cpu, "clocks": clocks, "e2e": e2e,
+                "gpu_launches": main_run["launches"],
+                "kernel_ms": {"plain_sweep": round(main_run["plain_launch_ms"], 4),
+                              "fused_sweep_l2": round(main_run["fused_launch_ms"], 4)},
+                "final_residual": main_run["residuals"][-1], "variants": variants}
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()
