@@ -234,6 +234,42 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
                            int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
+ * gscl_do_reduce_noalloc -- gscl_do_reduce for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this entry point exists for
+ * the library's users, not for the method.
+ *
+ * Who needs it: programs that give all device memory to their own allocator
+ * at start-up and forbid allocations afterwards (a C or Fortran simulation
+ * code with a fixed memory plan, or a host framework whose memory pool must
+ * not be bypassed, because cudaMalloc and cudaFree synchronise the device
+ * and fragment that pool), and plain C callers that hold their grid buffers
+ * but have no device allocator at hand for a workspace.
+ *
+ * Same arguments and results as gscl_do_reduce without `workspace` /
+ * `workspace_bytes`; same launch configuration, hence the same reduction
+ * order and bit-identical results.  Its scratch (arrival ticket, result slot
+ * and one 16-byte partial per CTA) is a fixed array inside the library of
+ * 256 + 16 * GSCL_NOALLOC_MAX_PARTIALS bytes (131,328 bytes), present on
+ * every GPU that loads the library until the process exits.  Nothing is
+ * allocated by the call (no cudaMalloc, no library allocator).
+ *
+ *  - Limit: a range whose launch needs more than GSCL_NOALLOC_MAX_PARTIALS
+ *    CTAs is rejected with GSCL_ERR_UNSUPPORTED (gscl_last_error gives the
+ *    count); use gscl_do_reduce with a workspace for it.
+ *  - The first call on each device looks up the scratch array's device
+ *    address (with that device current) and caches it; make that first call
+ *    before any stream capture.
+ *  - Every call, on every stream, shares the one array, which keeps the last
+ *    call's contents; each call clears the ticket it needs on its stream.
+ *    Calls that can overlap on the GPU (different streams, or several host
+ *    threads) race on it: keep them on one stream.
+ */
+#define GSCL_NOALLOC_MAX_PARTIALS 8192
+gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                                   const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
+                                   int32_t result_on_host, void *stream);
+
+/*
  * Waits for `stream` and reports device-side failures of the library's
  * kernels enqueued on this device since the last gscl_sync: GSCL_ERR_TIMEOUT
  * if a bounded wait inside a kernel gave up, GSCL_ERR_CUDA for a CUDA error.

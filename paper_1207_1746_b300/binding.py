@@ -94,6 +94,8 @@ def lib():
         "gscl_do_reduce": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double), i32,
                            vp, i64, vp],
         "gscl_sync": [vp],
+        "gscl_do_reduce_noalloc": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double),
+                                   i32, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -287,6 +289,25 @@ def do_reduce(reduce_op, op, ins, outs=(), rng=None, result=None, stream=None):
     check(lib().gscl_do_reduce(int(reduce_op), ctypes.byref(st.c) if st is not None else None, _handles(ins),
                                len(ins), _handles(outs), len(outs), _range(rng), rptr, int(on_host),
                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream_ptr(stream)))
+    return host.value if on_host else None
+
+
+def do_reduce_noalloc(reduce_op, op, ins, outs=(), rng=None, result=None, stream=None):
+    """gscl_do_reduce_noalloc: do_reduce with the library's built-in scratch
+    instead of a workspace, for callers that cannot allocate device memory.
+    Same ``result`` convention as do_reduce."""
+    st = as_stencil(op)
+    on_host = result is None
+    if on_host:
+        host = ctypes.c_double(0.0)
+        rptr = ctypes.pointer(host)
+    else:
+        if result.dtype != torch.float64 or not result.is_cuda:
+            raise ValueError("result must be a float64 CUDA tensor")
+        rptr = ctypes.cast(ctypes.c_void_p(result.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    check(lib().gscl_do_reduce_noalloc(int(reduce_op), ctypes.byref(st.c) if st is not None else None,
+                                       _handles(ins), len(ins), _handles(outs), len(outs), _range(rng), rptr,
+                                       int(on_host), stream_ptr(stream)))
     return host.value if on_host else None
 
 

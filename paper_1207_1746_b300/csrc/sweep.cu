@@ -356,3 +356,87 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
 }
 
 }  // extern "C"
+
+// ===================================================================== no-alloc reduce
+// A do_reduce for callers that cannot hand the library a workspace.  Its
+// scratch (the arrival ticket, the result slot and one partial sum per CTA)
+// lives in the fixed array below instead of caller memory.
+namespace gscl {
+namespace {
+
+constexpr int kNoAllocMaxCtas = GSCL_NOALLOC_MAX_PARTIALS;
+constexpr int64_t kNoAllocScratchBytes = 256 + 16LL * kNoAllocMaxCtas;
+constexpr int kMaxDevices = 64;
+
+// One copy per device that loads the library, zero at load, held until exit.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  The symbol's
+// name in host code is only a handle for the runtime, so the address is
+// asked for once per device, with that device current, and cached.
+gscl_status noalloc_scratch(unsigned char **out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(GSCL_ERR_UNSUPPORTED, "device %d beyond the supported count", dev);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the built-in reduce scratch");
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = (unsigned char *)g_noalloc_ptr[dev];
+  return GSCL_OK;
+}
+
+}  // namespace
+}  // namespace gscl
+
+extern "C" gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in,
+                                              int32_t n_in, const gscl_grid *out, int32_t n_out,
+                                              const gscl_range *range, double *result, int32_t result_on_host,
+                                              void *stream) {
+  int red;
+  switch (reduce_op) {
+    case GSCL_SUM: red = RED_SUM; break;
+    case GSCL_MAXABS: red = RED_MAXABS; break;
+    case GSCL_L2: red = RED_L2; break;
+    default: return fail(GSCL_ERR_INVALID, "unknown reduce op %d", reduce_op);
+  }
+  if (!result) return fail(GSCL_ERR_INVALID, "result is NULL");
+  Bound b;
+  if (gscl_status s = bind(op, true, in, n_in, out, n_out, range, &b)) return s;
+  unsigned char *scratch = nullptr;
+  if (gscl_status s = noalloc_scratch(&scratch)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  double *dev_result = result_on_host ? reinterpret_cast<double *>(scratch + 8) : result;
+  if (b.empty) {
+    cudaError_t e = cudaMemsetAsync(dev_result, 0, sizeof(double), st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+  } else {
+    Plan pl;
+    if (gscl_status s = make_plan(b, true, &pl)) return s;
+    if (pl.ctas > kNoAllocMaxCtas)
+      return fail(GSCL_ERR_UNSUPPORTED,
+                  "this range needs %d partial sums but the built-in scratch of gscl_do_reduce_noalloc holds %d; "
+                  "use gscl_do_reduce with a workspace",
+                  pl.ctas, kNoAllocMaxCtas);
+    // the arrival ticket must start at zero whatever an earlier call left
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    pl.P.workspace = scratch;
+    pl.P.result = dev_result;
+    if (gscl_status s = launch(pl, b.in[0].dtype, red, st)) return s;
+  }
+  if (result_on_host) {
+    cudaError_t e = cudaMemcpyAsync(result, dev_result, sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  }
+  return GSCL_OK;
+}
