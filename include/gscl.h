@@ -207,6 +207,21 @@ gscl_status gscl_swap(gscl_grid *a, gscl_grid *b);
 gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                         int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream);
 
+/*
+ * Which implementation gscl_do_all / gscl_do_reduce pick for this operator
+ * with n_in inputs and n_out outputs.  Section 1 of the paper keeps a generic
+ * implementation of every construct and uses a better-suited one where it
+ * exists; likewise the library runs any operator through a generic kernel
+ * that interprets the term list, and a few operator structures (the 7-point
+ * heat / Jacobi / Poisson / residual operators, the 2D 5-point Jacobi, the
+ * 8-input / 3-output climate operator, differences and identities) through
+ * kernels compiled for that structure, with the weights still taken from the
+ * descriptor.  Returns a non-negative id for a compiled structure, -1 for the
+ * generic kernel.  Host-only; setting the environment variable
+ * GSCL_GENERIC_ONLY=1 makes every call use the generic kernel.
+ */
+int32_t gscl_stencil_specialization(const gscl_stencil *op, int32_t n_in, int32_t n_out);
+
 /* Bytes of device workspace one gscl_do_reduce call needs (a constant). */
 int64_t gscl_reduce_workspace_bytes(void);
 

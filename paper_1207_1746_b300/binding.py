@@ -101,6 +101,8 @@ def lib():
         f = getattr(L, name)
         f.argtypes = args
         f.restype = ctypes.c_int
+    L.gscl_stencil_specialization.argtypes = [P(StencilC), i32, i32]
+    L.gscl_stencil_specialization.restype = i32
     L.gscl_reduce_workspace_bytes.argtypes = []
     L.gscl_reduce_workspace_bytes.restype = ctypes.c_int64
     L.gscl_status_str.argtypes = [ctypes.c_int]
@@ -139,6 +141,12 @@ def as_stencil(op):
     if op is None or isinstance(op, Stencil):
         return op
     return Stencil(op)
+
+
+def specialization(op, n_in, n_out):
+    """Id of the compiled operator structure the library will use, or -1 (generic kernel)."""
+    st = as_stencil(op)
+    return lib().gscl_stencil_specialization(ctypes.byref(st.c), n_in, n_out)
 
 
 def layout(n, halo, dtype="f64", ndim=3):

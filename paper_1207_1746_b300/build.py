@@ -10,6 +10,7 @@ import glob
 import os
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
@@ -20,8 +21,8 @@ NVCC_FLAGS = [
     "-gencode", "arch=compute_103a,code=sm_103a",
     "-O3", "-lineinfo", "-std=c++17",
     "-Xcompiler", "-fPIC,-O2",
-    "-shared", "-cudart", "static",
 ]
+OBJ_DIR = os.path.join(HERE, "_build")
 
 
 def sources():
@@ -41,15 +42,33 @@ def needs_build() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compiles every .cu under csrc/ into one shared library next to this file."""
+    """Compiles every .cu under csrc/ (in parallel) into one shared library next to this file."""
     if not force and not needs_build():
         return LIB
     nvcc = os.environ.get("NVCC", "nvcc")
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-o", tmp, *sources()]
-    if verbose:
-        print(" ".join(cmd), file=sys.stderr)
-    subprocess.check_call(cmd)
+    os.makedirs(OBJ_DIR, exist_ok=True)
+    tag = os.getpid()
+
+    def compile_one(src):
+        obj = os.path.join(OBJ_DIR, os.path.basename(src)[:-3] + f".{tag}.o")
+        cmd = [nvcc, *NVCC_FLAGS, *extra, "-I", INCLUDE, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), file=sys.stderr)
+        out = subprocess.run(cmd, capture_output=True, text=True)
+        if out.returncode != 0:
+            raise RuntimeError(f"nvcc failed on {src}:\n{out.stderr}")
+        if verbose and out.stderr:
+            print(out.stderr, file=sys.stderr)
+        return obj
+
+    srcs = sources()
+    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+        objs = list(ex.map(compile_one, srcs))
+    tmp = LIB + f".tmp{tag}"
+    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "static",
+                           "-o", tmp, *objs])
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -1,0 +1,114 @@
+// Operators whose structure is fixed at compile time.
+//
+// The paper's library keeps a generic implementation of every construct and
+// picks up a better-suited one when it exists (Section 1).  Here the generic
+// implementation is the runtime term loop of sweep_kernel; the operators
+// below are the structures the benchmark workloads use, compiled with every
+// offset, grid and ring position as a constant so that each term costs one
+// shared-memory load and one fused multiply-add per point.  A descriptor
+// matches one of them when its terms have the same (dx, dy, dz, in, coef,
+// out) multiset; the weights stay runtime values.  Host and device share
+// these tables (constexpr).
+#pragma once
+
+namespace gscl {
+
+// in = -1: the operator's value; out = -1: a term of the value; coef = -1: none
+struct OpTerm {
+  int dx, dy, dz, in, coef, out;
+};
+
+template <int N>
+struct TermTable {
+  OpTerm t[N];
+};
+
+enum StaticOpId {
+  OP_GENERIC = -1,
+  OP_HEAT7_RHS = 0,     // u' = w0 u + sum6 w_i u(nbr) + w7 f         (u, f) -> u'
+  OP_STAR7,             // u' = w0 u + sum6 w_i u(nbr)                 (u) -> u'
+  OP_JACOBI7_RHS,       // u' = sum6 w_i u(nbr) + w6 f                 (u, f) -> u'
+  OP_JACOBI5_2D,        // u' = sum4 w_i u(nbr)                        2D (u) -> u'
+  OP_CLIMATE,           // 13-point biharmonic x kappa + vertical advection x w + tendency, 8 -> 3
+  OP_HEAT7_RHS_FUSED,   // value r = sum6 + u + f terms; u' = u + w r  (u, f) -> u', r
+  OP_HEAT7_FUSED,       // value r = sum6 + u terms; u' = u + w r      (u) -> u', r
+  OP_RESIDUAL7_RHS,     // value r = sum6 + u + f terms, no output     (u, f) -> r
+  OP_DIFFERENCE,        // value a - b style: a(0), b(0) terms         (a, b) -> v
+  OP_IDENTITY,          // value in0(0)                                (a) -> v
+  OP_COUNT
+};
+
+#define GSCL_AXIAL6(in, out) {1, 0, 0, in, -1, out}, {-1, 0, 0, in, -1, out}, {0, 1, 0, in, -1, out}, \
+                             {0, -1, 0, in, -1, out}, {0, 0, 1, in, -1, out}, {0, 0, -1, in, -1, out}
+
+struct OpHeat7Rhs {
+  static constexpr int NIN = 2, NOUT = 1, NT = 8;
+  static constexpr TermTable<NT> table = {{{0, 0, 0, 0, -1, 0}, GSCL_AXIAL6(0, 0), {0, 0, 0, 1, -1, 0}}};
+};
+struct OpStar7 {
+  static constexpr int NIN = 1, NOUT = 1, NT = 7;
+  static constexpr TermTable<NT> table = {{{0, 0, 0, 0, -1, 0}, GSCL_AXIAL6(0, 0)}};
+};
+struct OpJacobi7Rhs {
+  static constexpr int NIN = 2, NOUT = 1, NT = 7;
+  static constexpr TermTable<NT> table = {{GSCL_AXIAL6(0, 0), {0, 0, 0, 1, -1, 0}}};
+};
+struct OpJacobi5_2D {
+  static constexpr int NIN = 1, NOUT = 1, NT = 4;
+  static constexpr TermTable<NT> table = {{{1, 0, 0, 0, -1, 0}, {-1, 0, 0, 0, -1, 0}, {0, 1, 0, 0, -1, 0},
+                                           {0, -1, 0, 0, -1, 0}}};
+};
+
+constexpr TermTable<51> climate_table() {
+  TermTable<51> r{};
+  const int bih[13][2] = {{0, 0}, {1, 0}, {-1, 0}, {0, 1}, {0, -1}, {1, 1}, {1, -1}, {-1, 1}, {-1, -1},
+                          {2, 0}, {-2, 0}, {0, 2}, {0, -2}};
+  int k = 0;
+  for (int m = 0; m < 3; ++m) {
+    r.t[k++] = OpTerm{0, 0, 0, m, -1, m};
+    for (int b = 0; b < 13; ++b) r.t[k++] = OpTerm{bih[b][0], bih[b][1], 0, m, 3, m};
+    r.t[k++] = OpTerm{0, 0, 1, m, 4, m};
+    r.t[k++] = OpTerm{0, 0, -1, m, 4, m};
+    r.t[k++] = OpTerm{0, 0, 0, 5 + m, -1, m};
+  }
+  return r;
+}
+struct OpClimate {
+  static constexpr int NIN = 8, NOUT = 3, NT = 51;
+  static constexpr TermTable<NT> table = climate_table();
+};
+
+// value terms come first: a table is evaluated in order
+struct OpHeat7RhsFused {
+  static constexpr int NIN = 2, NOUT = 1, NT = 10;
+  static constexpr TermTable<NT> table = {{GSCL_AXIAL6(0, -1), {0, 0, 0, 0, -1, -1}, {0, 0, 0, 1, -1, -1},
+                                           {0, 0, 0, 0, -1, 0}, {0, 0, 0, -1, -1, 0}}};
+};
+struct OpHeat7Fused {
+  static constexpr int NIN = 1, NOUT = 1, NT = 9;
+  static constexpr TermTable<NT> table = {{GSCL_AXIAL6(0, -1), {0, 0, 0, 0, -1, -1}, {0, 0, 0, 0, -1, 0},
+                                           {0, 0, 0, -1, -1, 0}}};
+};
+struct OpResidual7Rhs {
+  static constexpr int NIN = 2, NOUT = 0, NT = 8;
+  static constexpr TermTable<NT> table = {{GSCL_AXIAL6(0, -1), {0, 0, 0, 0, -1, -1}, {0, 0, 0, 1, -1, -1}}};
+};
+struct OpDifference {
+  static constexpr int NIN = 2, NOUT = 0, NT = 2;
+  static constexpr TermTable<NT> table = {{{0, 0, 0, 0, -1, -1}, {0, 0, 0, 1, -1, -1}}};
+};
+struct OpIdentity {
+  static constexpr int NIN = 1, NOUT = 0, NT = 1;
+  static constexpr TermTable<NT> table = {{{0, 0, 0, 0, -1, -1}}};
+};
+
+#undef GSCL_AXIAL6
+
+template <class Op>
+constexpr bool op_has_value() {
+  for (int i = 0; i < Op::NT; ++i)
+    if (Op::table.t[i].out < 0) return true;
+  return false;
+}
+
+}  // namespace gscl

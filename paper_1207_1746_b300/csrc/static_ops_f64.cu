@@ -1,0 +1,11 @@
+// Compile-time operators (static_ops.h) instantiated for double storage; one
+// translation unit per dtype so the build compiles them in parallel.
+#include "sweep_kernel.cuh"
+
+namespace gscl {
+
+gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream) {
+  return launch_static_t<double>(pl, red, stream);
+}
+
+}  // namespace gscl

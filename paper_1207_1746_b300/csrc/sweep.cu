@@ -29,7 +29,7 @@ bool overlaps(const Grid &a, const Grid &b) { return a.buf < b.buf + b.bytes && 
 gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                  int32_t n_out, const gscl_range *range, Bound *b) {
   if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
-  if (n_out < 0 || n_out > kMaxOut) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut);
+  if (n_out < 0 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut_);
   if (!in || (n_out > 0 && !out)) return fail(GSCL_ERR_INVALID, "grid arrays are required");
   b->op = op;
   b->in.resize(n_in);
@@ -115,12 +115,62 @@ gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, i
   return GSCL_OK;
 }
 
-struct Plan {
-  SweepParams P;
-  int threads = 0;
-  int ctas = 0;
-  size_t smem = 0;
+// ---------------------------------------------------------------- matching
+struct StaticDesc {
+  int id;
+  int nin, nout, nt;
+  const OpTerm *t;
 };
+
+template <class Def>
+StaticDesc desc_of(int id) {
+  return StaticDesc{id, Def::NIN, Def::NOUT, Def::NT, Def::table.t};
+}
+
+const std::vector<StaticDesc> &static_ops() {
+  static const std::vector<StaticDesc> ops = {
+      desc_of<OpHeat7Rhs>(OP_HEAT7_RHS),         desc_of<OpStar7>(OP_STAR7),
+      desc_of<OpJacobi7Rhs>(OP_JACOBI7_RHS),     desc_of<OpJacobi5_2D>(OP_JACOBI5_2D),
+      desc_of<OpClimate>(OP_CLIMATE),            desc_of<OpHeat7RhsFused>(OP_HEAT7_RHS_FUSED),
+      desc_of<OpHeat7Fused>(OP_HEAT7_FUSED),     desc_of<OpResidual7Rhs>(OP_RESIDUAL7_RHS),
+      desc_of<OpDifference>(OP_DIFFERENCE),      desc_of<OpIdentity>(OP_IDENTITY)};
+  return ops;
+}
+
+OpTerm key_of(const gscl_term &t) {
+  return OpTerm{t.dx, t.dy, t.dz, t.in == GSCL_VALUE ? -1 : (int)t.in, t.coef == GSCL_NONE ? -1 : (int)t.coef,
+                t.out == GSCL_VALUE ? -1 : (int)t.out};
+}
+
+bool same_key(const OpTerm &a, const OpTerm &b) {
+  return a.dx == b.dx && a.dy == b.dy && a.dz == b.dz && a.in == b.in && a.coef == b.coef && a.out == b.out;
+}
+
+// Finds a compile-time operator with the descriptor's structure; on success
+// perm[i] is the descriptor term that supplies table term i's weight.
+int match_static(const std::vector<gscl_term> &terms, int n_in, int n_out, std::vector<int> *perm) {
+  const char *env = getenv("GSCL_GENERIC_ONLY");
+  if (env && env[0] && env[0] != '0') return OP_GENERIC;
+  for (const StaticDesc &d : static_ops()) {
+    if (d.nin != n_in || d.nout != n_out || d.nt != (int)terms.size()) continue;
+    std::vector<bool> used(terms.size(), false);
+    perm->assign(d.nt, -1);
+    bool ok = true;
+    for (int i = 0; i < d.nt && ok; ++i) {
+      ok = false;
+      for (size_t j = 0; j < terms.size(); ++j) {
+        if (!used[j] && same_key(d.t[i], key_of(terms[j]))) {
+          used[j] = true;
+          (*perm)[i] = (int)j;
+          ok = true;
+          break;
+        }
+      }
+    }
+    if (ok) return d.id;
+  }
+  return OP_GENERIC;
+}
 
 // Columns per thread: TX = 32 * VX.
 int vx_for(int dtype) { return dtype == GSCL_F64 ? 2 : 4; }
@@ -177,15 +227,25 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
     d.wf = (float)t.w;
     d.wd = t.w;
   };
-  for (auto &t : terms)
-    if (t.out == GSCL_VALUE) push(t);
-  P.n_value_terms = nt;
-  for (int m = 0; m < n_out; ++m) {
-    P.out_begin[m] = nt;
+  std::vector<int> perm;
+  pl->op = match_static(terms, n_in, n_out, &perm);
+  if (pl->op != OP_GENERIC) {
+    // table order (value terms first); the kernel reads only the weights
+    for (int i : perm) push(terms[i]);
+    for (int i = 0; i < (int)perm.size(); ++i)
+      if (terms[perm[i]].out == GSCL_VALUE) P.n_value_terms = i + 1;
+    for (int m = 0; m <= n_out; ++m) P.out_begin[m] = nt;
+  } else {
     for (auto &t : terms)
-      if (t.out == m) push(t);
+      if (t.out == GSCL_VALUE) push(t);
+    P.n_value_terms = nt;
+    for (int m = 0; m < n_out; ++m) {
+      P.out_begin[m] = nt;
+      for (auto &t : terms)
+        if (t.out == m) push(t);
+    }
+    P.out_begin[n_out] = nt;
   }
-  P.out_begin[n_out] = nt;
   P.n_in = n_in;
   P.n_out = n_out;
   for (int m = 0; m < n_out; ++m) {
@@ -240,41 +300,30 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   return GSCL_OK;
 }
 
-template <typename T, int VX, int RED>
-gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
-  auto kern = sweep_kernel<T, VX, RED>;
-  static std::mutex mu;
-  static size_t attr_set = 0;
-  {
-    std::lock_guard<std::mutex> lk(mu);
-    if (pl.smem > attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      attr_set = pl.smem;
-    }
-  }
-  kern<<<pl.ctas, pl.threads, pl.smem, stream>>>(pl.P);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
-  return GSCL_OK;
-}
-
 template <typename T, int VX>
-gscl_status launch_red(const Plan &pl, int red, cudaStream_t stream) {
+gscl_status launch_generic(const Plan &pl, int red, cudaStream_t stream) {
   switch (red) {
-    case RED_NONE: return launch_t<T, VX, RED_NONE>(pl, stream);
-    case RED_SUM: return launch_t<T, VX, RED_SUM>(pl, stream);
-    case RED_MAXABS: return launch_t<T, VX, RED_MAXABS>(pl, stream);
-    case RED_L2: return launch_t<T, VX, RED_L2>(pl, stream);
+    case RED_NONE: return launch_t<T, VX, RED_NONE, GenericOp>(pl, stream);
+    case RED_SUM: return launch_t<T, VX, RED_SUM, GenericOp>(pl, stream);
+    case RED_MAXABS: return launch_t<T, VX, RED_MAXABS, GenericOp>(pl, stream);
+    case RED_L2: return launch_t<T, VX, RED_L2, GenericOp>(pl, stream);
   }
   return fail(GSCL_ERR_INVALID, "unknown reduction");
 }
 
 gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream) {
+  if (pl.op != OP_GENERIC) {
+    switch (dtype) {
+      case GSCL_F64: return launch_static_f64(pl, red, stream);
+      case GSCL_F32: return launch_static_f32(pl, red, stream);
+      case GSCL_BF16: return launch_static_bf16(pl, red, stream);
+    }
+    return fail(GSCL_ERR_DTYPE, "unknown dtype");
+  }
   switch (dtype) {
-    case GSCL_F64: return launch_red<double, 2>(pl, red, stream);
-    case GSCL_F32: return launch_red<float, 4>(pl, red, stream);
-    case GSCL_BF16: return launch_red<__nv_bfloat16, 4>(pl, red, stream);
+    case GSCL_F64: return launch_generic<double, 2>(pl, red, stream);
+    case GSCL_F32: return launch_generic<float, 4>(pl, red, stream);
+    case GSCL_BF16: return launch_generic<__nv_bfloat16, 4>(pl, red, stream);
   }
   return fail(GSCL_ERR_DTYPE, "unknown dtype");
 }
@@ -287,6 +336,13 @@ using namespace gscl;
 extern "C" {
 
 int64_t gscl_reduce_workspace_bytes(void) { return kWorkspaceBytes; }
+
+int32_t gscl_stencil_specialization(const gscl_stencil *op, int32_t n_in, int32_t n_out) {
+  if (!op || !op->terms || op->n_terms < 1 || op->n_terms > kMaxTerms) return OP_GENERIC;
+  std::vector<gscl_term> terms(op->terms, op->terms + op->n_terms);
+  std::vector<int> perm;
+  return match_static(terms, n_in, n_out, &perm);
+}
 
 gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                         int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream) {

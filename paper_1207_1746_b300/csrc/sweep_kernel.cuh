@@ -17,13 +17,17 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <utility>
+
 #include "gscl_internal.h"
+#include "static_ops.h"
 
 namespace gscl {
 
 constexpr int kMaxTerms = GSCL_MAX_TERMS;
 constexpr int kMaxIn = GSCL_MAX_IN;
-constexpr int kMaxOut = GSCL_MAX_OUT;
+constexpr int kMaxOut_ = GSCL_MAX_OUT;
 constexpr int kBarBytes = 256;                   // up to 32 ring-slot mbarriers
 constexpr int kMaxRing = kBarBytes / 8;
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
@@ -53,12 +57,12 @@ struct OutDesc {
 struct SweepParams {
   CUtensorMap tmap[kMaxIn];
   DevTerm terms[kMaxTerms];
-  OutDesc out[kMaxOut];
+  OutDesc out[kMaxOut_];
   int64_t lo[3], hi[3];
   int64_t x_base, y_base;
   int32_t tiles_x, tiles_y, zchunks, zc_len;
   int32_t n_in, n_out, n_value_terms;
-  int32_t out_begin[kMaxOut + 1];
+  int32_t out_begin[kMaxOut_ + 1];
   int32_t R, rz;
   int32_t BW, BH, AX, RY;
   int32_t slot_elems;
@@ -168,37 +172,137 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 }
 __device__ __forceinline__ unsigned long long abs_bits(float v) { return abs_bits((double)v); }
 
-// ---------------------------------------------------------------- one term
-template <typename T, int VX>
-__device__ __forceinline__ void add_term(const DevTerm &tm, const T *ring, int smod, int R, int SE, int thr, int center,
-                                         const typename Arith<T>::A (&v)[VX], typename Arith<T>::A (&acc)[VX]) {
-  using A = typename Arith<T>::A;
-  const A w = term_weight(tm, A(0));
-  A x[VX];
-  if (tm.in < 0) {
+// ---------------------------------------------------------------- operators
+// An operator policy evaluates the operator for the VX points a thread owns
+// at the current z step: v receives the returned value, o[m] output m.
+// ring: shared-memory ring of input planes; smod: ring slot of the current
+// plane; thr: this thread's element offset inside a slot.
+
+// Runtime term list (any descriptor the ABI accepts).
+struct GenericOp {
+  static constexpr int kMaxOut = kMaxOut_;
+  __device__ static int n_out(const SweepParams &P) { return P.n_out; }
+
+  template <typename T, int VX>
+  __device__ static __forceinline__ void term(const DevTerm &tm, const T *ring, int smod, int R, int SE, int thr,
+                                              int center, const typename Arith<T>::A (&v)[VX],
+                                              typename Arith<T>::A (&acc)[VX]) {
+    using A = typename Arith<T>::A;
+    const A w = term_weight(tm, A(0));
+    A x[VX];
+    if (tm.in < 0) {
 #pragma unroll
-    for (int e = 0; e < VX; ++e) x[e] = v[e];
-  } else {
-    int slot = smod + tm.dz;
-    slot = slot >= R ? slot - R : (slot < 0 ? slot + R : slot);
-    const T *p = ring + (tm.in * R + slot) * SE + tm.toff + thr;
+      for (int e = 0; e < VX; ++e) x[e] = v[e];
+    } else {
+      int slot = smod + tm.dz;
+      slot = slot >= R ? slot - R : (slot < 0 ? slot + R : slot);
+      const T *p = ring + (tm.in * R + slot) * SE + tm.toff + thr;
 #pragma unroll
-    for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
+      for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
+    }
+    if (tm.coef >= 0) {
+      const T *cp = ring + (tm.coef * R + smod) * SE + center + thr;
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
+    }
+#pragma unroll
+    for (int e = 0; e < VX; ++e) acc[e] = fma(w, x[e], acc[e]);
   }
-  if (tm.coef >= 0) {
-    const T *cp = ring + (tm.coef * R + smod) * SE + center + thr;
+
+  template <typename T, int VX>
+  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int thr,
+                                              typename Arith<T>::A (&v)[VX],
+                                              typename Arith<T>::A (&o)[kMaxOut][VX]) {
+    const int R = P.R, SE = P.slot_elems;
+    for (int t = 0; t < P.n_value_terms; ++t) term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, v);
 #pragma unroll
-    for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
+    for (int m = 0; m < kMaxOut; ++m)
+      if (m < P.n_out)
+        for (int t = P.out_begin[m]; t < P.out_begin[m + 1]; ++t)
+          term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, o[m]);
   }
+};
+
+// Compile-time term table (static_ops.h).  Term i's weight is P.terms[i]:
+// the host stores the matched descriptor's weights in table order.
+template <class Def>
+struct StaticOp {
+  static constexpr int kMaxOut = Def::NOUT > 0 ? Def::NOUT : 1;
+  __device__ static constexpr int n_out(const SweepParams &) { return Def::NOUT; }
+
+  static constexpr int radius(int axis) {
+    int r = 0;
+    for (int i = 0; i < Def::NT; ++i) {
+      const OpTerm &t = Def::table.t[i];
+      if (t.in < 0) continue;
+      const int d = axis == 0 ? t.dx : axis == 1 ? t.dy : t.dz;
+      r = d > r ? d : (-d > r ? -d : r);
+    }
+    return r;
+  }
+  static constexpr int RX = radius(0), RY = radius(1), RZ = radius(2);
+
+  template <typename T, int VX, int I>
+  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int R, int SE, int thr,
+                                              typename Arith<T>::A (&v)[VX],
+                                              typename Arith<T>::A (&o)[kMaxOut][VX]) {
+    using A = typename Arith<T>::A;
+    constexpr OpTerm t = Def::table.t[I];
+    constexpr int vec = 16 / (int)sizeof(T);
+    constexpr int AX = (RX + vec - 1) / vec * vec;
+    constexpr int BW = 32 * VX + 2 * AX;
+    constexpr int toff = (RY + t.dy) * BW + AX + t.dx;
+    constexpr int center = RY * BW + AX;
+    const A w = term_weight(P.terms[I], A(0));
+    A x[VX];
+    if constexpr (t.in < 0) {
 #pragma unroll
-  for (int e = 0; e < VX; ++e) acc[e] = fma(w, x[e], acc[e]);
-}
+      for (int e = 0; e < VX; ++e) x[e] = v[e];
+    } else {
+      int slot = smod + t.dz;
+      if constexpr (t.dz > 0) slot = slot >= R ? slot - R : slot;
+      if constexpr (t.dz < 0) slot = slot < 0 ? slot + R : slot;
+      const T *p = ring + (t.in * R + slot) * SE + thr + toff;
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
+    }
+    if constexpr (t.coef >= 0) {
+      const T *cp = ring + (t.coef * R + smod) * SE + thr + center;
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
+    }
+    if constexpr (t.out < 0) {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) v[e] = fma(w, x[e], v[e]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) o[t.out][e] = fma(w, x[e], o[t.out][e]);
+    }
+  }
+
+  template <typename T, int VX, int... I>
+  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int thr,
+                                                  typename Arith<T>::A (&v)[VX],
+                                                  typename Arith<T>::A (&o)[kMaxOut][VX],
+                                                  std::integer_sequence<int, I...>) {
+    const int R = P.R, SE = P.slot_elems;
+    (term<T, VX, I>(P, ring, smod, R, SE, thr, v, o), ...);
+  }
+
+  template <typename T, int VX>
+  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int thr,
+                                              typename Arith<T>::A (&v)[VX],
+                                              typename Arith<T>::A (&o)[kMaxOut][VX]) {
+    eval_seq<T, VX>(P, ring, smod, thr, v, o, std::make_integer_sequence<int, Def::NT>{});
+  }
+};
 
 // ---------------------------------------------------------------- kernel
-template <typename T, int VX, int RED>
-__global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ SweepParams P) {
+template <typename T, int VX, int RED, class Op>
+__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
   constexpr int TX = 32 * VX;
+  constexpr int NO = Op::kMaxOut;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
   T *ring = reinterpret_cast<T *>(smem + kBarBytes);
@@ -289,20 +393,23 @@ __global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ Swee
       if (ok) {
         const int64_t z = zb + s;
         A v[VX];
+        A o[NO][VX];
 #pragma unroll
-        for (int e = 0; e < VX; ++e) v[e] = A(0);
-        for (int t = 0; t < P.n_value_terms; ++t) add_term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, v);
-        for (int m = 0; m < P.n_out; ++m) {
-          A o[VX];
+        for (int e = 0; e < VX; ++e) {
+          v[e] = A(0);
 #pragma unroll
-          for (int e = 0; e < VX; ++e) o[e] = A(0);
-          for (int t = P.out_begin[m]; t < P.out_begin[m + 1]; ++t)
-            add_term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, o);
-          if (yok) {
-            T *dst = reinterpret_cast<T *>(P.out[m].base) + z * P.out[m].plane + y * P.out[m].pitch + x0 + lane;
+          for (int m = 0; m < NO; ++m) o[m][e] = A(0);
+        }
+        Op::template eval<T, VX>(P, ring, smod, thr, v, o);
+        if (yok) {
 #pragma unroll
-            for (int e = 0; e < VX; ++e)
-              if (xok[e]) dst[32 * e] = from_arith<T>(o[e]);
+          for (int m = 0; m < NO; ++m) {
+            if (m < Op::n_out(P)) {
+              T *dst = reinterpret_cast<T *>(P.out[m].base) + z * P.out[m].plane + y * P.out[m].pitch + x0 + lane;
+#pragma unroll
+              for (int e = 0; e < VX; ++e)
+                if (xok[e]) dst[32 * e] = from_arith<T>(o[m][e]);
+            }
           }
         }
         if (RED != RED_NONE && yok) {
@@ -415,6 +522,83 @@ __global__ void __launch_bounds__(512) sweep_kernel(const __grid_constant__ Swee
     *P.result = r;
     *ticket = 0u;  // ready for the next call
   }
+}
+
+// ---------------------------------------------------------------- launching
+struct Plan {
+  SweepParams P;
+  int threads = 0;
+  int ctas = 0;
+  size_t smem = 0;
+  int op = OP_GENERIC;  // StaticOpId of a matched compile-time operator
+};
+
+template <typename T, int VX, int RED, class Op>
+gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
+  auto kern = sweep_kernel<T, VX, RED, Op>;
+  static std::mutex mu;
+  static size_t attr_set = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (pl.smem > attr_set) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      attr_set = pl.smem;
+    }
+  }
+  kern<<<pl.ctas, pl.threads, pl.smem, stream>>>(pl.P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
+  return GSCL_OK;
+}
+
+// Columns per thread (TX = 32 VX) for each storage dtype.
+template <typename T> struct VxOf { static constexpr int value = 4; };
+template <> struct VxOf<double> { static constexpr int value = 2; };
+
+// Launches the compile-time operator pl.op for storage type T (one
+// translation unit per dtype instantiates these).
+gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream);
+gscl_status launch_static_f32(const Plan &pl, int red, cudaStream_t stream);
+gscl_status launch_static_bf16(const Plan &pl, int red, cudaStream_t stream);
+
+template <typename T, int RED, class Def>
+gscl_status launch_op(const Plan &pl, cudaStream_t stream) {
+  if constexpr (RED != RED_NONE && !op_has_value<Def>()) {
+    return fail(GSCL_ERR_INVALID, "reduction of an operator without a value");
+  } else if constexpr (RED == RED_NONE && Def::NOUT == 0) {
+    return fail(GSCL_ERR_INVALID, "sweep of an operator without outputs");
+  } else {
+    return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>>(pl, stream);
+  }
+}
+
+template <typename T, int RED>
+gscl_status launch_static_red(const Plan &pl, cudaStream_t stream) {
+  switch (pl.op) {
+    case OP_HEAT7_RHS: return launch_op<T, RED, OpHeat7Rhs>(pl, stream);
+    case OP_STAR7: return launch_op<T, RED, OpStar7>(pl, stream);
+    case OP_JACOBI7_RHS: return launch_op<T, RED, OpJacobi7Rhs>(pl, stream);
+    case OP_JACOBI5_2D: return launch_op<T, RED, OpJacobi5_2D>(pl, stream);
+    case OP_CLIMATE: return launch_op<T, RED, OpClimate>(pl, stream);
+    case OP_HEAT7_RHS_FUSED: return launch_op<T, RED, OpHeat7RhsFused>(pl, stream);
+    case OP_HEAT7_FUSED: return launch_op<T, RED, OpHeat7Fused>(pl, stream);
+    case OP_RESIDUAL7_RHS: return launch_op<T, RED, OpResidual7Rhs>(pl, stream);
+    case OP_DIFFERENCE: return launch_op<T, RED, OpDifference>(pl, stream);
+    case OP_IDENTITY: return launch_op<T, RED, OpIdentity>(pl, stream);
+  }
+  return fail(GSCL_ERR_INVALID, "unknown compile-time operator %d", pl.op);
+}
+
+template <typename T>
+gscl_status launch_static_t(const Plan &pl, int red, cudaStream_t stream) {
+  switch (red) {
+    case RED_NONE: return launch_static_red<T, RED_NONE>(pl, stream);
+    case RED_SUM: return launch_static_red<T, RED_SUM>(pl, stream);
+    case RED_MAXABS: return launch_static_red<T, RED_MAXABS>(pl, stream);
+    case RED_L2: return launch_static_red<T, RED_L2>(pl, stream);
+  }
+  return fail(GSCL_ERR_INVALID, "unknown reduction");
 }
 
 }  // namespace gscl

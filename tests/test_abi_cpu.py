@@ -163,3 +163,21 @@ def test_status_strings(L):
     for s in range(11):
         assert L.gscl_status_str(s)
     assert b"unknown" in L.gscl_status_str(99)
+
+
+def test_workload_operators_map_to_compiled_structures(monkeypatch):
+    from paper_1207_1746_b300 import stencils as S
+    cases = [(S.heat7(0.125), 2, 1, 0), (S.heat7(0.125, with_f=False), 1, 1, 1), (S.poisson_jacobi(), 2, 1, 2),
+             (S.jacobi5_2d(), 1, 1, 3), (S.climate(), 8, 3, 4), (S.heat7_fused(0.125), 2, 1, 5),
+             (S.heat7_fused(0.125, with_f=False), 1, 1, 6), (S.residual7(), 2, 0, 7), (S.difference(), 2, 0, 8)]
+    for terms, nin, nout, want in cases:
+        assert B.specialization(terms, nin, nout) == want
+        # any order of the same terms, and other weights, still match
+        shuffled = [(t[0], t[1], t[2], t[3], t[4], t[5], 0.5 * t[6] + 1.0) for t in reversed(terms)]
+        assert B.specialization(shuffled, nin, nout) == want
+    # a different structure or grid count falls back to the generic kernel
+    assert B.specialization(S.heat7(0.125)[:-1], 2, 1) == -1
+    assert B.specialization(S.heat7(0.125), 3, 1) == -1
+    assert B.specialization(S.fig1b()[:3] + [(2, 0, 0, 0, B.NONE, 0, 1.0)], 1, 1) == -1
+    monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+    assert B.specialization(S.heat7(0.125), 2, 1) == -1

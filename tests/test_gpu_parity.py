@@ -21,6 +21,17 @@ pytestmark = pytest.mark.gpu
 VALUE, NONE = B.VALUE, B.NONE
 
 
+@pytest.fixture(autouse=True, params=["compiled", "generic"])
+def kernel_path(request, monkeypatch):
+    """Every parity test runs once with operator structures compiled where they
+    match and once with the generic term-list kernel only."""
+    if request.param == "generic":
+        monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+    else:
+        monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    return request.param
+
+
 def int_field(rng, shape, lim):
     return rng.integers(-lim, lim + 1, size=shape).astype(np.float64)
 
