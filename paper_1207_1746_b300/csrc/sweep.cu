@@ -202,10 +202,15 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   const int BW = TX + 2 * AX;
   const int nz_range = (int)(b.hi[2] - b.lo[2]);
   const int smem_cap = max_smem_per_block();
-  int TY = 8, PF = nz_range > 1 ? 2 : 0;
+  // warps per CTA (each warp owns kVY rows of the tile) and planes prefetched
+  int NW = 4, PF = nz_range > 1 ? 2 : 0;
+  if (const char *e = getenv("GSCL_TILE_WARPS")) NW = std::max(1, std::min(8, atoi(e)));
+  if (const char *e = getenv("GSCL_PREFETCH")) PF = nz_range > 1 ? std::max(1, std::min(6, atoi(e))) : 0;
+  int TY = NW * kVY;
   size_t smem = 0;
   int R = 0, SE = 0, BH = 0;
   for (;;) {
+    TY = NW * kVY;
     BH = TY + 2 * ry;
     const int slot_bytes = (BW * BH * elem + 127) / 128 * 128;
     SE = slot_bytes / elem;
@@ -213,7 +218,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
     smem = kBarBytes + (size_t)n_in * R * slot_bytes;
     if (smem <= (size_t)smem_cap && R <= kMaxRing) break;
     if (PF > 1) --PF;
-    else if (TY > 2) TY /= 2;
+    else if (NW > 1) NW /= 2;
     else return fail(GSCL_ERR_UNSUPPORTED, "operator needs %zu bytes of shared memory per CTA", smem);
   }
   if (BW > 256 || BH > 256) return fail(GSCL_ERR_UNSUPPORTED, "tile box too large for TMA");
@@ -271,7 +276,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   P.tiles_y = (int32_t)((b.hi[1] - b.lo[1] + TY - 1) / TY);
   // z chunks: enough CTAs to fill every SM a few times over, while keeping
   // the re-read halo planes of each chunk a small share
-  const int threads = 32 * TY;
+  const int threads = 32 * NW;
   int per_sm = std::min(2048 / threads, (int)(228 * 1024 / (smem + 1024)));
   per_sm = std::max(per_sm, 1);
   const long long target = (long long)sm_count() * per_sm * 2;

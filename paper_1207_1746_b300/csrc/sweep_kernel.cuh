@@ -165,13 +165,6 @@ __device__ __forceinline__ double max_abs_bits(double a, double b) {
       (long long)max((unsigned long long)__double_as_longlong(a), (unsigned long long)__double_as_longlong(b)));
 }
 
-// |v| as the bits of a double: for non-negative doubles the unsigned order of
-// the bits is the numeric order, and every NaN sorts above +inf.
-__device__ __forceinline__ unsigned long long abs_bits(double v) {
-  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
-}
-__device__ __forceinline__ unsigned long long abs_bits(float v) { return abs_bits((double)v); }
-
 // ---------------------------------------------------------------- operators
 // An operator policy evaluates the operator for the VX points a thread owns
 // at the current z step: v receives the returned value, o[m] output m.
@@ -297,8 +290,51 @@ struct StaticOp {
   }
 };
 
+// ---------------------------------------------------------------- reduction keys
+// Exact FP32 -> FP64 widening from the IEEE 754 binary32 / binary64 layouts:
+// for a normal float the sign and fraction bits carry over and the exponent
+// bias changes from 127 to 1023 (+896), all on the integer pipe.  A group
+// containing a zero, subnormal, infinity or NaN takes the hardware conversion.
+template <int N>
+__device__ __forceinline__ void widen_group(const float (&x)[N], double (&d)[N]) {
+  bool normal = true;
+#pragma unroll
+  for (int i = 0; i < N; ++i) normal &= ((__float_as_uint(x[i]) >> 23) & 0xffu) - 1u < 254u;
+  if (__all_sync(0xffffffffu, normal)) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      const unsigned b = __float_as_uint(x[i]);
+      const unsigned long long bits = ((unsigned long long)(b & 0x80000000u) << 32) |
+                                      ((unsigned long long)(((b >> 23) & 0xffu) + 896u) << 52) |
+                                      ((unsigned long long)(b & 0x7fffffu) << 29);
+      d[i] = __longlong_as_double((long long)bits);
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) d[i] = (double)x[i];
+  }
+}
+template <int N>
+__device__ __forceinline__ void widen_group(const double (&x)[N], double (&d)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) d[i] = x[i];
+}
+
+// max |v| is tracked on the bits of |v| in the value's own format (for
+// non-negative IEEE numbers the unsigned order of the bits is the numeric
+// order, and NaN sorts above infinity), converted to double once at the end.
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ unsigned long long abs_key(float v) {
+  return (unsigned long long)(__float_as_uint(v) & 0x7fffffffu);
+}
+__device__ __forceinline__ double key_value(unsigned long long k, double) { return __longlong_as_double((long long)k); }
+__device__ __forceinline__ double key_value(unsigned long long k, float) { return (double)__uint_as_float((unsigned)k); }
+
 // ---------------------------------------------------------------- kernel
-template <typename T, int VX, int RED, class Op>
+// VY rows per thread: rows wy, wy + NW, ... of the tile (NW warps).
+template <typename T, int VX, int VY, int RED, class Op>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
   constexpr int TX = 32 * VX;
@@ -311,9 +347,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   __shared__ double s_red[2 * 16];
 
   const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
-  const int TY = blockDim.x >> 5;
-  const int R = P.R, rz = P.rz, SE = P.slot_elems;
-  const int thr = wy * P.BW + lane;
+  const int NW = blockDim.x >> 5;
+  const int TY = NW * VY;
+  const int R = P.R, rz = P.rz;
+  int thr[VY];
+#pragma unroll
+  for (int r = 0; r < VY; ++r) thr[r] = (wy + r * NW) * P.BW + lane;
 
   if (tid == 0) {
     for (int r = 0; r < R; ++r) mbar_init(&bars[r], 1);
@@ -323,10 +362,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   __syncthreads();
 
   Compensated acc;
-  unsigned long long maxbits = 0;
+  double sq = 0.0;          // L2: plain FP64 chain of squares within one tile
+  unsigned long long maxkey = 0;
   uint32_t seq = 0;         // planes issued by this CTA (identical in every thread)
   uint32_t issued_end = 0;  // thread 0: planes actually issued
   uint32_t waited_end = 0;  // planes this thread has waited for
+  int wslot = 0;            // ring slot and phase parity of the next plane to wait for
+  uint32_t wpar = 0;
+  int islot = 0;            // thread 0: ring slot of the next plane to issue
   bool ok = true;
 
   const long long n_tiles = (long long)P.tiles_x * P.tiles_y * P.zchunks;
@@ -344,22 +387,26 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     const uint32_t g0 = seq;
     seq += total;
 
-    // plane q of this tile (z = zb - rz + q) goes to ring slot (g0 + q) % R
+    // planes are issued and consumed in order, so slots and phases advance
+    // by one per plane: plane q of this tile is z = zb - rz + q
     auto issue = [&](int q) {
-      const uint32_t g = g0 + q;
-      const int slot = (int)(g % (uint32_t)R);
+      const int slot = islot;
+      islot = islot + 1 == R ? 0 : islot + 1;
       uint64_t *bar = &bars[slot];
       mbar_arrive_expect_tx(bar, P.tx_bytes);
       const int zp = (int)(zb - rz + q);
       for (int a = 0; a < P.n_in; ++a)
-        tma_load_3d(ring + (a * R + slot) * SE, &P.tmap[a], bar, (int)(x0 - P.AX) + P.cx_add[a],
+        tma_load_3d(ring + (a * R + slot) * P.slot_elems, &P.tmap[a], bar, (int)(x0 - P.AX) + P.cx_add[a],
                     (int)(y0 - P.RY) + P.cy_add[a], zp + P.cz_add[a]);
-      issued_end = g + 1;
+      issued_end = g0 + q + 1;
     };
-    auto wait = [&](int q) {
-      const uint32_t g = g0 + q;
-      if (!mbar_wait_bounded(&bars[g % (uint32_t)R], (g / (uint32_t)R) & 1u)) return false;
-      waited_end = g + 1;
+    auto wait_next = [&]() {
+      if (!mbar_wait_bounded(&bars[wslot], wpar)) return false;
+      ++waited_end;
+      if (++wslot == R) {
+        wslot = 0;
+        wpar ^= 1u;
+      }
       return true;
     };
 
@@ -368,22 +415,28 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       for (int q = 0; q < np; ++q) issue(q);
     }
 
-    const int64_t y = y0 + wy;
-    const bool yok = (y >= P.lo[1]) && (y < P.hi[1]);
+    int64_t y[VY];
+    bool yok[VY];
+#pragma unroll
+    for (int r = 0; r < VY; ++r) {
+      y[r] = y0 + wy + r * NW;
+      yok[r] = (y[r] >= P.lo[1]) && (y[r] < P.hi[1]);
+    }
     bool xok[VX];
 #pragma unroll
     for (int e = 0; e < VX; ++e) {
       const int64_t x = x0 + lane + 32 * e;
       xok[e] = (x >= P.lo[0]) && (x < P.hi[0]);
     }
-    int smod = (int)((g0 + (uint32_t)rz) % (uint32_t)R);
+    int smod = wslot + rz;  // slot of the centre plane of step 0
+    smod = smod >= R ? smod - R : smod;
 
     for (int s = 0; s < zlen; ++s) {
       if (ok) {
         if (s == 0) {
-          for (int d = 0; d <= 2 * rz && ok; ++d) ok = wait(d);
+          for (int d = 0; d <= 2 * rz && ok; ++d) ok = wait_next();
         } else {
-          ok = wait(s + 2 * rz);
+          ok = wait_next();
         }
         if (!ok) {
           s_abort = 1;
@@ -392,41 +445,46 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       }
       if (ok) {
         const int64_t z = zb + s;
-        A v[VX];
-        A o[NO][VX];
 #pragma unroll
-        for (int e = 0; e < VX; ++e) {
-          v[e] = A(0);
+        for (int r = 0; r < VY; ++r) {
+          A v[VX];
+          A o[NO][VX];
 #pragma unroll
-          for (int m = 0; m < NO; ++m) o[m][e] = A(0);
-        }
-        Op::template eval<T, VX>(P, ring, smod, thr, v, o);
-        if (yok) {
+          for (int e = 0; e < VX; ++e) {
+            v[e] = A(0);
 #pragma unroll
-          for (int m = 0; m < NO; ++m) {
-            if (m < Op::n_out(P)) {
-              T *dst = reinterpret_cast<T *>(P.out[m].base) + z * P.out[m].plane + y * P.out[m].pitch + x0 + lane;
+            for (int m = 0; m < NO; ++m) o[m][e] = A(0);
+          }
+          Op::template eval<T, VX>(P, ring, smod, thr[r], v, o);
+          if (yok[r]) {
 #pragma unroll
-              for (int e = 0; e < VX; ++e)
-                if (xok[e]) dst[32 * e] = from_arith<T>(o[m][e]);
+            for (int m = 0; m < NO; ++m) {
+              if (m < Op::n_out(P)) {
+                T *dst = reinterpret_cast<T *>(P.out[m].base) + z * P.out[m].plane + y[r] * P.out[m].pitch + x0 + lane;
+#pragma unroll
+                for (int e = 0; e < VX; ++e)
+                  if (xok[e]) dst[32 * e] = from_arith<T>(o[m][e]);
+              }
             }
           }
-        }
-        if (RED != RED_NONE && yok) {
           if (RED == RED_MAXABS) {
 #pragma unroll
             for (int e = 0; e < VX; ++e)
-              if (xok[e]) maxbits = max(maxbits, abs_bits(v[e]));
-          } else {
-            double gsum = 0.0;
+              if (yok[r] && xok[e]) maxkey = max(maxkey, abs_key(v[e]));
+          } else if (RED != RED_NONE) {
+            double d[VX];
+            widen_group<VX>(v, d);
+            if (RED == RED_L2) {
 #pragma unroll
-            for (int e = 0; e < VX; ++e) {
-              if (xok[e]) {
-                const double d = (double)v[e];
-                gsum = (RED == RED_L2) ? fma(d, d, gsum) : gsum + d;
-              }
+              for (int e = 0; e < VX; ++e)
+                if (yok[r] && xok[e]) sq = fma(d[e], d[e], sq);
+            } else {
+              double gsum = 0.0;
+#pragma unroll
+              for (int e = 0; e < VX; ++e)
+                if (yok[r] && xok[e]) gsum += d[e];
+              acc.add(gsum);
             }
-            acc.add(gsum);
           }
         }
       }
@@ -434,6 +492,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       __syncthreads();
       if (s_abort) break;
       if (tid == 0 && s + R < total) issue(s + R);
+    }
+    if (RED == RED_L2) {  // squares are non-negative: the chain's relative error is at most its length x eps
+      acc.add(sq);
+      sq = 0.0;
     }
     if (s_abort) break;
   }
@@ -452,7 +514,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   // ---- block reduction (fixed shuffle tree), then the last CTA folds all
   double s = 0.0, c = 0.0;
   if (RED == RED_MAXABS) {
-    s = __longlong_as_double((long long)maxbits);
+    s = key_value(maxkey, A(0));  // widened: one ordering (double bits) from here on
   } else {
     s = acc.s;
     c = acc.c;
@@ -533,9 +595,11 @@ struct Plan {
   int op = OP_GENERIC;  // StaticOpId of a matched compile-time operator
 };
 
+constexpr int kVY = 2;  // rows per thread
+
 template <typename T, int VX, int RED, class Op>
 gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
-  auto kern = sweep_kernel<T, VX, RED, Op>;
+  auto kern = sweep_kernel<T, VX, kVY, RED, Op>;
   static std::mutex mu;
   static size_t attr_set = 0;
   {
