@@ -534,7 +534,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   double *partials = reinterpret_cast<double *>(P.workspace + 256);
   if (tid == 0) {
     double bs = s_red[0], bc = s_red[1];
-    for (int w = 1; w < TY; ++w) {
+    for (int w = 1; w < NW; ++w) {
       if (RED == RED_MAXABS) bs = max_abs_bits(bs, s_red[2 * w]);
       else combine_pair(bs, bc, s_red[2 * w], s_red[2 * w + 1]);
     }
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   __syncthreads();
   if (tid == 0) {
     double bs = s_red[0], bc = s_red[1];
-    for (int w = 1; w < TY; ++w) {
+    for (int w = 1; w < NW; ++w) {
       if (RED == RED_MAXABS) bs = max_abs_bits(bs, s_red[2 * w]);
       else combine_pair(bs, bc, s_red[2 * w], s_red[2 * w + 1]);
     }
