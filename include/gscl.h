@@ -268,9 +268,10 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
  * every GPU that loads the library until the process exits.  Nothing is
  * allocated by the call (no cudaMalloc, no library allocator).
  *
- *  - Limit: a range whose launch needs more than GSCL_NOALLOC_MAX_PARTIALS
- *    CTAs is rejected with GSCL_ERR_UNSUPPORTED (gscl_last_error gives the
- *    count); use gscl_do_reduce with a workspace for it.
+ *  - Limit: a launch that needs more than GSCL_NOALLOC_MAX_PARTIALS CTAs is
+ *    rejected with GSCL_ERR_UNSUPPORTED (gscl_last_error gives the count);
+ *    use gscl_do_reduce with a workspace for it.  Launches use one wave of
+ *    CTAs (SMs x resident CTAs per SM; at most 4736 on a 148-SM GPU).
  *  - The first call on each device looks up the scratch array's device
  *    address (with that device current) and caches it; make that first call
  *    before any stream capture.

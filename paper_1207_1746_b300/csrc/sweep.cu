@@ -172,8 +172,9 @@ int match_static(const std::vector<gscl_term> &terms, int n_in, int n_out, std::
   return OP_GENERIC;
 }
 
-// Columns per thread: TX = 32 * VX.
-int vx_for(int dtype) { return dtype == GSCL_F64 ? 2 : 4; }
+// Columns (TX = 32 VX) and rows per thread, as the kernels are instantiated.
+int vx_for(int dtype) { return dtype == GSCL_F64 ? VxOf<double>::value : VxOf<float>::value; }
+int vy_for(int dtype) { return dtype == GSCL_F64 ? VyOf<double>::value : VyOf<float>::value; }
 
 gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   SweepParams &P = pl->P;
@@ -202,15 +203,16 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   const int BW = TX + 2 * AX;
   const int nz_range = (int)(b.hi[2] - b.lo[2]);
   const int smem_cap = max_smem_per_block();
-  // warps per CTA (each warp owns kVY rows of the tile) and planes prefetched
-  int NW = 4, PF = nz_range > 1 ? 2 : 0;
+  // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
+  const int VY = vy_for(g0.dtype);
+  int NW = g0.dtype == GSCL_F64 ? 8 : 4, PF = nz_range > 1 ? 2 : 0;
   if (const char *e = getenv("GSCL_TILE_WARPS")) NW = std::max(1, std::min(8, atoi(e)));
   if (const char *e = getenv("GSCL_PREFETCH")) PF = nz_range > 1 ? std::max(1, std::min(6, atoi(e))) : 0;
-  int TY = NW * kVY;
+  int TY = NW * VY;
   size_t smem = 0;
   int R = 0, SE = 0, BH = 0;
   for (;;) {
-    TY = NW * kVY;
+    TY = NW * VY;
     BH = TY + 2 * ry;
     const int slot_bytes = (BW * BH * elem + 127) / 128 * 128;
     SE = slot_bytes / elem;
@@ -274,19 +276,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   P.y_base = b.lo[1];
   P.tiles_x = (int32_t)((b.hi[0] - P.x_base + TX - 1) / TX);
   P.tiles_y = (int32_t)((b.hi[1] - b.lo[1] + TY - 1) / TY);
-  // z chunks: enough CTAs to fill every SM a few times over, while keeping
-  // the re-read halo planes of each chunk a small share
   const int threads = 32 * NW;
-  int per_sm = std::min(2048 / threads, (int)(228 * 1024 / (smem + 1024)));
-  per_sm = std::max(per_sm, 1);
-  const long long target = (long long)sm_count() * per_sm * 2;
-  const long long txy = (long long)P.tiles_x * P.tiles_y;
-  long long zchunks = std::max(1LL, std::min((long long)nz_range, (target + txy - 1) / txy));
-  int zc_len = (int)((nz_range + zchunks - 1) / zchunks);
-  zc_len = std::max(zc_len, std::min(nz_range, 4 * rz + 4));
-  zchunks = (nz_range + zc_len - 1) / zc_len;
-  P.zchunks = (int32_t)zchunks;
-  P.zc_len = zc_len;
   P.R = R;
   P.rz = rz;
   P.BW = BW;
@@ -298,10 +288,10 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   P.tx_bytes = (uint32_t)(n_in * BW * BH * elem);
   P.err = device_error_word();
   if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
-  const long long n_tiles = txy * zchunks;
   pl->threads = threads;
   pl->smem = smem;
-  pl->ctas = (int)std::min<long long>(n_tiles, reduce ? kMaxReduceCtas : 0x7fffffffLL);
+  pl->work = (long long)P.tiles_x * P.tiles_y * nz_range;
+  pl->max_ctas = reduce ? kMaxReduceCtas : 0x7fffffff;
   return GSCL_OK;
 }
 
@@ -481,11 +471,7 @@ extern "C" gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_sten
   } else {
     Plan pl;
     if (gscl_status s = make_plan(b, true, &pl)) return s;
-    if (pl.ctas > kNoAllocMaxCtas)
-      return fail(GSCL_ERR_UNSUPPORTED,
-                  "this range needs %d partial sums but the built-in scratch of gscl_do_reduce_noalloc holds %d; "
-                  "use gscl_do_reduce with a workspace",
-                  pl.ctas, kNoAllocMaxCtas);
+    pl.max_ctas = kNoAllocMaxCtas;  // launch rejects a grid whose partials would not fit
     // the arrival ticket must start at zero whatever an earlier call left
     cudaError_t e = cudaMemsetAsync(scratch, 0, 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");

@@ -60,7 +60,7 @@ struct SweepParams {
   OutDesc out[kMaxOut_];
   int64_t lo[3], hi[3];
   int64_t x_base, y_base;
-  int32_t tiles_x, tiles_y, zchunks, zc_len;
+  int32_t tiles_x, tiles_y;  // xy tiles covering the range; each CTA streams an equal share of (tile, z) planes
   int32_t n_in, n_out, n_value_terms;
   int32_t out_begin[kMaxOut_ + 1];
   int32_t R, rz;
@@ -372,17 +372,22 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   int islot = 0;            // thread 0: ring slot of the next plane to issue
   bool ok = true;
 
-  const long long n_tiles = (long long)P.tiles_x * P.tiles_y * P.zchunks;
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int txi = (int)(tile % P.tiles_x);
-    const long long rest = tile / P.tiles_x;
-    const int tyi = (int)(rest % P.tiles_y);
-    const int zci = (int)(rest / P.tiles_y);
+  // The (xy tile, z plane) pairs of the range, z fastest, split into
+  // gridDim.x equal contiguous runs (one wave of CTAs): CTA b streams
+  // through [W b / G, W (b+1) / G), one tile column segment at a time.
+  const long long nzr = P.hi[2] - P.lo[2];
+  const long long W = (long long)P.tiles_x * P.tiles_y * nzr;
+  const long long run_end = W * (blockIdx.x + 1) / gridDim.x;
+  for (long long pos = W * blockIdx.x / gridDim.x; pos < run_end;) {
+    const long long col = pos / nzr;
+    const long long zoff = pos - col * nzr;
+    const int zlen = (int)min(nzr - zoff, run_end - pos);
+    pos += zlen;
+    const int txi = (int)(col % P.tiles_x);
+    const int tyi = (int)(col / P.tiles_x);
     const int64_t x0 = P.x_base + (int64_t)txi * TX;
     const int64_t y0 = P.y_base + (int64_t)tyi * TY;
-    const int64_t zb = P.lo[2] + (int64_t)zci * P.zc_len;
-    const int64_t ze = min(zb + (int64_t)P.zc_len, P.hi[2]);
-    const int zlen = (int)(ze - zb);
+    const int64_t zb = P.lo[2] + zoff;
     const int total = zlen + 2 * rz;
     const uint32_t g0 = seq;
     seq += total;
@@ -590,18 +595,30 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 struct Plan {
   SweepParams P;
   int threads = 0;
-  int ctas = 0;
+  long long work = 0;       // (tile, z plane) pairs
+  int max_ctas = 0x7fffffff;  // CTAs the reduction scratch can take partials from
   size_t smem = 0;
   int op = OP_GENERIC;  // StaticOpId of a matched compile-time operator
 };
 
-constexpr int kVY = 2;  // rows per thread
+// Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: FP64
+// is bound by the FP64 pipe and wants warps; FP32 / BF16 want fewer, fatter
+// threads to amortise the per-plane synchronisation.
+template <typename T> struct VxOf { static constexpr int value = 4; };
+template <> struct VxOf<double> { static constexpr int value = 2; };
+template <typename T> struct VyOf { static constexpr int value = 2; };
+template <> struct VyOf<double> { static constexpr int value = 1; };
 
+// One wave: as many CTAs as the device holds at once (occupancy query per
+// kernel and shape, cached), never more than there are (tile, plane) pairs.
 template <typename T, int VX, int RED, class Op>
 gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
-  auto kern = sweep_kernel<T, VX, kVY, RED, Op>;
+  auto kern = sweep_kernel<T, VX, VyOf<T>::value, RED, Op>;
   static std::mutex mu;
   static size_t attr_set = 0;
+  static int cached_threads = -1, cached_blocks = 0, cached_dev = -1;
+  static size_t cached_smem = 0;
+  int per_sm = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
     if (pl.smem > attr_set) {
@@ -609,16 +626,29 @@ gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
       if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
       attr_set = pl.smem;
     }
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cached_threads != pl.threads || cached_smem != pl.smem || cached_dev != dev) {
+      int nb = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.threads, pl.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+      cached_threads = pl.threads;
+      cached_smem = pl.smem;
+      cached_dev = dev;
+      cached_blocks = nb > 0 ? nb : 1;
+    }
+    per_sm = cached_blocks;
   }
-  kern<<<pl.ctas, pl.threads, pl.smem, stream>>>(pl.P);
+  const long long slots = (long long)sm_count() * per_sm;
+  const long long ctas = std::min<long long>(pl.work, slots);
+  if (ctas > pl.max_ctas)
+    return fail(GSCL_ERR_UNSUPPORTED,
+                "this launch needs %lld partial sums but the reduction scratch holds %d", ctas, pl.max_ctas);
+  kern<<<(unsigned)ctas, pl.threads, pl.smem, stream>>>(pl.P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
   return GSCL_OK;
 }
-
-// Columns per thread (TX = 32 VX) for each storage dtype.
-template <typename T> struct VxOf { static constexpr int value = 4; };
-template <> struct VxOf<double> { static constexpr int value = 2; };
 
 // Launches the compile-time operator pl.op for storage type T (one
 // translation unit per dtype instantiates these).
