@@ -249,6 +249,57 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
                            int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
+ * Batched sweeps (many independent grid sets of one operator).
+ *
+ * A batch binds one operator to n_inst instances; instance i uses grids
+ * in[i * n_in .. i * n_in + n_in) and out[i * n_out .. i * n_out + n_out),
+ * each instance validated as gscl_do_all validates one call (instances may
+ * differ in extent, not in dtype).  Every sweep of all instances is one
+ * launch: a host-built work-list splits the instances' (tile, z plane) work
+ * evenly over one wave of CTAs, so uneven instances share the GPU without
+ * one launch per instance.  The batch owns a small device allocation for its
+ * tables (freed by gscl_batch_destroy); grid storage stays the caller's.
+ * Batches hold their instances' handles: destroy the batch before them.
+ * No counterpart in the paper: batching is how the library serves many
+ * small solves at once on one GPU.
+ */
+typedef uint64_t gscl_batch;
+
+gscl_status gscl_batch_create(const gscl_stencil *op, int32_t n_inst, const gscl_grid *in, int32_t n_in,
+                              const gscl_grid *out, int32_t n_out, gscl_batch *out_batch);
+gscl_status gscl_batch_destroy(gscl_batch b);
+
+/* Number of CTAs and work-list segments of one launch, and the compiled
+ * operator structure used (as gscl_stencil_specialization, -1 generic). */
+gscl_status gscl_batch_info(gscl_batch b, int32_t *ctas, int32_t *segments, int32_t *specialization);
+
+/*
+ * `sweeps` sweeps of every instance with in[0] / out[0] as the ping-pong
+ * pair, exactly as gscl_do_all(..., sweeps) on each instance alone (same
+ * point arithmetic, so bit-identical results); on return out[0] names the
+ * last result.  use_graph != 0 captures the group's launches once per
+ * (sweeps, starting buffer) in a CUDA graph and replays it on `stream`.
+ */
+gscl_status gscl_batch_run(gscl_batch b, int32_t sweeps, int32_t use_graph, void *stream);
+
+/*
+ * One sweep of the batch's operator (outputs written as gscl_do_reduce
+ * writes them) reducing its returned value per instance into results[i]
+ * (device memory, n_inst doubles).  Per-instance sums are folded in a fixed
+ * order for a given batch; they agree with gscl_do_reduce on the instance
+ * alone to rounding (the partition into partial sums differs).
+ */
+gscl_status gscl_batch_reduce(gscl_batch b, int32_t reduce_op, double *results, void *stream);
+
+/*
+ * Autotuner: times trial_sweeps sweeps (in[0] -> out[0], so in[0] is left
+ * unchanged and out[0] receives one sweep) for each tile shape (warps per
+ * CTA 2/4/8 x prefetched planes 1/2/3), keeps the fastest and reports it.
+ * Synchronises `stream`.
+ */
+gscl_status gscl_batch_tune(gscl_batch b, int32_t trial_sweeps, void *stream, int32_t *warps, int32_t *prefetch);
+
+/*
  * gscl_do_reduce_noalloc -- gscl_do_reduce for callers that cannot allocate
  * device memory.  The paper has no counterpart: this entry point exists for
  * the library's users, not for the method.

@@ -96,6 +96,12 @@ def lib():
         "gscl_sync": [vp],
         "gscl_do_reduce_noalloc": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double),
                                    i32, vp],
+        "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
+        "gscl_batch_destroy": [u64],
+        "gscl_batch_info": [u64, P(i32), P(i32), P(i32)],
+        "gscl_batch_run": [u64, i32, i32, vp],
+        "gscl_batch_reduce": [u64, i32, vp, vp],
+        "gscl_batch_tune": [u64, i32, vp, P(i32), P(i32)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -317,6 +323,56 @@ def do_reduce_noalloc(reduce_op, op, ins, outs=(), rng=None, result=None, stream
                                        _handles(ins), len(ins), _handles(outs), len(outs), _range(rng), rptr,
                                        int(on_host), stream_ptr(stream)))
     return host.value if on_host else None
+
+
+class Batch:
+    """A batch: one operator over many independent instances (uneven extents
+    allowed), each sweep of all of them in one launch (gscl_batch_*).
+
+    ``instances`` is a list of (ins, outs) grid lists; the batch keeps the
+    Grid objects alive and destroys its handle before them."""
+
+    def __init__(self, op, instances):
+        self.op = as_stencil(op)
+        self.instances = [(list(i), list(o)) for i, o in instances]
+        self.n_in = len(self.instances[0][0])
+        self.n_out = len(self.instances[0][1])
+        ins = [g for i, _ in self.instances for g in i]
+        outs = [g for _, o in self.instances for g in o]
+        h = ctypes.c_uint64()
+        check(lib().gscl_batch_create(ctypes.byref(self.op.c), len(self.instances), _handles(ins), self.n_in,
+                                      _handles(outs), self.n_out, ctypes.byref(h)))
+        self.handle = h.value
+
+    def __del__(self):
+        h = getattr(self, "handle", 0)
+        if h and _lib is not None:
+            _lib.gscl_batch_destroy(h)
+            self.handle = 0
+
+    def info(self):
+        c, s, sp = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().gscl_batch_info(self.handle, ctypes.byref(c), ctypes.byref(s), ctypes.byref(sp)))
+        return {"ctas": c.value, "segments": s.value, "specialization": sp.value}
+
+    def run(self, sweeps, graph=False, stream=None):
+        check(lib().gscl_batch_run(self.handle, int(sweeps), int(bool(graph)), stream_ptr(stream)))
+        if sweeps % 2 == 0:
+            for ins, outs in self.instances:
+                ins[0].buf, outs[0].buf = outs[0].buf, ins[0].buf
+
+    def reduce(self, reduce_op, results, stream=None):
+        """Per-instance reduction into ``results`` (float64 CUDA tensor of n_inst)."""
+        if results.dtype != torch.float64 or not results.is_cuda or results.numel() < len(self.instances):
+            raise ValueError("results must be a float64 CUDA tensor with one entry per instance")
+        check(lib().gscl_batch_reduce(self.handle, int(reduce_op), ctypes.c_void_p(results.data_ptr()),
+                                      stream_ptr(stream)))
+
+    def tune(self, trial_sweeps=3, stream=None):
+        w, p = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().gscl_batch_tune(self.handle, int(trial_sweeps), stream_ptr(stream), ctypes.byref(w),
+                                    ctypes.byref(p)))
+        return w.value, p.value
 
 
 def sync(stream=None):

@@ -1,0 +1,405 @@
+// Batched sweeps: many independent grid sets (instances) of one operator,
+// each sweep of all of them in one launch of the sweep kernel, whose CTAs
+// walk a host-built work-list of (instance, tile column, z run) segments
+// that splits the total (tile, plane) work evenly over one wave of CTAs.
+// Repeated sweeps alternate two device tables of instance descriptors
+// (in[0] -> out[0] and back), so a whole sweep group can be captured once in
+// a CUDA graph and replayed.  Per-instance reductions write one partial per
+// segment and a second kernel folds each instance's segments in order.
+#include <chrono>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <vector>
+
+#include "sweep_host.h"
+
+namespace gscl {
+namespace {
+
+struct Batch {
+  int n_inst = 0, n_in = 0, n_out = 0, dtype = 0;
+  std::vector<gscl_term> terms;
+  gscl_stencil st{};
+  std::vector<gscl_grid> in_h, out_h;
+  bool has_value = false;
+  TileCfg cfg;
+  // state built for the current buffers
+  bool built = false;
+  std::vector<char *> buf_a, buf_b;  // in[0] / out[0] storage when built (table 0 reads a, writes b)
+  Plan base;
+  int G = 0, S = 0;
+  char *dev = nullptr;
+  size_t dev_bytes = 0;
+  InstDesc *tab[2] = {nullptr, nullptr};
+  Segment *segs = nullptr;
+  int32_t *cta_seg = nullptr, *inst_seg = nullptr;
+  double *partials = nullptr;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (first table, sweeps)
+  cudaStream_t cap_stream = nullptr;
+  std::mutex mu;
+};
+
+std::mutex g_batch_mu;
+std::map<uint64_t, std::unique_ptr<Batch>> g_batches;
+uint64_t g_next_batch = 1;
+
+Batch *find_batch(gscl_batch h) {
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  auto it = g_batches.find(h);
+  return it == g_batches.end() ? nullptr : it->second.get();
+}
+
+void drop_graphs(Batch *bt) {
+  for (auto &kv : bt->graphs) cudaGraphExecDestroy(kv.second);
+  bt->graphs.clear();
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Plans every instance in both ping-pong directions, builds the work-list
+// for one wave and uploads the tables.
+gscl_status build(Batch *bt) {
+  drop_graphs(bt);
+  bt->built = false;
+  const int n = bt->n_inst;
+  std::vector<InstDesc> tabs[2];
+  tabs[0].resize(n);
+  tabs[1].resize(n);
+  std::vector<long long> work(n);
+  std::vector<int64_t> nz(n);
+  bt->buf_a.assign(n, nullptr);
+  bt->buf_b.assign(n, nullptr);
+  TileCfg cfg = bt->cfg;
+  for (int i = 0; i < n; ++i) {
+    Bound b;
+    if (gscl_status s = bind(&bt->st, false, &bt->in_h[(size_t)i * bt->n_in], bt->n_in,
+                             bt->n_out ? &bt->out_h[(size_t)i * bt->n_out] : nullptr, bt->n_out, nullptr, &b))
+      return s;
+    if (b.in[0].dtype != bt->dtype) return fail(GSCL_ERR_DTYPE, "instance %d has another dtype", i);
+    if (b.empty) return fail(GSCL_ERR_INVALID, "instance %d has an empty interior", i);
+    if (bt->n_out && (b.in[0].halo[0] != b.out[0].halo[0] || b.in[0].halo[1] != b.out[0].halo[1] ||
+                      b.in[0].halo[2] != b.out[0].halo[2] || overlaps(b.in[0], b.out[0])))
+      return fail(GSCL_ERR_SHAPE, "instance %d: in[0] and out[0] must be distinct grids of one layout", i);
+    for (int dir = 0; dir < 2; ++dir) {
+      Bound bd = b;
+      if (dir == 1) {
+        if (bt->n_out < 1) break;
+        std::swap(bd.in[0], bd.out[0]);
+        for (int a = 1; a < bt->n_in; ++a)
+          if (bd.in_h[a] == bd.in_h[0]) bd.in[a] = bd.in[0];
+      }
+      Plan pl;
+      if (gscl_status s = make_plan(bd, bt->has_value, &pl, cfg)) return s;
+      if (i == 0 && dir == 0) {
+        if (pl.op != OP_GENERIC && !batch_capable(pl.op)) {
+          cfg.generic = true;  // no batched kernel for this structure: interpret the term list
+          bt->cfg.generic = true;
+          if (gscl_status s = make_plan(bd, bt->has_value, &pl, cfg)) return s;
+        }
+        bt->base = pl;
+      } else if (pl.op != bt->base.op || pl.smem != bt->base.smem || pl.threads != bt->base.threads ||
+                 pl.P.BW != bt->base.P.BW || pl.P.BH != bt->base.P.BH || pl.P.R != bt->base.P.R) {
+        return fail(GSCL_ERR_SHAPE, "instance %d plans a different tile shape", i);
+      }
+      tabs[dir][i] = pl.P.inst;
+      if (dir == 0) {
+        work[i] = pl.work;
+        nz[i] = pl.P.inst.hi[2] - pl.P.inst.lo[2];
+      }
+    }
+    bt->buf_a[i] = b.in[0].buf;
+    bt->buf_b[i] = bt->n_out ? b.out[0].buf : nullptr;
+  }
+  Plan &base = bt->base;
+  base.batch = true;
+  // one wave of CTAs
+  int occ = 0;
+  const int red_probe = bt->n_out ? RED_NONE : RED_L2;
+  if (gscl_status s = launch(base, bt->dtype, red_probe, nullptr, &occ)) return s;
+  long long W = 0;
+  for (long long w : work) W += w;
+  const long long G = std::max(1LL, std::min<long long>(W, (long long)sm_count() * occ));
+  // work-list: run b = [W b / G, W (b+1) / G) split at instance and column ends
+  std::vector<Segment> segs;
+  std::vector<int32_t> cta_seg(G + 1), inst_seg(n + 1, -1);
+  int inst = 0;
+  long long inst_start = 0;
+  for (long long b = 0; b < G; ++b) {
+    cta_seg[b] = (int32_t)segs.size();
+    long long pos = W * b / G;
+    const long long end = W * (b + 1) / G;
+    while (pos < end) {
+      while (pos >= inst_start + work[inst]) inst_start += work[inst++];
+      if (inst_seg[inst] < 0) inst_seg[inst] = (int32_t)segs.size();
+      const long long local = pos - inst_start;
+      const long long col = local / nz[inst];
+      const long long zoff = local - col * nz[inst];
+      const long long len = std::min(end - pos, nz[inst] - zoff);
+      segs.push_back(Segment{inst, (int32_t)col, (int32_t)zoff, (int32_t)len});
+      pos += len;
+    }
+  }
+  cta_seg[G] = (int32_t)segs.size();
+  inst_seg[n] = (int32_t)segs.size();
+  for (int i = n - 1; i >= 0; --i)
+    if (inst_seg[i] < 0) inst_seg[i] = inst_seg[i + 1];
+  // device blob: two tables, segments, CTA and instance segment starts, partials
+  const size_t t_bytes = align_up(sizeof(InstDesc) * n, 256);
+  const size_t s_bytes = align_up(sizeof(Segment) * segs.size(), 256);
+  const size_t c_bytes = align_up(sizeof(int32_t) * (G + 1), 256);
+  const size_t i_bytes = align_up(sizeof(int32_t) * (n + 1), 256);
+  const size_t p_bytes = align_up(16 * segs.size(), 256);
+  const size_t need = 2 * t_bytes + s_bytes + c_bytes + i_bytes + p_bytes;
+  if (need > bt->dev_bytes) {
+    if (bt->dev) cudaFree(bt->dev);
+    bt->dev = nullptr;
+    bt->dev_bytes = 0;
+    cudaError_t e = cudaMalloc(&bt->dev, need);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc of the batch tables");
+    bt->dev_bytes = need;
+  }
+  char *p = bt->dev;
+  bt->tab[0] = (InstDesc *)p;
+  bt->tab[1] = (InstDesc *)(p + t_bytes);
+  bt->segs = (Segment *)(p + 2 * t_bytes);
+  bt->cta_seg = (int32_t *)(p + 2 * t_bytes + s_bytes);
+  bt->inst_seg = (int32_t *)(p + 2 * t_bytes + s_bytes + c_bytes);
+  bt->partials = (double *)(p + 2 * t_bytes + s_bytes + c_bytes + i_bytes);
+  cudaError_t e = cudaMemcpy(bt->tab[0], tabs[0].data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && bt->n_out)
+    e = cudaMemcpy(bt->tab[1], tabs[1].data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->segs, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->cta_seg, cta_seg.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->inst_seg, inst_seg.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the batch tables");
+  bt->G = (int)G;
+  bt->S = (int)segs.size();
+  base.batch_ctas = (int)G;
+  base.P.segs = bt->segs;
+  base.P.cta_seg = bt->cta_seg;
+  base.P.seg_partials = bt->partials;
+  bt->built = true;
+  return GSCL_OK;
+}
+
+// Which table reads the buffers in[0] names now (0 or 1); rebuilds the
+// tables when the instances' buffers are not the two the tables know.
+gscl_status current_table(Batch *bt, int *which) {
+  if (bt->built) {
+    int t = -1;
+    bool consistent = true;
+    for (int i = 0; i < bt->n_inst && consistent; ++i) {
+      Grid g;
+      if (gscl_status s = lookup(bt->in_h[(size_t)i * bt->n_in], &g)) return s;
+      const int ti = g.buf == bt->buf_a[i] ? 0 : (bt->n_out && g.buf == bt->buf_b[i] ? 1 : -1);
+      if (ti < 0 || (t >= 0 && ti != t)) consistent = false;
+      t = ti;
+    }
+    if (consistent) {
+      *which = t;
+      return GSCL_OK;
+    }
+  }
+  if (gscl_status s = build(bt)) return s;
+  *which = 0;
+  return GSCL_OK;
+}
+
+gscl_status enqueue_sweeps(Batch *bt, int first, int sweeps, cudaStream_t stream) {
+  Plan pl = bt->base;
+  for (int s = 0; s < sweeps; ++s) {
+    pl.P.insts = bt->tab[(first + s) & 1];
+    if (gscl_status st = launch(pl, bt->dtype, RED_NONE, stream, nullptr)) return st;
+  }
+  return GSCL_OK;
+}
+
+template <int RED>
+gscl_status finalize(Batch *bt, double *results, cudaStream_t stream) {
+  const int threads = 128;
+  batch_finalize_kernel<RED><<<(bt->n_inst + threads - 1) / threads, threads, 0, stream>>>(
+      bt->partials, bt->inst_seg, bt->n_inst, results);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "batch finalize launch");
+}
+
+}  // namespace
+}  // namespace gscl
+
+using namespace gscl;
+
+extern "C" {
+
+gscl_status gscl_batch_create(const gscl_stencil *op, int32_t n_inst, const gscl_grid *in, int32_t n_in,
+                              const gscl_grid *out, int32_t n_out, gscl_batch *out_batch) {
+  if (!out_batch) return fail(GSCL_ERR_INVALID, "out_batch is required");
+  *out_batch = 0;
+  if (!op || !op->terms || op->n_terms < 1 || op->n_terms > kMaxTerms)
+    return fail(GSCL_ERR_INVALID, "a batch needs an operator with 1..%d terms", kMaxTerms);
+  if (n_inst < 1 || n_inst > (1 << 20)) return fail(GSCL_ERR_INVALID, "n_inst = %d outside [1, 2^20]", n_inst);
+  if (n_in < 1 || n_in > kMaxIn || n_out < 0 || n_out > kMaxOut_ || !in || (n_out && !out))
+    return fail(GSCL_ERR_INVALID, "bad grid counts or arrays");
+  std::unique_ptr<Batch> bt(new Batch());
+  bt->n_inst = n_inst;
+  bt->n_in = n_in;
+  bt->n_out = n_out;
+  bt->terms.assign(op->terms, op->terms + op->n_terms);
+  bt->st = gscl_stencil{op->n_terms, 0, bt->terms.data()};
+  bt->in_h.assign(in, in + (size_t)n_inst * n_in);
+  if (n_out) bt->out_h.assign(out, out + (size_t)n_inst * n_out);
+  for (auto &t : bt->terms)
+    if (t.out == GSCL_VALUE) bt->has_value = true;
+  Grid g0;
+  if (gscl_status s = lookup(bt->in_h[0], &g0)) return s;
+  bt->dtype = g0.dtype;
+  if (gscl_status s = build(bt.get())) return s;  // validates every instance
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  const uint64_t id = g_next_batch++;
+  g_batches[id].reset(bt.release());
+  *out_batch = id;
+  return GSCL_OK;
+}
+
+gscl_status gscl_batch_destroy(gscl_batch h) {
+  std::unique_ptr<Batch> bt;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    auto it = g_batches.find(h);
+    if (it == g_batches.end()) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+    bt = std::move(it->second);
+    g_batches.erase(it);
+  }
+  drop_graphs(bt.get());
+  if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
+  if (bt->dev) cudaFree(bt->dev);
+  return GSCL_OK;
+}
+
+gscl_status gscl_batch_info(gscl_batch h, int32_t *ctas, int32_t *segments, int32_t *specialization) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  if (ctas) *ctas = bt->G;
+  if (segments) *segments = bt->S;
+  if (specialization) *specialization = bt->base.op;
+  return GSCL_OK;
+}
+
+gscl_status gscl_batch_run(gscl_batch h, int32_t sweeps, int32_t use_graph, void *stream) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  if (sweeps < 1) return fail(GSCL_ERR_INVALID, "sweeps must be >= 1");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  if (bt->n_out < 1) return fail(GSCL_ERR_INVALID, "this batch's operator has no output to sweep");
+  int first = 0;
+  if (gscl_status s = current_table(bt, &first)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (use_graph) {
+    auto key = std::make_pair(first, (int)sweeps);
+    auto it = bt->graphs.find(key);
+    if (it == bt->graphs.end()) {
+      if (!bt->cap_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+      }
+      cudaError_t e = cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeRelaxed);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+      gscl_status s = enqueue_sweeps(bt, first, sweeps, bt->cap_stream);
+      cudaGraph_t graph = nullptr;
+      e = cudaStreamEndCapture(bt->cap_stream, &graph);
+      if (s != GSCL_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return s;
+      }
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+      cudaGraphExec_t exec = nullptr;
+      e = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+      it = bt->graphs.emplace(key, exec).first;
+    }
+    cudaError_t e = cudaGraphLaunch(it->second, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
+  } else {
+    if (gscl_status s = enqueue_sweeps(bt, first, sweeps, st)) return s;
+  }
+  if (sweeps % 2 == 0)  // out[0] names the last sweep's result, as in gscl_do_all
+    for (int i = 0; i < bt->n_inst; ++i)
+      if (gscl_status s = swap_storage(bt->in_h[(size_t)i * bt->n_in], bt->out_h[(size_t)i * bt->n_out])) return s;
+  return GSCL_OK;
+}
+
+gscl_status gscl_batch_reduce(gscl_batch h, int32_t reduce_op, double *results, void *stream) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  if (!results) return fail(GSCL_ERR_INVALID, "results is NULL");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  if (!bt->has_value) return fail(GSCL_ERR_INVALID, "the batch's operator returns no value");
+  int red;
+  switch (reduce_op) {
+    case GSCL_SUM: red = RED_SUM; break;
+    case GSCL_MAXABS: red = RED_MAXABS; break;
+    case GSCL_L2: red = RED_L2; break;
+    default: return fail(GSCL_ERR_INVALID, "unknown reduce op %d", reduce_op);
+  }
+  int first = 0;
+  if (gscl_status s = current_table(bt, &first)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  Plan pl = bt->base;
+  pl.P.insts = bt->tab[first];
+  if (gscl_status s = launch(pl, bt->dtype, red, st, nullptr)) return s;
+  switch (red) {
+    case RED_SUM: return finalize<RED_SUM>(bt, results, st);
+    case RED_MAXABS: return finalize<RED_MAXABS>(bt, results, st);
+    default: return finalize<RED_L2>(bt, results, st);
+  }
+}
+
+gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, int32_t *warps, int32_t *prefetch) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  if (trial_sweeps < 1) return fail(GSCL_ERR_INVALID, "trial_sweeps must be >= 1");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int red = bt->n_out ? RED_NONE : RED_L2;
+  const TileCfg keep = bt->cfg;
+  float best_ms = 1e30f;
+  TileCfg best = keep;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int nws[] = {2, 4, 8};
+  const int pfs[] = {1, 2, 3};
+  for (int nw : nws)
+    for (int pf : pfs) {
+      bt->cfg = TileCfg{nw, pf, keep.generic};
+      if (build(bt) != GSCL_OK) continue;  // e.g. does not fit in shared memory
+      int first = 0;
+      if (current_table(bt, &first) != GSCL_OK) continue;
+      Plan pl = bt->base;
+      pl.P.insts = bt->tab[first];  // in[0] -> out[0] every trial: in[0] is left as it was
+      if (red != RED_NONE) pl.P.seg_partials = bt->partials;
+      if (launch(pl, bt->dtype, red, st, nullptr) != GSCL_OK) continue;
+      cudaEventRecord(e0, st);
+      for (int s = 0; s < trial_sweeps; ++s) launch(pl, bt->dtype, red, st, nullptr);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = bt->cfg;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  bt->cfg = best;
+  if (gscl_status s = build(bt)) return s;
+  if (warps) *warps = best.nw;
+  if (prefetch) *prefetch = best.pf;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "tuning launches");
+}
+
+}  // extern "C"

@@ -4,8 +4,8 @@
 
 namespace gscl {
 
-gscl_status launch_static_bf16(const Plan &pl, int red, cudaStream_t stream) {
-  return launch_static_t<__nv_bfloat16>(pl, red, stream);
+gscl_status launch_static_bf16(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only) {
+  return launch_static_t<__nv_bfloat16>(pl, red, stream, occupancy_only);
 }
 
 }  // namespace gscl

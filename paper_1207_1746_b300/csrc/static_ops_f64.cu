@@ -4,8 +4,8 @@
 
 namespace gscl {
 
-gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream) {
-  return launch_static_t<double>(pl, red, stream);
+gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only) {
+  return launch_static_t<double>(pl, red, stream, occupancy_only);
 }
 
 }  // namespace gscl

@@ -9,19 +9,9 @@
 #include <mutex>
 #include <vector>
 
-#include "sweep_kernel.cuh"
+#include "sweep_host.h"
 
 namespace gscl {
-
-namespace {
-
-struct Bound {
-  const gscl_stencil *op = nullptr;
-  std::vector<Grid> in, out;
-  std::vector<gscl_grid> in_h, out_h;
-  int64_t lo[3], hi[3];
-  bool empty = false;
-};
 
 bool overlaps(const Grid &a, const Grid &b) { return a.buf < b.buf + b.bytes && b.buf < a.buf + a.bytes; }
 
@@ -176,7 +166,7 @@ int match_static(const std::vector<gscl_term> &terms, int n_in, int n_out, std::
 int vx_for(int dtype) { return dtype == GSCL_F64 ? VxOf<double>::value : VxOf<float>::value; }
 int vy_for(int dtype) { return dtype == GSCL_F64 ? VyOf<double>::value : VyOf<float>::value; }
 
-gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
+gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   SweepParams &P = pl->P;
   memset(&P, 0, sizeof P);
   const Grid &g0 = b.in[0];
@@ -208,6 +198,8 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   int NW = g0.dtype == GSCL_F64 ? 8 : 4, PF = nz_range > 1 ? 2 : 0;
   if (const char *e = getenv("GSCL_TILE_WARPS")) NW = std::max(1, std::min(8, atoi(e)));
   if (const char *e = getenv("GSCL_PREFETCH")) PF = nz_range > 1 ? std::max(1, std::min(6, atoi(e))) : 0;
+  if (cfg.nw > 0) NW = std::min(8, cfg.nw);
+  if (cfg.pf > 0 && nz_range > 1) PF = std::min(6, cfg.pf);
   int TY = NW * VY;
   size_t smem = 0;
   int R = 0, SE = 0, BH = 0;
@@ -235,7 +227,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
     d.wd = t.w;
   };
   std::vector<int> perm;
-  pl->op = match_static(terms, n_in, n_out, &perm);
+  pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
   if (pl->op != OP_GENERIC) {
     // table order (value terms first); the kernel reads only the weights
     for (int i : perm) push(terms[i]);
@@ -257,25 +249,25 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   P.n_out = n_out;
   for (int m = 0; m < n_out; ++m) {
     const Grid &g = b.out[m];
-    P.out[m].base = g.elem_ptr(0, 0, 0);
-    P.out[m].pitch = g.pitch;
-    P.out[m].plane = g.plane;
+    P.inst.out[m].base = g.elem_ptr(0, 0, 0);
+    P.inst.out[m].pitch = g.pitch;
+    P.inst.out[m].plane = g.plane;
   }
   for (int a = 0; a < n_in; ++a) {
     const Grid &g = b.in[a];
-    if (gscl_status s = encode_tensor_map_3d(&P.tmap[a], g, (uint32_t)BW, (uint32_t)BH)) return s;
-    P.cx_add[a] = (int32_t)(g.halo[0] + g.off);
-    P.cy_add[a] = g.halo[1];
-    P.cz_add[a] = g.halo[2];
+    if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[a], g, (uint32_t)BW, (uint32_t)BH)) return s;
+    P.inst.cx_add[a] = (int32_t)(g.halo[0] + g.off);
+    P.inst.cy_add[a] = g.halo[1];
+    P.inst.cz_add[a] = g.halo[2];
   }
   for (int a = 0; a < 3; ++a) {
-    P.lo[a] = b.lo[a];
-    P.hi[a] = b.hi[a];
+    P.inst.lo[a] = b.lo[a];
+    P.inst.hi[a] = b.hi[a];
   }
-  P.x_base = b.lo[0] / TX * TX;
-  P.y_base = b.lo[1];
-  P.tiles_x = (int32_t)((b.hi[0] - P.x_base + TX - 1) / TX);
-  P.tiles_y = (int32_t)((b.hi[1] - b.lo[1] + TY - 1) / TY);
+  P.inst.x_base = b.lo[0] / TX * TX;
+  P.inst.y_base = b.lo[1];
+  P.inst.tiles_x = (int32_t)((b.hi[0] - P.inst.x_base + TX - 1) / TX);
+  P.inst.tiles_y = (int32_t)((b.hi[1] - b.lo[1] + TY - 1) / TY);
   const int threads = 32 * NW;
   P.R = R;
   P.rz = rz;
@@ -290,40 +282,51 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl) {
   if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
   pl->threads = threads;
   pl->smem = smem;
-  pl->work = (long long)P.tiles_x * P.tiles_y * nz_range;
+  pl->work = (long long)P.inst.tiles_x * P.inst.tiles_y * nz_range;
   pl->max_ctas = reduce ? kMaxReduceCtas : 0x7fffffff;
   return GSCL_OK;
 }
 
-template <typename T, int VX>
-gscl_status launch_generic(const Plan &pl, int red, cudaStream_t stream) {
+namespace {
+
+template <typename T, int VX, bool BATCH>
+gscl_status launch_generic_b(const Plan &pl, int red, cudaStream_t stream, int *occ) {
   switch (red) {
-    case RED_NONE: return launch_t<T, VX, RED_NONE, GenericOp>(pl, stream);
-    case RED_SUM: return launch_t<T, VX, RED_SUM, GenericOp>(pl, stream);
-    case RED_MAXABS: return launch_t<T, VX, RED_MAXABS, GenericOp>(pl, stream);
-    case RED_L2: return launch_t<T, VX, RED_L2, GenericOp>(pl, stream);
+    case RED_NONE: return launch_t<T, VX, RED_NONE, GenericOp, BATCH>(pl, stream, occ);
+    case RED_SUM: return launch_t<T, VX, RED_SUM, GenericOp, BATCH>(pl, stream, occ);
+    case RED_MAXABS: return launch_t<T, VX, RED_MAXABS, GenericOp, BATCH>(pl, stream, occ);
+    case RED_L2: return launch_t<T, VX, RED_L2, GenericOp, BATCH>(pl, stream, occ);
   }
   return fail(GSCL_ERR_INVALID, "unknown reduction");
 }
 
-gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream) {
+template <typename T>
+gscl_status launch_generic(const Plan &pl, int red, cudaStream_t stream, int *occ) {
+  constexpr int VX = VxOf<T>::value;
+  return pl.batch ? launch_generic_b<T, VX, true>(pl, red, stream, occ)
+                  : launch_generic_b<T, VX, false>(pl, red, stream, occ);
+}
+
+}  // namespace
+
+// Launches (or, with occupancy_only, sizes) the kernel a plan names.
+gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only) {
   if (pl.op != OP_GENERIC) {
     switch (dtype) {
-      case GSCL_F64: return launch_static_f64(pl, red, stream);
-      case GSCL_F32: return launch_static_f32(pl, red, stream);
-      case GSCL_BF16: return launch_static_bf16(pl, red, stream);
+      case GSCL_F64: return launch_static_f64(pl, red, stream, occupancy_only);
+      case GSCL_F32: return launch_static_f32(pl, red, stream, occupancy_only);
+      case GSCL_BF16: return launch_static_bf16(pl, red, stream, occupancy_only);
     }
     return fail(GSCL_ERR_DTYPE, "unknown dtype");
   }
   switch (dtype) {
-    case GSCL_F64: return launch_generic<double, 2>(pl, red, stream);
-    case GSCL_F32: return launch_generic<float, 4>(pl, red, stream);
-    case GSCL_BF16: return launch_generic<__nv_bfloat16, 4>(pl, red, stream);
+    case GSCL_F64: return launch_generic<double>(pl, red, stream, occupancy_only);
+    case GSCL_F32: return launch_generic<float>(pl, red, stream, occupancy_only);
+    case GSCL_BF16: return launch_generic<__nv_bfloat16>(pl, red, stream, occupancy_only);
   }
   return fail(GSCL_ERR_DTYPE, "unknown dtype");
 }
 
-}  // namespace
 }  // namespace gscl
 
 using namespace gscl;
@@ -359,8 +362,8 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
     for (size_t a = 1; a < b.in.size(); ++a)  // another input naming the ping-pong grid follows it
       if (b.in_h[a] == b.in_h[0]) b.in[a] = src;
     Plan pl;
-    if (gscl_status st = make_plan(b, false, &pl)) return st;
-    if (gscl_status st = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream)) return st;
+    if (gscl_status st = make_plan(b, false, &pl, TileCfg{})) return st;
+    if (gscl_status st = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream, nullptr)) return st;
     std::swap(src, dst);
   }
   if (sweeps > 1 && sweeps % 2 == 0) return swap_storage(in[0], out[0]);
@@ -392,10 +395,10 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   } else {
     Plan pl;
-    if (gscl_status s = make_plan(b, true, &pl)) return s;
+    if (gscl_status s = make_plan(b, true, &pl, TileCfg{})) return s;
     pl.P.workspace = (unsigned char *)workspace;
     pl.P.result = dev_result;
-    if (gscl_status s = launch(pl, b.in[0].dtype, red, st)) return s;
+    if (gscl_status s = launch(pl, b.in[0].dtype, red, st, nullptr)) return s;
   }
   if (result_on_host) {
     cudaError_t e = cudaMemcpyAsync(result, dev_result, sizeof(double), cudaMemcpyDeviceToHost, st);
@@ -470,14 +473,14 @@ extern "C" gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_sten
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
   } else {
     Plan pl;
-    if (gscl_status s = make_plan(b, true, &pl)) return s;
+    if (gscl_status s = make_plan(b, true, &pl, TileCfg{})) return s;
     pl.max_ctas = kNoAllocMaxCtas;  // launch rejects a grid whose partials would not fit
     // the arrival ticket must start at zero whatever an earlier call left
     cudaError_t e = cudaMemsetAsync(scratch, 0, 256, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     pl.P.workspace = scratch;
     pl.P.result = dev_result;
-    if (gscl_status s = launch(pl, b.in[0].dtype, red, st)) return s;
+    if (gscl_status s = launch(pl, b.in[0].dtype, red, st, nullptr)) return s;
   }
   if (result_on_host) {
     cudaError_t e = cudaMemcpyAsync(result, dev_result, sizeof(double), cudaMemcpyDeviceToHost, st);

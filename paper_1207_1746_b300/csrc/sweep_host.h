@@ -1,0 +1,44 @@
+// Host-side pieces shared by the single-grid entry points (sweep.cu) and the
+// batched ones (batch.cu): operator validation against grids, launch
+// planning and kernel dispatch.
+#pragma once
+
+#include <vector>
+
+#include "sweep_kernel.cuh"
+
+namespace gscl {
+
+// Handles resolved and validated for one call.
+struct Bound {
+  const gscl_stencil *op = nullptr;
+  std::vector<Grid> in, out;
+  std::vector<gscl_grid> in_h, out_h;
+  int64_t lo[3], hi[3];
+  bool empty = false;
+};
+
+// Tile shape knobs (0 = the default for the dtype).
+struct TileCfg {
+  int nw = 0;            // warps per CTA
+  int pf = 0;            // planes prefetched beyond the stencil's z reach
+  bool generic = false;  // interpret the term list even if a compiled structure matches
+};
+
+bool overlaps(const Grid &a, const Grid &b);
+
+// Validates handles, shapes, dtypes, the range, every term and aliasing
+// (Section 3's rules for stencil operators and do_all).
+gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                 int32_t n_out, const gscl_range *range, Bound *b);
+
+// Compile-time operator with the descriptor's structure, or OP_GENERIC.
+int match_static(const std::vector<gscl_term> &terms, int n_in, int n_out, std::vector<int> *perm);
+
+// Tile geometry, shared-memory ring, term table and the grid's InstDesc.
+gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg);
+
+// Launches (or, with occupancy_only, sizes) the kernel a plan names.
+gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only);
+
+}  // namespace gscl

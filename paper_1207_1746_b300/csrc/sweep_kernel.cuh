@@ -54,13 +54,27 @@ struct OutDesc {
   int64_t plane;  // elements
 };
 
-struct SweepParams {
+// Everything that differs between grid sets of one operator: a single-grid
+// launch carries one in its parameters, a batched launch a device table of
+// them (one per instance).  Aligned as strictly as its tensor maps.
+struct InstDesc {
   CUtensorMap tmap[kMaxIn];
-  DevTerm terms[kMaxTerms];
   OutDesc out[kMaxOut_];
   int64_t lo[3], hi[3];
   int64_t x_base, y_base;
-  int32_t tiles_x, tiles_y;  // xy tiles covering the range; each CTA streams an equal share of (tile, z) planes
+  int32_t tiles_x, tiles_y;  // xy tiles covering the range
+  int32_t cx_add[kMaxIn], cy_add[kMaxIn], cz_add[kMaxIn];
+};
+
+// One entry of a batched launch's work-list: planes [zoff, zoff + zlen) of
+// tile column `col` of instance `inst`.
+struct Segment {
+  int32_t inst, col, zoff, zlen;
+};
+
+struct SweepParams {
+  InstDesc inst;             // single-grid launches
+  DevTerm terms[kMaxTerms];
   int32_t n_in, n_out, n_value_terms;
   int32_t out_begin[kMaxOut_ + 1];
   int32_t R, rz;
@@ -68,9 +82,13 @@ struct SweepParams {
   int32_t slot_elems;
   int32_t center;     // RY * BW + AX
   uint32_t tx_bytes;  // bytes one plane delivers over all inputs
-  int32_t cx_add[kMaxIn], cy_add[kMaxIn], cz_add[kMaxIn];
-  unsigned char *workspace;  // reduce: ticket at +0, partials at +256
-  double *result;            // reduce: where the last CTA writes the value
+  // batched launches: CTA b runs segments [cta_seg[b], cta_seg[b + 1])
+  const InstDesc *insts;
+  const Segment *segs;
+  const int32_t *cta_seg;
+  double *seg_partials;      // batched reduce: one (s, c) pair per segment
+  unsigned char *workspace;  // single reduce: ticket at +0, partials at +256
+  double *result;            // single reduce: where the last CTA writes the value
   int *err;                  // device error word
 };
 
@@ -334,7 +352,39 @@ __device__ __forceinline__ double key_value(unsigned long long k, float) { retur
 
 // ---------------------------------------------------------------- kernel
 // VY rows per thread: rows wy, wy + NW, ... of the tile (NW warps).
-template <typename T, int VX, int VY, int RED, class Op>
+// Folds the CTA's per-thread (s, c) pairs (or max keys) in a fixed order;
+// the result is valid in thread 0.  Uses s_red[2 * warps].
+template <int RED>
+__device__ __forceinline__ void block_fold(double &s, double &c, double *s_red, int NW) {
+  const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
+  for (int off = 16; off > 0; off >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
+    else combine_pair(s, c, s2, c2);
+  }
+  __syncthreads();  // s_red may still be read from a previous fold
+  if (lane == 0) {
+    s_red[2 * wy] = s;
+    s_red[2 * wy + 1] = c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    s = s_red[0];
+    c = s_red[1];
+    for (int w = 1; w < NW; ++w) {
+      if (RED == RED_MAXABS) s = max_abs_bits(s, s_red[2 * w]);
+      else combine_pair(s, c, s_red[2 * w], s_red[2 * w + 1]);
+    }
+  }
+}
+
+// VY rows per thread: rows wy, wy + NW, ... of the tile (NW warps).
+// BATCH: segments come from the device work-list and each segment's
+// reduction goes to its own partial (per-instance results are folded by
+// batch_finalize_kernel); otherwise the CTA derives its run of (tile, plane)
+// pairs of the single grid and the last CTA folds all partials.
+template <typename T, int VX, int VY, int RED, class Op, bool BATCH>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
   constexpr int TX = 32 * VX;
@@ -362,7 +412,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   __syncthreads();
 
   Compensated acc;
-  double sq = 0.0;          // L2: plain FP64 chain of squares within one tile
+  double sq = 0.0;          // L2: plain FP64 chain of squares within one segment
   unsigned long long maxkey = 0;
   uint32_t seq = 0;         // planes issued by this CTA (identical in every thread)
   uint32_t issued_end = 0;  // thread 0: planes actually issued
@@ -372,28 +422,51 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   int islot = 0;            // thread 0: ring slot of the next plane to issue
   bool ok = true;
 
-  // The (xy tile, z plane) pairs of the range, z fastest, split into
-  // gridDim.x equal contiguous runs (one wave of CTAs): CTA b streams
-  // through [W b / G, W (b+1) / G), one tile column segment at a time.
-  const long long nzr = P.hi[2] - P.lo[2];
-  const long long W = (long long)P.tiles_x * P.tiles_y * nzr;
-  const long long run_end = W * (blockIdx.x + 1) / gridDim.x;
-  for (long long pos = W * blockIdx.x / gridDim.x; pos < run_end;) {
-    const long long col = pos / nzr;
-    const long long zoff = pos - col * nzr;
-    const int zlen = (int)min(nzr - zoff, run_end - pos);
-    pos += zlen;
-    const int txi = (int)(col % P.tiles_x);
-    const int tyi = (int)(col / P.tiles_x);
-    const int64_t x0 = P.x_base + (int64_t)txi * TX;
-    const int64_t y0 = P.y_base + (int64_t)tyi * TY;
-    const int64_t zb = P.lo[2] + zoff;
+  // Single grid: the (xy tile, z plane) pairs of the range, z fastest, split
+  // into gridDim.x equal contiguous runs (one wave of CTAs); CTA b streams
+  // through [W b / G, W (b+1) / G), one tile-column segment at a time.
+  long long pos = 0, run_end = 0;
+  int kseg = 0, kend = 0;
+  if constexpr (BATCH) {
+    kseg = P.cta_seg[blockIdx.x];
+    kend = P.cta_seg[blockIdx.x + 1];
+  } else {
+    const long long nzr = P.inst.hi[2] - P.inst.lo[2];
+    const long long W = (long long)P.inst.tiles_x * P.inst.tiles_y * nzr;
+    pos = W * blockIdx.x / gridDim.x;
+    run_end = W * (blockIdx.x + 1) / gridDim.x;
+  }
+  for (;;) {
+    const InstDesc *I;
+    long long col, zoff;
+    int zlen;
+    if constexpr (BATCH) {
+      if (kseg >= kend) break;
+      const Segment sg = P.segs[kseg];
+      I = &P.insts[sg.inst];
+      col = sg.col;
+      zoff = sg.zoff;
+      zlen = sg.zlen;
+    } else {
+      if (pos >= run_end) break;
+      I = &P.inst;
+      const long long nzr = I->hi[2] - I->lo[2];
+      col = pos / nzr;
+      zoff = pos - col * nzr;
+      zlen = (int)min(nzr - zoff, run_end - pos);
+      pos += zlen;
+    }
+    const int txi = (int)(col % I->tiles_x);
+    const int tyi = (int)(col / I->tiles_x);
+    const int64_t x0 = I->x_base + (int64_t)txi * TX;
+    const int64_t y0 = I->y_base + (int64_t)tyi * TY;
+    const int64_t zb = I->lo[2] + zoff;
     const int total = zlen + 2 * rz;
     const uint32_t g0 = seq;
     seq += total;
 
     // planes are issued and consumed in order, so slots and phases advance
-    // by one per plane: plane q of this tile is z = zb - rz + q
+    // by one per plane: plane q of this segment is z = zb - rz + q
     auto issue = [&](int q) {
       const int slot = islot;
       islot = islot + 1 == R ? 0 : islot + 1;
@@ -401,8 +474,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       mbar_arrive_expect_tx(bar, P.tx_bytes);
       const int zp = (int)(zb - rz + q);
       for (int a = 0; a < P.n_in; ++a)
-        tma_load_3d(ring + (a * R + slot) * P.slot_elems, &P.tmap[a], bar, (int)(x0 - P.AX) + P.cx_add[a],
-                    (int)(y0 - P.RY) + P.cy_add[a], zp + P.cz_add[a]);
+        tma_load_3d(ring + (a * R + slot) * P.slot_elems, &I->tmap[a], bar, (int)(x0 - P.AX) + I->cx_add[a],
+                    (int)(y0 - P.RY) + I->cy_add[a], zp + I->cz_add[a]);
       issued_end = g0 + q + 1;
     };
     auto wait_next = [&]() {
@@ -425,13 +498,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
       y[r] = y0 + wy + r * NW;
-      yok[r] = (y[r] >= P.lo[1]) && (y[r] < P.hi[1]);
+      yok[r] = (y[r] >= I->lo[1]) && (y[r] < I->hi[1]);
     }
     bool xok[VX];
 #pragma unroll
     for (int e = 0; e < VX; ++e) {
       const int64_t x = x0 + lane + 32 * e;
-      xok[e] = (x >= P.lo[0]) && (x < P.hi[0]);
+      xok[e] = (x >= I->lo[0]) && (x < I->hi[0]);
     }
     int smod = wslot + rz;  // slot of the centre plane of step 0
     smod = smod >= R ? smod - R : smod;
@@ -465,7 +538,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
               if (m < Op::n_out(P)) {
-                T *dst = reinterpret_cast<T *>(P.out[m].base) + z * P.out[m].plane + y[r] * P.out[m].pitch + x0 + lane;
+                T *dst =
+                    reinterpret_cast<T *>(I->out[m].base) + z * I->out[m].plane + y[r] * I->out[m].pitch + x0 + lane;
 #pragma unroll
                 for (int e = 0; e < VX; ++e)
                   if (xok[e]) dst[32 * e] = from_arith<T>(o[m][e]);
@@ -503,6 +577,19 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       sq = 0.0;
     }
     if (s_abort) break;
+    if constexpr (BATCH && RED != RED_NONE) {
+      // this segment's partial, in a fixed order; then start afresh
+      double fs = RED == RED_MAXABS ? key_value(maxkey, A(0)) : acc.s;
+      double fc = RED == RED_MAXABS ? 0.0 : acc.c;
+      block_fold<RED>(fs, fc, s_red, NW);
+      if (tid == 0) {
+        P.seg_partials[2 * kseg] = fs;
+        P.seg_partials[2 * kseg + 1] = fc;
+      }
+      acc = Compensated();
+      maxkey = 0;
+    }
+    if constexpr (BATCH) ++kseg;
   }
 
   if (s_abort) {
@@ -514,37 +601,17 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     return;
   }
 
-  if (RED == RED_NONE) return;
+  if constexpr (RED == RED_NONE || BATCH) return;
 
-  // ---- block reduction (fixed shuffle tree), then the last CTA folds all
-  double s = 0.0, c = 0.0;
-  if (RED == RED_MAXABS) {
-    s = key_value(maxkey, A(0));  // widened: one ordering (double bits) from here on
-  } else {
-    s = acc.s;
-    c = acc.c;
-  }
-  for (int off = 16; off > 0; off >>= 1) {
-    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
-    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
-    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
-    else combine_pair(s, c, s2, c2);
-  }
-  if (lane == 0) {
-    s_red[2 * wy] = s;
-    s_red[2 * wy + 1] = c;
-  }
-  __syncthreads();
+  // ---- single grid: CTA partial, then the last CTA folds all partials
+  double s = RED == RED_MAXABS ? key_value(maxkey, A(0)) : acc.s;  // widened: double bits from here on
+  double c = RED == RED_MAXABS ? 0.0 : acc.c;
+  block_fold<RED>(s, c, s_red, NW);
   unsigned int *ticket = reinterpret_cast<unsigned int *>(P.workspace);
   double *partials = reinterpret_cast<double *>(P.workspace + 256);
   if (tid == 0) {
-    double bs = s_red[0], bc = s_red[1];
-    for (int w = 1; w < NW; ++w) {
-      if (RED == RED_MAXABS) bs = max_abs_bits(bs, s_red[2 * w]);
-      else combine_pair(bs, bc, s_red[2 * w], s_red[2 * w + 1]);
-    }
-    partials[2 * blockIdx.x] = bs;
-    partials[2 * blockIdx.x + 1] = bc;
+    partials[2 * blockIdx.x] = s;
+    partials[2 * blockIdx.x + 1] = c;
     __threadfence();
     const unsigned int prev = atomicAdd(ticket, 1u);
     s_last = (prev == gridDim.x - 1);
@@ -553,7 +620,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   if (!s_last) return;
   __threadfence();
   // last CTA: thread i folds a fixed contiguous chunk of partials, then the
-  // fixed shuffle tree and thread 0 fold the threads in order.
+  // fixed tree of block_fold combines the threads in order.
   const int G = gridDim.x;
   const int chunk = (G + blockDim.x - 1) / blockDim.x;
   s = 0.0;
@@ -564,41 +631,43 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     if (RED == RED_MAXABS) s = max_abs_bits(s, ps);
     else combine_pair(s, c, ps, pc);
   }
-  for (int off = 16; off > 0; off >>= 1) {
-    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
-    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
-    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
-    else combine_pair(s, c, s2, c2);
-  }
-  __syncthreads();
-  if (lane == 0) {
-    s_red[2 * wy] = s;
-    s_red[2 * wy + 1] = c;
-  }
-  __syncthreads();
+  block_fold<RED>(s, c, s_red, NW);
   if (tid == 0) {
-    double bs = s_red[0], bc = s_red[1];
-    for (int w = 1; w < NW; ++w) {
-      if (RED == RED_MAXABS) bs = max_abs_bits(bs, s_red[2 * w]);
-      else combine_pair(bs, bc, s_red[2 * w], s_red[2 * w + 1]);
-    }
     double r;
-    if (RED == RED_MAXABS) r = bs;
-    else if (RED == RED_L2) r = sqrt(bs - bc);
-    else r = bs - bc;
+    if (RED == RED_MAXABS) r = s;
+    else if (RED == RED_L2) r = sqrt(s - c);
+    else r = s - c;
     *P.result = r;
     *ticket = 0u;  // ready for the next call
   }
+}
+
+// Per-instance results of a batched reduce: instance i's segments are the
+// contiguous range [inst_seg[i], inst_seg[i + 1]) of the work-list; folded
+// in order (deterministic for a given work-list).
+template <int RED>
+__global__ void batch_finalize_kernel(const double *seg_partials, const int32_t *inst_seg, int n_inst,
+                                      double *results) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_inst) return;
+  double s = 0.0, c = 0.0;
+  for (int k = inst_seg[i]; k < inst_seg[i + 1]; ++k) {
+    if (RED == RED_MAXABS) s = max_abs_bits(s, seg_partials[2 * k]);
+    else combine_pair(s, c, seg_partials[2 * k], seg_partials[2 * k + 1]);
+  }
+  results[i] = RED == RED_MAXABS ? s : (RED == RED_L2 ? sqrt(s - c) : s - c);
 }
 
 // ---------------------------------------------------------------- launching
 struct Plan {
   SweepParams P;
   int threads = 0;
-  long long work = 0;       // (tile, z plane) pairs
+  long long work = 0;         // (tile, z plane) pairs of a single-grid launch
   int max_ctas = 0x7fffffff;  // CTAs the reduction scratch can take partials from
   size_t smem = 0;
-  int op = OP_GENERIC;  // StaticOpId of a matched compile-time operator
+  int op = OP_GENERIC;        // StaticOpId of a matched compile-time operator
+  bool batch = false;         // work-list launch of a batch
+  int batch_ctas = 0;         // its grid (fixed when the work-list was built)
 };
 
 // Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: FP64
@@ -609,11 +678,12 @@ template <> struct VxOf<double> { static constexpr int value = 2; };
 template <typename T> struct VyOf { static constexpr int value = 2; };
 template <> struct VyOf<double> { static constexpr int value = 1; };
 
-// One wave: as many CTAs as the device holds at once (occupancy query per
-// kernel and shape, cached), never more than there are (tile, plane) pairs.
-template <typename T, int VX, int RED, class Op>
-gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
-  auto kern = sweep_kernel<T, VX, VyOf<T>::value, RED, Op>;
+// Launches one wave: as many CTAs as the device holds at once (occupancy
+// query per kernel and shape, cached), never more than there is work.  With
+// occupancy_only set, reports resident CTAs per SM instead of launching.
+template <typename T, int VX, int RED, class Op, bool BATCH>
+gscl_status launch_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
+  auto kern = sweep_kernel<T, VX, VyOf<T>::value, RED, Op, BATCH>;
   static std::mutex mu;
   static size_t attr_set = 0;
   static int cached_threads = -1, cached_blocks = 0, cached_dev = -1;
@@ -639,60 +709,87 @@ gscl_status launch_t(const Plan &pl, cudaStream_t stream) {
     }
     per_sm = cached_blocks;
   }
+  if (occupancy_only) {
+    *occupancy_only = per_sm;
+    return GSCL_OK;
+  }
   const long long slots = (long long)sm_count() * per_sm;
-  const long long ctas = std::min<long long>(pl.work, slots);
+  const long long ctas = BATCH ? (long long)pl.batch_ctas : std::min<long long>(pl.work, slots);
   if (ctas > pl.max_ctas)
     return fail(GSCL_ERR_UNSUPPORTED,
                 "this launch needs %lld partial sums but the reduction scratch holds %d", ctas, pl.max_ctas);
+  if (ctas < 1) return GSCL_OK;
   kern<<<(unsigned)ctas, pl.threads, pl.smem, stream>>>(pl.P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
   return GSCL_OK;
 }
 
+// Operator structures that batched launches are compiled for.
+template <class Def> struct BatchCapable { static constexpr bool value = false; };
+template <> struct BatchCapable<OpHeat7Rhs> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpStar7> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpJacobi7Rhs> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpHeat7RhsFused> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpHeat7Fused> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpResidual7Rhs> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpIdentity> { static constexpr bool value = true; };
+
+inline bool batch_capable(int op) {
+  return op == OP_HEAT7_RHS || op == OP_STAR7 || op == OP_JACOBI7_RHS || op == OP_HEAT7_RHS_FUSED ||
+         op == OP_HEAT7_FUSED || op == OP_RESIDUAL7_RHS || op == OP_IDENTITY;
+}
+
 // Launches the compile-time operator pl.op for storage type T (one
 // translation unit per dtype instantiates these).
-gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream);
-gscl_status launch_static_f32(const Plan &pl, int red, cudaStream_t stream);
-gscl_status launch_static_bf16(const Plan &pl, int red, cudaStream_t stream);
+gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
+gscl_status launch_static_f32(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
+gscl_status launch_static_bf16(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
 
-template <typename T, int RED, class Def>
-gscl_status launch_op(const Plan &pl, cudaStream_t stream) {
+template <typename T, int RED, class Def, bool BATCH>
+gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
   if constexpr (RED != RED_NONE && !op_has_value<Def>()) {
     return fail(GSCL_ERR_INVALID, "reduction of an operator without a value");
   } else if constexpr (RED == RED_NONE && Def::NOUT == 0) {
     return fail(GSCL_ERR_INVALID, "sweep of an operator without outputs");
+  } else if constexpr (BATCH && !BatchCapable<Def>::value) {
+    return fail(GSCL_ERR_INVALID, "no batched kernel for this operator structure");
   } else {
-    return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>>(pl, stream);
+    return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
   }
 }
 
-template <typename T, int RED>
-gscl_status launch_static_red(const Plan &pl, cudaStream_t stream) {
+template <typename T, int RED, bool BATCH>
+gscl_status launch_static_red(const Plan &pl, cudaStream_t stream, int *occ) {
   switch (pl.op) {
-    case OP_HEAT7_RHS: return launch_op<T, RED, OpHeat7Rhs>(pl, stream);
-    case OP_STAR7: return launch_op<T, RED, OpStar7>(pl, stream);
-    case OP_JACOBI7_RHS: return launch_op<T, RED, OpJacobi7Rhs>(pl, stream);
-    case OP_JACOBI5_2D: return launch_op<T, RED, OpJacobi5_2D>(pl, stream);
-    case OP_CLIMATE: return launch_op<T, RED, OpClimate>(pl, stream);
-    case OP_HEAT7_RHS_FUSED: return launch_op<T, RED, OpHeat7RhsFused>(pl, stream);
-    case OP_HEAT7_FUSED: return launch_op<T, RED, OpHeat7Fused>(pl, stream);
-    case OP_RESIDUAL7_RHS: return launch_op<T, RED, OpResidual7Rhs>(pl, stream);
-    case OP_DIFFERENCE: return launch_op<T, RED, OpDifference>(pl, stream);
-    case OP_IDENTITY: return launch_op<T, RED, OpIdentity>(pl, stream);
+    case OP_HEAT7_RHS: return launch_op<T, RED, OpHeat7Rhs, BATCH>(pl, stream, occ);
+    case OP_STAR7: return launch_op<T, RED, OpStar7, BATCH>(pl, stream, occ);
+    case OP_JACOBI7_RHS: return launch_op<T, RED, OpJacobi7Rhs, BATCH>(pl, stream, occ);
+    case OP_JACOBI5_2D: return launch_op<T, RED, OpJacobi5_2D, BATCH>(pl, stream, occ);
+    case OP_CLIMATE: return launch_op<T, RED, OpClimate, BATCH>(pl, stream, occ);
+    case OP_HEAT7_RHS_FUSED: return launch_op<T, RED, OpHeat7RhsFused, BATCH>(pl, stream, occ);
+    case OP_HEAT7_FUSED: return launch_op<T, RED, OpHeat7Fused, BATCH>(pl, stream, occ);
+    case OP_RESIDUAL7_RHS: return launch_op<T, RED, OpResidual7Rhs, BATCH>(pl, stream, occ);
+    case OP_DIFFERENCE: return launch_op<T, RED, OpDifference, BATCH>(pl, stream, occ);
+    case OP_IDENTITY: return launch_op<T, RED, OpIdentity, BATCH>(pl, stream, occ);
   }
   return fail(GSCL_ERR_INVALID, "unknown compile-time operator %d", pl.op);
 }
 
-template <typename T>
-gscl_status launch_static_t(const Plan &pl, int red, cudaStream_t stream) {
+template <typename T, bool BATCH>
+gscl_status launch_static_b(const Plan &pl, int red, cudaStream_t stream, int *occ) {
   switch (red) {
-    case RED_NONE: return launch_static_red<T, RED_NONE>(pl, stream);
-    case RED_SUM: return launch_static_red<T, RED_SUM>(pl, stream);
-    case RED_MAXABS: return launch_static_red<T, RED_MAXABS>(pl, stream);
-    case RED_L2: return launch_static_red<T, RED_L2>(pl, stream);
+    case RED_NONE: return launch_static_red<T, RED_NONE, BATCH>(pl, stream, occ);
+    case RED_SUM: return launch_static_red<T, RED_SUM, BATCH>(pl, stream, occ);
+    case RED_MAXABS: return launch_static_red<T, RED_MAXABS, BATCH>(pl, stream, occ);
+    case RED_L2: return launch_static_red<T, RED_L2, BATCH>(pl, stream, occ);
   }
   return fail(GSCL_ERR_INVALID, "unknown reduction");
+}
+
+template <typename T>
+gscl_status launch_static_t(const Plan &pl, int red, cudaStream_t stream, int *occ) {
+  return pl.batch ? launch_static_b<T, true>(pl, red, stream, occ) : launch_static_b<T, false>(pl, red, stream, occ);
 }
 
 }  // namespace gscl
