@@ -47,6 +47,13 @@ def make_instances(dtype, with_f, seed=0, halo_value=0.0):
     return insts, host
 
 
+def assert_same(got, ref, what):
+    if not torch.equal(got, ref):
+        d = (got.double() - ref.double()).abs()
+        bad = (d > 0).nonzero()
+        raise AssertionError(f"{what}: max diff {d.max().item()} at {bad.shape[0]} cells, first {bad[:3].tolist()}")
+
+
 def alone(dtype, op, u0, f, n, sweeps):
     u, v = B.Grid(n, H, dtype).upload(u0), B.Grid(n, H, dtype).upload(u0)
     ins = [u] + ([B.Grid(n, H, dtype).upload(f)] if f is not None else [])
@@ -67,17 +74,16 @@ def test_batch_sweeps_bitexact_with_single_grid(kernel_path, dtype, with_f, grap
         assert info["specialization"] == (0 if with_f else 1)
     else:
         assert info["specialization"] == -1
+    # like gscl_do_all, each run starts from in[0]: continuing the iteration
+    # swaps in[0] and out[0] between runs (Section 5.2's swap_grids)
     total = 0
-    for sweeps in (3, 4):                  # odd then even: both ping-pong parities
+    for sweeps in (3, 4, 3):               # odd, even, odd: both starting buffers, cached graphs reused
         batch.run(sweeps, graph=graph)
         total += sweeps
-        for (ins, outs), (u0, f), n in zip(insts, host, SHAPES):
+        for k, ((ins, outs), (u0, f), n) in enumerate(zip(insts, host, SHAPES)):
             ref = alone(dtype, op, u0, f, n, total)
-            assert torch.equal(outs[0].download(), ref)
-    batch.run(3, graph=graph)              # replays a cached graph from the other parity
-    total += 3
-    for (ins, outs), (u0, f), n in zip(insts, host, SHAPES):
-        assert torch.equal(outs[0].download(), alone(dtype, op, u0, f, n, total))
+            assert_same(outs[0].download(), ref, f"instance {k} {n} after {total} sweeps")
+            B.swap(ins[0], outs[0])
 
 
 def test_batch_matches_oracle():
@@ -131,8 +137,8 @@ def test_batch_tune_keeps_results():
     assert w in (2, 4, 8) and p in (1, 2, 3)
     # tuning leaves in[0] unchanged: sweeps from here match the instances alone
     batch.run(5, graph=True)
-    for (ins, outs), (u0, f), n in zip(insts, host, SHAPES):
-        assert torch.equal(outs[0].download(), alone("f32", S.heat7(0.125, with_f=False), u0, None, n, 5))
+    for k, ((ins, outs), (u0, f), n) in enumerate(zip(insts, host, SHAPES)):
+        assert_same(outs[0].download(), alone("f32", S.heat7(0.125, with_f=False), u0, None, n, 5), f"instance {k}")
 
 
 def test_batch_rejects_mismatched_instances():
