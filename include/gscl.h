@@ -222,6 +222,19 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
  */
 int32_t gscl_stencil_specialization(const gscl_stencil *op, int32_t n_in, int32_t n_out);
 
+/*
+ * dst(p) = alpha * src(p) (+ dst(p) when accumulate != 0) over `range`
+ * (NULL = the interior), for any pair of storage dtypes: the casts and the
+ * correction of mixed-precision iterative refinement (an FP64 iterate
+ * corrected by an FP32 solve: u64 += d32; an FP64 residual handed to the
+ * FP32 solve: r32 = r64).  Arithmetic in FP64, one rounding to dst's type
+ * (round to nearest even).  Halos are not touched.  Grids must share the
+ * interior extent (GSCL_ERR_SHAPE); src may be dst itself.  No counterpart
+ * in the paper: the mixed-precision solves of the serving workload need it.
+ */
+gscl_status gscl_convert(gscl_grid dst, gscl_grid src, double alpha, int32_t accumulate, const gscl_range *range,
+                         void *stream);
+
 /* Bytes of device workspace one gscl_do_reduce call needs (a constant). */
 int64_t gscl_reduce_workspace_bytes(void);
 

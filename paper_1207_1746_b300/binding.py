@@ -96,6 +96,7 @@ def lib():
         "gscl_sync": [vp],
         "gscl_do_reduce_noalloc": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double),
                                    i32, vp],
+        "gscl_convert": [u64, u64, ctypes.c_double, i32, P(RangeC), vp],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
         "gscl_batch_destroy": [u64],
         "gscl_batch_info": [u64, P(i32), P(i32), P(i32)],
@@ -323,6 +324,12 @@ def do_reduce_noalloc(reduce_op, op, ins, outs=(), rng=None, result=None, stream
                                        _handles(ins), len(ins), _handles(outs), len(outs), _range(rng), rptr,
                                        int(on_host), stream_ptr(stream)))
     return host.value if on_host else None
+
+
+def convert(dst, src, alpha=1.0, accumulate=False, rng=None, stream=None):
+    """gscl_convert: dst = alpha * src (+ dst), across storage dtypes."""
+    check(lib().gscl_convert(dst.handle, src.handle, float(alpha), int(bool(accumulate)), _range(rng),
+                             stream_ptr(stream)))
 
 
 class Batch:

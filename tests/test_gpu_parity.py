@@ -291,3 +291,20 @@ def test_degenerate_single_point_and_zero_halo():
 
 def test_sync_reports_clean_status():
     B.sync()
+
+
+@pytest.mark.parametrize("dst_t,src_t", [("f32", "f64"), ("f64", "f32"), ("f64", "f64"), ("bf16", "f32")])
+def test_convert_cast_and_accumulate(dst_t, src_t):
+    n, h = (70, 21, 9), (1, 1, 1)
+    a = I.random_interior(51, n, h, -3.0, 3.0, halo_value=7.0)
+    b = I.random_interior(52, n, h, -1.0, 1.0, halo_value=9.0)
+    src = B.Grid(n, h, src_t).upload(a)
+    dst = B.Grid(n, h, dst_t).upload(b)
+    B.convert(dst, src, alpha=0.5, accumulate=True, rng=((3, 1, 2), (66, 21, 8)))
+    got = dst.download().double().numpy()
+    sa = as_storage(a, src_t)
+    sb = as_storage(b, dst_t)
+    want = sb.copy()
+    sl = (slice(1 + 2, 1 + 8), slice(1 + 1, 1 + 21), slice(1 + 3, 1 + 66))
+    want[sl] = as_storage(0.5 * sa[sl] + sb[sl], dst_t)  # FP64 arithmetic, one rounding
+    assert np.array_equal(got, want)
