@@ -14,7 +14,7 @@ __device__ __forceinline__ double load_d(const float *p) { return (double)*p; }
 __device__ __forceinline__ double load_d(const __nv_bfloat16 *p) { return (double)__bfloat162float(*p); }
 __device__ __forceinline__ void store_d(double *p, double v) { *p = v; }
 __device__ __forceinline__ void store_d(float *p, double v) { *p = __double2float_rn(v); }
-__device__ __forceinline__ void store_d(__nv_bfloat16 *p, double v) { *p = __float2bfloat16_rn(__double2float_rn(v)); }
+__device__ __forceinline__ void store_d(__nv_bfloat16 *p, double v) { *p = __double2bfloat16(v); }
 
 struct ConvertArgs {
   char *dst;
