@@ -1,0 +1,45 @@
+"""Admission policy of the serving loop, on the CPU: requests are admitted in
+arrival order while the HBM budget and the slot limit allow, and always at
+least one when nothing is active (no GPU work: the solve start is faked)."""
+import numpy as np
+
+from paper_1207_1746_b300 import serving as SV
+
+
+class FakeServer(SV.PoissonServer):
+    def _start(self, req, need):
+        return SV._Slot(req=req, grids={}, bytes=need)
+
+
+def req(rid, n):
+    return SV.Request(rid=rid, n=n, f=np.zeros((n + 2,) * 3))
+
+
+def test_budget_limits_admission_in_fifo_order():
+    one = SV.request_bytes(32, "mixed")
+    srv = FakeServer(mode="mixed", hbm_budget=int(2.5 * one), max_active=10)
+    for r in range(5):
+        srv.submit(req(r, 32))
+    srv._admit()
+    assert [s.req.rid for s in srv.active] == [0, 1]
+    assert srv.in_use == 2 * one
+
+
+def test_oversized_request_runs_alone():
+    srv = FakeServer(mode="fp64", hbm_budget=1, max_active=10)
+    srv.submit(req(0, 64))
+    srv.submit(req(1, 16))
+    srv._admit()
+    assert [s.req.rid for s in srv.active] == [0]
+
+
+def test_slot_limit():
+    srv = FakeServer(mode="fp64", hbm_budget=1 << 40, max_active=3)
+    for r in range(6):
+        srv.submit(req(r, 16))
+    srv._admit()
+    assert len(srv.active) == 3 and len(srv.waiting) == 3
+
+
+def test_mixed_needs_more_memory_than_fp64_grids_alone():
+    assert SV.request_bytes(64, "mixed") > SV.request_bytes(64, "fp64")
