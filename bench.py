@@ -301,6 +301,38 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True):
             "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
 
 
+# ------------------------------------------------------------------ serving workload
+def run_serving(sample=8, window_s=2.0, rate=200.0, time_cap=30.0, check_every=200):
+    """Poisson Jacobi solves (side uniform on 64..256, f uniform in [-1, 1),
+    stop at ||f - A u|| / ||f|| <= 1e-6).  (a) The first `sample` requests all
+    arriving at t = 0, served by the FP64 path and by the mixed-precision path
+    (solves/s and latency of each, and the speedup).  (b) The literal arrival
+    process (Poisson, `rate` per second, seed 5050) over `window_s` seconds,
+    mixed path, stopped after `time_cap` seconds: completed, backlog, p50/p99."""
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import serving as SV
+
+    def reqs(k, arrivals=None):
+        out = []
+        for r in range(k):
+            n, f = I.poisson_request(r)
+            out.append(SV.Request(rid=r, n=n, f=f, arrival=0.0 if arrivals is None else arrivals[r]))
+        return out
+
+    closed = {}
+    for mode in ("mixed", "fp64"):
+        srv = SV.PoissonServer(mode=mode, check_every=check_every)
+        closed[mode] = srv.run_trace(reqs(sample))
+    arrivals = I.poisson_arrivals(rate, window_s)
+    srv = SV.PoissonServer(mode="mixed", check_every=check_every)
+    trace = srv.run_trace(reqs(len(arrivals), arrivals), time_cap=time_cap)
+    trace["rate_per_s"] = rate
+    trace["window_s"] = window_s
+    sides = [I.poisson_request(r)[0] for r in range(sample)]
+    return {"closed": closed, "trace": trace, "sample_sides": sides,
+            "speedup_solves_per_s": closed["mixed"]["solves_per_s"] / max(closed["fp64"]["solves_per_s"], 1e-30)}
+
+
 # ------------------------------------------------------------------ CPU oracle
 def oracle_sample(n=N_SIDE, sweeps=10):
     """The FP64 oracle as it stands on a bounded sample: one fused sweep +
@@ -388,7 +420,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "batched"],
+    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "batched", "serving"],
                     help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances")
     args = ap.parse_args()
     if args.sweeps % EVERY:
@@ -427,6 +459,19 @@ def main():
     torch.cuda.set_device(dist.local)
     dist.init("nccl")
     peaks = measured_peaks()
+    if args.workload == "serving":
+        r = run_serving()
+        line = {"metric": "solves/s", "value": round(r["closed"]["mixed"]["solves_per_s"], 4), "unit": "solves/s",
+                "n_gpus": args.gpus, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "serving: 3D 7-point Poisson Jacobi, side U{64..256}, f U[-1,1), "
+                                       "stop at relative L2 residual 1e-6 (FP64), continuous batching, "
+                                       "HBM-budget admission", "sample_sides": r["sample_sides"]},
+                "closed_sample": r["closed"], "poisson_trace": r["trace"],
+                "speedup_mixed_vs_fp64": round(r["speedup_solves_per_s"], 3)}
+        if dist.rank == 0:
+            print(json.dumps(line))
+        return
     if args.workload == "batched":
         r = run_batched(args.steps, args.warmup)
         t = dist.max(r["ms_per_step"])
