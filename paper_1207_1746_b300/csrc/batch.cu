@@ -6,6 +6,8 @@
 // (in[0] -> out[0] and back), so a whole sweep group can be captured once in
 // a CUDA graph and replayed.  Per-instance reductions write one partial per
 // segment and a second kernel folds each instance's segments in order.
+#include <string.h>
+
 #include <chrono>
 #include <map>
 #include <memory>
@@ -99,7 +101,8 @@ gscl_status build(Batch *bt) {
         }
         bt->base = pl;
       } else if (pl.op != bt->base.op || pl.smem != bt->base.smem || pl.threads != bt->base.threads ||
-                 pl.P.BW != bt->base.P.BW || pl.P.BH != bt->base.P.BH || pl.P.R != bt->base.P.R) {
+                 pl.P.R != bt->base.P.R || memcmp(pl.P.in_bw, bt->base.P.in_bw, sizeof pl.P.in_bw) != 0 ||
+                 memcmp(pl.P.in_bh, bt->base.P.in_bh, sizeof pl.P.in_bh) != 0) {
         return fail(GSCL_ERR_SHAPE, "instance %d plans a different tile shape", i);
       }
       tabs[dir][i] = pl.P.inst;

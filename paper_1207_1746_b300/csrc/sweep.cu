@@ -181,16 +181,20 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
     gscl_term id = {0, 0, 0, 0, GSCL_NONE, GSCL_VALUE, 0, 1.0};
     terms.push_back(id);
   }
-  int rx = 0, ry = 0, rz = 0;  // radii over every grid read
+  // reach per input grid (coefficient reads are at the core element)
+  int rxa[kMaxIn] = {}, rya[kMaxIn] = {}, rz = 0;
   for (auto &t : terms) {
     if (t.in == GSCL_VALUE) continue;
-    rx = std::max(rx, abs((int)t.dx));
-    ry = std::max(ry, abs((int)t.dy));
+    rxa[t.in] = std::max(rxa[t.in], abs((int)t.dx));
+    rya[t.in] = std::max(rya[t.in], abs((int)t.dy));
     rz = std::max(rz, abs((int)t.dz));
   }
   const int vec = 16 / elem;  // TMA x coordinates stay multiples of 16 bytes
-  const int AX = (rx + vec - 1) / vec * vec;
-  const int BW = TX + 2 * AX;
+  int AXa[kMaxIn], BWa[kMaxIn];
+  for (int a = 0; a < n_in; ++a) {
+    AXa[a] = (rxa[a] + vec - 1) / vec * vec;
+    BWa[a] = TX + 2 * AXa[a];
+  }
   const int nz_range = (int)(b.hi[2] - b.lo[2]);
   const int smem_cap = max_smem_per_block();
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
@@ -202,27 +206,31 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   if (cfg.pf > 0 && nz_range > 1) PF = std::min(6, cfg.pf);
   int TY = NW * VY;
   size_t smem = 0;
-  int R = 0, SE = 0, BH = 0;
+  int R = 0, SEa[kMaxIn] = {}, BHa[kMaxIn] = {};
   for (;;) {
     TY = NW * VY;
-    BH = TY + 2 * ry;
-    const int slot_bytes = (BW * BH * elem + 127) / 128 * 128;
-    SE = slot_bytes / elem;
     R = 2 * rz + 1 + PF;
-    smem = kBarBytes + (size_t)n_in * R * slot_bytes;
+    size_t ring = 0;
+    for (int a = 0; a < n_in; ++a) {
+      BHa[a] = TY + 2 * rya[a];
+      SEa[a] = (BWa[a] * BHa[a] * elem + 127) / 128 * 128 / elem;
+      ring += (size_t)R * SEa[a] * elem;
+    }
+    smem = kBarBytes + ring;
     if (smem <= (size_t)smem_cap && R <= kMaxRing) break;
     if (PF > 1) --PF;
     else if (NW > 1) NW /= 2;
     else return fail(GSCL_ERR_UNSUPPORTED, "operator needs %zu bytes of shared memory per CTA", smem);
   }
-  if (BW > 256 || BH > 256) return fail(GSCL_ERR_UNSUPPORTED, "tile box too large for TMA");
+  for (int a = 0; a < n_in; ++a)
+    if (BWa[a] > 256 || BHa[a] > 256) return fail(GSCL_ERR_UNSUPPORTED, "tile box too large for TMA");
   int nt = 0;
   auto push = [&](const gscl_term &t) {
     DevTerm &d = P.terms[nt++];
     d.in = t.in == GSCL_VALUE ? -1 : (int16_t)t.in;
     d.coef = t.coef == GSCL_NONE ? -1 : (int16_t)t.coef;
     d.dz = t.dz;
-    d.toff = (ry + t.dy) * BW + AX + t.dx;
+    d.toff = t.in == GSCL_VALUE ? 0 : (rya[t.in] + t.dy) * BWa[t.in] + AXa[t.in] + t.dx;
     d.wf = (float)t.w;
     d.wd = t.w;
   };
@@ -255,7 +263,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   }
   for (int a = 0; a < n_in; ++a) {
     const Grid &g = b.in[a];
-    if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[a], g, (uint32_t)BW, (uint32_t)BH)) return s;
+    if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[a], g, (uint32_t)BWa[a], (uint32_t)BHa[a])) return s;
     P.inst.cx_add[a] = (int32_t)(g.halo[0] + g.off);
     P.inst.cy_add[a] = g.halo[1];
     P.inst.cz_add[a] = g.halo[2];
@@ -271,13 +279,19 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const int threads = 32 * NW;
   P.R = R;
   P.rz = rz;
-  P.BW = BW;
-  P.BH = BH;
-  P.AX = AX;
-  P.RY = ry;
-  P.slot_elems = SE;
-  P.center = ry * BW + AX;
-  P.tx_bytes = (uint32_t)(n_in * BW * BH * elem);
+  uint32_t tx = 0;
+  int base = 0;
+  for (int a = 0; a < n_in; ++a) {
+    P.in_bw[a] = BWa[a];
+    P.in_bh[a] = BHa[a];
+    P.in_ax[a] = AXa[a];
+    P.in_ry[a] = rya[a];
+    P.in_se[a] = SEa[a];
+    P.in_base[a] = base;
+    base += R * SEa[a];
+    tx += (uint32_t)(BWa[a] * BHa[a] * elem);
+  }
+  P.tx_bytes = tx;
   P.err = device_error_word();
   if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
   pl->threads = threads;

@@ -43,7 +43,7 @@ struct DevTerm {
   int16_t coef;  // input ring of the coefficient, or -1
   int16_t dz;
   int16_t pad;
-  int32_t toff;  // (RY + dy) * BW + AX + dx
+  int32_t toff;  // (RY_in + dy) * BW_in + AX_in + dx, in the read input's box
   float wf;
   double wd;
 };
@@ -77,10 +77,10 @@ struct SweepParams {
   DevTerm terms[kMaxTerms];
   int32_t n_in, n_out, n_value_terms;
   int32_t out_begin[kMaxOut_ + 1];
-  int32_t R, rz;
-  int32_t BW, BH, AX, RY;
-  int32_t slot_elems;
-  int32_t center;     // RY * BW + AX
+  int32_t R, rz;      // ring slots (planes) per input, z reach of the operator
+  // per input: plane box width / height, x apron (rounded to 16 bytes), y
+  // reach, element offset of its ring in shared memory and slot size
+  int32_t in_bw[kMaxIn], in_bh[kMaxIn], in_ax[kMaxIn], in_ry[kMaxIn], in_base[kMaxIn], in_se[kMaxIn];
   uint32_t tx_bytes;  // bytes one plane delivers over all inputs
   // batched launches: CTA b runs segments [cta_seg[b], cta_seg[b + 1])
   const InstDesc *insts;
@@ -195,10 +195,11 @@ struct GenericOp {
   __device__ static int n_out(const SweepParams &P) { return P.n_out; }
 
   template <typename T, int VX>
-  __device__ static __forceinline__ void term(const DevTerm &tm, const T *ring, int smod, int R, int SE, int thr,
-                                              int center, const typename Arith<T>::A (&v)[VX],
+  __device__ static __forceinline__ void term(const SweepParams &P, const DevTerm &tm, const T *ring, int smod,
+                                              int row, int lane, const typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&acc)[VX]) {
     using A = typename Arith<T>::A;
+    const int R = P.R;
     const A w = term_weight(tm, A(0));
     A x[VX];
     if (tm.in < 0) {
@@ -207,12 +208,13 @@ struct GenericOp {
     } else {
       int slot = smod + tm.dz;
       slot = slot >= R ? slot - R : (slot < 0 ? slot + R : slot);
-      const T *p = ring + (tm.in * R + slot) * SE + tm.toff + thr;
+      const T *p = ring + P.in_base[tm.in] + slot * P.in_se[tm.in] + row * P.in_bw[tm.in] + lane + tm.toff;
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
     }
     if (tm.coef >= 0) {
-      const T *cp = ring + (tm.coef * R + smod) * SE + center + thr;
+      const int c = tm.coef;
+      const T *cp = ring + P.in_base[c] + smod * P.in_se[c] + (row + P.in_ry[c]) * P.in_bw[c] + P.in_ax[c] + lane;
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
     }
@@ -221,16 +223,15 @@ struct GenericOp {
   }
 
   template <typename T, int VX>
-  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int thr,
+  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int row, int lane,
                                               typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    const int R = P.R, SE = P.slot_elems;
-    for (int t = 0; t < P.n_value_terms; ++t) term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, v);
+    for (int t = 0; t < P.n_value_terms; ++t) term<T, VX>(P, P.terms[t], ring, smod, row, lane, v, v);
 #pragma unroll
     for (int m = 0; m < kMaxOut; ++m)
       if (m < P.n_out)
         for (int t = P.out_begin[m]; t < P.out_begin[m + 1]; ++t)
-          term<T, VX>(P.terms[t], ring, smod, R, SE, thr, P.center, v, o[m]);
+          term<T, VX>(P, P.terms[t], ring, smod, row, lane, v, o[m]);
   }
 };
 
@@ -241,44 +242,49 @@ struct StaticOp {
   static constexpr int kMaxOut = Def::NOUT > 0 ? Def::NOUT : 1;
   __device__ static constexpr int n_out(const SweepParams &) { return Def::NOUT; }
 
-  static constexpr int radius(int axis) {
+  // reach of the terms reading input `in` (-1: every input) along `axis`
+  __host__ __device__ static constexpr int radius(int axis, int in = -1) {
     int r = 0;
     for (int i = 0; i < Def::NT; ++i) {
       const OpTerm &t = Def::table.t[i];
-      if (t.in < 0) continue;
+      if (t.in < 0 || (in >= 0 && t.in != in)) continue;
       const int d = axis == 0 ? t.dx : axis == 1 ? t.dy : t.dz;
       r = d > r ? d : (-d > r ? -d : r);
     }
     return r;
   }
-  static constexpr int RX = radius(0), RY = radius(1), RZ = radius(2);
+  static constexpr int RZ = radius(2);
 
   template <typename T, int VX, int I>
-  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int R, int SE, int thr,
+  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int row, int lane,
                                               typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX]) {
     using A = typename Arith<T>::A;
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
-    constexpr int AX = (RX + vec - 1) / vec * vec;
-    constexpr int BW = 32 * VX + 2 * AX;
-    constexpr int toff = (RY + t.dy) * BW + AX + t.dx;
-    constexpr int center = RY * BW + AX;
+    const int R = P.R;
     const A w = term_weight(P.terms[I], A(0));
     A x[VX];
     if constexpr (t.in < 0) {
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = v[e];
     } else {
+      constexpr int RX = radius(0, t.in), RY = radius(1, t.in);
+      constexpr int AX = (RX + vec - 1) / vec * vec;
+      constexpr int BW = 32 * VX + 2 * AX;
+      constexpr int toff = (RY + t.dy) * BW + AX + t.dx;
       int slot = smod + t.dz;
       if constexpr (t.dz > 0) slot = slot >= R ? slot - R : slot;
       if constexpr (t.dz < 0) slot = slot < 0 ? slot + R : slot;
-      const T *p = ring + (t.in * R + slot) * SE + thr + toff;
+      const T *p = ring + P.in_base[t.in] + slot * P.in_se[t.in] + row * BW + lane + toff;
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
     }
     if constexpr (t.coef >= 0) {
-      const T *cp = ring + (t.coef * R + smod) * SE + thr + center;
+      constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
+      constexpr int AXc = (RXc + vec - 1) / vec * vec;
+      constexpr int BWc = 32 * VX + 2 * AXc;
+      const T *cp = ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
     }
@@ -292,19 +298,18 @@ struct StaticOp {
   }
 
   template <typename T, int VX, int... I>
-  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int thr,
+  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int row, int lane,
                                                   typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX],
                                                   std::integer_sequence<int, I...>) {
-    const int R = P.R, SE = P.slot_elems;
-    (term<T, VX, I>(P, ring, smod, R, SE, thr, v, o), ...);
+    (term<T, VX, I>(P, ring, smod, row, lane, v, o), ...);
   }
 
   template <typename T, int VX>
-  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int thr,
+  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int row, int lane,
                                               typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    eval_seq<T, VX>(P, ring, smod, thr, v, o, std::make_integer_sequence<int, Def::NT>{});
+    eval_seq<T, VX>(P, ring, smod, row, lane, v, o, std::make_integer_sequence<int, Def::NT>{});
   }
 };
 
@@ -400,9 +405,6 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   const int NW = blockDim.x >> 5;
   const int TY = NW * VY;
   const int R = P.R, rz = P.rz;
-  int thr[VY];
-#pragma unroll
-  for (int r = 0; r < VY; ++r) thr[r] = (wy + r * NW) * P.BW + lane;
 
   if (tid == 0) {
     for (int r = 0; r < R; ++r) mbar_init(&bars[r], 1);
@@ -474,8 +476,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       mbar_arrive_expect_tx(bar, P.tx_bytes);
       const int zp = (int)(zb - rz + q);
       for (int a = 0; a < P.n_in; ++a)
-        tma_load_3d(ring + (a * R + slot) * P.slot_elems, &I->tmap[a], bar, (int)(x0 - P.AX) + I->cx_add[a],
-                    (int)(y0 - P.RY) + I->cy_add[a], zp + I->cz_add[a]);
+        tma_load_3d(ring + P.in_base[a] + slot * P.in_se[a], &I->tmap[a], bar, (int)(x0 - P.in_ax[a]) + I->cx_add[a],
+                    (int)(y0 - P.in_ry[a]) + I->cy_add[a], zp + I->cz_add[a]);
       issued_end = g0 + q + 1;
     };
     auto wait_next = [&]() {
@@ -533,7 +535,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
             for (int m = 0; m < NO; ++m) o[m][e] = A(0);
           }
-          Op::template eval<T, VX>(P, ring, smod, thr[r], v, o);
+          Op::template eval<T, VX>(P, ring, smod, wy + r * NW, lane, v, o);
           if (yok[r]) {
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
