@@ -672,13 +672,13 @@ struct Plan {
   int batch_ctas = 0;         // its grid (fixed when the work-list was built)
 };
 
-// Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: FP64
-// is bound by the FP64 pipe and wants warps; FP32 / BF16 want fewer, fatter
-// threads to amortise the per-plane synchronisation.
+// Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: two
+// rows give each thread independent FMA chains and halve the per-point share
+// of the per-plane synchronisation.
 template <typename T> struct VxOf { static constexpr int value = 4; };
 template <> struct VxOf<double> { static constexpr int value = 2; };
 template <typename T> struct VyOf { static constexpr int value = 2; };
-template <> struct VyOf<double> { static constexpr int value = 1; };
+template <> struct VyOf<double> { static constexpr int value = 2; };
 
 // Launches one wave: as many CTAs as the device holds at once (occupancy
 // query per kernel and shape, cached), never more than there is work.  With
