@@ -372,17 +372,34 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
     if (overlaps(a, c)) return fail(GSCL_ERR_ALIAS, "multi-sweep ping-pong needs distinct in[0] and out[0]");
   }
   Grid src = b.in[0], dst = b.out[0];
-  for (int s = 0; s < sweeps; ++s) {
+  int K = 1;
+  if (sweeps > 1) {
+    std::vector<gscl_term> terms(op->terms, op->terms + op->n_terms);
+    std::vector<int> perm;
+    K = tb_factor(b, match_static(terms, n_in, n_out, &perm), sweeps);
+  }
+  int launches = 0;
+  for (int done = 0; done < sweeps; ++launches) {
     b.in[0] = src;
     b.out[0] = dst;
     for (size_t a = 1; a < b.in.size(); ++a)  // another input naming the ping-pong grid follows it
       if (b.in_h[a] == b.in_h[0]) b.in[a] = src;
     Plan pl;
-    if (gscl_status st = make_plan(b, false, &pl, TileCfg{})) return st;
-    if (gscl_status st = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream, nullptr)) return st;
+    if (K > 1 && sweeps - done >= K) {
+      // K sweeps in one pass over HBM, bit-identical to K single sweeps
+      if (gscl_status st = make_tb_plan(b, K, &pl)) return st;
+      if (gscl_status st = launch_tb(pl, b.in[0].dtype, K, (cudaStream_t)stream)) return st;
+      done += K;
+    } else {
+      if (gscl_status st = make_plan(b, false, &pl, TileCfg{})) return st;
+      if (gscl_status st = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream, nullptr)) return st;
+      done += 1;
+    }
     std::swap(src, dst);
   }
-  if (sweeps > 1 && sweeps % 2 == 0) return swap_storage(in[0], out[0]);
+  // an even number of launches leaves the result in in[0]'s storage: exchange
+  // the handles so out[0] names it
+  if (launches > 1 && launches % 2 == 0) return swap_storage(in[0], out[0]);
   return GSCL_OK;
 }
 

@@ -41,4 +41,10 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg);
 // Launches (or, with occupancy_only, sizes) the kernel a plan names.
 gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only);
 
+// Temporal blocking: sweeps fused per pass for a call (1 = none), the pass
+// plan and its launch (tb.cu).
+int tb_factor(const Bound &b, int op, int sweeps);
+gscl_status make_tb_plan(const Bound &b, int K, Plan *pl);
+gscl_status launch_tb(const Plan &pl, int dtype, int K, cudaStream_t stream);
+
 }  // namespace gscl

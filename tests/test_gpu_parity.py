@@ -308,3 +308,24 @@ def test_convert_cast_and_accumulate(dst_t, src_t):
     sl = (slice(1 + 2, 1 + 8), slice(1 + 1, 1 + 21), slice(1 + 3, 1 + 66))
     want[sl] = as_storage(0.5 * sa[sl] + sb[sl], dst_t)  # FP64 arithmetic, one rounding
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("which", ["heat_rhs", "heat", "poisson"])
+@pytest.mark.parametrize("n,hu", [((150, 37, 21), (1, 1, 1)), ((5, 3, 2), (2, 2, 2)), ((256, 40, 9), (1, 2, 1))])
+def test_temporal_blocking_bitexact_with_single_sweeps(monkeypatch, dtype, which, n, hu):
+    """K sweeps fused per pass (K = 2, 3, 4) give the bits of K single sweeps."""
+    op = {"heat_rhs": S.heat7(0.125), "heat": S.heat7(0.125, with_f=False), "poisson": S.poisson_jacobi()}[which]
+    rhs = which != "heat"
+    u0 = I.random_interior(61, n, hu, -1.0, 1.0, halo_value=0.375)
+    f = I.random_interior(62, n, (0, 0, 0), -1.0, 1.0) if rhs else None
+    results = {}
+    for K in ("1", "2", "3", "4"):
+        monkeypatch.setenv("GSCL_TEMPORAL", K)
+        a, b = B.Grid(n, hu, dtype).upload(u0), B.Grid(n, hu, dtype).upload(u0)
+        ins = [a] + ([B.Grid(n, (0, 0, 0), dtype).upload(f)] if rhs else [])
+        B.do_all(op, ins, [b], sweeps=7)
+        results[K] = b.download()
+    for K in ("2", "3", "4"):
+        d = (results[K].double() - results["1"].double()).abs()
+        assert torch.equal(results[K], results["1"]), (K, d.max().item(), int((d > 0).sum()))
