@@ -266,6 +266,9 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   for (int a = 0; a < n_in; ++a) {
     const Grid &g = b.in[a];
     if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[a], g, (uint32_t)BWa[a], (uint32_t)BHa[a])) return s;
+    P.inst.in[a].base = g.elem_ptr(0, 0, 0);
+    P.inst.in[a].pitch = g.pitch;
+    P.inst.in[a].plane = g.plane;
     P.inst.cx_add[a] = (int32_t)(g.halo[0] + g.off);
     P.inst.cy_add[a] = g.halo[1];
     P.inst.cz_add[a] = g.halo[2];

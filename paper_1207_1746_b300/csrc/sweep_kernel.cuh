@@ -60,6 +60,7 @@ struct OutDesc {
 struct InstDesc {
   CUtensorMap tmap[kMaxIn];
   OutDesc out[kMaxOut_];
+  OutDesc in[kMaxIn];        // the inputs' interior (0,0,0) addresses, for direct loads
   int64_t lo[3], hi[3];
   int64_t x_base, y_base;
   int32_t tiles_x, tiles_y;  // xy tiles covering the range

@@ -63,10 +63,9 @@ gscl_status launch_tb_k(const Plan &pl, int K, cudaStream_t stream) {
 }
 
 template <typename T>
-int max_factor(int op) {
-  const bool rhs = op != OP_STAR7;
-  if (rhs ? tb_fits<T, 4, true>() : tb_fits<T, 4, false>()) return 4;
-  if (rhs ? tb_fits<T, 3, true>() : tb_fits<T, 3, false>()) return 3;
+int max_factor(int) {
+  if (tb_fits<T, 4, true>()) return 4;
+  if (tb_fits<T, 3, true>()) return 3;
   return 2;
 }
 
@@ -91,33 +90,23 @@ int tb_factor(const Bound &b, int op, int sweeps) {
 
 // The single-sweep plan with its tiles and tensor-map boxes replaced by the
 // temporal-blocking tile (TX x TY grown by K) for the same operator.
+template <typename T>
+void tb_geometry(int K, int *TX, int *TY, int *BW0, int *BH0) {
+  switch (K) {
+    case 2: *TX = TbShape<T, 2>::TX, *TY = TbShape<T, 2>::TY, *BW0 = TbShape<T, 2>::BW0, *BH0 = TbShape<T, 2>::BH0; break;
+    case 3: *TX = TbShape<T, 3>::TX, *TY = TbShape<T, 3>::TY, *BW0 = TbShape<T, 3>::BW0, *BH0 = TbShape<T, 3>::BH0; break;
+    default: *TX = TbShape<T, 4>::TX, *TY = TbShape<T, 4>::TY, *BW0 = TbShape<T, 4>::BW0, *BH0 = TbShape<T, 4>::BH0;
+  }
+}
+
 gscl_status make_tb_plan(const Bound &b, int K, Plan *pl) {
   if (gscl_status s = make_plan(b, false, pl, TileCfg{})) return s;
   const Grid &g = b.in[0];
-  int TX, TY, BW0, BH0, BWF, BHF;
-  if (g.dtype == GSCL_F32) {
-    using S2 = TbShape<float, 2>;
-    TX = S2::TX;
-    TY = S2::TY;
-    const int vec = 16 / 4, axk = (K + vec - 1) / vec * vec;
-    BW0 = TX + 2 * axk;
-    BH0 = TY + 2 * K;
-    BWF = BW0;
-    BHF = TY + 2 * (K - 1);
-  } else {
-    using S2 = TbShape<__nv_bfloat16, 2>;
-    TX = S2::TX;
-    TY = S2::TY;
-    const int vec = 16 / 2, axk = (K + vec - 1) / vec * vec;
-    BW0 = TX + 2 * axk;
-    BH0 = TY + 2 * K;
-    BWF = BW0;
-    BHF = TY + 2 * (K - 1);
-  }
+  int TX, TY, BW0, BH0;
+  if (g.dtype == GSCL_F32) tb_geometry<float>(K, &TX, &TY, &BW0, &BH0);
+  else tb_geometry<__nv_bfloat16>(K, &TX, &TY, &BW0, &BH0);
   SweepParams &P = pl->P;
   if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[0], b.in[0], (uint32_t)BW0, (uint32_t)BH0)) return s;
-  if (b.in.size() > 1)
-    if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[1], b.in[1], (uint32_t)BWF, (uint32_t)BHF)) return s;
   P.inst.x_base = 0;
   P.inst.y_base = 0;
   P.inst.tiles_x = (int32_t)((g.n[0] + TX - 1) / TX);
