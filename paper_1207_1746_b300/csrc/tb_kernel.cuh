@@ -134,7 +134,33 @@ __global__ void __launch_bounds__(256) tb_kernel(const __grid_constant__ SweepPa
       yin[r] = Y >= 0 && Y < ny;
     }
 
+    // rhs register queue: fq[t - 1] holds this thread's rhs values of plane
+    // index s - t (what stage t reads at step s); plane s is loaded during
+    // step s, one step before its first use, and shifts down the queue.
+    A fq[RHS ? K : 1][S::VY][S::VX];
+#pragma unroll
+    for (int t = 0; t < (RHS ? K : 1); ++t)
+#pragma unroll
+      for (int r = 0; r < S::VY; ++r)
+#pragma unroll
+        for (int e = 0; e < S::VX; ++e) fq[t][r][e] = A(0);
+
     for (int s = 0; s < total; ++s) {
+      A fnext[S::VY][S::VX];
+      if constexpr (RHS) {
+        const int64_t qn = zb - K + s;
+        const bool zin = qn >= 0 && qn < nz;
+        const T *f_row = reinterpret_cast<const T *>(I.in[1].base) + qn * I.in[1].plane;
+#pragma unroll
+        for (int r = 0; r < S::VY; ++r) {
+          const int64_t Y = y0 + wy + 8 * r - (K - 1);
+#pragma unroll
+          for (int e = 0; e < S::VX; ++e) {
+            const int64_t X = x0 + lane + 32 * e - (K - 1);
+            fnext[r][e] = (zin && yin[r] && xin[e]) ? to_arith(f_row[Y * I.in[1].pitch + X]) : A(0);
+          }
+        }
+      }
       if (ok) {
         ok = mbar_wait_bounded(&bars[wslot], wpar);
         if (ok) {
@@ -156,8 +182,6 @@ __global__ void __launch_bounds__(256) tb_kernel(const __grid_constant__ SweepPa
             const int qi = s - t;                 // plane index of sweep t computed now
             const int64_t q = zb - K + qi;
             const bool zin = q >= 0 && q < nz;
-            const T *f_row = nullptr;
-            if constexpr (RHS) f_row = reinterpret_cast<const T *>(I.in[1].base) + q * I.in[1].plane;
 #pragma unroll
             for (int r = 0; r < S::VY; ++r) {
               const int ly = wy + 8 * r;
@@ -168,8 +192,7 @@ __global__ void __launch_bounds__(256) tb_kernel(const __grid_constant__ SweepPa
                 const int64_t X = x0 + lx - (K - 1);
                 const bool in = zin && yin[r] && xin[e];
                 A f = 0;
-                if constexpr (RHS)
-                  if (in) f = to_arith(f_row[Y * I.in[1].pitch + X]);
+                if constexpr (RHS) f = fq[t - 1][r][e];
                 T val;
                 if (t == 1) {
                   const int off = (ly + 1) * S::BW0 + lx - (K - 1) + S::AXK;
@@ -205,6 +228,18 @@ __global__ void __launch_bounds__(256) tb_kernel(const __grid_constant__ SweepPa
           }
         }
         if (t < K) __syncthreads();
+      }
+      if constexpr (RHS) {
+#pragma unroll
+        for (int t = K - 1; t > 0; --t)
+#pragma unroll
+          for (int r = 0; r < S::VY; ++r)
+#pragma unroll
+            for (int e = 0; e < S::VX; ++e) fq[t][r][e] = fq[t - 1][r][e];
+#pragma unroll
+        for (int r = 0; r < S::VY; ++r)
+#pragma unroll
+          for (int e = 0; e < S::VX; ++e) fq[0][r][e] = fnext[r][e];
       }
       __syncthreads();
       if (s_abort) break;
