@@ -235,6 +235,19 @@ int32_t gscl_stencil_specialization(const gscl_stencil *op, int32_t n_in, int32_
 gscl_status gscl_convert(gscl_grid dst, gscl_grid src, double alpha, int32_t accumulate, const gscl_range *range,
                          void *stream);
 
+/*
+ * Autotuner for multi-sweep gscl_do_all: times K = 1 .. 4 sweeps fused per
+ * pass over memory (temporal blocking; the paper's wide ghost areas,
+ * Section 2, kept on chip) on these grids, trial_sweeps sweeps from in[0]
+ * into out[0] per factor (in[0] is left unchanged), and records the fastest
+ * for this operator structure, dtype and extent; later multi-sweep calls use
+ * it (GSCL_TEMPORAL=K overrides).  Fused passes are bit-identical to single
+ * sweeps.  Only the radius-1 7-point star operators with FP32 / BF16 storage
+ * over the whole interior fuse; otherwise *best_factor = 1.  Synchronises.
+ */
+gscl_status gscl_tune_sweeps(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                             int32_t n_out, int32_t trial_sweeps, void *stream, int32_t *best_factor);
+
 /* Bytes of device workspace one gscl_do_reduce call needs (a constant). */
 int64_t gscl_reduce_workspace_bytes(void);
 

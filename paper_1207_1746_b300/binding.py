@@ -97,6 +97,7 @@ def lib():
         "gscl_do_reduce_noalloc": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double),
                                    i32, vp],
         "gscl_convert": [u64, u64, ctypes.c_double, i32, P(RangeC), vp],
+        "gscl_tune_sweeps": [P(StencilC), P(u64), i32, P(u64), i32, i32, vp, P(i32)],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
         "gscl_batch_destroy": [u64],
         "gscl_batch_info": [u64, P(i32), P(i32), P(i32)],
@@ -324,6 +325,15 @@ def do_reduce_noalloc(reduce_op, op, ins, outs=(), rng=None, result=None, stream
                                        _handles(ins), len(ins), _handles(outs), len(outs), _range(rng), rptr,
                                        int(on_host), stream_ptr(stream)))
     return host.value if on_host else None
+
+
+def tune_sweeps(op, ins, outs, trial_sweeps=8, stream=None):
+    """gscl_tune_sweeps: picks (and remembers) the fastest temporal factor."""
+    st = as_stencil(op)
+    k = ctypes.c_int32()
+    check(lib().gscl_tune_sweeps(ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
+                                 int(trial_sweeps), stream_ptr(stream), ctypes.byref(k)))
+    return k.value
 
 
 def convert(dst, src, alpha=1.0, accumulate=False, rng=None, stream=None):

@@ -406,6 +406,21 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
   return GSCL_OK;
 }
 
+gscl_status gscl_tune_sweeps(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                             int32_t n_out, int32_t trial_sweeps, void *stream, int32_t *best_factor) {
+  if (!best_factor) return fail(GSCL_ERR_INVALID, "best_factor is required");
+  if (trial_sweeps < 1) return fail(GSCL_ERR_INVALID, "trial_sweeps must be >= 1");
+  Bound b;
+  if (gscl_status s = bind(op, false, in, n_in, out, n_out, nullptr, &b)) return s;
+  if (n_out < 1 || b.empty) return fail(GSCL_ERR_INVALID, "tuning needs an output and a non-empty interior");
+  std::vector<gscl_term> terms(op->terms, op->terms + op->n_terms);
+  std::vector<int> perm;
+  int best = 1;
+  gscl_status s = tune_sweeps(b, match_static(terms, n_in, n_out, &perm), trial_sweeps, (cudaStream_t)stream, &best);
+  *best_factor = best;
+  return s;
+}
+
 gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
                            const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
                            int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream) {

@@ -46,5 +46,6 @@ gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int 
 int tb_factor(const Bound &b, int op, int sweeps);
 gscl_status make_tb_plan(const Bound &b, int K, Plan *pl);
 gscl_status launch_tb(const Plan &pl, int dtype, int K, cudaStream_t stream);
+gscl_status tune_sweeps(const Bound &b, int op, int trial_sweeps, cudaStream_t st, int *best_out);
 
 }  // namespace gscl

@@ -2,7 +2,9 @@
 // launching of K fused sweeps per pass.
 #include <stdlib.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "sweep_host.h"
 #include "tb_kernel.cuh"
@@ -71,21 +73,42 @@ int max_factor(int) {
 
 }  // namespace
 
-// Sweeps fused per pass for this call (1: none).  Only the radius-1 star
-// operators in FP32 / BF16 over the whole interior of a 3D grid qualify:
-// FP64 sweeps are bound by the FP64 pipe, where the redundant halo work of
-// fused sweeps costs more than the bytes it saves.
-int tb_factor(const Bound &b, int op, int sweeps) {
-  if (sweeps < 2 || (op != OP_STAR7 && op != OP_HEAT7_RHS && op != OP_JACOBI7_RHS)) return 1;
+// Temporal factors chosen by gscl_tune_sweeps, per (operator, dtype, extent).
+std::mutex g_tb_mu;
+std::map<std::tuple<int, int, int64_t, int64_t, int64_t>, int> g_tb_tuned;
+
+std::tuple<int, int, int64_t, int64_t, int64_t> tb_key(int op, const Grid &g) {
+  return std::make_tuple(op, g.dtype, g.n[0], g.n[1], g.n[2]);
+}
+
+bool tb_eligible(const Bound &b, int op) {
+  if (op != OP_STAR7 && op != OP_HEAT7_RHS && op != OP_JACOBI7_RHS) return false;
   const Grid &g = b.in[0];
-  if (g.ndim != 3 || (g.dtype != GSCL_F32 && g.dtype != GSCL_BF16)) return 1;
+  if (g.ndim != 3 || (g.dtype != GSCL_F32 && g.dtype != GSCL_BF16)) return false;
   for (int a = 0; a < 3; ++a)
-    if (b.lo[a] != 0 || b.hi[a] != g.n[a]) return 1;
-  int K = 2;
-  if (const char *e = getenv("GSCL_TEMPORAL")) K = atoi(e);
+    if (b.lo[a] != 0 || b.hi[a] != g.n[a]) return false;
+  return true;
+}
+
+// Sweeps fused per pass for this call (1: none): GSCL_TEMPORAL if set, else
+// what gscl_tune_sweeps measured for this operator, dtype and extent, else 1
+// (on B300 the single 7-point sweep outruns fused ones; see the tuner).
+// Only the radius-1 star operators in FP32 / BF16 over the whole interior of
+// a 3D grid qualify: FP64 sweeps are bound by the FP64 pipe, where the
+// redundant halo work of fused sweeps costs more than the bytes it saves.
+int tb_factor(const Bound &b, int op, int sweeps) {
+  if (sweeps < 2 || !tb_eligible(b, op)) return 1;
+  const Grid &g = b.in[0];
+  int K = 1;
+  if (const char *e = getenv("GSCL_TEMPORAL")) {
+    K = atoi(e);
+  } else {
+    std::lock_guard<std::mutex> lk(g_tb_mu);
+    auto it = g_tb_tuned.find(tb_key(op, g));
+    if (it != g_tb_tuned.end()) K = it->second;
+  }
   const int kmax = g.dtype == GSCL_F32 ? max_factor<float>(op) : max_factor<__nv_bfloat16>(op);
-  K = std::max(1, std::min(K, std::min(kmax, sweeps)));
-  return K;
+  return std::max(1, std::min(K, std::min(kmax, sweeps)));
 }
 
 // The single-sweep plan with its tiles and tensor-map boxes replaced by the
@@ -119,6 +142,48 @@ gscl_status launch_tb(const Plan &pl, int dtype, int K, cudaStream_t stream) {
   if (dtype == GSCL_F32) return launch_tb_k<float>(pl, K, stream);
   if (dtype == GSCL_BF16) return launch_tb_k<__nv_bfloat16>(pl, K, stream);
   return fail(GSCL_ERR_DTYPE, "temporal blocking is for FP32 / BF16 storage");
+}
+
+// Times K = 1 .. 4 fused sweeps per pass on the caller's grids (trial_sweeps
+// sweeps from in[0] into out[0] per factor) and records the fastest.
+gscl_status tune_sweeps(const Bound &b, int op, int trial_sweeps, cudaStream_t st, int *best_out) {
+  int best = 1;
+  *best_out = 1;
+  if (!tb_eligible(b, op)) return GSCL_OK;
+  const Grid &g = b.in[0];
+  const int kmax = g.dtype == GSCL_F32 ? max_factor<float>(op) : max_factor<__nv_bfloat16>(op);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best_ms = 1e30f;
+  for (int K = 1; K <= kmax; ++K) {
+    Plan pl;
+    gscl_status s = K == 1 ? make_plan(b, false, &pl, TileCfg{}) : make_tb_plan(b, K, &pl);
+    if (s != GSCL_OK) continue;
+    auto once = [&] { return K == 1 ? launch(pl, g.dtype, RED_NONE, st, nullptr) : launch_tb(pl, g.dtype, K, st); };
+    if (once() != GSCL_OK) continue;  // warm-up (and kernel set-up)
+    const int passes = std::max(1, trial_sweeps / K);
+    cudaEventRecord(e0, st);
+    for (int i = 0; i < passes; ++i) once();
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) break;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const float per_sweep = ms / (passes * K);
+    if (per_sweep < best_ms) {
+      best_ms = per_sweep;
+      best = K;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  {
+    std::lock_guard<std::mutex> lk(g_tb_mu);
+    g_tb_tuned[tb_key(op, g)] = best;
+  }
+  *best_out = best;
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "temporal tuning launches");
 }
 
 }  // namespace gscl

@@ -329,3 +329,23 @@ def test_temporal_blocking_bitexact_with_single_sweeps(monkeypatch, dtype, which
     for K in ("2", "3", "4"):
         d = (results[K].double() - results["1"].double()).abs()
         assert torch.equal(results[K], results["1"]), (K, d.max().item(), int((d > 0).sum()))
+
+
+def test_temporal_tuner_picks_a_factor_and_keeps_bits(monkeypatch):
+    monkeypatch.delenv("GSCL_TEMPORAL", raising=False)
+    n, h = (128, 64, 48), (1, 1, 1)
+    u0 = I.random_interior(71, n, h, -1.0, 1.0)
+    f = I.random_interior(72, n, h, -1.0, 1.0)
+    a, b, F = B.Grid(n, h, "f32").upload(u0), B.Grid(n, h, "f32").upload(u0), B.Grid(n, h, "f32").upload(f)
+    k = B.tune_sweeps(S.heat7(0.125), [a, F], [b], trial_sweeps=4)
+    assert 1 <= k <= 4
+    assert torch.equal(a.download(), torch.from_numpy(u0).float())   # in[0] untouched
+    B.do_all(S.heat7(0.125), [a, F], [b], sweeps=6)
+    tuned = b.download()
+    monkeypatch.setenv("GSCL_TEMPORAL", "1")
+    c, d = B.Grid(n, h, "f32").upload(u0), B.Grid(n, h, "f32").upload(u0)
+    B.do_all(S.heat7(0.125), [c, F], [d], sweeps=6)
+    assert torch.equal(tuned, d.download())
+    # FP64 never fuses
+    e, g = B.Grid(n, h).upload(u0), B.Grid(n, h).upload(u0)
+    assert B.tune_sweeps(S.heat7(0.125, with_f=False), [e], [g]) == 1
