@@ -370,6 +370,16 @@ gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_stencil *op, co
  */
 gscl_status gscl_sync(void *stream);
 
+/*
+ * FMA throughput of this device in FLOP/s (2 per fused multiply-add) for
+ * dtype GSCL_F64 or GSCL_F32: a measurement aid for the ALU roofline of the
+ * FP64 sweeps, not an operation of the paper.  Every SM is filled with
+ * threads running 8 independent a <- a * b + c chains for `iters` rounds;
+ * the second of two launches is timed with CUDA events on `stream`.
+ * Synchronises the stream; GSCL_ERR_DTYPE for other dtypes.
+ */
+gscl_status gscl_fma_throughput(int32_t dtype, int32_t iters, double *flops_per_s, void *stream);
+
 /* Static English description of a status code. */
 const char *gscl_status_str(gscl_status s);
 

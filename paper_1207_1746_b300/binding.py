@@ -98,6 +98,7 @@ def lib():
                                    i32, vp],
         "gscl_convert": [u64, u64, ctypes.c_double, i32, P(RangeC), vp],
         "gscl_tune_sweeps": [P(StencilC), P(u64), i32, P(u64), i32, i32, vp, P(i32)],
+        "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
         "gscl_batch_destroy": [u64],
         "gscl_batch_info": [u64, P(i32), P(i32), P(i32)],
@@ -325,6 +326,13 @@ def do_reduce_noalloc(reduce_op, op, ins, outs=(), rng=None, result=None, stream
                                        _handles(ins), len(ins), _handles(outs), len(outs), _range(rng), rptr,
                                        int(on_host), stream_ptr(stream)))
     return host.value if on_host else None
+
+
+def fma_throughput(dtype="f64", iters=2048, stream=None):
+    """gscl_fma_throughput: measured FMA FLOP/s of the device for "f64" / "f32"."""
+    out = ctypes.c_double()
+    check(lib().gscl_fma_throughput(_DTYPES[dtype][0], int(iters), ctypes.byref(out), stream_ptr(stream)))
+    return out.value
 
 
 def tune_sweeps(op, ins, outs, trial_sweeps=8, stream=None):

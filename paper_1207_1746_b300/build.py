@@ -62,14 +62,18 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         return obj
 
     srcs = sources()
-    with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
-        objs = list(ex.map(compile_one, srcs))
+    objs = [os.path.join(OBJ_DIR, os.path.basename(s)[:-3] + f".{tag}.o") for s in srcs]
     tmp = LIB + f".tmp{tag}"
-    subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "static",
-                           "-o", tmp, *objs])
-    for o in objs:
-        os.remove(o)
-    os.replace(tmp, LIB)
+    try:
+        with ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 1))) as ex:
+            list(ex.map(compile_one, srcs))
+        subprocess.check_call([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-cudart", "static",
+                               "-o", tmp, *objs])
+        os.replace(tmp, LIB)
+    finally:  # no objects left behind, whether or not a step failed
+        for o in objs + [tmp]:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

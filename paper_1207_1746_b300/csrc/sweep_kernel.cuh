@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <type_traits>
 #include <utility>
 
 #include "gscl_internal.h"
@@ -83,6 +84,7 @@ struct SweepParams {
   // reach, element offset of its ring in shared memory and slot size
   int32_t in_bw[kMaxIn], in_bh[kMaxIn], in_ax[kMaxIn], in_ry[kMaxIn], in_base[kMaxIn], in_se[kMaxIn];
   uint32_t tx_bytes;  // bytes one plane delivers over all inputs
+  int32_t zalt;       // column-aligned launches: odd z ranges stream downwards
   // batched launches: CTA b runs segments [cta_seg[b], cta_seg[b + 1])
   const InstDesc *insts;
   const Segment *segs;
@@ -439,6 +441,23 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     pos = W * blockIdx.x / gridDim.x;
     run_end = W * (blockIdx.x + 1) / gridDim.x;
   }
+  // With a grid that is a whole multiple of the tile columns, the runs above
+  // are exactly k z ranges of each column (CTA c k + j: range j of column c),
+  // so CTAs j of all columns cover the same planes at the same time and
+  // neighbouring tiles read their shared halo rows close together.  Odd
+  // ranges then stream downwards, so that the plane two consecutive ranges
+  // share is read by both at the start (or both at the end) of their runs.
+  // Slots are then used in decreasing order; slot(z + dz) = slot(z) + dz
+  // still holds, so the operators index the ring the same way.
+  // (compiled for the HBM-bound storage types only: FP64 sweeps keep the
+  // plain even split, see the host planner)
+  bool rev = false;
+  if constexpr (!BATCH && !std::is_same<T, double>::value) {
+    const unsigned long long cols = (unsigned long long)P.inst.tiles_x * (unsigned long long)P.inst.tiles_y;
+    if (P.zalt && cols > 0 && gridDim.x % cols == 0) rev = ((blockIdx.x % (gridDim.x / cols)) & 1u) != 0;
+  }
+  const int dstep = rev ? R - 1 : 1;  // +1 or -1 modulo R
+  auto adv = [&](int sl) { return sl + dstep >= R ? sl + dstep - R : sl + dstep; };
   for (;;) {
     const InstDesc *I;
     long long col, zoff;
@@ -472,10 +491,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     // by one per plane: plane q of this segment is z = zb - rz + q
     auto issue = [&](int q) {
       const int slot = islot;
-      islot = islot + 1 == R ? 0 : islot + 1;
+      islot = adv(islot);
       uint64_t *bar = &bars[slot];
       mbar_arrive_expect_tx(bar, P.tx_bytes);
-      const int zp = (int)(zb - rz + q);
+      const int zp = rev ? (int)(zb + zlen - 1 + rz - q) : (int)(zb - rz + q);
       for (int a = 0; a < P.n_in; ++a)
         tma_load_3d(ring + P.in_base[a] + slot * P.in_se[a], &I->tmap[a], bar, (int)(x0 - P.in_ax[a]) + I->cx_add[a],
                     (int)(y0 - P.in_ry[a]) + I->cy_add[a], zp + I->cz_add[a]);
@@ -484,10 +503,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     auto wait_next = [&]() {
       if (!mbar_wait_bounded(&bars[wslot], wpar)) return false;
       ++waited_end;
-      if (++wslot == R) {
-        wslot = 0;
-        wpar ^= 1u;
-      }
+      wslot = adv(wslot);
+      if (wslot == 0) wpar ^= 1u;
       return true;
     };
 
@@ -509,8 +526,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       const int64_t x = x0 + lane + 32 * e;
       xok[e] = (x >= I->lo[0]) && (x < I->hi[0]);
     }
-    int smod = wslot + rz;  // slot of the centre plane of step 0
-    smod = smod >= R ? smod - R : smod;
+    int smod = wslot;  // slot of the centre plane of step 0
+    for (int i = 0; i < rz; ++i) smod = adv(smod);
 
     for (int s = 0; s < zlen; ++s) {
       if (ok) {
@@ -525,7 +542,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
         }
       }
       if (ok) {
-        const int64_t z = zb + s;
+        const int64_t z = rev ? zb + zlen - 1 - s : zb + s;
 #pragma unroll
         for (int r = 0; r < VY; ++r) {
           A v[VX];
@@ -570,7 +587,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
           }
         }
       }
-      smod = smod + 1 == R ? 0 : smod + 1;
+      smod = adv(smod);
       __syncthreads();
       if (s_abort) break;
       if (tid == 0 && s + R < total) issue(s + R);
@@ -598,8 +615,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   if (s_abort) {
     // a wait gave up: let every copy this CTA issued land before exiting
     if (tid == 0)
-      for (uint32_t g = waited_end; g < issued_end; ++g)
-        mbar_wait_bounded(&bars[g % (uint32_t)R], (g / (uint32_t)R) & 1u);
+      for (uint32_t g = waited_end; g < issued_end; ++g) {
+        const uint32_t r0 = g % (uint32_t)R;
+        mbar_wait_bounded(&bars[rev && r0 ? (uint32_t)R - r0 : r0], (g / (uint32_t)R) & 1u);
+      }
     __syncthreads();
     return;
   }
@@ -717,7 +736,13 @@ gscl_status launch_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
     return GSCL_OK;
   }
   const long long slots = (long long)sm_count() * per_sm;
-  const long long ctas = BATCH ? (long long)pl.batch_ctas : std::min<long long>(pl.work, slots);
+  long long ctas = BATCH ? (long long)pl.batch_ctas : std::min<long long>(pl.work, slots);
+  if (!BATCH && pl.P.zalt) {
+    // column-aligned wave: k z ranges per tile column (see sweep_kernel)
+    const long long cols = (long long)pl.P.inst.tiles_x * pl.P.inst.tiles_y;
+    const long long nz = pl.P.inst.hi[2] - pl.P.inst.lo[2];
+    if (cols > 0 && cols <= slots && nz > 0) ctas = cols * std::min(nz, slots / cols);
+  }
   if (ctas > pl.max_ctas)
     return fail(GSCL_ERR_UNSUPPORTED,
                 "this launch needs %lld partial sums but the reduction scratch holds %d", ctas, pl.max_ctas);

@@ -349,3 +349,16 @@ def test_temporal_tuner_picks_a_factor_and_keeps_bits(monkeypatch):
     # FP64 never fuses
     e, g = B.Grid(n, h).upload(u0), B.Grid(n, h).upload(u0)
     assert B.tune_sweeps(S.heat7(0.125, with_f=False), [e], [g]) == 1
+
+
+def test_fma_throughput_is_plausible():
+    """The measured FP64 / FP32 FMA rates are positive and no faster than the
+    SM count x FMA lanes x maximum clock allows (FP64: 2 per SM per clock on
+    B300-class parts, FP32: 128)."""
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    f64 = B.fma_throughput("f64", 512)
+    f32 = B.fma_throughput("f32", 8192)
+    clock_hz = 2.2e9  # above any B300 SM clock
+    assert 0 < f32 <= sms * 128 * 2 * clock_hz
+    assert 0 < f64 <= f32
