@@ -301,8 +301,111 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True):
             "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
 
 
+# ------------------------------------------------------------------ 2D Laplace workload
+def run_laplace2d(steps, warmup, n=256, sweeps=100):
+    """2D 5-point Jacobi for Laplace on a 256 x 256 FP64 interior (halo
+    sin(pi x), interior uniform [0, 1) from seed 101): one step = 100 sweeps
+    with two ping-pong grids, then the max-abs residual |u_100 - u_99|.  The
+    grid (0.5 MB) lives in L2 and one sweep is ~0.5 us of work, so the sweeps
+    are launch-bound: they run as one batch launch per sweep replayed as a
+    CUDA graph; the same sweeps as one gscl_do_all call (100 launches, no
+    graph) are timed for comparison."""
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    u0 = I.laplace2d(101, n)
+    shape, h = (n, n, 1), (1, 1, 0)
+    u, v = B.Grid(shape, h, "f64", 2).upload(u0), B.Grid(shape, h, "f64", 2).upload(u0)
+    op, diff = B.Stencil(S.jacobi5_2d()), B.Stencil(S.difference())
+    batch = B.Batch(op, [([u], [v])])
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step_graph():
+        batch.run(sweeps, graph=True)          # even: u holds u_100, v holds u_99
+        B.do_reduce(B.MAXABS, diff, [u, v], result=res)
+
+    def step_plain():
+        B.do_all(op, [u], [v], sweeps=sweeps)
+        B.do_reduce(B.MAXABS, diff, [u, v], result=res)
+
+    def timed(fn, k, w):
+        for _ in range(w):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k
+
+    ms_graph = timed(step_graph, steps, warmup)
+    ms_plain = timed(step_plain, steps, warmup)
+    B.sync()
+    return {"points": n * n, "ms_per_step": ms_graph, "ms_per_step_no_graph": ms_plain,
+            "residual": float(res.cpu()[0]), "sweeps": sweeps}
+
+
+# ------------------------------------------------------------------ climate workload
+def run_climate(dtype, steps, warmup, sweeps=50):
+    """The multi-grid operator on 256 x 256 x 80 (halo 2, 2, 1): 8 input grids
+    (q0..q2, kappa, w, t0..t2; smooth fields from seed 303) -> 3 outputs
+    q0'..q2', 50 sweeps per step with the three q grids ping-ponged.  Every
+    input is read once per sweep from HBM: 88 B per point in FP64, 44 B in
+    FP32."""
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    n, h = (256, 256, 80), (2, 2, 1)
+    fields = I.climate(303, n, h)
+    g = {k: B.Grid(n, h, dtype).upload(a) for k, a in fields.items()}
+    cur = [g["q0"], g["q1"], g["q2"]]
+    nxt = [B.Grid(n, h, dtype).upload(fields[k]) for k in ("q0", "q1", "q2")]
+    fixed = [g["kappa"], g["w"], g["t0"], g["t1"], g["t2"]]
+    op = B.Stencil(S.climate())
+    stream = torch.cuda.current_stream()
+    launch_ms = []
+
+    def step(timed_launches=False):
+        nonlocal cur, nxt
+        for k in range(sweeps):
+            if timed_launches and k == sweeps // 2:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                B.do_all(op, cur + fixed, nxt)
+                e1.record(stream)
+                launch_ms.append((e0, e1))
+            else:
+                B.do_all(op, cur + fixed, nxt)
+            cur, nxt = nxt, cur
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step(True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.sync()
+    ms = e0.elapsed_time(e1) / steps
+    lms = sum(a.elapsed_time(b) for a, b in launch_ms) / len(launch_ms)
+    pts = n[0] * n[1] * n[2]
+    return {"points": pts, "ms_per_step": ms, "launch_ms": lms, "sweeps": sweeps,
+            "specialization": B.specialization(op, len(cur + fixed), len(nxt))}
+
+
 # ------------------------------------------------------------------ serving workload
-def run_serving(sample=8, window_s=1.0, rate=200.0, time_cap=20.0, check_every=200):
+def run_serving(sample=8, window_s=10.0, rate=200.0, time_cap=30.0, check_every=200):
     """Poisson Jacobi solves (side uniform on 64..256, f uniform in [-1, 1),
     stop at ||f - A u|| / ||f|| <= 1e-6).  (a) The first `sample` requests all
     arriving at t = 0, served by the FP64 path and by the mixed-precision path
@@ -396,6 +499,12 @@ def roofline_hbm(dtype, plain_ms, points, peaks):
             "peak_source": src}
 
 
+def B_fma():
+    """Measured FP64 FMA rate of this GPU in TFLOP/s (gscl_fma_throughput)."""
+    from paper_1207_1746_b300 import binding as B
+    return B.fma_throughput("f64", 2048) / 1e12
+
+
 # ------------------------------------------------------------------ main
 class _Dist:
     def __init__(self):
@@ -434,8 +543,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "batched", "serving"],
-                    help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances")
+    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "batched", "serving", "laplace2d", "climate"],
+                    help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances; "
+                         "serving: Poisson solve requests; laplace2d: 256^2 FP64 Jacobi, 100 sweeps; "
+                         "climate: 8 -> 3 grid operator on 256 x 256 x 80, FP64 and FP32, 50 sweeps")
     args = ap.parse_args()
     if args.sweeps % EVERY:
         ap.error("--sweeps must be a multiple of 10")
@@ -487,6 +598,69 @@ def main():
         if dist.rank == 0:
             print(json.dumps(line))
         return
+    if args.workload == "laplace2d":
+        r = run_laplace2d(args.steps, args.warmup)
+        t = dist.max(r["ms_per_step"])
+        upd = r["sweeps"] * r["points"]
+        fma_tflops = B_fma()
+        achieved = 2.0 * 4 * upd / (t * 1e-3) / 1e12  # 4 FMA-pipe operations per point
+        line = {"metric": "GPoint-updates/s", "value": round(dist.world * upd / (t * 1e-3) / 1e9, 3),
+                "unit": "GPoint-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(t, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "laplace2d: 2D 5-point Jacobi, 256x256 FP64, halo sin(pi x), interior "
+                                       "U[0,1) seed 101, 100 sweeps (ping-pong, one CUDA graph) + max-abs "
+                                       "residual |u_100 - u_99|", "grid": [256, 256], "halo": 1,
+                           "l2": "L2-resident (2 x 0.5 MB): launch-bound, not HBM-bound"},
+                "roofline": {"bound": "alu", "achieved": round(achieved, 5), "peak": round(fma_tflops, 4),
+                             "unit": "TFLOP/s", "frac": round(achieved / fma_tflops, 5), "traffic": None,
+                             "peak_source": "measured FP64 FMA rate (gscl_fma_throughput)",
+                             "note": "per-sweep time includes the graph's launch gaps"},
+                "ms_per_step_no_graph": round(r["ms_per_step_no_graph"], 4),
+                "graph_speedup": round(r["ms_per_step_no_graph"] / t, 3),
+                "residual_maxabs": r["residual"], "gpu_launches": args.steps * (r["sweeps"] + 1)}
+        if dist.rank == 0:
+            print(json.dumps(line))
+        return
+    if args.workload == "climate":
+        out = {}
+        for dt in ("f64", "f32"):
+            r = run_climate(dt, args.steps, args.warmup)
+            t = dist.max(r["ms_per_step"])
+            upd = r["sweeps"] * r["points"]
+            bpp = {"f64": 88, "f32": 44}[dt]
+            out[dt] = {"value": round(dist.world * upd / (t * 1e-3) / 1e9, 3), "ms_per_step": round(t, 3),
+                       "launch_ms": round(r["launch_ms"], 4), "specialization": r["specialization"],
+                       "hbm_gbs": round(bpp * r["points"] / (r["launch_ms"] * 1e-3) / 1e9, 1)}
+        fma_tflops = B_fma()
+        f64 = out["f64"]
+        # FP64 pipe operations per point of the compile-time climate operator: per output 1 (q) + 13 + 1
+        # (biharmonic run, times kappa) + 2 + 1 (advection run, times w) + 1 (tendency) = 19, x 3 outputs
+        ops = 57
+        ach = 2.0 * ops * 256 * 256 * 80 / (f64["launch_ms"] * 1e-3) / 1e12
+        peak_hbm = measured_peaks().get("hbm_gbs", 6400.0)
+        line = {"metric": "GPoint-updates/s", "value": f64["value"], "unit": "GPoint-updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": f64["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "climate: 8 -> 3 grid operator (13-point biharmonic x kappa + centred "
+                                       "vertical advection x w + tendency), 256x256x80, halo (2,2,1), smooth "
+                                       "fields seed 303, 50 sweeps", "l2": "working set 11 grids > L2"},
+                "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(fma_tflops, 4),
+                             "unit": "TFLOP/s", "frac": round(ach / fma_tflops, 4), "traffic": None,
+                             "peak_source": "measured FP64 FMA rate (gscl_fma_throughput); 57 FP64-pipe "
+                                            "operations per point counted as FMAs"},
+                "kernel_ms": f64["launch_ms"], "hbm_gbs": f64["hbm_gbs"],
+                "variants": {"f32": {"dtype": "f32", "value": out["f32"]["value"],
+                                     "ms_per_step": out["f32"]["ms_per_step"], "kernel_ms": out["f32"]["launch_ms"],
+                                     "roofline": {"bound": "hbm", "achieved": out["f32"]["hbm_gbs"],
+                                                  "peak": peak_hbm, "unit": "GB/s",
+                                                  "frac": round(out["f32"]["hbm_gbs"] / peak_hbm, 4),
+                                                  "traffic": None, "peak_source": "measured"}}},
+                "gpu_launches": 2 * args.steps * 50}
+        if dist.rank == 0:
+            print(json.dumps(line))
+        return
     if args.workload == "batched":
         r = run_batched(args.steps, args.warmup)
         t = dist.max(r["ms_per_step"])
@@ -514,8 +688,7 @@ def main():
     updates = dist.world * args.steps * args.sweeps * args.n ** 3
     value = updates / (t_max * 1e-3) / 1e9
     clocks = sampler.summary()
-    from paper_1207_1746_b300 import binding as B
-    fma_tflops = B.fma_throughput("f64", 2048) / 1e12  # measured FP64 FMA rate (gscl_fma_throughput)
+    fma_tflops = B_fma()
     roof = roofline_fp64(main_run["plain_launch_ms"], args.n ** 3, peaks, clocks.get("sm_mhz"), fma_tflops)
 
     variants = {}

@@ -374,8 +374,9 @@ gscl_status gscl_sync(void *stream);
  * FMA throughput of this device in FLOP/s (2 per fused multiply-add) for
  * dtype GSCL_F64 or GSCL_F32: a measurement aid for the ALU roofline of the
  * FP64 sweeps, not an operation of the paper.  Every SM is filled with
- * threads running 8 independent a <- a * b + c chains for `iters` rounds;
- * the second of two launches is timed with CUDA events on `stream`.
+ * threads running independent a <- a * b + c chains (8 * iters FMAs per
+ * thread); several chain counts and block sizes are timed with CUDA events
+ * on `stream` (best of three launches each) and the fastest is reported.
  * Synchronises the stream; GSCL_ERR_DTYPE for other dtypes.
  */
 gscl_status gscl_fma_throughput(int32_t dtype, int32_t iters, double *flops_per_s, void *stream);

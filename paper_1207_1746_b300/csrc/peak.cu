@@ -4,57 +4,77 @@
 //
 // Every thread runs CH independent chains a <- a * b + c (|b| < 1, so the
 // chains stay bounded and normal), CTAs fill every SM at full occupancy, and
-// the elapsed time of `iters` rounds comes from CUDA events on the caller's
-// stream after one warm-up launch.
+// the elapsed time comes from CUDA events on the caller's stream.  Several
+// chain counts and block sizes are timed (best of three launches each, after
+// a warm-up) and the fastest is reported.
+#include <algorithm>
+
 #include "gscl_internal.h"
 
 namespace gscl {
 namespace {
 
-constexpr int kChains = 8;
-constexpr int kThreads = 256;
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads) fma_chain_kernel(int iters, T b, T c, T *sink) {
-  T a[kChains];
+template <typename T, int CH, int NT>
+__global__ void __launch_bounds__(NT) fma_chain_kernel(int iters, T b, T c, T *sink) {
+  T a[CH];
 #pragma unroll
-  for (int i = 0; i < kChains; ++i) a[i] = T(threadIdx.x + 1 + i) * T(1e-3);
+  for (int i = 0; i < CH; ++i) a[i] = T(threadIdx.x + 1 + i) * T(1e-3);
 #pragma unroll 4
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
-    for (int i = 0; i < kChains; ++i) a[i] = fma(a[i], b, c);
+    for (int i = 0; i < CH; ++i) a[i] = fma(a[i], b, c);
   }
   T s = T(0);
 #pragma unroll
-  for (int i = 0; i < kChains; ++i) s += a[i];
+  for (int i = 0; i < CH; ++i) s += a[i];
   if (s == T(-1)) sink[0] = s;  // never true (the chains converge to c / (1 - b) > 0): keeps them live
+}
+
+// Best of three timed launches (after one warm-up) of one chain count and
+// block size, at full occupancy; FLOP/s, or a negative value on failure.
+template <typename T, int CH, int NT>
+double time_config(int iters, T *sink, cudaStream_t st, cudaEvent_t e0, cudaEvent_t e1) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_chain_kernel<T, CH, NT>, NT, 0) != cudaSuccess)
+    return -1.0;
+  const int blocks = sm_count() * (per_sm > 0 ? per_sm : 1);
+  const int it = std::max(1, iters * 8 / CH);  // the same FMA count per thread for every chain count
+  const T b = T(0.9999), c = T(1e-4);
+  fma_chain_kernel<T, CH, NT><<<blocks, NT, 0, st>>>(it, b, c, sink);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, st);
+    fma_chain_kernel<T, CH, NT><<<blocks, NT, 0, st>>>(it, b, c, sink);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.0;
+    best = std::min(best, ms);
+  }
+  return 2.0 * CH * (double)it * blocks * NT / (best * 1e-3);
 }
 
 template <typename T>
 gscl_status measure(int iters, double *flops_per_s, cudaStream_t st) {
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fma_chain_kernel<T>, kThreads, 0);
-  if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
-  const int blocks = sm_count() * (per_sm > 0 ? per_sm : 1);
   T *sink = nullptr;
-  if ((e = cudaMallocAsync(&sink, sizeof(T), st)) != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
+  cudaError_t e = cudaMallocAsync(&sink, sizeof(T), st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync");
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const T b = T(0.9999), c = T(1e-4);
-  fma_chain_kernel<T><<<blocks, kThreads, 0, st>>>(iters, b, c, sink);  // warm-up
-  cudaEventRecord(e0, st);
-  fma_chain_kernel<T><<<blocks, kThreads, 0, st>>>(iters, b, c, sink);
-  cudaEventRecord(e1, st);
-  e = cudaEventSynchronize(e1);
-  float ms = 0.f;
-  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  const double r[] = {time_config<T, 4, 256>(iters, sink, st, e0, e1), time_config<T, 8, 256>(iters, sink, st, e0, e1),
+                      time_config<T, 16, 256>(iters, sink, st, e0, e1), time_config<T, 8, 128>(iters, sink, st, e0, e1),
+                      time_config<T, 16, 512>(iters, sink, st, e0, e1)};
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFreeAsync(sink, st);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "FMA microbenchmark");
-  *flops_per_s = 2.0 * kChains * (double)iters * blocks * kThreads / (ms * 1e-3);
+  double best = -1.0;
+  for (double v : r) best = std::max(best, v);
+  if (best <= 0.0) return fail(GSCL_ERR_CUDA, "FMA microbenchmark: no configuration ran");
+  *flops_per_s = best;
   return GSCL_OK;
 }
 

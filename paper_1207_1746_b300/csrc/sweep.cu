@@ -299,9 +299,10 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   P.tx_bytes = tx;
   // Column-aligned launches with alternating z direction let L2 serve the
   // halo planes and rows that neighbouring tiles share; they pay off where
-  // the sweep is bound by HBM (FP32 / BF16).  FP64 sweeps are bound by the
-  // FP64 pipe and keep the even split over every resident CTA slot.
-  P.zalt = g0.dtype == GSCL_F64 ? 0 : 1;
+  // the sweep is bound by HBM (FP32 / BF16 sweeps).  FP64 sweeps and fused
+  // reductions (FP64 accumulation) are bound by the FP64 pipe and keep the
+  // even split over every resident CTA slot.
+  P.zalt = (g0.dtype == GSCL_F64 || reduce) ? 0 : 1;
   if (const char *e = getenv("GSCL_ZALT")) P.zalt = atoi(e) != 0;
   P.err = device_error_word();
   if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");

@@ -258,10 +258,22 @@ struct StaticOp {
   }
   static constexpr int RZ = radius(2);
 
+  // A run: consecutive table terms with one coefficient grid and one
+  // destination.  Its terms are summed first and the sum is multiplied by the
+  // coefficient once (sum_t w_t X_t C = C sum_t w_t X_t): one multiply per run
+  // instead of one per term.
+  __host__ __device__ static constexpr bool same_run(int i, int j) {
+    return Def::table.t[i].coef >= 0 && Def::table.t[i].coef == Def::table.t[j].coef &&
+           Def::table.t[i].out == Def::table.t[j].out;
+  }
+  __host__ __device__ static constexpr bool run_first(int i) { return i == 0 || !same_run(i - 1, i); }
+  __host__ __device__ static constexpr bool run_last(int i) { return i == Def::NT - 1 || !same_run(i, i + 1); }
+
   template <typename T, int VX, int I>
   __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int row, int lane,
                                               typename Arith<T>::A (&v)[VX],
-                                              typename Arith<T>::A (&o)[kMaxOut][VX]) {
+                                              typename Arith<T>::A (&o)[kMaxOut][VX],
+                                              typename Arith<T>::A (&g)[VX]) {
     using A = typename Arith<T>::A;
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
@@ -284,14 +296,20 @@ struct StaticOp {
       for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
     }
     if constexpr (t.coef >= 0) {
-      constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
-      constexpr int AXc = (RXc + vec - 1) / vec * vec;
-      constexpr int BWc = 32 * VX + 2 * AXc;
-      const T *cp = ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
 #pragma unroll
-      for (int e = 0; e < VX; ++e) x[e] = x[e] * to_arith(cp[32 * e]);
-    }
-    if constexpr (t.out < 0) {
+      for (int e = 0; e < VX; ++e) g[e] = run_first(I) ? w * x[e] : fma(w, x[e], g[e]);
+      if constexpr (run_last(I)) {
+        constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
+        constexpr int AXc = (RXc + vec - 1) / vec * vec;
+        constexpr int BWc = 32 * VX + 2 * AXc;
+        const T *cp = ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
+#pragma unroll
+        for (int e = 0; e < VX; ++e) {
+          if constexpr (t.out < 0) v[e] = fma(to_arith(cp[32 * e]), g[e], v[e]);
+          else o[t.out][e] = fma(to_arith(cp[32 * e]), g[e], o[t.out][e]);
+        }
+      }
+    } else if constexpr (t.out < 0) {
 #pragma unroll
       for (int e = 0; e < VX; ++e) v[e] = fma(w, x[e], v[e]);
     } else {
@@ -305,7 +323,8 @@ struct StaticOp {
                                                   typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX],
                                                   std::integer_sequence<int, I...>) {
-    (term<T, VX, I>(P, ring, smod, row, lane, v, o), ...);
+    typename Arith<T>::A g[VX];
+    (term<T, VX, I>(P, ring, smod, row, lane, v, o, g), ...);
   }
 
   template <typename T, int VX>
@@ -762,10 +781,11 @@ template <> struct BatchCapable<OpHeat7RhsFused> { static constexpr bool value =
 template <> struct BatchCapable<OpHeat7Fused> { static constexpr bool value = true; };
 template <> struct BatchCapable<OpResidual7Rhs> { static constexpr bool value = true; };
 template <> struct BatchCapable<OpIdentity> { static constexpr bool value = true; };
+template <> struct BatchCapable<OpJacobi5_2D> { static constexpr bool value = true; };
 
 inline bool batch_capable(int op) {
   return op == OP_HEAT7_RHS || op == OP_STAR7 || op == OP_JACOBI7_RHS || op == OP_HEAT7_RHS_FUSED ||
-         op == OP_HEAT7_FUSED || op == OP_RESIDUAL7_RHS || op == OP_IDENTITY;
+         op == OP_HEAT7_FUSED || op == OP_RESIDUAL7_RHS || op == OP_IDENTITY || op == OP_JACOBI5_2D;
 }
 
 // Launches the compile-time operator pl.op for storage type T (one

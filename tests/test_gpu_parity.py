@@ -362,3 +362,32 @@ def test_fma_throughput_is_plausible():
     clock_hz = 2.2e9  # above any B300 SM clock
     assert 0 < f32 <= sms * 128 * 2 * clock_hz
     assert 0 < f64 <= f32
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_heat3d_error_after_200_sweeps_reported(dtype):
+    """Error after N sweeps against the FP64 oracle run from the same initial
+    data (reported, gated only loosely): the heat workload's recipe (seed 202,
+    lam = 1/8, fused L2 residual every 10 sweeps) on a 64^3 interior, 200
+    sweeps, FP64 and FP32 storage.  The FP32 figure is the accumulated
+    storage rounding of 200 sweeps; the FP64 one is rounding-order noise."""
+    n = 64
+    u0, f = I.heat3d(202, n)
+    shape, h = (n, n, n), (1, 1, 1)
+    u, v = B.Grid(shape, h, dtype).upload(u0), B.Grid(shape, h, dtype).upload(u0)
+    F = B.Grid(shape, h, dtype).upload(f)
+    fused, plain = B.Stencil(S.heat7_fused(0.125)), B.Stencil(S.heat7(0.125))
+    res = []
+    for _ in range(20):
+        res.append(B.do_reduce(B.L2, fused, [u, F], [v]))
+        B.swap(u, v)
+        B.do_all(plain, [u, F], [v], sweeps=9)
+        B.swap(u, v)
+    got = u.download().double().numpy()
+    ou, ores = D.heat_run(O.Grid(as_storage(u0, dtype), h), O.Grid(as_storage(f, dtype), h), 0.125, 200, every=10)
+    err = np.max(np.abs(got - ou.a)) / np.max(np.abs(ou.a))
+    rerr = max(abs(a - b) / b for a, b in zip(res, ores))
+    print(f"heat3d 64^3 {dtype}: |u_200 - oracle|_inf / |oracle|_inf = {err:.3e}; "
+          f"max relative residual error = {rerr:.3e}")
+    bound = 1e-12 if dtype == "f64" else 1e-4
+    assert err <= bound and rerr <= bound, (err, rerr)
