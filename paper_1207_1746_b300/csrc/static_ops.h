@@ -11,6 +11,14 @@
 // these tables (constexpr).
 #pragma once
 
+#include <stdint.h>
+
+#ifdef __CUDACC__
+#define GSCL_HD __host__ __device__
+#else
+#define GSCL_HD
+#endif
+
 namespace gscl {
 
 // in = -1: the operator's value; out = -1: a term of the value; coef = -1: none
@@ -104,11 +112,55 @@ struct OpIdentity {
 
 #undef GSCL_AXIAL6
 
+// Inputs an operator reads only at the core element (as a term's grid at
+// offset (0,0,0), or as a coefficient, which is always read there) need one
+// plane box without halo per z step: the sweep kernel stages them in a
+// two-slot "centre ring" loaded one step ahead, apart from the ring of plane
+// boxes that the neighbourhood reads need.
+template <class Def>
+GSCL_HD constexpr bool centre_only(int in) {
+  bool used = false;
+  for (int i = 0; i < Def::NT; ++i) {
+    const OpTerm &t = Def::table.t[i];
+    if (t.coef == in) used = true;
+    if (t.in == in) {
+      used = true;
+      if (t.dx != 0 || t.dy != 0 || t.dz != 0) return false;
+    }
+  }
+  return used;
+}
+
+template <class Def>
+constexpr uint32_t centre_mask() {
+  uint32_t m = 0;
+  for (int a = 0; a < Def::NIN; ++a)
+    if (centre_only<Def>(a)) m |= 1u << a;
+  return m;
+}
+
 template <class Op>
 constexpr bool op_has_value() {
   for (int i = 0; i < Op::NT; ++i)
     if (Op::table.t[i].out < 0) return true;
   return false;
+}
+
+// Centre-ring inputs of a compile-time operator (none for the generic one).
+inline uint32_t static_centre_mask(int op) {
+  switch (op) {
+    case OP_HEAT7_RHS: return centre_mask<OpHeat7Rhs>();
+    case OP_STAR7: return centre_mask<OpStar7>();
+    case OP_JACOBI7_RHS: return centre_mask<OpJacobi7Rhs>();
+    case OP_JACOBI5_2D: return centre_mask<OpJacobi5_2D>();
+    case OP_CLIMATE: return centre_mask<OpClimate>();
+    case OP_HEAT7_RHS_FUSED: return centre_mask<OpHeat7RhsFused>();
+    case OP_HEAT7_FUSED: return centre_mask<OpHeat7Fused>();
+    case OP_RESIDUAL7_RHS: return centre_mask<OpResidual7Rhs>();
+    case OP_DIFFERENCE: return centre_mask<OpDifference>();
+    case OP_IDENTITY: return centre_mask<OpIdentity>();
+  }
+  return 0;
 }
 
 }  // namespace gscl

@@ -197,6 +197,11 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   }
   const int nz_range = (int)(b.hi[2] - b.lo[2]);
   const int smem_cap = max_smem_per_block();
+  std::vector<int> perm;
+  pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
+  // inputs read only at the core element go to the two-slot centre ring
+  const uint32_t cmask = static_centre_mask(pl->op);
+  auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
   const int VY = vy_for(g0.dtype);
   // defaults from tile sweeps on the 256^3 heat workload (B300): FP64 4 warps,
@@ -216,7 +221,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
     for (int a = 0; a < n_in; ++a) {
       BHa[a] = TY + 2 * rya[a];
       SEa[a] = (BWa[a] * BHa[a] * elem + 127) / 128 * 128 / elem;
-      ring += (size_t)R * SEa[a] * elem;
+      ring += (size_t)(centre(a) ? 2 : R) * SEa[a] * elem;
     }
     smem = kBarBytes + ring;
     if (smem <= (size_t)smem_cap && R <= kMaxRing) break;
@@ -236,8 +241,6 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
     d.wf = (float)t.w;
     d.wd = t.w;
   };
-  std::vector<int> perm;
-  pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
   if (pl->op != OP_GENERIC) {
     // table order (value terms first); the kernel reads only the weights
     for (int i : perm) push(terms[i]);
@@ -284,7 +287,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const int threads = 32 * NW;
   P.R = R;
   P.rz = rz;
-  uint32_t tx = 0;
+  uint32_t tx = 0, ctx = 0;
   int base = 0;
   for (int a = 0; a < n_in; ++a) {
     P.in_bw[a] = BWa[a];
@@ -293,10 +296,13 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
     P.in_ry[a] = rya[a];
     P.in_se[a] = SEa[a];
     P.in_base[a] = base;
-    base += R * SEa[a];
-    tx += (uint32_t)(BWa[a] * BHa[a] * elem);
+    base += (centre(a) ? 2 : R) * SEa[a];
+    if (centre(a)) ctx += (uint32_t)(BWa[a] * BHa[a] * elem);
+    else tx += (uint32_t)(BWa[a] * BHa[a] * elem);
   }
   P.tx_bytes = tx;
+  P.cmask = cmask;
+  P.ctx_bytes = ctx;
   // Column-aligned launches with alternating z direction let L2 serve the
   // halo planes and rows that neighbouring tiles share; they pay off where
   // the sweep is bound by HBM (FP32 / BF16 sweeps).  FP64 sweeps and fused

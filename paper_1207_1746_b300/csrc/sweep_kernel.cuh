@@ -30,7 +30,7 @@ constexpr int kMaxTerms = GSCL_MAX_TERMS;
 constexpr int kMaxIn = GSCL_MAX_IN;
 constexpr int kMaxOut_ = GSCL_MAX_OUT;
 constexpr int kBarBytes = 256;                   // up to 32 ring-slot mbarriers
-constexpr int kMaxRing = kBarBytes / 8;
+constexpr int kMaxRing = kBarBytes / 8 - 2;      // the last two serve the centre ring
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz: bounded mbarrier waits
 constexpr int kMaxReduceCtas = 65536;
 constexpr int64_t kWorkspaceBytes = 256 + 16LL * kMaxReduceCtas;
@@ -83,7 +83,11 @@ struct SweepParams {
   // per input: plane box width / height, x apron (rounded to 16 bytes), y
   // reach, element offset of its ring in shared memory and slot size
   int32_t in_bw[kMaxIn], in_bh[kMaxIn], in_ax[kMaxIn], in_ry[kMaxIn], in_base[kMaxIn], in_se[kMaxIn];
-  uint32_t tx_bytes;  // bytes one plane delivers over all inputs
+  uint32_t tx_bytes;  // bytes one plane delivers over all ring inputs
+  // centre-ring inputs (read only at the core element; compile-time operators):
+  // two slots of one TX x TY box each, at in_base[a] + slot * in_se[a]
+  uint32_t cmask;
+  uint32_t ctx_bytes;  // bytes one centre-ring slot receives over all such inputs
   int32_t zalt;       // column-aligned launches: odd z ranges stream downwards
   // batched launches: CTA b runs segments [cta_seg[b], cta_seg[b + 1])
   const InstDesc *insts;
@@ -226,7 +230,7 @@ struct GenericOp {
   }
 
   template <typename T, int VX>
-  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int row, int lane,
+  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int, int row, int lane,
                                               typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX]) {
     for (int t = 0; t < P.n_value_terms; ++t) term<T, VX>(P, P.terms[t], ring, smod, row, lane, v, v);
@@ -269,9 +273,16 @@ struct StaticOp {
   __host__ __device__ static constexpr bool run_first(int i) { return i == 0 || !same_run(i - 1, i); }
   __host__ __device__ static constexpr bool run_last(int i) { return i == Def::NT - 1 || !same_run(i, i + 1); }
 
+  // element (row, lane) of centre-ring input `in` in slot cslot
+  template <typename T, int VX>
+  __device__ static __forceinline__ const T *centre_ptr(const SweepParams &P, const T *ring, int in, int cslot,
+                                                        int row, int lane) {
+    return ring + P.in_base[in] + cslot * P.in_se[in] + row * (32 * VX) + lane;
+  }
+
   template <typename T, int VX, int I>
-  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int row, int lane,
-                                              typename Arith<T>::A (&v)[VX],
+  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int cslot, int row,
+                                              int lane, typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX],
                                               typename Arith<T>::A (&g)[VX]) {
     using A = typename Arith<T>::A;
@@ -283,6 +294,10 @@ struct StaticOp {
     if constexpr (t.in < 0) {
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = v[e];
+    } else if constexpr (centre_only<Def>(t.in)) {
+      const T *p = centre_ptr<T, VX>(P, ring, t.in, cslot, row, lane);
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
     } else {
       constexpr int RX = radius(0, t.in), RY = radius(1, t.in);
       constexpr int AX = (RX + vec - 1) / vec * vec;
@@ -302,7 +317,9 @@ struct StaticOp {
         constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
         constexpr int AXc = (RXc + vec - 1) / vec * vec;
         constexpr int BWc = 32 * VX + 2 * AXc;
-        const T *cp = ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
+        const T *cp = centre_only<Def>(t.coef)
+                          ? centre_ptr<T, VX>(P, ring, t.coef, cslot, row, lane)
+                          : ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
 #pragma unroll
         for (int e = 0; e < VX; ++e) {
           if constexpr (t.out < 0) v[e] = fma(to_arith(cp[32 * e]), g[e], v[e]);
@@ -319,19 +336,19 @@ struct StaticOp {
   }
 
   template <typename T, int VX, int... I>
-  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int row, int lane,
-                                                  typename Arith<T>::A (&v)[VX],
+  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int cslot, int row,
+                                                  int lane, typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX],
                                                   std::integer_sequence<int, I...>) {
     typename Arith<T>::A g[VX];
-    (term<T, VX, I>(P, ring, smod, row, lane, v, o, g), ...);
+    (term<T, VX, I>(P, ring, smod, cslot, row, lane, v, o, g), ...);
   }
 
   template <typename T, int VX>
-  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int row, int lane,
-                                              typename Arith<T>::A (&v)[VX],
+  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int cslot, int row,
+                                              int lane, typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    eval_seq<T, VX>(P, ring, smod, row, lane, v, o, std::make_integer_sequence<int, Def::NT>{});
+    eval_seq<T, VX>(P, ring, smod, cslot, row, lane, v, o, std::make_integer_sequence<int, Def::NT>{});
   }
 };
 
@@ -428,8 +445,14 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   const int TY = NW * VY;
   const int R = P.R, rz = P.rz;
 
+  uint64_t *cbars = bars + kMaxRing;  // the centre ring's two slots
+  const bool has_c = P.cmask != 0;
   if (tid == 0) {
     for (int r = 0; r < R; ++r) mbar_init(&bars[r], 1);
+    if (has_c) {
+      mbar_init(&cbars[0], 1);
+      mbar_init(&cbars[1], 1);
+    }
     fence_mbar_init();
     s_abort = 0;
   }
@@ -444,6 +467,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   int wslot = 0;            // ring slot and phase parity of the next plane to wait for
   uint32_t wpar = 0;
   int islot = 0;            // thread 0: ring slot of the next plane to issue
+  // centre ring: its planes are numbered over the CTA's whole run; plane g
+  // uses slot g & 1 with phase parity (g >> 1) & 1
+  uint32_t c_issued = 0;    // thread 0: centre planes issued
+  uint32_t c_waited = 0;    // centre planes waited for (identical in every thread)
   bool ok = true;
 
   // Single grid: the (xy tile, z plane) pairs of the range, z fastest, split
@@ -515,8 +542,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       mbar_arrive_expect_tx(bar, P.tx_bytes);
       const int zp = rev ? (int)(zb + zlen - 1 + rz - q) : (int)(zb - rz + q);
       for (int a = 0; a < P.n_in; ++a)
-        tma_load_3d(ring + P.in_base[a] + slot * P.in_se[a], &I->tmap[a], bar, (int)(x0 - P.in_ax[a]) + I->cx_add[a],
-                    (int)(y0 - P.in_ry[a]) + I->cy_add[a], zp + I->cz_add[a]);
+        if (!((P.cmask >> a) & 1u))
+          tma_load_3d(ring + P.in_base[a] + slot * P.in_se[a], &I->tmap[a], bar,
+                      (int)(x0 - P.in_ax[a]) + I->cx_add[a], (int)(y0 - P.in_ry[a]) + I->cy_add[a],
+                      zp + I->cz_add[a]);
       issued_end = g0 + q + 1;
     };
     auto wait_next = [&]() {
@@ -527,9 +556,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       return true;
     };
 
+    const uint32_t c0 = c_waited;  // centre plane of this segment's step 0
+    // centre-ring inputs of step s (plane z of that step) into slot (c0 + s) & 1
+    auto issue_c = [&](int st) {
+      const uint32_t g = c0 + (uint32_t)st;
+      uint64_t *bar = &cbars[g & 1u];
+      mbar_arrive_expect_tx(bar, P.ctx_bytes);
+      const int zp = rev ? (int)(zb + zlen - 1 - st) : (int)(zb + st);
+      for (int a = 0; a < P.n_in; ++a)
+        if ((P.cmask >> a) & 1u)
+          tma_load_3d(ring + P.in_base[a] + (int)(g & 1u) * P.in_se[a], &I->tmap[a], bar,
+                      (int)x0 + I->cx_add[a], (int)y0 + I->cy_add[a], zp + I->cz_add[a]);
+      c_issued = g + 1;
+    };
+
     if (tid == 0) {
       const int np = min(R, total);
       for (int q = 0; q < np; ++q) issue(q);
+      if (has_c) {
+        issue_c(0);
+        if (zlen > 1) issue_c(1);
+      }
     }
 
     int64_t y[VY];
@@ -549,11 +596,16 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     for (int i = 0; i < rz; ++i) smod = adv(smod);
 
     for (int s = 0; s < zlen; ++s) {
+      const int cslot = (int)((c0 + (uint32_t)s) & 1u);
       if (ok) {
         if (s == 0) {
           for (int d = 0; d <= 2 * rz && ok; ++d) ok = wait_next();
         } else {
           ok = wait_next();
+        }
+        if (ok && has_c) {
+          ok = mbar_wait_bounded(&cbars[cslot], ((c0 + (uint32_t)s) >> 1) & 1u);
+          if (ok) ++c_waited;
         }
         if (!ok) {
           s_abort = 1;
@@ -572,7 +624,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
             for (int m = 0; m < NO; ++m) o[m][e] = A(0);
           }
-          Op::template eval<T, VX>(P, ring, smod, wy + r * NW, lane, v, o);
+          Op::template eval<T, VX>(P, ring, smod, cslot, wy + r * NW, lane, v, o);
           if (yok[r]) {
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
@@ -610,6 +662,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       __syncthreads();
       if (s_abort) break;
       if (tid == 0 && s + R < total) issue(s + R);
+      if (tid == 0 && has_c && s + 2 < zlen) issue_c(s + 2);
     }
     if (RED == RED_L2) {  // squares are non-negative: the chain's relative error is at most its length x eps
       acc.add(sq);
@@ -638,6 +691,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
         const uint32_t r0 = g % (uint32_t)R;
         mbar_wait_bounded(&bars[rev && r0 ? (uint32_t)R - r0 : r0], (g / (uint32_t)R) & 1u);
       }
+    if (tid == 0)
+      for (uint32_t g = c_waited; g < c_issued; ++g) mbar_wait_bounded(&cbars[g & 1u], (g >> 1) & 1u);
     __syncthreads();
     return;
   }
@@ -760,7 +815,11 @@ gscl_status launch_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
     // column-aligned wave: k z ranges per tile column (see sweep_kernel)
     const long long cols = (long long)pl.P.inst.tiles_x * pl.P.inst.tiles_y;
     const long long nz = pl.P.inst.hi[2] - pl.P.inst.lo[2];
-    if (cols > 0 && cols <= slots && nz > 0) ctas = cols * std::min(nz, slots / cols);
+    // only where it keeps at least 90% of the CTA slots busy
+    if (cols > 0 && cols <= slots && nz > 0) {
+      const long long aligned = cols * std::min(nz, slots / cols);
+      if (10 * aligned >= 9 * std::min(pl.work, slots)) ctas = aligned;
+    }
   }
   if (ctas > pl.max_ctas)
     return fail(GSCL_ERR_UNSUPPORTED,
