@@ -200,7 +200,8 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   std::vector<int> perm;
   pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
   // inputs read only at the core element go to the two-slot centre ring
-  const uint32_t cmask = static_centre_mask(pl->op);
+  // (FP32 / BF16 storage; the kernel's operator tables make the same choice)
+  const uint32_t cmask = g0.dtype == GSCL_F64 ? 0u : static_centre_mask(pl->op);
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
   const int VY = vy_for(g0.dtype);

@@ -273,6 +273,14 @@ struct StaticOp {
   __host__ __device__ static constexpr bool run_first(int i) { return i == 0 || !same_run(i - 1, i); }
   __host__ __device__ static constexpr bool run_last(int i) { return i == Def::NT - 1 || !same_run(i, i + 1); }
 
+  // Centre ring for FP32 / BF16 storage only: FP64 sweeps are bound by the
+  // FP64 pipe, and its extra wait per step costs them more than the shared
+  // memory it frees gains (the host planner makes the same choice).
+  template <typename T>
+  __host__ __device__ static constexpr bool in_centre_ring(int in) {
+    return !std::is_same<T, double>::value && centre_only<Def>(in);
+  }
+
   // element (row, lane) of centre-ring input `in` in slot cslot
   template <typename T, int VX>
   __device__ static __forceinline__ const T *centre_ptr(const SweepParams &P, const T *ring, int in, int cslot,
@@ -294,7 +302,7 @@ struct StaticOp {
     if constexpr (t.in < 0) {
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = v[e];
-    } else if constexpr (centre_only<Def>(t.in)) {
+    } else if constexpr (in_centre_ring<T>(t.in)) {
       const T *p = centre_ptr<T, VX>(P, ring, t.in, cslot, row, lane);
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
@@ -317,7 +325,7 @@ struct StaticOp {
         constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
         constexpr int AXc = (RXc + vec - 1) / vec * vec;
         constexpr int BWc = 32 * VX + 2 * AXc;
-        const T *cp = centre_only<Def>(t.coef)
+        const T *cp = in_centre_ring<T>(t.coef)
                           ? centre_ptr<T, VX>(P, ring, t.coef, cslot, row, lane)
                           : ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
 #pragma unroll
