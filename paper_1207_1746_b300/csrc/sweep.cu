@@ -304,9 +304,9 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   P.tx_bytes = tx;
   P.cmask = cmask;
   P.ctx_bytes = ctx;
-  // Column-aligned launches with alternating z direction let L2 serve the
-  // halo planes and rows that neighbouring tiles share; they pay off where
-  // the sweep is bound by HBM (FP32 / BF16 sweeps).  FP64 sweeps and fused
+  // Column-aligned launches (one z range of one tile column per CTA) let L2
+  // serve the halo rows that neighbouring tiles share; they pay off where the
+  // sweep is bound by HBM (FP32 / BF16 sweeps).  FP64 sweeps and fused
   // reductions (FP64 accumulation) are bound by the FP64 pipe and keep the
   // even split over every resident CTA slot.
   P.zalt = (g0.dtype == GSCL_F64 || reduce) ? 0 : 1;

@@ -1,7 +1,7 @@
 // Device side of the do_all / do_reduce sweep (Section 3 iteration spaces).
 //
 // One kernel serves every dtype, operator and grid shape.  A CTA owns an
-// xy tile of TX x TY core elements (TX = 32 * VX, one warp per tile row,
+// xy tile of TX x TY core elements (TX = 32 * VX, VY adjacent rows per warp,
 // lane l of a warp computing x = l, l + 32, ..., so every shared-memory read
 // of a term is 32 consecutive elements: conflict-free) and streams along z
 // through a chunk of planes (2.5D blocking).  For every input grid it keeps
@@ -88,7 +88,7 @@ struct SweepParams {
   // two slots of one TX x TY box each, at in_base[a] + slot * in_se[a]
   uint32_t cmask;
   uint32_t ctx_bytes;  // bytes one centre-ring slot receives over all such inputs
-  int32_t zalt;       // column-aligned launches: odd z ranges stream downwards
+  int32_t zalt;       // launch a whole multiple of the tile columns (one z range per CTA)
   // batched launches: CTA b runs segments [cta_seg[b], cta_seg[b + 1])
   const InstDesc *insts;
   const Segment *segs;
@@ -160,6 +160,17 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
       : "memory");
 }
 
+// Calls f(std::integral_constant<int, i>) for i = 0 .. N-1 (a loop whose
+// index is a compile-time constant in the body).
+template <class F, int... I>
+__device__ __forceinline__ void static_for_impl(F &&f, std::integer_sequence<int, I...>) {
+  (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_for(F &&f) {
+  static_for_impl(f, std::make_integer_sequence<int, N>{});
+}
+
 // --------------------------------------------------------------- reduction
 // FP64 accumulation of the per-element values.  Within one z-step a thread
 // first adds its VX values in plain FP64, then folds that group sum into a
@@ -199,7 +210,20 @@ __device__ __forceinline__ double max_abs_bits(double a, double b) {
 // Runtime term list (any descriptor the ABI accepts).
 struct GenericOp {
   static constexpr int kMaxOut = kMaxOut_;
+  static constexpr int kQueue = 1;  // no z register queue (size of the unused array)
   __device__ static int n_out(const SweepParams &P) { return P.n_out; }
+
+  template <typename T, int VX, int VY>
+  __device__ static __forceinline__ void advance_queue(const SweepParams &, const T *, int, int, int, bool,
+                                                       typename Arith<T>::A (&)[kQueue][VY][VX]) {}
+
+  template <typename T, int VX, int VY, int r>
+  __device__ static __forceinline__ void eval_row(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
+                                                  int lane, const typename Arith<T>::A (&)[kQueue][VY][VX],
+                                                  typename Arith<T>::A (&v)[VX],
+                                                  typename Arith<T>::A (&o)[kMaxOut][VX]) {
+    eval<T, VX>(P, ring, smod, cslot, row0 + r, lane, v, o);
+  }
 
   template <typename T, int VX>
   __device__ static __forceinline__ void term(const SweepParams &P, const DevTerm &tm, const T *ring, int smod,
@@ -262,6 +286,76 @@ struct StaticOp {
   }
   static constexpr int RZ = radius(2);
 
+  // The z register queue: the one ring input whose centre column is read at
+  // z offsets (the star / heat family's u) keeps that column for planes
+  // z - RZ .. z + RZ in registers, so each step loads one new plane centre
+  // from shared memory instead of 2 RZ + 1, and the y neighbours of a
+  // thread's inner rows are its other rows' centres.  Operators with several
+  // such inputs (the climate operator) read them all from shared memory.
+  __host__ __device__ static constexpr int queue_input() {
+    int found = -1, count = 0;
+    for (int a = 0; a < Def::NIN; ++a) {
+      bool zcol = false;
+      for (int i = 0; i < Def::NT; ++i) {
+        const OpTerm &t = Def::table.t[i];
+        if (t.in == a && t.dx == 0 && t.dy == 0 && t.dz != 0) zcol = true;
+      }
+      if (zcol) {
+        found = a;
+        ++count;
+      }
+    }
+    return count == 1 ? found : -1;
+  }
+  static constexpr int ZQ = queue_input();
+  static constexpr int kQueue = ZQ >= 0 ? 2 * RZ + 1 : 1;
+
+  // centre of the queue input at ring slot `sl`, tile row row0 + r
+  template <typename T, int VX>
+  __device__ static __forceinline__ typename Arith<T>::A queue_load(const SweepParams &P, const T *ring, int sl,
+                                                                    int row, int lane, int e) {
+    constexpr int vec = 16 / (int)sizeof(T);
+    constexpr int AXq = (radius(0, ZQ) + vec - 1) / vec * vec;
+    constexpr int RYq = radius(1, ZQ);
+    constexpr int BWq = 32 * VX + 2 * AXq;
+    return to_arith(ring[P.in_base[ZQ] + sl * P.in_se[ZQ] + (row + RYq) * BWq + AXq + lane + 32 * e]);
+  }
+
+  // Step start: the queue holds planes z - RZ .. z + RZ (all loaded on the
+  // first step of a z range, then shifted by one plane per step).
+  template <typename T, int VX, int VY>
+  __device__ static __forceinline__ void advance_queue(const SweepParams &P, const T *ring, int smod, int row0,
+                                                       int lane, bool first,
+                                                       typename Arith<T>::A (&zq)[kQueue][VY][VX]) {
+    if constexpr (ZQ >= 0) {
+      const int R = P.R;
+      if (first) {
+#pragma unroll
+        for (int k = 0; k <= 2 * RZ; ++k) {
+          int sl = smod + k - RZ;
+          sl = sl >= R ? sl - R : (sl < 0 ? sl + R : sl);
+#pragma unroll
+          for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int e = 0; e < VX; ++e) zq[k][r][e] = queue_load<T, VX>(P, ring, sl, row0 + r, lane, e);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2 * RZ; ++k)
+#pragma unroll
+          for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int e = 0; e < VX; ++e) zq[k][r][e] = zq[k + 1][r][e];
+        int sl = smod + RZ;
+        sl = sl >= R ? sl - R : sl;
+#pragma unroll
+        for (int r = 0; r < VY; ++r)
+#pragma unroll
+          for (int e = 0; e < VX; ++e) zq[2 * RZ][r][e] = queue_load<T, VX>(P, ring, sl, row0 + r, lane, e);
+      }
+    }
+  }
+
   // A run: consecutive table terms with one coefficient grid and one
   // destination.  Its terms are summed first and the sum is multiplied by the
   // coefficient once (sum_t w_t X_t C = C sum_t w_t X_t): one multiply per run
@@ -288,11 +382,14 @@ struct StaticOp {
     return ring + P.in_base[in] + cslot * P.in_se[in] + row * (32 * VX) + lane;
   }
 
-  template <typename T, int VX, int I>
-  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int cslot, int row,
-                                              int lane, typename Arith<T>::A (&v)[VX],
+  // Term I at tile row row0 + r of this thread's VY rows.
+  template <typename T, int VX, int VY, int r, int I>
+  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
+                                              int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                              typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX],
                                               typename Arith<T>::A (&g)[VX]) {
+    const int row = row0 + r;
     using A = typename Arith<T>::A;
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
@@ -306,6 +403,12 @@ struct StaticOp {
       const T *p = centre_ptr<T, VX>(P, ring, t.in, cslot, row, lane);
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
+    } else if constexpr (t.in == ZQ && t.dx == 0 && t.dy == 0) {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = zq[t.dz + RZ][r][e];
+    } else if constexpr (t.in == ZQ && t.dx == 0 && t.dz == 0 && r + t.dy >= 0 && r + t.dy < VY) {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = zq[RZ][r + t.dy][e];
     } else {
       constexpr int RX = radius(0, t.in), RY = radius(1, t.in);
       constexpr int AX = (RX + vec - 1) / vec * vec;
@@ -343,20 +446,22 @@ struct StaticOp {
     }
   }
 
-  template <typename T, int VX, int... I>
-  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int cslot, int row,
-                                                  int lane, typename Arith<T>::A (&v)[VX],
+  template <typename T, int VX, int VY, int r, int... I>
+  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
+                                                  int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                                  typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX],
                                                   std::integer_sequence<int, I...>) {
     typename Arith<T>::A g[VX];
-    (term<T, VX, I>(P, ring, smod, cslot, row, lane, v, o, g), ...);
+    (term<T, VX, VY, r, I>(P, ring, smod, cslot, row0, lane, zq, v, o, g), ...);
   }
 
-  template <typename T, int VX>
-  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int cslot, int row,
-                                              int lane, typename Arith<T>::A (&v)[VX],
-                                              typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    eval_seq<T, VX>(P, ring, smod, cslot, row, lane, v, o, std::make_integer_sequence<int, Def::NT>{});
+  template <typename T, int VX, int VY, int r>
+  __device__ static __forceinline__ void eval_row(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
+                                                  int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                                  typename Arith<T>::A (&v)[VX],
+                                                  typename Arith<T>::A (&o)[kMaxOut][VX]) {
+    eval_seq<T, VX, VY, r>(P, ring, smod, cslot, row0, lane, zq, v, o, std::make_integer_sequence<int, Def::NT>{});
   }
 };
 
@@ -403,7 +508,6 @@ __device__ __forceinline__ double key_value(unsigned long long k, double) { retu
 __device__ __forceinline__ double key_value(unsigned long long k, float) { return (double)__uint_as_float((unsigned)k); }
 
 // ---------------------------------------------------------------- kernel
-// VY rows per thread: rows wy, wy + NW, ... of the tile (NW warps).
 // Folds the CTA's per-thread (s, c) pairs (or max keys) in a fixed order;
 // the result is valid in thread 0.  Uses s_red[2 * warps].
 template <int RED>
@@ -431,7 +535,9 @@ __device__ __forceinline__ void block_fold(double &s, double &c, double *s_red, 
   }
 }
 
-// VY rows per thread: rows wy, wy + NW, ... of the tile (NW warps).
+// Warp wy owns the VY adjacent tile rows wy VY .. wy VY + VY - 1, so the
+// y neighbour of one of its rows is the centre of the next (one shared-memory
+// load serves both).
 // BATCH: segments come from the device work-list and each segment's
 // reduction goes to its own partial (per-instance results are folded by
 // batch_finalize_kernel); otherwise the CTA derives its run of (tile, plane)
@@ -495,23 +601,12 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     pos = W * blockIdx.x / gridDim.x;
     run_end = W * (blockIdx.x + 1) / gridDim.x;
   }
-  // With a grid that is a whole multiple of the tile columns, the runs above
-  // are exactly k z ranges of each column (CTA c k + j: range j of column c),
-  // so CTAs j of all columns cover the same planes at the same time and
-  // neighbouring tiles read their shared halo rows close together.  Odd
-  // ranges then stream downwards, so that the plane two consecutive ranges
-  // share is read by both at the start (or both at the end) of their runs.
-  // Slots are then used in decreasing order; slot(z + dz) = slot(z) + dz
-  // still holds, so the operators index the ring the same way.
-  // (compiled for the HBM-bound storage types only: FP64 sweeps keep the
-  // plain even split, see the host planner)
-  bool rev = false;
-  if constexpr (!BATCH && !std::is_same<T, double>::value) {
-    const unsigned long long cols = (unsigned long long)P.inst.tiles_x * (unsigned long long)P.inst.tiles_y;
-    if (P.zalt && cols > 0 && gridDim.x % cols == 0) rev = ((blockIdx.x % (gridDim.x / cols)) & 1u) != 0;
-  }
-  const int dstep = rev ? R - 1 : 1;  // +1 or -1 modulo R
-  auto adv = [&](int sl) { return sl + dstep >= R ? sl + dstep - R : sl + dstep; };
+  // With a grid that is a whole multiple of the tile columns (zalt), the
+  // runs above are exactly k z ranges of each column (CTA c k + j: range j of
+  // column c), so the CTAs j of all columns cover the same planes at the same
+  // time and neighbouring tiles read their shared halo rows close together
+  // (the second read is served by L2).
+  auto adv = [&](int sl) { return sl + 1 == R ? 0 : sl + 1; };
   for (;;) {
     const InstDesc *I;
     long long col, zoff;
@@ -548,7 +643,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       islot = adv(islot);
       uint64_t *bar = &bars[slot];
       mbar_arrive_expect_tx(bar, P.tx_bytes);
-      const int zp = rev ? (int)(zb + zlen - 1 + rz - q) : (int)(zb - rz + q);
+      const int zp = (int)(zb - rz + q);
       for (int a = 0; a < P.n_in; ++a)
         if (!((P.cmask >> a) & 1u))
           tma_load_3d(ring + P.in_base[a] + slot * P.in_se[a], &I->tmap[a], bar,
@@ -570,7 +665,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       const uint32_t g = c0 + (uint32_t)st;
       uint64_t *bar = &cbars[g & 1u];
       mbar_arrive_expect_tx(bar, P.ctx_bytes);
-      const int zp = rev ? (int)(zb + zlen - 1 - st) : (int)(zb + st);
+      const int zp = (int)(zb + st);
       for (int a = 0; a < P.n_in; ++a)
         if ((P.cmask >> a) & 1u)
           tma_load_3d(ring + P.in_base[a] + (int)(g & 1u) * P.in_se[a], &I->tmap[a], bar,
@@ -591,7 +686,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     bool yok[VY];
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
-      y[r] = y0 + wy + r * NW;
+      y[r] = y0 + wy * VY + r;
       yok[r] = (y[r] >= I->lo[1]) && (y[r] < I->hi[1]);
     }
     bool xok[VX];
@@ -602,6 +697,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     }
     int smod = wslot;  // slot of the centre plane of step 0
     for (int i = 0; i < rz; ++i) smod = adv(smod);
+    A zq[Op::kQueue][VY][VX];  // z register queue (compile-time operators of the star family)
 
     for (int s = 0; s < zlen; ++s) {
       const int cslot = (int)((c0 + (uint32_t)s) & 1u);
@@ -621,9 +717,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
         }
       }
       if (ok) {
-        const int64_t z = rev ? zb + zlen - 1 - s : zb + s;
-#pragma unroll
-        for (int r = 0; r < VY; ++r) {
+        const int64_t z = zb + s;
+        Op::template advance_queue<T, VX, VY>(P, ring, smod, wy * VY, lane, s == 0, zq);
+        static_for<VY>([&](auto rc) {
+          constexpr int r = decltype(rc)::value;
           A v[VX];
           A o[NO][VX];
 #pragma unroll
@@ -632,7 +729,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
             for (int m = 0; m < NO; ++m) o[m][e] = A(0);
           }
-          Op::template eval<T, VX>(P, ring, smod, cslot, wy + r * NW, lane, v, o);
+          Op::template eval_row<T, VX, VY, r>(P, ring, smod, cslot, wy * VY, lane, zq, v, o);
           if (yok[r]) {
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
@@ -664,7 +761,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
               acc.add(gsum);
             }
           }
-        }
+        });
       }
       smod = adv(smod);
       __syncthreads();
@@ -695,10 +792,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   if (s_abort) {
     // a wait gave up: let every copy this CTA issued land before exiting
     if (tid == 0)
-      for (uint32_t g = waited_end; g < issued_end; ++g) {
-        const uint32_t r0 = g % (uint32_t)R;
-        mbar_wait_bounded(&bars[rev && r0 ? (uint32_t)R - r0 : r0], (g / (uint32_t)R) & 1u);
-      }
+      for (uint32_t g = waited_end; g < issued_end; ++g)
+        mbar_wait_bounded(&bars[g % (uint32_t)R], (g / (uint32_t)R) & 1u);
     if (tid == 0)
       for (uint32_t g = c_waited; g < c_issued; ++g) mbar_wait_bounded(&cbars[g & 1u], (g >> 1) & 1u);
     __syncthreads();
