@@ -152,6 +152,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
   return true;
 }
 
+// Programmatic dependent launch: a grid launched with the programmatic
+// serialisation attribute may start while the previous grid on its stream is
+// still running.  launch_dependents lets the next grid begin launching;
+// wait blocks until every prerequisite grid has completed and its memory is
+// visible (a no-op for a grid launched without the attribute).
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
@@ -571,6 +579,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     s_abort = 0;
   }
   __syncthreads();
+  // Nothing above touches global memory: wait here for the previous sweep
+  // (its outputs are this sweep's inputs).
+  pdl_wait();
 
   Compensated acc;
   double sq = 0.0;          // L2: plain FP64 chain of squares within one segment
@@ -789,6 +800,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     if constexpr (BATCH) ++kseg;
   }
 
+  // this CTA's sweep work is done: the next sweep may begin launching (it
+  // still waits for this whole grid before reading anything)
+  pdl_launch_dependents();
+
   if (s_abort) {
     // a wait gave up: let every copy this CTA issued land before exiting
     if (tid == 0)
@@ -928,8 +943,19 @@ gscl_status launch_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
     return fail(GSCL_ERR_UNSUPPORTED,
                 "this launch needs %lld partial sums but the reduction scratch holds %d", ctas, pl.max_ctas);
   if (ctas < 1) return GSCL_OK;
-  kern<<<(unsigned)ctas, pl.threads, pl.smem, stream>>>(pl.P);
-  cudaError_t e = cudaGetLastError();
+  // programmatic dependent launch: the kernel waits for its predecessor on
+  // the stream itself, so the launch latency overlaps the previous sweep
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3((unsigned)pl.threads);
+  cfg.dynamicSmemBytes = pl.smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, pl.P);
   if (e != cudaSuccess) return cuda_fail(e, "sweep kernel launch");
   return GSCL_OK;
 }
