@@ -53,16 +53,17 @@ def measured_peaks():
 
 
 def profile_traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary (a line
-    'traffic <key> <bytes>' in profiles/sweep_kernel_heat3d_256.md), else None."""
-    path = os.path.join(ROOT, "profiles", "sweep_kernel_heat3d_256.md")
-    try:
-        for line in open(path):
-            parts = line.strip().strip("`").split()
-            if len(parts) == 3 and parts[0] == "traffic" and parts[1] == kernel_key:
-                return float(parts[2])
-    except OSError:
-        pass
+    """DRAM bytes per launch from the committed ncu summaries (a line
+    'traffic <key> <bytes>' in one of profiles/*.md), else None."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        try:
+            for line in open(path):
+                parts = line.strip().strip("`").split()
+                if len(parts) == 3 and parts[0] == "traffic" and parts[1] == kernel_key:
+                    return float(parts[2])
+        except OSError:
+            pass
     return None
 
 
@@ -247,7 +248,7 @@ def run_e2e(dtype, steps, warmup, n=N_SIDE, sweeps=SWEEPS):
 
 
 # ------------------------------------------------------------------ batched workload
-def run_batched(steps, warmup, count=96, sweeps=100, tune=True):
+def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
     """96 independent 3D 7-point heat instances (sides uniform on 32..224 per
     axis, FP32 storage, zero 1-cell halo, lam = 1/8), `sweeps` sweeps of all
     of them per step: one launch per sweep from the batch's work-list, the
@@ -285,6 +286,12 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True):
         return e0.elapsed_time(e1) / k
 
     ms_batch = timed(lambda: batch.run(sweeps, graph=True), steps, warmup)
+    if not compare:  # profiling run: the graph replay only
+        B.sync()
+        return {"points": points, "ms_per_step": ms_batch, "value": sweeps * points / (ms_batch * 1e-3) / 1e9,
+                "sweep_ms": ms_batch / sweeps, "hbm_gbs": 8 * points / (ms_batch / sweeps * 1e-3) / 1e9,
+                "per_instance_loop_ms": float("nan"), "speedup_vs_loop": float("nan"), "tuned": cfg, "info": info,
+                "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
     # one sweep of the batch alone (no graph) for the roofline
     ms_sweep = timed(lambda: batch.run(1), 5 * steps, 2)
 
@@ -302,7 +309,7 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True):
 
 
 # ------------------------------------------------------------------ 2D Laplace workload
-def run_laplace2d(steps, warmup, n=256, sweeps=100):
+def run_laplace2d(steps, warmup, n=256, sweeps=100, compare=True):
     """2D 5-point Jacobi for Laplace on a 256 x 256 FP64 interior (halo
     sin(pi x), interior uniform [0, 1) from seed 101): one step = 100 sweeps
     with two ping-pong grids, then the max-abs residual |u_100 - u_99|.  The
@@ -345,7 +352,7 @@ def run_laplace2d(steps, warmup, n=256, sweeps=100):
         return e0.elapsed_time(e1) / k
 
     ms_graph = timed(step_graph, steps, warmup)
-    ms_plain = timed(step_plain, steps, warmup)
+    ms_plain = timed(step_plain, steps, warmup) if compare else float("nan")
     B.sync()
     return {"points": n * n, "ms_per_step": ms_graph, "ms_per_step_no_graph": ms_plain,
             "residual": float(res.cpu()[0]), "sweeps": sweeps}
@@ -499,8 +506,13 @@ def roofline_hbm(dtype, plain_ms, points, peaks):
             "peak_source": src}
 
 
+PROFILE = False  # --profile: short runs for profilers, without the FMA microbenchmark
+
+
 def B_fma():
     """Measured FP64 FMA rate of this GPU in TFLOP/s (gscl_fma_throughput)."""
+    if PROFILE:
+        return float("nan")
     from paper_1207_1746_b300 import binding as B
     return B.fma_throughput("f64", 2048) / 1e12
 
@@ -543,11 +555,18 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="one short step for profilers: no warm-up, tuner, comparison runs, e2e, CPU leg or "
+                         "FMA microbenchmark (the printed numbers are not benchmark values)")
     ap.add_argument("--workload", default="heat3d", choices=["heat3d", "batched", "serving", "laplace2d", "climate"],
                     help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances; "
                          "serving: Poisson solve requests; laplace2d: 256^2 FP64 Jacobi, 100 sweeps; "
                          "climate: 8 -> 3 grid operator on 256 x 256 x 80, FP64 and FP32, 50 sweeps")
     args = ap.parse_args()
+    if args.profile:
+        global PROFILE
+        PROFILE = True
+        args.steps, args.warmup, args.no_e2e, args.no_cpu = 1, 0, True, True
     if args.sweeps % EVERY:
         ap.error("--sweeps must be a multiple of 10")
     dist = _Dist()
@@ -599,7 +618,7 @@ def main():
             print(json.dumps(line))
         return
     if args.workload == "laplace2d":
-        r = run_laplace2d(args.steps, args.warmup)
+        r = run_laplace2d(args.steps, args.warmup, compare=not args.profile)
         t = dist.max(r["ms_per_step"])
         upd = r["sweeps"] * r["points"]
         fma_tflops = B_fma()
@@ -647,7 +666,7 @@ def main():
                                        "vertical advection x w + tendency), 256x256x80, halo (2,2,1), smooth "
                                        "fields seed 303, 50 sweeps", "l2": "working set 11 grids > L2"},
                 "roofline": {"bound": "alu", "achieved": round(ach, 4), "peak": round(fma_tflops, 4),
-                             "unit": "TFLOP/s", "frac": round(ach / fma_tflops, 4), "traffic": None,
+                             "unit": "TFLOP/s", "frac": round(ach / fma_tflops, 4), "traffic": profile_traffic("climate_f64"),
                              "peak_source": "measured FP64 FMA rate (gscl_fma_throughput); 57 FP64-pipe "
                                             "operations per point counted as FMAs"},
                 "kernel_ms": f64["launch_ms"], "hbm_gbs": f64["hbm_gbs"],
@@ -656,13 +675,14 @@ def main():
                                      "roofline": {"bound": "hbm", "achieved": out["f32"]["hbm_gbs"],
                                                   "peak": peak_hbm, "unit": "GB/s",
                                                   "frac": round(out["f32"]["hbm_gbs"] / peak_hbm, 4),
-                                                  "traffic": None, "peak_source": "measured"}}},
+                                                  "traffic": profile_traffic("climate_f32"),
+                                                  "peak_source": "measured"}}},
                 "gpu_launches": 2 * args.steps * 50}
         if dist.rank == 0:
             print(json.dumps(line))
         return
     if args.workload == "batched":
-        r = run_batched(args.steps, args.warmup)
+        r = run_batched(args.steps, args.warmup, tune=not args.profile, compare=not args.profile)
         t = dist.max(r["ms_per_step"])
         line = {"metric": "GPoint-updates/s", "value": round(dist.world * 100 * r["points"] / (t * 1e-3) / 1e9, 3),
                 "unit": "GPoint-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -674,7 +694,7 @@ def main():
                            "l2": "working set 2 x %.2f GB > L2" % (4 * r["points"] / 1e9)},
                 "roofline": {"bound": "hbm", "achieved": round(r["hbm_gbs"], 1), "peak": peaks.get("hbm_gbs", 6400.0),
                              "unit": "GB/s", "frac": round(r["hbm_gbs"] / peaks.get("hbm_gbs", 6400.0), 4),
-                             "traffic": None},
+                             "traffic": profile_traffic("batched_sweep")},
                 "per_instance_loop_ms": round(r["per_instance_loop_ms"], 3),
                 "speedup_vs_per_instance_loop": round(r["speedup_vs_loop"], 3),
                 "tuned_warps_prefetch": r["tuned"], "batch": r["info"], "gpu_launches": args.steps * 100}
