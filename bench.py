@@ -183,6 +183,53 @@ def run_gpu(dtype, steps, warmup, dist, n=N_SIDE, sweeps=SWEEPS, clocks=None):
             "launches": steps * sweeps, "points": n ** 3, "residuals": residuals}
 
 
+def run_fusion_ablation(dtype, reps=20, n=N_SIDE):
+    """Section 5.2's fused diffusion + convergence test against the two-pass
+    form on the heat workload: one fused sweep returning the L2 residual of
+    the iterate it reads, against a plain sweep plus a separate residual
+    reduction over the same iterate (u and f read twice).  Mean per pair of
+    operations, CUDA events on the launching stream."""
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    h = (1, 1, 1)
+    shape = (n, n, n)
+    u0, f = I.heat3d(SEED, n)
+    u, v = B.Grid(shape, h, dtype).upload(u0), B.Grid(shape, h, dtype).upload(u0)
+    F = B.Grid(shape, h, dtype).upload(f)
+    fused, plain, resid = B.Stencil(S.heat7_fused(LAM)), B.Stencil(S.heat7(LAM)), B.Stencil(S.residual7())
+    res = torch.zeros(2, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def fused_step():
+        B.do_reduce(B.L2, fused, [u, F], [v], result=res[0:1])
+
+    def two_pass_step():
+        B.do_all(plain, [u, F], [v])
+        B.do_reduce(B.L2, resid, [u, F], [], result=res[1:2])
+
+    out = {}
+    for name, fn in (("fused_ms", fused_step), ("two_pass_ms", two_pass_step)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / reps, 4)
+    B.sync()
+    out["speedup"] = round(out["two_pass_ms"] / out["fused_ms"], 3)
+    r = res.cpu().tolist()
+    out["residuals_agree_rel"] = abs(r[0] - r[1]) / max(abs(r[1]), 1e-300)
+    return out
+
+
 class _Null:
     def __enter__(self):
         return self
@@ -730,6 +777,11 @@ def main():
                "unit": "GPoint-updates/s", "h2d_bytes_per_step": e["h2d"], "d2h_bytes_per_step": e["d2h"],
                "ms_per_step": round(e_ms, 3)}
 
+    # Section 5.2's fused vs two-pass comparison (outside the timed region)
+    ablation = None
+    if not args.profile:
+        ablation = {dt: run_fusion_ablation(dt, n=args.n) for dt in ("f64", "f32")}
+
     cpu = None
     if dist.rank == 0 and not args.no_cpu:
         c = oracle_sample(args.n, EVERY)
@@ -745,7 +797,8 @@ def main():
                 "gpu_launches": main_run["launches"],
                 "kernel_ms": {"plain_sweep": round(main_run["plain_launch_ms"], 4),
                               "fused_sweep_l2": round(main_run["fused_launch_ms"], 4)},
-                "final_residual": main_run["residuals"][-1], "variants": variants}
+                "final_residual": main_run["residuals"][-1], "variants": variants,
+                "fusion_ablation": ablation}
         print(json.dumps(line))
 
 

@@ -275,6 +275,20 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
                            int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
+ * The convergence test of Section 5.2 as a reduction: do_reduce of the
+ * operator's returned value with logical_and over the per-element tests
+ * |value| <= eps.  *result is 1.0 if every element of the range passes (also
+ * for an empty range) and 0.0 otherwise; a NaN value fails.  Equivalent to
+ * max |value| <= eps, computed by the MAXABS tree and decided on the device
+ * by the last CTA, so the decision can stay on the GPU (result_on_host = 0).
+ * Arguments, outputs, workspace and errors as gscl_do_reduce; eps must be
+ * >= 0 (GSCL_ERR_INVALID otherwise).
+ */
+gscl_status gscl_do_reduce_within(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                                  int32_t n_out, const gscl_range *range, double eps, double *result,
+                                  int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
  * Batched sweeps (many independent grid sets of one operator).
  *
  * A batch binds one operator to n_inst instances; instance i uses grids

@@ -60,7 +60,7 @@
 #define ORC_NONE 255  /* coef == ORC_NONE: no coefficient grid */
 
 enum { ORC_OK = 0, ORC_BAD_ARG = 1, ORC_BAD_RANGE = 2 };
-enum { ORC_SUM = 0, ORC_MAXABS = 1, ORC_L2 = 2 };
+enum { ORC_SUM = 0, ORC_MAXABS = 1, ORC_L2 = 2, ORC_WITHIN = 3 };
 
 typedef struct {
   int32_t dx, dy, dz;
@@ -200,10 +200,9 @@ static void orc_neumaier_add(orc_neumaier *a, double x) {
  * n_terms == 0 the per-element value is In_0(p) and no output is written;
  * otherwise the operator runs as in orc_do_all (outputs included) and its
  * value is reduced. */
-int orc_do_reduce(int op, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
-                  const orc_out_grid *out, int n_terms, const orc_term *terms,
-                  const int64_t lo[3], const int64_t hi[3], double *result) {
-  if (op != ORC_SUM && op != ORC_MAXABS && op != ORC_L2) return ORC_BAD_ARG;
+static int reduce_impl(int op, double eps, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                       const orc_out_grid *out, int n_terms, const orc_term *terms,
+                       const int64_t lo[3], const int64_t hi[3], double *result) {
   if (n_terms == 0) {
     if (n_in < 1 || n_out != 0) return ORC_BAD_ARG;
     orc_term id = {0, 0, 0, 0, ORC_NONE, ORC_VALUE, 1.0};
@@ -216,6 +215,7 @@ int orc_do_reduce(int op, const orc_extent *e, int n_in, const orc_grid *in, int
   orc_neumaier acc = {0.0, 0.0};
   double mx = 0.0;
   int saw_nan = 0;
+  int all_within = 1; /* logical_and of |v| <= eps (a NaN compares false) */
   for (int64_t k = lo[2]; k < hi[2]; ++k)
     for (int64_t j = lo[1]; j < hi[1]; ++j)
       for (int64_t i = lo[0]; i < hi[0]; ++i) {
@@ -229,7 +229,9 @@ int orc_do_reduce(int op, const orc_extent *e, int n_in, const orc_grid *in, int
             out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r;
           }
         }
-        if (op == ORC_SUM) {
+        if (op == ORC_WITHIN) {
+          all_within = all_within && (fabs(v) <= eps);
+        } else if (op == ORC_SUM) {
           orc_neumaier_add(&acc, v);
         } else if (op == ORC_L2) {
 #if ORC_MUTANT == 8
@@ -246,8 +248,25 @@ int orc_do_reduce(int op, const orc_extent *e, int n_in, const orc_grid *in, int
           else if (fabs(v) > mx) mx = fabs(v);
         }
       }
-  if (op == ORC_SUM) *result = acc.s + acc.c;
+  if (op == ORC_WITHIN) *result = all_within ? 1.0 : 0.0;
+  else if (op == ORC_SUM) *result = acc.s + acc.c;
   else if (op == ORC_L2) *result = sqrt(acc.s + acc.c);
   else *result = saw_nan ? NAN : mx;
   return ORC_OK;
+}
+
+int orc_do_reduce(int op, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                  const orc_out_grid *out, int n_terms, const orc_term *terms,
+                  const int64_t lo[3], const int64_t hi[3], double *result) {
+  if (op != ORC_SUM && op != ORC_MAXABS && op != ORC_L2) return ORC_BAD_ARG;
+  return reduce_impl(op, 0.0, e, n_in, in, n_out, out, n_terms, terms, lo, hi, result);
+}
+
+/* Section 5.2's convergence test as a reduction: the logical_and over the
+ * range of |value| <= eps, as 1.0 or 0.0 (1.0 for an empty range). */
+int orc_do_reduce_within(double eps, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                         const orc_out_grid *out, int n_terms, const orc_term *terms,
+                         const int64_t lo[3], const int64_t hi[3], double *result) {
+  if (!(eps >= 0.0)) return ORC_BAD_ARG;
+  return reduce_impl(ORC_WITHIN, eps, e, n_in, in, n_out, out, n_terms, terms, lo, hi, result);
 }

@@ -89,6 +89,8 @@ def _get_lib():
                                       ctypes.c_int, ctypes.POINTER(_Term), i64p, i64p,
                                       ctypes.POINTER(ctypes.c_double)]
         lib.orc_do_reduce.restype = ctypes.c_int
+        lib.orc_do_reduce_within.argtypes = [ctypes.c_double] + lib.orc_do_reduce.argtypes[1:]
+        lib.orc_do_reduce_within.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -164,6 +166,18 @@ def do_all(terms, ins, outs, lo=None, hi=None, abs_mode=False, want_value=False)
     if rc != 0:
         raise ValueError(f"oracle do_all rejected the call (code {rc})")
     return val
+
+
+def do_reduce_within(eps, terms, ins, outs=(), lo=None, hi=None) -> float:
+    """Section 5.2's convergence test as a reduction: 1.0 if every element of
+    ``[lo, hi)`` has |value| <= eps (logical_and; a NaN fails), else 0.0."""
+    ext, gin, gout, tt, clo, chi = _marshal(terms, ins, outs, lo, hi)
+    res = ctypes.c_double(0.0)
+    rc = _get_lib().orc_do_reduce_within(ctypes.c_double(eps), ctypes.byref(ext), len(ins), gin, len(outs), gout,
+                                         len(terms), tt, clo, chi, ctypes.byref(res))
+    if rc != 0:
+        raise ValueError(f"oracle do_reduce_within rejected the call (code {rc})")
+    return float(res.value)
 
 
 def do_reduce(op, terms, ins, outs=(), lo=None, hi=None) -> float:

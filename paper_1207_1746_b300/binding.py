@@ -99,6 +99,8 @@ def lib():
         "gscl_convert": [u64, u64, ctypes.c_double, i32, P(RangeC), vp],
         "gscl_tune_sweeps": [P(StencilC), P(u64), i32, P(u64), i32, i32, vp, P(i32)],
         "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
+        "gscl_do_reduce_within": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), ctypes.c_double,
+                                  P(ctypes.c_double), i32, vp, i64, vp],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
         "gscl_batch_destroy": [u64],
         "gscl_batch_info": [u64, P(i32), P(i32), P(i32)],
@@ -306,6 +308,27 @@ def do_reduce(reduce_op, op, ins, outs=(), rng=None, result=None, stream=None):
     check(lib().gscl_do_reduce(int(reduce_op), ctypes.byref(st.c) if st is not None else None, _handles(ins),
                                len(ins), _handles(outs), len(outs), _range(rng), rptr, int(on_host),
                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream_ptr(stream)))
+    return host.value if on_host else None
+
+
+def do_reduce_within(eps, op, ins, outs=(), rng=None, result=None, stream=None):
+    """gscl_do_reduce_within: 1.0 if every |value| <= eps over the range (the
+    logical_and convergence test of Section 5.2), else 0.0.  Same ``result``
+    convention as do_reduce."""
+    st = as_stencil(op)
+    ws = workspace(stream)
+    on_host = result is None
+    if on_host:
+        host = ctypes.c_double(0.0)
+        rptr = ctypes.pointer(host)
+    else:
+        if result.dtype != torch.float64 or not result.is_cuda:
+            raise ValueError("result must be a float64 CUDA tensor")
+        rptr = ctypes.cast(ctypes.c_void_p(result.data_ptr()), ctypes.POINTER(ctypes.c_double))
+    check(lib().gscl_do_reduce_within(ctypes.byref(st.c) if st is not None else None, _handles(ins), len(ins),
+                                      _handles(outs), len(outs), _range(rng), ctypes.c_double(eps), rptr,
+                                      int(on_host), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                      stream_ptr(stream)))
     return host.value if on_host else None
 
 

@@ -169,6 +169,7 @@ int vy_for(int dtype) { return dtype == GSCL_F64 ? VyOf<double>::value : VyOf<fl
 gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   SweepParams &P = pl->P;
   memset(&P, 0, sizeof P);
+  P.within = -1.0;  // MAXABS reports the maximum (gscl_do_reduce_within sets a tolerance)
   const Grid &g0 = b.in[0];
   const int n_in = (int)b.in.size(), n_out = (int)b.out.size();
   const int elem = g0.elem;
@@ -435,16 +436,15 @@ gscl_status gscl_tune_sweeps(const gscl_stencil *op, const gscl_grid *in, int32_
   return s;
 }
 
-gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
-                           const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
-                           int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream) {
-  int red;
-  switch (reduce_op) {
-    case GSCL_SUM: red = RED_SUM; break;
-    case GSCL_MAXABS: red = RED_MAXABS; break;
-    case GSCL_L2: red = RED_L2; break;
-    default: return fail(GSCL_ERR_INVALID, "unknown reduce op %d", reduce_op);
-  }
+}  // extern "C"
+
+namespace gscl {
+namespace {
+
+// do_reduce with `red`; within >= 0 turns MAXABS into the all-within test.
+gscl_status reduce_call(int red, double within, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                        const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
+                        int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream) {
   if (!result) return fail(GSCL_ERR_INVALID, "result is NULL");
   if (!workspace) return fail(GSCL_ERR_INVALID, "workspace is NULL");
   if (((uintptr_t)workspace) % 16) return fail(GSCL_ERR_INVALID, "workspace must be 16-byte aligned");
@@ -456,13 +456,22 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
   cudaStream_t st = (cudaStream_t)stream;
   double *dev_result = result_on_host ? reinterpret_cast<double *>((char *)workspace + 8) : result;
   if (b.empty) {
-    cudaError_t e = cudaMemsetAsync(dev_result, 0, sizeof(double), st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    // an empty range: 0 for the sums and the maximum, "all within" for the test
+    if (within >= 0.0) {
+      static const double one = 1.0;
+      cudaError_t e = cudaMemcpyAsync(dev_result, &one, sizeof(double), cudaMemcpyHostToDevice, st);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // `one` is pageable host memory
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
+    } else {
+      cudaError_t e = cudaMemsetAsync(dev_result, 0, sizeof(double), st);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
+    }
   } else {
     Plan pl;
     if (gscl_status s = make_plan(b, true, &pl, TileCfg{})) return s;
     pl.P.workspace = (unsigned char *)workspace;
     pl.P.result = dev_result;
+    pl.P.within = within;
     if (gscl_status s = launch(pl, b.in[0].dtype, red, st, nullptr)) return s;
   }
   if (result_on_host) {
@@ -472,6 +481,33 @@ gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
   }
   return GSCL_OK;
+}
+
+}  // namespace
+}  // namespace gscl
+
+extern "C" {
+
+gscl_status gscl_do_reduce(int32_t reduce_op, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                           const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
+                           int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream) {
+  int red;
+  switch (reduce_op) {
+    case GSCL_SUM: red = RED_SUM; break;
+    case GSCL_MAXABS: red = RED_MAXABS; break;
+    case GSCL_L2: red = RED_L2; break;
+    default: return fail(GSCL_ERR_INVALID, "unknown reduce op %d", reduce_op);
+  }
+  return reduce_call(red, -1.0, op, in, n_in, out, n_out, range, result, result_on_host, workspace,
+                     workspace_bytes, stream);
+}
+
+gscl_status gscl_do_reduce_within(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                                  int32_t n_out, const gscl_range *range, double eps, double *result,
+                                  int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream) {
+  if (!(eps >= 0.0)) return fail(GSCL_ERR_INVALID, "eps must be >= 0");
+  return reduce_call(RED_MAXABS, eps, op, in, n_in, out, n_out, range, result, result_on_host, workspace,
+                     workspace_bytes, stream);
 }
 
 }  // extern "C"

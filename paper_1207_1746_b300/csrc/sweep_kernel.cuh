@@ -96,6 +96,7 @@ struct SweepParams {
   double *seg_partials;      // batched reduce: one (s, c) pair per segment
   unsigned char *workspace;  // single reduce: ticket at +0, partials at +256
   double *result;            // single reduce: where the last CTA writes the value
+  double within;             // >= 0: MAXABS reports 1 if max |value| <= within, else 0
   int *err;                  // device error word
 };
 
@@ -848,7 +849,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   block_fold<RED>(s, c, s_red, NW);
   if (tid == 0) {
     double r;
-    if (RED == RED_MAXABS) r = s;
+    if (RED == RED_MAXABS) r = P.within >= 0.0 ? (s <= P.within ? 1.0 : 0.0) : s;  // NaN fails the test
     else if (RED == RED_L2) r = sqrt(s - c);
     else r = s - c;
     *P.result = r;

@@ -391,3 +391,33 @@ def test_heat3d_error_after_200_sweeps_reported(dtype):
           f"max relative residual error = {rerr:.3e}")
     bound = 1e-12 if dtype == "f64" else 1e-4
     assert err <= bound and rerr <= bound, (err, rerr)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_reduce_within_matches_oracle(dtype):
+    """gscl_do_reduce_within (logical_and of |value| <= eps) against the
+    oracle: eps below and above the largest difference (and exactly at it in
+    FP64, where both sides form a - b in the same precision), a planted NaN,
+    an empty range, and the device-resident result."""
+    n, h = (70, 33, 21), (1, 1, 1)
+    a = I.random_interior(81, n, h, -1.0, 1.0)
+    b = a + I.random_interior(82, n, h, -1e-3, 1e-3)
+    A, Bg = as_storage(a, dtype), as_storage(b, dtype)
+    oa, ob = O.Grid(A, h), O.Grid(Bg, h)
+    dmax = O.do_reduce(O.MAXABS, D.difference_terms(), [oa, ob])
+    ga, gb = B.Grid(n, h, dtype).upload(a), B.Grid(n, h, dtype).upload(b)
+    op = S.difference()
+    eps_list = [0.5 * dmax, 2.0 * dmax] + ([dmax] if dtype == "f64" else [])
+    for eps in eps_list:
+        want = O.do_reduce_within(eps, D.difference_terms(), [oa, ob])
+        assert B.do_reduce_within(eps, op, [ga, gb]) == want, eps
+    res = torch.full((1,), -7.0, dtype=torch.float64, device="cuda")
+    B.do_reduce_within(2.0 * dmax, op, [ga, gb], result=res)
+    assert float(res.cpu()[0]) == 1.0
+    assert B.do_reduce_within(0.0, op, [ga, gb], rng=((3, 3, 3), (3, 9, 9))) == 1.0
+    a2 = a.copy()
+    a2[5, 6, 7] = np.nan
+    gn = B.Grid(n, h, dtype).upload(a2)
+    assert B.do_reduce_within(1e9, op, [gn, gb]) == 0.0
+    with pytest.raises(B.GsclError):
+        B.do_reduce_within(-1.0, op, [ga, gb])

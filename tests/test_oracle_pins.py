@@ -407,3 +407,27 @@ def test_poisson_jacobi_solution_matches_sparse_direct_solve():
     assert np.max(np.abs(u.interior().ravel() - exact)) <= 1e-10 * np.max(np.abs(exact))
     r, fn = D.poisson_residual(u, f)
     assert r <= 1e-12 * fn
+
+
+def test_within_reduction_is_the_logical_and_of_the_pointwise_tests():
+    """Section 5.2's convergence test do_reduce(fuse(diff, conv), logical_and),
+    checked by brute force on small grids: numpy's all(|a - b| <= eps) decides
+    the same for eps below, at and above the largest difference, for a planted
+    NaN and for an empty range."""
+    rng = np.random.default_rng(7)
+    n, h = (9, 7, 5), (1, 1, 1)
+    a = np.zeros((n[2] + 2, n[1] + 2, n[0] + 2))
+    b = np.zeros_like(a)
+    a[1:-1, 1:-1, 1:-1] = rng.uniform(-1, 1, size=(n[2], n[1], n[0]))
+    b[1:-1, 1:-1, 1:-1] = a[1:-1, 1:-1, 1:-1] + rng.uniform(-1e-3, 1e-3, size=(n[2], n[1], n[0]))
+    d = np.abs(a[1:-1, 1:-1, 1:-1] - b[1:-1, 1:-1, 1:-1])
+    terms = D.difference_terms()
+    for eps in (0.0, 0.5 * d.max(), d.max(), 2.0 * d.max()):
+        got = O.do_reduce_within(eps, terms, [O.Grid(a, h), O.Grid(b, h)])
+        assert got == (1.0 if np.all(d <= eps) else 0.0)
+    a2 = a.copy()
+    a2[3, 4, 5] = np.nan
+    assert O.do_reduce_within(1.0, terms, [O.Grid(a2, h), O.Grid(b, h)]) == 0.0
+    assert O.do_reduce_within(0.0, terms, [O.Grid(a, h), O.Grid(b, h)], lo=(2, 2, 2), hi=(2, 5, 5)) == 1.0
+    with pytest.raises(ValueError):
+        O.do_reduce_within(-1.0, terms, [O.Grid(a, h), O.Grid(b, h)])
