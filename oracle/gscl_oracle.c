@@ -180,6 +180,39 @@ int orc_do_all(const orc_extent *e, int n_in, const orc_grid *in, int n_out, con
   return ORC_OK;
 }
 
+/* Ordered iteration spaces (Section 3): do_i/j/k_inc visit (i-1,j,k),
+ * (i,j-1,k), (i,j,k-1) respectively before (i,j,k); the _dec forms visit the
+ * +1 neighbour first.  axis: 0 = i, 1 = j, 2 = k; inc: 1 for _inc, 0 for
+ * _dec.  The ordered axis is the outer loop, walked in that direction, so
+ * every element comes after its predecessor along it.  Reads see the grids'
+ * current contents: an output grid that is also bound as an input is seen
+ * already updated at the elements visited before.  At each element every
+ * output is computed before any is stored. */
+int orc_do_ordered(int axis, int inc, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                   const orc_out_grid *out, int n_terms, const orc_term *terms, const int64_t lo[3],
+                   const int64_t hi[3]) {
+  if (axis < 0 || axis > 2 || n_out < 1 || n_out > 8) return ORC_BAD_ARG;
+  int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
+  if (rc) return rc;
+  const int a1 = axis == 0 ? 1 : 0, a2 = axis == 2 ? 1 : 2; /* the two other axes */
+  double r[8];
+  for (int64_t s = 0; s < hi[axis] - lo[axis]; ++s) {
+    const int64_t c = inc ? lo[axis] + s : hi[axis] - 1 - s;
+    for (int64_t u = lo[a2]; u < hi[a2]; ++u)
+      for (int64_t w = lo[a1]; w < hi[a1]; ++w) {
+        int64_t p[3];
+        p[axis] = c;
+        p[a1] = w;
+        p[a2] = u;
+        double v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, 0, p[0], p[1], p[2]);
+        for (int m = 0; m < n_out; ++m) r[m] = orc_term_sum(e, in, n_terms, terms, m, v, 0, p[0], p[1], p[2]);
+        for (int m = 0; m < n_out; ++m)
+          out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, p[0], p[1], p[2])] = r[m];
+      }
+  }
+  return ORC_OK;
+}
+
 /* Neumaier's improvement of Kahan summation: the running compensation c
  * collects the rounding error of every addition, taken from whichever
  * operand is larger in magnitude. */

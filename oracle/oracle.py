@@ -91,6 +91,8 @@ def _get_lib():
         lib.orc_do_reduce.restype = ctypes.c_int
         lib.orc_do_reduce_within.argtypes = [ctypes.c_double] + lib.orc_do_reduce.argtypes[1:]
         lib.orc_do_reduce_within.restype = ctypes.c_int
+        lib.orc_do_ordered.argtypes = [ctypes.c_int, ctypes.c_int] + lib.orc_do_reduce.argtypes[1:-1]
+        lib.orc_do_ordered.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -122,7 +124,7 @@ def zeros(n, halo) -> Grid:
     return Grid(np.zeros((nz + 2 * hz, ny + 2 * hy, nx + 2 * hx), dtype=np.float64), tuple(halo))
 
 
-def _marshal(terms, ins, outs, lo, hi):
+def _marshal(terms, ins, outs, lo, hi, allow_alias=False):
     if not ins:
         raise ValueError("at least one input grid")
     n = ins[0].n
@@ -133,7 +135,7 @@ def _marshal(terms, ins, outs, lo, hi):
             raise ValueError("oracle grids are C-contiguous float64")
     in_ids = {id(g.a) for g in ins}
     for g in outs:
-        if id(g.a) in in_ids:
+        if id(g.a) in in_ids and not allow_alias:
             raise ValueError("the oracle requires output arrays distinct from inputs")
     ext = _Extent(*n)
     gin = (_Grid * len(ins))(*[_Grid(g.a.ctypes.data, *g.halo) for g in ins])
@@ -166,6 +168,20 @@ def do_all(terms, ins, outs, lo=None, hi=None, abs_mode=False, want_value=False)
     if rc != 0:
         raise ValueError(f"oracle do_all rejected the call (code {rc})")
     return val
+
+
+I_INC, I_DEC, J_INC, J_DEC, K_INC, K_DEC = range(6)
+
+
+def do_ordered(order, terms, ins, outs, lo=None, hi=None):
+    """Ordered iteration space (Section 3): ``order`` is one of I_INC .. K_DEC.
+    Along the ordered axis each element is visited after its predecessor; an
+    output passed also as an input (the same Grid) is read as updated so far."""
+    ext, gin, gout, tt, clo, chi = _marshal(terms, ins, outs, lo, hi, allow_alias=True)
+    rc = _get_lib().orc_do_ordered(order // 2, 1 if order % 2 == 0 else 0, ctypes.byref(ext), len(ins), gin,
+                                   len(outs), gout, len(terms), tt, clo, chi)
+    if rc != 0:
+        raise ValueError(f"oracle do_ordered rejected the call (code {rc})")
 
 
 def do_reduce_within(eps, terms, ins, outs=(), lo=None, hi=None) -> float:

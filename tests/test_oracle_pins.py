@@ -431,3 +431,57 @@ def test_within_reduction_is_the_logical_and_of_the_pointwise_tests():
     assert O.do_reduce_within(0.0, terms, [O.Grid(a, h), O.Grid(b, h)], lo=(2, 2, 2), hi=(2, 5, 5)) == 1.0
     with pytest.raises(ValueError):
         O.do_reduce_within(-1.0, terms, [O.Grid(a, h), O.Grid(b, h)])
+
+
+# ---------------------------------------------------------------- ordered iteration spaces
+def _column_grids(n, h, seed):
+    rng = np.random.default_rng(seed)
+    shape = (n[2] + 2 * h[2], n[1] + 2 * h[1], n[0] + 2 * h[0])
+    f = np.zeros(shape)
+    f[h[2]:h[2] + n[2], h[1]:h[1] + n[1], h[0]:h[0] + n[0]] = rng.integers(-50, 50, size=(n[2], n[1], n[0]))
+    return f
+
+
+@pytest.mark.parametrize("order,axis,rev", [(O.K_INC, 0, False), (O.K_DEC, 0, True),
+                                            (O.J_INC, 1, False), (O.J_DEC, 1, True),
+                                            (O.I_INC, 2, False), (O.I_DEC, 2, True)])
+def test_ordered_recurrence_is_a_running_sum(order, axis, rev):
+    """do_*_inc / _dec (Section 3) with out = out(previous) + f, the output
+    bound also as the input it reads one step back: a running sum along the
+    ordered axis (numpy cumsum, reversed for _dec), starting from the halo."""
+    n, h = (6, 5, 7), (1, 1, 1)
+    f = _column_grids(n, h, 11)
+    x = np.zeros_like(f)
+    step = {O.I_INC: (-1, 0, 0), O.I_DEC: (1, 0, 0), O.J_INC: (0, -1, 0), O.J_DEC: (0, 1, 0),
+            O.K_INC: (0, 0, -1), O.K_DEC: (0, 0, 1)}[order]
+    terms = [(step[0], step[1], step[2], 0, 255, 0, 1.0), (0, 0, 0, 1, 255, 0, 1.0)]
+    X = O.Grid(x, h)
+    O.do_ordered(order, terms, [X, O.Grid(f, h)], [X])
+    core = f[1:-1, 1:-1, 1:-1]
+    want = np.flip(np.cumsum(np.flip(core, axis), axis=axis), axis) if rev else np.cumsum(core, axis=axis)
+    assert np.array_equal(x[1:-1, 1:-1, 1:-1], want)
+    assert np.all(x[0] == 0) and np.all(x[-1] == 0)  # halos untouched
+
+
+def test_ordered_bidiagonal_forward_substitution():
+    """do_k_inc solving L x = g per (i, j) column, L unit lower bidiagonal
+    with sub-diagonal m(k): x(k) = g(k) - m(k) x(k-1), the coefficient grid
+    m multiplying the previous element.  Checked against a dense triangular
+    solve of every column (scipy)."""
+    import scipy.linalg as sla
+    n, h = (4, 3, 9), (0, 0, 1)
+    rng = np.random.default_rng(5)
+    shape = (n[2] + 2, n[1], n[0])
+    g = np.zeros(shape)
+    m = np.zeros(shape)
+    g[1:-1] = rng.uniform(-1, 1, size=(n[2], n[1], n[0]))
+    m[1:-1] = rng.uniform(-0.9, 0.9, size=(n[2], n[1], n[0]))
+    x = np.zeros(shape)
+    X = O.Grid(x, h)
+    terms = [(0, 0, 0, 1, 255, 0, 1.0), (0, 0, -1, 0, 2, 0, -1.0)]
+    O.do_ordered(O.K_INC, terms, [X, O.Grid(g, h), O.Grid(m, h)], [X])
+    for j in range(n[1]):
+        for i in range(n[0]):
+            L = np.eye(n[2]) + np.diag(m[2:-1, j, i], -1)
+            want = sla.solve_triangular(L, g[1:-1, j, i], lower=True)
+            assert np.allclose(x[1:-1, j, i], want, rtol=1e-13, atol=1e-15)
