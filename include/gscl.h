@@ -248,6 +248,44 @@ gscl_status gscl_convert(gscl_grid dst, gscl_grid src, double alpha, int32_t acc
 gscl_status gscl_tune_sweeps(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                              int32_t n_out, int32_t trial_sweeps, void *stream, int32_t *best_factor);
 
+/* Orders of the ordered iteration spaces (Section 3). */
+typedef enum {
+  GSCL_I_INC = 0, /* (i-1, j, k) is visited before (i, j, k) */
+  GSCL_I_DEC = 1, /* (i+1, j, k) before (i, j, k) */
+  GSCL_J_INC = 2, /* (i, j-1, k) before (i, j, k) */
+  GSCL_J_DEC = 3, /* (i, j+1, k) before (i, j, k) */
+  GSCL_K_INC = 4, /* (i, j, k-1) before (i, j, k) */
+  GSCL_K_DEC = 5  /* (i, j, k+1) before (i, j, k) */
+} gscl_order;
+
+/*
+ * Ordered iteration spaces (Section 3: do_j_inc, do_j_dec, do_k_inc,
+ * do_k_dec): applies the operator at every core element of the range so that
+ * along the ordered axis each element comes after its predecessor (other
+ * axes in any order); outputs are written as by gscl_do_all.
+ *
+ *  - An output grid may also be bound as an input (the same handle, or a
+ *    handle of the same storage and layout).  Terms read it at offset 0 (the
+ *    value before this element is written) or at the element visited just
+ *    before along the ordered axis ((0,0,-1) for GSCL_K_INC, (0,1,0) for
+ *    GSCL_J_DEC, ...), which holds the value this call wrote there, or at the
+ *    range's first element the grid's current content (halo or untouched
+ *    interior).  Any other read of it is GSCL_ERR_ALIAS.  This is how a
+ *    recurrence along a column is written: running sums, bidiagonal forward
+ *    or backward substitution (x(k) = g(k) - m(k) x(k-1) with m a coefficient
+ *    grid), upwind integration.
+ *  - At each element every output is computed before any is stored; the
+ *    stored (rounded) value is what the next element reads.
+ *  - Terms may also write the returned value (out = GSCL_VALUE) and read it
+ *    (in = GSCL_VALUE), as in do_all; it is not reduced.
+ *  - GSCL_I_INC / GSCL_I_DEC return GSCL_ERR_UNSUPPORTED: one thread walks one
+ *    column, and columns along x would place a warp's accesses a row apart.
+ *  - Errors, range and dtype rules as gscl_do_all (n_out >= 1).  Asynchronous
+ *    on `stream`.
+ */
+gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                            const gscl_grid *out, int32_t n_out, const gscl_range *range, void *stream);
+
 /* Bytes of device workspace one gscl_do_reduce call needs (a constant). */
 int64_t gscl_reduce_workspace_bytes(void);
 

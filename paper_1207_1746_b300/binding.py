@@ -99,6 +99,7 @@ def lib():
         "gscl_convert": [u64, u64, ctypes.c_double, i32, P(RangeC), vp],
         "gscl_tune_sweeps": [P(StencilC), P(u64), i32, P(u64), i32, i32, vp, P(i32)],
         "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
+        "gscl_do_ordered": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
         "gscl_do_reduce_within": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), ctypes.c_double,
                                   P(ctypes.c_double), i32, vp, i64, vp],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
@@ -309,6 +310,18 @@ def do_reduce(reduce_op, op, ins, outs=(), rng=None, result=None, stream=None):
                                len(ins), _handles(outs), len(outs), _range(rng), rptr, int(on_host),
                                ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream_ptr(stream)))
     return host.value if on_host else None
+
+
+I_INC, I_DEC, J_INC, J_DEC, K_INC, K_DEC = range(6)
+
+
+def do_ordered(order, op, ins, outs, rng=None, stream=None):
+    """gscl_do_ordered: ordered iteration space (Section 3), ``order`` one of
+    J_INC, J_DEC, K_INC, K_DEC.  An output passed also as an input is read at
+    the element visited just before (a recurrence along the column)."""
+    st = as_stencil(op)
+    check(lib().gscl_do_ordered(int(order), ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
+                                _range(rng), stream_ptr(stream)))
 
 
 def do_reduce_within(eps, op, ins, outs=(), rng=None, result=None, stream=None):

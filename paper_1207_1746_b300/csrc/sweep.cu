@@ -17,7 +17,7 @@ bool overlaps(const Grid &a, const Grid &b) { return a.buf < b.buf + b.bytes && 
 
 // Validates handles, shapes, dtypes, the range, every term and aliasing.
 gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
-                 int32_t n_out, const gscl_range *range, Bound *b) {
+                 int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis, int ordered_step) {
   if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
   if (n_out < 0 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut_);
   if (!in || (n_out > 0 && !out)) return fail(GSCL_ERR_INVALID, "grid arrays are required");
@@ -93,12 +93,20 @@ gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, i
   }
   if (need_value && !has_value) return fail(GSCL_ERR_INVALID, "do_reduce needs a term with out == GSCL_VALUE");
   // an output may also be an input only if every read of it is at offset 0
+  // (ordered iteration spaces: or at the element visited just before)
   for (int m = 0; m < n_out; ++m)
     for (int a = 0; a < n_in; ++a) {
       if (!overlaps(b->out[m], b->in[a])) continue;
+      const Grid &go = b->out[m], &gi = b->in[a];
+      if (ordered_axis >= 0 && (go.buf != gi.buf || go.off != gi.off || go.pitch != gi.pitch || go.plane != gi.plane))
+        return fail(GSCL_ERR_ALIAS, "output %d overlaps input %d without being the same grid", m, a);
       for (int t = 0; t < op->n_terms; ++t) {
         const gscl_term &tm = op->terms[t];
-        if (tm.in == a && (tm.dx || tm.dy || tm.dz))
+        if (tm.in != a || !(tm.dx || tm.dy || tm.dz)) continue;
+        const int d[3] = {tm.dx, tm.dy, tm.dz};
+        const bool previous = ordered_axis >= 0 && d[ordered_axis] == ordered_step &&
+                              d[(ordered_axis + 1) % 3] == 0 && d[(ordered_axis + 2) % 3] == 0;
+        if (!previous)
           return fail(GSCL_ERR_ALIAS, "output %d is input %d, read at a non-zero offset by term %d", m, a, t);
       }
     }

@@ -1,0 +1,109 @@
+"""GPU parity of the ordered iteration spaces (Section 3: do_j_inc/dec,
+do_k_inc/dec) against the oracle: integer running sums are bit-exact in
+FP64 and FP32 (every partial sum is an integer below 2^24), random
+bidiagonal substitutions match within tolerance, and the alias rules are
+enforced."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import as_storage
+from oracle import oracle as O
+from paper_1207_1746_b300 import binding as B
+from paper_1207_1746_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+NONE, VALUE = B.NONE, B.VALUE
+STEP = {B.J_INC: (0, -1, 0), B.J_DEC: (0, 1, 0), B.K_INC: (0, 0, -1), B.K_DEC: (0, 0, 1)}
+
+
+def integer_grid(seed, n, h, lo=-50, hi=50):
+    a = np.zeros(I.padded_shape(n, h))
+    rng = np.random.default_rng(seed)
+    I.interior_view(a, n, h)[...] = rng.integers(lo, hi, size=(n[2], n[1], n[0]))
+    return a
+
+
+def run_both(order, terms, arrays, h, n, dtype, n_out=1, alias=(0,), rng=None):
+    """arrays[0 .. n_out-1] are the outputs (also bound as inputs 0 .. n_out-1);
+    the rest are read-only inputs.  Returns (gpu outputs, oracle outputs)."""
+    gg = [B.Grid(n, h, dtype).upload(a) for a in arrays]
+    B.do_ordered(order, terms, gg, gg[:n_out], rng=rng)
+    got = [g.download().double().numpy() for g in gg[:n_out]]
+    og = [O.Grid(as_storage(a, dtype), h) for a in arrays]
+    lo, hi = (rng if rng is not None else (None, None))
+    O.do_ordered(order, terms, og, og[:n_out], lo=lo, hi=hi)
+    return got, [g.a for g in og[:n_out]]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC, B.J_DEC])
+def test_running_sum_bitexact(order, dtype):
+    n, h = (131, 37, 29), (1, 1, 1)
+    x0 = integer_grid(1, n, h, -3, 3)       # the halo seeds the recurrence (interior overwritten)
+    f = integer_grid(2, n, h)
+    d = STEP[order]
+    terms = [(d[0], d[1], d[2], 0, NONE, 0, 1.0), (0, 0, 0, 1, NONE, 0, 1.0)]
+    got, want = run_both(order, terms, [x0, f], h, n, dtype)
+    assert np.array_equal(got[0], want[0])
+
+
+@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC])
+def test_subrange_reads_untouched_interior_first(order):
+    """A range not starting at the boundary: the first element reads the
+    grid's existing value just outside the range."""
+    n, h = (70, 20, 24), (1, 1, 1)
+    x0 = integer_grid(3, n, h)
+    f = integer_grid(4, n, h)
+    d = STEP[order]
+    terms = [(d[0], d[1], d[2], 0, NONE, 0, 1.0), (0, 0, 0, 1, NONE, 0, 2.0)]
+    got, want = run_both(order, terms, [x0, f], h, n, "f64", rng=((3, 2, 5), (61, 17, 19)))
+    assert np.array_equal(got[0], want[0])
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 1e-5)])
+def test_bidiagonal_substitution(dtype, tol):
+    """Two recurrences in one call: x(k) = g(k) - m(k) x(k-1) (coefficient
+    grid m) and y(k) = g(k) / 2 + y(k-1) / 4; random data, tolerance relative
+    to the largest magnitude (FP32 storage rounds every stored element)."""
+    n, h = (96, 40, 33), (1, 1, 1)
+    g = I.random_interior(5, n, h, -1.0, 1.0)
+    m = I.random_interior(6, n, h, -0.9, 0.9)
+    x, y = np.zeros_like(g), np.zeros_like(g)
+    terms = [(0, 0, 0, 2, NONE, 0, 1.0), (0, 0, -1, 0, 3, 0, -1.0),
+             (0, 0, 0, 2, NONE, 1, 0.5), (0, 0, -1, 1, NONE, 1, 0.25)]
+    got, want = run_both(B.K_INC, terms, [x, y, g, m], h, n, dtype, n_out=2)
+    for a, b in zip(got, want):
+        assert np.max(np.abs(a - b)) <= tol * np.max(np.abs(b))
+
+
+def test_value_terms_feed_outputs():
+    """The returned value computed per element and read by the output terms:
+    x(k) = v, v = x(k-1) + f(k) (a running sum through the value)."""
+    n, h = (64, 9, 17), (1, 1, 1)
+    f = integer_grid(7, n, h)
+    x = np.zeros_like(f)
+    terms = [(0, 0, -1, 0, NONE, VALUE, 1.0), (0, 0, 0, 1, NONE, VALUE, 1.0), (0, 0, 0, VALUE, NONE, 0, 1.0)]
+    gx, gf = B.Grid(n, h).upload(x), B.Grid(n, h).upload(f)
+    B.do_ordered(B.K_INC, terms, [gx, gf], [gx])
+    want = np.cumsum(I.interior_view(f, n, h), axis=0)
+    assert np.array_equal(I.interior_view(gx.download().numpy(), n, h), want)
+
+
+def test_alias_rules_and_unsupported_axis():
+    n, h = (32, 8, 8), (1, 1, 1)
+    gx = B.Grid(n, h).upload(np.zeros(I.padded_shape(n, h)))
+    gf = B.Grid(n, h).upload(integer_grid(8, n, h))
+    with pytest.raises(B.GsclError) as e:   # K_DEC's predecessor is (0, 0, +1), not (0, 0, -1)
+        B.do_ordered(B.K_DEC, [(0, 0, -1, 0, NONE, 0, 1.0), (0, 0, 0, 1, NONE, 0, 1.0)], [gx, gf], [gx])
+    assert e.value.status == 3  # GSCL_ERR_ALIAS
+    with pytest.raises(B.GsclError) as e:   # a neighbouring column is not ordered
+        B.do_ordered(B.K_INC, [(1, 0, -1, 0, NONE, 0, 1.0)], [gx, gf], [gx])
+    assert e.value.status == 3
+    with pytest.raises(B.GsclError) as e:
+        B.do_ordered(B.I_INC, [(-1, 0, 0, 0, NONE, 0, 1.0)], [gx, gf], [gx])
+    assert e.value.status == 10  # GSCL_ERR_UNSUPPORTED
+    # reading the output at offset 0 (its old value) is allowed
+    B.do_ordered(B.K_INC, [(0, 0, 0, 0, NONE, 0, 2.0), (0, 0, 0, 1, NONE, 0, 1.0)], [gx, gf], [gx])
+    B.sync()
