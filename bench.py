@@ -458,6 +458,44 @@ def run_climate(dtype, steps, warmup, sweeps=50):
             "specialization": B.specialization(op, len(cur + fixed), len(nxt))}
 
 
+# ------------------------------------------------------------------ ordered workload
+def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10):
+    """Ordered iteration space (do_k_inc): bidiagonal forward substitution
+    x(k) = g(k) - m(k) x(k-1) down every (i, j) column of a 256 x 256 x 80
+    grid (g uniform [-1, 1), m uniform [-0.9, 0.9], seeds 606 / 607), `reps`
+    solves per step.  Algorithmic bytes per point: g and m read, x written."""
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+
+    h = (1, 1, 1)
+    g = B.Grid(n, h, dtype).upload(I.random_interior(606, n, h, -1.0, 1.0))
+    m = B.Grid(n, h, dtype).upload(I.random_interior(607, n, h, -0.9, 0.9))
+    x = B.Grid(n, h, dtype).upload(I.random_interior(608, n, h, 0.0, 0.0))
+    terms = [(0, 0, 0, 1, B.NONE, 0, 1.0), (0, 0, -1, 0, 2, 0, -1.0)]
+    op = B.Stencil(terms)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        for _ in range(reps):
+            B.do_ordered(B.K_INC, op, [x, g, m], [x])
+
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    B.sync()
+    ms = e0.elapsed_time(e1) / steps
+    pts = n[0] * n[1] * n[2]
+    return {"points": pts, "ms_per_step": ms, "solve_ms": ms / reps, "reps": reps}
+
+
 # ------------------------------------------------------------------ serving workload
 def run_serving(sample=8, window_s=10.0, rate=200.0, time_cap=30.0, check_every=200):
     """Poisson Jacobi solves (side uniform on 64..256, f uniform in [-1, 1),
@@ -605,10 +643,12 @@ def main():
     ap.add_argument("--profile", action="store_true",
                     help="one short step for profilers: no warm-up, tuner, comparison runs, e2e, CPU leg or "
                          "FMA microbenchmark (the printed numbers are not benchmark values)")
-    ap.add_argument("--workload", default="heat3d", choices=["heat3d", "batched", "serving", "laplace2d", "climate"],
+    ap.add_argument("--workload", default="heat3d",
+                    choices=["heat3d", "batched", "serving", "laplace2d", "climate", "ordered"],
                     help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances; "
                          "serving: Poisson solve requests; laplace2d: 256^2 FP64 Jacobi, 100 sweeps; "
-                         "climate: 8 -> 3 grid operator on 256 x 256 x 80, FP64 and FP32, 50 sweeps")
+                         "climate: 8 -> 3 grid operator on 256 x 256 x 80, FP64 and FP32, 50 sweeps; "
+                         "ordered: do_k_inc bidiagonal solve down 256 x 256 columns of 80")
     args = ap.parse_args()
     if args.profile:
         global PROFILE
@@ -725,6 +765,30 @@ def main():
                                                   "traffic": profile_traffic("climate_f32"),
                                                   "peak_source": "measured"}}},
                 "gpu_launches": 2 * args.steps * 50}
+        if dist.rank == 0:
+            print(json.dumps(line))
+        return
+    if args.workload == "ordered":
+        peak_hbm = peaks.get("hbm_gbs", 6400.0)
+        out = {}
+        for dt in ("f64", "f32"):
+            r = run_ordered(dt, args.steps, args.warmup)
+            t = dist.max(r["ms_per_step"])
+            bpp = {"f64": 24, "f32": 12}[dt]
+            gbs = bpp * r["points"] / (r["solve_ms"] * 1e-3) / 1e9
+            out[dt] = {"value": round(dist.world * r["reps"] * r["points"] / (t * 1e-3) / 1e9, 3),
+                       "ms_per_step": round(t, 3), "solve_ms": round(r["solve_ms"], 4),
+                       "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm, "unit": "GB/s",
+                                    "frac": round(gbs / peak_hbm, 4), "traffic": None, "peak_source": "measured"}}
+        line = {"metric": "GPoint-updates/s", "value": out["f64"]["value"], "unit": "GPoint-updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": out["f64"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "ordered: do_k_inc bidiagonal forward substitution x(k) = g(k) - m(k) x(k-1) "
+                                       "down every column of 256x256x80, 10 solves per step",
+                           "l2": "working set 3 grids > L2 in FP64"},
+                "roofline": out["f64"]["roofline"], "kernel_ms": out["f64"]["solve_ms"],
+                "variants": {"f32": {"dtype": "f32", **out["f32"]}}, "gpu_launches": args.steps * 10}
         if dist.rank == 0:
             print(json.dumps(line))
         return
