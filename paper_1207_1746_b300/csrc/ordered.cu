@@ -9,8 +9,15 @@
 // that a warp's loads and stores are 32 consecutive elements; each thread
 // walks its column in order and keeps the element just written in registers
 // (the recurrence never goes through memory).  The term list is interpreted
-// at run time.  The ordered axis must be y or z: columns along x would put a
-// warp's accesses a whole row apart.
+// at run time.  Operators with at most kLoads distinct element loads per
+// step take a pipelined path: every load of the element kAhead steps ahead is
+// issued together into a register ring, so a column waits for memory once
+// per kAhead steps instead of once per term and step.  The ring lives in
+// shared memory, one private column of slots per thread, filled by cp.async
+// (one commit group per step; a thread waits only for its own copies), so
+// slots can be indexed at run time.  FP32 / FP64 storage (cp.async moves 4 or
+// 8 bytes); BF16 takes the simple path.  The ordered axis must
+// be y or z: columns along x would put a warp's accesses a whole row apart.
 #include "sweep_host.h"
 #include "sweep_kernel.cuh"
 
@@ -18,6 +25,16 @@ namespace gscl {
 namespace {
 
 constexpr int kOrdThreads = 128;
+constexpr int kLoads = 8;   // distinct element loads per step on the pipelined path
+constexpr int kAheadFew = 16;  // steps of look-ahead for operators with at most kFewLoads loads
+constexpr int kAheadMany = 4;  // ... and for the others (up to kLoads)
+constexpr int kFewLoads = 3;
+
+struct OrdLoad {
+  int16_t grid, nc, dx, dy, dz, pad;
+  int64_t start;  // element offset of the read at the column's first step, without the column's base
+  int64_t step;   // element offset from one step to the next (signed)
+};
 
 struct OrdTerm {
   int16_t in;    // input grid, or -1: the operator's value
@@ -27,6 +44,8 @@ struct OrdTerm {
   int16_t nc;    // the input is not written by this call (read-only cache path)
   int16_t cnc;   // the same for the coefficient grid
   int16_t dx, dy, dz;
+  int16_t xslot;  // pipelined path: ring slot of the input value (-1: value or previous element)
+  int16_t cslot;  // ring slot of the coefficient (-1: none)
   float wf;
   double wd;
 };
@@ -40,6 +59,9 @@ struct OrdParams {
   int32_t n_terms, n_out;
   int32_t need_prev[kMaxOut_];  // some term reads this output's previous element
   int64_t lo[3], hi[3];
+  OrdLoad loads[kLoads];        // pipelined path: the distinct loads (n_loads <= kLoads)
+  int32_t n_loads;              // > kLoads: the simple path
+  int64_t out_start[kMaxOut_], out_step[kMaxOut_];  // the outputs' element at the first step, step offset
 };
 
 __device__ __forceinline__ double ord_weight(const OrdTerm &t, double) { return t.wd; }
@@ -51,8 +73,31 @@ __device__ __forceinline__ typename Arith<T>::A ord_load(const char *base, int64
   return to_arith(nc ? __ldg(p) : *p);
 }
 
-// AXIS: 1 (y) or 2 (z); INC: increasing along it.
-template <typename T, int AXIS, bool INC>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem, int bytes) {
+  const uint32_t sa = (uint32_t)__cvta_generic_to_shared(smem);
+  if (bytes == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gmem) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Copies the pipelined path's loads of step `step` into ring slot `slot` of
+// this thread (element [slot][l][threadIdx.x] of the ring); src[l] points at
+// load l's element of the column's first step.
+template <typename T>
+__device__ __forceinline__ void issue_loads(const OrdParams &P, const T *const (&src)[kLoads], int64_t step, T *ring,
+                                            int slot) {
+  T *dst = ring + (int64_t)slot * P.n_loads * kOrdThreads + threadIdx.x;
+#pragma unroll
+  for (int l = 0; l < kLoads; ++l)
+    if (l < P.n_loads) cp_async(dst + l * kOrdThreads, src[l] + step * P.loads[l].step, (int)sizeof(T));
+}
+
+// AXIS: 1 (y) or 2 (z); INC: increasing along it; AHEAD: look-ahead of the
+// pipelined path (0: the simple path), whose ring is the dynamic shared
+// memory (AHEAD x n_loads x kOrdThreads elements).
+template <typename T, int AXIS, bool INC, int AHEAD>
 __global__ void __launch_bounds__(kOrdThreads) ordered_kernel(const __grid_constant__ OrdParams P) {
   using A = typename Arith<T>::A;
   constexpr int OTHER = AXIS == 2 ? 1 : 2;
@@ -75,59 +120,139 @@ __global__ void __launch_bounds__(kOrdThreads) ordered_kernel(const __grid_const
       prev[m] = to_arith(reinterpret_cast<const T *>(P.out[m])[index(P.out_pitch[m], P.out_plane[m], 0, 0, 0)]);
     }
   }
-  for (int64_t s = 0; s < len; ++s) {
-    p[AXIS] = INC ? P.lo[AXIS] + s : P.hi[AXIS] - 1 - s;
-    A v = A(0);
-    A o[kMaxOut_];
+  if constexpr (AHEAD > 0) {
+    // pipelined path: ring slot s % AHEAD holds the loads of step s
+    extern __shared__ __align__(16) unsigned char ord_smem[];
+    T *ring = reinterpret_cast<T *>(ord_smem);
+    // the column's base in each grid (x and the non-ordered coordinate)
+    auto colbase = [&](int64_t pitch, int64_t plane) { return p[0] + p[OTHER] * (OTHER == 1 ? pitch : plane); };
+    const T *src[kLoads];
 #pragma unroll
-    for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
-    for (int t = 0; t < P.n_terms; ++t) {  // value terms come first
-      const OrdTerm &tm = P.terms[t];
-      A x;
-      if (tm.in < 0) {
-        x = v;
-      } else if (tm.prev >= 0) {
-        x = prev[0];
-#pragma unroll
-        for (int m = 1; m < kMaxOut_; ++m)
-          if (tm.prev == m) x = prev[m];
-      } else {
-        x = ord_load<T>(P.in[tm.in], index(P.in_pitch[tm.in], P.in_plane[tm.in], tm.dx, tm.dy, tm.dz), tm.nc);
-      }
-      if (tm.coef >= 0)
-        x = x * ord_load<T>(P.in[tm.coef], index(P.in_pitch[tm.coef], P.in_plane[tm.coef], 0, 0, 0), tm.cnc);
-      const A w = ord_weight(tm, A(0));
-      if (tm.out < 0) {
-        v = fma(w, x, v);
-      } else {
-#pragma unroll
-        for (int m = 0; m < kMaxOut_; ++m)
-          if (tm.out == m) o[m] = fma(w, x, o[m]);
+    for (int l = 0; l < kLoads; ++l) {
+      src[l] = nullptr;
+      if (l < P.n_loads) {
+        const OrdLoad &ld = P.loads[l];
+        src[l] = reinterpret_cast<const T *>(P.in[ld.grid]) + colbase(P.in_pitch[ld.grid], P.in_plane[ld.grid]) +
+                 ld.start;
       }
     }
-    // every output of this element is computed before any is stored
+    T *dst[kMaxOut_];
 #pragma unroll
-    for (int m = 0; m < kMaxOut_; ++m) {
-      if (m < P.n_out) {
-        reinterpret_cast<T *>(P.out[m])[index(P.out_pitch[m], P.out_plane[m], 0, 0, 0)] = from_arith<T>(o[m]);
-        prev[m] = to_arith(from_arith<T>(o[m]));  // the stored (rounded) value feeds the recurrence
+    for (int m = 0; m < kMaxOut_; ++m)
+      dst[m] = m < P.n_out ? reinterpret_cast<T *>(P.out[m]) + colbase(P.out_pitch[m], P.out_plane[m]) + P.out_start[m]
+                           : nullptr;
+#pragma unroll
+    for (int d = 0; d < AHEAD; ++d) {
+      if (d < len) issue_loads<T>(P, src, d, ring, d);
+      cp_async_commit();
+    }
+    for (int64_t s = 0; s < len; ++s) {
+      cp_async_wait<AHEAD - 1>();  // this thread's copies of step s have landed
+      const int slot = (int)(s % AHEAD);
+      const T *r = ring + (int64_t)slot * P.n_loads * kOrdThreads + threadIdx.x;
+      A v = A(0);
+      A o[kMaxOut_];
+#pragma unroll
+      for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
+      for (int t = 0; t < P.n_terms; ++t) {
+        const OrdTerm &tm = P.terms[t];
+        A x = v;
+        if (tm.prev >= 0) {
+          x = prev[0];
+#pragma unroll
+          for (int m = 1; m < kMaxOut_; ++m)
+            if (tm.prev == m) x = prev[m];
+        } else if (tm.xslot >= 0) {
+          x = to_arith(r[tm.xslot * kOrdThreads]);
+        }
+        if (tm.cslot >= 0) x = x * to_arith(r[tm.cslot * kOrdThreads]);
+        const A w = ord_weight(tm, A(0));
+        if (tm.out < 0) {
+          v = fma(w, x, v);
+        } else {
+#pragma unroll
+          for (int m = 0; m < kMaxOut_; ++m)
+            if (tm.out == m) o[m] = fma(w, x, o[m]);
+        }
+      }
+#pragma unroll
+      for (int m = 0; m < kMaxOut_; ++m) {
+        if (m < P.n_out) {
+          dst[m][s * P.out_step[m]] = from_arith<T>(o[m]);
+          prev[m] = to_arith(from_arith<T>(o[m]));
+        }
+      }
+      // the slot just used takes the element AHEAD steps on (issued after this
+      // element's stores; that element is written only at its own step)
+      if (s + AHEAD < len) issue_loads<T>(P, src, s + AHEAD, ring, slot);
+      cp_async_commit();
+    }
+    cp_async_wait<0>();
+  } else {
+    for (int64_t s = 0; s < len; ++s) {
+      p[AXIS] = INC ? P.lo[AXIS] + s : P.hi[AXIS] - 1 - s;
+      A v = A(0);
+      A o[kMaxOut_];
+  #pragma unroll
+      for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
+      for (int t = 0; t < P.n_terms; ++t) {  // value terms come first
+        const OrdTerm &tm = P.terms[t];
+        A x;
+        if (tm.in < 0) {
+          x = v;
+        } else if (tm.prev >= 0) {
+          x = prev[0];
+  #pragma unroll
+          for (int m = 1; m < kMaxOut_; ++m)
+            if (tm.prev == m) x = prev[m];
+        } else {
+          x = ord_load<T>(P.in[tm.in], index(P.in_pitch[tm.in], P.in_plane[tm.in], tm.dx, tm.dy, tm.dz), tm.nc);
+        }
+        if (tm.coef >= 0)
+          x = x * ord_load<T>(P.in[tm.coef], index(P.in_pitch[tm.coef], P.in_plane[tm.coef], 0, 0, 0), tm.cnc);
+        const A w = ord_weight(tm, A(0));
+        if (tm.out < 0) {
+          v = fma(w, x, v);
+        } else {
+  #pragma unroll
+          for (int m = 0; m < kMaxOut_; ++m)
+            if (tm.out == m) o[m] = fma(w, x, o[m]);
+        }
+      }
+      // every output of this element is computed before any is stored
+  #pragma unroll
+      for (int m = 0; m < kMaxOut_; ++m) {
+        if (m < P.n_out) {
+          reinterpret_cast<T *>(P.out[m])[index(P.out_pitch[m], P.out_plane[m], 0, 0, 0)] = from_arith<T>(o[m]);
+          prev[m] = to_arith(from_arith<T>(o[m]));  // the stored (rounded) value feeds the recurrence
+        }
       }
     }
   }
 }
 
-template <typename T>
-gscl_status launch_ordered_t(const OrdParams &P, int axis, bool inc, long long cols, cudaStream_t st) {
+template <typename T, int AXIS, bool INC>
+gscl_status launch_ordered_dir(const OrdParams &P, long long cols, cudaStream_t st) {
   const unsigned blocks = (unsigned)((cols + kOrdThreads - 1) / kOrdThreads);
-  if (axis == 2) {
-    if (inc) ordered_kernel<T, 2, true><<<blocks, kOrdThreads, 0, st>>>(P);
-    else ordered_kernel<T, 2, false><<<blocks, kOrdThreads, 0, st>>>(P);
-  } else {
-    if (inc) ordered_kernel<T, 1, true><<<blocks, kOrdThreads, 0, st>>>(P);
-    else ordered_kernel<T, 1, false><<<blocks, kOrdThreads, 0, st>>>(P);
+  if constexpr (sizeof(T) >= 4) {
+    if (P.n_loads <= kLoads) {
+      const bool few = P.n_loads <= kFewLoads;
+      const size_t smem = (size_t)(few ? kAheadFew : kAheadMany) * P.n_loads * kOrdThreads * sizeof(T);
+      if (few) ordered_kernel<T, AXIS, INC, kAheadFew><<<blocks, kOrdThreads, smem, st>>>(P);
+      else ordered_kernel<T, AXIS, INC, kAheadMany><<<blocks, kOrdThreads, smem, st>>>(P);
+      cudaError_t e = cudaGetLastError();
+      return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
+    }
   }
+  ordered_kernel<T, AXIS, INC, 0><<<blocks, kOrdThreads, 0, st>>>(P);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
+}
+
+template <typename T>
+gscl_status launch_ordered_t(const OrdParams &P, int axis, bool inc, long long cols, cudaStream_t st) {
+  if (axis == 2) return inc ? launch_ordered_dir<T, 2, true>(P, cols, st) : launch_ordered_dir<T, 2, false>(P, cols, st);
+  return inc ? launch_ordered_dir<T, 1, true>(P, cols, st) : launch_ordered_dir<T, 1, false>(P, cols, st);
 }
 
 }  // namespace
@@ -189,6 +314,38 @@ extern "C" gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, co
     }
   P.n_terms = nt;
   P.n_out = n_out;
+  // distinct element loads of one step (inputs at their offsets, coefficients
+  // at the element) for the pipelined path
+  int nl = 0;
+  auto slot_of = [&](int grid, int dx, int dy, int dz, int nc) -> int {
+    for (int l = 0; l < nl && l < kLoads; ++l) {
+      const OrdLoad &q = P.loads[l];
+      if (q.grid == grid && q.dx == dx && q.dy == dy && q.dz == dz) return l;
+    }
+    if (nl < kLoads) P.loads[nl] = OrdLoad{(int16_t)grid, (int16_t)nc, (int16_t)dx, (int16_t)dy, (int16_t)dz, 0};
+    return nl++;
+  };
+  for (int t = 0; t < nt; ++t) {
+    OrdTerm &d = P.terms[t];
+    d.xslot = (d.in >= 0 && d.prev < 0) ? (int16_t)slot_of(d.in, d.dx, d.dy, d.dz, d.nc) : (int16_t)-1;
+    d.cslot = d.coef >= 0 ? (int16_t)slot_of(d.coef, 0, 0, 0, d.cnc) : (int16_t)-1;
+  }
+  P.n_loads = nl;
+  // element offsets along the column: first step a0, direction +-1 per step
+  const int64_t a0 = inc ? b.lo[axis] : b.hi[axis] - 1, dir = inc ? 1 : -1;
+  for (int l = 0; l < nl && l < kLoads; ++l) {
+    OrdLoad &ld = P.loads[l];
+    const Grid &g = b.in[ld.grid];
+    const int64_t S = axis == 2 ? g.plane : g.pitch;
+    ld.start = (int64_t)ld.dz * g.plane + (int64_t)ld.dy * g.pitch + ld.dx + a0 * S;
+    ld.step = dir * S;
+  }
+  for (int m = 0; m < n_out; ++m) {
+    const Grid &g = b.out[m];
+    const int64_t S = axis == 2 ? g.plane : g.pitch;
+    P.out_start[m] = a0 * S;
+    P.out_step[m] = dir * S;
+  }
   for (int a = 0; a < 3; ++a) {
     P.lo[a] = b.lo[a];
     P.hi[a] = b.hi[a];
