@@ -317,6 +317,7 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
     batch = B.Batch(op, insts)
     cfg = batch.tune(trial_sweeps=3) if tune else None
     info = batch.info()
+    tile = batch.tile()
     points = sum(a * b * c for a, b, c in sides)
     stream = torch.cuda.current_stream()
 
@@ -338,6 +339,7 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
         return {"points": points, "ms_per_step": ms_batch, "value": sweeps * points / (ms_batch * 1e-3) / 1e9,
                 "sweep_ms": ms_batch / sweeps, "hbm_gbs": 8 * points / (ms_batch / sweeps * 1e-3) / 1e9,
                 "per_instance_loop_ms": float("nan"), "speedup_vs_loop": float("nan"), "tuned": cfg, "info": info,
+                "tile": tile,
                 "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
     # one sweep of the batch alone (no graph) for the roofline
     ms_sweep = timed(lambda: batch.run(1), 5 * steps, 2)
@@ -352,6 +354,7 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
     return {"points": points, "ms_per_step": ms_batch, "value": sweeps * points / (ms_batch * 1e-3) / 1e9,
             "sweep_ms": ms_sweep, "hbm_gbs": nbytes / (ms_sweep * 1e-3) / 1e9,
             "per_instance_loop_ms": ms_loop, "speedup_vs_loop": ms_loop / ms_batch, "tuned": cfg, "info": info,
+            "tile": tile,
             "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
 
 
@@ -808,7 +811,8 @@ def main():
                              "traffic": profile_traffic("batched_sweep")},
                 "per_instance_loop_ms": round(r["per_instance_loop_ms"], 3),
                 "speedup_vs_per_instance_loop": round(r["speedup_vs_loop"], 3),
-                "tuned_warps_prefetch": r["tuned"], "batch": r["info"], "gpu_launches": args.steps * 100}
+                "tuned_warps_prefetch": r["tuned"], "tile": r["tile"], "batch": r["info"],
+                "gpu_launches": args.steps * 100}
         if dist.rank == 0:
             print(json.dumps(line))
         return

@@ -351,6 +351,12 @@ gscl_status gscl_batch_destroy(gscl_batch b);
  * operator structure used (as gscl_stencil_specialization, -1 generic). */
 gscl_status gscl_batch_info(gscl_batch b, int32_t *ctas, int32_t *segments, int32_t *specialization);
 
+/* Tile shape (core elements, x by y) the batch's launches use: the dtype's
+ * default, or what gscl_batch_tune chose (FP32 / BF16 batches may get
+ * 64-column tiles with 4 rows per warp, which waste fewer lanes on narrow
+ * grids). */
+gscl_status gscl_batch_tile(gscl_batch b, int32_t *tile_x, int32_t *tile_y);
+
 /*
  * `sweeps` sweeps of every instance with in[0] / out[0] as the ping-pong
  * pair, exactly as gscl_do_all(..., sweeps) on each instance alone (same
@@ -372,8 +378,10 @@ gscl_status gscl_batch_reduce(gscl_batch b, int32_t reduce_op, double *results, 
 /*
  * Autotuner: times trial_sweeps sweeps (in[0] -> out[0], so in[0] is left
  * unchanged and out[0] receives one sweep) for each tile shape (warps per
- * CTA 2/4/8 x prefetched planes 1/2/3), keeps the fastest and reports it.
- * Synchronises `stream`.
+ * CTA 2/4/8 x prefetched planes 1/2/3, and for FP32 / BF16 batches both the
+ * default 128-column tiles and 64-column tiles with 4 rows per warp), keeps
+ * the fastest and reports its warps and prefetch (gscl_batch_tile gives the
+ * tile).  Synchronises `stream`.
  */
 gscl_status gscl_batch_tune(gscl_batch b, int32_t trial_sweeps, void *stream, int32_t *warps, int32_t *prefetch);
 

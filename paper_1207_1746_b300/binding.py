@@ -100,6 +100,7 @@ def lib():
         "gscl_tune_sweeps": [P(StencilC), P(u64), i32, P(u64), i32, i32, vp, P(i32)],
         "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
         "gscl_do_ordered": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
+        "gscl_batch_tile": [u64, P(i32), P(i32)],
         "gscl_do_reduce_within": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), ctypes.c_double,
                                   P(ctypes.c_double), i32, vp, i64, vp],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
@@ -428,6 +429,12 @@ class Batch:
             raise ValueError("results must be a float64 CUDA tensor with one entry per instance")
         check(lib().gscl_batch_reduce(self.handle, int(reduce_op), ctypes.c_void_p(results.data_ptr()),
                                       stream_ptr(stream)))
+
+    def tile(self):
+        """(tile_x, tile_y) of the batch's launches (gscl_batch_tile)."""
+        x, y = ctypes.c_int32(), ctypes.c_int32()
+        check(lib().gscl_batch_tile(self.handle, ctypes.byref(x), ctypes.byref(y)))
+        return x.value, y.value
 
     def tune(self, trial_sweeps=3, stream=None):
         w, p = ctypes.c_int32(), ctypes.c_int32()

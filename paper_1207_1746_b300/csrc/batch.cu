@@ -6,6 +6,7 @@
 // (in[0] -> out[0] and back), so a whole sweep group can be captured once in
 // a CUDA graph and replayed.  Per-instance reductions write one partial per
 // segment and a second kernel folds each instance's segments in order.
+#include <stdlib.h>
 #include <string.h>
 
 #include <chrono>
@@ -253,6 +254,9 @@ gscl_status gscl_batch_create(const gscl_stencil *op, int32_t n_inst, const gscl
   if (n_out) bt->out_h.assign(out, out + (size_t)n_inst * n_out);
   for (auto &t : bt->terms)
     if (t.out == GSCL_VALUE) bt->has_value = true;
+  // GSCL_BATCH_NARROW=1 starts the batch on the narrow tiles (the tuner
+  // chooses between the shapes by timing)
+  if (const char *e = getenv("GSCL_BATCH_NARROW")) bt->cfg.narrow = atoi(e) != 0;
   Grid g0;
   if (gscl_status s = lookup(bt->in_h[0], &g0)) return s;
   bt->dtype = g0.dtype;
@@ -286,6 +290,17 @@ gscl_status gscl_batch_info(gscl_batch h, int32_t *ctas, int32_t *segments, int3
   if (ctas) *ctas = bt->G;
   if (segments) *segments = bt->S;
   if (specialization) *specialization = bt->base.op;
+  return GSCL_OK;
+}
+
+gscl_status gscl_batch_tile(gscl_batch h, int32_t *tile_x, int32_t *tile_y) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  const int vx = bt->base.narrow ? 2 : (bt->dtype == GSCL_F64 ? 2 : 4);
+  const int vy = bt->base.narrow ? 4 : 2;
+  if (tile_x) *tile_x = 32 * vx;
+  if (tile_y) *tile_y = bt->base.threads / 32 * vy;
   return GSCL_OK;
 }
 
@@ -374,9 +389,13 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
   cudaEventCreate(&e1);
   const int nws[] = {2, 4, 8};
   const int pfs[] = {1, 2, 3};
+  // tile shape: the dtype's default, and for FP32 / BF16 the narrow 64-column
+  // tiles (4 rows per warp) that waste fewer lanes on narrow grids
+  const int shapes = bt->dtype == GSCL_F64 ? 1 : 2;
+  for (int narrow = 0; narrow < shapes; ++narrow)
   for (int nw : nws)
     for (int pf : pfs) {
-      bt->cfg = TileCfg{nw, pf, keep.generic};
+      bt->cfg = TileCfg{nw, pf, keep.generic, narrow != 0};
       if (build(bt) != GSCL_OK) continue;  // e.g. does not fit in shared memory
       int first = 0;
       if (current_table(bt, &first) != GSCL_OK) continue;

@@ -181,8 +181,6 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const Grid &g0 = b.in[0];
   const int n_in = (int)b.in.size(), n_out = (int)b.out.size();
   const int elem = g0.elem;
-  const int VX = vx_for(g0.dtype);
-  const int TX = 32 * VX;
   std::vector<gscl_term> terms;
   if (b.op) {
     terms.assign(b.op->terms, b.op->terms + b.op->n_terms);
@@ -190,6 +188,12 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
     gscl_term id = {0, 0, 0, 0, GSCL_NONE, GSCL_VALUE, 0, 1.0};
     terms.push_back(id);
   }
+  std::vector<int> perm;
+  pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
+  // narrow tiles: compiled for batches of compile-time operators, FP32 / BF16
+  const bool narrow = cfg.narrow && g0.dtype != GSCL_F64 && batch_capable(pl->op);
+  const int VX = narrow ? 2 : vx_for(g0.dtype);
+  const int TX = 32 * VX;
   // reach per input grid (coefficient reads are at the core element)
   int rxa[kMaxIn] = {}, rya[kMaxIn] = {}, rz = 0;
   for (auto &t : terms) {
@@ -206,14 +210,12 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   }
   const int nz_range = (int)(b.hi[2] - b.lo[2]);
   const int smem_cap = max_smem_per_block();
-  std::vector<int> perm;
-  pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
   // inputs read only at the core element go to the two-slot centre ring
   // (FP32 / BF16 storage; the kernel's operator tables make the same choice)
   const uint32_t cmask = g0.dtype == GSCL_F64 ? 0u : static_centre_mask(pl->op);
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
-  const int VY = vy_for(g0.dtype);
+  const int VY = narrow ? 4 : vy_for(g0.dtype);
   // defaults from tile sweeps on the 256^3 heat workload (B300): FP64 4 warps,
   // FP32 / BF16 8 warps, one plane prefetched beyond the stencil's reach
   int NW = g0.dtype == GSCL_F64 ? 4 : 8, PF = nz_range > 1 ? 1 : 0;
@@ -324,6 +326,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
   pl->threads = threads;
   pl->smem = smem;
+  pl->narrow = narrow;
   pl->work = (long long)P.inst.tiles_x * P.inst.tiles_y * nz_range;
   pl->max_ctas = reduce ? kMaxReduceCtas : 0x7fffffff;
   return GSCL_OK;

@@ -23,6 +23,7 @@ struct TileCfg {
   int nw = 0;            // warps per CTA
   int pf = 0;            // planes prefetched beyond the stencil's z reach
   bool generic = false;  // interpret the term list even if a compiled structure matches
+  bool narrow = false;   // batches, FP32 / BF16: 64-column tiles with 4 rows per warp
 };
 
 bool overlaps(const Grid &a, const Grid &b);

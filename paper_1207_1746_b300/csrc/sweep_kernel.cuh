@@ -883,6 +883,7 @@ struct Plan {
   int op = OP_GENERIC;        // StaticOpId of a matched compile-time operator
   bool batch = false;         // work-list launch of a batch
   int batch_ctas = 0;         // its grid (fixed when the work-list was built)
+  bool narrow = false;        // batches of FP32 / BF16 grids: 64-column tiles, 4 rows per warp
 };
 
 // Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: two
@@ -896,9 +897,9 @@ template <> struct VyOf<double> { static constexpr int value = 2; };
 // Launches one wave: as many CTAs as the device holds at once (occupancy
 // query per kernel and shape, cached), never more than there is work.  With
 // occupancy_only set, reports resident CTAs per SM instead of launching.
-template <typename T, int VX, int RED, class Op, bool BATCH>
+template <typename T, int VX, int RED, class Op, bool BATCH, int VY = VyOf<T>::value>
 gscl_status launch_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
-  auto kern = sweep_kernel<T, VX, VyOf<T>::value, RED, Op, BATCH>;
+  auto kern = sweep_kernel<T, VX, VY, RED, Op, BATCH>;
   static std::mutex mu;
   static size_t attr_set = 0;
   static int cached_threads = -1, cached_blocks = 0, cached_dev = -1;
@@ -992,6 +993,11 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
   } else if constexpr (BATCH && !BatchCapable<Def>::value) {
     return fail(GSCL_ERR_INVALID, "no batched kernel for this operator structure");
   } else {
+    // narrow tiles (64 x 4 rows per warp, the same 8 points per thread) for
+    // batches of FP32 / BF16 grids whose widths leave 128-column tiles idle
+    if constexpr (BATCH && !std::is_same<T, double>::value) {
+      if (pl.narrow) return launch_t<T, 2, RED, StaticOp<Def>, BATCH, 4>(pl, stream, occ);
+    }
     return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
   }
 }

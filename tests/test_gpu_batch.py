@@ -23,12 +23,16 @@ SHAPES = [(33, 40, 35), (64, 17, 50), (90, 90, 20), (31, 64, 64), (130, 10, 40),
 H = (1, 1, 1)
 
 
-@pytest.fixture(params=["compiled", "generic"])
+@pytest.fixture(params=["compiled", "generic", "narrow"])
 def kernel_path(request, monkeypatch):
+    """compiled: the operator tables; generic: the runtime term loop; narrow:
+    the tables on 64-column tiles with 4 rows per warp (FP32 / BF16 batches)."""
+    monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    monkeypatch.delenv("GSCL_BATCH_NARROW", raising=False)
     if request.param == "generic":
         monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
-    else:
-        monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    elif request.param == "narrow":
+        monkeypatch.setenv("GSCL_BATCH_NARROW", "1")
     return request.param
 
 
@@ -70,7 +74,7 @@ def test_batch_sweeps_bitexact_with_single_grid(kernel_path, dtype, with_f, grap
     batch = B.Batch(op, insts)
     info = batch.info()
     assert info["ctas"] >= 1 and info["segments"] >= info["ctas"]
-    if kernel_path == "compiled":
+    if kernel_path in ("compiled", "narrow"):
         assert info["specialization"] == (0 if with_f else 1)
     else:
         assert info["specialization"] == -1
@@ -128,6 +132,15 @@ def test_batch_fused_reduce_writes_outputs():
         want = B.do_reduce(B.L2, S.heat7_fused(0.125), ins, [v])
         assert abs(res[k].item() - want) <= 1e-13 * want
         assert torch.equal(outs[0].download(), v.download())
+
+
+def test_batch_tile_reports_the_shape(monkeypatch):
+    monkeypatch.setenv("GSCL_BATCH_NARROW", "1")
+    insts, _ = make_instances("f32", False, seed=3)
+    assert B.Batch(S.heat7(0.125, with_f=False), insts).tile() == (64, 32)
+    monkeypatch.delenv("GSCL_BATCH_NARROW")
+    insts, _ = make_instances("f32", False, seed=3)
+    assert B.Batch(S.heat7(0.125, with_f=False), insts).tile() == (128, 16)
 
 
 def test_batch_tune_keeps_results():
