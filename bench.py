@@ -37,7 +37,7 @@ SWEEPS = 200
 EVERY = 10
 SEED = 202
 TERMS_PLAIN = 8                # FMAs per point of the plain sweep (one per stencil input)
-BYTES_PER_PT = {"f64": 24, "f32": 12}  # u read, f read, u' written
+BYTES_PER_PT = {"f64": 24, "f32": 12, "bf16": 6}  # u read, f read, u' written
 
 
 def load_json(path):
@@ -828,14 +828,16 @@ def main():
 
     variants = {}
     if not args.no_variants:
-        r32 = run_gpu("f32", args.steps, args.warmup, dist, args.n, args.sweeps)
-        t32 = dist.max(r32["ms_total"])
-        variants["f32"] = {
-            "dtype": "f32", "value": round(updates / (t32 * 1e-3) / 1e9, 3), "unit": "GPoint-updates/s",
-            "ms_per_step": round(t32 / args.steps, 3),
-            "roofline": roofline_hbm("f32", r32["plain_launch_ms"], args.n ** 3, peaks),
-            "fused_launch_ms": round(r32["fused_launch_ms"], 4), "plain_launch_ms": round(r32["plain_launch_ms"], 4),
-            "final_residual": r32["residuals"][-1]}
+        # FP32 storage, and BF16 storage (FP32 arithmetic; a smoothing-grade precision)
+        for vdt in ("f32", "bf16"):
+            rv = run_gpu(vdt, args.steps, args.warmup, dist, args.n, args.sweeps)
+            tv = dist.max(rv["ms_total"])
+            variants[vdt] = {
+                "dtype": vdt, "value": round(updates / (tv * 1e-3) / 1e9, 3), "unit": "GPoint-updates/s",
+                "ms_per_step": round(tv / args.steps, 3),
+                "roofline": roofline_hbm(vdt, rv["plain_launch_ms"], args.n ** 3, peaks),
+                "fused_launch_ms": round(rv["fused_launch_ms"], 4), "plain_launch_ms": round(rv["plain_launch_ms"], 4),
+                "final_residual": rv["residuals"][-1]}
 
     e2e = None
     if not args.no_e2e:
