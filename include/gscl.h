@@ -286,6 +286,26 @@ typedef enum {
 gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
                             const gscl_grid *out, int32_t n_out, const gscl_range *range, void *stream);
 
+/*
+ * Arithmetic of FP64 grids (not an operation of the paper; a B300 precision
+ * mode).  GSCL_FP64_IEEE (default): IEEE FP64 fused multiply-adds, bound on
+ * B300 by its FP64 pipe (about 1.7 per clock per SM).  GSCL_FP64_PAIR: each
+ * double read is split on the integer pipe into two floats (24 + 24
+ * significant bits; the split error is below 2^-47 |x|), terms are
+ * accumulated with an exact FP32 two-product and a two-sum, and the stored
+ * value is the double nearest the pair.  The error of one operator
+ * evaluation is then a small multiple of 2^-47 S(p), S(p) = sum |w X C|
+ * (the absolute stencil), inside the FP64 tolerance of 1e-13 S(p) but about
+ * 2^6 above IEEE FP64.  Storage, traffic and reductions (FP64 accumulation)
+ * are the same in both modes; ordered iteration spaces and gscl_convert keep
+ * IEEE FP64.  Process-wide; the environment variable GSCL_FP64_ARITH=pair sets
+ * the initial mode.  Kernels already enqueued keep the mode they were
+ * launched with.
+ */
+typedef enum { GSCL_FP64_IEEE = 0, GSCL_FP64_PAIR = 1 } gscl_fp64_arithmetic;
+gscl_status gscl_set_fp64_arithmetic(int32_t mode);
+int32_t gscl_get_fp64_arithmetic(void);
+
 /* Bytes of device workspace one gscl_do_reduce call needs (a constant). */
 int64_t gscl_reduce_workspace_bytes(void);
 

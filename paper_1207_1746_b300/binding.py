@@ -101,6 +101,8 @@ def lib():
         "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
         "gscl_do_ordered": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
+        "gscl_set_fp64_arithmetic": [i32],
+        "gscl_get_fp64_arithmetic": [],
         "gscl_do_reduce_within": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), ctypes.c_double,
                                   P(ctypes.c_double), i32, vp, i64, vp],
         "gscl_batch_create": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
@@ -363,6 +365,19 @@ def do_reduce_noalloc(reduce_op, op, ins, outs=(), rng=None, result=None, stream
                                        _handles(ins), len(ins), _handles(outs), len(outs), _range(rng), rptr,
                                        int(on_host), stream_ptr(stream)))
     return host.value if on_host else None
+
+
+FP64_IEEE, FP64_PAIR = 0, 1
+
+
+def set_fp64_arithmetic(mode):
+    """gscl_set_fp64_arithmetic: "ieee" (default) or "pair" (FP64 grids
+    evaluated in pairs of FP32 numbers, off the FP64 pipe)."""
+    check(lib().gscl_set_fp64_arithmetic({"ieee": FP64_IEEE, "pair": FP64_PAIR}[mode]))
+
+
+def get_fp64_arithmetic():
+    return {FP64_IEEE: "ieee", FP64_PAIR: "pair"}[lib().gscl_get_fp64_arithmetic()]
 
 
 def fma_throughput(dtype="f64", iters=2048, stream=None):

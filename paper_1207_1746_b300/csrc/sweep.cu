@@ -2,6 +2,7 @@
 // grids (Section 3's rules: reads only at fixed offsets inside the stencil
 // shape's halo, writes only at the core element, no order promised),
 // launch planning and the C ABI entry points.
+#include <atomic>
 #include <stdlib.h>
 #include <string.h>
 
@@ -252,6 +253,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
     d.toff = t.in == GSCL_VALUE ? 0 : (rya[t.in] + t.dy) * BWa[t.in] + AXa[t.in] + t.dx;
     d.wf = (float)t.w;
     d.wd = t.w;
+    d.wl = (float)(t.w - (double)d.wf);
   };
   if (pl->op != OP_GENERIC) {
     // table order (value terms first); the kernel reads only the weights
@@ -354,18 +356,38 @@ gscl_status launch_generic(const Plan &pl, int red, cudaStream_t stream, int *oc
 
 }  // namespace
 
+// Arithmetic of FP64 grids: IEEE FP64 (default) or pairs of FP32 numbers.
+std::atomic<int> g_fp64_arith{-1};
+
+int fp64_arith() {
+  int m = g_fp64_arith.load();
+  if (m < 0) {  // first use: GSCL_FP64_ARITH=pair selects the pair arithmetic
+    const char *e = getenv("GSCL_FP64_ARITH");
+    m = (e && strcmp(e, "pair") == 0) ? GSCL_FP64_PAIR : GSCL_FP64_IEEE;
+    int expect = -1;
+    g_fp64_arith.compare_exchange_strong(expect, m);
+    m = g_fp64_arith.load();
+  }
+  return m;
+}
+
 // Launches (or, with occupancy_only, sizes) the kernel a plan names.
 gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only) {
+  const bool pair = dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_PAIR;
   if (pl.op != OP_GENERIC) {
     switch (dtype) {
-      case GSCL_F64: return launch_static_f64(pl, red, stream, occupancy_only);
+      case GSCL_F64:
+        return pair ? launch_static_f64pair(pl, red, stream, occupancy_only)
+                    : launch_static_f64(pl, red, stream, occupancy_only);
       case GSCL_F32: return launch_static_f32(pl, red, stream, occupancy_only);
       case GSCL_BF16: return launch_static_bf16(pl, red, stream, occupancy_only);
     }
     return fail(GSCL_ERR_DTYPE, "unknown dtype");
   }
   switch (dtype) {
-    case GSCL_F64: return launch_generic<double>(pl, red, stream, occupancy_only);
+    case GSCL_F64:
+      return pair ? launch_generic<f64pair>(pl, red, stream, occupancy_only)
+                  : launch_generic<double>(pl, red, stream, occupancy_only);
     case GSCL_F32: return launch_generic<float>(pl, red, stream, occupancy_only);
     case GSCL_BF16: return launch_generic<__nv_bfloat16>(pl, red, stream, occupancy_only);
   }
@@ -379,6 +401,14 @@ using namespace gscl;
 extern "C" {
 
 int64_t gscl_reduce_workspace_bytes(void) { return kWorkspaceBytes; }
+
+gscl_status gscl_set_fp64_arithmetic(int32_t mode) {
+  if (mode != GSCL_FP64_IEEE && mode != GSCL_FP64_PAIR) return fail(GSCL_ERR_INVALID, "unknown FP64 arithmetic %d", mode);
+  g_fp64_arith.store(mode);
+  return GSCL_OK;
+}
+
+int32_t gscl_get_fp64_arithmetic(void) { return fp64_arith(); }
 
 int32_t gscl_stencil_specialization(const gscl_stencil *op, int32_t n_in, int32_t n_out) {
   if (!op || !op->terms || op->n_terms < 1 || op->n_terms > kMaxTerms) return OP_GENERIC;

@@ -22,6 +22,7 @@
 #include <utility>
 
 #include "gscl_internal.h"
+#include "pair64.cuh"
 #include "static_ops.h"
 
 namespace gscl {
@@ -47,6 +48,8 @@ struct DevTerm {
   int32_t toff;  // (RY_in + dy) * BW_in + AX_in + dx, in the read input's box
   float wf;
   double wd;
+  float wl;      // pair arithmetic: the weight's low part, wd - (double)wf
+  int32_t pad2;
 };
 
 struct OutDesc {
@@ -104,18 +107,27 @@ template <typename T> struct Arith;
 template <> struct Arith<double> { using A = double; };
 template <> struct Arith<float> { using A = float; };
 template <> struct Arith<__nv_bfloat16> { using A = float; };
+template <> struct Arith<f64pair> { using A = Df64; };
+
+// Storage types held as FP64 in memory (IEEE or pair arithmetic).
+template <typename T> struct IsFp64Storage { static constexpr bool value = false; };
+template <> struct IsFp64Storage<double> { static constexpr bool value = true; };
+template <> struct IsFp64Storage<f64pair> { static constexpr bool value = true; };
 
 __device__ __forceinline__ double to_arith(double x) { return x; }
 __device__ __forceinline__ float to_arith(float x) { return x; }
 __device__ __forceinline__ float to_arith(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ Df64 to_arith(f64pair x) { return split_f64(x.v); }
 
 template <typename T> __device__ __forceinline__ T from_arith(typename Arith<T>::A x);
 template <> __device__ __forceinline__ double from_arith<double>(double x) { return x; }
 template <> __device__ __forceinline__ float from_arith<float>(float x) { return x; }
 template <> __device__ __forceinline__ __nv_bfloat16 from_arith<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+template <> __device__ __forceinline__ f64pair from_arith<f64pair>(Df64 x) { return f64pair{combine_f64(x)}; }
 
 __device__ __forceinline__ double term_weight(const DevTerm &t, double) { return t.wd; }
 __device__ __forceinline__ float term_weight(const DevTerm &t, float) { return t.wf; }
+__device__ __forceinline__ Df64 term_weight(const DevTerm &t, Df64) { return Df64(t.wf, t.wl); }
 
 // ------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -381,7 +393,7 @@ struct StaticOp {
   // memory it frees gains (the host planner makes the same choice).
   template <typename T>
   __host__ __device__ static constexpr bool in_centre_ring(int in) {
-    return !std::is_same<T, double>::value && centre_only<Def>(in);
+    return !IsFp64Storage<T>::value && centre_only<Def>(in);
   }
 
   // element (row, lane) of centre-ring input `in` in slot cslot
@@ -503,6 +515,11 @@ __device__ __forceinline__ void widen_group(const double (&x)[N], double (&d)[N]
 #pragma unroll
   for (int i = 0; i < N; ++i) d[i] = x[i];
 }
+template <int N>
+__device__ __forceinline__ void widen_group(const Df64 (&x)[N], double (&d)[N]) {
+#pragma unroll
+  for (int i = 0; i < N; ++i) d[i] = combine_f64(x[i]);
+}
 
 // max |v| is tracked on the bits of |v| in the value's own format (for
 // non-negative IEEE numbers the unsigned order of the bits is the numeric
@@ -513,7 +530,9 @@ __device__ __forceinline__ unsigned long long abs_key(double v) {
 __device__ __forceinline__ unsigned long long abs_key(float v) {
   return (unsigned long long)(__float_as_uint(v) & 0x7fffffffu);
 }
+__device__ __forceinline__ unsigned long long abs_key(Df64 v) { return abs_key(combine_f64(v)); }
 __device__ __forceinline__ double key_value(unsigned long long k, double) { return __longlong_as_double((long long)k); }
+__device__ __forceinline__ double key_value(unsigned long long k, Df64) { return __longlong_as_double((long long)k); }
 __device__ __forceinline__ double key_value(unsigned long long k, float) { return (double)__uint_as_float((unsigned)k); }
 
 // ---------------------------------------------------------------- kernel
@@ -891,6 +910,7 @@ struct Plan {
 // of the per-plane synchronisation.
 template <typename T> struct VxOf { static constexpr int value = 4; };
 template <> struct VxOf<double> { static constexpr int value = 2; };
+template <> struct VxOf<f64pair> { static constexpr int value = 2; };
 template <typename T> struct VyOf { static constexpr int value = 2; };
 template <> struct VyOf<double> { static constexpr int value = 2; };
 
@@ -983,6 +1003,7 @@ inline bool batch_capable(int op) {
 gscl_status launch_static_f64(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
 gscl_status launch_static_f32(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
 gscl_status launch_static_bf16(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
+gscl_status launch_static_f64pair(const Plan &pl, int red, cudaStream_t stream, int *occupancy_only);
 
 template <typename T, int RED, class Def, bool BATCH>
 gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
@@ -995,7 +1016,7 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
   } else {
     // narrow tiles (64 x 4 rows per warp, the same 8 points per thread) for
     // batches of FP32 / BF16 grids whose widths leave 128-column tiles idle
-    if constexpr (BATCH && !std::is_same<T, double>::value) {
+    if constexpr (BATCH && !IsFp64Storage<T>::value) {
       if (pl.narrow) return launch_t<T, 2, RED, StaticOp<Def>, BATCH, 4>(pl, stream, occ);
     }
     return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);

@@ -1,0 +1,136 @@
+"""FP64 grids in pair arithmetic (gscl_set_fp64_arithmetic(GSCL_FP64_PAIR)):
+parity against the FP64 oracle at the FP64 tolerance |gpu - oracle| <=
+1e-13 S(p), bit-exactness where every partial result is representable in
+24 + 24 bits (integer data, dyadic weights), and the split of special
+values."""
+import numpy as np
+import pytest
+import torch
+
+from gpu_common import assert_within, run_pair
+from oracle import drivers as D
+from oracle import oracle as O
+from paper_1207_1746_b300 import binding as B
+from paper_1207_1746_b300 import inputs as I
+from paper_1207_1746_b300 import stencils as S
+from test_gpu_parity import SHAPES, dyadic_terms, int_field
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-13
+
+
+@pytest.fixture(autouse=True)
+def pair_mode():
+    B.set_fp64_arithmetic("pair")
+    yield
+    B.set_fp64_arithmetic("ieee")
+
+
+@pytest.fixture(params=["compiled", "generic"])
+def kernel_path(request, monkeypatch):
+    if request.param == "generic":
+        monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+    else:
+        monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    return request.param
+
+
+def test_mode_switch():
+    assert B.get_fp64_arithmetic() == "pair"
+    with pytest.raises(B.GsclError):
+        B.lib().gscl_set_fp64_arithmetic(7)
+
+
+def test_heat_fused_and_plain_within_fp64_tolerance(kernel_path):
+    n, h = (97, 45, 33), (1, 1, 1)
+    u = I.random_interior(5, n, h, -1.0, 1.0)
+    f = I.random_interior(6, n, h, -1.0, 1.0)
+    got, ref, gv, ov, Sab = run_pair(S.heat7_fused(0.125), [u, f], [h, h], n, [h], "f64", reduce_op=B.L2)
+    assert_within(got[0], ref[0], Sab[0], TOL)
+    assert abs(gv - ov) <= TOL * ov
+    got2, ref2, _, _, Sab2 = run_pair(S.heat7(0.125), [u, f], [h, h], n, [h], "f64")
+    assert_within(got2[0], ref2[0], Sab2[0], TOL)
+
+
+def test_weights_not_representable_in_fp32(kernel_path):
+    """Weights with a non-zero low part (1/3, 1/7, pi/10) exercise the pair
+    weights: still within the FP64 tolerance, far inside FP32's."""
+    n, h = (70, 30, 20), (1, 1, 1)
+    u = I.random_interior(15, n, h, -3.0, 3.0)
+    terms = [(0, 0, 0, 0, B.NONE, 0, 1.0 / 3.0)] + [(dx, dy, dz, 0, B.NONE, 0, w)
+                                                   for (dx, dy, dz), w in zip(S.X6, [1 / 7, np.pi / 10] * 3)]
+    got, ref, _, _, Sab = run_pair(terms, [u], [h], n, [h], "f64")
+    assert_within(got[0], ref[0], Sab[0], TOL)
+
+
+def test_jacobi2d_and_climate_within_fp64_tolerance(kernel_path):
+    n2, h2 = (200, 70, 1), (1, 1, 0)
+    a = I.random_interior(21, n2, h2, 0.0, 1.0, halo_value=0.5)
+    got, ref, _, _, Sab = run_pair(S.jacobi5_2d(), [a], [h2], n2, [h2], "f64")
+    assert_within(got[0], ref[0], Sab[0], TOL)
+    n3, h3 = (70, 40, 12), (2, 2, 1)
+    fields = I.climate(303, n3, h3)
+    ins = [fields[k] for k in I.CLIMATE_FIELDS]
+    got, ref, _, _, Sab = run_pair(S.climate(), ins, [h3] * 8, n3, [h3] * 3, "f64")
+    for g, r, s in zip(got, ref, Sab):
+        assert_within(g, r, s, TOL)
+
+
+@pytest.mark.parametrize("shape_id", range(len(SHAPES)))
+def test_bitexact_integer_data(shape_id):
+    """Integers below 2^10 and dyadic weights: every split is exact (lo = 0),
+    every product and partial sum is representable, so the pair arithmetic
+    gives the oracle's bits."""
+    n, in_halos, out_halos = SHAPES[shape_id]
+    rng = np.random.default_rng(100 + shape_id)
+    dims = 2 if n[2] == 1 else 3
+    arrays = [int_field(rng, I.padded_shape(n, h), 64) for h in in_halos]
+    arrays[2] = int_field(rng, I.padded_shape(n, in_halos[2]), 8)
+    terms = dyadic_terms(rng, 3, 2, in_halos, 14, dims=dims)
+    got, ref, _, _, _ = run_pair(terms, arrays, in_halos, n, out_halos, "f64")
+    for g, r in zip(got, ref):
+        assert np.array_equal(g, r, equal_nan=True)
+
+
+def test_special_values_through_the_split():
+    """Zeros of both signs, values below 2^-74 and above 2^100 (the hardware
+    conversion path), an infinity and a NaN copied by the identity operator
+    (value 1 x): exact for the normal values, propagated for inf and NaN."""
+    n, h = (64, 4, 3), (0, 0, 0)
+    a = np.full(I.padded_shape(n, h), 1.0)
+    v = a.reshape(-1)
+    v[:8] = [0.0, -0.0, 3e-30, -1e-40, 1e110, -7.5e120, np.inf, np.nan]
+    v[8:40] = np.random.default_rng(3).uniform(-1, 1, 32) * 2.0 ** np.arange(-60, 100, 5)
+    terms = [(0, 0, 0, 0, B.NONE, 0, 1.0)]
+    got, ref, _, _, _ = run_pair(terms, [a], [h], n, [h], "f64")
+    g, r = got[0].reshape(-1), ref[0].reshape(-1)
+    assert np.isnan(g[7]) and g[6] == np.inf
+    assert np.array_equal(np.signbit(g[:2]), [False, True]) and np.all(g[:2] == 0)
+    # normal values: the split keeps 47 of 53 bits of each
+    m = np.isfinite(r)
+    assert np.all(np.abs(g[m] - r[m]) <= 2.0 ** -46 * np.abs(r[m]))
+
+
+def test_error_after_200_heat_sweeps_reported():
+    """Pair arithmetic over the heat workload's 200 sweeps (64^3, seed 202,
+    fused L2 residual every 10): error against the FP64 oracle, reported and
+    loosely gated."""
+    n = 64
+    u0, f = I.heat3d(202, n)
+    shape, h = (n, n, n), (1, 1, 1)
+    u, v = B.Grid(shape, h).upload(u0), B.Grid(shape, h).upload(u0)
+    F = B.Grid(shape, h).upload(f)
+    fused, plain = B.Stencil(S.heat7_fused(0.125)), B.Stencil(S.heat7(0.125))
+    res = []
+    for _ in range(20):
+        res.append(B.do_reduce(B.L2, fused, [u, F], [v]))
+        B.swap(u, v)
+        B.do_all(plain, [u, F], [v], sweeps=9)
+        B.swap(u, v)
+    got = u.download().numpy()
+    ou, ores = D.heat_run(O.Grid(u0.copy(), h), O.Grid(f.copy(), h), 0.125, 200, every=10)
+    err = np.max(np.abs(got - ou.a)) / np.max(np.abs(ou.a))
+    rerr = max(abs(a - b) / b for a, b in zip(res, ores))
+    print(f"heat3d 64^3 f64 pair: |u_200 - oracle|_inf / |oracle|_inf = {err:.3e}; "
+          f"max relative residual error = {rerr:.3e}")
+    assert err <= 1e-11 and rerr <= 1e-11
