@@ -296,7 +296,11 @@ gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_gr
  * value is the double nearest the pair.  The error of one operator
  * evaluation is then a small multiple of 2^-47 S(p), S(p) = sum |w X C|
  * (the absolute stencil), inside the FP64 tolerance of 1e-13 S(p) but about
- * 2^6 above IEEE FP64.  Storage, traffic and reductions (FP64 accumulation)
+ * 2^6 above IEEE FP64.  A pair holds magnitudes from about 2^-100 to below
+ * 2^128 (FP32's exponent range): grids whose values or intermediate results
+ * leave that range need IEEE FP64 (beyond it values become infinite, below it
+ * they lose bits); NaN propagates, and an infinity becomes NaN.  Storage,
+ * traffic and reductions (FP64 accumulation)
  * are the same in both modes; ordered iteration spaces and gscl_convert keep
  * IEEE FP64.  Process-wide; the environment variable GSCL_FP64_ARITH=pair sets
  * the initial mode.  Kernels already enqueued keep the mode they were

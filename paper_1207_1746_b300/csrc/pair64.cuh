@@ -10,6 +10,8 @@
 // as the double nearest hi + lo (one FP64 add per stored element).  The
 // arithmetic error of an operator is then a small multiple of 2^-47 times
 // sum_t |w_t x_t| (the absolute stencil), against 2^-53 for IEEE FP64.
+// A pair spans FP32's exponent range: magnitudes from about 2^-100 (below,
+// the low part underflows) to below 2^128 (above, the high part overflows).
 // Storage, TMA traffic and reductions (FP64 accumulation) are unchanged.
 #pragma once
 
@@ -29,26 +31,22 @@ struct Df64 {
   __device__ __forceinline__ Df64(float h, float l) : hi(h), lo(l) {}
 };
 
-// x -> hi + lo on the integer pipe (IEEE 754 binary64 / binary32 layouts).
-// Normal doubles with 2^-74 <= |x| < 2^128 take the bit path; zero is a
-// signed zero pair; anything else (tiny, huge, inf, NaN) takes the hardware
-// conversions.
+// x -> hi + lo: hi keeps the sign, exponent and top 23 fraction bits of x
+// (integer pipe); lo is the 29-bit remainder converted to float (rounded to
+// 24 bits) and scaled by 2^(E - 52) with an exponent add, which stays exact
+// while the result is normal.  Normal doubles with 2^-74 <= |x| < 2^128 take
+// this path; zero is a signed zero pair; anything else (tiny, huge, inf,
+// NaN) takes the hardware conversions.
 __device__ __forceinline__ Df64 split_f64(double x) {
   const unsigned long long b = (unsigned long long)__double_as_longlong(x);
   const unsigned h32 = (unsigned)(b >> 32), l32 = (unsigned)b;
   const unsigned sign = h32 & 0x80000000u;
   const int E = (int)((h32 >> 20) & 0x7ffu) - 1023;  // unbiased exponent
   if (E >= -74 && E <= 127) {
-    // hi: sign, exponent and the top 23 of the 52 fraction bits
     const unsigned hb = sign | ((unsigned)(E + 127) << 23) | ((h32 & 0xfffffu) << 3) | (l32 >> 29);
-    // lo: the 29 remaining fraction bits, worth rem * 2^(E - 52)
-    const unsigned rem = l32 & 0x1fffffffu;
-    unsigned lb = sign;
-    if (rem) {
-      const int p = 31 - __clz(rem);  // position of the leading one, 0 .. 28
-      const unsigned m = p >= 23 ? (rem >> (p - 23)) : (rem << (23 - p));
-      lb = sign | ((unsigned)(E - 52 + p + 127) << 23) | (m & 0x7fffffu);
-    }
+    const unsigned rem = l32 & 0x1fffffffu;  // worth rem * 2^(E - 52)
+    const unsigned r = __float_as_uint(__uint2float_rn(rem));
+    const unsigned lb = rem ? (sign | (r + ((unsigned)(E - 52) << 23))) : sign;
     return Df64(__uint_as_float(hb), __uint_as_float(lb));
   }
   if ((b << 1) == 0) return Df64(__uint_as_float(sign), 0.f);

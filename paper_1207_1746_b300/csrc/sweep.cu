@@ -211,9 +211,11 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   }
   const int nz_range = (int)(b.hi[2] - b.lo[2]);
   const int smem_cap = max_smem_per_block();
+  // FP64 grids: the arithmetic is fixed here, with the plan
+  pl->pair = g0.dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_PAIR;
   // inputs read only at the core element go to the two-slot centre ring
-  // (FP32 / BF16 storage; the kernel's operator tables make the same choice)
-  const uint32_t cmask = g0.dtype == GSCL_F64 ? 0u : static_centre_mask(pl->op);
+  // (all but IEEE FP64; the kernel's operator tables make the same choice)
+  const uint32_t cmask = (g0.dtype == GSCL_F64 && !pl->pair) ? 0u : static_centre_mask(pl->op);
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
   const int VY = narrow ? 4 : vy_for(g0.dtype);
@@ -373,7 +375,7 @@ int fp64_arith() {
 
 // Launches (or, with occupancy_only, sizes) the kernel a plan names.
 gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only) {
-  const bool pair = dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_PAIR;
+  const bool pair = dtype == GSCL_F64 && pl.pair;
   if (pl.op != OP_GENERIC) {
     switch (dtype) {
       case GSCL_F64:

@@ -45,6 +45,8 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg);
 
 // Launches (or, with occupancy_only, sizes) the kernel a plan names.
 gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only);
+// Current arithmetic of FP64 grids (GSCL_FP64_IEEE or GSCL_FP64_PAIR); make_plan records it in the plan.
+int fp64_arith();
 
 // Temporal blocking: sweeps fused per pass for a call (1 = none), the pass
 // plan and its launch (tb.cu).

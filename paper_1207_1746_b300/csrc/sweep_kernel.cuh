@@ -388,12 +388,12 @@ struct StaticOp {
   __host__ __device__ static constexpr bool run_first(int i) { return i == 0 || !same_run(i - 1, i); }
   __host__ __device__ static constexpr bool run_last(int i) { return i == Def::NT - 1 || !same_run(i, i + 1); }
 
-  // Centre ring for FP32 / BF16 storage only: FP64 sweeps are bound by the
-  // FP64 pipe, and its extra wait per step costs them more than the shared
-  // memory it frees gains (the host planner makes the same choice).
+  // Centre ring for every storage but IEEE FP64: those sweeps are bound by
+  // the FP64 pipe, and the ring's extra wait per step costs them more than
+  // the shared memory it frees gains (the host planner makes the same choice).
   template <typename T>
   __host__ __device__ static constexpr bool in_centre_ring(int in) {
-    return !IsFp64Storage<T>::value && centre_only<Def>(in);
+    return !std::is_same<T, double>::value && centre_only<Def>(in);
   }
 
   // element (row, lane) of centre-ring input `in` in slot cslot
@@ -903,6 +903,7 @@ struct Plan {
   bool batch = false;         // work-list launch of a batch
   int batch_ctas = 0;         // its grid (fixed when the work-list was built)
   bool narrow = false;        // batches of FP32 / BF16 grids: 64-column tiles, 4 rows per warp
+  bool pair = false;          // FP64 grids in pair arithmetic (fixed when the plan is made)
 };
 
 // Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: two
