@@ -137,3 +137,28 @@ def test_error_after_200_heat_sweeps_reported():
     print(f"heat3d 64^3 f64 pair: |u_200 - oracle|_inf / |oracle|_inf = {err:.3e}; "
           f"max relative residual error = {rerr:.3e}")
     assert err <= 1e-11 and rerr <= 1e-11
+
+
+def test_batch_in_pair_mode_matches_single_grids():
+    """A batch planned in pair mode sweeps each instance exactly like
+    gscl_do_all on that instance alone in pair mode (same kernel
+    arithmetic), and its per-instance L2 norms agree to rounding."""
+    shapes = [(33, 40, 35), (64, 17, 50), (90, 90, 20)]
+    h = (1, 1, 1)
+    op = S.heat7(0.125, with_f=False)
+    insts, hosts = [], []
+    for k, n in enumerate(shapes):
+        u0 = I.random_interior(60 + k, n, h, -1.0, 1.0)
+        hosts.append(u0)
+        insts.append(([B.Grid(n, h).upload(u0)], [B.Grid(n, h).upload(u0)]))
+    batch = B.Batch(op, insts)
+    batch.run(4)  # like gscl_do_all, out[0] names the result after the run
+    res = torch.zeros(len(shapes), dtype=torch.float64, device="cuda")
+    fused = B.Batch(S.heat7_fused(0.125, with_f=False), [([outs[0]], [ins[0]]) for ins, outs in insts])
+    fused.reduce(B.L2, res)
+    for (ins, outs), u0, n, r in zip(insts, hosts, shapes, res.cpu().tolist()):
+        u, v = B.Grid(n, h).upload(u0), B.Grid(n, h).upload(u0)
+        B.do_all(op, [u], [v], sweeps=4)
+        assert torch.equal(outs[0].download(), v.download())
+        ref = B.do_reduce(B.L2, S.heat7_fused(0.125, with_f=False), [v], [u])
+        assert abs(r - ref) <= 1e-13 * ref
