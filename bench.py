@@ -645,7 +645,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gscl", choices=["gscl", "reference"])
-    ap.add_argument("--n", type=int, default=N_SIDE)
+    ap.add_argument("--n", "--side", dest="n", type=int, default=N_SIDE,
+                    help="grid side of the heat workload (--side also works under torchrun)")
     ap.add_argument("--sweeps", type=int, default=SWEEPS)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
