@@ -462,11 +462,12 @@ def run_climate(dtype, steps, warmup, sweeps=50):
 
 
 # ------------------------------------------------------------------ ordered workload
-def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10):
+def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10, interpreted=False):
     """Ordered iteration space (do_k_inc): bidiagonal forward substitution
     x(k) = g(k) - m(k) x(k-1) down every (i, j) column of a 256 x 256 x 80
     grid (g uniform [-1, 1), m uniform [-0.9, 0.9], seeds 606 / 607), `reps`
-    solves per step.  Algorithmic bytes per point: g and m read, x written."""
+    solves per step.  Algorithmic bytes per point: g and m read, x written.
+    `interpreted`: the runtime term loop instead of the compiled recurrence."""
     import torch
 
     from paper_1207_1746_b300 import binding as B
@@ -479,6 +480,12 @@ def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10):
     terms = [(0, 0, 0, 1, B.NONE, 0, 1.0), (0, 0, -1, 0, 2, 0, -1.0)]
     op = B.Stencil(terms)
     stream = torch.cuda.current_stream()
+    saved = os.environ.get("GSCL_GENERIC_ONLY")
+    if interpreted:
+        os.environ["GSCL_GENERIC_ONLY"] = "1"
+    else:
+        os.environ.pop("GSCL_GENERIC_ONLY", None)
+    path = B.ordered_specialization(B.K_INC, op, [x, g, m], [x])
 
     def step():
         for _ in range(reps):
@@ -494,9 +501,13 @@ def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10):
     e1.record(stream)
     torch.cuda.synchronize()
     B.sync()
+    if saved is None:
+        os.environ.pop("GSCL_GENERIC_ONLY", None)
+    else:
+        os.environ["GSCL_GENERIC_ONLY"] = saved
     ms = e0.elapsed_time(e1) / steps
     pts = n[0] * n[1] * n[2]
-    return {"points": pts, "ms_per_step": ms, "solve_ms": ms / reps, "reps": reps}
+    return {"points": pts, "ms_per_step": ms, "solve_ms": ms / reps, "reps": reps, "path": path}
 
 
 # ------------------------------------------------------------------ serving workload
@@ -783,15 +794,26 @@ def main():
     if args.workload == "ordered":
         peak_hbm = peaks.get("hbm_gbs", 6400.0)
         out = {}
-        for dt in ("f64", "f32"):
-            r = run_ordered(dt, args.steps, args.warmup)
+        runs = [("f64", False), ("f32", False)] + ([] if args.profile else [("f64", True), ("f32", True)])
+        for dt, interp in runs:
+            r = run_ordered(dt, args.steps, args.warmup, interpreted=interp)
             t = dist.max(r["ms_per_step"])
             bpp = {"f64": 24, "f32": 12}[dt]
             gbs = bpp * r["points"] / (r["solve_ms"] * 1e-3) / 1e9
-            out[dt] = {"value": round(dist.world * r["reps"] * r["points"] / (t * 1e-3) / 1e9, 3),
-                       "ms_per_step": round(t, 3), "solve_ms": round(r["solve_ms"], 4),
-                       "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm, "unit": "GB/s",
-                                    "frac": round(gbs / peak_hbm, 4), "traffic": None, "peak_source": "measured"}}
+            out[dt + ("_interpreted" if interp else "")] = {
+                "value": round(dist.world * r["reps"] * r["points"] / (t * 1e-3) / 1e9, 3),
+                "ms_per_step": round(t, 3), "solve_ms": round(r["solve_ms"], 4), "path": r["path"],
+                "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm, "unit": "GB/s",
+                             "frac": round(gbs / peak_hbm, 4), "traffic": None, "peak_source": "measured"}}
+        # FP64: three FP64-pipe instructions per point (DFMA a g, DMUL m x(k-1),
+        # DFMA of the sum), each taking the pipe as long as one DFMA
+        fma = B_fma() if not args.profile else None
+        if fma:
+            f64 = out["f64"]
+            g_ops = 3 * r["points"] / (f64["solve_ms"] * 1e-3) / 1e9
+            peak_ops = fma * 1e3 / 2          # measured FMA rate in G DFMA/s
+            f64["fp64_pipe"] = {"achieved_g_ops": round(g_ops, 1), "peak_g_dfma_measured": round(peak_ops, 1),
+                                "frac": round(g_ops / peak_ops, 4)}
         line = {"metric": "GPoint-updates/s", "value": out["f64"]["value"], "unit": "GPoint-updates/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": out["f64"]["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -800,7 +822,9 @@ def main():
                                        "down every column of 256x256x80, 10 solves per step",
                            "l2": "working set 3 grids > L2 in FP64"},
                 "roofline": out["f64"]["roofline"], "kernel_ms": out["f64"]["solve_ms"],
-                "variants": {"f32": {"dtype": "f32", **out["f32"]}}, "gpu_launches": args.steps * 10}
+                "fp64_pipe": out["f64"].get("fp64_pipe"), "path": out["f64"]["path"],
+                "variants": {k: {"dtype": k.split("_")[0], **v} for k, v in out.items() if k != "f64"},
+                "gpu_launches": args.steps * 10}
         if dist.rank == 0:
             print(json.dumps(line))
         return

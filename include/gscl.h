@@ -287,6 +287,27 @@ gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_gr
                             const gscl_grid *out, int32_t n_out, const gscl_range *range, void *stream);
 
 /*
+ * Which implementation gscl_do_ordered picks for this call (the interior as
+ * range), in *shape: a non-negative id for a recurrence compiled for its
+ * structure, -1 for the interpreted term loop with look-ahead loads, -2 for
+ * the interpreted loop with loads per term (more than 8 distinct loads per
+ * element, or BF16 storage).  The compiled structures, with the terms in
+ * this order and the weights a, b, c any values:
+ *   0  x = a x(prev) + b f                   (running sums)
+ *   1  x = b f + a x(prev)
+ *   2  x = a g + b m x(prev)                 (bidiagonal substitution)
+ *   3  x = b m x(prev) + a g
+ *   4  x = a f + b g + c x(prev)
+ * where x(prev) is the output read at the element just visited and f, g, m
+ * are grids read at any offsets.  Every path computes the same operations in
+ * the same order, so their results are bit-identical.  Host-only; arguments
+ * and errors as gscl_do_ordered; GSCL_GENERIC_ONLY=1 in the environment
+ * turns the compiled structures off.
+ */
+gscl_status gscl_ordered_specialization(int32_t order, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                                        const gscl_grid *out, int32_t n_out, int32_t *shape);
+
+/*
  * Arithmetic of FP64 grids (not an operation of the paper; a B300 precision
  * mode).  GSCL_FP64_IEEE (default): IEEE FP64 fused multiply-adds, bound on
  * B300 by its FP64 pipe (about 1.7 per clock per SM).  GSCL_FP64_PAIR: each

@@ -100,6 +100,7 @@ def lib():
         "gscl_tune_sweeps": [P(StencilC), P(u64), i32, P(u64), i32, i32, vp, P(i32)],
         "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
         "gscl_do_ordered": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
+        "gscl_ordered_specialization": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(i32)],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
         "gscl_set_fp64_arithmetic": [i32],
         "gscl_get_fp64_arithmetic": [],
@@ -325,6 +326,17 @@ def do_ordered(order, op, ins, outs, rng=None, stream=None):
     st = as_stencil(op)
     check(lib().gscl_do_ordered(int(order), ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
                                 _range(rng), stream_ptr(stream)))
+
+
+def ordered_specialization(order, op, ins, outs):
+    """gscl_ordered_specialization: the compiled recurrence id (>= 0) that
+    do_ordered uses for this call, -1 for the interpreted loop with look-ahead
+    loads, -2 for the interpreted loop with loads per term."""
+    st = as_stencil(op)
+    shape = ctypes.c_int32()
+    check(lib().gscl_ordered_specialization(int(order), ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs),
+                                            len(outs), ctypes.byref(shape)))
+    return shape.value
 
 
 def do_reduce_within(eps, op, ins, outs=(), rng=None, result=None, stream=None):

@@ -18,6 +18,14 @@
 // slots can be indexed at run time.  FP32 / FP64 storage (cp.async moves 4 or
 // 8 bytes); BF16 takes the simple path.  The ordered axis must
 // be y or z: columns along x would put a warp's accesses a whole row apart.
+//
+// The common recurrences (running sums, first-order recurrences, bidiagonal
+// substitution) are also compiled: their shape (which load, output or value
+// each term reads, and in what order) is a constant, the step loop is
+// unrolled by the look-ahead so the ring is a register array with constant
+// slots, and a step costs its loads, its multiply-adds and its stores.
+// Grids, offsets, direction and weights stay runtime values, and the
+// arithmetic is the interpreted loop's, operation for operation.
 #include "sweep_host.h"
 #include "sweep_kernel.cuh"
 
@@ -231,11 +239,211 @@ __global__ void __launch_bounds__(kOrdThreads) ordered_kernel(const __grid_const
   }
 }
 
+// ------------------------------------------------------------ compiled shapes
+// A term of a compiled shape: where its input value comes from (xs: a load
+// slot 0..kLoads-1, kSrcValue for the operator's value, kSrcPrev + m for
+// output m at the element just visited), its coefficient slot (cs, -1: none)
+// and where it adds (out, -1: the value).  Slots are numbered in the order
+// the terms first use them, as the host numbers the loads.
+constexpr int kSrcValue = -1;
+constexpr int kSrcPrev = 16;
+struct OrdShapeTerm {
+  int xs, cs, out;
+};
+template <int N>
+struct OrdShapeTable {
+  OrdShapeTerm t[N];
+};
+
+enum OrdShapeId { ORD_INTERPRETED = -1, ORD_SIMPLE = -2, ORD_RUNSUM_PREV_FIRST = 0, ORD_RUNSUM, ORD_BIDIAG,
+                  ORD_BIDIAG_PREV_FIRST, ORD_AXPY2, ORD_SHAPES };
+
+struct OrdRunSumPrevFirst {  // x = a x(prev) + b f
+  static constexpr int NL = 1, NT = 2, NOUT = 1;
+  static constexpr OrdShapeTable<NT> table = {{{kSrcPrev, -1, 0}, {0, -1, 0}}};
+};
+struct OrdRunSum {  // x = b f + a x(prev)
+  static constexpr int NL = 1, NT = 2, NOUT = 1;
+  static constexpr OrdShapeTable<NT> table = {{{0, -1, 0}, {kSrcPrev, -1, 0}}};
+};
+struct OrdBidiag {  // x = a g + b m x(prev): forward / backward substitution
+  static constexpr int NL = 2, NT = 2, NOUT = 1;
+  static constexpr OrdShapeTable<NT> table = {{{0, -1, 0}, {kSrcPrev, 1, 0}}};
+};
+struct OrdBidiagPrevFirst {  // x = b m x(prev) + a g
+  static constexpr int NL = 2, NT = 2, NOUT = 1;
+  static constexpr OrdShapeTable<NT> table = {{{kSrcPrev, 0, 0}, {1, -1, 0}}};
+};
+struct OrdAxpy2 {  // x = a f + b g + c x(prev): upwind integration with two sources
+  static constexpr int NL = 2, NT = 3, NOUT = 1;
+  static constexpr OrdShapeTable<NT> table = {{{0, -1, 0}, {1, -1, 0}, {kSrcPrev, -1, 0}}};
+};
+
+template <class S>
+GSCL_HD constexpr bool shape_reads_prev(int m) {
+  for (int t = 0; t < S::NT; ++t)
+    if (S::table.t[t].xs == kSrcPrev + m) return true;
+  return false;
+}
+
+// One thread per column as above; the step loop is unrolled by AHEAD so that
+// ring slot j (registers) always holds the loads of steps = j mod AHEAD.  At
+// each step the loads of the element AHEAD steps on are issued after this
+// element's stores (that element is written only at its own step).
+template <typename T, int AXIS, bool INC, class S, int AHEAD>
+__global__ void __launch_bounds__(kOrdThreads) ordered_compiled_kernel(const __grid_constant__ OrdParams P) {
+  using A = typename Arith<T>::A;
+  constexpr int NL = S::NL, NT = S::NT, NO = S::NOUT;
+  constexpr int OTHER = AXIS == 2 ? 1 : 2;
+  const int64_t nx = P.hi[0] - P.lo[0], no = P.hi[OTHER] - P.lo[OTHER];
+  const int64_t col = (int64_t)blockIdx.x * kOrdThreads + threadIdx.x;
+  if (col >= nx * no) return;
+  const int64_t x0 = P.lo[0] + col % nx, y0 = P.lo[OTHER] + col / nx;
+  const int len = (int)(P.hi[AXIS] - P.lo[AXIS]);
+  const T *q[NL];  // the next element each load fetches
+  int64_t qs[NL];
+#pragma unroll
+  for (int l = 0; l < NL; ++l) {
+    const OrdLoad &ld = P.loads[l];
+    q[l] = reinterpret_cast<const T *>(P.in[ld.grid]) + x0 +
+           y0 * (OTHER == 1 ? P.in_pitch[ld.grid] : P.in_plane[ld.grid]) + ld.start;
+    qs[l] = ld.step;
+  }
+  T *d[NO];
+  int64_t ds[NO];
+  A prev[NO];
+#pragma unroll
+  for (int m = 0; m < NO; ++m) {
+    d[m] = reinterpret_cast<T *>(P.out[m]) + x0 + y0 * (OTHER == 1 ? P.out_pitch[m] : P.out_plane[m]) +
+           P.out_start[m];
+    ds[m] = P.out_step[m];
+    prev[m] = A(0);
+  }
+  static_for<NO>([&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    if constexpr (shape_reads_prev<S>(m)) prev[m] = to_arith(d[m][-ds[m]]);
+  });
+  T r[AHEAD][NL];
+#pragma unroll
+  for (int j = 0; j < AHEAD; ++j) {
+    if (j < len) {
+#pragma unroll
+      for (int l = 0; l < NL; ++l) r[j][l] = q[l][j * qs[l]];
+    }
+  }
+#pragma unroll
+  for (int l = 0; l < NL; ++l) q[l] += AHEAD * qs[l];
+  auto element = [&](const T (&rj)[NL]) {
+    A v = A(0);
+    A o[NO];
+#pragma unroll
+    for (int m = 0; m < NO; ++m) o[m] = A(0);
+    static_for<NT>([&](auto tc) {
+      constexpr int t = decltype(tc)::value;
+      constexpr OrdShapeTerm st = S::table.t[t];
+      A x;
+      if constexpr (st.xs == kSrcValue) x = v;
+      else if constexpr (st.xs >= kSrcPrev) x = prev[st.xs - kSrcPrev];
+      else x = to_arith(rj[st.xs]);
+      if constexpr (st.cs >= 0) x = x * to_arith(rj[st.cs]);
+      const A w = ord_weight(P.terms[t], A(0));
+      if constexpr (st.out < 0) v = fma(w, x, v);
+      else o[st.out] = fma(w, x, o[st.out]);
+    });
+#pragma unroll
+    for (int m = 0; m < NO; ++m) {
+      const T y = from_arith<T>(o[m]);
+      *d[m] = y;
+      d[m] += ds[m];
+      prev[m] = to_arith(y);
+    }
+  };
+  int s0 = 0;
+  for (; s0 + AHEAD <= len; s0 += AHEAD) {
+    static_for<AHEAD>([&](auto jc) {
+      constexpr int j = decltype(jc)::value;
+      element(r[j]);
+      if (s0 + j + AHEAD < len) {
+#pragma unroll
+        for (int l = 0; l < NL; ++l) r[j][l] = *q[l];
+      }
+#pragma unroll
+      for (int l = 0; l < NL; ++l) q[l] += qs[l];
+    });
+  }
+  // the last len mod AHEAD steps: their loads are in slots 0.. already
+  static_for<AHEAD>([&](auto jc) {
+    constexpr int j = decltype(jc)::value;
+    if (s0 + j < len) element(r[j]);
+  });
+}
+
+struct OrdShapeDesc {
+  int id, nl, nt, nout;
+  const OrdShapeTerm *t;
+};
+
+template <class S>
+OrdShapeDesc shape_desc(int id) {
+  return OrdShapeDesc{id, S::NL, S::NT, S::NOUT, S::table.t};
+}
+
+const std::vector<OrdShapeDesc> &ord_shapes() {
+  static const std::vector<OrdShapeDesc> v = {
+      shape_desc<OrdRunSumPrevFirst>(ORD_RUNSUM_PREV_FIRST), shape_desc<OrdRunSum>(ORD_RUNSUM),
+      shape_desc<OrdBidiag>(ORD_BIDIAG), shape_desc<OrdBidiagPrevFirst>(ORD_BIDIAG_PREV_FIRST),
+      shape_desc<OrdAxpy2>(ORD_AXPY2)};
+  return v;
+}
+
+// The compiled shape the prepared parameters have, else ORD_INTERPRETED
+// (pipelined term loop) or ORD_SIMPLE (per-term loads).
+int ordered_shape(const OrdParams &P, gscl_dtype dt) {
+  const bool ring_dtype = dt == GSCL_F32 || dt == GSCL_F64;
+  if (P.n_loads > kLoads) return ORD_SIMPLE;
+  const char *env = getenv("GSCL_GENERIC_ONLY");
+  const bool generic = env && env[0] && env[0] != '0';
+  if (!generic) {
+    for (const OrdShapeDesc &d : ord_shapes()) {
+      if (d.nl != P.n_loads || d.nt != P.n_terms || d.nout != P.n_out) continue;
+      bool ok = true;
+      for (int t = 0; t < d.nt && ok; ++t) {
+        const OrdTerm &tm = P.terms[t];
+        const int xs = tm.prev >= 0 ? kSrcPrev + tm.prev : tm.in < 0 ? kSrcValue : tm.xslot;
+        ok = xs == d.t[t].xs && tm.cslot == d.t[t].cs && tm.out == d.t[t].out;
+      }
+      if (ok) return d.id;
+    }
+  }
+  return ring_dtype ? ORD_INTERPRETED : ORD_SIMPLE;
+}
+
+template <typename T, int AXIS, bool INC, class S>
+gscl_status launch_compiled(const OrdParams &P, long long cols, cudaStream_t st) {
+  const unsigned blocks = (unsigned)((cols + kOrdThreads - 1) / kOrdThreads);
+  ordered_compiled_kernel<T, AXIS, INC, S, kAheadFew><<<blocks, kOrdThreads, 0, st>>>(P);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
+}
+
 template <typename T, int AXIS, bool INC>
-gscl_status launch_ordered_dir(const OrdParams &P, long long cols, cudaStream_t st) {
+gscl_status launch_shape(const OrdParams &P, int shape, long long cols, cudaStream_t st) {
+  switch (shape) {
+    case ORD_RUNSUM_PREV_FIRST: return launch_compiled<T, AXIS, INC, OrdRunSumPrevFirst>(P, cols, st);
+    case ORD_RUNSUM: return launch_compiled<T, AXIS, INC, OrdRunSum>(P, cols, st);
+    case ORD_BIDIAG: return launch_compiled<T, AXIS, INC, OrdBidiag>(P, cols, st);
+    case ORD_BIDIAG_PREV_FIRST: return launch_compiled<T, AXIS, INC, OrdBidiagPrevFirst>(P, cols, st);
+    case ORD_AXPY2: return launch_compiled<T, AXIS, INC, OrdAxpy2>(P, cols, st);
+  }
+  return fail(GSCL_ERR_INVALID, "unknown ordered shape %d", shape);
+}
+
+template <typename T, int AXIS, bool INC>
+gscl_status launch_ordered_dir(const OrdParams &P, int shape, long long cols, cudaStream_t st) {
+  if (shape >= 0) return launch_shape<T, AXIS, INC>(P, shape, cols, st);
   const unsigned blocks = (unsigned)((cols + kOrdThreads - 1) / kOrdThreads);
   if constexpr (sizeof(T) >= 4) {
-    if (P.n_loads <= kLoads) {
+    if (shape == ORD_INTERPRETED) {
       const bool few = P.n_loads <= kFewLoads;
       const size_t smem = (size_t)(few ? kAheadFew : kAheadMany) * P.n_loads * kOrdThreads * sizeof(T);
       if (few) ordered_kernel<T, AXIS, INC, kAheadFew><<<blocks, kOrdThreads, smem, st>>>(P);
@@ -250,18 +458,33 @@ gscl_status launch_ordered_dir(const OrdParams &P, long long cols, cudaStream_t 
 }
 
 template <typename T>
-gscl_status launch_ordered_t(const OrdParams &P, int axis, bool inc, long long cols, cudaStream_t st) {
-  if (axis == 2) return inc ? launch_ordered_dir<T, 2, true>(P, cols, st) : launch_ordered_dir<T, 2, false>(P, cols, st);
-  return inc ? launch_ordered_dir<T, 1, true>(P, cols, st) : launch_ordered_dir<T, 1, false>(P, cols, st);
+gscl_status launch_ordered_t(const OrdParams &P, int shape, int axis, bool inc, long long cols, cudaStream_t st) {
+  if (axis == 2)
+    return inc ? launch_ordered_dir<T, 2, true>(P, shape, cols, st) : launch_ordered_dir<T, 2, false>(P, shape, cols, st);
+  return inc ? launch_ordered_dir<T, 1, true>(P, shape, cols, st) : launch_ordered_dir<T, 1, false>(P, shape, cols, st);
 }
+
+// Binds the call and fills the kernel parameters (shared by gscl_do_ordered
+// and gscl_ordered_specialization).
+struct OrdCall {
+  OrdParams P;
+  int axis;
+  bool inc, empty;
+  long long cols;
+  gscl_dtype dtype;
+};
+
 
 }  // namespace
 }  // namespace gscl
 
 using namespace gscl;
 
-extern "C" gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
-                                       const gscl_grid *out, int32_t n_out, const gscl_range *range, void *stream) {
+namespace gscl {
+namespace {
+
+gscl_status prepare_ordered(int32_t order, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                            const gscl_grid *out, int32_t n_out, const gscl_range *range, OrdCall *c) {
   if (order < GSCL_I_INC || order > GSCL_K_DEC) return fail(GSCL_ERR_INVALID, "unknown order %d", order);
   const int axis = order / 2;
   const bool inc = order % 2 == 0;
@@ -271,9 +494,13 @@ extern "C" gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, co
   if (n_out < 1) return fail(GSCL_ERR_INVALID, "do_ordered needs an output");
   Bound b;
   if (gscl_status s = bind(op, false, in, n_in, out, n_out, range, &b, axis, inc ? -1 : 1)) return s;
+  memset(c, 0, sizeof *c);
+  c->axis = axis;
+  c->inc = inc;
+  c->empty = b.empty;
+  c->dtype = (gscl_dtype)b.in[0].dtype;
   if (b.empty) return GSCL_OK;
-  OrdParams P;
-  memset(&P, 0, sizeof P);
+  OrdParams &P = c->P;
   int alias[kMaxIn];
   for (int a = 0; a < n_in; ++a) {
     const Grid &g = b.in[a];
@@ -351,12 +578,34 @@ extern "C" gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, co
     P.hi[a] = b.hi[a];
   }
   const int other = axis == 2 ? 1 : 2;
-  const long long cols = (long long)(b.hi[0] - b.lo[0]) * (b.hi[other] - b.lo[other]);
+  c->cols = (long long)(b.hi[0] - b.lo[0]) * (b.hi[other] - b.lo[other]);
+  return GSCL_OK;
+}
+
+}  // namespace
+}  // namespace gscl
+
+extern "C" gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_grid *in, int32_t n_in,
+                                       const gscl_grid *out, int32_t n_out, const gscl_range *range, void *stream) {
+  OrdCall c;
+  if (gscl_status s = prepare_ordered(order, op, in, n_in, out, n_out, range, &c)) return s;
+  if (c.empty) return GSCL_OK;
+  const int shape = ordered_shape(c.P, c.dtype);
   cudaStream_t st = (cudaStream_t)stream;
-  switch (b.in[0].dtype) {
-    case GSCL_F64: return launch_ordered_t<double>(P, axis, inc, cols, st);
-    case GSCL_F32: return launch_ordered_t<float>(P, axis, inc, cols, st);
-    case GSCL_BF16: return launch_ordered_t<__nv_bfloat16>(P, axis, inc, cols, st);
+  switch (c.dtype) {
+    case GSCL_F64: return launch_ordered_t<double>(c.P, shape, c.axis, c.inc, c.cols, st);
+    case GSCL_F32: return launch_ordered_t<float>(c.P, shape, c.axis, c.inc, c.cols, st);
+    case GSCL_BF16: return launch_ordered_t<__nv_bfloat16>(c.P, shape, c.axis, c.inc, c.cols, st);
   }
   return fail(GSCL_ERR_DTYPE, "unknown dtype");
+}
+
+extern "C" gscl_status gscl_ordered_specialization(int32_t order, const gscl_stencil *op, const gscl_grid *in,
+                                                   int32_t n_in, const gscl_grid *out, int32_t n_out,
+                                                   int32_t *shape) {
+  if (!shape) return fail(GSCL_ERR_INVALID, "shape is NULL");
+  OrdCall c;
+  if (gscl_status s = prepare_ordered(order, op, in, n_in, out, n_out, nullptr, &c)) return s;
+  *shape = ordered_shape(c.P, c.dtype);
+  return GSCL_OK;
 }

@@ -58,3 +58,26 @@ def assert_within(got, ref, S, tol):
     bound = tol * S[m] + 1e-300
     worst = np.max(err / bound) if err.size else 0.0
     assert np.all(err <= bound), f"max error / bound = {worst}"
+
+
+# Ordered iteration spaces: the predecessor offset of each order, and the
+# recurrences compiled for their structure (gscl_ordered_specialization ids
+# 0..4) with the terms in the order that defines each id.
+ORDER_STEP = {B.J_INC: (0, -1, 0), B.J_DEC: (0, 1, 0), B.K_INC: (0, 0, -1), B.K_DEC: (0, 0, 1)}
+
+
+def ordered_shape_terms(shape, order):
+    """Input 0 is the output x, read at its predecessor; inputs 1, 2 are f, g
+    or g, m."""
+    prev = ORDER_STEP[order]
+    a, b, c = 0.75, -0.5, 0.25
+    if shape == 0:   # x = a x(prev) + b f
+        return [(*prev, 0, B.NONE, 0, a), (0, 0, 0, 1, B.NONE, 0, b)]
+    if shape == 1:   # x = b f + a x(prev), f read at an offset
+        return [(1, 0, -1, 1, B.NONE, 0, b), (*prev, 0, B.NONE, 0, a)]
+    if shape == 2:   # x = a g + b m x(prev)
+        return [(0, 0, 0, 1, B.NONE, 0, a), (*prev, 0, 2, 0, b)]
+    if shape == 3:   # x = b m x(prev) + a g, g read at an offset
+        return [(*prev, 0, 2, 0, b), (-1, 1, 0, 1, B.NONE, 0, a)]
+    # x = a f + b g + c x(prev)
+    return [(0, 0, 0, 1, B.NONE, 0, a), (0, -1, 1, 2, B.NONE, 0, b), (*prev, 0, B.NONE, 0, c)]

@@ -181,3 +181,36 @@ def test_workload_operators_map_to_compiled_structures(monkeypatch):
     assert B.specialization(S.fig1b()[:3] + [(2, 0, 0, 0, B.NONE, 0, 1.0)], 1, 1) == -1
     monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
     assert B.specialization(S.heat7(0.125), 2, 1) == -1
+
+
+def test_ordered_recurrences_map_to_compiled_shapes(monkeypatch):
+    """gscl_ordered_specialization on host-only handles: the five compiled
+    recurrences in every order and storage dtype, the interpreted paths
+    otherwise."""
+    from gpu_common import ordered_shape_terms
+    monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    n, h = (16, 8, 8), (1, 1, 1)
+    for dtype in ("f64", "f32", "bf16"):
+        g = [FakeGrid(n, h, dtype) for _ in range(3)]
+        interp = -2 if dtype == "bf16" else -1
+        for order in (B.J_INC, B.J_DEC, B.K_INC, B.K_DEC):
+            for shape in range(5):
+                ins = g[:3] if shape >= 2 else g[:2]
+                assert B.ordered_specialization(order, ordered_shape_terms(shape, order), ins, g[:1]) == shape
+            # the returned value in the loop, and a second output: interpreted
+            prev = (0, 0, -1) if order == B.K_INC else (0, 0, 1) if order == B.K_DEC else \
+                (0, -1, 0) if order == B.J_INC else (0, 1, 0)
+            via_value = [(*prev, 0, B.NONE, B.VALUE, 1.0), (0, 0, 0, 1, B.NONE, B.VALUE, 1.0),
+                         (0, 0, 0, B.VALUE, B.NONE, 0, 1.0)]
+            assert B.ordered_specialization(order, via_value, g[:2], g[:1]) == interp
+            two_out = ordered_shape_terms(0, order) + [(0, 0, 0, 1, B.NONE, 1, 1.0)]
+            assert B.ordered_specialization(order, two_out, g[:2], [g[0], g[2]]) == interp
+        # more than 8 distinct loads per element: loads per term
+        many = [(dx, dy, 0, 1, B.NONE, 0, 1.0) for dx in (-1, 0, 1) for dy in (-1, 0, 1)]
+        assert B.ordered_specialization(B.K_INC, many, g[:2], g[:1]) == -2
+        monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+        assert B.ordered_specialization(B.K_INC, ordered_shape_terms(2, B.K_INC), g, g[:1]) == interp
+        monkeypatch.delenv("GSCL_GENERIC_ONLY")
+        # alias rules apply as in gscl_do_ordered
+        with pytest.raises(B.GsclError):
+            B.ordered_specialization(B.K_DEC, ordered_shape_terms(0, B.K_INC), g[:2], g[:1])

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_common import as_storage
+from gpu_common import as_storage, ordered_shape_terms
 from oracle import oracle as O
 from paper_1207_1746_b300 import binding as B
 from paper_1207_1746_b300 import inputs as I
@@ -107,3 +107,42 @@ def test_alias_rules_and_unsupported_axis():
     # reading the output at offset 0 (its old value) is allowed
     B.do_ordered(B.K_INC, [(0, 0, 0, 0, NONE, 0, 2.0), (0, 0, 0, 1, NONE, 0, 1.0)], [gx, gf], [gx])
     B.sync()
+
+
+
+@pytest.mark.parametrize("n", [(67, 13, 37), (40, 16, 32), (33, 5, 1)])
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC, B.J_DEC])
+@pytest.mark.parametrize("shape", range(5))
+def test_compiled_recurrence_matches_interpreted_and_oracle(shape, order, dtype, n, monkeypatch):
+    """The compiled recurrences run the interpreted loop's operations in the
+    same order: bit-identical results, on columns shorter than, equal to and
+    longer than the look-ahead (with a ragged tail), and close to the FP64
+    oracle (FP32 / BF16 storage rounds every stored element)."""
+    h = (1, 1, 1)
+    terms = ordered_shape_terms(shape, order)
+    arrays = [I.random_interior(40 + shape, n, h, -1.0, 1.0, halo_value=0.5),
+              I.random_interior(50 + shape, n, h, -1.0, 1.0)]
+    if shape >= 2:
+        arrays.append(I.random_interior(60 + shape, n, h, -0.9, 0.9))
+
+    def run():
+        gg = [B.Grid(n, h, dtype).upload(a) for a in arrays]
+        path = B.ordered_specialization(order, terms, gg, gg[:1])
+        B.do_ordered(order, terms, gg, gg[:1])
+        return path, gg[0].download()
+
+    monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    path, got = run()
+    assert path == shape
+    monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+    path_i, got_i = run()
+    assert path_i == (-2 if dtype == "bf16" else -1)
+    assert torch.equal(got, got_i)
+
+    og = [O.Grid(as_storage(a, dtype), h) for a in arrays]
+    O.do_ordered(order, terms, og, og[:1])
+    want = I.interior_view(og[0].a, n, h)
+    mine = I.interior_view(got.double().numpy(), n, h)
+    tol = {"f64": 1e-13, "f32": 1e-5, "bf16": 5e-2}[dtype]
+    assert np.max(np.abs(mine - want)) <= tol * max(1.0, np.max(np.abs(want)))
