@@ -1,6 +1,7 @@
 /*
  * gscl_oracle.c -- plain FP64 CPU oracle for the two iteration spaces of the
- * generic stencil library: do_all and do_reduce (Section 3).
+ * generic stencil library: do_all and do_reduce, the ordered iteration
+ * spaces and red-black colouring (Section 3).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline / reference leg may load this code.  The CUDA
@@ -210,6 +211,37 @@ int orc_do_ordered(int axis, int inc, const orc_extent *e, int n_in, const orc_g
           out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, p[0], p[1], p[2])] = r[m];
       }
   }
+  return ORC_OK;
+}
+
+/* Coloured (red-black) application, the use Section 3 gives for stateful
+ * stencils (operators that may query the index of the core element): the
+ * operator is applied only at core elements whose index sum i + j + k (a 2D
+ * grid has k = 0) has the parity `color` (0 or 1), in lexicographic order,
+ * reading the grids' current contents.  An output may also be bound as an
+ * input; at each element every output is computed before any is stored.
+ * Elements of the other colour are left as they are.  With the 7-point
+ * Poisson operator in place, colour 0 then colour 1 is one red-black
+ * Gauss-Seidel iteration. */
+int orc_do_colored(int color, const orc_extent *e, int n_in, const orc_grid *in, int n_out,
+                   const orc_out_grid *out, int n_terms, const orc_term *terms, const int64_t lo[3],
+                   const int64_t hi[3]) {
+  if ((color != 0 && color != 1) || n_out < 1 || n_out > 8) return ORC_BAD_ARG;
+  int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
+  if (rc) return rc;
+  double r[8];
+  for (int64_t k = lo[2]; k < hi[2]; ++k)
+    for (int64_t j = lo[1]; j < hi[1]; ++j)
+      for (int64_t i = lo[0]; i < hi[0]; ++i) {
+#if ORC_MUTANT == 9
+        if (((i + j) & 1) != color) continue; /* k left out of the colour */
+#else
+        if (((i + j + k) & 1) != color) continue;
+#endif
+        double v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, 0, i, j, k);
+        for (int m = 0; m < n_out; ++m) r[m] = orc_term_sum(e, in, n_terms, terms, m, v, 0, i, j, k);
+        for (int m = 0; m < n_out; ++m) out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r[m];
+      }
   return ORC_OK;
 }
 

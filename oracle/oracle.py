@@ -93,6 +93,8 @@ def _get_lib():
         lib.orc_do_reduce_within.restype = ctypes.c_int
         lib.orc_do_ordered.argtypes = [ctypes.c_int, ctypes.c_int] + lib.orc_do_reduce.argtypes[1:-1]
         lib.orc_do_ordered.restype = ctypes.c_int
+        lib.orc_do_colored.argtypes = [ctypes.c_int] + lib.orc_do_reduce.argtypes[1:-1]
+        lib.orc_do_colored.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -182,6 +184,18 @@ def do_ordered(order, terms, ins, outs, lo=None, hi=None):
                                    len(outs), gout, len(terms), tt, clo, chi)
     if rc != 0:
         raise ValueError(f"oracle do_ordered rejected the call (code {rc})")
+
+
+def do_colored(color, terms, ins, outs, lo=None, hi=None):
+    """Red-black colouring (Section 3, stateful stencils): the operator at the
+    core elements of ``[lo, hi)`` whose index sum i + j + k has parity
+    ``color``, in lexicographic order; an output passed also as an input (the
+    same Grid) is updated in place."""
+    ext, gin, gout, tt, clo, chi = _marshal(terms, ins, outs, lo, hi, allow_alias=True)
+    rc = _get_lib().orc_do_colored(int(color), ctypes.byref(ext), len(ins), gin, len(outs), gout, len(terms), tt,
+                                   clo, chi)
+    if rc != 0:
+        raise ValueError(f"oracle do_colored rejected the call (code {rc})")
 
 
 def do_reduce_within(eps, terms, ins, outs=(), lo=None, hi=None) -> float:

@@ -21,6 +21,7 @@ MUTANTS = {
     6: "NaN ignored by max-abs",
     7: "the operator's value read as zero by fused terms",
     8: "1-norm instead of 2-norm",
+    9: "red-black colour taken from i + j only",
 }
 
 RUNNER = r"""

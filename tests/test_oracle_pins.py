@@ -485,3 +485,102 @@ def test_ordered_bidiagonal_forward_substitution():
             L = np.eye(n[2]) + np.diag(m[2:-1, j, i], -1)
             want = sla.solve_triangular(L, g[1:-1, j, i], lower=True)
             assert np.allclose(x[1:-1, j, i], want, rtol=1e-13, atol=1e-15)
+
+
+# ------------------------------------------------------------------ red-black colouring
+AXIAL6 = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+
+
+def sor_terms(omega=1.0):
+    """In-place SOR update of the 7-point Poisson equation 6u - sum6 = f:
+    u <- (1 - omega) u + omega (sum6 + f) / 6; omega = 1 is Gauss-Seidel."""
+    t = [(dx, dy, dz, 0, O.NONE, 0, omega / 6.0) for dx, dy, dz in AXIAL6]
+    t.append((0, 0, 0, 1, O.NONE, 0, omega / 6.0))
+    if omega != 1.0:
+        t.append((0, 0, 0, 0, O.NONE, 0, 1.0 - omega))
+    return t
+
+
+def poisson_residual_np(u, f):
+    """f - (6u - sum6 u) on the interior, by array slicing (halo width 1)."""
+    a = u.a
+    lap = (6.0 * a[1:-1, 1:-1, 1:-1] - a[2:, 1:-1, 1:-1] - a[:-2, 1:-1, 1:-1] - a[1:-1, 2:, 1:-1]
+           - a[1:-1, :-2, 1:-1] - a[1:-1, 1:-1, 2:] - a[1:-1, 1:-1, :-2])
+    return f.interior() - lap
+
+
+def colour_of(n):
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    return (i + j + k) % 2
+
+
+def test_redblack_half_sweep_solves_its_colour():
+    """Gauss-Seidel on one colour solves the equation exactly at every element
+    of that colour (its neighbours are all of the other colour and do not
+    change), and leaves the other colour and the halo untouched."""
+    n, h = (7, 6, 5), (1, 1, 1)
+    rng = np.random.default_rng(31)
+    u, f = O.zeros(n, h), O.zeros(n, h)
+    u.a[...] = rng.uniform(-1, 1, u.a.shape)        # the halo holds Dirichlet values
+    f.interior()[...] = rng.uniform(-1, 1, n[::-1])
+    col = colour_of(n)
+    halo0 = u.a.copy()
+    for colour in (0, 1, 0, 1):
+        before = u.interior().copy()
+        O.do_colored(colour, sor_terms(), [u, f], [u])
+        r = poisson_residual_np(u, f)
+        assert np.max(np.abs(r[col == colour])) <= 1e-14 * 16
+        assert np.array_equal(u.interior()[col != colour], before[col != colour])
+        assert np.abs(r[col != colour]).max() > 1e-6    # the other colour is not solved yet
+        inner = np.zeros(u.a.shape, bool)
+        inner[1:-1, 1:-1, 1:-1] = True
+        assert np.array_equal(u.a[~inner], halo0[~inner])
+
+
+def sor_rate(omega, mu):
+    """Spectral radius of SOR for a consistently ordered matrix whose Jacobi
+    iteration has spectral radius mu, for omega up to the optimum (Young):
+    the largest root of (lambda + omega - 1)^2 = lambda omega^2 mu^2."""
+    s = (omega * mu + math.sqrt(omega * omega * mu * mu - 4.0 * (omega - 1.0))) / 2.0
+    return s * s
+
+
+@pytest.mark.parametrize("omega", [1.0, 1.3])
+def test_redblack_sor_asymptotic_rate(omega):
+    """Red-black ordering makes the 7-point matrix consistently ordered, so
+    red-black Gauss-Seidel contracts the error by mu^2 per iteration and SOR
+    by the root above, with mu = cos(pi / (n + 1)) the Jacobi radius of the
+    n^3 Dirichlet problem."""
+    n, h = (8, 8, 8), (1, 1, 1)
+    rng = np.random.default_rng(32)
+    u, f = O.zeros(n, h), O.zeros(n, h)
+    u.interior()[...] = rng.uniform(-1, 1, n)
+    terms = sor_terms(omega)
+    norms = []
+    for _ in range(160):
+        O.do_colored(0, terms, [u, f], [u])
+        O.do_colored(1, terms, [u, f], [u])
+        norms.append(np.linalg.norm(u.interior()))
+    rate = norms[-1] / norms[-2]
+    want = sor_rate(omega, math.cos(math.pi / 9))
+    assert abs(rate - want) <= 2e-4 * want, (rate, want)
+
+
+def test_redblack_gauss_seidel_converges_to_direct_solve():
+    n = 6
+    rng = np.random.default_rng(33)
+    u, f = O.zeros((n, n, n), (1, 1, 1)), O.zeros((n, n, n), (1, 1, 1))
+    f.interior()[...] = rng.uniform(-1, 1, (n, n, n))
+    for _ in range(200):
+        O.do_colored(0, sor_terms(), [u, f], [u])
+        O.do_colored(1, sor_terms(), [u, f], [u])
+    exact = spla.spsolve(poisson_matrix(n), f.interior().ravel())
+    assert np.max(np.abs(u.interior().ravel() - exact)) <= 1e-11 * np.max(np.abs(exact))
+
+
+def test_colored_rejects_bad_colour_and_ranges():
+    u, f = O.zeros((4, 4, 4), (1, 1, 1)), O.zeros((4, 4, 4), (1, 1, 1))
+    with pytest.raises(ValueError):
+        O.do_colored(2, sor_terms(), [u, f], [u])
+    with pytest.raises(ValueError):
+        O.do_colored(0, [(2, 0, 0, 0, O.NONE, 0, 1.0)], [u, f], [u])
