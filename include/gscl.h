@@ -208,6 +208,29 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
                         int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream);
 
 /*
+ * Red-black colouring, the use Section 3 gives for stateful stencils
+ * (operators that may query the index of their core element): applies the
+ * operator only at the core elements of `range` whose interior index sum
+ * i + j + k (k = 0 on 2D grids) has the parity `color` (0 or 1); elements of
+ * the other colour are not written.  half_sweeps >= 1 applications alternate
+ * the colour, starting with `color`, each reading the previous one's result.
+ *
+ *  - An output may also be an input when both name the same grid (the same
+ *    storage and layout; GSCL_ERR_ALIAS otherwise), read at offset 0 or at
+ *    offsets with odd dx + dy + dz: elements of the other colour, which the
+ *    call does not write, so the update is well defined in place.  Any other
+ *    read of it is GSCL_ERR_ALIAS.
+ *  - With the 7-point Poisson operator u <- (sum6 u + f) / 6 in place, colour
+ *    0 then colour 1 is one red-black Gauss-Seidel iteration; the weights
+ *    (1 - w) on u(0) and w / 6 on the others give SOR with factor w.
+ *  - Other rules as gscl_do_all (n_out >= 1, GSCL_ERR_INVALID for a colour
+ *    outside {0, 1} or half_sweeps < 1).  Asynchronous on `stream`.
+ */
+gscl_status gscl_do_colored(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                            int32_t n_out, const gscl_range *range, int32_t color, int32_t half_sweeps,
+                            void *stream);
+
+/*
  * Which implementation gscl_do_all / gscl_do_reduce pick for this operator
  * with n_in inputs and n_out outputs.  Section 1 of the paper keeps a generic
  * implementation of every construct and uses a better-suited one where it

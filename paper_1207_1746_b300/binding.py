@@ -101,6 +101,7 @@ def lib():
         "gscl_fma_throughput": [i32, i32, P(ctypes.c_double), vp],
         "gscl_do_ordered": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
         "gscl_ordered_specialization": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(i32)],
+        "gscl_do_colored": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), i32, i32, vp],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
         "gscl_set_fp64_arithmetic": [i32],
         "gscl_get_fp64_arithmetic": [],
@@ -326,6 +327,16 @@ def do_ordered(order, op, ins, outs, rng=None, stream=None):
     st = as_stencil(op)
     check(lib().gscl_do_ordered(int(order), ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
                                 _range(rng), stream_ptr(stream)))
+
+
+def do_colored(op, ins, outs, color=0, half_sweeps=1, rng=None, stream=None):
+    """gscl_do_colored: the operator at the elements whose index sum i + j + k
+    has parity ``color`` (Section 3, red-black colouring), ``half_sweeps``
+    times with alternating colour.  In place (an output also passed as an
+    input) when it reads that grid only at offset 0 or at odd offsets."""
+    st = as_stencil(op)
+    check(lib().gscl_do_colored(ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
+                                _range(rng), int(color), int(half_sweeps), stream_ptr(stream)))
 
 
 def ordered_specialization(order, op, ins, outs):

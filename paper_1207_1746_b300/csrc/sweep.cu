@@ -18,7 +18,8 @@ bool overlaps(const Grid &a, const Grid &b) { return a.buf < b.buf + b.bytes && 
 
 // Validates handles, shapes, dtypes, the range, every term and aliasing.
 gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
-                 int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis, int ordered_step) {
+                 int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis, int ordered_step,
+                 bool colored) {
   if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
   if (n_out < 0 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut_);
   if (!in || (n_out > 0 && !out)) return fail(GSCL_ERR_INVALID, "grid arrays are required");
@@ -94,12 +95,15 @@ gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, i
   }
   if (need_value && !has_value) return fail(GSCL_ERR_INVALID, "do_reduce needs a term with out == GSCL_VALUE");
   // an output may also be an input only if every read of it is at offset 0
-  // (ordered iteration spaces: or at the element visited just before)
+  // (ordered iteration spaces: or at the element visited just before;
+  // red-black colouring: or at an offset with odd dx + dy + dz, an element of
+  // the other colour, which the call does not write)
   for (int m = 0; m < n_out; ++m)
     for (int a = 0; a < n_in; ++a) {
       if (!overlaps(b->out[m], b->in[a])) continue;
       const Grid &go = b->out[m], &gi = b->in[a];
-      if (ordered_axis >= 0 && (go.buf != gi.buf || go.off != gi.off || go.pitch != gi.pitch || go.plane != gi.plane))
+      if ((ordered_axis >= 0 || colored) &&
+          (go.buf != gi.buf || go.off != gi.off || go.pitch != gi.pitch || go.plane != gi.plane))
         return fail(GSCL_ERR_ALIAS, "output %d overlaps input %d without being the same grid", m, a);
       for (int t = 0; t < op->n_terms; ++t) {
         const gscl_term &tm = op->terms[t];
@@ -107,7 +111,8 @@ gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, i
         const int d[3] = {tm.dx, tm.dy, tm.dz};
         const bool previous = ordered_axis >= 0 && d[ordered_axis] == ordered_step &&
                               d[(ordered_axis + 1) % 3] == 0 && d[(ordered_axis + 2) % 3] == 0;
-        if (!previous)
+        const bool other_colour = colored && ((d[0] + d[1] + d[2]) & 1);
+        if (!previous && !other_colour)
           return fail(GSCL_ERR_ALIAS, "output %d is input %d, read at a non-zero offset by term %d", m, a, t);
       }
     }
@@ -179,6 +184,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   SweepParams &P = pl->P;
   memset(&P, 0, sizeof P);
   P.within = -1.0;  // MAXABS reports the maximum (gscl_do_reduce_within sets a tolerance)
+  P.color = -1;     // every element (gscl_do_colored sets a colour)
   const Grid &g0 = b.in[0];
   const int n_in = (int)b.in.size(), n_out = (int)b.out.size();
   const int elem = g0.elem;
@@ -461,6 +467,24 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
   // an even number of launches leaves the result in in[0]'s storage: exchange
   // the handles so out[0] names it
   if (launches > 1 && launches % 2 == 0) return swap_storage(in[0], out[0]);
+  return GSCL_OK;
+}
+
+gscl_status gscl_do_colored(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                            int32_t n_out, const gscl_range *range, int32_t color, int32_t half_sweeps,
+                            void *stream) {
+  if (color != 0 && color != 1) return fail(GSCL_ERR_INVALID, "color must be 0 or 1, got %d", color);
+  if (half_sweeps < 1) return fail(GSCL_ERR_INVALID, "half_sweeps must be >= 1");
+  if (n_out < 1) return fail(GSCL_ERR_INVALID, "do_colored needs at least one output");
+  Bound b;
+  if (gscl_status s = bind(op, false, in, n_in, out, n_out, range, &b, -1, 0, true)) return s;
+  if (b.empty) return GSCL_OK;
+  Plan pl;
+  if (gscl_status s = make_plan(b, false, &pl, TileCfg{})) return s;
+  for (int h = 0; h < half_sweeps; ++h) {
+    pl.P.color = (color + h) & 1;
+    if (gscl_status s = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream, nullptr)) return s;
+  }
   return GSCL_OK;
 }
 

@@ -35,7 +35,8 @@ bool overlaps(const Grid &a, const Grid &b);
 // input must be the same grid, read only at offset 0 or one step of
 // ordered_step along ordered_axis (the element visited just before).
 gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
-                 int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis = -1, int ordered_step = 0);
+                 int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis = -1, int ordered_step = 0,
+                 bool colored = false);
 
 // Compile-time operator with the descriptor's structure, or OP_GENERIC.
 int match_static(const std::vector<gscl_term> &terms, int n_in, int n_out, std::vector<int> *perm);

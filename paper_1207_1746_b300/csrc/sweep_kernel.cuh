@@ -100,6 +100,7 @@ struct SweepParams {
   unsigned char *workspace;  // single reduce: ticket at +0, partials at +256
   double *result;            // single reduce: where the last CTA writes the value
   double within;             // >= 0: MAXABS reports 1 if max |value| <= within, else 0
+  int32_t color;             // 0 / 1: outputs written only where (i + j + k) % 2 == color; -1: everywhere
   int *err;                  // device error word
 };
 
@@ -761,7 +762,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
             for (int m = 0; m < NO; ++m) o[m][e] = A(0);
           }
           Op::template eval_row<T, VX, VY, r>(P, ring, smod, cslot, wy * VY, lane, zq, v, o);
-          if (yok[r]) {
+          // red-black colouring: a thread's columns x0 + lane + 32 e share one parity
+          if (yok[r] && (P.color < 0 || (int)((x0 + lane + y[r] + z) & 1) == P.color)) {
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
               if (m < Op::n_out(P)) {

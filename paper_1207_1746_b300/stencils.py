@@ -53,6 +53,16 @@ def poisson_jacobi():
     return [(dx, dy, dz, 0, NONE, 0, 1.0 / 6.0) for dx, dy, dz in X6] + [(0, 0, 0, 1, NONE, 0, 1.0 / 6.0)]
 
 
+def poisson_sor(omega):
+    """SOR update of the Poisson equation 6u - sum6 = f in place, for red-black
+    colouring: u' = (1 - omega) u + omega (sum6 + f) / 6 (inputs 0 = u,
+    1 = f); omega = 1 is Gauss-Seidel, the Jacobi operator applied per colour."""
+    if omega == 1.0:
+        return poisson_jacobi()
+    return ([(0, 0, 0, 0, NONE, 0, 1.0 - omega)] + [(dx, dy, dz, 0, NONE, 0, omega / 6.0) for dx, dy, dz in X6]
+            + [(0, 0, 0, 1, NONE, 0, omega / 6.0)])
+
+
 def fig1b():
     """The operator printed in Fig. 1b: v = (6 u - sum6) / 36."""
     return [(0, 0, 0, 0, NONE, 0, 6.0 / 36.0)] + [(dx, dy, dz, 0, NONE, 0, -1.0 / 36.0) for dx, dy, dz in X6]

@@ -214,3 +214,25 @@ def test_ordered_recurrences_map_to_compiled_shapes(monkeypatch):
         # alias rules apply as in gscl_do_ordered
         with pytest.raises(B.GsclError):
             B.ordered_specialization(B.K_DEC, ordered_shape_terms(0, B.K_INC), g[:2], g[:1])
+
+
+def colored_status(terms, ins, outs, color=0, half_sweeps=1):
+    st = B.Stencil(terms)
+    return B.lib().gscl_do_colored(ctypes.byref(st.c), B._handles(ins), len(ins), B._handles(outs), len(outs), None,
+                                   color, half_sweeps, None)
+
+
+def test_colored_validation_errors():
+    """Red-black colouring: in place only through the same grid, and then
+    read only at offset 0 or at odd offsets (the other colour)."""
+    u, f = FakeGrid((16, 8, 8), (1, 1, 1)), FakeGrid((16, 8, 8), (1, 1, 1))
+    gs = [(dx, dy, dz, 0, B.NONE, 0, 1.0 / 6) for dx, dy, dz in
+          ((1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))] + [(0, 0, 0, 1, B.NONE, 0, 1.0 / 6)]
+    assert colored_status([(1, 1, 0, 0, B.NONE, 0, 1.0)], [u], [u]) == 3     # same colour
+    assert colored_status([(2, 0, 0, 0, B.NONE, 0, 1.0)], [u], [u]) == 2     # beyond the halo
+    assert colored_status(gs, [u, f], [u], color=2) == 1
+    assert colored_status(gs, [u, f], [u], color=-1) == 1
+    assert colored_status(gs, [u, f], [u], half_sweeps=0) == 1
+    assert colored_status(gs, [u, f], []) == 1
+    # ordinary do_all still refuses the in-place Gauss-Seidel operator
+    assert do_all_status(gs, [u, f], [u]) == 3

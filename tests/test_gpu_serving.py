@@ -29,7 +29,7 @@ def poisson_matrix(n):
     return (sp.kron(sp.kron(Id, Id), T) + sp.kron(sp.kron(Id, T), Id) + sp.kron(sp.kron(T, Id), Id)).tocsc()
 
 
-@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+@pytest.mark.parametrize("mode", ["mixed", "fp64", "rbsor"])
 def test_requests_converge_by_oracle_residual(mode):
     reqs = small_requests(4)
     srv = SV.PoissonServer(mode=mode, check_every=20, keep_solution=True)
@@ -44,7 +44,7 @@ def test_requests_converge_by_oracle_residual(mode):
         assert err <= 1e-4, (r.rid, err)
 
 
-@pytest.mark.parametrize("mode", ["mixed", "fp64"])
+@pytest.mark.parametrize("mode", ["mixed", "fp64", "rbsor"])
 def test_result_same_alone_and_in_the_mix(mode):
     target = small_requests(1, base=950)[0]
     alone = SV.PoissonServer(mode=mode, check_every=20, keep_solution=True)
@@ -70,3 +70,17 @@ def test_fp64_and_mixed_agree():
     for r in reqs:
         a, b = sols["fp64"][r.rid], sols["mixed"][r.rid]
         assert np.max(np.abs(a - b)) <= 2e-4 * np.max(np.abs(a))
+
+
+def test_rbsor_needs_far_fewer_iterations_than_jacobi():
+    """Red-black SOR with the optimal factor: O(n) iterations against Jacobi's
+    O(n^2), on the same requests and the same stopping rule."""
+    reqs = small_requests(2, lo=24, hi=30, base=980)
+    sweeps = {}
+    for mode in ("fp64", "rbsor"):
+        srv = SV.PoissonServer(mode=mode, check_every=10, sor_check_every=5, keep_solution=True)
+        st = srv.run_trace([SV.Request(rid=r.rid, n=r.n, f=r.f.copy()) for r in reqs])
+        assert st["completed"] == 2 and st["max_rel_residual"] <= 1e-6
+        sweeps[mode] = {r.rid: r.sweeps for r in srv.done}
+    for r in reqs:
+        assert sweeps["rbsor"][r.rid] * 5 < sweeps["fp64"][r.rid], (r.n, sweeps)
