@@ -200,7 +200,10 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   // narrow tiles: compiled for batches of compile-time operators, FP32 / BF16
   const bool narrow = cfg.narrow && g0.dtype != GSCL_F64 && batch_capable(pl->op);
   const int VX = narrow ? 2 : vx_for(g0.dtype);
-  const int TX = 32 * VX;
+  // colour-compacted red-black sweeps: a warp spans 64 VX columns
+  const bool compact = cfg.compact && g0.dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_IEEE && !cfg.generic &&
+                       compact_capable(pl->op) && !reduce;
+  const int TX = (compact ? 64 : 32) * VX;
   // reach per input grid (coefficient reads are at the core element)
   int rxa[kMaxIn] = {}, rya[kMaxIn] = {}, rz = 0;
   for (auto &t : terms) {
@@ -337,6 +340,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   pl->threads = threads;
   pl->smem = smem;
   pl->narrow = narrow;
+  pl->compact = compact;
   pl->work = (long long)P.inst.tiles_x * P.inst.tiles_y * nz_range;
   pl->max_ctas = reduce ? kMaxReduceCtas : 0x7fffffff;
   return GSCL_OK;
@@ -470,6 +474,13 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
   return GSCL_OK;
 }
 
+// Colour-compacted red-black sweeps where they exist (GSCL_COLOR_COMPACT=0
+// turns them off: every element evaluated, the colour's stored).
+static bool colour_compact() {
+  const char *e = getenv("GSCL_COLOR_COMPACT");
+  return !(e && e[0] == '0');
+}
+
 gscl_status gscl_do_colored(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                             int32_t n_out, const gscl_range *range, int32_t color, int32_t half_sweeps,
                             void *stream) {
@@ -480,7 +491,9 @@ gscl_status gscl_do_colored(const gscl_stencil *op, const gscl_grid *in, int32_t
   if (gscl_status s = bind(op, false, in, n_in, out, n_out, range, &b, -1, 0, true)) return s;
   if (b.empty) return GSCL_OK;
   Plan pl;
-  if (gscl_status s = make_plan(b, false, &pl, TileCfg{})) return s;
+  TileCfg cfg;
+  cfg.compact = colour_compact();
+  if (gscl_status s = make_plan(b, false, &pl, cfg)) return s;
   for (int h = 0; h < half_sweeps; ++h) {
     pl.P.color = (color + h) & 1;
     if (gscl_status s = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream, nullptr)) return s;

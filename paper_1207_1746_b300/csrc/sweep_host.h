@@ -24,6 +24,7 @@ struct TileCfg {
   int pf = 0;            // planes prefetched beyond the stencil's z reach
   bool generic = false;  // interpret the term list even if a compiled structure matches
   bool narrow = false;   // batches, FP32 / BF16: 64-column tiles with 4 rows per warp
+  bool compact = false;  // red-black sweeps, IEEE FP64, star family: only the colour's elements
 };
 
 bool overlaps(const Grid &a, const Grid &b);

@@ -233,6 +233,7 @@ __device__ __forceinline__ double max_abs_bits(double a, double b) {
 struct GenericOp {
   static constexpr int kMaxOut = kMaxOut_;
   static constexpr int kQueue = 1;  // no z register queue (size of the unused array)
+  static constexpr int kXStep = 1;  // a thread's columns: lane + 32 e
   __device__ static int n_out(const SweepParams &P) { return P.n_out; }
 
   template <typename T, int VX, int VY>
@@ -290,8 +291,16 @@ struct GenericOp {
 
 // Compile-time term table (static_ops.h).  Term i's weight is P.terms[i]:
 // the host stores the matched descriptor's weights in table order.
-template <class Def>
+//
+// XS = 2 is the colour-compacted evaluation of red-black sweeps (FP64): a
+// warp covers 64 VX columns and a thread only the elements of the launch's
+// colour, x = x0 + col + 64 e with col = 2 lane + the row's parity offset.
+// The kernel passes col for the warp's first row as `lane`; row r flips its
+// low bit (the warp's rows start at an even row).  The column changes from
+// plane to plane, so there is no z register queue and no centre ring.
+template <class Def, int XS = 1>
 struct StaticOp {
+  static constexpr int kXStep = XS;
   static constexpr int kMaxOut = Def::NOUT > 0 ? Def::NOUT : 1;
   __device__ static constexpr int n_out(const SweepParams &) { return Def::NOUT; }
 
@@ -329,8 +338,11 @@ struct StaticOp {
     }
     return count == 1 ? found : -1;
   }
-  static constexpr int ZQ = queue_input();
+  static constexpr int ZQ = XS == 1 ? queue_input() : -1;
   static constexpr int kQueue = ZQ >= 0 ? 2 * RZ + 1 : 1;
+
+  // this thread's first column in tile row row0 + r (see XS above)
+  __device__ static __forceinline__ int column(int lane, int r) { return XS == 1 ? lane : (lane ^ (r & 1)); }
 
   // centre of the queue input at ring slot `sl`, tile row row0 + r
   template <typename T, int VX>
@@ -394,7 +406,7 @@ struct StaticOp {
   // the shared memory it frees gains (the host planner makes the same choice).
   template <typename T>
   __host__ __device__ static constexpr bool in_centre_ring(int in) {
-    return !std::is_same<T, double>::value && centre_only<Def>(in);
+    return XS == 1 && !std::is_same<T, double>::value && centre_only<Def>(in);
   }
 
   // element (row, lane) of centre-ring input `in` in slot cslot
@@ -412,6 +424,8 @@ struct StaticOp {
                                               typename Arith<T>::A (&o)[kMaxOut][VX],
                                               typename Arith<T>::A (&g)[VX]) {
     const int row = row0 + r;
+    const int col = column(lane, r);
+    constexpr int ES = 32 * XS;  // element stride of a thread's columns
     using A = typename Arith<T>::A;
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
@@ -434,14 +448,14 @@ struct StaticOp {
     } else {
       constexpr int RX = radius(0, t.in), RY = radius(1, t.in);
       constexpr int AX = (RX + vec - 1) / vec * vec;
-      constexpr int BW = 32 * VX + 2 * AX;
+      constexpr int BW = ES * VX + 2 * AX;
       constexpr int toff = (RY + t.dy) * BW + AX + t.dx;
       int slot = smod + t.dz;
       if constexpr (t.dz > 0) slot = slot >= R ? slot - R : slot;
       if constexpr (t.dz < 0) slot = slot < 0 ? slot + R : slot;
-      const T *p = ring + P.in_base[t.in] + slot * P.in_se[t.in] + row * BW + lane + toff;
+      const T *p = ring + P.in_base[t.in] + slot * P.in_se[t.in] + row * BW + col + toff;
 #pragma unroll
-      for (int e = 0; e < VX; ++e) x[e] = to_arith(p[32 * e]);
+      for (int e = 0; e < VX; ++e) x[e] = to_arith(p[ES * e]);
     }
     if constexpr (t.coef >= 0) {
 #pragma unroll
@@ -449,14 +463,14 @@ struct StaticOp {
       if constexpr (run_last(I)) {
         constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
         constexpr int AXc = (RXc + vec - 1) / vec * vec;
-        constexpr int BWc = 32 * VX + 2 * AXc;
+        constexpr int BWc = ES * VX + 2 * AXc;
         const T *cp = in_centre_ring<T>(t.coef)
                           ? centre_ptr<T, VX>(P, ring, t.coef, cslot, row, lane)
-                          : ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + lane + (RYc * BWc + AXc);
+                          : ring + P.in_base[t.coef] + smod * P.in_se[t.coef] + row * BWc + col + (RYc * BWc + AXc);
 #pragma unroll
         for (int e = 0; e < VX; ++e) {
-          if constexpr (t.out < 0) v[e] = fma(to_arith(cp[32 * e]), g[e], v[e]);
-          else o[t.out][e] = fma(to_arith(cp[32 * e]), g[e], o[t.out][e]);
+          if constexpr (t.out < 0) v[e] = fma(to_arith(cp[ES * e]), g[e], v[e]);
+          else o[t.out][e] = fma(to_arith(cp[ES * e]), g[e], o[t.out][e]);
         }
       }
     } else if constexpr (t.out < 0) {
@@ -574,7 +588,8 @@ __device__ __forceinline__ void block_fold(double &s, double &c, double *s_red, 
 template <typename T, int VX, int VY, int RED, class Op, bool BATCH>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
-  constexpr int TX = 32 * VX;
+  constexpr int XS = Op::kXStep;
+  constexpr int TX = 32 * XS * VX;
   constexpr int NO = Op::kMaxOut;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -750,6 +765,10 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       }
       if (ok) {
         const int64_t z = zb + s;
+        // colour-compacted sweeps: the warp's first row starts at column
+        // 2 lane + p, p making (x + y + z) even for colour 0 (x0 and the
+        // warp's first row y0 + wy VY differ from y0 by even amounts)
+        const int carg = XS == 1 ? lane : 2 * lane + (int)((P.color + y0 + z) & 1);
         Op::template advance_queue<T, VX, VY>(P, ring, smod, wy * VY, lane, s == 0, zq);
         static_for<VY>([&](auto rc) {
           constexpr int r = decltype(rc)::value;
@@ -761,17 +780,34 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
             for (int m = 0; m < NO; ++m) o[m][e] = A(0);
           }
-          Op::template eval_row<T, VX, VY, r>(P, ring, smod, cslot, wy * VY, lane, zq, v, o);
-          // red-black colouring: a thread's columns x0 + lane + 32 e share one parity
-          if (yok[r] && (P.color < 0 || (int)((x0 + lane + y[r] + z) & 1) == P.color)) {
+          Op::template eval_row<T, VX, VY, r>(P, ring, smod, cslot, wy * VY, carg, zq, v, o);
+          if constexpr (XS == 1) {
+            // red-black colouring: a thread's columns x0 + lane + 32 e share one parity
+            if (yok[r] && (P.color < 0 || (int)((x0 + lane + y[r] + z) & 1) == P.color)) {
+#pragma unroll
+              for (int m = 0; m < NO; ++m) {
+                if (m < Op::n_out(P)) {
+                  T *dst = reinterpret_cast<T *>(I->out[m].base) + z * I->out[m].plane + y[r] * I->out[m].pitch +
+                           x0 + lane;
+#pragma unroll
+                  for (int e = 0; e < VX; ++e)
+                    if (xok[e]) dst[32 * e] = from_arith<T>(o[m][e]);
+                }
+              }
+            }
+          } else if (yok[r]) {
+            // colour-compacted: every element this thread computed is of the colour
+            const int col = carg ^ (r & 1);
 #pragma unroll
             for (int m = 0; m < NO; ++m) {
               if (m < Op::n_out(P)) {
-                T *dst =
-                    reinterpret_cast<T *>(I->out[m].base) + z * I->out[m].plane + y[r] * I->out[m].pitch + x0 + lane;
+                T *dst = reinterpret_cast<T *>(I->out[m].base) + z * I->out[m].plane + y[r] * I->out[m].pitch +
+                         x0 + col;
 #pragma unroll
-                for (int e = 0; e < VX; ++e)
-                  if (xok[e]) dst[32 * e] = from_arith<T>(o[m][e]);
+                for (int e = 0; e < VX; ++e) {
+                  const int64_t x = x0 + col + 64 * e;
+                  if (x >= I->lo[0] && x < I->hi[0]) dst[64 * e] = from_arith<T>(o[m][e]);
+                }
               }
             }
           }
@@ -906,6 +942,7 @@ struct Plan {
   int batch_ctas = 0;         // its grid (fixed when the work-list was built)
   bool narrow = false;        // batches of FP32 / BF16 grids: 64-column tiles, 4 rows per warp
   bool pair = false;          // FP64 grids in pair arithmetic (fixed when the plan is made)
+  bool compact = false;       // colour-compacted red-black sweep (XS = 2 tiles)
 };
 
 // Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: two
@@ -996,6 +1033,18 @@ template <> struct BatchCapable<OpResidual7Rhs> { static constexpr bool value = 
 template <> struct BatchCapable<OpIdentity> { static constexpr bool value = true; };
 template <> struct BatchCapable<OpJacobi5_2D> { static constexpr bool value = true; };
 
+// Operator structures with a colour-compacted kernel (red-black Gauss-Seidel
+// and SOR of the 7-point and 2D 5-point families, IEEE FP64).
+template <class Def> struct CompactCapable { static constexpr bool value = false; };
+template <> struct CompactCapable<OpHeat7Rhs> { static constexpr bool value = true; };
+template <> struct CompactCapable<OpStar7> { static constexpr bool value = true; };
+template <> struct CompactCapable<OpJacobi7Rhs> { static constexpr bool value = true; };
+template <> struct CompactCapable<OpJacobi5_2D> { static constexpr bool value = true; };
+
+inline bool compact_capable(int op) {
+  return op == OP_HEAT7_RHS || op == OP_STAR7 || op == OP_JACOBI7_RHS || op == OP_JACOBI5_2D;
+}
+
 inline bool batch_capable(int op) {
   return op == OP_HEAT7_RHS || op == OP_STAR7 || op == OP_JACOBI7_RHS || op == OP_HEAT7_RHS_FUSED ||
          op == OP_HEAT7_FUSED || op == OP_RESIDUAL7_RHS || op == OP_IDENTITY || op == OP_JACOBI5_2D;
@@ -1021,6 +1070,10 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
     // batches of FP32 / BF16 grids whose widths leave 128-column tiles idle
     if constexpr (BATCH && !IsFp64Storage<T>::value) {
       if (pl.narrow) return launch_t<T, 2, RED, StaticOp<Def>, BATCH, 4>(pl, stream, occ);
+    }
+    // colour-compacted red-black sweeps of the star family on IEEE FP64 grids
+    if constexpr (!BATCH && RED == RED_NONE && std::is_same<T, double>::value && CompactCapable<Def>::value) {
+      if (pl.compact) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
     }
     return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
   }

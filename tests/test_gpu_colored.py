@@ -4,6 +4,7 @@ sub-ranges whose colour follows the interior index, the compiled and the
 generic kernels, and the alias rules."""
 import numpy as np
 import pytest
+import torch
 
 from gpu_common import as_storage
 from oracle import oracle as O
@@ -16,11 +17,17 @@ pytestmark = pytest.mark.gpu
 TOL = {"f64": 1e-13, "f32": 3e-6, "bf16": 2e-2}
 
 
-@pytest.fixture(params=["compiled", "generic"])
+@pytest.fixture(params=["compiled", "generic", "uncompacted"])
 def kernel_path(request, monkeypatch):
+    """compiled: the operator tables (FP64 star operators: colour-compacted,
+    each thread computing only the colour's elements); generic: the runtime
+    term loop; uncompacted: the tables evaluating both colours and storing one."""
     monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    monkeypatch.delenv("GSCL_COLOR_COMPACT", raising=False)
     if request.param == "generic":
         monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+    elif request.param == "uncompacted":
+        monkeypatch.setenv("GSCL_COLOR_COMPACT", "0")
     return request.param
 
 
@@ -60,6 +67,25 @@ def test_redblack_2d_jacobi_operator(kernel_path):
     for s in range(4):
         O.do_colored(s % 2, S.jacobi5_2d(), [ou], [ou])
     assert np.max(np.abs(gu.download().numpy() - ou.a)) <= 1e-14
+
+
+@pytest.mark.parametrize("n", [(256, 9, 6), (130, 17, 5), (37, 4, 3)])
+def test_compacted_equals_uncompacted_bit_for_bit(n, monkeypatch):
+    """The colour-compacted FP64 kernel and the one evaluating both colours
+    run the same operations per element: identical results, on widths that
+    fill whole 128-column tiles, leave a ragged tile, or fit in one."""
+    h = (1, 1, 1)
+    u0 = I.random_interior(77, n, h, -1.0, 1.0, halo_value=0.5)
+    f0 = I.random_interior(78, n, h, -1.0, 1.0)
+    got = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GSCL_COLOR_COMPACT", flag)
+        for omega in (1.0, 1.7):
+            gu, gf = B.Grid(n, h).upload(u0), B.Grid(n, h).upload(f0)
+            B.do_colored(S.poisson_sor(omega), [gu, gf], [gu], color=1, half_sweeps=5, rng=((1, 0, 1), n))
+            got[flag, omega] = gu.download()
+    for omega in (1.0, 1.7):
+        assert torch.equal(got["1", omega], got["0", omega])
 
 
 def test_redblack_converges_like_the_oracle():
