@@ -1,7 +1,7 @@
 /*
  * gscl_oracle.c -- plain FP64 CPU oracle for the two iteration spaces of the
  * generic stencil library: do_all and do_reduce, the ordered iteration
- * spaces and red-black colouring (Section 3).
+ * spaces, do_diamond and red-black colouring (Section 3).
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * benchmark's CPU-baseline / reference leg may load this code.  The CUDA
@@ -242,6 +242,36 @@ int orc_do_colored(int color, const orc_extent *e, int n_in, const orc_grid *in,
         for (int m = 0; m < n_out; ++m) r[m] = orc_term_sum(e, in, n_terms, terms, m, v, 0, i, j, k);
         for (int m = 0; m < n_out; ++m) out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r[m];
       }
+  return ORC_OK;
+}
+
+/* do_diamond (Section 3): cells (i-1, j) and (i, j-1) are processed before
+ * cell (i, j).  The paper has it for 2D grids; a 3D grid is taken plane by
+ * plane, the planes independent.  Lexicographic order (j outer, i inner)
+ * is one order that respects it.  Reads see the grids' current contents, so
+ * an output bound also as an input is seen updated at elements processed
+ * before (offsets with dx, dy <= 0) and not yet updated at elements
+ * processed after (dx, dy >= 0); at each element every output is computed
+ * before any is stored. */
+int orc_do_diamond(const orc_extent *e, int n_in, const orc_grid *in, int n_out, const orc_out_grid *out,
+                   int n_terms, const orc_term *terms, const int64_t lo[3], const int64_t hi[3]) {
+  if (n_out < 1 || n_out > 8) return ORC_BAD_ARG;
+  int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
+  if (rc) return rc;
+  double r[8];
+  for (int64_t k = lo[2]; k < hi[2]; ++k)
+    for (int64_t jj = lo[1]; jj < hi[1]; ++jj) {
+#if ORC_MUTANT == 10
+      const int64_t j = hi[1] - 1 - (jj - lo[1]); /* rows in reverse */
+#else
+      const int64_t j = jj;
+#endif
+      for (int64_t i = lo[0]; i < hi[0]; ++i) {
+        double v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, 0, i, j, k);
+        for (int m = 0; m < n_out; ++m) r[m] = orc_term_sum(e, in, n_terms, terms, m, v, 0, i, j, k);
+        for (int m = 0; m < n_out; ++m) out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r[m];
+      }
+    }
   return ORC_OK;
 }
 

@@ -95,6 +95,8 @@ def _get_lib():
         lib.orc_do_ordered.restype = ctypes.c_int
         lib.orc_do_colored.argtypes = [ctypes.c_int] + lib.orc_do_reduce.argtypes[1:-1]
         lib.orc_do_colored.restype = ctypes.c_int
+        lib.orc_do_diamond.argtypes = lib.orc_do_reduce.argtypes[1:-1]
+        lib.orc_do_diamond.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -184,6 +186,16 @@ def do_ordered(order, terms, ins, outs, lo=None, hi=None):
                                    len(outs), gout, len(terms), tt, clo, chi)
     if rc != 0:
         raise ValueError(f"oracle do_ordered rejected the call (code {rc})")
+
+
+def do_diamond(terms, ins, outs, lo=None, hi=None):
+    """do_diamond (Section 3): (i-1, j) and (i, j-1) are processed before
+    (i, j), here in lexicographic order, plane by plane; an output passed also
+    as an input (the same Grid) is read as updated so far."""
+    ext, gin, gout, tt, clo, chi = _marshal(terms, ins, outs, lo, hi, allow_alias=True)
+    rc = _get_lib().orc_do_diamond(ctypes.byref(ext), len(ins), gin, len(outs), gout, len(terms), tt, clo, chi)
+    if rc != 0:
+        raise ValueError(f"oracle do_diamond rejected the call (code {rc})")
 
 
 def do_colored(color, terms, ins, outs, lo=None, hi=None):

@@ -22,6 +22,7 @@ MUTANTS = {
     7: "the operator's value read as zero by fused terms",
     8: "1-norm instead of 2-norm",
     9: "red-black colour taken from i + j only",
+    10: "do_diamond rows visited in reverse",
 }
 
 RUNNER = r"""

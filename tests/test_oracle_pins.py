@@ -584,3 +584,78 @@ def test_colored_rejects_bad_colour_and_ranges():
         O.do_colored(2, sor_terms(), [u, f], [u])
     with pytest.raises(ValueError):
         O.do_colored(0, [(2, 0, 0, 0, O.NONE, 0, 1.0)], [u, f], [u])
+
+
+# ------------------------------------------------------------------ do_diamond
+def sat_terms():
+    """Summed-area table: x = f + x(i-1, j) + x(i, j-1) - x(i-1, j-1) (x input 0, f input 1)."""
+    return [(0, 0, 0, 1, O.NONE, 0, 1.0), (-1, 0, 0, 0, O.NONE, 0, 1.0), (0, -1, 0, 0, O.NONE, 0, 1.0),
+            (-1, -1, 0, 0, O.NONE, 0, -1.0)]
+
+
+@pytest.mark.parametrize("n,h", [((13, 9, 1), (1, 1, 0)), ((7, 6, 3), (1, 1, 1))])
+def test_diamond_summed_area_table(n, h):
+    """With (i-1, j) and (i, j-1) done before (i, j), the recurrence builds the
+    2D prefix sum of f in each plane: numpy's cumsum along both axes, exactly
+    on integer data."""
+    rng = np.random.default_rng(41)
+    x, f = O.zeros(n, h), O.zeros(n, h)
+    f.interior()[...] = rng.integers(-20, 20, size=n[::-1])
+    O.do_diamond(sat_terms(), [x, f], [x])
+    want = np.cumsum(np.cumsum(f.interior(), axis=2), axis=1)
+    assert np.array_equal(x.interior(), want)
+
+
+def diamond_by_antidiagonals(terms, arrays, h, n):
+    """do_diamond computed another way: every anti-diagonal i + j = t at once,
+    t ascending (numpy), each element from the arrays as they stand; outputs
+    are input 0 (in place)."""
+    hx, hy, hz = h
+    a = [x.copy() for x in arrays]
+    for k in range(n[2]):
+        for t in range(n[0] + n[1] - 1):
+            j = np.arange(max(0, t - n[0] + 1), min(n[1], t + 1))
+            i = t - j
+            acc = np.zeros(len(j))
+            for dx, dy, dz, src, coef, out, w in terms:
+                xv = a[src][k + hz + dz, j + hy + dy, i + hx + dx]
+                cv = 1.0 if coef == O.NONE else a[coef][k + hz, j + hy, i + hx]
+                acc = acc + (w * xv) * cv
+            a[0][k + hz, j + hy, i + hx] = acc
+    return a[0]
+
+
+def test_diamond_is_independent_of_the_wavefront_order():
+    """Reads of the output at offsets with dx, dy <= 0 see updated elements and
+    at dx, dy >= 0 old ones, whichever order respects the diamond: the
+    lexicographic loop equals a sweep by anti-diagonals."""
+    n, h = (11, 8, 2), (1, 1, 1)
+    rng = np.random.default_rng(42)
+    x0 = rng.uniform(-1, 1, (n[2] + 2, n[1] + 2, n[0] + 2))
+    f0 = rng.uniform(-1, 1, x0.shape)
+    terms = [(-1, 0, 0, 0, O.NONE, 0, 0.3), (0, -1, 0, 0, O.NONE, 0, 0.2), (-1, -1, 0, 0, O.NONE, 0, -0.1),
+             (1, 0, 0, 0, O.NONE, 0, 0.15), (0, 1, 0, 0, O.NONE, 0, 0.25), (1, 1, 0, 0, 1, 0, 0.05),
+             (0, 0, 0, 0, O.NONE, 0, -0.4), (0, 0, 1, 1, O.NONE, 0, 0.5)]
+    x = O.Grid(x0.copy(), h)
+    O.do_diamond(terms, [x, O.Grid(f0.copy(), h)], [x])
+    want = diamond_by_antidiagonals(terms, [x0, f0], h, n)
+    assert np.array_equal(x.a, want)
+
+
+def test_diamond_lexicographic_gauss_seidel_rate():
+    """Gauss-Seidel in the natural order on the 5-point Laplacian, in place:
+    the matrix is consistently ordered, so the error contracts by
+    cos^2(pi / (n + 1)) per sweep (n x n Dirichlet problem)."""
+    n, h = (10, 10, 1), (1, 1, 0)
+    rng = np.random.default_rng(43)
+    u = O.zeros(n, h)
+    u.interior()[...] = rng.uniform(-1, 1, (1, 10, 10))
+    terms = [(1, 0, 0, 0, O.NONE, 0, 0.25), (-1, 0, 0, 0, O.NONE, 0, 0.25), (0, 1, 0, 0, O.NONE, 0, 0.25),
+             (0, -1, 0, 0, O.NONE, 0, 0.25)]
+    norms = []
+    for _ in range(150):
+        O.do_diamond(terms, [u], [u])
+        norms.append(np.linalg.norm(u.interior()))
+    rate = norms[-1] / norms[-2]
+    want = math.cos(math.pi / 11) ** 2
+    assert abs(rate - want) <= 2e-4 * want, (rate, want)
