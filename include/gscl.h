@@ -331,6 +331,33 @@ gscl_status gscl_ordered_specialization(int32_t order, const gscl_stencil *op, c
                                         const gscl_grid *out, int32_t n_out, int32_t *shape);
 
 /*
+ * do_diamond (Section 3): applies the operator at every core element of the
+ * range so that (i-1, j, k) and (i, j-1, k) are processed before (i, j, k).
+ * The paper defines it for 2D grids; a 3D grid is taken plane by plane, the
+ * planes independent (and in any order).
+ *
+ *  - An output may also be an input when both name the same grid (the same
+ *    storage and layout; GSCL_ERR_ALIAS otherwise).  Terms read it in the
+ *    same plane (dz = 0) at offsets whose dx and dy have one sign: dx, dy <= 0
+ *    reads an element already processed, holding the value this call wrote
+ *    there (or the grid's content outside the range), and dx, dy >= 0 one not
+ *    yet processed, holding its value from before the call.  Mixed signs, or
+ *    another plane, would depend on the schedule: GSCL_ERR_ALIAS.  This is how
+ *    2D recurrences are written: summed-area tables
+ *    (x = f + x(i-1,j) + x(i,j-1) - x(i-1,j-1)) and Gauss-Seidel in the
+ *    natural order (u = (u(i-1,j) + u(i,j-1) + u(i+1,j) + u(i,j+1)) / 4).
+ *  - At each element every output is computed before any is stored; the
+ *    stored (rounded) value is what later elements read.
+ *  - Value terms (out = GSCL_VALUE, in = GSCL_VALUE) as in gscl_do_all; the
+ *    value is not reduced.
+ *  - GSCL_ERR_UNSUPPORTED beyond 65535 planes, or when the input tiles with
+ *    their aprons exceed shared memory.  Other errors, range and dtype rules
+ *    as gscl_do_all (n_out >= 1).  Asynchronous on `stream`.
+ */
+gscl_status gscl_do_diamond(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                            int32_t n_out, const gscl_range *range, void *stream);
+
+/*
  * Arithmetic of FP64 grids (not an operation of the paper; a B300 precision
  * mode).  GSCL_FP64_IEEE (default): IEEE FP64 fused multiply-adds, bound on
  * B300 by its FP64 pipe (about 1.7 per clock per SM).  GSCL_FP64_PAIR: each

@@ -102,6 +102,7 @@ def lib():
         "gscl_do_ordered": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
         "gscl_ordered_specialization": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(i32)],
         "gscl_do_colored": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), i32, i32, vp],
+        "gscl_do_diamond": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
         "gscl_set_fp64_arithmetic": [i32],
         "gscl_get_fp64_arithmetic": [],
@@ -327,6 +328,15 @@ def do_ordered(order, op, ins, outs, rng=None, stream=None):
     st = as_stencil(op)
     check(lib().gscl_do_ordered(int(order), ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
                                 _range(rng), stream_ptr(stream)))
+
+
+def do_diamond(op, ins, outs, rng=None, stream=None):
+    """gscl_do_diamond: (i-1, j) and (i, j-1) processed before (i, j)
+    (Section 3), plane by plane.  An output passed also as an input is read
+    updated at offsets dx, dy <= 0 and not yet updated at dx, dy >= 0."""
+    st = as_stencil(op)
+    check(lib().gscl_do_diamond(ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs), _range(rng),
+                                stream_ptr(stream)))
 
 
 def do_colored(op, ins, outs, color=0, half_sweeps=1, rng=None, stream=None):

@@ -19,7 +19,7 @@ bool overlaps(const Grid &a, const Grid &b) { return a.buf < b.buf + b.bytes && 
 // Validates handles, shapes, dtypes, the range, every term and aliasing.
 gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                  int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis, int ordered_step,
-                 bool colored) {
+                 bool colored, bool diamond) {
   if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
   if (n_out < 0 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut_);
   if (!in || (n_out > 0 && !out)) return fail(GSCL_ERR_INVALID, "grid arrays are required");
@@ -102,7 +102,7 @@ gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, i
     for (int a = 0; a < n_in; ++a) {
       if (!overlaps(b->out[m], b->in[a])) continue;
       const Grid &go = b->out[m], &gi = b->in[a];
-      if ((ordered_axis >= 0 || colored) &&
+      if ((ordered_axis >= 0 || colored || diamond) &&
           (go.buf != gi.buf || go.off != gi.off || go.pitch != gi.pitch || go.plane != gi.plane))
         return fail(GSCL_ERR_ALIAS, "output %d overlaps input %d without being the same grid", m, a);
       for (int t = 0; t < op->n_terms; ++t) {
@@ -112,7 +112,8 @@ gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, i
         const bool previous = ordered_axis >= 0 && d[ordered_axis] == ordered_step &&
                               d[(ordered_axis + 1) % 3] == 0 && d[(ordered_axis + 2) % 3] == 0;
         const bool other_colour = colored && ((d[0] + d[1] + d[2]) & 1);
-        if (!previous && !other_colour)
+        const bool one_sign = diamond && d[2] == 0 && ((d[0] <= 0 && d[1] <= 0) || (d[0] >= 0 && d[1] >= 0));
+        if (!previous && !other_colour && !one_sign)
           return fail(GSCL_ERR_ALIAS, "output %d is input %d, read at a non-zero offset by term %d", m, a, t);
       }
     }

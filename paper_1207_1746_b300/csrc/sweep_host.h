@@ -30,14 +30,17 @@ struct TileCfg {
 bool overlaps(const Grid &a, const Grid &b);
 
 // Validates handles, shapes, dtypes, the range, every term and aliasing
-// (Section 3's rules for stencil operators and do_all).
-// Validates handles, shapes, dtypes, the range, every term and aliasing.
-// ordered_axis >= 0 (ordered iteration spaces): an output bound also as an
-// input must be the same grid, read only at offset 0 or one step of
-// ordered_step along ordered_axis (the element visited just before).
+// (Section 3's rules for stencil operators and do_all: an output bound also
+// as an input is read only at offset 0).  The other iteration spaces allow
+// more reads of such an output, which must then be the same grid:
+//  - ordered_axis >= 0 (ordered iteration spaces): one step of ordered_step
+//    along ordered_axis (the element visited just before);
+//  - colored (red-black colouring): offsets with odd dx + dy + dz;
+//  - diamond (do_diamond): dz = 0 and dx, dy of one sign (elements processed
+//    before, or after, the core element).
 gscl_status bind(const gscl_stencil *op, bool need_value, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                  int32_t n_out, const gscl_range *range, Bound *b, int ordered_axis = -1, int ordered_step = 0,
-                 bool colored = false);
+                 bool colored = false, bool diamond = false);
 
 // Compile-time operator with the descriptor's structure, or OP_GENERIC.
 int match_static(const std::vector<gscl_term> &terms, int n_in, int n_out, std::vector<int> *perm);

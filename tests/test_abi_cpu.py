@@ -236,3 +236,25 @@ def test_colored_validation_errors():
     assert colored_status(gs, [u, f], []) == 1
     # ordinary do_all still refuses the in-place Gauss-Seidel operator
     assert do_all_status(gs, [u, f], [u]) == 3
+
+
+def diamond_status(terms, ins, outs, rng=None):
+    st = B.Stencil(terms)
+    return B.lib().gscl_do_diamond(ctypes.byref(st.c), B._handles(ins), len(ins), B._handles(outs), len(outs),
+                                   B._range(rng), None)
+
+
+def test_diamond_validation_errors():
+    """do_diamond: an output read in place only in its own plane, at offsets
+    whose dx and dy have one sign (elements processed before or after)."""
+    x, f = FakeGrid((16, 8, 4), (1, 1, 1)), FakeGrid((16, 8, 4), (1, 1, 1))
+    assert diamond_status([(1, -1, 0, 0, B.NONE, 0, 1.0)], [x], [x]) == 3      # mixed signs
+    assert diamond_status([(-1, 1, 0, 0, B.NONE, 0, 1.0)], [x], [x]) == 3
+    assert diamond_status([(0, 0, 1, 0, B.NONE, 0, 1.0)], [x], [x]) == 3       # another plane
+    assert diamond_status([(2, 0, 0, 0, B.NONE, 0, 1.0)], [x], [x]) == 2       # beyond the halo
+    assert diamond_status([(0, 0, 0, 0, B.NONE, 0, 1.0)], [x], []) == 1
+    # allowed in place (an empty range enqueues nothing, so no GPU is needed)
+    empty = ((0, 0, 2), (16, 8, 2))
+    ok = [(-1, 0, 0, 0, B.NONE, 0, 1.0), (0, -1, 0, 0, B.NONE, 0, 1.0), (-1, -1, 0, 0, B.NONE, 0, -1.0),
+          (1, 1, 0, 0, B.NONE, 0, 0.5), (0, 0, 0, 1, B.NONE, 0, 1.0), (1, -1, 1, 1, B.NONE, 0, 1.0)]
+    assert diamond_status(ok, [x, f], [x], rng=empty) == 0
