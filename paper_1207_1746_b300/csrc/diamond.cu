@@ -30,13 +30,17 @@ namespace {
 
 constexpr int kDT = 32;  // tile side (one lane per tile row)
 
+// Every staged tile has the same apron (AX columns, RY rows: the largest
+// reach of any term) and row width TW = kDT + 2 AX, so element (i, j) of the
+// tile sits at j TW + i plus a per-term constant, and a lane's position
+// advances by one element per step.
 struct DiaTerm {
-  int16_t in;    // input grid, or -1: the operator's value
-  int16_t coef;  // coefficient grid, or -1
-  int16_t out;   // output, or -1: a term of the value
-  int16_t dx, dy, dz;
+  int16_t in;      // input grid, or -1: the operator's value
+  int16_t coef;    // coefficient grid, or -1
   int16_t direct;  // dz != 0: read from global memory
-  int16_t pad;
+  int16_t dx, dy, dz;
+  int32_t soff;    // staged read: shared-memory offset of the read minus j TW + i
+  int32_t coff;    // the coefficient's, likewise
   float wf;
   double wd;
 };
@@ -46,14 +50,14 @@ struct DiaParams {
   int64_t in_pitch[kMaxIn], in_plane[kMaxIn];  // elements
   int64_t in_x0[kMaxIn], in_x1[kMaxIn];        // the grid's storage along x: [-h, n + h)
   int64_t in_y0[kMaxIn], in_y1[kMaxIn];        // ... and along y
-  int32_t ax[kMaxIn], ry[kMaxIn];              // apron of input a's tile
-  int32_t tw[kMaxIn];                          // its row width, kDT + 2 ax
-  int32_t toff[kMaxIn];                        // its element offset in shared memory
+  int32_t toff[kMaxIn];                        // element offset of input a's tile (-1: not staged)
+  int32_t AX, RY, TW;                          // the common apron and row width
   char *out[kMaxOut_];
   int64_t out_pitch[kMaxOut_], out_plane[kMaxOut_];
   uint32_t alias[kMaxOut_];  // bit a: input a names output m's grid
-  DiaTerm terms[kMaxTerms];
-  int32_t n_in, n_out, n_terms;
+  DiaTerm terms[kMaxTerms];  // value terms, then output 0's, output 1's, ...
+  int32_t n_in, n_out, n_value_terms;
+  int32_t out_begin[kMaxOut_ + 1];
   int64_t lo[3], hi[3];
   int32_t d, ti0;  // this launch's tile diagonal and its first tile's column
 };
@@ -61,7 +65,55 @@ struct DiaParams {
 __device__ __forceinline__ double dia_weight(const DiaTerm &t, double) { return t.wd; }
 __device__ __forceinline__ float dia_weight(const DiaTerm &t, float) { return t.wf; }
 
+// Compiled operators: the common 2D recurrences with every term's input and
+// offset a constant (weights stay runtime values, in P.terms order).  Input 0
+// is the output updated in place, input 1 the right-hand side; the reach is
+// one element, so tile rows are kDT + 2 wide.  A term is (dx, dy, input).
+struct DiaShapeTerm {
+  int dx, dy, in;
+};
+template <int N>
+struct DiaShapeTable {
+  DiaShapeTerm t[N];
+};
+enum DiaShapeId { DIA_INTERPRETED = -1, DIA_SAT = 0, DIA_GS5, DIA_GS5F, DIA_SOR5F, DIA_SHAPES };
+struct DiaSat {  // x = f + x(i-1,j) + x(i,j-1) - x(i-1,j-1): summed-area table
+  static constexpr int NT = 4, NIN = 2;
+  static constexpr DiaShapeTable<NT> table = {{{0, 0, 1}, {-1, 0, 0}, {0, -1, 0}, {-1, -1, 0}}};
+};
+struct DiaGs5 {  // x = sum of the 4 neighbours (natural-order Gauss-Seidel, Laplace)
+  static constexpr int NT = 4, NIN = 1;
+  static constexpr DiaShapeTable<NT> table = {{{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}}};
+};
+struct DiaGs5F {  // ... and a right-hand side
+  static constexpr int NT = 5, NIN = 2;
+  static constexpr DiaShapeTable<NT> table = {{{1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}}};
+};
+struct DiaSor5F {  // x = a x + sum of the 4 neighbours + f: SOR
+  static constexpr int NT = 6, NIN = 2;
+  static constexpr DiaShapeTable<NT> table = {{{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}}};
+};
+struct DiaInterpreted {};
+
 template <typename T>
+__device__ __forceinline__ typename Arith<T>::A dia_term(const DiaParams &P, const DiaTerm &tm, const T *tiles,
+                                                         int pos, int64_t z, int64_t y, int64_t x,
+                                                         typename Arith<T>::A v) {
+  using A = typename Arith<T>::A;
+  A r;
+  if (tm.in < 0) {
+    r = v;
+  } else if (tm.direct) {
+    const T *g = reinterpret_cast<const T *>(P.in[tm.in]);
+    r = to_arith(g[(z + tm.dz) * P.in_plane[tm.in] + (y + tm.dy) * P.in_pitch[tm.in] + (x + tm.dx)]);
+  } else {
+    r = to_arith(tiles[pos + tm.soff]);
+  }
+  if (tm.coef >= 0) r = r * to_arith(tiles[pos + tm.coff]);
+  return r;
+}
+
+template <typename T, class S>
 __global__ void __launch_bounds__(kDT) diamond_kernel(const __grid_constant__ DiaParams P) {
   using A = typename Arith<T>::A;
   extern __shared__ __align__(16) unsigned char dia_smem[];
@@ -70,58 +122,71 @@ __global__ void __launch_bounds__(kDT) diamond_kernel(const __grid_constant__ Di
   const int ti = P.ti0 + (int)blockIdx.x, tj = P.d - ti;
   const int64_t z = P.lo[2] + blockIdx.y;
   const int64_t x0 = P.lo[0] + (int64_t)ti * kDT, y0 = P.lo[1] + (int64_t)tj * kDT;
+  const int TW = P.TW, rows = kDT + 2 * P.RY;
 
   // stage each input's tile and apron; cells outside the grid's storage are
-  // skipped (no term reads them: the binding checked every read of the range)
+  // skipped (no term reads them: the binding checked every read of the range).
+  // FP32 / FP64: cp.async, so every row of every tile is in flight at once.
   for (int a = 0; a < P.n_in; ++a) {
+    if (P.toff[a] < 0) continue;
     const T *g = reinterpret_cast<const T *>(P.in[a]) + z * P.in_plane[a];
     T *t = tiles + P.toff[a];
-    const int rows = kDT + 2 * P.ry[a], w = P.tw[a];
     for (int r = 0; r < rows; ++r) {
-      const int64_t y = y0 - P.ry[a] + r;
+      const int64_t y = y0 - P.RY + r;
       if (y < P.in_y0[a] || y >= P.in_y1[a]) continue;
-      for (int c = lane; c < w; c += 32) {
-        const int64_t x = x0 - P.ax[a] + c;
-        if (x >= P.in_x0[a] && x < P.in_x1[a]) t[r * w + c] = g[y * P.in_pitch[a] + x];
+      for (int c = lane; c < TW; c += 32) {
+        const int64_t x = x0 - P.AX + c;
+        if (x < P.in_x0[a] || x >= P.in_x1[a]) continue;
+        if constexpr (sizeof(T) >= 4) {
+          const uint32_t sa = (uint32_t)__cvta_generic_to_shared(t + r * TW + c);
+          const T *src = g + y * P.in_pitch[a] + x;
+          if constexpr (sizeof(T) == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(src) : "memory");
+          else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(src) : "memory");
+        } else {
+          t[r * TW + c] = g[y * P.in_pitch[a] + x];
+        }
       }
     }
   }
+  if constexpr (sizeof(T) >= 4) asm volatile("cp.async.wait_all;" ::: "memory");
   __syncwarp();
 
   const int j = lane;
   const int64_t y = y0 + j;
   const int ni = (int)min((int64_t)kDT, P.hi[0] - x0), nj = (int)min((int64_t)kDT, P.hi[1] - y0);
+  const int centre = P.RY * TW + P.AX;  // offset of the core element of a staged read
   for (int t = 0; t < ni + nj - 1; ++t) {
     const int i = t - j;
-    if (j < nj && i >= 0 && i < ni) {
+    if constexpr (!std::is_same<S, DiaInterpreted>::value) {
+      // compiled: one output, updated in place in input 0's tile
+      if (j < nj && i >= 0 && i < ni) {
+        constexpr int TWc = kDT + 2;
+        const int pos = j * TWc + i + TWc + 1;
+        A o = A(0);
+        static_for<S::NT>([&](auto qc) {
+          constexpr int q = decltype(qc)::value;
+          constexpr DiaShapeTerm st = S::table.t[q];
+          const T *src = tiles + P.toff[st.in];
+          o = fma(dia_weight(P.terms[q], A(0)), to_arith(src[pos + st.dy * TWc + st.dx]), o);
+        });
+        tiles[P.toff[0] + pos] = from_arith<T>(o);
+      }
+    } else if (j < nj && i >= 0 && i < ni) {
+      const int pos = j * TW + i;
       A v = A(0);
+      for (int q = 0; q < P.n_value_terms; ++q) {
+        const DiaTerm &tm = P.terms[q];
+        v = fma(dia_weight(tm, A(0)), dia_term<T>(P, tm, tiles, pos, z, y, x0 + i, v), v);
+      }
       A o[kMaxOut_];
 #pragma unroll
-      for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
-      for (int q = 0; q < P.n_terms; ++q) {  // value terms come first
-        const DiaTerm &tm = P.terms[q];
-        A x;
-        if (tm.in < 0) {
-          x = v;
-        } else if (tm.direct) {
-          const T *g = reinterpret_cast<const T *>(P.in[tm.in]);
-          x = to_arith(g[(z + tm.dz) * P.in_plane[tm.in] + (y + tm.dy) * P.in_pitch[tm.in] + (x0 + i + tm.dx)]);
-        } else {
-          const int a = tm.in;
-          x = to_arith(tiles[P.toff[a] + (j + P.ry[a] + tm.dy) * P.tw[a] + (i + P.ax[a] + tm.dx)]);
-        }
-        if (tm.coef >= 0) {
-          const int c = tm.coef;
-          x = x * to_arith(tiles[P.toff[c] + (j + P.ry[c]) * P.tw[c] + (i + P.ax[c])]);
-        }
-        const A w = dia_weight(tm, A(0));
-        if (tm.out < 0) {
-          v = fma(w, x, v);
-        } else {
-#pragma unroll
-          for (int m = 0; m < kMaxOut_; ++m)
-            if (tm.out == m) o[m] = fma(w, x, o[m]);
-        }
+      for (int m = 0; m < kMaxOut_; ++m) {
+        o[m] = A(0);
+        if (m < P.n_out)
+          for (int q = P.out_begin[m]; q < P.out_begin[m + 1]; ++q) {
+            const DiaTerm &tm = P.terms[q];
+            o[m] = fma(dia_weight(tm, A(0)), dia_term<T>(P, tm, tiles, pos, z, y, x0 + i, v), o[m]);
+          }
       }
       // every output of this element is computed before any is stored
 #pragma unroll
@@ -130,7 +195,7 @@ __global__ void __launch_bounds__(kDT) diamond_kernel(const __grid_constant__ Di
         const T val = from_arith<T>(o[m]);
         if (P.alias[m]) {
           for (int a = 0; a < P.n_in; ++a)
-            if ((P.alias[m] >> a) & 1u) tiles[P.toff[a] + (j + P.ry[a]) * P.tw[a] + (i + P.ax[a])] = val;
+            if ((P.alias[m] >> a) & 1u) tiles[P.toff[a] + pos + centre] = val;
         } else {
           reinterpret_cast<T *>(P.out[m])[z * P.out_plane[m] + y * P.out_pitch[m] + (x0 + i)] = val;
         }
@@ -144,15 +209,15 @@ __global__ void __launch_bounds__(kDT) diamond_kernel(const __grid_constant__ Di
     if (!P.alias[m]) continue;
     const int a = __ffs((int)P.alias[m]) - 1;
     T *g = reinterpret_cast<T *>(P.out[m]) + z * P.out_plane[m];
-    const T *t = tiles + P.toff[a];
+    const T *t = tiles + P.toff[a] + centre;
     for (int r = 0; r < nj; ++r)
-      for (int c = lane; c < ni; c += 32) g[(y0 + r) * P.out_pitch[m] + x0 + c] = t[(r + P.ry[a]) * P.tw[a] + c + P.ax[a]];
+      for (int c = lane; c < ni; c += 32) g[(y0 + r) * P.out_pitch[m] + x0 + c] = t[r * TW + c];
   }
 }
 
-template <typename T>
-gscl_status launch_diamond_t(DiaParams &P, size_t smem, int tiles_x, int tiles_y, int planes, cudaStream_t st) {
-  auto kern = diamond_kernel<T>;
+template <typename T, class S>
+gscl_status launch_diamond_s(DiaParams &P, size_t smem, int tiles_x, int tiles_y, int planes, cudaStream_t st) {
+  auto kern = diamond_kernel<T, S>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "do_diamond set-up");
@@ -166,6 +231,50 @@ gscl_status launch_diamond_t(DiaParams &P, size_t smem, int tiles_x, int tiles_y
     if (e != cudaSuccess) return cuda_fail(e, "do_diamond launch");
   }
   return GSCL_OK;
+}
+
+template <typename T>
+gscl_status launch_diamond_t(DiaParams &P, int shape, size_t smem, int tiles_x, int tiles_y, int planes,
+                             cudaStream_t st) {
+  switch (shape) {
+    case DIA_SAT: return launch_diamond_s<T, DiaSat>(P, smem, tiles_x, tiles_y, planes, st);
+    case DIA_GS5: return launch_diamond_s<T, DiaGs5>(P, smem, tiles_x, tiles_y, planes, st);
+    case DIA_GS5F: return launch_diamond_s<T, DiaGs5F>(P, smem, tiles_x, tiles_y, planes, st);
+    case DIA_SOR5F: return launch_diamond_s<T, DiaSor5F>(P, smem, tiles_x, tiles_y, planes, st);
+  }
+  return launch_diamond_s<T, DiaInterpreted>(P, smem, tiles_x, tiles_y, planes, st);
+}
+
+struct DiaShapeDesc {
+  int id, nt, nin;
+  const DiaShapeTerm *t;
+};
+
+template <class S>
+DiaShapeDesc dia_desc(int id) {
+  return DiaShapeDesc{id, S::NT, S::NIN, S::table.t};
+}
+
+// The compiled shape of a call: one output, bound also as input 0 and as no
+// other input, no value terms, no coefficients, every term in the table's
+// order with the table's offsets (GSCL_GENERIC_ONLY=1: none).
+int diamond_shape(const gscl_stencil *op, int n_in, int n_out, const DiaParams &P) {
+  const char *env = getenv("GSCL_GENERIC_ONLY");
+  if (env && env[0] && env[0] != '0') return DIA_INTERPRETED;
+  if (n_out != 1 || P.alias[0] != 1u || P.AX != 1 || P.RY != 1) return DIA_INTERPRETED;
+  static const DiaShapeDesc shapes[] = {dia_desc<DiaSat>(DIA_SAT), dia_desc<DiaGs5>(DIA_GS5),
+                                        dia_desc<DiaGs5F>(DIA_GS5F), dia_desc<DiaSor5F>(DIA_SOR5F)};
+  for (const DiaShapeDesc &d : shapes) {
+    if (d.nt != op->n_terms || d.nin != n_in) continue;
+    bool ok = true;
+    for (int q = 0; q < d.nt && ok; ++q) {
+      const gscl_term &tm = op->terms[q];
+      ok = tm.out == 0 && tm.coef == GSCL_NONE && tm.dz == 0 && tm.in == d.t[q].in && tm.dx == d.t[q].dx &&
+           tm.dy == d.t[q].dy;
+    }
+    if (ok) return d.id;
+  }
+  return DIA_INTERPRETED;
 }
 
 }  // namespace
@@ -188,16 +297,28 @@ extern "C" gscl_status gscl_do_diamond(const gscl_stencil *op, const gscl_grid *
   P.n_out = n_out;
   const int elem = b.in[0].elem;
   const int align = 16 / elem;
+  // the common apron: the largest x / y reach of any staged read
+  int AX = 0, RY = 0;
+  bool staged[kMaxIn] = {};
+  for (int t = 0; t < op->n_terms; ++t) {
+    const gscl_term &tm = op->terms[t];
+    if (tm.coef != GSCL_NONE) staged[tm.coef] = true;
+    if (tm.in == GSCL_VALUE || tm.dz != 0) continue;
+    staged[tm.in] = true;
+    AX = std::max(AX, abs((int)tm.dx));
+    RY = std::max(RY, abs((int)tm.dy));
+  }
+  for (int m = 0; m < n_out; ++m)  // an output updated in place is staged even if no term reads it
+    for (int a = 0; a < n_in; ++a)
+      if (overlaps(b.out[m], b.in[a])) staged[a] = true;
+  const int TW = kDT + 2 * AX;
+  const int tile = (TW * (kDT + 2 * RY) + align - 1) / align * align;
+  P.AX = AX;
+  P.RY = RY;
+  P.TW = TW;
   int base = 0;
   for (int a = 0; a < n_in; ++a) {
     const Grid &g = b.in[a];
-    int ax = 0, ry = 0;
-    for (int t = 0; t < op->n_terms; ++t) {
-      const gscl_term &tm = op->terms[t];
-      if (tm.in != a) continue;
-      ax = std::max(ax, abs((int)tm.dx));
-      ry = std::max(ry, abs((int)tm.dy));
-    }
     P.in[a] = g.elem_ptr(0, 0, 0);
     P.in_pitch[a] = g.pitch;
     P.in_plane[a] = g.plane;
@@ -205,11 +326,8 @@ extern "C" gscl_status gscl_do_diamond(const gscl_stencil *op, const gscl_grid *
     P.in_x1[a] = g.n[0] + g.halo[0];
     P.in_y0[a] = -g.halo[1];
     P.in_y1[a] = g.n[1] + g.halo[1];
-    P.ax[a] = ax;
-    P.ry[a] = ry;
-    P.tw[a] = kDT + 2 * ax;
-    P.toff[a] = base;
-    base += (P.tw[a] * (kDT + 2 * ry) + align - 1) / align * align;
+    P.toff[a] = staged[a] ? base : -1;
+    if (staged[a]) base += tile;
   }
   const size_t smem = (size_t)base * elem;
   if (smem > (size_t)max_smem_per_block())
@@ -222,35 +340,42 @@ extern "C" gscl_status gscl_do_diamond(const gscl_stencil *op, const gscl_grid *
     for (int a = 0; a < n_in; ++a)
       if (overlaps(g, b.in[a])) P.alias[m] |= 1u << a;  // bind has checked it is the same grid
   }
-  // value terms first, then the outputs' terms, each group in descriptor order
+  // value terms, then each output's terms, each group in descriptor order
   int nt = 0;
-  for (int pass = 0; pass < 2; ++pass)
-    for (int t = 0; t < op->n_terms; ++t) {
-      const gscl_term &tm = op->terms[t];
-      if ((tm.out == GSCL_VALUE) != (pass == 0)) continue;
-      DiaTerm &d = P.terms[nt++];
-      d.in = tm.in == GSCL_VALUE ? -1 : (int16_t)tm.in;
-      d.coef = tm.coef == GSCL_NONE ? -1 : (int16_t)tm.coef;
-      d.out = tm.out == GSCL_VALUE ? -1 : (int16_t)tm.out;
-      d.dx = tm.dx;
-      d.dy = tm.dy;
-      d.dz = tm.dz;
-      d.direct = (int16_t)(d.in >= 0 && tm.dz != 0);
-      d.wf = (float)tm.w;
-      d.wd = tm.w;
-    }
-  P.n_terms = nt;
+  auto push = [&](const gscl_term &tm) {
+    DiaTerm &d = P.terms[nt++];
+    d.in = tm.in == GSCL_VALUE ? -1 : (int16_t)tm.in;
+    d.coef = tm.coef == GSCL_NONE ? -1 : (int16_t)tm.coef;
+    d.dx = tm.dx;
+    d.dy = tm.dy;
+    d.dz = tm.dz;
+    d.direct = (int16_t)(d.in >= 0 && tm.dz != 0);
+    d.soff = (d.in >= 0 && !d.direct) ? P.toff[d.in] + (RY + tm.dy) * TW + AX + tm.dx : 0;
+    d.coff = d.coef >= 0 ? P.toff[d.coef] + RY * TW + AX : 0;
+    d.wf = (float)tm.w;
+    d.wd = tm.w;
+  };
+  for (int t = 0; t < op->n_terms; ++t)
+    if (op->terms[t].out == GSCL_VALUE) push(op->terms[t]);
+  P.n_value_terms = nt;
+  for (int m = 0; m < n_out; ++m) {
+    P.out_begin[m] = nt;
+    for (int t = 0; t < op->n_terms; ++t)
+      if (op->terms[t].out == m) push(op->terms[t]);
+  }
+  P.out_begin[n_out] = nt;
   for (int a = 0; a < 3; ++a) {
     P.lo[a] = b.lo[a];
     P.hi[a] = b.hi[a];
   }
   const int tiles_x = (int)((b.hi[0] - b.lo[0] + kDT - 1) / kDT);
   const int tiles_y = (int)((b.hi[1] - b.lo[1] + kDT - 1) / kDT);
+  const int shape = diamond_shape(op, n_in, n_out, P);
   cudaStream_t st = (cudaStream_t)stream;
   switch (b.in[0].dtype) {
-    case GSCL_F64: return launch_diamond_t<double>(P, smem, tiles_x, tiles_y, (int)planes, st);
-    case GSCL_F32: return launch_diamond_t<float>(P, smem, tiles_x, tiles_y, (int)planes, st);
-    case GSCL_BF16: return launch_diamond_t<__nv_bfloat16>(P, smem, tiles_x, tiles_y, (int)planes, st);
+    case GSCL_F64: return launch_diamond_t<double>(P, shape, smem, tiles_x, tiles_y, (int)planes, st);
+    case GSCL_F32: return launch_diamond_t<float>(P, shape, smem, tiles_x, tiles_y, (int)planes, st);
+    case GSCL_BF16: return launch_diamond_t<__nv_bfloat16>(P, shape, smem, tiles_x, tiles_y, (int)planes, st);
   }
   return fail(GSCL_ERR_DTYPE, "unknown dtype");
 }

@@ -4,6 +4,7 @@ operators reading the output on both sides of the wavefront, natural-order
 Gauss-Seidel, several tiles with ragged edges, 2D and 3D grids, sub-ranges."""
 import numpy as np
 import pytest
+import torch
 
 from gpu_common import as_storage
 from oracle import oracle as O
@@ -39,10 +40,20 @@ def run_both(terms, arrays, n, h, dtype, rng=None):
     return got, og[0].a
 
 
+@pytest.fixture(params=["compiled", "interpreted"])
+def kernel_path(request, monkeypatch):
+    """compiled: the summed-area table and natural-order Gauss-Seidel shapes
+    with constant offsets; interpreted: the runtime term loop."""
+    monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    if request.param == "interpreted":
+        monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
+    return request.param
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 @pytest.mark.parametrize("n,h,rng", [((100, 70, 1), (1, 1, 0), None), ((40, 37, 5), (1, 1, 1), None),
                                      ((129, 65, 3), (1, 1, 1), ((5, 3, 1), (120, 64, 3)))])
-def test_summed_area_table_bitexact(dtype, n, h, rng):
+def test_summed_area_table_bitexact(kernel_path, dtype, n, h, rng):
     x0 = integer_grid(1, n, h, -3, 3)   # the halo rows/columns seed the sums (interior overwritten)
     f = integer_grid(2, n, h, -20, 20)
     got, want = run_both(SAT, [x0, f], n, h, dtype, rng)
@@ -61,7 +72,27 @@ def test_operator_reading_both_sides_of_the_wavefront(dtype, tol, n, h):
     assert np.max(np.abs(got - want)) <= tol * max(1.0, np.max(np.abs(want)))
 
 
-def test_natural_order_gauss_seidel_sweeps():
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("terms", ["gs5", "gs5f", "sor5f", "sat"])
+def test_compiled_shapes_equal_interpreted_bit_for_bit(terms, dtype, monkeypatch):
+    n, h = (77, 70, 2), (1, 1, 1)
+    ops = {"gs5": GS5[:4], "gs5f": GS5,
+           "sor5f": [(0, 0, 0, 0, NONE, 0, -0.6)] + [(dx, dy, dz, a, c, o, 0.4) for dx, dy, dz, a, c, o, _ in GS5],
+           "sat": SAT}
+    op = ops[terms]
+    arrays = [I.random_interior(9, n, h, -1.0, 1.0, halo_value=0.25), I.random_interior(10, n, h, -1.0, 1.0)]
+    if terms == "gs5":
+        arrays = arrays[:1]
+    got = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("GSCL_GENERIC_ONLY", flag)
+        gg = [B.Grid(n, h, dtype).upload(a) for a in arrays]
+        B.do_diamond(op, gg, gg[:1], rng=((2, 1, 0), (77, 70, 2)))
+        got[flag] = gg[0].download()
+    assert torch.equal(got["0"], got["1"])
+
+
+def test_natural_order_gauss_seidel_sweeps(kernel_path):
     n, h = (96, 80, 1), (1, 1, 0)
     u0 = I.random_interior(5, n, h, -1.0, 1.0, halo_value=1.0)
     f = I.random_interior(6, n, h, -1.0, 1.0)
