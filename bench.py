@@ -960,7 +960,10 @@ def main():
                            "l2": "working set (2 grids, 268 MB) larger than the 126 MB L2, no flush"},
                 "iteration_ms": round(t, 4),
                 "roofline": {"bound": "alu", "achieved": round(g_ops * 2 / 1e3, 4), "peak": fma, "unit": "TFLOP/s",
-                             "frac": round(g_ops * 2 / 1e3 / fma, 4) if fma == fma else None, "traffic": None,
+                             "frac": round(g_ops * 2 / 1e3 / fma, 4) if fma == fma else None,
+                             "traffic": (2 * profile_traffic("redblack_half_sweep")
+                                         if profile_traffic("redblack_half_sweep") else None),
+                             "traffic_note": "DRAM bytes per iteration: two half-sweeps of the ncu capture",
                              "peak_source": "measured FP64 FMA rate (gscl_fma_throughput); 8 FMAs per point "
                                             "and iteration (each colour evaluated once)",
                              "hbm_gbs": round(gbs, 1)},
@@ -982,7 +985,9 @@ def main():
                 "value": round(dist.world * r["reps"] * r["points"] / (t * 1e-3) / 1e9, 3),
                 "ms_per_step": round(t, 3), "solve_ms": round(r["solve_ms"], 4), "path": r["path"],
                 "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm, "unit": "GB/s",
-                             "frac": round(gbs / peak_hbm, 4), "traffic": None, "peak_source": "measured"}}
+                             "frac": round(gbs / peak_hbm, 4),
+                             "traffic": profile_traffic("ordered_f64") if (dt, interp) == ("f64", False) else None,
+                             "peak_source": "measured"}}
         # FP64: three FP64-pipe instructions per point (DFMA a g, DMUL m x(k-1),
         # DFMA of the sum), each taking the pipe as long as one DFMA
         fma = B_fma() if not args.profile else None
