@@ -519,11 +519,49 @@ gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_stencil *op, co
 
 /*
  * Waits for `stream` and reports device-side failures of the library's
- * kernels enqueued on this device since the last gscl_sync: GSCL_ERR_TIMEOUT
- * if a bounded wait inside a kernel gave up, GSCL_ERR_CUDA for a CUDA error.
- * Clears the device-side flag.
+ * kernels enqueued on this device since the last gscl_sync: GSCL_ERR_RANGE if
+ * a run-time compiled operator read outside its declared reach (the read
+ * returned 0 and touched no memory), GSCL_ERR_TIMEOUT if a bounded wait inside
+ * a kernel gave up, GSCL_ERR_CUDA for a CUDA error.  Clears the device-side
+ * flag.
  */
 gscl_status gscl_sync(void *stream);
+
+/*
+ * Point operators compiled at run time.  In the paper a stencil operator is a
+ * C++ function object compiled with the program (Section 3, Fig. 1b), so any
+ * arithmetic can run at a core element; here the operator may also be given
+ * as source text, compiled by NVRTC for sm_103a into a do_all kernel.
+ *
+ * `body` is a block of CUDA C++ statements, run once per core element, that
+ *  - reads input a at an offset as in<a>(dx, dy, dz) (in0 .. in<n_in - 1>),
+ *    a value of type `real` (double for FP64 grids, float for FP32 and BF16);
+ *  - may use the core element's interior index i, j, k (long long), as the
+ *    paper's stateful stencils query indices;
+ *  - assigns out0 .. out<n_out - 1> (type real, starting at 0), stored at the
+ *    core element after the body has run;
+ *  - may call CUDA's device math functions.
+ * `reach[3]` bounds |dx|, |dy|, |dz| of every read.  A read beyond it returns
+ * 0, touches no memory and makes the next gscl_sync return GSCL_ERR_RANGE.
+ *
+ * gscl_program_create compiles the body for grids of `dtype` (host-only; no
+ * GPU needed): GSCL_ERR_INVALID with the compiler's log in gscl_last_error()
+ * if it does not compile, GSCL_ERR_UNSUPPORTED if NVRTC is not installed.
+ * gscl_program_destroy releases it (GSCL_ERR_STATE for an unknown handle).
+ *
+ * gscl_do_all_program runs it as gscl_do_all runs an operator: n_in / n_out
+ * and the dtype must be the program's; the range and halo rules apply to the
+ * declared reach; an output may also be an input only with reach {0, 0, 0};
+ * sweeps > 1 ping-pongs in[0] and out[0] as gscl_do_all does.  The module is
+ * loaded on the current device at its first launch there.  Asynchronous on
+ * `stream`.
+ */
+typedef uint64_t gscl_program;
+gscl_status gscl_program_create(const char *body, int32_t n_in, int32_t n_out, int32_t dtype, const int32_t reach[3],
+                                gscl_program *out);
+gscl_status gscl_program_destroy(gscl_program p);
+gscl_status gscl_do_all_program(gscl_program p, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                                int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream);
 
 /*
  * FMA throughput of this device in FLOP/s (2 per fused multiply-add) for

@@ -235,3 +235,58 @@ def do_reduce(op, terms, ins, outs=(), lo=None, hi=None) -> float:
     if rc != 0:
         raise ValueError(f"oracle do_reduce rejected the call (code {rc})")
     return float(res.value)
+
+
+# ------------------------------------------------------------------ run-time point operators
+_PROG_TEMPLATE = os.path.join(_HERE, "program_template.c")
+
+
+class Program:
+    """A point operator given as C statements (reads ``in<a>(dx, dy, dz)``, the
+    index ``i, j, k``; assigns ``out<m>``), compiled with gcc and applied at
+    every core element of a range in lexicographic order (Section 3, do_all).
+    ``reach`` bounds every read's offset; reads beyond it return 0 and are
+    counted in ``outside``."""
+
+    def __init__(self, body, n_in, n_out, reach=(1, 1, 1)):
+        import hashlib
+        defs = "".join(f"#define in{a}(dx, dy, dz) orc_in(e, &in[{a}], i, j, k, (dx), (dy), (dz), reach, outside)\n"
+                       for a in range(n_in))
+        decl = "".join(f"        real out{m} = 0;\n" for m in range(n_out))
+        stores = "".join(f"        out[{m}].data[orc_at(e, out[{m}].hx, out[{m}].hy, out[{m}].hz, i, j, k)] = out{m};\n"
+                         for m in range(n_out))
+        with open(_PROG_TEMPLATE) as f:
+            src = f.read()
+        src = (src.replace("/*@DEFS@*/", defs).replace("/*@DECL@*/", decl).replace("/*@BODY@*/", body)
+               .replace("/*@STORES@*/", stores))
+        key = hashlib.sha1(src.encode()).hexdigest()[:16]
+        os.makedirs(_LIB_DIR, exist_ok=True)
+        path = os.path.join(_LIB_DIR, f"prog_{key}.so")
+        if not os.path.exists(path):
+            c = os.path.join(_LIB_DIR, f"prog_{key}.c")
+            with open(c, "w") as f:
+                f.write(src)
+            tmp = path + f".tmp{os.getpid()}"
+            subprocess.check_call(["gcc", "-std=gnu99", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                                   "-shared", "-o", tmp, c, "-lm"])
+            os.replace(tmp, path)
+        self._lib = ctypes.CDLL(path)
+        self._lib.orc_program.restype = ctypes.c_int
+        self.n_in, self.n_out, self.reach = n_in, n_out, tuple(int(v) for v in reach)
+        self.outside = 0
+
+    def run(self, ins, outs, lo=None, hi=None):
+        if len(ins) != self.n_in or len(outs) != self.n_out:
+            raise ValueError("the program was made for another number of grids")
+        ext, gin, gout, _, clo, chi = _marshal([], ins, outs, lo, hi, allow_alias=True)
+        for a in range(3):
+            if clo[a] < 0 or chi[a] > (ext.nx, ext.ny, ext.nz)[a] or clo[a] > chi[a]:
+                raise ValueError("range outside the interior")
+        for g in ins:
+            for a in range(3):
+                if clo[a] < chi[a] and self.reach[a] > g.halo[a]:
+                    raise ValueError("reach beyond a grid's halo")
+        r = (ctypes.c_int32 * 3)(*self.reach)
+        n = ctypes.c_int64(0)
+        self._lib.orc_program(ctypes.byref(ext), gin, gout, clo, chi, r, ctypes.byref(n))
+        self.outside += n.value

@@ -103,6 +103,9 @@ def lib():
         "gscl_ordered_specialization": [i32, P(StencilC), P(u64), i32, P(u64), i32, P(i32)],
         "gscl_do_colored": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), i32, i32, vp],
         "gscl_do_diamond": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
+        "gscl_program_create": [ctypes.c_char_p, i32, i32, i32, P(i32), P(u64)],
+        "gscl_program_destroy": [u64],
+        "gscl_do_all_program": [u64, P(u64), i32, P(u64), i32, P(RangeC), i32, vp],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
         "gscl_set_fp64_arithmetic": [i32],
         "gscl_get_fp64_arithmetic": [],
@@ -328,6 +331,30 @@ def do_ordered(order, op, ins, outs, rng=None, stream=None):
     st = as_stencil(op)
     check(lib().gscl_do_ordered(int(order), ctypes.byref(st.c), _handles(ins), len(ins), _handles(outs), len(outs),
                                 _range(rng), stream_ptr(stream)))
+
+
+class Program:
+    """gscl_program_create: a point operator given as CUDA C++ statements
+    (reads in0(dx, dy, dz) .., the index i, j, k; assigns out0 ..), compiled at
+    run time for grids of ``dtype``; ``reach`` bounds every read's offset."""
+
+    def __init__(self, body, n_in, n_out, dtype="f64", reach=(1, 1, 1)):
+        h = ctypes.c_uint64()
+        r = (ctypes.c_int32 * 3)(*[int(v) for v in reach])
+        check(lib().gscl_program_create(body.encode(), int(n_in), int(n_out), _DTYPES[dtype][0], r,
+                                        ctypes.byref(h)))
+        self.handle = h.value
+        self.n_in, self.n_out, self.dtype = n_in, n_out, dtype
+
+    def __del__(self):
+        h = getattr(self, "handle", 0)
+        if h and _lib is not None:
+            _lib.gscl_program_destroy(h)
+
+    def run(self, ins, outs, rng=None, sweeps=1, stream=None):
+        """gscl_do_all_program."""
+        check(lib().gscl_do_all_program(self.handle, _handles(ins), len(ins), _handles(outs), len(outs), _range(rng),
+                                        int(sweeps), stream_ptr(stream)))
 
 
 def do_diamond(op, ins, outs, rng=None, stream=None):

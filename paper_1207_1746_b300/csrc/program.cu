@@ -1,0 +1,358 @@
+// Point operators compiled at run time.
+//
+// In the paper a stencil operator is a C++ function object compiled with the
+// program (Section 3, Fig. 1b), so any arithmetic can run at each core
+// element.  Here an operator can also arrive as source text: a block of CUDA
+// C++ statements that reads inputs through in0(dx, dy, dz) .. in7(..), may
+// use the core element's index (i, j, k) as the paper's stateful stencils do,
+// and assigns out0 .. out2.  NVRTC compiles it into a do_all kernel for
+// sm_103a when the program is created; the module is loaded on a device at
+// its first launch there.
+//
+// The kernel is a plain one: a 32 x 8 block of threads per (x, y) tile of the
+// range, each thread walking z with a grid-stride loop, every read a load
+// from global memory (L1 and L2 keep the neighbours of adjacent elements).
+// Each read checks its offset against the reach declared at creation, so a
+// body that reads farther stays inside the grids: the read returns 0 and
+// sets bit 1 of the device error word, which gscl_sync reports as
+// GSCL_ERR_RANGE.
+//
+// NVRTC is opened with dlopen and the driver's module calls are taken from
+// the runtime (cudaGetDriverEntryPointByVersion), so the library loads on
+// machines without either.
+#include <cuda.h>
+#include <dlfcn.h>
+#include <nvrtc.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sweep_host.h"
+
+namespace gscl {
+namespace {
+
+// ------------------------------------------------------------------ NVRTC
+struct Nvrtc {
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+  bool ok = false;
+};
+
+const Nvrtc &nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    const char *names[] = {"libnvrtc.so.13", "libnvrtc.so"};
+    void *h = nullptr;
+    for (const char *nm : names)
+      if ((h = dlopen(nm, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) return;
+    n.create = (decltype(n.create))dlsym(h, "nvrtcCreateProgram");
+    n.compile = (decltype(n.compile))dlsym(h, "nvrtcCompileProgram");
+    n.log_size = (decltype(n.log_size))dlsym(h, "nvrtcGetProgramLogSize");
+    n.log = (decltype(n.log))dlsym(h, "nvrtcGetProgramLog");
+    n.cubin_size = (decltype(n.cubin_size))dlsym(h, "nvrtcGetCUBINSize");
+    n.cubin = (decltype(n.cubin))dlsym(h, "nvrtcGetCUBIN");
+    n.destroy = (decltype(n.destroy))dlsym(h, "nvrtcDestroyProgram");
+    n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+  });
+  return n;
+}
+
+// ------------------------------------------------------------------ driver module calls
+struct Driver {
+  decltype(&cuModuleLoadData) load = nullptr;
+  decltype(&cuModuleGetFunction) get = nullptr;
+  decltype(&cuLaunchKernel) launch = nullptr;
+  decltype(&cuModuleUnload) unload = nullptr;
+  bool ok = false;
+};
+
+const Driver &driver() {
+  static Driver d;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    auto get = [](const char *name) -> void * {
+      void *p = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      if (cudaGetDriverEntryPointByVersion(name, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+          q != cudaDriverEntryPointSuccess)
+        return nullptr;
+      return p;
+    };
+    d.load = (decltype(d.load))get("cuModuleLoadData");
+    d.get = (decltype(d.get))get("cuModuleGetFunction");
+    d.launch = (decltype(d.launch))get("cuLaunchKernel");
+    d.unload = (decltype(d.unload))get("cuModuleUnload");
+    d.ok = d.load && d.get && d.launch && d.unload;
+  });
+  return d;
+}
+
+// ------------------------------------------------------------------ kernel source
+// Parameters of the generated kernel; the source below declares the same
+// layout (every field 8 bytes).
+struct JitParams {
+  const void *in[kMaxIn];
+  long long in_pitch[kMaxIn], in_plane[kMaxIn];
+  void *out[kMaxOut_];
+  long long out_pitch[kMaxOut_], out_plane[kMaxOut_];
+  long long lo[3], hi[3];
+  int *err;
+};
+
+const char *kJitTemplate = R"SRC(
+typedef %s real;
+typedef %s gscl_stor;
+#define GSCL_RX %d
+#define GSCL_RY %d
+#define GSCL_RZ %d
+struct GsclJitParams {
+  const gscl_stor *in[%d];
+  long long in_pitch[%d], in_plane[%d];
+  gscl_stor *out[%d];
+  long long out_pitch[%d], out_plane[%d];
+  long long lo[3], hi[3];
+  int *err;
+};
+__device__ __forceinline__ real gscl_ld(double x) { return (real)x; }
+__device__ __forceinline__ real gscl_ld(float x) { return (real)x; }
+__device__ __forceinline__ real gscl_ld(unsigned short x) { return (real)__uint_as_float((unsigned)x << 16); }
+__device__ __forceinline__ void gscl_st(double *p, real v) { *p = (double)v; }
+__device__ __forceinline__ void gscl_st(float *p, real v) { *p = (float)v; }
+// float -> bfloat16, round to nearest even on the bit pattern (NaN kept quiet)
+__device__ __forceinline__ void gscl_st(unsigned short *p, real v) {
+  unsigned u = __float_as_uint((float)v);
+  if ((u & 0x7fffffffu) > 0x7f800000u) { *p = (unsigned short)((u >> 16) | 0x40u); return; }
+  u += 0x7fffu + ((u >> 16) & 1u);
+  *p = (unsigned short)(u >> 16);
+}
+extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel(const __grid_constant__ GsclJitParams P) {
+  const long long i = P.lo[0] + (long long)blockIdx.x * 32 + threadIdx.x;
+  const long long j = P.lo[1] + (long long)blockIdx.y * 8 + threadIdx.y;
+  if (i >= P.hi[0] || j >= P.hi[1]) return;
+  bool gscl_bad = false;
+  for (long long k = P.lo[2] + blockIdx.z; k < P.hi[2]; k += gridDim.z) {
+    auto gscl_rd = [&](int a, int dx, int dy, int dz) -> real {
+      if (dx < -GSCL_RX || dx > GSCL_RX || dy < -GSCL_RY || dy > GSCL_RY || dz < -GSCL_RZ || dz > GSCL_RZ) {
+        gscl_bad = true;
+        return (real)0;
+      }
+      return gscl_ld(P.in[a][(k + dz) * P.in_plane[a] + (j + dy) * P.in_pitch[a] + (i + dx)]);
+    };
+%s
+    real value = 0;
+%s
+    {
+%s
+    }
+    (void)value;
+%s
+  }
+  if (gscl_bad) atomicOr(P.err, 2);
+}
+)SRC";
+
+std::string make_source(const char *body, int n_in, int n_out, int dtype, const int32_t reach[3]) {
+  std::string defs, decl, stores;
+  for (int a = 0; a < n_in; ++a)
+    defs += "#define in" + std::to_string(a) + "(dx, dy, dz) gscl_rd(" + std::to_string(a) + ", (dx), (dy), (dz))\n";
+  for (int m = 0; m < n_out; ++m) {
+    decl += "    real out" + std::to_string(m) + " = 0;\n";
+    stores += "    gscl_st(P.out[" + std::to_string(m) + "] + k * P.out_plane[" + std::to_string(m) + "] + j * P.out_pitch[" +
+              std::to_string(m) + "] + i, out" + std::to_string(m) + ");\n";
+  }
+  const char *real = dtype == GSCL_F64 ? "double" : "float";
+  const char *stor = dtype == GSCL_F64 ? "double" : dtype == GSCL_F32 ? "float" : "unsigned short";
+  // the generated struct has fixed-size arrays like JitParams
+  std::vector<char> buf(strlen(kJitTemplate) + defs.size() + decl.size() + strlen(body) + stores.size() + 512);
+  snprintf(buf.data(), buf.size(), kJitTemplate, real, stor, reach[0], reach[1], reach[2], kMaxIn, kMaxIn, kMaxIn,
+           kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(), body, stores.c_str());
+  return std::string(buf.data());
+}
+
+// ------------------------------------------------------------------ program registry
+struct Program {
+  int n_in = 0, n_out = 0, dtype = 0;
+  int32_t reach[3] = {0, 0, 0};
+  std::vector<char> cubin;
+  std::map<int, CUfunction> fn;  // per device
+  std::map<int, CUmodule> mod;
+};
+
+std::mutex g_prog_mu;
+std::map<uint64_t, Program> g_progs;
+uint64_t g_prog_next = 1;
+
+CUfunction program_function(Program &p, gscl_status *st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto it = p.fn.find(dev);
+  if (it != p.fn.end()) return it->second;
+  const Driver &d = driver();
+  if (!d.ok) {
+    *st = fail(GSCL_ERR_CUDA, "the driver's module functions are not available");
+    return nullptr;
+  }
+  cudaFree(nullptr);  // the runtime's context is current on this thread
+  CUmodule m = nullptr;
+  CUresult r = d.load(&m, p.cubin.data());
+  if (r != CUDA_SUCCESS) {
+    *st = fail(GSCL_ERR_CUDA, "loading the compiled operator failed (%d)", (int)r);
+    return nullptr;
+  }
+  CUfunction f = nullptr;
+  r = d.get(&f, m, "gscl_program_kernel");
+  if (r != CUDA_SUCCESS) {
+    d.unload(m);
+    *st = fail(GSCL_ERR_CUDA, "the compiled operator has no kernel (%d)", (int)r);
+    return nullptr;
+  }
+  p.mod[dev] = m;
+  p.fn[dev] = f;
+  return f;
+}
+
+}  // namespace
+}  // namespace gscl
+
+using namespace gscl;
+
+extern "C" gscl_status gscl_program_create(const char *body, int32_t n_in, int32_t n_out, int32_t dtype,
+                                           const int32_t reach[3], gscl_program *out) {
+  if (!body || !out || !reach) return fail(GSCL_ERR_INVALID, "body, reach and out are required");
+  if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
+  if (n_out < 1 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [1, %d]", n_out, kMaxOut_);
+  if (dtype != GSCL_F64 && dtype != GSCL_F32 && dtype != GSCL_BF16) return fail(GSCL_ERR_DTYPE, "unknown dtype");
+  for (int a = 0; a < 3; ++a)
+    if (reach[a] < 0 || reach[a] > 64) return fail(GSCL_ERR_INVALID, "reach[%d] = %d outside [0, 64]", a, reach[a]);
+  const Nvrtc &nv = nvrtc();
+  if (!nv.ok) return fail(GSCL_ERR_UNSUPPORTED, "NVRTC (libnvrtc.so) is not available");
+  const std::string src = make_source(body, n_in, n_out, dtype, reach);
+  nvrtcProgram prog = nullptr;
+  if (nv.create(&prog, src.c_str(), "gscl_program.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
+    return fail(GSCL_ERR_INVALID, "NVRTC could not create the program");
+  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device", "--diag-suppress=177,550"};
+  const nvrtcResult cr = nv.compile(prog, 4, opts);
+  if (cr != NVRTC_SUCCESS) {
+    size_t n = 0;
+    nv.log_size(prog, &n);
+    std::string log(n + 1, '\0');
+    if (n) nv.log(prog, &log[0]);
+    nv.destroy(&prog);
+    return fail(GSCL_ERR_INVALID, "the operator did not compile: %s", log.c_str());
+  }
+  size_t n = 0;
+  nv.cubin_size(prog, &n);
+  Program p;
+  p.cubin.resize(n);
+  nv.cubin(prog, p.cubin.data());
+  nv.destroy(&prog);
+  p.n_in = n_in;
+  p.n_out = n_out;
+  p.dtype = dtype;
+  for (int a = 0; a < 3; ++a) p.reach[a] = reach[a];
+  std::lock_guard<std::mutex> lk(g_prog_mu);
+  const uint64_t h = g_prog_next++;
+  g_progs[h] = std::move(p);
+  *out = h;
+  return GSCL_OK;
+}
+
+extern "C" gscl_status gscl_program_destroy(gscl_program h) {
+  std::lock_guard<std::mutex> lk(g_prog_mu);
+  auto it = g_progs.find(h);
+  if (it == g_progs.end()) return fail(GSCL_ERR_STATE, "no such program");
+  const Driver &d = driver();
+  if (d.ok) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    for (auto &m : it->second.mod) {
+      cudaSetDevice(m.first);
+      d.unload(m.second);
+    }
+    cudaSetDevice(cur);
+  }
+  g_progs.erase(it);
+  return GSCL_OK;
+}
+
+extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                                           int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream) {
+  if (sweeps < 1) return fail(GSCL_ERR_INVALID, "sweeps must be >= 1");
+  std::lock_guard<std::mutex> lk(g_prog_mu);
+  auto it = g_progs.find(h);
+  if (it == g_progs.end()) return fail(GSCL_ERR_STATE, "no such program");
+  Program &p = it->second;
+  if (n_in != p.n_in || n_out != p.n_out)
+    return fail(GSCL_ERR_INVALID, "the program was compiled for %d inputs and %d outputs", p.n_in, p.n_out);
+  // bind with the corners of the declared reach of every input: the range and
+  // halo checks, and the alias rule (an output may be an input only with reach 0)
+  std::vector<gscl_term> terms;
+  for (int a = 0; a < n_in; ++a)
+    for (int s = -1; s <= 1; s += 2)
+      terms.push_back(gscl_term{(int8_t)(s * p.reach[0]), (int8_t)(s * p.reach[1]), (int8_t)(s * p.reach[2]),
+                                (uint8_t)a, GSCL_NONE, GSCL_VALUE, 0, 0.0});
+  gscl_stencil st{(int32_t)terms.size(), 0, terms.data()};
+  Bound b;
+  if (gscl_status s = bind(&st, false, in, n_in, out, n_out, range, &b)) return s;
+  if (b.in[0].dtype != p.dtype) return fail(GSCL_ERR_DTYPE, "the program was compiled for another dtype");
+  if (b.empty) return GSCL_OK;
+  if (sweeps > 1) {
+    const Grid &a = b.in[0], &c = b.out[0];
+    if (a.halo[0] != c.halo[0] || a.halo[1] != c.halo[1] || a.halo[2] != c.halo[2])
+      return fail(GSCL_ERR_SHAPE, "multi-sweep ping-pong needs in[0] and out[0] of identical layout");
+    if (overlaps(a, c)) return fail(GSCL_ERR_ALIAS, "multi-sweep ping-pong needs distinct in[0] and out[0]");
+  }
+  gscl_status fst = GSCL_OK;
+  CUfunction f = program_function(p, &fst);
+  if (!f) return fst;
+  int *err = device_error_word();
+  if (!err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
+  JitParams P;
+  memset(&P, 0, sizeof P);
+  for (int a = 0; a < n_in; ++a) {
+    P.in_pitch[a] = b.in[a].pitch;
+    P.in_plane[a] = b.in[a].plane;
+  }
+  for (int m = 0; m < n_out; ++m) {
+    P.out_pitch[m] = b.out[m].pitch;
+    P.out_plane[m] = b.out[m].plane;
+  }
+  for (int a = 0; a < 3; ++a) {
+    P.lo[a] = b.lo[a];
+    P.hi[a] = b.hi[a];
+  }
+  P.err = err;
+  const long long nx = b.hi[0] - b.lo[0], ny = b.hi[1] - b.lo[1], nz = b.hi[2] - b.lo[2];
+  const unsigned gx = (unsigned)((nx + 31) / 32), gy = (unsigned)((ny + 7) / 8);
+  const long long target = (long long)sm_count() * 8;  // 8 CTAs of 256 threads per SM
+  const unsigned gz = (unsigned)std::max(1LL, std::min(nz, (target + gx * gy - 1) / ((long long)gx * gy)));
+  if (gy > 65535 || gz > 65535) return fail(GSCL_ERR_UNSUPPORTED, "range too large for one launch");
+  const Driver &d = driver();
+  Grid src = b.in[0], dst = b.out[0];
+  for (int s = 0; s < sweeps; ++s) {
+    for (int a = 0; a < n_in; ++a) P.in[a] = b.in[a].elem_ptr(0, 0, 0);
+    for (int m = 0; m < n_out; ++m) P.out[m] = b.out[m].elem_ptr(0, 0, 0);
+    P.in[0] = src.elem_ptr(0, 0, 0);
+    for (int a = 1; a < n_in; ++a)  // another input naming the ping-pong grid follows it
+      if (b.in_h[a] == b.in_h[0]) P.in[a] = src.elem_ptr(0, 0, 0);
+    P.out[0] = dst.elem_ptr(0, 0, 0);
+    void *args[] = {&P};
+    CUresult r = d.launch(f, gx, gy, gz, 32, 8, 1, 0, (CUstream)stream, args, nullptr);
+    if (r != CUDA_SUCCESS) return fail(GSCL_ERR_CUDA, "launching the compiled operator failed (%d)", (int)r);
+    std::swap(src, dst);
+  }
+  if (sweeps > 1 && sweeps % 2 == 0) return swap_storage(in[0], out[0]);
+  return GSCL_OK;
+}

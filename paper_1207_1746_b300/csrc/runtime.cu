@@ -142,7 +142,8 @@ int max_smem_per_block() {
   return v;
 }
 
-// One int per device: bit 0 = a bounded wait timed out.  A __device__
+// One int per device: bit 0 = a bounded wait timed out, bit 1 = a run-time
+// compiled operator read outside its declared reach.  A __device__
 // variable exists once per device and is zero when the module loads.  Host
 // code reaches it only through cudaGetSymbolAddress.
 __device__ int g_device_error;
@@ -350,6 +351,7 @@ gscl_status gscl_sync(void *stream) {
   if (flag) {
     int zero = 0;
     cudaMemcpy(word, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (flag & 2) return fail(GSCL_ERR_RANGE, "a run-time compiled operator read outside its declared reach");
     return fail(GSCL_ERR_TIMEOUT, "a bounded device-side wait gave up (flag %d)", flag);
   }
   return GSCL_OK;

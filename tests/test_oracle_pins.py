@@ -659,3 +659,56 @@ def test_diamond_lexicographic_gauss_seidel_rate():
     rate = norms[-1] / norms[-2]
     want = math.cos(math.pi / 11) ** 2
     assert abs(rate - want) <= 2e-4 * want, (rate, want)
+
+
+# ------------------------------------------------------------------ run-time point operators
+HEAT_BODY = ("out0 = 0.25 * in0(0,0,0) + 0.125 * (in0(1,0,0) + in0(-1,0,0) + in0(0,1,0) + in0(0,-1,0)"
+             " + in0(0,0,1) + in0(0,0,-1)) + 0.125 * in1(0,0,0);")
+
+
+def test_program_linear_body_equals_the_term_list():
+    """The heat operator written as a body gives what the term-list oracle
+    gives (a separate implementation), up to the order of the additions."""
+    n, h = (9, 7, 6), (1, 1, 1)
+    rng = np.random.default_rng(51)
+    u, f = O.zeros(n, h), O.zeros(n, h)
+    u.a[...] = rng.uniform(-1, 1, u.a.shape)
+    f.a[...] = rng.uniform(-1, 1, f.a.shape)
+    a, b = O.zeros(n, h), O.zeros(n, h)
+    O.Program(HEAT_BODY, 2, 1).run([u, f], [a])
+    terms = ([(0, 0, 0, 0, O.NONE, 0, 0.25)] + [(dx, dy, dz, 0, O.NONE, 0, 0.125) for dx, dy, dz in AXIAL6]
+             + [(0, 0, 0, 1, O.NONE, 0, 0.125)])
+    O.do_all(terms, [u, f], [b])
+    assert np.max(np.abs(a.a - b.a)) <= 8 * EPS
+
+
+def test_program_index_and_products_exact():
+    """The index query of a stateful operator and a product of reads, on
+    integer data: exact."""
+    n, h = (6, 5, 4), (1, 1, 1)
+    u = grid_from(lambda i, j, k: i - 2 * j + 3 * k, n, h)
+    a, b = O.zeros(n, h), O.zeros(n, h)
+    O.Program("out0 = (real)(i + 10 * j + 100 * k); out1 = in0(0,0,0) * in0(1,0,0);", 1, 2).run([u], [a, b])
+    k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
+    assert np.array_equal(a.interior(), i + 10 * j + 100 * k)
+    assert np.array_equal(b.interior(), (i - 2 * j + 3 * k) * (i + 1 - 2 * j + 3 * k))
+
+
+def test_program_laplacian_of_a_quadratic_is_constant():
+    n, h = (7, 6, 5), (1, 1, 1)
+    u = grid_from(lambda i, j, k: 2 * i * i - j * j + 3 * k * k + i * j, n, h)
+    a = O.zeros(n, h)
+    body = ("out0 = in0(1,0,0) + in0(-1,0,0) + in0(0,1,0) + in0(0,-1,0) + in0(0,0,1) + in0(0,0,-1)"
+            " - 6.0 * in0(0,0,0);")
+    O.Program(body, 1, 1).run([u], [a])
+    assert np.all(a.interior() == 2 * (2 - 1 + 3))
+
+
+def test_program_reads_beyond_the_reach_are_refused():
+    n, h = (5, 4, 3), (2, 2, 2)
+    u = grid_from(lambda i, j, k: i + j + k + 1.0, n, h)
+    a = O.zeros(n, h)
+    p = O.Program("out0 = in0(2,0,0) + in0(0,0,0);", 1, 1, reach=(1, 1, 1))
+    p.run([u], [a])
+    assert p.outside == 5 * 4 * 3
+    assert np.array_equal(a.interior(), u.interior())
