@@ -592,6 +592,50 @@ def run_redblack(steps, warmup, n=256, iters=10, solve_n=128, solve=True):
     return out
 
 
+# ------------------------------------------------------------------ run-time compiled operators
+# (real) casts keep FP32 programs in FP32 arithmetic (a double literal would
+# promote the expression to FP64, as C++ does)
+HEAT_BODY = ("out0 = (real)0.25 * in0(0,0,0) + (real)0.125 * (in0(1,0,0) + in0(-1,0,0) + in0(0,1,0)"
+             " + in0(0,-1,0) + in0(0,0,1) + in0(0,0,-1)) + (real)0.125 * in1(0,0,0);")
+
+
+def run_program(dtype, steps, warmup, n=256, sweeps=20):
+    """The heat sweep of the default workload (lam = 1/8) given as a body of
+    CUDA C++ statements and compiled at run time (NVRTC), `sweeps` ping-pong
+    sweeps per step on n^3, against the same sweeps through gscl_do_all's
+    compiled operator table.  Returns per-sweep device times."""
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    h = (1, 1, 1)
+    u0, f0 = I.heat3d(SEED, n)
+    u, v, f = (B.Grid((n,) * 3, h, dtype).upload(a) for a in (u0, u0, f0))
+    t = time.perf_counter()
+    prog = B.Program(HEAT_BODY, 2, 1, dtype, (1, 1, 1))
+    compile_s = time.perf_counter() - t
+    op = B.Stencil(S.heat7(LAM))
+    stream = torch.cuda.current_stream()
+    out = {"compile_s": compile_s}
+    for key, fn in (("program", lambda: prog.run([u, f], [v], sweeps=sweeps)),
+                    ("table", lambda: B.do_all(op, [u, f], [v], sweeps=sweeps))):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[key] = e0.elapsed_time(e1) / (steps * sweeps)
+    B.sync()
+    out["points"] = n ** 3
+    return out
+
+
 # ------------------------------------------------------------------ do_diamond workload
 def run_diamond(steps, warmup, n=(512, 512, 64), single=(4096, 4096, 1)):
     """do_diamond (Section 3): one natural-order Gauss-Seidel sweep of the
@@ -790,13 +834,14 @@ def main():
                          "FMA microbenchmark (the printed numbers are not benchmark values)")
     ap.add_argument("--workload", default="heat3d",
                     choices=["heat3d", "batched", "serving", "laplace2d", "climate", "ordered", "redblack",
-                             "diamond"],
+                             "diamond", "program"],
                     help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances; "
                          "serving: Poisson solve requests; laplace2d: 256^2 FP64 Jacobi, 100 sweeps; "
                          "climate: 8 -> 3 grid operator on 256 x 256 x 80, FP64 and FP32, 50 sweeps; "
                          "ordered: do_k_inc bidiagonal solve down 256 x 256 columns of 80; "
                          "redblack: red-black SOR on the 256^3 FP64 Poisson problem; "
-                         "diamond: natural-order Gauss-Seidel (do_diamond) on 64 planes of 512^2 FP64")
+                         "diamond: natural-order Gauss-Seidel (do_diamond) on 64 planes of 512^2 FP64; "
+                         "program: the 256^3 heat sweep as a run-time compiled body")
     args = ap.parse_args()
     if args.profile:
         global PROFILE
@@ -915,6 +960,37 @@ def main():
                                                   "traffic": profile_traffic("climate_f32"),
                                                   "peak_source": "measured"}}},
                 "gpu_launches": 2 * args.steps * 50}
+        if dist.rank == 0:
+            print(json.dumps(line))
+        return
+    if args.workload == "program":
+        peak_hbm = peaks.get("hbm_gbs", 6400.0)
+        fma = B_fma()
+        res = {}
+        for dt in ("f64", "f32"):
+            r = run_program(dt, args.steps, args.warmup)
+            t = dist.max(r["program"])
+            if dt == "f64":   # 8 FMAs per point on the FP64 pipe
+                ach = 2 * 8 * r["points"] / (t * 1e-3) / 1e12
+                roof = {"bound": "alu", "achieved": round(ach, 4), "peak": fma, "unit": "TFLOP/s",
+                        "frac": round(ach / fma, 4) if fma == fma else None, "traffic": None,
+                        "peak_source": "measured FP64 FMA rate (gscl_fma_throughput)"}
+            else:
+                gbs = BYTES_PER_PT["f32"] * r["points"] / (t * 1e-3) / 1e9
+                roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm, "unit": "GB/s",
+                        "frac": round(gbs / peak_hbm, 4), "traffic": None, "peak_source": "measured"}
+            res[dt] = {"value": round(dist.world * r["points"] / (t * 1e-3) / 1e9, 3), "sweep_ms": round(t, 4),
+                       "table_sweep_ms": round(r["table"], 4), "program_vs_table": round(r["table"] / t, 3),
+                       "compile_s": round(r["compile_s"], 3), "roofline": roof}
+        line = {"metric": "GPoint-updates/s", "value": res["f64"]["value"], "unit": "GPoint-updates/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(res["f64"]["sweep_ms"] * 20, 4), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "program: the 256^3 7-point heat sweep (lam 1/8) as a body of CUDA C++ "
+                                       "statements compiled at run time, 20 ping-pong sweeps per step",
+                           "l2": "working set (3 grids) larger than the 126 MB L2, no flush"},
+                "roofline": res["f64"]["roofline"], "f64": res["f64"], "variants": {"f32": res["f32"]},
+                "gpu_launches": args.steps * 20}
         if dist.rank == 0:
             print(json.dumps(line))
         return

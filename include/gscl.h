@@ -540,7 +540,9 @@ gscl_status gscl_sync(void *stream);
  *    paper's stateful stencils query indices;
  *  - assigns out0 .. out<n_out - 1> (type real, starting at 0), stored at the
  *    core element after the body has run;
- *  - may call CUDA's device math functions.
+ *  - may call CUDA's device math functions.  C++ promotion applies: a double
+ *    literal makes an FP32 program's expression FP64; write (real) casts or
+ *    f-suffixed literals to keep FP32 arithmetic.
  * `reach[3]` bounds |dx|, |dy|, |dz| of every read.  A read beyond it returns
  * 0, touches no memory and makes the next gscl_sync return GSCL_ERR_RANGE.
  *

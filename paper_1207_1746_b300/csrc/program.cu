@@ -10,7 +10,7 @@
 // its first launch there.
 //
 // The kernel is a plain one: a 32 x 8 block of threads per (x, y) tile of the
-// range, each thread walking z with a grid-stride loop, every read a load
+// range, each CTA walking a run of planes two at a time, every read a load
 // from global memory (L1 and L2 keep the neighbours of adjacent elements).
 // Each read checks its offset against the reach declared at creation, so a
 // body that reads farther stays inside the grids: the read returns 0 and
@@ -128,6 +128,11 @@ struct GsclJitParams {
 __device__ __forceinline__ real gscl_ld(double x) { return (real)x; }
 __device__ __forceinline__ real gscl_ld(float x) { return (real)x; }
 __device__ __forceinline__ real gscl_ld(unsigned short x) { return (real)__uint_as_float((unsigned)x << 16); }
+__device__ __forceinline__ unsigned short __ldg(const unsigned short *p) {
+  unsigned short v;
+  asm("ld.global.nc.u16 %%0, [%%1];" : "=h"(v) : "l"(p));
+  return v;
+}
 __device__ __forceinline__ void gscl_st(double *p, real v) { *p = (double)v; }
 __device__ __forceinline__ void gscl_st(float *p, real v) { *p = (float)v; }
 // float -> bfloat16, round to nearest even on the bit pattern (NaN kept quiet)
@@ -137,19 +142,25 @@ __device__ __forceinline__ void gscl_st(unsigned short *p, real v) {
   u += 0x7fffu + ((u >> 16) & 1u);
   *p = (unsigned short)(u >> 16);
 }
-extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel(const __grid_constant__ GsclJitParams P) {
+// NC: no output shares storage with an input, so reads take the read-only path
+template <bool NC>
+__device__ __forceinline__ void gscl_program_body(const GsclJitParams &P) {
   const long long i = P.lo[0] + (long long)blockIdx.x * 32 + threadIdx.x;
   const long long j = P.lo[1] + (long long)blockIdx.y * 8 + threadIdx.y;
   if (i >= P.hi[0] || j >= P.hi[1]) return;
   bool gscl_bad = false;
-  for (long long k = P.lo[2] + blockIdx.z; k < P.hi[2]; k += gridDim.z) {
-    auto gscl_rd = [&](int a, int dx, int dy, int dz) -> real {
-      if (dx < -GSCL_RX || dx > GSCL_RX || dy < -GSCL_RY || dy > GSCL_RY || dz < -GSCL_RZ || dz > GSCL_RZ) {
-        gscl_bad = true;
-        return (real)0;
-      }
-      return gscl_ld(P.in[a][(k + dz) * P.in_plane[a] + (j + dy) * P.in_pitch[a] + (i + dx)]);
-    };
+  auto gscl_rd = [&](int a, long long k, int dx, int dy, int dz) -> real {
+    if (dx < -GSCL_RX || dx > GSCL_RX || dy < -GSCL_RY || dy > GSCL_RY || dz < -GSCL_RZ || dz > GSCL_RZ) {
+      gscl_bad = true;
+      return (real)0;
+    }
+    const gscl_stor *p = P.in[a] + k * P.in_plane[a] + j * P.in_pitch[a] + i;
+    const long long off = dz * P.in_plane[a] + dy * P.in_pitch[a] + dx;
+    if (NC) return gscl_ld(__ldg(p + off));
+    return gscl_ld(p[off]);
+  };
+  // the body at element (i, j, k), its outputs returned through o[]
+  auto gscl_eval = [&](long long k, real *gscl_o) {
 %s
     real value = 0;
 %s
@@ -158,26 +169,49 @@ extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel(const __gr
     }
     (void)value;
 %s
+  };
+  // this CTA's run of planes, two at a time: both elements' reads are issued
+  // before either is stored, and neighbouring planes share their reads in L1
+  const long long nz = P.hi[2] - P.lo[2];
+  const long long chunk = (nz + gridDim.z - 1) / gridDim.z;
+  const long long k0 = P.lo[2] + (long long)blockIdx.z * chunk;
+  const long long k1 = k0 + chunk < P.hi[2] ? k0 + chunk : P.hi[2];
+  for (long long k = k0; k < k1; k += 2) {
+    real oa[%d], ob[%d];
+    gscl_eval(k, oa);
+    const bool two = k + 1 < k1;
+    if (two) gscl_eval(k + 1, ob);
+%s
   }
   if (gscl_bad) atomicOr(P.err, 2);
+}
+extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel(const __grid_constant__ GsclJitParams P) {
+  gscl_program_body<false>(P);
+}
+extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel_nc(const __grid_constant__ GsclJitParams P) {
+  gscl_program_body<true>(P);
 }
 )SRC";
 
 std::string make_source(const char *body, int n_in, int n_out, int dtype, const int32_t reach[3]) {
-  std::string defs, decl, stores;
+  std::string defs, decl, ret, stores;
   for (int a = 0; a < n_in; ++a)
-    defs += "#define in" + std::to_string(a) + "(dx, dy, dz) gscl_rd(" + std::to_string(a) + ", (dx), (dy), (dz))\n";
+    defs += "#define in" + std::to_string(a) + "(dx, dy, dz) gscl_rd(" + std::to_string(a) + ", k, (dx), (dy), (dz))\n";
   for (int m = 0; m < n_out; ++m) {
-    decl += "    real out" + std::to_string(m) + " = 0;\n";
-    stores += "    gscl_st(P.out[" + std::to_string(m) + "] + k * P.out_plane[" + std::to_string(m) + "] + j * P.out_pitch[" +
-              std::to_string(m) + "] + i, out" + std::to_string(m) + ");\n";
+    const std::string M = std::to_string(m);
+    decl += "    real out" + M + " = 0;\n";
+    ret += "    gscl_o[" + M + "] = out" + M + ";\n";
+    stores += "    gscl_st(P.out[" + M + "] + k * P.out_plane[" + M + "] + j * P.out_pitch[" + M + "] + i, oa[" + M +
+              "]);\n    if (two) gscl_st(P.out[" + M + "] + (k + 1) * P.out_plane[" + M + "] + j * P.out_pitch[" + M +
+              "] + i, ob[" + M + "]);\n";
   }
   const char *real = dtype == GSCL_F64 ? "double" : "float";
   const char *stor = dtype == GSCL_F64 ? "double" : dtype == GSCL_F32 ? "float" : "unsigned short";
   // the generated struct has fixed-size arrays like JitParams
-  std::vector<char> buf(strlen(kJitTemplate) + defs.size() + decl.size() + strlen(body) + stores.size() + 512);
+  std::vector<char> buf(strlen(kJitTemplate) + defs.size() + decl.size() + strlen(body) + ret.size() +
+                        stores.size() + 512);
   snprintf(buf.data(), buf.size(), kJitTemplate, real, stor, reach[0], reach[1], reach[2], kMaxIn, kMaxIn, kMaxIn,
-           kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(), body, stores.c_str());
+           kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(), body, ret.c_str(), n_out, n_out, stores.c_str());
   return std::string(buf.data());
 }
 
@@ -186,19 +220,20 @@ struct Program {
   int n_in = 0, n_out = 0, dtype = 0;
   int32_t reach[3] = {0, 0, 0};
   std::vector<char> cubin;
-  std::map<int, CUfunction> fn;  // per device
+  std::map<int, CUfunction> fn, fn_nc;  // per device: plain reads / read-only path
   std::map<int, CUmodule> mod;
 };
 
 std::mutex g_prog_mu;
 std::map<uint64_t, Program> g_progs;
 uint64_t g_prog_next = 1;
+std::map<std::string, std::vector<char>> g_cubins;  // generated source -> its cubin (compile once per process)
 
-CUfunction program_function(Program &p, gscl_status *st) {
+CUfunction program_function(Program &p, bool nc, gscl_status *st) {
   int dev = 0;
   cudaGetDevice(&dev);
   auto it = p.fn.find(dev);
-  if (it != p.fn.end()) return it->second;
+  if (it != p.fn.end()) return nc ? p.fn_nc[dev] : it->second;
   const Driver &d = driver();
   if (!d.ok) {
     *st = fail(GSCL_ERR_CUDA, "the driver's module functions are not available");
@@ -211,8 +246,9 @@ CUfunction program_function(Program &p, gscl_status *st) {
     *st = fail(GSCL_ERR_CUDA, "loading the compiled operator failed (%d)", (int)r);
     return nullptr;
   }
-  CUfunction f = nullptr;
+  CUfunction f = nullptr, fnc = nullptr;
   r = d.get(&f, m, "gscl_program_kernel");
+  if (r == CUDA_SUCCESS) r = d.get(&fnc, m, "gscl_program_kernel_nc");
   if (r != CUDA_SUCCESS) {
     d.unload(m);
     *st = fail(GSCL_ERR_CUDA, "the compiled operator has no kernel (%d)", (int)r);
@@ -220,7 +256,8 @@ CUfunction program_function(Program &p, gscl_status *st) {
   }
   p.mod[dev] = m;
   p.fn[dev] = f;
-  return f;
+  p.fn_nc[dev] = fnc;
+  return nc ? fnc : f;
 }
 
 }  // namespace
@@ -239,6 +276,22 @@ extern "C" gscl_status gscl_program_create(const char *body, int32_t n_in, int32
   const Nvrtc &nv = nvrtc();
   if (!nv.ok) return fail(GSCL_ERR_UNSUPPORTED, "NVRTC (libnvrtc.so) is not available");
   const std::string src = make_source(body, n_in, n_out, dtype, reach);
+  Program p;
+  p.n_in = n_in;
+  p.n_out = n_out;
+  p.dtype = dtype;
+  for (int a = 0; a < 3; ++a) p.reach[a] = reach[a];
+  {
+    std::lock_guard<std::mutex> lk(g_prog_mu);
+    auto c = g_cubins.find(src);
+    if (c != g_cubins.end()) {
+      p.cubin = c->second;
+      const uint64_t h = g_prog_next++;
+      g_progs[h] = std::move(p);
+      *out = h;
+      return GSCL_OK;
+    }
+  }
   nvrtcProgram prog = nullptr;
   if (nv.create(&prog, src.c_str(), "gscl_program.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS)
     return fail(GSCL_ERR_INVALID, "NVRTC could not create the program");
@@ -254,15 +307,11 @@ extern "C" gscl_status gscl_program_create(const char *body, int32_t n_in, int32
   }
   size_t n = 0;
   nv.cubin_size(prog, &n);
-  Program p;
   p.cubin.resize(n);
   nv.cubin(prog, p.cubin.data());
   nv.destroy(&prog);
-  p.n_in = n_in;
-  p.n_out = n_out;
-  p.dtype = dtype;
-  for (int a = 0; a < 3; ++a) p.reach[a] = reach[a];
   std::lock_guard<std::mutex> lk(g_prog_mu);
+  g_cubins[src] = p.cubin;
   const uint64_t h = g_prog_next++;
   g_progs[h] = std::move(p);
   *out = h;
@@ -314,8 +363,11 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
       return fail(GSCL_ERR_SHAPE, "multi-sweep ping-pong needs in[0] and out[0] of identical layout");
     if (overlaps(a, c)) return fail(GSCL_ERR_ALIAS, "multi-sweep ping-pong needs distinct in[0] and out[0]");
   }
+  bool shared = false;  // an output is also an input (reach 0, point-wise in place)
+  for (int m = 0; m < n_out; ++m)
+    for (int a = 0; a < n_in; ++a) shared |= overlaps(b.out[m], b.in[a]);
   gscl_status fst = GSCL_OK;
-  CUfunction f = program_function(p, &fst);
+  CUfunction f = program_function(p, !shared, &fst);
   if (!f) return fst;
   int *err = device_error_word();
   if (!err) return fail(GSCL_ERR_CUDA, "device error word unavailable");

@@ -258,3 +258,50 @@ def test_diamond_validation_errors():
     ok = [(-1, 0, 0, 0, B.NONE, 0, 1.0), (0, -1, 0, 0, B.NONE, 0, 1.0), (-1, -1, 0, 0, B.NONE, 0, -1.0),
           (1, 1, 0, 0, B.NONE, 0, 0.5), (0, 0, 0, 1, B.NONE, 0, 1.0), (1, -1, 1, 1, B.NONE, 0, 1.0)]
     assert diamond_status(ok, [x, f], [x], rng=empty) == 0
+
+
+def test_program_compiles_on_the_host_and_reports_errors():
+    """NVRTC compiles run-time operators without a GPU; a body that does not
+    compile is GSCL_ERR_INVALID with the compiler's message; arguments are
+    checked before compiling."""
+    p = B.Program("out0 = 0.5 * (in0(1,0,0) + in0(-1,0,0)) + sin(in1(0,0,0)) + (real)i;", 2, 1, "f64")
+    assert p.handle
+    for dt in ("f32", "bf16"):
+        assert B.Program("out0 = in0(0,0,0) * in0(0,0,0); out1 = (real)(i + j + k);", 1, 2, dt, (0, 0, 0)).handle
+    with pytest.raises(B.GsclError) as e:
+        B.Program("out0 = in0(0,0,0) +;", 1, 1)
+    assert e.value.status == 1 and b"did not compile" in B.lib().gscl_last_error()
+    with pytest.raises(B.GsclError) as e:
+        B.Program("out0 = in1(0,0,0);", 1, 1)          # only in0 exists
+    assert e.value.status == 1
+    with pytest.raises(B.GsclError) as e:
+        B.Program("out0 = 1;", 9, 1)
+    assert e.value.status == 10
+    with pytest.raises(B.GsclError) as e:
+        B.Program("out0 = 1;", 1, 1, reach=(-1, 0, 0))
+    assert e.value.status == 1
+    L = B.lib()
+    assert L.gscl_program_destroy(p.handle) == 0
+    assert L.gscl_program_destroy(p.handle) == 8
+    p.handle = 0
+
+
+def test_program_binding_rules():
+    """A program runs under do_all's range, halo and alias rules for its
+    declared reach; no GPU work happens for an empty range."""
+    u, v = FakeGrid((16, 8, 8), (1, 1, 1)), FakeGrid((16, 8, 8), (1, 1, 1))
+    fa, fb = FakeGrid((16, 8, 8), (1, 1, 1), "f32"), FakeGrid((16, 8, 8), (1, 1, 1), "f32")
+    p = B.Program("out0 = in0(1,0,0);", 1, 1, "f64", (1, 1, 1))
+    L = B.lib()
+
+    def run(prog, ins, outs, rng=None, sweeps=1):
+        return L.gscl_do_all_program(prog.handle, B._handles(ins), len(ins), B._handles(outs), len(outs),
+                                     B._range(rng), sweeps, None)
+
+    assert run(p, [u], [u]) == 3                         # in place needs reach 0
+    assert run(p, [u, v], [v]) == 1                      # compiled for one input
+    assert run(p, [fa], [fb]) == 4                       # compiled for FP64 grids
+    wide = B.Program("out0 = in0(0,0,0);", 1, 1, "f64", (2, 0, 0))
+    assert run(wide, [u], [v]) == 2                      # reach beyond the halo
+    assert run(p, [u], [v], sweeps=0) == 1
+    assert run(p, [u], [v], rng=((0, 0, 3), (16, 8, 3))) == 0
