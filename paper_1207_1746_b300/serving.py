@@ -23,6 +23,9 @@ Two solve modes:
             where Jacobi takes O(n^2).  Each active request runs its own
             launches (colouring is not batched); the residual is measured
             every `sor_check_every` iterations.
+  "mixed_rbsor" - the refinement of "mixed" with red-black SOR in FP32 as
+            the inner solver: r = f - A u in FP64, FP32 SOR on A d = r until
+            ||r - A d|| <= inner_tol ||r||, u += d in FP64.
 Each request follows the same sequence of operations whatever else is
 active, so its result does not depend on the mix (batched sweeps are
 bit-identical to single-grid ones; batched norms agree to rounding).
@@ -80,6 +83,8 @@ def _grid_bytes(n, dtype):
 def request_bytes(n, mode):
     if mode == "rbsor":
         return 2 * _grid_bytes(n, "f64")
+    if mode == "mixed_rbsor":
+        return 3 * _grid_bytes(n, "f64") + 2 * _grid_bytes(n, "f32")
     if mode == "fp64":
         return 3 * _grid_bytes(n, "f64")
     return 3 * _grid_bytes(n, "f64") + 3 * _grid_bytes(n, "f32")
@@ -88,8 +93,8 @@ def request_bytes(n, mode):
 class PoissonServer:
     def __init__(self, mode="mixed", hbm_budget=64 << 30, max_active=256, check_every=200, tol=1e-6,
                  inner_tol=1e-3, max_sweeps=2_000_000, keep_solution=False, use_graph=True, sor_check_every=20):
-        if mode not in ("mixed", "fp64", "rbsor"):
-            raise ValueError("mode is 'mixed', 'fp64' or 'rbsor'")
+        if mode not in ("mixed", "fp64", "rbsor", "mixed_rbsor"):
+            raise ValueError("mode is 'mixed', 'fp64', 'rbsor' or 'mixed_rbsor'")
         self.mode = mode
         self.sor_check_every = sor_check_every
         self.budget = hbm_budget
@@ -136,6 +141,13 @@ class PoissonServer:
         if self.mode == "rbsor":
             g["u"] = B.Grid(n, H, "f64").upload(np.zeros_like(req.f))
             g["f"] = B.Grid(n, H, "f64").upload(req.f)
+        elif self.mode == "mixed_rbsor":
+            z = np.zeros_like(req.f)
+            g["u"] = B.Grid(n, H, "f64").upload(z)
+            g["f"] = B.Grid(n, H, "f64").upload(req.f)
+            g["r"] = B.Grid(n, H, "f64").upload(z)
+            g["da"] = B.Grid(n, H, "f32").upload(z)
+            g["r32"] = B.Grid(n, H, "f32").upload(z)
         elif self.mode == "fp64":
             g["u"] = B.Grid(n, H, "f64").upload(np.zeros_like(req.f))
             g["v"] = B.Grid(n, H, "f64").upload(np.zeros_like(req.f))
@@ -150,7 +162,7 @@ class PoissonServer:
             g["r32"] = B.Grid(n, H, "f32").upload(z)
         slot = _Slot(req=req, grids=g, bytes=need)
         slot.norm_f = B.do_reduce(B.L2, None, [g["f"]])
-        if self.mode == "mixed":
+        if self.mode in ("mixed", "mixed_rbsor"):
             self._outer_start(slot, first=True)
         return slot
 
@@ -215,6 +227,20 @@ class PoissonServer:
                 rel = rv / s.norm_f
                 if rel <= self.tol or s.req.sweeps >= self.max_sweeps:
                     self._finish(s, rel)
+        elif self.mode == "mixed_rbsor":
+            k = self.sor_check_every
+            for i, s in enumerate(self.active):
+                g = s.grids
+                B.do_colored(self.sor_operator(s.req.n), [g["da"], g["r32"]], [g["da"]], color=0, half_sweeps=2 * k)
+                B.do_reduce(B.L2, self.resid, [g["da"], g["r32"]], result=res[i:i + 1])
+            r = res.cpu().numpy()
+            for s, rv in zip(self.active, r):
+                s.req.sweeps += k
+                s.phase_sweeps += k
+                if rv <= self.inner_tol * s.norm_r or s.req.sweeps >= self.max_sweeps:
+                    self._outer_start(s)
+                    if not s.done and s.req.sweeps >= self.max_sweeps:
+                        self._finish(s, s.norm_r / s.norm_f)
         elif self.mode == "fp64":
             # k - 1 plain sweeps, then the fused sweep that returns the residual of the iterate it reads
             insts = [([s.grids["u"], s.grids["f"]], [s.grids["v"]]) for s in self.active]

@@ -29,7 +29,7 @@ def poisson_matrix(n):
     return (sp.kron(sp.kron(Id, Id), T) + sp.kron(sp.kron(Id, T), Id) + sp.kron(sp.kron(T, Id), Id)).tocsc()
 
 
-@pytest.mark.parametrize("mode", ["mixed", "fp64", "rbsor"])
+@pytest.mark.parametrize("mode", ["mixed", "fp64", "rbsor", "mixed_rbsor"])
 def test_requests_converge_by_oracle_residual(mode):
     reqs = small_requests(4)
     srv = SV.PoissonServer(mode=mode, check_every=20, keep_solution=True)
@@ -44,7 +44,7 @@ def test_requests_converge_by_oracle_residual(mode):
         assert err <= 1e-4, (r.rid, err)
 
 
-@pytest.mark.parametrize("mode", ["mixed", "fp64", "rbsor"])
+@pytest.mark.parametrize("mode", ["mixed", "fp64", "rbsor", "mixed_rbsor"])
 def test_result_same_alone_and_in_the_mix(mode):
     target = small_requests(1, base=950)[0]
     alone = SV.PoissonServer(mode=mode, check_every=20, keep_solution=True)

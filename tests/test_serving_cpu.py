@@ -43,3 +43,18 @@ def test_slot_limit():
 
 def test_mixed_needs_more_memory_than_fp64_grids_alone():
     assert SV.request_bytes(64, "mixed") > SV.request_bytes(64, "fp64")
+
+
+def test_memory_per_mode():
+    """Grids held per request: FP64 Jacobi u, v, f; red-black SOR u, f in place;
+    the mixed modes add FP32 correction grids (two for red-black, in place)."""
+    g64 = SV.request_bytes(64, "rbsor") // 2
+    assert SV.request_bytes(64, "fp64") == 3 * g64
+    assert SV.request_bytes(64, "mixed_rbsor") < SV.request_bytes(64, "mixed")
+    assert SV.request_bytes(64, "mixed_rbsor") > SV.request_bytes(64, "fp64")
+
+
+def test_unknown_mode_rejected():
+    import pytest
+    with pytest.raises(ValueError):
+        SV.PoissonServer(mode="jacobi32")
