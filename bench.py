@@ -675,14 +675,16 @@ def run_diamond(steps, warmup, n=(512, 512, 64), single=(4096, 4096, 1)):
 
 # ------------------------------------------------------------------ serving workload
 def run_serving(sample=8, window_s=10.0, rate=200.0, time_cap=30.0, check_every=200):
-    """Poisson Jacobi solves (side uniform on 64..256, f uniform in [-1, 1),
-    stop at ||f - A u|| / ||f|| <= 1e-6).  (a) The first `sample` requests all
-    arriving at t = 0, served by the mixed-precision path, by the FP64 path
-    with continuous batching, and by the plain FP64 per-request path (one
-    request on the GPU at a time): solves/s and latency of each, and the
-    speedups.  (b) The literal arrival
-    process (Poisson, `rate` per second, seed 5050) over `window_s` seconds,
-    mixed path, stopped after `time_cap` seconds: completed, backlog, p50/p99."""
+    """Poisson solves (side uniform on 64..256, f uniform in [-1, 1), stop at
+    ||f - A u|| / ||f|| <= 1e-6).  (a) The first `sample` requests all
+    arriving at t = 0, served by every solve mode: Jacobi with continuous
+    batching in mixed precision and in FP64, FP64 Jacobi one request at a
+    time, red-black SOR in FP64 and as the FP32 inner solver of the mixed
+    refinement: solves/s and latency of each, and the speedups.  (b) The
+    literal arrival process (Poisson, `rate` per second, seed 5050) over
+    `window_s` seconds and (c) a load-scaled one at 70% of the measured
+    capacity, both served by the fastest mode of (a), stopped after
+    `time_cap` seconds: completed, backlog, p50/p99."""
     from paper_1207_1746_b300 import inputs as I
     from paper_1207_1746_b300 import serving as SV
 
@@ -705,21 +707,23 @@ def run_serving(sample=8, window_s=10.0, rate=200.0, time_cap=30.0, check_every=
     for mode in ("rbsor", "mixed_rbsor"):
         srv = SV.PoissonServer(mode=mode)
         closed[mode] = srv.run_trace(reqs(sample))
+    best = max(closed, key=lambda m: closed[m]["solves_per_s"])
+    best_mode = "fp64" if best == "fp64_per_request" else best
     # literal arrival rate: the offered load is far above capacity, so report the backlog
     arrivals = I.poisson_arrivals(rate, window_s)
-    srv = SV.PoissonServer(mode="mixed", check_every=check_every, max_active=32)
+    srv = SV.PoissonServer(mode=best_mode, check_every=check_every, max_active=32)
     trace = srv.run_trace(reqs(len(arrivals), arrivals), time_cap=time_cap)
     trace["rate_per_s"] = rate
     trace["window_s"] = window_s
-    # load-scaled: arrivals at 70% of the measured mixed-path capacity
-    scaled_rate = 0.7 * closed["mixed"]["solves_per_s"]
+    # load-scaled: arrivals at 70% of the measured capacity of that mode
+    scaled_rate = 0.7 * closed[best]["solves_per_s"]
     arr2 = I.poisson_arrivals(scaled_rate, 20.0)
-    srv = SV.PoissonServer(mode="mixed", check_every=check_every, max_active=32)
+    srv = SV.PoissonServer(mode=best_mode, check_every=check_every, max_active=32)
     scaled = srv.run_trace(reqs(len(arr2), arr2), time_cap=90.0)
     scaled["rate_per_s"] = scaled_rate
     scaled["window_s"] = 20.0
     sides = [I.poisson_request(r)[0] for r in range(sample)]
-    return {"closed": closed, "trace": trace, "scaled": scaled, "sample_sides": sides,
+    return {"closed": closed, "trace": trace, "scaled": scaled, "sample_sides": sides, "best": best,
             "speedup_solves_per_s": closed["mixed"]["solves_per_s"] / max(closed["fp64"]["solves_per_s"], 1e-30),
             "speedup_vs_per_request": closed["mixed"]["solves_per_s"]
             / max(closed["fp64_per_request"]["solves_per_s"], 1e-30),
@@ -889,12 +893,14 @@ def main():
     peaks = measured_peaks()
     if args.workload == "serving":
         r = run_serving()
-        line = {"metric": "solves/s", "value": round(r["closed"]["mixed"]["solves_per_s"], 4), "unit": "solves/s",
+        best = r["best"]
+        line = {"metric": "solves/s", "value": round(r["closed"][best]["solves_per_s"], 4), "unit": "solves/s",
                 "n_gpus": args.gpus, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64", "data": "synthetic",
-                "config": {"workload": "serving: 3D 7-point Poisson Jacobi, side U{64..256}, f U[-1,1), "
-                                       "stop at relative L2 residual 1e-6 (FP64), continuous batching, "
-                                       "HBM-budget admission", "sample_sides": r["sample_sides"]},
+                "dtype": "f32+f64" if best.startswith("mixed") else "f64", "data": "synthetic",
+                "config": {"workload": "serving: 3D 7-point Poisson solves, side U{64..256}, f U[-1,1), "
+                                       "stop at relative L2 residual 1e-6 (FP64), HBM-budget admission; value = "
+                                       "the fastest solve mode of the closed sample", "mode": best,
+                           "sample_sides": r["sample_sides"]},
                 "closed_sample": r["closed"], "poisson_trace_literal": r["trace"],
                 "poisson_trace_load_scaled": r["scaled"],
                 "speedup_mixed_vs_fp64": round(r["speedup_solves_per_s"], 3),
