@@ -9,9 +9,13 @@
 // sm_103a when the program is created; the module is loaded on a device at
 // its first launch there.
 //
-// The kernel is a plain one: a 32 x 8 block of threads per (x, y) tile of the
-// range, each CTA walking a run of planes two at a time, every read a load
-// from global memory (L1 and L2 keep the neighbours of adjacent elements).
+// Two kernels are generated.  The plain one: a 32 x 8 block of threads per
+// (x, y) tile of the range, each CTA walking a run of planes two at a time,
+// every read a load from global memory (L1 and L2 keep the neighbours of
+// adjacent elements); it serves FP64 grids and in-place calls.  The staged
+// one (FP32 / BF16): a 64 x 8 tile per CTA whose inputs' planes, with their
+// apron, stream through a shared-memory ring filled two planes ahead by
+// 16-byte cp.async copies; the body reads the ring.
 // Each read checks its offset against the reach declared at creation, so a
 // body that reads farther stays inside the grids: the read returns 0 and
 // sets bit 1 of the device error word, which gscl_sync reports as
@@ -75,6 +79,7 @@ struct Driver {
   decltype(&cuModuleGetFunction) get = nullptr;
   decltype(&cuLaunchKernel) launch = nullptr;
   decltype(&cuModuleUnload) unload = nullptr;
+  decltype(&cuFuncSetAttribute) set_attr = nullptr;
   bool ok = false;
 };
 
@@ -94,7 +99,8 @@ const Driver &driver() {
     d.get = (decltype(d.get))get("cuModuleGetFunction");
     d.launch = (decltype(d.launch))get("cuLaunchKernel");
     d.unload = (decltype(d.unload))get("cuModuleUnload");
-    d.ok = d.load && d.get && d.launch && d.unload;
+    d.set_attr = (decltype(d.set_attr))get("cuFuncSetAttribute");
+    d.ok = d.load && d.get && d.launch && d.unload && d.set_attr;
   });
   return d;
 }
@@ -105,6 +111,7 @@ const Driver &driver() {
 struct JitParams {
   const void *in[kMaxIn];
   long long in_pitch[kMaxIn], in_plane[kMaxIn];
+  long long in_x0[kMaxIn], in_x1[kMaxIn], in_y0[kMaxIn], in_y1[kMaxIn];  // storage: [-h, n + h)
   void *out[kMaxOut_];
   long long out_pitch[kMaxOut_], out_plane[kMaxOut_];
   long long lo[3], hi[3];
@@ -117,9 +124,12 @@ typedef %s gscl_stor;
 #define GSCL_RX %d
 #define GSCL_RY %d
 #define GSCL_RZ %d
+#define GSCL_NIN %d
+#define GSCL_PF 2
 struct GsclJitParams {
   const gscl_stor *in[%d];
   long long in_pitch[%d], in_plane[%d];
+  long long in_x0[%d], in_x1[%d], in_y0[%d], in_y1[%d];
   gscl_stor *out[%d];
   long long out_pitch[%d], out_plane[%d];
   long long lo[3], hi[3];
@@ -191,6 +201,88 @@ extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel(const __gr
 extern "C" __global__ void __launch_bounds__(256) gscl_program_kernel_nc(const __grid_constant__ GsclJitParams P) {
   gscl_program_body<true>(P);
 }
+// Staged variant: a 64 x 8 tile of core elements per CTA, each input's planes
+// with their apron in a shared-memory ring of R slots, copied GSCL_PF planes
+// ahead with cp.async (BF16: plain copies); the CTA walks its run of planes.
+__device__ __forceinline__ void gscl_cp16(void *s, const void *g) {
+  asm volatile("cp.async.cg.shared.global [%%0], [%%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(s)), "l"(g) : "memory");
+}
+// Rows are staged in 16-byte vectors: the tile's columns start at a multiple
+// of 64 from the interior origin (128-byte aligned), the apron AX is the reach
+// rounded up to a vector, so every vector is aligned; a vector is copied when
+// it lies within [-c, pitch - c) of its row (c = leading pad + halo, see the
+// host), inside the grid's storage whatever its row.
+extern "C" __global__ void __launch_bounds__(256) gscl_program_staged(const __grid_constant__ GsclJitParams P) {
+  extern __shared__ __align__(16) unsigned char gscl_sm[];
+  gscl_stor *ring = reinterpret_cast<gscl_stor *>(gscl_sm);
+  constexpr int VEC = 16 / (int)sizeof(gscl_stor);
+  constexpr int AX = (GSCL_RX + VEC - 1) / VEC * VEC;
+  constexpr int W = 64 + 2 * AX, WV = W / VEC, H = 8 + 2 * GSCL_RY, SLOT = W * H, R = 2 * GSCL_RZ + 1 + GSCL_PF;
+  const int tid = threadIdx.y * 32 + threadIdx.x, lane = threadIdx.x, wy = threadIdx.y;
+  const long long x0 = P.lo[0] / 64 * 64 + (long long)blockIdx.x * 64, y0 = P.lo[1] + (long long)blockIdx.y * 8;
+  const long long nz = P.hi[2] - P.lo[2];
+  const long long chunk = (nz + gridDim.z - 1) / gridDim.z;
+  const long long k0 = P.lo[2] + (long long)blockIdx.z * chunk;
+  const long long k1 = k0 + chunk < P.hi[2] ? k0 + chunk : P.hi[2];
+  if (k0 >= k1) return;
+  const long long kb = k0 - GSCL_RZ;  // the plane slot 0 held first
+  bool gscl_bad = false;
+  auto issue = [&](long long kp) {  // copies of plane kp into its slot, one commit group
+    if (kp < k1 + GSCL_RZ) {
+      const int slot = (int)((kp - kb) %% R);
+      for (int a = 0; a < GSCL_NIN; ++a) {
+        const gscl_stor *g = P.in[a] + kp * P.in_plane[a];
+        gscl_stor *sl = ring + (a * R + slot) * SLOT;
+        for (int idx = tid; idx < H * WV; idx += 256) {
+          const int row = idx / WV, cv = idx - row * WV;
+          const long long x = x0 - AX + cv * VEC, y = y0 - GSCL_RY + row;
+          if (x < P.in_x0[a] || x + VEC > P.in_x1[a] || y < P.in_y0[a] || y >= P.in_y1[a]) continue;
+          gscl_cp16(sl + row * W + cv * VEC, g + y * P.in_pitch[a] + x);
+        }
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  // pos: the core element's offset in a slot; sk: the slot of plane k
+  auto gscl_rs = [&](int a, int pos, int sk, int dx, int dy, int dz) -> real {
+    if (dx < -GSCL_RX || dx > GSCL_RX || dy < -GSCL_RY || dy > GSCL_RY || dz < -GSCL_RZ || dz > GSCL_RZ) {
+      gscl_bad = true;
+      return (real)0;
+    }
+    int sl = sk + dz;
+    sl = sl >= R ? sl - R : (sl < 0 ? sl + R : sl);
+    return gscl_ld(ring[(a * R + sl) * SLOT + pos + dy * W + dx]);
+  };
+  auto gscl_eval = [&](long long i, long long j, long long k, int gscl_pos, int gscl_sk, real *gscl_o) {
+%s
+    real value = 0;
+%s
+    {
+%s
+    }
+    (void)value;
+%s
+  };
+  for (long long kp = kb; kp < k0 + GSCL_RZ + GSCL_PF; ++kp) issue(kp);
+  for (long long k = k0; k < k1; ++k) {
+    asm volatile("cp.async.wait_group %%0;" ::"n"(GSCL_PF - 1) : "memory");  // this thread's copies of plane k + RZ
+    __syncthreads();                     // everyone's; and every read of plane k - RZ - 1 is done
+    issue(k + GSCL_RZ + GSCL_PF);        // into the slot plane k - RZ - 1 held
+    const long long j = y0 + wy;
+    const int sk = (int)((k - kb) %% R);
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const long long i = x0 + lane + 32 * e;
+      if (i >= P.lo[0] && i < P.hi[0] && j < P.hi[1]) {
+        real o[%d];
+        gscl_eval(i, j, k, (wy + GSCL_RY) * W + lane + 32 * e + AX, sk, o);
+%s
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;" ::: "memory");
+  if (gscl_bad) atomicOr(P.err, 2);
+}
 )SRC";
 
 std::string make_source(const char *body, int n_in, int n_out, int dtype, const int32_t reach[3]) {
@@ -205,13 +297,27 @@ std::string make_source(const char *body, int n_in, int n_out, int dtype, const 
               "]);\n    if (two) gscl_st(P.out[" + M + "] + (k + 1) * P.out_plane[" + M + "] + j * P.out_pitch[" + M +
               "] + i, ob[" + M + "]);\n";
   }
+  std::string defs_s, undefs, stores_s;
+  for (int a = 0; a < n_in; ++a) {
+    const std::string A = std::to_string(a);
+    undefs += "#undef in" + A + "\n";
+    defs_s += "#define in" + A + "(dx, dy, dz) gscl_rs(" + A + ", gscl_pos, gscl_sk, (dx), (dy), (dz))\n";
+  }
+  for (int m = 0; m < n_out; ++m) {
+    const std::string M = std::to_string(m);
+    stores_s += "        gscl_st(P.out[" + M + "] + k * P.out_plane[" + M + "] + j * P.out_pitch[" + M + "] + i, o[" + M +
+                "]);\n";
+  }
   const char *real = dtype == GSCL_F64 ? "double" : "float";
   const char *stor = dtype == GSCL_F64 ? "double" : dtype == GSCL_F32 ? "float" : "unsigned short";
   // the generated struct has fixed-size arrays like JitParams
-  std::vector<char> buf(strlen(kJitTemplate) + defs.size() + decl.size() + strlen(body) + ret.size() +
-                        stores.size() + 512);
-  snprintf(buf.data(), buf.size(), kJitTemplate, real, stor, reach[0], reach[1], reach[2], kMaxIn, kMaxIn, kMaxIn,
-           kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(), body, ret.c_str(), n_out, n_out, stores.c_str());
+  std::vector<char> buf(strlen(kJitTemplate) + 2 * (defs.size() + decl.size() + strlen(body) + ret.size()) +
+                        stores.size() + stores_s.size() + undefs.size() + defs_s.size() + 1024);
+  const std::string defs2 = undefs + defs_s;
+  snprintf(buf.data(), buf.size(), kJitTemplate, real, stor, reach[0], reach[1], reach[2], n_in, kMaxIn, kMaxIn,
+           kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(), body,
+           ret.c_str(), n_out, n_out, stores.c_str(), defs2.c_str(), decl.c_str(), body, ret.c_str(), n_out,
+           stores_s.c_str());
   return std::string(buf.data());
 }
 
@@ -220,7 +326,7 @@ struct Program {
   int n_in = 0, n_out = 0, dtype = 0;
   int32_t reach[3] = {0, 0, 0};
   std::vector<char> cubin;
-  std::map<int, CUfunction> fn, fn_nc;  // per device: plain reads / read-only path
+  std::map<int, CUfunction> fn, fn_nc, fn_st;  // per device: plain reads / read-only path / staged
   std::map<int, CUmodule> mod;
 };
 
@@ -229,11 +335,18 @@ std::map<uint64_t, Program> g_progs;
 uint64_t g_prog_next = 1;
 std::map<std::string, std::vector<char>> g_cubins;  // generated source -> its cubin (compile once per process)
 
-CUfunction program_function(Program &p, bool nc, gscl_status *st) {
+// kind: 0 plain reads, 1 read-only path, 2 staged in shared memory
+// GSCL_PROGRAM_STAGED=0 keeps every launch on the plain kernels.
+bool staged_enabled() {
+  const char *e = getenv("GSCL_PROGRAM_STAGED");
+  return !(e && e[0] == '0');
+}
+
+CUfunction program_function(Program &p, int kind, gscl_status *st) {
   int dev = 0;
   cudaGetDevice(&dev);
   auto it = p.fn.find(dev);
-  if (it != p.fn.end()) return nc ? p.fn_nc[dev] : it->second;
+  if (it != p.fn.end()) return kind == 2 ? p.fn_st[dev] : kind == 1 ? p.fn_nc[dev] : it->second;
   const Driver &d = driver();
   if (!d.ok) {
     *st = fail(GSCL_ERR_CUDA, "the driver's module functions are not available");
@@ -246,9 +359,10 @@ CUfunction program_function(Program &p, bool nc, gscl_status *st) {
     *st = fail(GSCL_ERR_CUDA, "loading the compiled operator failed (%d)", (int)r);
     return nullptr;
   }
-  CUfunction f = nullptr, fnc = nullptr;
+  CUfunction f = nullptr, fnc = nullptr, fst = nullptr;
   r = d.get(&f, m, "gscl_program_kernel");
   if (r == CUDA_SUCCESS) r = d.get(&fnc, m, "gscl_program_kernel_nc");
+  if (r == CUDA_SUCCESS) r = d.get(&fst, m, "gscl_program_staged");
   if (r != CUDA_SUCCESS) {
     d.unload(m);
     *st = fail(GSCL_ERR_CUDA, "the compiled operator has no kernel (%d)", (int)r);
@@ -257,7 +371,8 @@ CUfunction program_function(Program &p, bool nc, gscl_status *st) {
   p.mod[dev] = m;
   p.fn[dev] = f;
   p.fn_nc[dev] = fnc;
-  return nc ? fnc : f;
+  p.fn_st[dev] = fst;
+  return kind == 2 ? fst : kind == 1 ? fnc : f;
 }
 
 }  // namespace
@@ -366,16 +481,34 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
   bool shared = false;  // an output is also an input (reach 0, point-wise in place)
   for (int m = 0; m < n_out; ++m)
     for (int a = 0; a < n_in; ++a) shared |= overlaps(b.out[m], b.in[a]);
+  // the staged kernel for FP32 / BF16 grids when its shared-memory ring fits
+  // and no output is an input (the ring would hold a copy older than this
+  // element's write).  FP64 sweeps are bound by the FP64 pipe, where the plain
+  // kernel's extra warps win (0.291 against 0.333 ms per 256^3 heat sweep).
+  const int elem = b.in[0].elem;
+  const int vec = 16 / elem, ax = (p.reach[0] + vec - 1) / vec * vec;
+  const size_t ring_bytes = (size_t)n_in * (2 * p.reach[2] + 3) * (64 + 2 * ax) * (8 + 2 * p.reach[1]) * elem;
+  const bool staged = !shared && elem <= 4 && ring_bytes <= 200 * 1024 && staged_enabled();
   gscl_status fst = GSCL_OK;
-  CUfunction f = program_function(p, !shared, &fst);
+  CUfunction f = program_function(p, staged ? 2 : shared ? 0 : 1, &fst);
   if (!f) return fst;
+  if (staged) {
+    CUresult ra = driver().set_attr(f, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)ring_bytes);
+    if (ra != CUDA_SUCCESS) return fail(GSCL_ERR_CUDA, "shared memory for the compiled operator (%d)", (int)ra);
+  }
   int *err = device_error_word();
   if (!err) return fail(GSCL_ERR_CUDA, "device error word unavailable");
   JitParams P;
   memset(&P, 0, sizeof P);
   for (int a = 0; a < n_in; ++a) {
-    P.in_pitch[a] = b.in[a].pitch;
-    P.in_plane[a] = b.in[a].plane;
+    const Grid &g = b.in[a];
+    P.in_pitch[a] = g.pitch;
+    P.in_plane[a] = g.plane;
+    // the staged kernel's vectors: [-c, pitch - c) of a row, c = leading pad + halo
+    P.in_x0[a] = -(g.off + g.halo[0]);
+    P.in_x1[a] = g.pitch - (g.off + g.halo[0]);
+    P.in_y0[a] = -g.halo[1];
+    P.in_y1[a] = g.n[1] + g.halo[1];
   }
   for (int m = 0; m < n_out; ++m) {
     P.out_pitch[m] = b.out[m].pitch;
@@ -387,9 +520,14 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
   }
   P.err = err;
   const long long nx = b.hi[0] - b.lo[0], ny = b.hi[1] - b.lo[1], nz = b.hi[2] - b.lo[2];
-  const unsigned gx = (unsigned)((nx + 31) / 32), gy = (unsigned)((ny + 7) / 8);
-  const long long target = (long long)sm_count() * 8;  // 8 CTAs of 256 threads per SM
-  const unsigned gz = (unsigned)std::max(1LL, std::min(nz, (target + gx * gy - 1) / ((long long)gx * gy)));
+  const long long xspan = staged ? b.hi[0] - b.lo[0] / 64 * 64 : nx;  // staged tiles start at a multiple of 64
+  const unsigned gx = (unsigned)((xspan + (staged ? 63 : 31)) / (staged ? 64 : 32)), gy = (unsigned)((ny + 7) / 8);
+  // CTAs of 256 threads: 8 per SM, or as many as the staged rings fit; the
+  // staged kernel keeps runs of at least 8 planes (each run reloads its z halo)
+  const long long per_sm = staged ? std::max<long long>(1, std::min<long long>(8, (227 * 1024) / (long long)ring_bytes)) : 8;
+  const long long target = (long long)sm_count() * per_sm;
+  const long long zmax = staged ? std::max(1LL, nz / 8) : nz;
+  const unsigned gz = (unsigned)std::max(1LL, std::min(zmax, (target + gx * gy - 1) / ((long long)gx * gy)));
   if (gy > 65535 || gz > 65535) return fail(GSCL_ERR_UNSUPPORTED, "range too large for one launch");
   const Driver &d = driver();
   Grid src = b.in[0], dst = b.out[0];
@@ -401,7 +539,7 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
       if (b.in_h[a] == b.in_h[0]) P.in[a] = src.elem_ptr(0, 0, 0);
     P.out[0] = dst.elem_ptr(0, 0, 0);
     void *args[] = {&P};
-    CUresult r = d.launch(f, gx, gy, gz, 32, 8, 1, 0, (CUstream)stream, args, nullptr);
+    CUresult r = d.launch(f, gx, gy, gz, 32, 8, 1, staged ? (unsigned)ring_bytes : 0, (CUstream)stream, args, nullptr);
     if (r != CUDA_SUCCESS) return fail(GSCL_ERR_CUDA, "launching the compiled operator failed (%d)", (int)r);
     std::swap(src, dst);
   }

@@ -106,3 +106,36 @@ def test_read_beyond_reach_is_reported_not_performed():
     assert e.value.status == 2
     assert np.array_equal(I.interior_view(gv.download().numpy(), n, h), I.interior_view(u, n, h))
     B.sync()  # the flag is cleared
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("n,rng,reach", [((200, 45, 21), None, (1, 1, 1)),
+                                          ((67, 9, 30), ((3, 1, 2), (60, 9, 29)), (1, 1, 1)),
+                                          ((130, 20, 12), None, (2, 1, 2))])
+def test_staged_kernel_equals_plain_kernel(dtype, n, rng, reach, monkeypatch):
+    """The shared-memory staged kernel and the plain-load kernel evaluate the
+    same body on the same values: identical results, on tiles with ragged
+    edges, sub-ranges, short runs of planes and reaches of 2."""
+    h = (2, 2, 2)
+    body = ("out0 = in0(0,0,0) * (real)0.5 + (real)0.125 * (in0(1,0,0) + in0(-1,0,0) + in0(0,1,0) + in0(0,-1,0))"
+            " + (real)0.0625 * (in0(0,0,1) + in0(0,0,-1)) + in1(0,0,0) * in1(0,0,0);")
+    if reach[0] == 2:
+        body += " out0 += (real)0.01 * (in0(2,0,0) - in0(-2,0,-2) + in1(0,1,2));"
+    u = I.random_interior(120, n, h, -1.0, 1.0, halo_value=0.3)
+    f = I.random_interior(121, n, h, -1.0, 1.0, halo_value=-0.2)
+    prog = B.Program(body, 2, 1, dtype, reach)
+    got = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GSCL_PROGRAM_STAGED", flag)
+        gi = [B.Grid(n, h, dtype).upload(a) for a in (u, f)]
+        go = B.Grid(n, h, dtype).upload(np.zeros(I.padded_shape(n, h)))
+        prog.run(gi, [go], rng=rng)
+        got[flag] = go.download()
+    B.sync()
+    assert torch.equal(got["1"], got["0"])
+    oi = [O.Grid(as_storage(a, dtype), h) for a in (u, f)]
+    oo = O.Grid(np.zeros(I.padded_shape(n, h)), h)
+    lo, hi = rng if rng is not None else (None, None)
+    O.Program(body, 2, 1, reach).run(oi, [oo], lo=lo, hi=hi)
+    tol = {"f64": 1e-14, "f32": 3e-6, "bf16": 2e-2}[dtype]
+    assert np.max(np.abs(got["1"].double().numpy() - oo.a)) <= tol * 4
