@@ -208,6 +208,14 @@ gscl_status encode_tensor_map_3d(CUtensorMap *map, const Grid &g, uint32_t box_x
   return GSCL_OK;
 }
 
+// Host copies: rows of a dense array (width elements each) into the grid's pitched rows:
+// one CTA per row at a time, threads across the row.
+template <typename E>
+__global__ void unpack_rows_kernel(E *dst, const E *src, int64_t width, int64_t pitch, int64_t rows) {
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t c = threadIdx.x; c < width; c += blockDim.x) dst[r * pitch + c] = src[r * width + c];
+}
+
 }  // namespace gscl
 
 using namespace gscl;
@@ -307,14 +315,41 @@ gscl_status gscl_grid_info(gscl_grid h, gscl_grid_desc *out) {
   return GSCL_OK;
 }
 
+// Host -> device goes through a dense device copy and a row-scatter kernel:
+// a strided host-to-device copy of short rows runs at 15.6 GB/s on B300
+// against 38.8 GB/s for one contiguous copy (256^3 FP64 grid, pinned memory).
+// Device -> host strided copies run at full speed (56 GB/s) and stay 2D.
 static gscl_status copy2d(const Grid &g, void *host, bool to_host, void *stream) {
   const size_t width = (size_t)(g.n[0] + 2 * g.halo[0]) * g.elem;
   const size_t rows = (size_t)(g.n[1] + 2 * g.halo[1]) * (size_t)(g.n[2] + 2 * g.halo[2]);
   char *dev = g.buf + g.off * g.elem;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!to_host) {
+    void *tmp = nullptr;
+    if (cudaMallocAsync(&tmp, width * rows, st) == cudaSuccess) {
+      cudaError_t e = cudaMemcpyAsync(tmp, host, width * rows, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) {
+        cudaFreeAsync(tmp, st);
+        return cuda_fail(e, "cudaMemcpyAsync");
+      }
+      const int64_t w = (int64_t)(width / g.elem);
+      const unsigned blocks = (unsigned)std::min<size_t>(rows, (size_t)sm_count() * 16);
+      switch (g.elem) {
+        case 8: unpack_rows_kernel<<<blocks, 256, 0, st>>>((uint64_t *)dev, (const uint64_t *)tmp, w, g.pitch, (int64_t)rows); break;
+        case 4: unpack_rows_kernel<<<blocks, 256, 0, st>>>((uint32_t *)dev, (const uint32_t *)tmp, w, g.pitch, (int64_t)rows); break;
+        default: unpack_rows_kernel<<<blocks, 256, 0, st>>>((uint16_t *)dev, (const uint16_t *)tmp, w, g.pitch, (int64_t)rows); break;
+      }
+      e = cudaGetLastError();
+      cudaFreeAsync(tmp, st);
+      if (e != cudaSuccess) return cuda_fail(e, "unpacking host rows");
+      return GSCL_OK;
+    }
+    cudaGetLastError();  // no room for the dense copy: the strided copy below
+  }
   cudaError_t e = to_host ? cudaMemcpy2DAsync(host, width, dev, g.pitch * g.elem, width, rows,
-                                              cudaMemcpyDeviceToHost, (cudaStream_t)stream)
+                                              cudaMemcpyDeviceToHost, st)
                           : cudaMemcpy2DAsync(dev, g.pitch * g.elem, host, width, width, rows,
-                                              cudaMemcpyHostToDevice, (cudaStream_t)stream);
+                                              cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy2DAsync");
   return GSCL_OK;
 }
