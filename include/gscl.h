@@ -539,7 +539,8 @@ gscl_status gscl_sync(void *stream);
  *  - may use the core element's interior index i, j, k (long long), as the
  *    paper's stateful stencils query indices;
  *  - assigns out0 .. out<n_out - 1> (type real, starting at 0), stored at the
- *    core element after the body has run;
+ *    core element after the body has run (0 <= n_out <= GSCL_MAX_OUT), and may
+ *    assign `value`, which gscl_do_reduce_program reduces;
  *  - may call CUDA's device math functions.  C++ promotion applies: a double
  *    literal makes an FP32 program's expression FP64; write (real) casts or
  *    f-suffixed literals to keep FP32 arithmetic.
@@ -564,6 +565,21 @@ gscl_status gscl_program_create(const char *body, int32_t n_in, int32_t n_out, i
 gscl_status gscl_program_destroy(gscl_program p);
 gscl_status gscl_do_all_program(gscl_program p, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                                 int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream);
+
+/*
+ * do_reduce with a compiled body (Section 3): the body may also assign
+ * `value` (type real, starting at 0); its value at every core element of the
+ * range is reduced with reduce_op (GSCL_SUM compensated, GSCL_MAXABS, GSCL_L2)
+ * in FP64, deterministically, and outputs (n_out may be 0 for a program
+ * created with n_out = 0) are written as by gscl_do_all_program: a fused sweep
+ * and its residual in one call.  The values go through a stream-ordered FP64
+ * array over the range (8 bytes per element, allocated and freed on
+ * `stream`).  result, result_on_host, workspace and errors as gscl_do_reduce;
+ * an empty range reduces nothing (SUM, MAXABS and L2 give 0).
+ */
+gscl_status gscl_do_reduce_program(gscl_program p, int32_t reduce_op, const gscl_grid *in, int32_t n_in,
+                                   const gscl_grid *out, int32_t n_out, const gscl_range *range, double *result,
+                                   int32_t result_on_host, void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
  * FMA throughput of this device in FLOP/s (2 per fused multiply-add) for

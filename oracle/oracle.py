@@ -275,7 +275,9 @@ class Program:
         self.n_in, self.n_out, self.reach = n_in, n_out, tuple(int(v) for v in reach)
         self.outside = 0
 
-    def run(self, ins, outs, lo=None, hi=None):
+    def run(self, ins, outs, lo=None, hi=None, want_value=False):
+        """Applies the body over ``[lo, hi)``; with ``want_value`` returns the
+        body's ``value`` at every core element, shape (hz - lz, hy - ly, hx - lx)."""
         if len(ins) != self.n_in or len(outs) != self.n_out:
             raise ValueError("the program was made for another number of grids")
         ext, gin, gout, _, clo, chi = _marshal([], ins, outs, lo, hi, allow_alias=True)
@@ -288,5 +290,9 @@ class Program:
                     raise ValueError("reach beyond a grid's halo")
         r = (ctypes.c_int32 * 3)(*self.reach)
         n = ctypes.c_int64(0)
-        self._lib.orc_program(ctypes.byref(ext), gin, gout, clo, chi, r, ctypes.byref(n))
+        shape = tuple(int(chi[a] - clo[a]) for a in (2, 1, 0))
+        val = np.zeros(shape) if want_value else None
+        vptr = val.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if want_value else None
+        self._lib.orc_program(ctypes.byref(ext), gin, gout, clo, chi, r, ctypes.byref(n), vptr)
         self.outside += n.value
+        return val

@@ -6,7 +6,8 @@
  * and assigning out<m>) into the marked places, compiles it with gcc
  * (-O2 -ffp-contract=off, FP64) and runs it over a range in lexicographic
  * order, as do_all applies a stencil operator at every core element
- * (Section 3).  A read beyond the declared reach returns 0 and is counted.
+ * (Section 3); the body's `value` at each element can be returned for
+ * do_reduce.  A read beyond the declared reach returns 0 and is counted.
  */
 #include <math.h>
 #include <stdint.h>
@@ -40,8 +41,11 @@ static double orc_in(const orc_extent *e, const orc_grid *g, int64_t i, int64_t 
   return g->data[orc_at(e, g->hx, g->hy, g->hz, i + dx, j + dy, k + dz)];
 }
 
+/* values (optional): the body's `value` at every core element of the range,
+ * dense in (k, j, i) order. */
 int orc_program(const orc_extent *e, const orc_grid *in, const orc_out_grid *out, const int64_t lo[3],
-                const int64_t hi[3], const int32_t reach[3], int64_t *outside) {
+                const int64_t hi[3], const int32_t reach[3], int64_t *outside, double *values) {
+  int64_t q = 0;
   for (int64_t k = lo[2]; k < hi[2]; ++k)
     for (int64_t j = lo[1]; j < hi[1]; ++j)
       for (int64_t i = lo[0]; i < hi[0]; ++i) {
@@ -51,7 +55,7 @@ int orc_program(const orc_extent *e, const orc_grid *in, const orc_out_grid *out
         {
 /*@BODY@*/
         }
-        (void)value;
+        if (values) values[q++] = value;
 /*@STORES@*/
       }
   return 0;

@@ -106,6 +106,8 @@ def lib():
         "gscl_program_create": [ctypes.c_char_p, i32, i32, i32, P(i32), P(u64)],
         "gscl_program_destroy": [u64],
         "gscl_do_all_program": [u64, P(u64), i32, P(u64), i32, P(RangeC), i32, vp],
+        "gscl_do_reduce_program": [u64, i32, P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double), i32, vp,
+                                   i64, vp],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
         "gscl_set_fp64_arithmetic": [i32],
         "gscl_get_fp64_arithmetic": [],
@@ -355,6 +357,21 @@ class Program:
         """gscl_do_all_program."""
         check(lib().gscl_do_all_program(self.handle, _handles(ins), len(ins), _handles(outs), len(outs), _range(rng),
                                         int(sweeps), stream_ptr(stream)))
+
+    def reduce(self, reduce_op, ins, outs=(), rng=None, result=None, stream=None):
+        """gscl_do_reduce_program: reduces the body's ``value`` over the range
+        (outputs written as by run).  ``result`` as in do_reduce."""
+        ws = workspace(stream)
+        on_host = result is None
+        if on_host:
+            host = ctypes.c_double(0.0)
+            rptr = ctypes.pointer(host)
+        else:
+            rptr = ctypes.cast(ctypes.c_void_p(result.data_ptr()), ctypes.POINTER(ctypes.c_double))
+        check(lib().gscl_do_reduce_program(self.handle, int(reduce_op), _handles(ins), len(ins), _handles(outs),
+                                           len(outs), _range(rng), rptr, 1 if on_host else 0,
+                                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), stream_ptr(stream)))
+        return host.value if on_host else None
 
 
 def do_diamond(op, ins, outs, rng=None, stream=None):

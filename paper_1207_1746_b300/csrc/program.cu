@@ -111,10 +111,12 @@ const Driver &driver() {
 struct JitParams {
   const void *in[kMaxIn];
   long long in_pitch[kMaxIn], in_plane[kMaxIn];
-  long long in_x0[kMaxIn], in_x1[kMaxIn], in_y0[kMaxIn], in_y1[kMaxIn];  // storage: [-h, n + h)
+  long long in_x0[kMaxIn], in_x1[kMaxIn], in_y0[kMaxIn], in_y1[kMaxIn];  // staged copies: row bounds
   void *out[kMaxOut_];
   long long out_pitch[kMaxOut_], out_plane[kMaxOut_];
   long long lo[3], hi[3];
+  double *vout;  // do_reduce: the value at (i, j, k) goes to vout[(k-lo) v_plane + (j-lo) v_pitch + (i-lo)]
+  long long v_pitch, v_plane;
   int *err;
 };
 
@@ -125,6 +127,7 @@ typedef %s gscl_stor;
 #define GSCL_RY %d
 #define GSCL_RZ %d
 #define GSCL_NIN %d
+#define GSCL_NOUT %d
 #define GSCL_PF 2
 struct GsclJitParams {
   const gscl_stor *in[%d];
@@ -133,6 +136,8 @@ struct GsclJitParams {
   gscl_stor *out[%d];
   long long out_pitch[%d], out_plane[%d];
   long long lo[3], hi[3];
+  double *vout;
+  long long v_pitch, v_plane;
   int *err;
 };
 __device__ __forceinline__ real gscl_ld(double x) { return (real)x; }
@@ -177,8 +182,8 @@ __device__ __forceinline__ void gscl_program_body(const GsclJitParams &P) {
     {
 %s
     }
-    (void)value;
 %s
+    gscl_o[GSCL_NOUT] = value;
   };
   // this CTA's run of planes, two at a time: both elements' reads are issued
   // before either is stored, and neighbouring planes share their reads in L1
@@ -187,11 +192,16 @@ __device__ __forceinline__ void gscl_program_body(const GsclJitParams &P) {
   const long long k0 = P.lo[2] + (long long)blockIdx.z * chunk;
   const long long k1 = k0 + chunk < P.hi[2] ? k0 + chunk : P.hi[2];
   for (long long k = k0; k < k1; k += 2) {
-    real oa[%d], ob[%d];
+    real oa[GSCL_NOUT + 1], ob[GSCL_NOUT + 1];
     gscl_eval(k, oa);
     const bool two = k + 1 < k1;
     if (two) gscl_eval(k + 1, ob);
 %s
+    if (P.vout) {
+      double *v = P.vout + (k - P.lo[2]) * P.v_plane + (j - P.lo[1]) * P.v_pitch + (i - P.lo[0]);
+      v[0] = (double)oa[GSCL_NOUT];
+      if (two) v[P.v_plane] = (double)ob[GSCL_NOUT];
+    }
   }
   if (gscl_bad) atomicOr(P.err, 2);
 }
@@ -260,8 +270,8 @@ extern "C" __global__ void __launch_bounds__(256) gscl_program_staged(const __gr
     {
 %s
     }
-    (void)value;
 %s
+    gscl_o[GSCL_NOUT] = value;
   };
   for (long long kp = kb; kp < k0 + GSCL_RZ + GSCL_PF; ++kp) issue(kp);
   for (long long k = k0; k < k1; ++k) {
@@ -274,9 +284,10 @@ extern "C" __global__ void __launch_bounds__(256) gscl_program_staged(const __gr
     for (int e = 0; e < 2; ++e) {
       const long long i = x0 + lane + 32 * e;
       if (i >= P.lo[0] && i < P.hi[0] && j < P.hi[1]) {
-        real o[%d];
+        real o[GSCL_NOUT + 1];
         gscl_eval(i, j, k, (wy + GSCL_RY) * W + lane + 32 * e + AX, sk, o);
 %s
+        if (P.vout) P.vout[(k - P.lo[2]) * P.v_plane + (j - P.lo[1]) * P.v_pitch + (i - P.lo[0])] = (double)o[GSCL_NOUT];
       }
     }
   }
@@ -314,10 +325,9 @@ std::string make_source(const char *body, int n_in, int n_out, int dtype, const 
   std::vector<char> buf(strlen(kJitTemplate) + 2 * (defs.size() + decl.size() + strlen(body) + ret.size()) +
                         stores.size() + stores_s.size() + undefs.size() + defs_s.size() + 1024);
   const std::string defs2 = undefs + defs_s;
-  snprintf(buf.data(), buf.size(), kJitTemplate, real, stor, reach[0], reach[1], reach[2], n_in, kMaxIn, kMaxIn,
-           kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(), body,
-           ret.c_str(), n_out, n_out, stores.c_str(), defs2.c_str(), decl.c_str(), body, ret.c_str(), n_out,
-           stores_s.c_str());
+  snprintf(buf.data(), buf.size(), kJitTemplate, real, stor, reach[0], reach[1], reach[2], n_in, n_out, kMaxIn,
+           kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxIn, kMaxOut_, kMaxOut_, kMaxOut_, defs.c_str(), decl.c_str(),
+           body, ret.c_str(), stores.c_str(), defs2.c_str(), decl.c_str(), body, ret.c_str(), stores_s.c_str());
   return std::string(buf.data());
 }
 
@@ -384,7 +394,7 @@ extern "C" gscl_status gscl_program_create(const char *body, int32_t n_in, int32
                                            const int32_t reach[3], gscl_program *out) {
   if (!body || !out || !reach) return fail(GSCL_ERR_INVALID, "body, reach and out are required");
   if (n_in < 1 || n_in > kMaxIn) return fail(GSCL_ERR_UNSUPPORTED, "n_in = %d outside [1, %d]", n_in, kMaxIn);
-  if (n_out < 1 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [1, %d]", n_out, kMaxOut_);
+  if (n_out < 0 || n_out > kMaxOut_) return fail(GSCL_ERR_UNSUPPORTED, "n_out = %d outside [0, %d]", n_out, kMaxOut_);
   if (dtype != GSCL_F64 && dtype != GSCL_F32 && dtype != GSCL_BF16) return fail(GSCL_ERR_DTYPE, "unknown dtype");
   for (int a = 0; a < 3; ++a)
     if (reach[a] < 0 || reach[a] > 64) return fail(GSCL_ERR_INVALID, "reach[%d] = %d outside [0, 64]", a, reach[a]);
@@ -451,8 +461,15 @@ extern "C" gscl_status gscl_program_destroy(gscl_program h) {
   return GSCL_OK;
 }
 
-extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
-                                           int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream) {
+namespace gscl {
+namespace {
+
+// The program over the range `sweeps` times (do_all); with vout, one sweep
+// that also stores the body's value at every core element of the range into
+// the dense FP64 array vout (rows of v_pitch, planes of v_plane elements).
+gscl_status run_program(gscl_program h, const gscl_grid *in, int32_t n_in, const gscl_grid *out, int32_t n_out,
+                        const gscl_range *range, int32_t sweeps, void *stream, double *vout, long long v_pitch,
+                        long long v_plane, Bound *bound_out) {
   if (sweeps < 1) return fail(GSCL_ERR_INVALID, "sweeps must be >= 1");
   std::lock_guard<std::mutex> lk(g_prog_mu);
   auto it = g_progs.find(h);
@@ -471,8 +488,10 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
   Bound b;
   if (gscl_status s = bind(&st, false, in, n_in, out, n_out, range, &b)) return s;
   if (b.in[0].dtype != p.dtype) return fail(GSCL_ERR_DTYPE, "the program was compiled for another dtype");
-  if (b.empty) return GSCL_OK;
+  if (bound_out) *bound_out = b;
+  if (b.empty || (vout && v_pitch == 0)) return GSCL_OK;
   if (sweeps > 1) {
+    if (n_out < 1) return fail(GSCL_ERR_INVALID, "multi-sweep ping-pong needs an output");
     const Grid &a = b.in[0], &c = b.out[0];
     if (a.halo[0] != c.halo[0] || a.halo[1] != c.halo[1] || a.halo[2] != c.halo[2])
       return fail(GSCL_ERR_SHAPE, "multi-sweep ping-pong needs in[0] and out[0] of identical layout");
@@ -519,6 +538,9 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
     P.hi[a] = b.hi[a];
   }
   P.err = err;
+  P.vout = vout;
+  P.v_pitch = v_pitch;
+  P.v_plane = v_plane;
   const long long nx = b.hi[0] - b.lo[0], ny = b.hi[1] - b.lo[1], nz = b.hi[2] - b.lo[2];
   const long long xspan = staged ? b.hi[0] - b.lo[0] / 64 * 64 : nx;  // staged tiles start at a multiple of 64
   const unsigned gx = (unsigned)((xspan + (staged ? 63 : 31)) / (staged ? 64 : 32)), gy = (unsigned)((ny + 7) / 8);
@@ -530,14 +552,15 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
   const unsigned gz = (unsigned)std::max(1LL, std::min(zmax, (target + gx * gy - 1) / ((long long)gx * gy)));
   if (gy > 65535 || gz > 65535) return fail(GSCL_ERR_UNSUPPORTED, "range too large for one launch");
   const Driver &d = driver();
-  Grid src = b.in[0], dst = b.out[0];
+  Grid src = b.in[0], dst;  // ping-pong pair in[0] / out[0] (no output: in[0] alone)
+  if (n_out > 0) dst = b.out[0];
   for (int s = 0; s < sweeps; ++s) {
     for (int a = 0; a < n_in; ++a) P.in[a] = b.in[a].elem_ptr(0, 0, 0);
     for (int m = 0; m < n_out; ++m) P.out[m] = b.out[m].elem_ptr(0, 0, 0);
     P.in[0] = src.elem_ptr(0, 0, 0);
     for (int a = 1; a < n_in; ++a)  // another input naming the ping-pong grid follows it
       if (b.in_h[a] == b.in_h[0]) P.in[a] = src.elem_ptr(0, 0, 0);
-    P.out[0] = dst.elem_ptr(0, 0, 0);
+    if (n_out > 0) P.out[0] = dst.elem_ptr(0, 0, 0);
     void *args[] = {&P};
     CUresult r = d.launch(f, gx, gy, gz, 32, 8, 1, staged ? (unsigned)ring_bytes : 0, (CUstream)stream, args, nullptr);
     if (r != CUDA_SUCCESS) return fail(GSCL_ERR_CUDA, "launching the compiled operator failed (%d)", (int)r);
@@ -545,4 +568,53 @@ extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, 
   }
   if (sweeps > 1 && sweeps % 2 == 0) return swap_storage(in[0], out[0]);
   return GSCL_OK;
+}
+
+}  // namespace
+}  // namespace gscl
+
+extern "C" gscl_status gscl_do_all_program(gscl_program h, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
+                                           int32_t n_out, const gscl_range *range, int32_t sweeps, void *stream) {
+  if (n_out < 1) return fail(GSCL_ERR_INVALID, "do_all needs at least one output");
+  return run_program(h, in, n_in, out, n_out, range, sweeps, stream, nullptr, 0, 0, nullptr);
+}
+
+extern "C" gscl_status gscl_do_reduce_program(gscl_program h, int32_t reduce_op, const gscl_grid *in, int32_t n_in,
+                                              const gscl_grid *out, int32_t n_out, const gscl_range *range,
+                                              double *result, int32_t result_on_host, void *workspace,
+                                              int64_t workspace_bytes, void *stream) {
+  if (!result) return fail(GSCL_ERR_INVALID, "result is NULL");
+  if (reduce_op != GSCL_SUM && reduce_op != GSCL_MAXABS && reduce_op != GSCL_L2)
+    return fail(GSCL_ERR_INVALID, "unknown reduce op %d", reduce_op);
+  // validate first (no launch), then size the value array on the range
+  Bound b;
+  if (gscl_status s = run_program(h, in, n_in, out, n_out, range, 1, stream, (double *)1, 0, 0, &b)) return s;
+  const int64_t ext[3] = {std::max<int64_t>(1, b.hi[0] - b.lo[0]), std::max<int64_t>(1, b.hi[1] - b.lo[1]),
+                          std::max<int64_t>(1, b.hi[2] - b.lo[2])};
+  const int32_t nohalo[3] = {0, 0, 0};
+  int64_t pitch = 0, off = 0, bytes = 0;
+  if (gscl_status s = gscl_grid_layout(3, ext, nohalo, GSCL_F64, &pitch, &off, &bytes)) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  void *buf = nullptr;
+  cudaError_t e = cudaMallocAsync(&buf, (size_t)bytes, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync of the value array");
+  gscl_grid vg = 0;
+  gscl_status s = gscl_grid_create(3, ext, nohalo, GSCL_F64, buf, bytes, &vg);
+  if (s == GSCL_OK) {
+    double *vout = (double *)buf + off;
+    if (b.empty) {
+      // an empty range: reduce nothing (the value array is not read)
+      gscl_range none = {{0, 0, 0}, {0, 0, 0}};
+      s = gscl_do_reduce(reduce_op, nullptr, &vg, 1, nullptr, 0, &none, result, result_on_host, workspace,
+                         workspace_bytes, stream);
+    } else {
+      s = run_program(h, in, n_in, out, n_out, range, 1, stream, vout, pitch, pitch * ext[1], nullptr);
+      if (s == GSCL_OK)
+        s = gscl_do_reduce(reduce_op, nullptr, &vg, 1, nullptr, 0, nullptr, result, result_on_host, workspace,
+                           workspace_bytes, stream);
+    }
+    gscl_grid_destroy(vg);
+  }
+  cudaFreeAsync(buf, st);
+  return s;
 }

@@ -305,3 +305,20 @@ def test_program_binding_rules():
     assert run(wide, [u], [v]) == 2                      # reach beyond the halo
     assert run(p, [u], [v], sweeps=0) == 1
     assert run(p, [u], [v], rng=((0, 0, 3), (16, 8, 3))) == 0
+
+
+def test_program_reduce_validation():
+    u = FakeGrid((16, 8, 8), (1, 1, 1))
+    p = B.Program("value = in0(0,0,0);", 1, 0, "f64", (0, 0, 0))
+    L = B.lib()
+    res = ctypes.c_double()
+    ws = ctypes.c_void_p(1 << 30)
+
+    def red(op, result=True, outs=()):
+        return L.gscl_do_reduce_program(p.handle, op, B._handles([u]), 1, B._handles(list(outs)), len(outs), None,
+                                        ctypes.byref(res) if result else None, 1, ws, 1 << 22, None)
+
+    assert red(7) == 1                    # unknown reduce op
+    assert red(0, result=False) == 1      # no result pointer
+    assert red(0, outs=[u]) == 1          # compiled for no outputs
+    assert L.gscl_do_all_program(p.handle, B._handles([u]), 1, None, 0, None, 1, None) == 1   # do_all needs an output

@@ -139,3 +139,53 @@ def test_staged_kernel_equals_plain_kernel(dtype, n, rng, reach, monkeypatch):
     O.Program(body, 2, 1, reach).run(oi, [oo], lo=lo, hi=hi)
     tol = {"f64": 1e-14, "f32": 3e-6, "bf16": 2e-2}[dtype]
     assert np.max(np.abs(got["1"].double().numpy() - oo.a)) <= tol * 4
+
+
+RESID = ("value = in0(1,0,0) + in0(-1,0,0) + in0(0,1,0) + in0(0,-1,0) + in0(0,0,1) + in0(0,0,-1)"
+         " - (real)6 * in0(0,0,0) + in1(0,0,0);")
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 1e-5)])
+@pytest.mark.parametrize("red", [B.SUM, B.MAXABS, B.L2])
+def test_reduce_body_value_matches_oracle(dtype, tol, red):
+    """The body's value reduced over a sub-range, against the oracle's values
+    reduced with math.fsum (SUM, L2) or max |v|."""
+    import math
+    n, h = (90, 41, 23), (1, 1, 1)
+    u = I.random_interior(130, n, h, -1.0, 1.0, halo_value=0.5)
+    f = I.random_interior(131, n, h, -1.0, 1.0)
+    rng = ((2, 3, 1), (87, 41, 22))
+    gi = [B.Grid(n, h, dtype).upload(a) for a in (u, f)]
+    got = B.Program(RESID, 2, 0, dtype).reduce(red, gi, [], rng=rng)
+    vals = O.Program(RESID.replace("(real)6", "6.0"), 2, 0).run(
+        [O.Grid(as_storage(u, dtype), h), O.Grid(as_storage(f, dtype), h)], [], lo=rng[0], hi=rng[1],
+        want_value=True).ravel()
+    want = {B.SUM: math.fsum(vals), B.MAXABS: float(np.max(np.abs(vals))),
+            B.L2: math.sqrt(math.fsum(vals * vals))}[red]
+    scale = np.sum(np.abs(vals)) if red == B.SUM else abs(want)
+    assert abs(got - want) <= tol * scale
+
+
+def test_reduce_body_with_outputs_is_a_fused_sweep():
+    """value = the residual r, out0 = u + r / 8: one call gives the sweep and
+    its residual norm, as the library's fused heat operator does."""
+    n, h = (64, 64, 32), (1, 1, 1)
+    u = I.random_interior(132, n, h, -1.0, 1.0)
+    f = I.random_interior(133, n, h, -1.0, 1.0)
+    body = RESID + " out0 = in0(0,0,0) + (real)0.125 * value;"
+    gu, gf, gv = B.Grid(n, h).upload(u), B.Grid(n, h).upload(f), B.Grid(n, h).upload(u)
+    got = B.Program(body, 2, 1).reduce(B.L2, [gu, gf], [gv])
+    ru, rv = B.Grid(n, h).upload(u), B.Grid(n, h).upload(u)
+    want = B.do_reduce(B.L2, S.heat7_fused(0.125), [ru, B.Grid(n, h).upload(f)], [rv])
+    assert abs(got - want) <= 1e-13 * want
+    assert np.max(np.abs(gv.download().numpy() - rv.download().numpy())) <= 1e-14
+
+
+def test_reduce_body_empty_range_and_device_result():
+    n, h = (40, 10, 6), (1, 1, 1)
+    gu = B.Grid(n, h).upload(I.random_interior(134, n, h, 1.0, 2.0))
+    p = B.Program("value = in0(0,0,0);", 1, 0, "f64", (0, 0, 0))
+    assert p.reduce(B.SUM, [gu], [], rng=((0, 0, 3), (40, 10, 3))) == 0.0
+    res = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p.reduce(B.MAXABS, [gu], [], result=res)
+    assert float(res.cpu()[0]) == float(np.max(I.interior_view(I.random_interior(134, n, h, 1.0, 2.0), n, h)))

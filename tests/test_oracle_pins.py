@@ -712,3 +712,21 @@ def test_program_reads_beyond_the_reach_are_refused():
     p.run([u], [a])
     assert p.outside == 5 * 4 * 3
     assert np.array_equal(a.interior(), u.interior())
+
+
+def test_program_value_is_the_term_list_value():
+    """The body's `value` (the heat residual written as a body) is the value the
+    term-list oracle returns for the same operator, element by element."""
+    n, h = (8, 6, 5), (1, 1, 1)
+    rng = np.random.default_rng(52)
+    u, f = O.zeros(n, h), O.zeros(n, h)
+    u.a[...] = rng.uniform(-1, 1, u.a.shape)
+    f.a[...] = rng.uniform(-1, 1, f.a.shape)
+    body = ("value = in0(1,0,0) + in0(-1,0,0) + in0(0,1,0) + in0(0,-1,0) + in0(0,0,1) + in0(0,0,-1)"
+            " - 6.0 * in0(0,0,0) + in1(0,0,0);")
+    got = O.Program(body, 2, 0).run([u, f], [], lo=(1, 0, 1), hi=(8, 5, 4), want_value=True)
+    terms = ([(dx, dy, dz, 0, O.NONE, O.VALUE, 1.0) for dx, dy, dz in AXIAL6]
+             + [(0, 0, 0, 0, O.NONE, O.VALUE, -6.0), (0, 0, 0, 1, O.NONE, O.VALUE, 1.0)])
+    want = O.do_all(terms, [u, f], [], lo=(1, 0, 1), hi=(8, 5, 4), want_value=True)
+    assert got.shape == want.shape == (3, 5, 7)
+    assert np.max(np.abs(got - want)) <= 16 * EPS
