@@ -503,12 +503,13 @@ def run_climate(dtype, steps, warmup, sweeps=50):
 
 
 # ------------------------------------------------------------------ ordered workload
-def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10, interpreted=False):
+def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10, interpreted=False, along_x=False):
     """Ordered iteration space (do_k_inc): bidiagonal forward substitution
     x(k) = g(k) - m(k) x(k-1) down every (i, j) column of a 256 x 256 x 80
     grid (g uniform [-1, 1), m uniform [-0.9, 0.9], seeds 606 / 607), `reps`
     solves per step.  Algorithmic bytes per point: g and m read, x written.
-    `interpreted`: the runtime term loop instead of the compiled recurrence."""
+    `interpreted`: the runtime term loop instead of the compiled recurrence;
+    `along_x`: the same recurrence along x (do_i_inc, rows of 256)."""
     import torch
 
     from paper_1207_1746_b300 import binding as B
@@ -518,7 +519,9 @@ def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10, interpreted=Fal
     g = B.Grid(n, h, dtype).upload(I.random_interior(606, n, h, -1.0, 1.0))
     m = B.Grid(n, h, dtype).upload(I.random_interior(607, n, h, -0.9, 0.9))
     x = B.Grid(n, h, dtype).upload(I.random_interior(608, n, h, 0.0, 0.0))
-    terms = [(0, 0, 0, 1, B.NONE, 0, 1.0), (0, 0, -1, 0, 2, 0, -1.0)]
+    order = B.I_INC if along_x else B.K_INC
+    prev = (-1, 0, 0) if along_x else (0, 0, -1)
+    terms = [(0, 0, 0, 1, B.NONE, 0, 1.0), (*prev, 0, 2, 0, -1.0)]
     op = B.Stencil(terms)
     stream = torch.cuda.current_stream()
     saved = os.environ.get("GSCL_GENERIC_ONLY")
@@ -526,11 +529,11 @@ def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10, interpreted=Fal
         os.environ["GSCL_GENERIC_ONLY"] = "1"
     else:
         os.environ.pop("GSCL_GENERIC_ONLY", None)
-    path = B.ordered_specialization(B.K_INC, op, [x, g, m], [x])
+    path = B.ordered_specialization(order, op, [x, g, m], [x])
 
     def step():
         for _ in range(reps):
-            B.do_ordered(B.K_INC, op, [x, g, m], [x])
+            B.do_ordered(order, op, [x, g, m], [x])
 
     for _ in range(warmup):
         step()
@@ -1103,18 +1106,21 @@ def main():
     if args.workload == "ordered":
         peak_hbm = peaks.get("hbm_gbs", 6400.0)
         out = {}
-        runs = [("f64", False), ("f32", False)] + ([] if args.profile else [("f64", True), ("f32", True)])
-        for dt, interp in runs:
-            r = run_ordered(dt, args.steps, args.warmup, interpreted=interp)
+        runs = [("f64", False, False), ("f32", False, False)]
+        if not args.profile:
+            runs += [("f64", True, False), ("f32", True, False), ("f64", False, True), ("f32", False, True)]
+        for dt, interp, along_x in runs:
+            r = run_ordered(dt, args.steps, args.warmup, interpreted=interp, along_x=along_x)
             t = dist.max(r["ms_per_step"])
             bpp = {"f64": 24, "f32": 12}[dt]
             gbs = bpp * r["points"] / (r["solve_ms"] * 1e-3) / 1e9
-            out[dt + ("_interpreted" if interp else "")] = {
+            out[dt + ("_interpreted" if interp else "") + ("_along_x" if along_x else "")] = {
                 "value": round(dist.world * r["reps"] * r["points"] / (t * 1e-3) / 1e9, 3),
                 "ms_per_step": round(t, 3), "solve_ms": round(r["solve_ms"], 4), "path": r["path"],
                 "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak_hbm, "unit": "GB/s",
                              "frac": round(gbs / peak_hbm, 4),
-                             "traffic": profile_traffic("ordered_f64") if (dt, interp) == ("f64", False) else None,
+                             "traffic": profile_traffic("ordered_f64") if (dt, interp, along_x) == ("f64", False, False)
+                             else None,
                              "peak_source": "measured"}}
         # FP64: three FP64-pipe instructions per point (DFMA a g, DMUL m x(k-1),
         # DFMA of the sum), each taking the pipe as long as one DFMA

@@ -301,8 +301,10 @@ typedef enum {
  *    stored (rounded) value is what the next element reads.
  *  - Terms may also write the returned value (out = GSCL_VALUE) and read it
  *    (in = GSCL_VALUE), as in do_all; it is not reduced.
- *  - GSCL_I_INC / GSCL_I_DEC return GSCL_ERR_UNSUPPORTED: one thread walks one
- *    column, and columns along x would place a warp's accesses a row apart.
+ *  - Along y and z one thread walks one column; along x (GSCL_I_INC /
+ *    GSCL_I_DEC) a warp stages 32 steps of 32 rows in shared memory at a time
+ *    and takes operators with at most 8 distinct element loads per element
+ *    (GSCL_ERR_UNSUPPORTED beyond).
  *  - Errors, range and dtype rules as gscl_do_all (n_out >= 1).  Asynchronous
  *    on `stream`.
  */
@@ -314,7 +316,9 @@ gscl_status gscl_do_ordered(int32_t order, const gscl_stencil *op, const gscl_gr
  * range), in *shape: a non-negative id for a recurrence compiled for its
  * structure, -1 for the interpreted term loop with look-ahead loads, -2 for
  * the interpreted loop with loads per term (more than 8 distinct loads per
- * element, or BF16 storage).  The compiled structures, with the terms in
+ * element, or BF16 storage), -3 for the interpreted loop on rows along x
+ * staged in shared memory (GSCL_I_INC / GSCL_I_DEC; the compiled structures
+ * report their ids along x too).  The compiled structures, with the terms in
  * this order and the weights a, b, c any values:
  *   0  x = a x(prev) + b f                   (running sums)
  *   1  x = b f + a x(prev)

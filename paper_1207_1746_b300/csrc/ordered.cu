@@ -16,8 +16,9 @@
 // shared memory, one private column of slots per thread, filled by cp.async
 // (one commit group per step; a thread waits only for its own copies), so
 // slots can be indexed at run time.  FP32 / FP64 storage (cp.async moves 4 or
-// 8 bytes); BF16 takes the simple path.  The ordered axis must
-// be y or z: columns along x would put a warp's accesses a whole row apart.
+// 8 bytes); BF16 takes the simple path.  Along x (do_i_inc / do_i_dec) a
+// thread per row would put a warp's accesses a whole row apart, so rows go
+// through shared memory in 32-step chunks (ordered_x_kernel below).
 //
 // The common recurrences (running sums, first-order recurrences, bidiagonal
 // substitution) are also compiled: their shape (which load, output or value
@@ -255,7 +256,7 @@ struct OrdShapeTable {
   OrdShapeTerm t[N];
 };
 
-enum OrdShapeId { ORD_INTERPRETED = -1, ORD_SIMPLE = -2, ORD_RUNSUM_PREV_FIRST = 0, ORD_RUNSUM, ORD_BIDIAG,
+enum OrdShapeId { ORD_ROWS_X = -3, ORD_INTERPRETED = -1, ORD_SIMPLE = -2, ORD_RUNSUM_PREV_FIRST = 0, ORD_RUNSUM, ORD_BIDIAG,
                   ORD_BIDIAG_PREV_FIRST, ORD_AXPY2, ORD_SHAPES };
 
 struct OrdRunSumPrevFirst {  // x = a x(prev) + b f
@@ -457,8 +458,183 @@ gscl_status launch_ordered_dir(const OrdParams &P, int shape, long long cols, cu
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
 }
 
+// ------------------------------------------------------------ ordered along x
+// do_i_inc / do_i_dec: rows along x are walked in order, one lane per row,
+// 32 rows per warp.  A warp stages 32 steps of each distinct load for its 32
+// rows in shared memory (lane j fetches element j of a row: coalesced row
+// reads, every row of every load in flight at once), walks its rows through
+// those 32 steps reading the transposed tile (lane = row, stride kXC + 1
+// keeps the banks apart), keeps each output's element just written in
+// registers, and writes the 32 steps of every output back with coalesced row
+// stores.  The compiled recurrences and the interpreted term loop compute
+// the same operations in the same order as on the other axes.
+constexpr int kXC = 32;
+
+struct OrdInterpretedX {};
+
+template <typename T, bool INC, class S>
+__global__ void __launch_bounds__(128) ordered_x_kernel(const __grid_constant__ OrdParams P) {
+  using A = typename Arith<T>::A;
+  extern __shared__ __align__(16) unsigned char ox_smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nl = P.n_loads, no = P.n_out;
+  constexpr int TS = kXC + 1;       // row stride of a tile
+  constexpr int TILE = 32 * TS;     // one load's or one output's tile: 32 rows
+  T *lt = reinterpret_cast<T *>(ox_smem) + (size_t)w * (nl + no) * TILE;
+  T *ot = lt + (size_t)nl * TILE;
+  const int64_t ny = P.hi[1] - P.lo[1], rows = ny * (P.hi[2] - P.lo[2]);
+  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * 32;
+  if (row0 >= rows) return;  // the whole warp: only warp-level synchronisation below
+  const int64_t my = row0 + lane;
+  const bool live = my < rows;
+  const int yl = live ? (int)(P.lo[1] + my % ny) : 0, zl = live ? (int)(P.lo[2] + my / ny) : 0;
+  const int64_t len = P.hi[0] - P.lo[0];
+  A prev[kMaxOut_];
+#pragma unroll
+  for (int m = 0; m < kMaxOut_; ++m) {
+    prev[m] = A(0);
+    if (live && m < no && P.need_prev[m])
+      prev[m] = to_arith(reinterpret_cast<const T *>(P.out[m])[zl * P.out_plane[m] + yl * P.out_pitch[m] +
+                                                                 (INC ? P.lo[0] - 1 : P.hi[0])]);
+  }
+  const int nrows = (int)min((int64_t)32, rows - row0);
+  for (int64_t c0 = 0; c0 < len; c0 += kXC) {
+    const int clen = (int)min((int64_t)kXC, len - c0);
+    const int64_t xs = INC ? P.lo[0] + c0 : P.hi[0] - c0 - clen;  // the chunk's lowest x
+    const int sj = INC ? lane : clen - 1 - lane;                    // step of x = xs + lane
+    // every row of every load in flight at once (cp.async for 4- and 8-byte
+    // elements; BF16 rows are copied through registers)
+    for (int l = 0; l < nl; ++l) {
+      const OrdLoad &ld = P.loads[l];
+      const T *g = reinterpret_cast<const T *>(P.in[ld.grid]);
+      for (int rr = 0; rr < nrows; ++rr) {
+        const int ry = __shfl_sync(0xffffffffu, yl, rr) + ld.dy, rz = __shfl_sync(0xffffffffu, zl, rr) + ld.dz;
+        if (lane < clen) {
+          const T *src = g + (int64_t)rz * P.in_plane[ld.grid] + (int64_t)ry * P.in_pitch[ld.grid] + xs + lane + ld.dx;
+          if constexpr (sizeof(T) >= 4) cp_async(lt + l * TILE + rr * TS + sj, src, (int)sizeof(T));
+          else lt[l * TILE + rr * TS + sj] = *src;
+        }
+      }
+    }
+    if constexpr (sizeof(T) >= 4) {
+      cp_async_commit();
+      cp_async_wait<0>();
+    }
+    __syncwarp();
+    if constexpr (!std::is_same<S, OrdInterpretedX>::value) {
+      // compiled recurrence: every term's slot a constant
+      if (live) {
+        const T *r = lt + lane * TS;
+        for (int s = 0; s < clen; ++s) {
+          A v = A(0);
+          A o[S::NOUT];
+#pragma unroll
+          for (int m = 0; m < S::NOUT; ++m) o[m] = A(0);
+          static_for<S::NT>([&](auto tc) {
+            constexpr int t = decltype(tc)::value;
+            constexpr OrdShapeTerm st = S::table.t[t];
+            A x;
+            if constexpr (st.xs == kSrcValue) x = v;
+            else if constexpr (st.xs >= kSrcPrev) x = prev[st.xs - kSrcPrev];
+            else x = to_arith(r[st.xs * TILE + s]);
+            if constexpr (st.cs >= 0) x = x * to_arith(r[st.cs * TILE + s]);
+            const A wgt = ord_weight(P.terms[t], A(0));
+            if constexpr (st.out < 0) v = fma(wgt, x, v);
+            else o[st.out] = fma(wgt, x, o[st.out]);
+          });
+#pragma unroll
+          for (int m = 0; m < S::NOUT; ++m) {
+            const T y = from_arith<T>(o[m]);
+            ot[m * TILE + lane * TS + s] = y;
+            prev[m] = to_arith(y);
+          }
+        }
+      }
+    } else if (live) {
+      const T *r = lt + lane * TS;
+      for (int s = 0; s < clen; ++s) {
+        A v = A(0);
+        A o[kMaxOut_];
+#pragma unroll
+        for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
+        for (int t = 0; t < P.n_terms; ++t) {
+          const OrdTerm &tm = P.terms[t];
+          A x = v;
+          if (tm.prev >= 0) {
+            x = prev[0];
+#pragma unroll
+            for (int m = 1; m < kMaxOut_; ++m)
+              if (tm.prev == m) x = prev[m];
+          } else if (tm.xslot >= 0) {
+            x = to_arith(r[tm.xslot * TILE + s]);
+          }
+          if (tm.cslot >= 0) x = x * to_arith(r[tm.cslot * TILE + s]);
+          const A wgt = ord_weight(tm, A(0));
+          if (tm.out < 0) {
+            v = fma(wgt, x, v);
+          } else {
+#pragma unroll
+            for (int m = 0; m < kMaxOut_; ++m)
+              if (tm.out == m) o[m] = fma(wgt, x, o[m]);
+          }
+        }
+#pragma unroll
+        for (int m = 0; m < kMaxOut_; ++m) {
+          if (m < no) {
+            const T y = from_arith<T>(o[m]);
+            ot[m * TILE + lane * TS + s] = y;
+            prev[m] = to_arith(y);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    for (int m = 0; m < no; ++m) {
+      T *g = reinterpret_cast<T *>(P.out[m]);
+      for (int rr = 0; rr < nrows; ++rr) {
+        const int ry = __shfl_sync(0xffffffffu, yl, rr), rz = __shfl_sync(0xffffffffu, zl, rr);
+        if (lane < clen)
+          g[(int64_t)rz * P.out_plane[m] + (int64_t)ry * P.out_pitch[m] + xs + lane] = ot[m * TILE + rr * TS + sj];
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, class S>
+gscl_status launch_ordered_x_s(const OrdParams &P, bool inc, long long rows, cudaStream_t st) {
+  const size_t per_warp = (size_t)(P.n_loads + P.n_out) * 32 * (kXC + 1) * sizeof(T);
+  const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
+  const size_t smem = per_warp * warps;
+  const unsigned blocks = (unsigned)((rows + 32LL * warps - 1) / (32LL * warps));
+  auto kern = inc ? ordered_x_kernel<T, true, S> : ordered_x_kernel<T, false, S>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e, "ordered kernel set-up");
+  }
+  kern<<<blocks, 32 * warps, smem, st>>>(P);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
+}
+
+// shape: a compiled recurrence (>= 0) or the interpreted term loop
+template <typename T>
+gscl_status launch_ordered_x(const OrdParams &P, int shape, bool inc, long long rows, cudaStream_t st) {
+  if (P.n_loads > kLoads)
+    return fail(GSCL_ERR_UNSUPPORTED, "ordered iteration along x takes at most %d distinct loads per element", kLoads);
+  switch (shape) {
+    case ORD_RUNSUM_PREV_FIRST: return launch_ordered_x_s<T, OrdRunSumPrevFirst>(P, inc, rows, st);
+    case ORD_RUNSUM: return launch_ordered_x_s<T, OrdRunSum>(P, inc, rows, st);
+    case ORD_BIDIAG: return launch_ordered_x_s<T, OrdBidiag>(P, inc, rows, st);
+    case ORD_BIDIAG_PREV_FIRST: return launch_ordered_x_s<T, OrdBidiagPrevFirst>(P, inc, rows, st);
+    case ORD_AXPY2: return launch_ordered_x_s<T, OrdAxpy2>(P, inc, rows, st);
+  }
+  return launch_ordered_x_s<T, OrdInterpretedX>(P, inc, rows, st);
+}
+
 template <typename T>
 gscl_status launch_ordered_t(const OrdParams &P, int shape, int axis, bool inc, long long cols, cudaStream_t st) {
+  if (axis == 0) return launch_ordered_x<T>(P, shape, inc, cols, st);
   if (axis == 2)
     return inc ? launch_ordered_dir<T, 2, true>(P, shape, cols, st) : launch_ordered_dir<T, 2, false>(P, shape, cols, st);
   return inc ? launch_ordered_dir<T, 1, true>(P, shape, cols, st) : launch_ordered_dir<T, 1, false>(P, shape, cols, st);
@@ -488,8 +664,6 @@ gscl_status prepare_ordered(int32_t order, const gscl_stencil *op, const gscl_gr
   if (order < GSCL_I_INC || order > GSCL_K_DEC) return fail(GSCL_ERR_INVALID, "unknown order %d", order);
   const int axis = order / 2;
   const bool inc = order % 2 == 0;
-  if (axis == 0)
-    return fail(GSCL_ERR_UNSUPPORTED, "ordered iteration along x is not built (columns must run along y or z)");
   if (!op) return fail(GSCL_ERR_INVALID, "do_ordered needs an operator");
   if (n_out < 1) return fail(GSCL_ERR_INVALID, "do_ordered needs an output");
   Bound b;
@@ -578,7 +752,8 @@ gscl_status prepare_ordered(int32_t order, const gscl_stencil *op, const gscl_gr
     P.hi[a] = b.hi[a];
   }
   const int other = axis == 2 ? 1 : 2;
-  c->cols = (long long)(b.hi[0] - b.lo[0]) * (b.hi[other] - b.lo[other]);
+  c->cols = axis == 0 ? (long long)(b.hi[1] - b.lo[1]) * (b.hi[2] - b.lo[2])  // rows along x
+                      : (long long)(b.hi[0] - b.lo[0]) * (b.hi[other] - b.lo[other]);
   return GSCL_OK;
 }
 
@@ -606,6 +781,9 @@ extern "C" gscl_status gscl_ordered_specialization(int32_t order, const gscl_ste
   if (!shape) return fail(GSCL_ERR_INVALID, "shape is NULL");
   OrdCall c;
   if (gscl_status s = prepare_ordered(order, op, in, n_in, out, n_out, nullptr, &c)) return s;
-  *shape = ordered_shape(c.P, c.dtype);
+  if (c.axis == 0 && c.P.n_loads > kLoads)
+    return fail(GSCL_ERR_UNSUPPORTED, "ordered iteration along x takes at most %d distinct loads per element", kLoads);
+  const int sh = ordered_shape(c.P, c.dtype);
+  *shape = c.axis == 0 && sh < 0 ? ORD_ROWS_X : sh;
   return GSCL_OK;
 }

@@ -63,7 +63,8 @@ def assert_within(got, ref, S, tol):
 # Ordered iteration spaces: the predecessor offset of each order, and the
 # recurrences compiled for their structure (gscl_ordered_specialization ids
 # 0..4) with the terms in the order that defines each id.
-ORDER_STEP = {B.J_INC: (0, -1, 0), B.J_DEC: (0, 1, 0), B.K_INC: (0, 0, -1), B.K_DEC: (0, 0, 1)}
+ORDER_STEP = {B.I_INC: (-1, 0, 0), B.I_DEC: (1, 0, 0), B.J_INC: (0, -1, 0), B.J_DEC: (0, 1, 0), B.K_INC: (0, 0, -1),
+              B.K_DEC: (0, 0, 1)}
 
 
 def ordered_shape_terms(shape, order):

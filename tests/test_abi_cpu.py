@@ -208,6 +208,19 @@ def test_ordered_recurrences_map_to_compiled_shapes(monkeypatch):
         # more than 8 distinct loads per element: loads per term
         many = [(dx, dy, 0, 1, B.NONE, 0, 1.0) for dx in (-1, 0, 1) for dy in (-1, 0, 1)]
         assert B.ordered_specialization(B.K_INC, many, g[:2], g[:1]) == -2
+        # rows along x: staged in shared memory (up to 8 loads per element),
+        # the same compiled shapes, the interpreted loop reported as -3
+        for order in (B.I_INC, B.I_DEC):
+            for shape in range(5):
+                ins = g[:3] if shape >= 2 else g[:2]
+                assert B.ordered_specialization(order, ordered_shape_terms(shape, order), ins, g[:1]) == shape
+            assert B.ordered_specialization(order,
+                                            [(-1 if order == B.I_INC else 1, 0, 0, 0, B.NONE, B.VALUE, 1.0),
+                                             (0, 0, 0, 1, B.NONE, B.VALUE, 1.0), (0, 0, 0, B.VALUE, B.NONE, 0, 1.0)],
+                                            g[:2], g[:1]) == -3
+        with pytest.raises(B.GsclError) as e:
+            B.ordered_specialization(B.I_INC, many, g[:2], g[:1])
+        assert e.value.status == 10
         monkeypatch.setenv("GSCL_GENERIC_ONLY", "1")
         assert B.ordered_specialization(B.K_INC, ordered_shape_terms(2, B.K_INC), g, g[:1]) == interp
         monkeypatch.delenv("GSCL_GENERIC_ONLY")

@@ -15,7 +15,8 @@ from paper_1207_1746_b300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 NONE, VALUE = B.NONE, B.VALUE
-STEP = {B.J_INC: (0, -1, 0), B.J_DEC: (0, 1, 0), B.K_INC: (0, 0, -1), B.K_DEC: (0, 0, 1)}
+STEP = {B.I_INC: (-1, 0, 0), B.I_DEC: (1, 0, 0), B.J_INC: (0, -1, 0), B.J_DEC: (0, 1, 0), B.K_INC: (0, 0, -1),
+        B.K_DEC: (0, 0, 1)}
 
 
 def integer_grid(seed, n, h, lo=-50, hi=50):
@@ -38,7 +39,7 @@ def run_both(order, terms, arrays, h, n, dtype, n_out=1, alias=(0,), rng=None):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC, B.J_DEC])
+@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC, B.J_DEC, B.I_INC, B.I_DEC])
 def test_running_sum_bitexact(order, dtype):
     n, h = (131, 37, 29), (1, 1, 1)
     x0 = integer_grid(1, n, h, -3, 3)       # the halo seeds the recurrence (interior overwritten)
@@ -49,7 +50,7 @@ def test_running_sum_bitexact(order, dtype):
     assert np.array_equal(got[0], want[0])
 
 
-@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC])
+@pytest.mark.parametrize("order", [B.K_INC, B.K_DEC, B.J_INC, B.I_INC, B.I_DEC])
 def test_subrange_reads_untouched_interior_first(order):
     """A range not starting at the boundary: the first element reads the
     grid's existing value just outside the range."""
@@ -101,8 +102,9 @@ def test_alias_rules_and_unsupported_axis():
     with pytest.raises(B.GsclError) as e:   # a neighbouring column is not ordered
         B.do_ordered(B.K_INC, [(1, 0, -1, 0, NONE, 0, 1.0)], [gx, gf], [gx])
     assert e.value.status == 3
-    with pytest.raises(B.GsclError) as e:
-        B.do_ordered(B.I_INC, [(-1, 0, 0, 0, NONE, 0, 1.0)], [gx, gf], [gx])
+    with pytest.raises(B.GsclError) as e:   # along x: at most 8 distinct loads per element
+        B.do_ordered(B.I_INC, [(dx, dy, 0, 1, NONE, 0, 1.0) for dx in (-1, 0, 1) for dy in (-1, 0, 1)], [gx, gf],
+                     [gx])
     assert e.value.status == 10  # GSCL_ERR_UNSUPPORTED
     # reading the output at offset 0 (its old value) is allowed
     B.do_ordered(B.K_INC, [(0, 0, 0, 0, NONE, 0, 2.0), (0, 0, 0, 1, NONE, 0, 1.0)], [gx, gf], [gx])
@@ -146,3 +148,49 @@ def test_compiled_recurrence_matches_interpreted_and_oracle(shape, order, dtype,
     mine = I.interior_view(got.double().numpy(), n, h)
     tol = {"f64": 1e-13, "f32": 1e-5, "bf16": 5e-2}[dtype]
     assert np.max(np.abs(mine - want)) <= tol * max(1.0, np.max(np.abs(want)))
+
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 1e-5), ("bf16", 5e-2)])
+@pytest.mark.parametrize("order", [B.I_INC, B.I_DEC])
+@pytest.mark.parametrize("n", [(100, 37, 5), (32, 40, 3), (70, 1, 33), (1, 9, 4)])
+def test_rows_along_x_match_oracle(order, dtype, tol, n):
+    """do_i_inc / do_i_dec: rows staged through shared memory in 32-step chunks
+    (row lengths 1, 32, 70, 100; row counts not a multiple of 32), the five
+    compiled recurrence structures and an interpreted two-output bidiagonal
+    pair, against the oracle."""
+    h = (1, 1, 1)
+    d = STEP[order]
+    x0 = I.random_interior(140, n, h, -1.0, 1.0, halo_value=0.5)
+    f = I.random_interior(141, n, h, -1.0, 1.0)
+    m = I.random_interior(142, n, h, -0.9, 0.9)
+    cases = [ordered_shape_terms(k, order) for k in range(5)]
+    cases.append([(0, 0, 0, 2, NONE, 0, 1.0), (*d, 0, 3, 0, -1.0), (0, 0, 0, 2, NONE, 1, 0.5), (*d, 1, NONE, 1, 0.25)])
+    for k, terms in enumerate(cases):
+        if k < 5:
+            arrays = [x0, f] + ([m] if k >= 2 else [])
+            got, want = run_both(order, terms, arrays, h, n, dtype)
+        else:
+            got, want = run_both(order, terms, [x0, x0.copy(), f, m], h, n, dtype, n_out=2)
+        for a, b in zip(got, want):
+            assert np.max(np.abs(a - b)) <= tol * max(1.0, np.max(np.abs(b))), (k, order, dtype, n)
+        gg = [B.Grid(n, h, dtype).upload(a) for a in ([x0, f, m] if k != 5 else [x0, x0, f, m])]
+        assert B.ordered_specialization(order, terms, gg, gg[:1] if k != 5 else gg[:2]) == (k if k < 5 else -3)
+
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("order", [B.I_INC, B.I_DEC])
+def test_rows_along_x_compiled_equal_interpreted(order, dtype, monkeypatch):
+    n, h = (77, 33, 3), (1, 1, 1)
+    arrays = [I.random_interior(150, n, h, -1.0, 1.0, halo_value=0.5), I.random_interior(151, n, h, -1.0, 1.0),
+              I.random_interior(152, n, h, -0.9, 0.9)]
+    for shape in range(5):
+        terms = ordered_shape_terms(shape, order)
+        got = {}
+        for flag in ("0", "1"):
+            monkeypatch.setenv("GSCL_GENERIC_ONLY", flag)
+            gg = [B.Grid(n, h, dtype).upload(a) for a in arrays[:3 if shape >= 2 else 2]]
+            B.do_ordered(order, terms, gg, gg[:1])
+            got[flag] = gg[0].download()
+        assert torch.equal(got["0"], got["1"]), shape
