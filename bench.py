@@ -752,22 +752,29 @@ def run_serving(sample=8, window_s=10.0, rate=200.0, time_cap=30.0, check_every=
         srv = SV.PoissonServer(mode=mode)
         closed[mode] = srv.run_trace(reqs(sample))
     best = max(closed, key=lambda m: closed[m]["solves_per_s"])
-    best_mode = "fp64" if best == "fp64_per_request" else best
-    # literal arrival rate: the offered load is far above capacity, so report the backlog
-    arrivals = I.poisson_arrivals(rate, window_s)
-    srv = SV.PoissonServer(mode=best_mode, check_every=check_every, max_active=32)
-    trace = srv.run_trace(reqs(len(arrivals), arrivals), time_cap=time_cap)
-    trace["rate_per_s"] = rate
-    trace["window_s"] = window_s
-    # load-scaled: arrivals at 70% of the measured capacity of that mode
-    scaled_rate = 0.7 * closed[best]["solves_per_s"]
-    arr2 = I.poisson_arrivals(scaled_rate, 20.0)
-    srv = SV.PoissonServer(mode=best_mode, check_every=check_every, max_active=32)
-    scaled = srv.run_trace(reqs(len(arr2), arr2), time_cap=90.0)
-    scaled["rate_per_s"] = scaled_rate
-    scaled["window_s"] = 20.0
+
+    def traces(mode):
+        # literal arrival rate: the offered load is far above capacity, so report the backlog
+        arrivals = I.poisson_arrivals(rate, window_s)
+        srv = SV.PoissonServer(mode=mode, check_every=check_every, max_active=32)
+        trace = srv.run_trace(reqs(len(arrivals), arrivals), time_cap=time_cap)
+        trace["rate_per_s"] = rate
+        trace["window_s"] = window_s
+        # load-scaled: arrivals at 70% of the measured capacity of that mode
+        scaled_rate = 0.7 * closed[mode]["solves_per_s"]
+        arr2 = I.poisson_arrivals(scaled_rate, 20.0)
+        srv = SV.PoissonServer(mode=mode, check_every=check_every, max_active=32)
+        scaled = srv.run_trace(reqs(len(arr2), arr2), time_cap=90.0)
+        scaled["rate_per_s"] = scaled_rate
+        scaled["window_s"] = 20.0
+        return trace, scaled
+
+    # the configured method (Jacobi sweeps in FP32 with the FP64 correction), and the fastest mode
+    trace, scaled = traces("mixed")
+    best_trace, best_scaled = traces(best) if best not in ("mixed", "fp64_per_request") else (None, None)
     sides = [I.poisson_request(r)[0] for r in range(sample)]
     return {"closed": closed, "trace": trace, "scaled": scaled, "sample_sides": sides, "best": best,
+            "best_trace": best_trace, "best_scaled": best_scaled,
             "speedup_solves_per_s": closed["mixed"]["solves_per_s"] / max(closed["fp64"]["solves_per_s"], 1e-30),
             "speedup_vs_per_request": closed["mixed"]["solves_per_s"]
             / max(closed["fp64_per_request"]["solves_per_s"], 1e-30),
@@ -938,15 +945,18 @@ def main():
     if args.workload == "serving":
         r = run_serving()
         best = r["best"]
-        line = {"metric": "solves/s", "value": round(r["closed"][best]["solves_per_s"], 4), "unit": "solves/s",
+        line = {"metric": "solves/s", "value": round(r["closed"]["mixed"]["solves_per_s"], 4), "unit": "solves/s",
                 "n_gpus": args.gpus, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64" if best.startswith("mixed") else "f64", "data": "synthetic",
-                "config": {"workload": "serving: 3D 7-point Poisson solves, side U{64..256}, f U[-1,1), "
-                                       "stop at relative L2 residual 1e-6 (FP64), HBM-budget admission; value = "
-                                       "the fastest solve mode of the closed sample", "mode": best,
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": {"workload": "serving: 3D 7-point Poisson Jacobi solves, side U{64..256}, f U[-1,1), "
+                                       "stop at relative L2 residual 1e-6 (FP64), FP32 sweeps + FP64 correction, "
+                                       "continuous batching, HBM-budget admission", "mode": "mixed",
                            "sample_sides": r["sample_sides"]},
                 "closed_sample": r["closed"], "poisson_trace_literal": r["trace"],
                 "poisson_trace_load_scaled": r["scaled"],
+                "fastest_mode": {"mode": best, "solves_per_s": round(r["closed"][best]["solves_per_s"], 4),
+                                 "poisson_trace_literal": r["best_trace"],
+                                 "poisson_trace_load_scaled": r["best_scaled"]},
                 "speedup_mixed_vs_fp64": round(r["speedup_solves_per_s"], 3),
                 "speedup_mixed_vs_fp64_per_request": round(r["speedup_vs_per_request"], 3),
                 "speedup_rbsor_vs_mixed": round(r["speedup_rbsor_vs_mixed"], 3),
