@@ -532,6 +532,15 @@ gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_stencil *op, co
 gscl_status gscl_sync(void *stream);
 
 /*
+ * Self-test of the failure path above (no counterpart in the paper): enqueues
+ * one thread that waits, with the library's bounded device-side wait, on a
+ * barrier nothing arrives on.  After about 2 s the wait gives up and flags
+ * the device error word, so the next gscl_sync returns GSCL_ERR_TIMEOUT; the
+ * context stays usable.  Nothing faults, traps or hangs.
+ */
+gscl_status gscl_selftest_bounded_wait(void *stream);
+
+/*
  * Point operators compiled at run time.  In the paper a stencil operator is a
  * C++ function object compiled with the program (Section 3, Fig. 1b), so any
  * arithmetic can run at a core element; here the operator may also be given

@@ -105,6 +105,7 @@ def lib():
         "gscl_do_diamond": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), vp],
         "gscl_program_create": [ctypes.c_char_p, i32, i32, i32, P(i32), P(u64)],
         "gscl_program_destroy": [u64],
+        "gscl_selftest_bounded_wait": [vp],
         "gscl_do_all_program": [u64, P(u64), i32, P(u64), i32, P(RangeC), i32, vp],
         "gscl_do_reduce_program": [u64, i32, P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double), i32, vp,
                                    i64, vp],

@@ -421,3 +421,18 @@ def test_reduce_within_matches_oracle(dtype):
     assert B.do_reduce_within(1e9, op, [gn, gb]) == 0.0
     with pytest.raises(B.GsclError):
         B.do_reduce_within(-1.0, op, [ga, gb])
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable():
+    """A wait on a barrier nothing arrives on gives up after its cycle limit;
+    gscl_sync reports GSCL_ERR_TIMEOUT once, and the next sweeps run normally."""
+    B.check(B.lib().gscl_selftest_bounded_wait(None))
+    with pytest.raises(B.GsclError) as e:
+        B.sync()
+    assert e.value.status == 9
+    B.sync()  # the flag was cleared
+    n, h = (40, 12, 9), (1, 1, 1)
+    u0 = I.random_interior(160, n, h, -1.0, 1.0)
+    f0 = I.random_interior(161, n, h, -1.0, 1.0)
+    got, want, _, _, S_ = run_pair(S.heat7(0.125), [u0, f0], [h, h], n, [h], "f64")
+    assert_within(got[0], want[0], S_[0], TOL["f64"])
