@@ -202,8 +202,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const bool narrow = cfg.narrow && g0.dtype != GSCL_F64 && batch_capable(pl->op);
   const int VX = narrow ? 2 : vx_for(g0.dtype);
   // colour-compacted red-black sweeps: a warp spans 64 VX columns
-  const bool compact = cfg.compact && g0.dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_IEEE && !cfg.generic &&
-                       compact_capable(pl->op) && !reduce;
+  const bool compact = cfg.compact && g0.dtype == GSCL_F64 && !cfg.generic && compact_capable(pl->op) && !reduce;
   const int TX = (compact ? 64 : 32) * VX;
   // reach per input grid (coefficient reads are at the core element)
   int rxa[kMaxIn] = {}, rya[kMaxIn] = {}, rz = 0;
@@ -225,7 +224,8 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   pl->pair = g0.dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_PAIR;
   // inputs read only at the core element go to the two-slot centre ring
   // (all but IEEE FP64; the kernel's operator tables make the same choice)
-  const uint32_t cmask = (g0.dtype == GSCL_F64 && !pl->pair) ? 0u : static_centre_mask(pl->op);
+  // (the colour-compacted kernel reads every input from the plane ring)
+  const uint32_t cmask = (compact || (g0.dtype == GSCL_F64 && !pl->pair)) ? 0u : static_centre_mask(pl->op);
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
   const int VY = narrow ? 4 : vy_for(g0.dtype);

@@ -1034,7 +1034,7 @@ template <> struct BatchCapable<OpIdentity> { static constexpr bool value = true
 template <> struct BatchCapable<OpJacobi5_2D> { static constexpr bool value = true; };
 
 // Operator structures with a colour-compacted kernel (red-black Gauss-Seidel
-// and SOR of the 7-point and 2D 5-point families, IEEE FP64).
+// and SOR of the 7-point and 2D 5-point families, FP64 grids).
 template <class Def> struct CompactCapable { static constexpr bool value = false; };
 template <> struct CompactCapable<OpHeat7Rhs> { static constexpr bool value = true; };
 template <> struct CompactCapable<OpStar7> { static constexpr bool value = true; };
@@ -1071,8 +1071,9 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
     if constexpr (BATCH && !IsFp64Storage<T>::value) {
       if (pl.narrow) return launch_t<T, 2, RED, StaticOp<Def>, BATCH, 4>(pl, stream, occ);
     }
-    // colour-compacted red-black sweeps of the star family on IEEE FP64 grids
-    if constexpr (!BATCH && RED == RED_NONE && std::is_same<T, double>::value && CompactCapable<Def>::value) {
+    // colour-compacted red-black sweeps of the star family on FP64 grids
+    // (IEEE or pair arithmetic)
+    if constexpr (!BATCH && RED == RED_NONE && IsFp64Storage<T>::value && CompactCapable<Def>::value) {
       if (pl.compact) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
     }
     return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
