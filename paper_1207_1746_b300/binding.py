@@ -233,6 +233,13 @@ class Grid:
         hx, hy, hz = self.halo
         return self.view()[hz:hz + nz, hy:hy + ny, hx:hx + nx]
 
+    def zero(self, stream=None):
+        """Sets every cell (halo included) to zero on the device: a memset of
+        the grid's buffer, without a host copy."""
+        with torch.cuda.stream(stream or torch.cuda.current_stream()):
+            self.buf.zero_()
+        return self
+
     def upload(self, host, stream=None):
         """Copies a dense host array (halo included) through gscl_grid_copy_from_host."""
         t = host if isinstance(host, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(host))

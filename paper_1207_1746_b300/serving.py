@@ -137,29 +137,15 @@ class PoissonServer:
     def _start(self, req, need):
         n = (req.n,) * 3
         req.t_admit = self.now()
-        g = {}
-        if self.mode == "rbsor":
-            g["u"] = B.Grid(n, H, "f64").upload(np.zeros_like(req.f))
-            g["f"] = B.Grid(n, H, "f64").upload(req.f)
-        elif self.mode == "mixed_rbsor":
-            z = np.zeros_like(req.f)
-            g["u"] = B.Grid(n, H, "f64").upload(z)
-            g["f"] = B.Grid(n, H, "f64").upload(req.f)
-            g["r"] = B.Grid(n, H, "f64").upload(z)
-            g["da"] = B.Grid(n, H, "f32").upload(z)
-            g["r32"] = B.Grid(n, H, "f32").upload(z)
-        elif self.mode == "fp64":
-            g["u"] = B.Grid(n, H, "f64").upload(np.zeros_like(req.f))
-            g["v"] = B.Grid(n, H, "f64").upload(np.zeros_like(req.f))
-            g["f"] = B.Grid(n, H, "f64").upload(req.f)
-        else:
-            z = np.zeros_like(req.f)
-            g["u"] = B.Grid(n, H, "f64").upload(z)
-            g["f"] = B.Grid(n, H, "f64").upload(req.f)
-            g["r"] = B.Grid(n, H, "f64").upload(z)
-            g["da"] = B.Grid(n, H, "f32").upload(z)
-            g["db"] = B.Grid(n, H, "f32").upload(z)
-            g["r32"] = B.Grid(n, H, "f32").upload(z)
+        # the right-hand side is the request's payload (one host copy); every
+        # other grid starts at zero, halo included, set on the device
+        g = {"f": B.Grid(n, H, "f64").upload(req.f)}
+        zeros = {"rbsor": [("u", "f64")],
+                 "mixed_rbsor": [("u", "f64"), ("r", "f64"), ("da", "f32"), ("r32", "f32")],
+                 "fp64": [("u", "f64"), ("v", "f64")],
+                 "mixed": [("u", "f64"), ("r", "f64"), ("da", "f32"), ("db", "f32"), ("r32", "f32")]}[self.mode]
+        for name, dtype in zeros:
+            g[name] = B.Grid(n, H, dtype).zero()
         slot = _Slot(req=req, grids=g, bytes=need)
         slot.norm_f = B.do_reduce(B.L2, None, [g["f"]])
         if self.mode in ("mixed", "mixed_rbsor"):
