@@ -18,7 +18,7 @@
 // slots can be indexed at run time.  FP32 / FP64 storage (cp.async moves 4 or
 // 8 bytes); BF16 takes the simple path.  Along x (do_i_inc / do_i_dec) a
 // thread per row would put a warp's accesses a whole row apart, so rows go
-// through shared memory in 32-step chunks (ordered_x_kernel below).
+// through shared memory in chunks of 32 or 64 steps (ordered_x_kernel below).
 //
 // The common recurrences (running sums, first-order recurrences, bidiagonal
 // substitution) are also compiled: their shape (which load, output or value
@@ -460,35 +460,60 @@ gscl_status launch_ordered_dir(const OrdParams &P, int shape, long long cols, cu
 
 // ------------------------------------------------------------ ordered along x
 // do_i_inc / do_i_dec: rows along x are walked in order, one lane per row,
-// 32 rows per warp.  A warp stages 32 steps of each distinct load for its 32
-// rows in shared memory (lane j fetches element j of a row: coalesced row
+// 32 rows per warp and one warp per block.  A row is cut into chunks of
+// XChunk<T> steps.  For each chunk the warp stages every distinct load of its
+// 32 rows in shared memory (lane e fetches element e of a row: coalesced row
 // reads, every row of every load in flight at once), walks its rows through
-// those 32 steps reading the transposed tile (lane = row, stride kXC + 1
-// keeps the banks apart), keeps each output's element just written in
-// registers, and writes the 32 steps of every output back with coalesced row
-// stores.  The compiled recurrences and the interpreted term loop compute
-// the same operations in the same order as on the other axes.
-constexpr int kXC = 32;
+// the chunk reading the transposed tile (lane = row; a row stride of
+// XChunk + 1 elements keeps the banks apart), keeps each output's element
+// just written in registers, and writes the chunk of every output back with
+// coalesced row stores.  The load tiles are double-buffered: the copies of
+// chunk c + 1 are in flight while chunk c is computed and stored (an output
+// read as an input is read only at the element itself, which chunk c never
+// writes for chunk c + 1).  The row offsets of every load and output are
+// computed once per lane and shared through shared memory.  The compiled
+// recurrences and the interpreted term loop compute the same operations in
+// the same order as on the other axes.
+template <typename T>
+struct XChunk {
+  static constexpr int value = sizeof(T) == 8 ? 32 : 64;
+};
+
+// Dynamic shared memory of one block (one warp): two buffers of load tiles
+// and one tile per output, 32 rows of XChunk + 1 elements each.
+template <typename T>
+size_t ordered_x_smem(int n_loads, int n_out) {
+  return (size_t)(2 * n_loads + n_out) * 32 * (XChunk<T>::value + 1) * sizeof(T);
+}
 
 struct OrdInterpretedX {};
 
 template <typename T, bool INC, class S>
-__global__ void __launch_bounds__(128) ordered_x_kernel(const __grid_constant__ OrdParams P) {
+__global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ OrdParams P) {
   using A = typename Arith<T>::A;
+  constexpr int KC = XChunk<T>::value;
+  constexpr int TS = KC + 1;     // row stride of a tile
+  constexpr int TILE = 32 * TS;  // one load's or one output's tile: 32 rows
   extern __shared__ __align__(16) unsigned char ox_smem[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // element offset of row r's first element (x = 0) in load l's grid, with
+  // the load's offset, at [l][r]; output m's at [kLoads + m][r]
+  __shared__ int64_t rbase[kLoads + kMaxOut_][32];
+  const int lane = threadIdx.x;
   const int nl = P.n_loads, no = P.n_out;
-  constexpr int TS = kXC + 1;       // row stride of a tile
-  constexpr int TILE = 32 * TS;     // one load's or one output's tile: 32 rows
-  T *lt = reinterpret_cast<T *>(ox_smem) + (size_t)w * (nl + no) * TILE;
-  T *ot = lt + (size_t)nl * TILE;
+  T *lt = reinterpret_cast<T *>(ox_smem);  // load tiles: [buffer][load]
+  T *ot = lt + (size_t)2 * nl * TILE;      // output tiles
   const int64_t ny = P.hi[1] - P.lo[1], rows = ny * (P.hi[2] - P.lo[2]);
-  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * 32;
-  if (row0 >= rows) return;  // the whole warp: only warp-level synchronisation below
+  const int64_t row0 = (int64_t)blockIdx.x * 32;
+  if (row0 >= rows) return;  // the whole warp
   const int64_t my = row0 + lane;
   const bool live = my < rows;
-  const int yl = live ? (int)(P.lo[1] + my % ny) : 0, zl = live ? (int)(P.lo[2] + my / ny) : 0;
+  const int64_t yl = live ? P.lo[1] + my % ny : 0, zl = live ? P.lo[2] + my / ny : 0;
   const int64_t len = P.hi[0] - P.lo[0];
+  for (int l = 0; l < nl; ++l) {
+    const OrdLoad &ld = P.loads[l];
+    rbase[l][lane] = (zl + ld.dz) * P.in_plane[ld.grid] + (yl + ld.dy) * P.in_pitch[ld.grid] + ld.dx;
+  }
+  for (int m = 0; m < no; ++m) rbase[kLoads + m][lane] = zl * P.out_plane[m] + yl * P.out_pitch[m];
   A prev[kMaxOut_];
 #pragma unroll
   for (int m = 0; m < kMaxOut_; ++m) {
@@ -497,35 +522,57 @@ __global__ void __launch_bounds__(128) ordered_x_kernel(const __grid_constant__ 
       prev[m] = to_arith(reinterpret_cast<const T *>(P.out[m])[zl * P.out_plane[m] + yl * P.out_pitch[m] +
                                                                  (INC ? P.lo[0] - 1 : P.hi[0])]);
   }
+  __syncwarp();
   const int nrows = (int)min((int64_t)32, rows - row0);
-  for (int64_t c0 = 0; c0 < len; c0 += kXC) {
-    const int clen = (int)min((int64_t)kXC, len - c0);
-    const int64_t xs = INC ? P.lo[0] + c0 : P.hi[0] - c0 - clen;  // the chunk's lowest x
-    const int sj = INC ? lane : clen - 1 - lane;                    // step of x = xs + lane
-    // every row of every load in flight at once (cp.async for 4- and 8-byte
-    // elements; BF16 rows are copied through registers)
+  const int64_t nchunks = (len + KC - 1) / KC;
+  // chunk c: its length and its lowest x; step j of the chunk is element
+  // e = j (increasing) or e = clen - 1 - j (decreasing) of it
+  auto chunk = [&](int64_t c, int &clen) -> int64_t {
+    const int64_t c0 = c * KC;
+    clen = (int)min((int64_t)KC, len - c0);
+    return INC ? P.lo[0] + c0 : P.hi[0] - c0 - clen;
+  };
+  // stages chunk c of every load into buffer c & 1 (one commit group)
+  auto issue = [&](int64_t c) {
+    int clen;
+    const int64_t xs = chunk(c, clen);
+    T *buf = lt + (size_t)(c & 1) * nl * TILE;
     for (int l = 0; l < nl; ++l) {
-      const OrdLoad &ld = P.loads[l];
-      const T *g = reinterpret_cast<const T *>(P.in[ld.grid]);
+      const T *g = reinterpret_cast<const T *>(P.in[P.loads[l].grid]) + xs;
+      T *tl = buf + l * TILE;
+#pragma unroll 4
       for (int rr = 0; rr < nrows; ++rr) {
-        const int ry = __shfl_sync(0xffffffffu, yl, rr) + ld.dy, rz = __shfl_sync(0xffffffffu, zl, rr) + ld.dz;
-        if (lane < clen) {
-          const T *src = g + (int64_t)rz * P.in_plane[ld.grid] + (int64_t)ry * P.in_pitch[ld.grid] + xs + lane + ld.dx;
-          if constexpr (sizeof(T) >= 4) cp_async(lt + l * TILE + rr * TS + sj, src, (int)sizeof(T));
-          else lt[l * TILE + rr * TS + sj] = *src;
+        const T *src = g + rbase[l][rr];
+#pragma unroll
+        for (int k = 0; k < KC / 32; ++k) {
+          const int e = lane + 32 * k;
+          if (e < clen) {
+            T *d = tl + rr * TS + (INC ? e : clen - 1 - e);
+            if constexpr (sizeof(T) >= 4) cp_async(d, src + e, (int)sizeof(T));
+            else *d = src[e];
+          }
         }
       }
     }
-    if constexpr (sizeof(T) >= 4) {
-      cp_async_commit();
+    if constexpr (sizeof(T) >= 4) cp_async_commit();
+  };
+  issue(0);
+  for (int64_t c = 0; c < nchunks; ++c) {
+    if (c + 1 < nchunks) {
+      issue(c + 1);
+      if constexpr (sizeof(T) >= 4) cp_async_wait<1>();  // chunk c has landed
+    } else if constexpr (sizeof(T) >= 4) {
       cp_async_wait<0>();
     }
     __syncwarp();
-    if constexpr (!std::is_same<S, OrdInterpretedX>::value) {
-      // compiled recurrence: every term's slot a constant
-      if (live) {
-        const T *r = lt + lane * TS;
-        for (int s = 0; s < clen; ++s) {
+    int clen;
+    const int64_t xs = chunk(c, clen);
+    if (live) {
+      const T *r = lt + (size_t)(c & 1) * nl * TILE + lane * TS;
+      T *o_t = ot + lane * TS;
+      if constexpr (!std::is_same<S, OrdInterpretedX>::value) {
+        // compiled recurrence: every term's slot a constant
+        auto step = [&](int s) {
           A v = A(0);
           A o[S::NOUT];
 #pragma unroll
@@ -545,74 +592,82 @@ __global__ void __launch_bounds__(128) ordered_x_kernel(const __grid_constant__ 
 #pragma unroll
           for (int m = 0; m < S::NOUT; ++m) {
             const T y = from_arith<T>(o[m]);
-            ot[m * TILE + lane * TS + s] = y;
+            o_t[m * TILE + s] = y;
             prev[m] = to_arith(y);
           }
+        };
+        if (clen == KC) {
+#pragma unroll 8
+          for (int s = 0; s < KC; ++s) step(s);
+        } else {
+          for (int s = 0; s < clen; ++s) step(s);
         }
-      }
-    } else if (live) {
-      const T *r = lt + lane * TS;
-      for (int s = 0; s < clen; ++s) {
-        A v = A(0);
-        A o[kMaxOut_];
+      } else {
+        for (int s = 0; s < clen; ++s) {
+          A v = A(0);
+          A o[kMaxOut_];
 #pragma unroll
-        for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
-        for (int t = 0; t < P.n_terms; ++t) {
-          const OrdTerm &tm = P.terms[t];
-          A x = v;
-          if (tm.prev >= 0) {
-            x = prev[0];
+          for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
+          for (int t = 0; t < P.n_terms; ++t) {
+            const OrdTerm &tm = P.terms[t];
+            A x = v;
+            if (tm.prev >= 0) {
+              x = prev[0];
 #pragma unroll
-            for (int m = 1; m < kMaxOut_; ++m)
-              if (tm.prev == m) x = prev[m];
-          } else if (tm.xslot >= 0) {
-            x = to_arith(r[tm.xslot * TILE + s]);
+              for (int m = 1; m < kMaxOut_; ++m)
+                if (tm.prev == m) x = prev[m];
+            } else if (tm.xslot >= 0) {
+              x = to_arith(r[tm.xslot * TILE + s]);
+            }
+            if (tm.cslot >= 0) x = x * to_arith(r[tm.cslot * TILE + s]);
+            const A wgt = ord_weight(tm, A(0));
+            if (tm.out < 0) {
+              v = fma(wgt, x, v);
+            } else {
+#pragma unroll
+              for (int m = 0; m < kMaxOut_; ++m)
+                if (tm.out == m) o[m] = fma(wgt, x, o[m]);
+            }
           }
-          if (tm.cslot >= 0) x = x * to_arith(r[tm.cslot * TILE + s]);
-          const A wgt = ord_weight(tm, A(0));
-          if (tm.out < 0) {
-            v = fma(wgt, x, v);
-          } else {
 #pragma unroll
-            for (int m = 0; m < kMaxOut_; ++m)
-              if (tm.out == m) o[m] = fma(wgt, x, o[m]);
-          }
-        }
-#pragma unroll
-        for (int m = 0; m < kMaxOut_; ++m) {
-          if (m < no) {
-            const T y = from_arith<T>(o[m]);
-            ot[m * TILE + lane * TS + s] = y;
-            prev[m] = to_arith(y);
+          for (int m = 0; m < kMaxOut_; ++m) {
+            if (m < no) {
+              const T y = from_arith<T>(o[m]);
+              o_t[m * TILE + s] = y;
+              prev[m] = to_arith(y);
+            }
           }
         }
       }
     }
     __syncwarp();
     for (int m = 0; m < no; ++m) {
-      T *g = reinterpret_cast<T *>(P.out[m]);
+      T *g = reinterpret_cast<T *>(P.out[m]) + xs;
+      const T *to = ot + m * TILE;
+#pragma unroll 4
       for (int rr = 0; rr < nrows; ++rr) {
-        const int ry = __shfl_sync(0xffffffffu, yl, rr), rz = __shfl_sync(0xffffffffu, zl, rr);
-        if (lane < clen)
-          g[(int64_t)rz * P.out_plane[m] + (int64_t)ry * P.out_pitch[m] + xs + lane] = ot[m * TILE + rr * TS + sj];
+        T *dst = g + rbase[kLoads + m][rr];
+#pragma unroll
+        for (int k = 0; k < KC / 32; ++k) {
+          const int e = lane + 32 * k;
+          if (e < clen) dst[e] = to[rr * TS + (INC ? e : clen - 1 - e)];
+        }
       }
     }
-    __syncwarp();
+    __syncwarp();  // the tiles of chunk c are read before chunk c + 2 is staged
   }
 }
 
 template <typename T, class S>
 gscl_status launch_ordered_x_s(const OrdParams &P, bool inc, long long rows, cudaStream_t st) {
-  const size_t per_warp = (size_t)(P.n_loads + P.n_out) * 32 * (kXC + 1) * sizeof(T);
-  const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (200 * 1024) / per_warp));
-  const size_t smem = per_warp * warps;
-  const unsigned blocks = (unsigned)((rows + 32LL * warps - 1) / (32LL * warps));
+  const size_t smem = ordered_x_smem<T>(P.n_loads, P.n_out);
+  const unsigned blocks = (unsigned)((rows + 31) / 32);
   auto kern = inc ? ordered_x_kernel<T, true, S> : ordered_x_kernel<T, false, S>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "ordered kernel set-up");
   }
-  kern<<<blocks, 32 * warps, smem, st>>>(P);
+  kern<<<blocks, 32, smem, st>>>(P);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
 }
