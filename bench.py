@@ -1125,7 +1125,8 @@ def main():
         out = {}
         runs = [("f64", False, False), ("f32", False, False)]
         if not args.profile:
-            runs += [("f64", True, False), ("f32", True, False), ("f64", False, True), ("f32", False, True)]
+            runs += [("f64", True, False), ("f32", True, False)]
+        runs += [("f64", False, True), ("f32", False, True)]
         for dt, interp, along_x in runs:
             r = run_ordered(dt, args.steps, args.warmup, interpreted=interp, along_x=along_x)
             t = dist.max(r["ms_per_step"])

@@ -540,7 +540,7 @@ __global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ O
     for (int l = 0; l < nl; ++l) {
       const T *g = reinterpret_cast<const T *>(P.in[P.loads[l].grid]) + xs;
       T *tl = buf + l * TILE;
-#pragma unroll 4
+#pragma unroll 8
       for (int rr = 0; rr < nrows; ++rr) {
         const T *src = g + rbase[l][rr];
 #pragma unroll
@@ -571,8 +571,10 @@ __global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ O
       const T *r = lt + (size_t)(c & 1) * nl * TILE + lane * TS;
       T *o_t = ot + lane * TS;
       if constexpr (!std::is_same<S, OrdInterpretedX>::value) {
-        // compiled recurrence: every term's slot a constant
-        auto step = [&](int s) {
+        // compiled recurrence: every term's slot a constant.  One step reads
+        // the staged value of load slot l as val(l) and leaves output m's
+        // element in y[m].
+        auto step = [&](auto val, T (&y)[S::NOUT]) {
           A v = A(0);
           A o[S::NOUT];
 #pragma unroll
@@ -583,24 +585,54 @@ __global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ O
             A x;
             if constexpr (st.xs == kSrcValue) x = v;
             else if constexpr (st.xs >= kSrcPrev) x = prev[st.xs - kSrcPrev];
-            else x = to_arith(r[st.xs * TILE + s]);
-            if constexpr (st.cs >= 0) x = x * to_arith(r[st.cs * TILE + s]);
+            else x = val(st.xs);
+            if constexpr (st.cs >= 0) x = x * val(st.cs);
             const A wgt = ord_weight(P.terms[t], A(0));
             if constexpr (st.out < 0) v = fma(wgt, x, v);
             else o[st.out] = fma(wgt, x, o[st.out]);
           });
 #pragma unroll
           for (int m = 0; m < S::NOUT; ++m) {
-            const T y = from_arith<T>(o[m]);
-            o_t[m * TILE + s] = y;
-            prev[m] = to_arith(y);
+            y[m] = from_arith<T>(o[m]);
+            prev[m] = to_arith(y[m]);
           }
         };
         if (clen == KC) {
-#pragma unroll 8
-          for (int s = 0; s < KC; ++s) step(s);
+          // groups of G steps: the next group's staged values are read into
+          // registers before this group is computed (the reads are not held
+          // behind this group's output writes), and a group's outputs are
+          // written to the tile together
+          constexpr int G = 8;
+          A cur[S::NL][G], nxt[S::NL][G];
+          auto fetch = [&](int s0, A(&d)[S::NL][G]) {
+#pragma unroll
+            for (int l = 0; l < S::NL; ++l)
+#pragma unroll
+              for (int g = 0; g < G; ++g) d[l][g] = to_arith(r[l * TILE + s0 + g]);
+          };
+          fetch(0, cur);
+#pragma unroll
+          for (int s0 = 0; s0 < KC; s0 += G) {
+            if (s0 + G < KC) fetch(s0 + G, nxt);
+            T ys[G][S::NOUT];
+#pragma unroll
+            for (int g = 0; g < G; ++g) step([&](int l) { return cur[l][g]; }, ys[g]);
+#pragma unroll
+            for (int g = 0; g < G; ++g)
+#pragma unroll
+              for (int m = 0; m < S::NOUT; ++m) o_t[m * TILE + s0 + g] = ys[g][m];
+#pragma unroll
+            for (int l = 0; l < S::NL; ++l)
+#pragma unroll
+              for (int g = 0; g < G; ++g) cur[l][g] = nxt[l][g];
+          }
         } else {
-          for (int s = 0; s < clen; ++s) step(s);
+          for (int s = 0; s < clen; ++s) {
+            T y[S::NOUT];
+            step([&](int l) { return to_arith(r[l * TILE + s]); }, y);
+#pragma unroll
+            for (int m = 0; m < S::NOUT; ++m) o_t[m * TILE + s] = y[m];
+          }
         }
       } else {
         for (int s = 0; s < clen; ++s) {
@@ -644,7 +676,7 @@ __global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ O
     for (int m = 0; m < no; ++m) {
       T *g = reinterpret_cast<T *>(P.out[m]) + xs;
       const T *to = ot + m * TILE;
-#pragma unroll 4
+#pragma unroll 8
       for (int rr = 0; rr < nrows; ++rr) {
         T *dst = g + rbase[kLoads + m][rr];
 #pragma unroll
