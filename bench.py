@@ -125,6 +125,25 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def warm(fn, warmup, min_s=0.25):
+    """Untimed warm-up: at least `warmup` calls of `fn`, and more until about
+    `min_s` seconds of them have run on the device, so that a workload whose
+    step lasts well under a millisecond still starts its timed region at the
+    GPU's working clocks.  Under --profile only the `warmup` calls run, so
+    that profiler launch counts stay fixed."""
+    import torch
+
+    if PROFILE:
+        min_s = 0.0
+    t0, k = time.perf_counter(), 0
+    while k < warmup or (time.perf_counter() - t0 < min_s and k < 100000):
+        fn()
+        k += 1
+        if k % 4 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
+
+
 # ------------------------------------------------------------------ GPU arm
 def run_gpu(dtype, steps, warmup, dist, n=N_SIDE, sweeps=SWEEPS, clocks=None):
     import torch
@@ -485,9 +504,7 @@ def run_climate(dtype, steps, warmup, sweeps=50):
                 B.do_all(op, cur + fixed, nxt)
             cur, nxt = nxt, cur
 
-    for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
+    warm(step, warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
@@ -535,9 +552,7 @@ def run_ordered(dtype, steps, warmup, n=(256, 256, 80), reps=10, interpreted=Fal
         for _ in range(reps):
             B.do_ordered(order, op, [x, g, m], [x])
 
-    for _ in range(warmup):
-        step()
-    torch.cuda.synchronize()
+    warm(step, warmup)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
@@ -586,9 +601,7 @@ def run_redblack(steps, warmup, n=256, iters=10, solve_n=128, solve=True):
         saved = os.environ.get("GSCL_COLOR_COMPACT")
         os.environ["GSCL_COLOR_COMPACT"] = "1" if compact else "0"
         try:
-            for _ in range(warmup):
-                B.do_colored(op, [u, f], [u], color=0, half_sweeps=2 * iters)
-            torch.cuda.synchronize()
+            warm(lambda: B.do_colored(op, [u, f], [u], color=0, half_sweeps=2 * iters), warmup)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(steps):
@@ -671,9 +684,7 @@ def run_program(dtype, steps, warmup, n=256, sweeps=20):
     out = {"compile_s": compile_s}
     for key, fn in (("program", lambda: prog.run([u, f], [v], sweeps=sweeps)),
                     ("table", lambda: B.do_all(op, [u, f], [v], sweeps=sweeps))):
-        for _ in range(warmup):
-            fn()
-        torch.cuda.synchronize()
+        warm(fn, warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
@@ -708,9 +719,7 @@ def run_diamond(steps, warmup, n=(512, 512, 64), single=(4096, 4096, 1)):
         h = (1, 1, 1) if m[2] > 1 else (1, 1, 0)
         u = B.Grid(m, h, "f64").upload(I.random_interior(808, m, h, -1.0, 1.0, halo_value=0.5))
         f = B.Grid(m, h, "f64").upload(I.random_interior(809, m, h, -1.0, 1.0))
-        for _ in range(warmup):
-            B.do_diamond(op, [u, f], [u])
-        torch.cuda.synchronize()
+        warm(lambda: B.do_diamond(op, [u, f], [u]), warmup)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
