@@ -460,38 +460,47 @@ gscl_status launch_ordered_dir(const OrdParams &P, int shape, long long cols, cu
 
 // ------------------------------------------------------------ ordered along x
 // do_i_inc / do_i_dec: rows along x are walked in order, one lane per row,
-// 32 rows per warp and one warp per block.  A row is cut into chunks of
-// XChunk<T> steps.  For each chunk the warp stages every distinct load of its
-// 32 rows in shared memory (lane e fetches element e of a row: coalesced row
-// reads, every row of every load in flight at once), walks its rows through
-// the chunk reading the transposed tile (lane = row; a row stride of
-// XChunk + 1 elements keeps the banks apart), keeps each output's element
-// just written in registers, and writes the chunk of every output back with
-// coalesced row stores.  The load tiles are double-buffered: the copies of
-// chunk c + 1 are in flight while chunk c is computed and stored (an output
-// read as an input is read only at the element itself, which chunk c never
-// writes for chunk c + 1).  The row offsets of every load and output are
-// computed once per lane and shared through shared memory.  The compiled
-// recurrences and the interpreted term loop compute the same operations in
-// the same order as on the other axes.
+// 32 rows at a time.  A lane walking its row through global memory would put
+// a warp's accesses a whole row apart, so rows go through shared memory in
+// chunks: every distinct load of a chunk is staged for the 32 rows with
+// coalesced row reads (every row of every load in flight at once), the lanes
+// walk their rows through the transposed tile (a row stride of chunk + 1
+// elements keeps the banks apart) keeping each output's element just written
+// in registers, and the outputs of the chunk go back through a transposed
+// output tile with coalesced row stores.  Staging runs ahead of the compute:
+// an output read as an input is read only at the element itself, which no
+// chunk writes for a later one, so early staging reads the right values.
+// The compiled recurrences and the interpreted term loop compute the same
+// operations in the same order as on the other axes.  Two kernels:
+//  - ordered_x_pair_kernel (8-byte elements): blocks of two warps, one
+//    computing and one moving data.  The FP64 recurrence is long (its chain
+//    of dependent FP64-pipe operations), and the second warp takes the
+//    staging and the stores off it.
+//  - ordered_x_kernel (4- and 2-byte elements): one warp per block, which
+//    stages chunk c + 1 before computing and storing chunk c.  Its longer
+//    chunks (64 steps, in the shared memory a warp pair would need for 32)
+//    measured faster where the recurrence itself is cheap.
+struct OrdInterpretedX {};
+
+// One warp per block: load tiles double-buffered, one output tile; the row
+// offsets of every load and output are computed once per lane and shared
+// through shared memory.
 template <typename T>
-struct XChunk {
+struct XChunkWarp {
   static constexpr int value = sizeof(T) == 8 ? 32 : 64;
 };
 
 // Dynamic shared memory of one block (one warp): two buffers of load tiles
-// and one tile per output, 32 rows of XChunk + 1 elements each.
+// and one tile per output, 32 rows of XChunkWarp + 1 elements each.
 template <typename T>
 size_t ordered_x_smem(int n_loads, int n_out) {
-  return (size_t)(2 * n_loads + n_out) * 32 * (XChunk<T>::value + 1) * sizeof(T);
+  return (size_t)(2 * n_loads + n_out) * 32 * (XChunkWarp<T>::value + 1) * sizeof(T);
 }
-
-struct OrdInterpretedX {};
 
 template <typename T, bool INC, class S>
 __global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ OrdParams P) {
   using A = typename Arith<T>::A;
-  constexpr int KC = XChunk<T>::value;
+  constexpr int KC = XChunkWarp<T>::value;
   constexpr int TS = KC + 1;     // row stride of a tile
   constexpr int TILE = 32 * TS;  // one load's or one output's tile: 32 rows
   extern __shared__ __align__(16) unsigned char ox_smem[];
@@ -690,16 +699,267 @@ __global__ void __launch_bounds__(32) ordered_x_kernel(const __grid_constant__ O
   }
 }
 
+// Two warps per block: the first walks the rows, the second moves data.
+// While chunk c is computed the mover has chunk c + 1 staged, is staging
+// chunk c + 2 and is storing chunk c - 1; one block barrier per chunk hands
+// the buffers over (three load buffers, two output buffers).
+template <typename T>
+struct XChunkPair {
+  static constexpr int value = sizeof(T) == 8 ? 16 : 32;
+};
+constexpr int kXLoadBufs = 3;
+
+// Dynamic shared memory of one block: kXLoadBufs buffers of load tiles and
+// two of output tiles, 32 rows of XChunkPair + 1 elements each.
+template <typename T>
+size_t ordered_x_pair_smem(int n_loads, int n_out) {
+  return (size_t)(kXLoadBufs * n_loads + 2 * n_out) * 32 * (XChunkPair<T>::value + 1) * sizeof(T);
+}
+
+template <typename T, bool INC, class S>
+__global__ void __launch_bounds__(64) ordered_x_pair_kernel(const __grid_constant__ OrdParams P) {
+  using A = typename Arith<T>::A;
+  constexpr int KC = XChunkPair<T>::value;
+  constexpr int TS = KC + 1;     // row stride of a tile
+  constexpr int TILE = 32 * TS;  // one load's or one output's tile: 32 rows
+  constexpr int RPI = 32 / KC;   // rows covered by one copy instruction of the mover
+  extern __shared__ __align__(16) unsigned char oxp_smem[];
+  // element offset of row r's first element (x = 0) in load l's grid, with
+  // the load's offset, at [l][r]; output m's at [kLoads + m][r]
+  __shared__ int64_t rbase[kLoads + kMaxOut_][32];
+  const int lane = threadIdx.x & 31;
+  const bool mover = threadIdx.x >= 32;
+  const int nl = P.n_loads, no = P.n_out;
+  T *lt = reinterpret_cast<T *>(oxp_smem);          // load tiles: [buffer][load]
+  T *ot = lt + (size_t)kXLoadBufs * nl * TILE;     // output tiles: [buffer][output]
+  const int64_t ny = P.hi[1] - P.lo[1], rows = ny * (P.hi[2] - P.lo[2]);
+  const int64_t row0 = (int64_t)blockIdx.x * 32;
+  if (row0 >= rows) return;  // the whole block
+  const int64_t my = row0 + lane;
+  const bool live = my < rows;
+  const int64_t yl = live ? P.lo[1] + my % ny : 0, zl = live ? P.lo[2] + my / ny : 0;
+  const int64_t len = P.hi[0] - P.lo[0];
+  A prev[kMaxOut_];
+#pragma unroll
+  for (int m = 0; m < kMaxOut_; ++m) prev[m] = A(0);
+  if (mover) {
+    for (int l = 0; l < nl; ++l) {
+      const OrdLoad &ld = P.loads[l];
+      rbase[l][lane] = (zl + ld.dz) * P.in_plane[ld.grid] + (yl + ld.dy) * P.in_pitch[ld.grid] + ld.dx;
+    }
+    for (int m = 0; m < no; ++m) rbase[kLoads + m][lane] = zl * P.out_plane[m] + yl * P.out_pitch[m];
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int m = 0; m < kMaxOut_; ++m)
+      if (live && m < no && P.need_prev[m])
+        prev[m] = to_arith(reinterpret_cast<const T *>(P.out[m])[zl * P.out_plane[m] + yl * P.out_pitch[m] +
+                                                                   (INC ? P.lo[0] - 1 : P.hi[0])]);
+  }
+  const int nrows = (int)min((int64_t)32, rows - row0);
+  const int64_t nchunks = (len + KC - 1) / KC;
+  // chunk c: its length and its lowest x; step j of the chunk is element
+  // e = j (increasing) or e = clen - 1 - j (decreasing) of it
+  auto chunk = [&](int64_t c, int &clen) -> int64_t {
+    const int64_t c0 = c * KC;
+    clen = (int)min((int64_t)KC, len - c0);
+    return INC ? P.lo[0] + c0 : P.hi[0] - c0 - clen;
+  };
+  // mover lane: row rr0 + lane / KC of a group of RPI rows, element lane % KC
+  const int lr = lane / KC, le = lane % KC;
+  // mover: stages chunk c of every load into load buffer c % kXLoadBufs (one
+  // commit group)
+  auto issue = [&](int64_t c) {
+    int clen;
+    const int64_t xs = chunk(c, clen);
+    T *buf = lt + (size_t)(c % kXLoadBufs) * nl * TILE;
+    for (int l = 0; l < nl; ++l) {
+      const T *g = reinterpret_cast<const T *>(P.in[P.loads[l].grid]) + xs;
+      T *tl = buf + l * TILE;
+#pragma unroll 8
+      for (int r0 = 0; r0 < nrows; r0 += RPI) {
+        const int rr = r0 + lr;
+        if (rr < nrows && le < clen) {
+          const T *src = g + rbase[l][rr] + le;
+          T *d = tl + rr * TS + (INC ? le : clen - 1 - le);
+          if constexpr (sizeof(T) >= 4) cp_async(d, src, (int)sizeof(T));
+          else *d = *src;
+        }
+      }
+    }
+    if constexpr (sizeof(T) >= 4) cp_async_commit();
+  };
+  // mover: writes chunk c of every output back from output buffer c & 1
+  auto store = [&](int64_t c) {
+    int clen;
+    const int64_t xs = chunk(c, clen);
+    const T *buf = ot + (size_t)(c & 1) * no * TILE;
+    for (int m = 0; m < no; ++m) {
+      T *g = reinterpret_cast<T *>(P.out[m]) + xs;
+      const T *to = buf + m * TILE;
+#pragma unroll 8
+      for (int r0 = 0; r0 < nrows; r0 += RPI) {
+        const int rr = r0 + lr;
+        if (rr < nrows && le < clen) g[rbase[kLoads + m][rr] + le] = to[rr * TS + (INC ? le : clen - 1 - le)];
+      }
+    }
+  };
+  if (mover) {
+    issue(0);
+    if (nchunks > 1) {
+      issue(1);
+      if constexpr (sizeof(T) >= 4) cp_async_wait<1>();  // chunk 0 has landed
+    } else if constexpr (sizeof(T) >= 4) {
+      cp_async_wait<0>();
+    }
+  }
+  __syncthreads();
+  // Both warps pass the same barriers: one before the loop and one per chunk.
+  for (int64_t c = 0; c < nchunks; ++c) {
+    int clen;
+    chunk(c, clen);
+    if (mover) {
+      // load buffer (c + 2) % 3 was last read by the compute of chunk c - 1,
+      // output buffer (c - 1) & 1 written by it: both finished before the
+      // barrier that ended the previous chunk
+      if (c + 2 < nchunks) issue(c + 2);
+      if (c >= 1) store(c - 1);
+      if constexpr (sizeof(T) >= 4) {
+        if (c + 2 < nchunks) cp_async_wait<1>();  // chunk c + 1 has landed
+        else cp_async_wait<0>();
+      }
+    } else {
+      if (live) {
+        const T *r = lt + (size_t)(c % kXLoadBufs) * nl * TILE + lane * TS;
+        T *o_t = ot + (size_t)(c & 1) * no * TILE + lane * TS;
+        if constexpr (!std::is_same<S, OrdInterpretedX>::value) {
+          // compiled recurrence: every term's slot a constant.  One step reads
+          // the staged value of load slot l as val(l) and leaves output m's
+          // element in y[m].
+          auto step = [&](auto val, T (&y)[S::NOUT]) {
+            A v = A(0);
+            A o[S::NOUT];
+#pragma unroll
+            for (int m = 0; m < S::NOUT; ++m) o[m] = A(0);
+            static_for<S::NT>([&](auto tc) {
+              constexpr int t = decltype(tc)::value;
+              constexpr OrdShapeTerm st = S::table.t[t];
+              A x;
+              if constexpr (st.xs == kSrcValue) x = v;
+              else if constexpr (st.xs >= kSrcPrev) x = prev[st.xs - kSrcPrev];
+              else x = val(st.xs);
+              if constexpr (st.cs >= 0) x = x * val(st.cs);
+              const A wgt = ord_weight(P.terms[t], A(0));
+              if constexpr (st.out < 0) v = fma(wgt, x, v);
+              else o[st.out] = fma(wgt, x, o[st.out]);
+            });
+#pragma unroll
+            for (int m = 0; m < S::NOUT; ++m) {
+              y[m] = from_arith<T>(o[m]);
+              prev[m] = to_arith(y[m]);
+            }
+          };
+          if (clen == KC) {
+            // groups of G steps: the next group's staged values are read into
+            // registers before this group is computed (the reads are not held
+            // behind this group's output writes), and a group's outputs are
+            // written to the tile together
+            constexpr int G = 8;
+            A cur[S::NL][G], nxt[S::NL][G];
+            auto fetch = [&](int s0, A(&d)[S::NL][G]) {
+#pragma unroll
+              for (int l = 0; l < S::NL; ++l)
+#pragma unroll
+                for (int g = 0; g < G; ++g) d[l][g] = to_arith(r[l * TILE + s0 + g]);
+            };
+            fetch(0, cur);
+#pragma unroll
+            for (int s0 = 0; s0 < KC; s0 += G) {
+              if (s0 + G < KC) fetch(s0 + G, nxt);
+              T ys[G][S::NOUT];
+#pragma unroll
+              for (int g = 0; g < G; ++g) step([&](int l) { return cur[l][g]; }, ys[g]);
+#pragma unroll
+              for (int g = 0; g < G; ++g)
+#pragma unroll
+                for (int m = 0; m < S::NOUT; ++m) o_t[m * TILE + s0 + g] = ys[g][m];
+#pragma unroll
+              for (int l = 0; l < S::NL; ++l)
+#pragma unroll
+                for (int g = 0; g < G; ++g) cur[l][g] = nxt[l][g];
+            }
+          } else {
+            for (int s = 0; s < clen; ++s) {
+              T y[S::NOUT];
+              step([&](int l) { return to_arith(r[l * TILE + s]); }, y);
+#pragma unroll
+              for (int m = 0; m < S::NOUT; ++m) o_t[m * TILE + s] = y[m];
+            }
+          }
+        } else {
+          for (int s = 0; s < clen; ++s) {
+            A v = A(0);
+            A o[kMaxOut_];
+#pragma unroll
+            for (int m = 0; m < kMaxOut_; ++m) o[m] = A(0);
+            for (int t = 0; t < P.n_terms; ++t) {
+              const OrdTerm &tm = P.terms[t];
+              A x = v;
+              if (tm.prev >= 0) {
+                x = prev[0];
+#pragma unroll
+                for (int m = 1; m < kMaxOut_; ++m)
+                  if (tm.prev == m) x = prev[m];
+              } else if (tm.xslot >= 0) {
+                x = to_arith(r[tm.xslot * TILE + s]);
+              }
+              if (tm.cslot >= 0) x = x * to_arith(r[tm.cslot * TILE + s]);
+              const A wgt = ord_weight(tm, A(0));
+              if (tm.out < 0) {
+                v = fma(wgt, x, v);
+              } else {
+#pragma unroll
+                for (int m = 0; m < kMaxOut_; ++m)
+                  if (tm.out == m) o[m] = fma(wgt, x, o[m]);
+              }
+            }
+#pragma unroll
+            for (int m = 0; m < kMaxOut_; ++m) {
+              if (m < no) {
+                const T y = from_arith<T>(o[m]);
+                o_t[m * TILE + s] = y;
+                prev[m] = to_arith(y);
+              }
+            }
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (mover && nchunks > 0) store(nchunks - 1);
+}
+
 template <typename T, class S>
 gscl_status launch_ordered_x_s(const OrdParams &P, bool inc, long long rows, cudaStream_t st) {
-  const size_t smem = ordered_x_smem<T>(P.n_loads, P.n_out);
   const unsigned blocks = (unsigned)((rows + 31) / 32);
-  auto kern = inc ? ordered_x_kernel<T, true, S> : ordered_x_kernel<T, false, S>;
+  size_t smem;
+  int threads;
+  void (*kern)(const OrdParams);
+  if constexpr (sizeof(T) == 8) {
+    smem = ordered_x_pair_smem<T>(P.n_loads, P.n_out);
+    threads = 64;
+    kern = inc ? ordered_x_pair_kernel<T, true, S> : ordered_x_pair_kernel<T, false, S>;
+  } else {
+    smem = ordered_x_smem<T>(P.n_loads, P.n_out);
+    threads = 32;
+    kern = inc ? ordered_x_kernel<T, true, S> : ordered_x_kernel<T, false, S>;
+  }
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "ordered kernel set-up");
   }
-  kern<<<blocks, 32, smem, st>>>(P);
+  kern<<<blocks, threads, smem, st>>>(P);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "ordered kernel launch");
 }

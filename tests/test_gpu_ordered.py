@@ -155,9 +155,10 @@ def test_compiled_recurrence_matches_interpreted_and_oracle(shape, order, dtype,
 @pytest.mark.parametrize("order", [B.I_INC, B.I_DEC])
 @pytest.mark.parametrize("n", [(100, 37, 5), (32, 40, 3), (70, 1, 33), (1, 9, 4), (150, 5, 2)])
 def test_rows_along_x_match_oracle(order, dtype, tol, n):
-    """do_i_inc / do_i_dec: rows staged through shared memory in double-buffered
-    chunks of 32 (FP64) or 64 steps (row lengths 1, 32, 70, 100, 150: partial,
-    single, and up to five chunks; row counts not a multiple of 32), the five
+    """do_i_inc / do_i_dec: rows staged through shared memory in chunks of 16
+    steps by a second warp (FP64) or of 64 steps (row lengths 1, 32, 70, 100,
+    150: partial, single, and up to ten chunks; row counts not a multiple of
+    32), the five
     compiled recurrence structures and an interpreted two-output bidiagonal
     pair, against the oracle."""
     h = (1, 1, 1)
