@@ -113,6 +113,87 @@ __device__ __forceinline__ typename Arith<T>::A dia_term(const DiaParams &P, con
   return r;
 }
 
+// A compiled term that reads a value the wavefront has just produced: the
+// output (input 0) at (i-1, j), (i, j-1) or (i-1, j-1).
+GSCL_HD constexpr int dia_wave(const DiaShapeTerm &st) {
+  return st.in != 0 ? 0 : (st.dx == -1 && st.dy == 0) ? 1 : (st.dx == 0 && st.dy == -1) ? 2
+                                                       : (st.dx == -1 && st.dy == -1) ? 3 : 0;
+}
+
+template <class S>
+GSCL_HD constexpr bool dia_has_sw() {
+  for (int q = 0; q < S::NT; ++q)
+    if (dia_wave(S::table.t[q]) == 3) return true;
+  return false;
+}
+
+// The compiled walk of one tile: lane j computes element (t - j, j) at step
+// t.  The values the wavefront produced reach the element in registers: its
+// own result of step t - 1 is (i-1, j), lane j-1's results of steps t - 1
+// and t - 2 (a warp shuffle) are (i, j-1) and (i-1, j-1); on the tile's first
+// column or row they are the staged apron (finished by an earlier launch).
+// Every other read (old values at dx, dy >= 0 and the right-hand side) is of
+// an element that no step of this launch has written yet, so the reads for
+// step t + 1 are issued during step t.  Results are also written to input
+// 0's tile for the write-back.  Each element takes the same terms in the
+// same order as the interpreted loop.
+template <typename T, class S>
+__device__ __forceinline__ void dia_walk_compiled(const DiaParams &P, T *tiles, int j, int ni, int nj) {
+  using A = typename Arith<T>::A;
+  constexpr int TWc = kDT + 2;
+  constexpr bool kSW = dia_has_sw<S>();
+  T *u = tiles + P.toff[0];
+  const int jrow = (j + 1) * TWc + 1;  // tile offset of element (0, j)
+  const bool jok = j < nj;
+  A pre[S::NT];
+#pragma unroll
+  for (int q = 0; q < S::NT; ++q) pre[q] = A(0);
+  // the reads of element (i, j) that the wavefront does not produce
+  auto prefetch = [&](int i) {
+    if (jok && i >= 0 && i < ni) {
+      const int pos = jrow + i;
+      static_for<S::NT>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr DiaShapeTerm st = S::table.t[q];
+        if constexpr (dia_wave(st) == 0) pre[q] = to_arith(tiles[P.toff[st.in] + pos + st.dy * TWc + st.dx]);
+      });
+    }
+  };
+  prefetch(-j);
+  A prev1 = A(0), prev2 = A(0);  // this lane's results of the last two steps
+  for (int t = 0; t < ni + nj - 1; ++t) {
+    const int i = t - j;
+    const A up1 = __shfl_up_sync(0xffffffffu, prev1, 1);
+    A up2 = A(0);
+    if constexpr (kSW) up2 = __shfl_up_sync(0xffffffffu, prev2, 1);
+    A cur[S::NT];
+#pragma unroll
+    for (int q = 0; q < S::NT; ++q) cur[q] = pre[q];
+    prefetch(i + 1);
+    A res = A(0);
+    if (jok && i >= 0 && i < ni) {
+      const int pos = jrow + i;
+      A o = A(0);
+      static_for<S::NT>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        constexpr DiaShapeTerm st = S::table.t[q];
+        constexpr int wv = dia_wave(st);
+        A x;
+        if constexpr (wv == 1) x = i > 0 ? prev1 : to_arith(u[pos - 1]);
+        else if constexpr (wv == 2) x = j > 0 ? up1 : to_arith(u[pos - TWc]);
+        else if constexpr (wv == 3) x = (i > 0 && j > 0) ? up2 : to_arith(u[pos - TWc - 1]);
+        else x = cur[q];
+        o = fma(dia_weight(P.terms[q], A(0)), x, o);
+      });
+      const T r = from_arith<T>(o);
+      u[pos] = r;
+      res = to_arith(r);
+    }
+    prev2 = prev1;
+    prev1 = res;
+  }
+}
+
 template <typename T, class S>
 __global__ void __launch_bounds__(kDT) diamond_kernel(const __grid_constant__ DiaParams P) {
   using A = typename Arith<T>::A;
@@ -155,54 +236,45 @@ __global__ void __launch_bounds__(kDT) diamond_kernel(const __grid_constant__ Di
   const int64_t y = y0 + j;
   const int ni = (int)min((int64_t)kDT, P.hi[0] - x0), nj = (int)min((int64_t)kDT, P.hi[1] - y0);
   const int centre = P.RY * TW + P.AX;  // offset of the core element of a staged read
-  for (int t = 0; t < ni + nj - 1; ++t) {
-    const int i = t - j;
-    if constexpr (!std::is_same<S, DiaInterpreted>::value) {
-      // compiled: one output, updated in place in input 0's tile
+  if constexpr (!std::is_same<S, DiaInterpreted>::value) {
+    dia_walk_compiled<T, S>(P, tiles, j, ni, nj);
+  } else {
+    for (int t = 0; t < ni + nj - 1; ++t) {
+      const int i = t - j;
       if (j < nj && i >= 0 && i < ni) {
-        constexpr int TWc = kDT + 2;
-        const int pos = j * TWc + i + TWc + 1;
-        A o = A(0);
-        static_for<S::NT>([&](auto qc) {
-          constexpr int q = decltype(qc)::value;
-          constexpr DiaShapeTerm st = S::table.t[q];
-          const T *src = tiles + P.toff[st.in];
-          o = fma(dia_weight(P.terms[q], A(0)), to_arith(src[pos + st.dy * TWc + st.dx]), o);
-        });
-        tiles[P.toff[0] + pos] = from_arith<T>(o);
-      }
-    } else if (j < nj && i >= 0 && i < ni) {
-      const int pos = j * TW + i;
-      A v = A(0);
-      for (int q = 0; q < P.n_value_terms; ++q) {
-        const DiaTerm &tm = P.terms[q];
-        v = fma(dia_weight(tm, A(0)), dia_term<T>(P, tm, tiles, pos, z, y, x0 + i, v), v);
-      }
-      A o[kMaxOut_];
+        const int pos = j * TW + i;
+        A v = A(0);
+        for (int q = 0; q < P.n_value_terms; ++q) {
+          const DiaTerm &tm = P.terms[q];
+          v = fma(dia_weight(tm, A(0)), dia_term<T>(P, tm, tiles, pos, z, y, x0 + i, v), v);
+        }
+        A o[kMaxOut_];
 #pragma unroll
-      for (int m = 0; m < kMaxOut_; ++m) {
-        o[m] = A(0);
-        if (m < P.n_out)
-          for (int q = P.out_begin[m]; q < P.out_begin[m + 1]; ++q) {
-            const DiaTerm &tm = P.terms[q];
-            o[m] = fma(dia_weight(tm, A(0)), dia_term<T>(P, tm, tiles, pos, z, y, x0 + i, v), o[m]);
+        for (int m = 0; m < kMaxOut_; ++m) {
+          o[m] = A(0);
+          if (m < P.n_out)
+            for (int q = P.out_begin[m]; q < P.out_begin[m + 1]; ++q) {
+              const DiaTerm &tm = P.terms[q];
+              o[m] = fma(dia_weight(tm, A(0)), dia_term<T>(P, tm, tiles, pos, z, y, x0 + i, v), o[m]);
+            }
+        }
+        // every output of this element is computed before any is stored
+#pragma unroll
+        for (int m = 0; m < kMaxOut_; ++m) {
+          if (m >= P.n_out) continue;
+          const T val = from_arith<T>(o[m]);
+          if (P.alias[m]) {
+            for (int a = 0; a < P.n_in; ++a)
+              if ((P.alias[m] >> a) & 1u) tiles[P.toff[a] + pos + centre] = val;
+          } else {
+            reinterpret_cast<T *>(P.out[m])[z * P.out_plane[m] + y * P.out_pitch[m] + (x0 + i)] = val;
           }
-      }
-      // every output of this element is computed before any is stored
-#pragma unroll
-      for (int m = 0; m < kMaxOut_; ++m) {
-        if (m >= P.n_out) continue;
-        const T val = from_arith<T>(o[m]);
-        if (P.alias[m]) {
-          for (int a = 0; a < P.n_in; ++a)
-            if ((P.alias[m] >> a) & 1u) tiles[P.toff[a] + pos + centre] = val;
-        } else {
-          reinterpret_cast<T *>(P.out[m])[z * P.out_plane[m] + y * P.out_pitch[m] + (x0 + i)] = val;
         }
       }
+      __syncwarp();
     }
-    __syncwarp();
   }
+  __syncwarp();
 
   // outputs updated in shared memory go back with coalesced rows
   for (int m = 0; m < P.n_out; ++m) {
