@@ -181,6 +181,26 @@ def test_rows_along_x_match_oracle(order, dtype, tol, n):
 
 
 
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 1e-5), ("bf16", 5e-2)])
+@pytest.mark.parametrize("order", [B.I_INC, B.I_DEC])
+@pytest.mark.parametrize("n", [(150, 5, 3), (33, 40, 2)])
+def test_rows_along_x_eight_loads_three_outputs(order, dtype, tol, n):
+    """Rows along x at the largest staging: 8 distinct loads (one grid at five
+    offsets across rows and planes, one at two offsets along x, one behind)
+    and 3 outputs, two of them recurrences; against the oracle."""
+    h = (2, 1, 1)
+    d = STEP[order]
+    arrays = [I.random_interior(160 + k, n, h, -1.0, 1.0, halo_value=0.5) for k in range(6)]
+    x, y, z, a, b, c = range(6)
+    terms = [(0, 0, 0, a, NONE, 0, 1.0), (0, 1, 0, a, NONE, 0, 0.1), (0, -1, 0, a, NONE, 0, 0.1),
+             (0, 0, 1, a, NONE, 0, 0.1), (0, 0, -1, a, NONE, 0, 0.1), (*d, x, NONE, 0, -0.5),
+             (0, 0, 0, b, NONE, 1, 0.5), (2, 0, 0, b, NONE, 1, 0.25), (*d, y, NONE, 1, 0.3),
+             (-1, 0, 0, c, NONE, 2, 1.0), (0, 0, 0, a, NONE, 2, 0.5)]
+    got, want = run_both(order, terms, arrays, h, n, dtype, n_out=3)
+    for g, w in zip(got, want):
+        assert np.max(np.abs(g - w)) <= tol * max(1.0, np.max(np.abs(w))), (order, dtype, n)
+
+
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
 @pytest.mark.parametrize("order", [B.I_INC, B.I_DEC])
 def test_rows_along_x_compiled_equal_interpreted(order, dtype, monkeypatch):
