@@ -1,6 +1,6 @@
-// Ordered iteration spaces (Section 3): do_j_inc / do_j_dec / do_k_inc /
-// do_k_dec visit (i, j-1, k) / (i, j+1, k) / (i, j, k-1) / (i, j, k+1)
-// before (i, j, k).  The operator is a term list as for do_all; an output
+// Ordered iteration spaces (Section 3): do_i_inc / do_i_dec / do_j_inc /
+// do_j_dec / do_k_inc / do_k_dec visit (i-1, j, k) / (i+1, j, k) /
+// (i, j-1, k) / (i, j+1, k) / (i, j, k-1) / (i, j, k+1) before (i, j, k).  The operator is a term list as for do_all; an output
 // bound also as an input is read at the element just visited (a recurrence:
 // running sums, bidiagonal forward and backward substitution, upwind
 // integration along a column).
@@ -18,7 +18,8 @@
 // slots can be indexed at run time.  FP32 / FP64 storage (cp.async moves 4 or
 // 8 bytes); BF16 takes the simple path.  Along x (do_i_inc / do_i_dec) a
 // thread per row would put a warp's accesses a whole row apart, so rows go
-// through shared memory in chunks of 32 or 64 steps (ordered_x_kernel below).
+// through shared memory in chunks of 16 to 64 steps (ordered_x_kernel and
+// ordered_x_pair_kernel below).
 //
 // The common recurrences (running sums, first-order recurrences, bidiagonal
 // substitution) are also compiled: their shape (which load, output or value
