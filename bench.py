@@ -1094,6 +1094,13 @@ def main():
                            "l2": "working set 2 x 134 MB larger than the 126 MB L2, no flush"},
                 "roofline": res["planes"]["roofline"], "variants": {"single_4096": res["single"]},
                 "gpu_launches": args.steps * r["planes"]["launches"]}
+        # the FP64 pipe: five DFMAs per point, one chain per element
+        fma = B_fma() if not args.profile else None
+        if fma:
+            g_ops = 5 * r["planes"]["points"] / (res["planes"]["ms_per_sweep"] * 1e-3) / 1e9
+            peak_ops = fma * 1e3 / 2
+            line["fp64_pipe"] = {"achieved_g_dfma": round(g_ops, 1), "peak_g_dfma_measured": round(peak_ops, 1),
+                                 "frac": round(g_ops / peak_ops, 4)}
         if dist.rank == 0:
             print(json.dumps(line))
         return
