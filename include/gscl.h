@@ -397,11 +397,17 @@ int64_t gscl_reduce_workspace_bytes(void);
  *
  *  - result: one double.  result_on_host = 0: a device pointer, written
  *    asynchronously.  result_on_host = 1: a host pointer; the call copies the
- *    value back and synchronises `stream` before returning.
- *  - workspace: device memory of gscl_reduce_workspace_bytes() bytes, zero
- *    before its first use; every call leaves it ready for the next.  Calls
- *    that may overlap on the GPU (different streams) need separate
- *    workspaces.  GSCL_ERR_OOM if workspace_bytes is too small.
+ *    value back, synchronises `stream` and then reads the device error word
+ *    as gscl_sync does: if a bounded device-side wait gave up (in this call
+ *    or in earlier work on the device) the value is not to be trusted and the
+ *    call returns GSCL_ERR_TIMEOUT (GSCL_ERR_RANGE for a run-time compiled
+ *    operator's out-of-reach read), clearing the flag.
+ *  - workspace: device memory of gscl_reduce_workspace_bytes() bytes.  Each
+ *    call clears the arrival ticket it needs (its first 256 bytes) on
+ *    `stream` before the launch, so the contents left by any earlier call,
+ *    including one whose wait gave up, do not matter.  Calls that may
+ *    overlap on the GPU (different streams) need separate workspaces.
+ *    GSCL_ERR_OOM if workspace_bytes is too small.
  *  - Accumulation is FP64 for every dtype: SUM and L2 are compensated across
  *    z-steps, threads and CTAs, and combined in a fixed order, so a given
  *    launch configuration gives bit-identical results run to run.  An empty

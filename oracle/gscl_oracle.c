@@ -154,7 +154,13 @@ static double orc_term_sum(const orc_extent *e, const orc_grid *in, int n_terms,
     double c = (tm->coef == ORC_NONE) ? 1.0 : orc_read(e, &in[tm->coef], i, j, k);
 #endif
     double w = tm->w;
+#if ORC_MUTANT == 11
+    if (abs_mode) { x = fabs(x); w = fabs(w); } /* the coefficient's absolute value dropped */
+#elif ORC_MUTANT == 12
+    if (abs_mode) { c = fabs(c); w = fabs(w); } /* the read value's absolute value dropped */
+#else
     if (abs_mode) { x = fabs(x); c = fabs(c); w = fabs(w); }
+#endif
     acc = acc + (w * x) * c;
   }
   return acc;

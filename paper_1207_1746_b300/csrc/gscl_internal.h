@@ -45,6 +45,9 @@ gscl_status cuda_fail(cudaError_t e, const char *what);
 
 // Device-side error word of the current device (bounded-wait timeouts).
 int *device_error_word();
+// After a synchronisation: reads and clears the word; GSCL_ERR_TIMEOUT or
+// GSCL_ERR_RANGE if a flag was set, GSCL_OK otherwise.
+gscl_status take_device_error();
 
 // Tensor-map encoder reached through the runtime's driver entry point.
 gscl_status encode_tensor_map_3d(CUtensorMap *map, const Grid &g, uint32_t box_x, uint32_t box_y);

@@ -154,6 +154,23 @@ int *device_error_word() {
   return (int *)p;
 }
 
+// Reads the current device's error word after the caller has synchronised,
+// clears it and turns a set flag into a status (reported once).
+gscl_status take_device_error() {
+  int *word = device_error_word();
+  if (!word) return fail(GSCL_ERR_CUDA, "device error word unavailable");
+  int flag = 0;
+  cudaError_t e = cudaMemcpy(&flag, word, sizeof flag, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+  if (flag) {
+    int zero = 0;
+    cudaMemcpy(word, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (flag & 2) return fail(GSCL_ERR_RANGE, "a run-time compiled operator read outside its declared reach");
+    return fail(GSCL_ERR_TIMEOUT, "a bounded device-side wait gave up (flag %d)", flag);
+  }
+  return GSCL_OK;
+}
+
 // ------------------------------------------------------------------ tensor maps
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
@@ -378,18 +395,7 @@ gscl_status gscl_swap(gscl_grid *a, gscl_grid *b) {
 gscl_status gscl_sync(void *stream) {
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
-  int *word = device_error_word();
-  if (!word) return fail(GSCL_ERR_CUDA, "device error word unavailable");
-  int flag = 0;
-  e = cudaMemcpy(&flag, word, sizeof flag, cudaMemcpyDeviceToHost);
-  if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
-  if (flag) {
-    int zero = 0;
-    cudaMemcpy(word, &zero, sizeof zero, cudaMemcpyHostToDevice);
-    if (flag & 2) return fail(GSCL_ERR_RANGE, "a run-time compiled operator read outside its declared reach");
-    return fail(GSCL_ERR_TIMEOUT, "a bounded device-side wait gave up (flag %d)", flag);
-  }
-  return GSCL_OK;
+  return take_device_error();
 }
 
 }  // extern "C"

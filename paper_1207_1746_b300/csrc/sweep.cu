@@ -550,6 +550,10 @@ gscl_status reduce_call(int red, double within, const gscl_stencil *op, const gs
   } else {
     Plan pl;
     if (gscl_status s = make_plan(b, true, &pl, TileCfg{})) return s;
+    // the arrival ticket starts at zero whatever an earlier call left: a CTA
+    // whose bounded wait gave up returns without taking its ticket
+    cudaError_t e = cudaMemsetAsync(workspace, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync");
     pl.P.workspace = (unsigned char *)workspace;
     pl.P.result = dev_result;
     pl.P.within = within;
@@ -560,6 +564,8 @@ gscl_status reduce_call(int red, double within, const gscl_stencil *op, const gs
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    // a wait that gave up leaves a partial result: report it with the value
+    return take_device_error();
   }
   return GSCL_OK;
 }
@@ -669,6 +675,7 @@ extern "C" gscl_status gscl_do_reduce_noalloc(int32_t reduce_op, const gscl_sten
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync");
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    return take_device_error();
   }
   return GSCL_OK;
 }

@@ -218,6 +218,41 @@ __device__ __forceinline__ void combine_pair(double &s, double &c, double s2, do
   c = (c + c2) - err;
 }
 
+// Sum of squares of FP32 values on the FP32 pipe, held as the unevaluated
+// pair hi + lo (the L2 reduction of FP32 / BF16 sweeps).  Each square is
+// formed exactly as p + pe (the product and its rounding error from one
+// FMA; exact while |x| lies in [2^-50, 2^50], which the caller checks) and
+// added with Knuth's error-free TwoSum, the error going to lo.  The
+// intrinsics keep the compiler from contracting the adds into FMAs, which
+// would break the error-free steps.  renormalize() keeps |lo| within an ulp
+// of hi; the caller widens the pair into the FP64 compensated sum once per
+// z range, so the FP64 pipe sees two adds per range instead of one FMA per
+// element.  Relative error of one range's sum: about (3 + elements) 2^-48.
+struct SquareSum32 {
+  float hi = 0.0f, lo = 0.0f;
+  __device__ __forceinline__ void add_square(float x) {
+    const float p = __fmul_rn(x, x);
+    const float pe = __fmaf_rn(x, x, -p);
+    const float t = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, pe));
+  }
+  __device__ __forceinline__ void renormalize() {
+    const float t = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(t, hi));
+    hi = t;
+  }
+};
+
+// |x| in [2^-50, 2^50] or x == 0: its square and the square's rounding error
+// are normal floats (NaN and infinities fail).
+__device__ __forceinline__ bool square_exact_f32(float x) {
+  const float a = fabsf(x);
+  return a <= 0x1p50f && (a >= 0x1p-50f || a == 0.0f);
+}
+
 __device__ __forceinline__ double max_abs_bits(double a, double b) {
   return __longlong_as_double(
       (long long)max((unsigned long long)__double_as_longlong(a), (unsigned long long)__double_as_longlong(b)));
@@ -621,6 +656,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 
   Compensated acc;
   double sq = 0.0;          // L2: plain FP64 chain of squares within one segment
+  // L2 of FP32 arithmetic (FP32 / BF16 storage): squares summed on the FP32 pipe
+  constexpr bool kSq32 = RED == RED_L2 && std::is_same<A, float>::value;
+  SquareSum32 sq32;
   unsigned long long maxkey = 0;
   uint32_t seq = 0;         // planes issued by this CTA (identical in every thread)
   uint32_t issued_end = 0;  // thread 0: planes actually issued
@@ -811,11 +849,24 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
               }
             }
           }
-          if (RED == RED_MAXABS) {
+          if constexpr (RED == RED_MAXABS) {
 #pragma unroll
             for (int e = 0; e < VX; ++e)
               if (yok[r] && xok[e]) maxkey = max(maxkey, abs_key(v[e]));
-          } else if (RED != RED_NONE) {
+          } else if constexpr (kSq32) {
+            bool exact = true;
+#pragma unroll
+            for (int e = 0; e < VX; ++e) exact &= square_exact_f32(v[e]);
+            if (exact) {
+#pragma unroll
+              for (int e = 0; e < VX; ++e)
+                if (yok[r] && xok[e]) sq32.add_square(v[e]);
+            } else {  // huge, tiny, infinite or NaN values: FP64 squares
+#pragma unroll
+              for (int e = 0; e < VX; ++e)
+                if (yok[r] && xok[e]) sq = fma((double)v[e], (double)v[e], sq);
+            }
+          } else if constexpr (RED != RED_NONE) {
             double d[VX];
             widen_group<VX>(v, d);
             if (RED == RED_L2) {
@@ -831,6 +882,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
             }
           }
         });
+        if constexpr (kSq32) sq32.renormalize();
       }
       smod = adv(smod);
       __syncthreads();
@@ -841,6 +893,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     if (RED == RED_L2) {  // squares are non-negative: the chain's relative error is at most its length x eps
       acc.add(sq);
       sq = 0.0;
+      if constexpr (kSq32) {
+        acc.add((double)sq32.hi);
+        acc.add((double)sq32.lo);
+        sq32 = SquareSum32();
+      }
     }
     if (s_abort) break;
     if constexpr (BATCH && RED != RED_NONE) {
@@ -961,19 +1018,22 @@ template <typename T, int VX, int RED, class Op, bool BATCH, int VY = VyOf<T>::v
 gscl_status launch_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
   auto kern = sweep_kernel<T, VX, VY, RED, Op, BATCH>;
   static std::mutex mu;
-  static size_t attr_set = 0;
+  // the shared-memory limit raised so far, per device (a function attribute
+  // is set on the current device only)
+  constexpr int kAttrDevices = 64;
+  static size_t attr_set[kAttrDevices] = {};
   static int cached_threads = -1, cached_blocks = 0, cached_dev = -1;
   static size_t cached_smem = 0;
   int per_sm = 0;
   {
     std::lock_guard<std::mutex> lk(mu);
-    if (pl.smem > attr_set) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-      attr_set = pl.smem;
-    }
     int dev = 0;
     cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kAttrDevices || pl.smem > attr_set[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+      if (dev >= 0 && dev < kAttrDevices) attr_set[dev] = pl.smem;
+    }
     if (cached_threads != pl.threads || cached_smem != pl.smem || cached_dev != dev) {
       int nb = 0;
       cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, pl.threads, pl.smem);

@@ -26,16 +26,26 @@ gscl_status launch_tb_t(const Plan &pl, cudaStream_t stream) {
   } else {
     auto kern = tb_kernel<T, K, Def>;
     constexpr size_t smem = S::smem_bytes(RHS);
-    static std::once_flag once;
-    static cudaError_t attr_err = cudaSuccess;
-    static int per_sm = 1;
-    std::call_once(once, [&] {
-      attr_err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      int nb = 0;
-      if (attr_err == cudaSuccess) attr_err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem);
-      per_sm = nb > 0 ? nb : 1;
-    });
-    if (attr_err != cudaSuccess) return cuda_fail(attr_err, "temporal-blocking kernel set-up");
+    // the shared-memory attribute is per device: set it, and ask the
+    // occupancy, once on each device the kernel runs on
+    constexpr int kDevices = 64;
+    static std::mutex mu;
+    static int per_sm_of[kDevices] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= kDevices) return fail(GSCL_ERR_UNSUPPORTED, "device %d beyond the supported count", dev);
+    int per_sm = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!per_sm_of[dev]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int nb = 0;
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "temporal-blocking kernel set-up");
+        per_sm_of[dev] = nb > 0 ? nb : 1;
+      }
+      per_sm = per_sm_of[dev];
+    }
     const long long ctas = std::min<long long>(pl.work, (long long)sm_count() * per_sm);
     if (ctas < 1) return GSCL_OK;
     kern<<<(unsigned)ctas, 256, smem, stream>>>(pl.P);

@@ -331,6 +331,76 @@ def test_temporal_blocking_bitexact_with_single_sweeps(monkeypatch, dtype, which
         assert torch.equal(results[K], results["1"]), (K, d.max().item(), int((d > 0).sum()))
 
 
+TEMPORAL_OPS = {  # library operator, oracle operator (the fused form of the same update), lambda, RHS
+    "heat_rhs": (lambda: S.heat7(0.125), 0.125, True),
+    "heat": (lambda: S.heat7(0.125, with_f=False), 0.125, False),
+    "poisson": (lambda: S.poisson_jacobi(), 1.0 / 6.0, True),
+}
+
+
+@pytest.mark.parametrize("which", ["heat_rhs", "heat"])
+@pytest.mark.parametrize("n,hu", [((150, 37, 21), (1, 1, 1)), ((256, 40, 9), (1, 2, 1))])
+def test_temporal_blocking_bitexact_with_oracle_on_integer_data(monkeypatch, which, n, hu):
+    """K sweeps in one pass (K = 1..4) against the oracle's K sweeps, FP32
+    storage, integer data (|u|, |f| <= 64) and lambda = 1/8: after s sweeps
+    every value and every partial sum is a multiple of 2^-3s below 2^7, which
+    FP32 holds exactly for s <= 4, so the GPU's blocked sweeps and the
+    oracle's one-at-a-time FP64 sweeps must agree bit for bit."""
+    mk, lam, rhs = TEMPORAL_OPS[which]
+    rng = np.random.default_rng(70 + n[0])
+    u0 = int_field(rng, I.padded_shape(n, hu), 64)
+    f = int_field(rng, I.padded_shape(n, (0, 0, 0)), 64)
+    for K in (1, 2, 3, 4):
+        monkeypatch.setenv("GSCL_TEMPORAL", str(K))
+        a, b = B.Grid(n, hu, "f32").upload(u0), B.Grid(n, hu, "f32").upload(u0)
+        ins = [a] + ([B.Grid(n, (0, 0, 0), "f32").upload(f)] if rhs else [])
+        B.do_all(mk(), ins, [b], sweeps=K)
+        got = b.download().double().numpy()
+        want, _ = D.heat_run(O.Grid(u0.copy(), hu), O.Grid(f.copy(), (0, 0, 0)) if rhs else None, lam, K)
+        assert np.array_equal(got, want.a), (K, float(np.max(np.abs(got - want.a))))
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("which", ["heat_rhs", "heat", "poisson"])
+def test_temporal_blocking_within_tolerance_of_oracle(monkeypatch, dtype, which):
+    """K sweeps per pass (K = 1..4), 7 sweeps, against the FP64 oracle's 7
+    sweeps from the same storage-rounded data.  Each GPU sweep may differ from
+    the exact update of its own input by tol * S(p) (FP32 storage: 2e-6; BF16:
+    2^-8, one rounding to 8 fraction bits plus FP32 arithmetic), and these
+    updates have non-negative weights summing to 1 with fixed halos, so an
+    error never grows from one sweep to the next: after N sweeps
+    |g - o| <= tol * sum_i max_p S_i(p), S_i the absolute stencil of sweep i.
+    The relative error ||g - o||_inf / ||o||_inf is printed for each K."""
+    mk, lam, rhs = TEMPORAL_OPS[which]
+    tol = {"f32": 2e-6, "bf16": 2.0 ** -8}[dtype]
+    n, hu, sweeps = (150, 37, 21), (1, 1, 1), 7
+    u0 = I.random_interior(63, n, hu, -1.0, 1.0, halo_value=0.375)
+    f = I.random_interior(64, n, (0, 0, 0), -1.0, 1.0)
+    a_o = O.Grid(as_storage(u0, dtype), hu)
+    f_o = O.Grid(as_storage(f, dtype), (0, 0, 0)) if rhs else None
+    terms = D.heat_terms(lam, rhs)
+    bound = 0.0
+    cur = a_o.copy()
+    for _ in range(sweeps):
+        Sab = O.zeros(n, hu)
+        O.do_all(terms, [cur] + ([f_o] if rhs else []), [Sab], abs_mode=True)
+        bound += tol * float(np.max(Sab.interior()))
+        nxt = cur.copy()
+        O.do_all(terms, [cur] + ([f_o] if rhs else []), [nxt])
+        cur = nxt
+    want = cur.a
+    for K in (1, 2, 3, 4):
+        monkeypatch.setenv("GSCL_TEMPORAL", str(K))
+        a, b = B.Grid(n, hu, dtype).upload(u0), B.Grid(n, hu, dtype).upload(u0)
+        ins = [a] + ([B.Grid(n, (0, 0, 0), dtype).upload(f)] if rhs else [])
+        B.do_all(mk(), ins, [b], sweeps=sweeps)
+        got = b.download().double().numpy()
+        err = float(np.max(np.abs(got - want)))
+        print(f"temporal K={K} {which} {dtype}: ||g - o||_inf / ||o||_inf after {sweeps} sweeps = "
+              f"{err / float(np.max(np.abs(want))):.3e} (bound {bound:.3e})")
+        assert err <= bound, (K, err, bound)
+
+
 def test_temporal_tuner_picks_a_factor_and_keeps_bits(monkeypatch):
     monkeypatch.delenv("GSCL_TEMPORAL", raising=False)
     n, h = (128, 64, 48), (1, 1, 1)
@@ -421,6 +491,31 @@ def test_reduce_within_matches_oracle(dtype):
     assert B.do_reduce_within(1e9, op, [gn, gb]) == 0.0
     with pytest.raises(B.GsclError):
         B.do_reduce_within(-1.0, op, [ga, gb])
+
+
+def test_reduce_clears_a_stale_ticket_and_reports_a_timeout():
+    """A workspace whose arrival ticket an interrupted call left non-zero (here
+    planted by hand) still gives the oracle's value: each call clears the
+    ticket first.  A bounded wait that gave up (the self-test sets the same
+    device flag a timed-out reduction sets) is reported by the next reduction
+    that returns its value to the host, as GSCL_ERR_TIMEOUT, once."""
+    n, h = (70, 33, 21), (1, 1, 1)
+    u0 = I.random_interior(171, n, h, -1.0, 1.0)
+    f0 = I.random_interior(172, n, h, -1.0, 1.0)
+    u, F, v = B.Grid(n, h).upload(u0), B.Grid(n, h).upload(f0), B.Grid(n, h).zero()
+    want = O.do_reduce(O.L2, D.heat_terms(0.125), [O.Grid(u0.copy(), h), O.Grid(f0.copy(), h)], [O.zeros(n, h)])
+    ws = B.workspace()
+    ws[:256].fill_(0x5a)
+    B.sync()
+    got = B.do_reduce(B.L2, S.heat7_fused(0.125), [u, F], [v])
+    assert abs(got - want) <= TOL["f64"] * want, (got, want)
+    B.check(B.lib().gscl_selftest_bounded_wait(None))
+    with pytest.raises(B.GsclError) as e:
+        B.do_reduce(B.L2, S.heat7_fused(0.125), [u, F], [v])
+    assert e.value.status == 9
+    got = B.do_reduce(B.L2, S.heat7_fused(0.125), [u, F], [v])  # the flag was cleared
+    assert abs(got - want) <= TOL["f64"] * want, (got, want)
+    B.sync()
 
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable():

@@ -1,8 +1,9 @@
 """Each planted mistake in the oracle (compiled in only with -DORC_MUTANT=k) must
 make at least one pin of tests/test_oracle_pins.py fail: the pins are sharp
 enough to catch a wrong sign, a misplaced coefficient, a dropped term, an
-uncompensated sum, transposed axes, lost NaNs, an ignored fused value or the
-wrong norm.  Each mutant runs in its own process."""
+uncompensated sum, transposed axes, lost NaNs, an ignored fused value, the
+wrong norm or an absolute stencil (the tolerance scale) missing a |.|.
+Each mutant runs in its own process."""
 import json
 import os
 import subprocess
@@ -23,6 +24,8 @@ MUTANTS = {
     8: "1-norm instead of 2-norm",
     9: "red-black colour taken from i + j only",
     10: "do_diamond rows visited in reverse",
+    11: "absolute stencil without |C| on the coefficient",
+    12: "absolute stencil without |X| on the value read",
 }
 
 RUNNER = r"""

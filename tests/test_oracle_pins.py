@@ -283,6 +283,88 @@ def test_bruteforce_dense_matrix(n, halos, seed):
         assert np.max(np.abs(outs[m].interior().ravel() - Om[m] @ x)) <= 1e-13 * scale
 
 
+# ------------------------------------------------- absolute stencil S(p) (abs_mode)
+def distinct_read_terms(rng, n_in, n_out, halos):
+    """A random operator in which no two terms read the same element of the
+    same grid at the same core element (distinct (input, offset) pairs), each
+    output has at most one term reading the returned value, and coefficient
+    grids appear on direct and value terms alike."""
+    pairs = set()
+    terms = []
+    while len(terms) < 13:
+        a = int(rng.integers(0, n_in))
+        hx, hy, hz = halos[a]
+        o = (int(rng.integers(-hx, hx + 1)), int(rng.integers(-hy, hy + 1)), int(rng.integers(-hz, hz + 1)))
+        if (a, o) in pairs:
+            continue
+        pairs.add((a, o))
+        c = int(rng.integers(0, n_in)) if rng.random() < 0.4 else O.NONE
+        m = O.VALUE if len(terms) % 3 == 0 else int(rng.integers(0, n_out))
+        terms.append((*o, a, c, m, float(rng.choice([-1.0, 1.0]) * rng.uniform(0.25, 2.0))))
+    for m in range(n_out):
+        terms.append((0, 0, 0, O.VALUE, int(rng.integers(0, n_in)) if m == 0 else O.NONE, m,
+                      float(rng.uniform(-2.0, -0.5))))
+    return terms
+
+
+@pytest.mark.parametrize("n,halos,seed", [
+    ((6, 5, 4), [(1, 1, 1), (2, 1, 1), (1, 0, 1)], 11),
+    ((7, 6, 1), [(1, 1, 0), (2, 2, 0), (0, 0, 0)], 12),
+])
+def test_abs_stencil_is_abs_matrix_times_abs_input(n, halos, seed):
+    """S(p) = sum_t |w_t| |X_t(p)| |C_t(p)| (with the value's own S for terms that
+    read the value).  For a linear operator whose terms read distinct
+    elements, that is the row of |A| (the element-wise absolute value of the
+    dense matrix assembled independently above) times |x|: no two terms share
+    a matrix entry, and a value term's entries are the value row scaled by
+    w C.  Inputs and coefficients take both signs, so a missing absolute
+    value on any factor changes S."""
+    rng = np.random.default_rng(seed)
+    ins = [O.zeros(n, h) for h in halos]
+    for g in ins:
+        g.a[...] = rng.uniform(-1, 1, g.a.shape)
+        g.a[np.abs(g.a) < 0.05] = -0.5
+    n_out = 2
+    terms = distinct_read_terms(rng, len(ins), n_out, halos)
+    outs = [O.zeros(n, (0, 0, 0)) for _ in range(n_out)]
+    O.do_all(terms, ins, outs, abs_mode=True)
+    val = O.do_all(terms, ins, [O.zeros(n, (0, 0, 0)) for _ in range(n_out)], abs_mode=True, want_value=True)
+    Vm, Om = dense_operator(terms, ins, n_out)
+    ax = np.abs(np.concatenate([g.a.ravel() for g in ins]))
+    want_v = np.abs(Vm) @ ax
+    assert np.allclose(val.ravel(), want_v, rtol=32 * EPS, atol=0.0)
+    for m in range(n_out):
+        want = np.abs(Om[m]) @ ax
+        assert np.allclose(outs[m].interior().ravel(), want, rtol=32 * EPS, atol=0.0), m
+    # S bounds |operator| at every element (triangle inequality), with equality
+    # only where no cancellation occurs
+    plain = [O.zeros(n, (0, 0, 0)) for _ in range(n_out)]
+    O.do_all(terms, ins, plain)
+    for m in range(n_out):
+        assert np.all(np.abs(plain[m].interior()) <= outs[m].interior() * (1 + 32 * EPS))
+
+
+def test_abs_stencil_on_constant_grids():
+    """Closed form: every input constant c_a (negative), so S_value = sum over the
+    value's terms of |w| |c_in| |c_coef|, and S_m adds |w| S_value |c_coef| for
+    the terms of output m that read the value."""
+    n, halos = (5, 4, 3), [(1, 1, 1), (1, 1, 1), (0, 0, 0)]
+    consts = [-2.0, -0.5, -3.0]
+    ins = [O.zeros(n, h) for h in halos]
+    for g, c in zip(ins, consts):
+        g.a[...] = c
+    V, N = O.VALUE, O.NONE
+    terms = [(1, 0, 0, 0, N, V, 1.5), (0, 0, -1, 1, 2, V, -0.25), (0, 0, 0, 0, 1, 0, -1.0),
+             (0, 0, 0, V, 2, 0, 0.5), (0, 1, 0, 1, N, 1, 2.0), (0, 0, 0, V, N, 1, -4.0)]
+    s_val = 1.5 * 2.0 + 0.25 * 0.5 * 3.0
+    s0 = 1.0 * 2.0 * 0.5 + 0.5 * s_val * 3.0
+    s1 = 2.0 * 0.5 + 4.0 * s_val
+    outs = [O.zeros(n, (0, 0, 0)) for _ in range(2)]
+    val = O.do_all(terms, ins, outs, abs_mode=True, want_value=True)
+    assert np.all(val == s_val)
+    assert np.all(outs[0].interior() == s0) and np.all(outs[1].interior() == s1)
+
+
 # ------------------------------------------------------------- paper's operator
 def load_fig1b():
     rows = []
