@@ -799,9 +799,20 @@ def run_serving(sample=8, window_s=10.0, rate=200.0, time_cap=30.0, check_every=
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_sample(n=N_SIDE, sweeps=10):
-    """The FP64 oracle as it stands on a bounded sample: one fused sweep +
-    residual and sweeps-1 plain sweeps of the same 256^3 workload."""
+def host_cores():
+    """Cores this process may run on (its affinity mask), and the machine's count."""
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        avail = os.cpu_count() or 1
+    return avail, os.cpu_count() or avail
+
+
+def oracle_sample(n=N_SIDE, sweeps=10, threads=0):
+    """The FP64 oracle on a bounded sample: one fused sweep + residual and
+    sweeps-1 plain sweeps of the same 256^3 workload.  threads = 0: the
+    checker build (gcc -O2, one thread); threads >= 1: the timing build
+    (-O3 -march=native -fopenmp, same results) on that many threads."""
     from oracle import drivers as D
     from oracle import oracle as O
     from paper_1207_1746_b300 import inputs as I
@@ -810,15 +821,95 @@ def oracle_sample(n=N_SIDE, sweeps=10):
     u0, f = I.heat3d(SEED, n)
     a, b, F = O.Grid(u0.copy(), h), O.Grid(u0.copy(), h), O.Grid(f, h)
     terms = D.heat_terms(LAM)
-    t = time.perf_counter()
-    for s in range(sweeps):
-        if s % EVERY == 0:
-            O.do_reduce(O.L2, terms, [a, F], [b])
-        else:
-            O.do_all(terms, [a, F], [b])
-        a, b = b, a
-    sec = time.perf_counter() - t
-    return {"value": sweeps * n ** 3 / sec / 1e9, "sec": sec, "sweeps": sweeps}
+    used = 1
+    try:
+        if threads >= 1:
+            O.use_library(O.build(timing=True))
+            used = O.threads(threads)
+        t = time.perf_counter()
+        for s in range(sweeps):
+            if s % EVERY == 0:
+                O.do_reduce(O.L2, terms, [a, F], [b])
+            else:
+                O.do_all(terms, [a, F], [b])
+            a, b = b, a
+        sec = time.perf_counter() - t
+    finally:
+        if threads >= 1:
+            O.use_library(None)
+    return {"value": sweeps * n ** 3 / sec / 1e9, "sec": sec, "sweeps": sweeps, "threads": used}
+
+
+def cpu_baseline_heat(n=N_SIDE):
+    """The oracle timed on the host: the timing build on every available core
+    (the line's value) and on one thread, and the checker build on one thread,
+    each over one fused and nine plain sweeps of the 256^3 workload."""
+    avail, total = host_cores()
+    allc = oracle_sample(n, EVERY, threads=avail)
+    one = oracle_sample(n, EVERY, threads=1)
+    chk = oracle_sample(n, EVERY, threads=0)
+    sample = f"{EVERY} sweeps (1 fused + {EVERY - 1} plain) of the 256^3 FP64 grid"
+    return {"value": round(allc["value"], 6), "unit": "GPoint-updates/s", "cores": allc["threads"],
+            "kind": "oracle", "sample": f"{sample}, {allc['sec']:.2f} s",
+            "build": "gcc -O3 -march=native -fopenmp -ffp-contract=off (timing build: planes over threads, "
+                     "same results as the checker)",
+            "nproc": total, "cores_available": avail,
+            "single_thread": {"value": round(one["value"], 6), "cores": 1, "sample": f"{sample}, {one['sec']:.2f} s"},
+            "checker_single_thread": {"value": round(chk["value"], 6), "cores": 1,
+                                      "build": "gcc -O2 -ffp-contract=off (the checker as it stands)",
+                                      "sample": f"{sample}, {chk['sec']:.2f} s"}}
+
+
+def run_error_vs_oracle(n=64, sweeps=SWEEPS):
+    """Error after the step's sweeps against the FP64 oracle, per arithmetic:
+    the heat step's recipe (seed, lambda, fused L2 residual every 10 sweeps)
+    on an n^3 grid, the oracle run in FP64 from the same storage-rounded
+    initial data.  ||g - o||_inf / ||o||_inf of the final grid, and the
+    largest relative error of the residuals."""
+    import numpy as np
+    import torch
+
+    from oracle import drivers as D
+    from oracle import oracle as O
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    h, shape = (1, 1, 1), (n, n, n)
+    u0, f = I.heat3d(SEED, n)
+    tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+    fused, plain = B.Stencil(S.heat7_fused(LAM)), B.Stencil(S.heat7(LAM))
+    oracle_runs = {}
+    out = {"grid": f"{n}^3", "sweeps": sweeps, "residual_every": EVERY}
+    avail, _ = host_cores()
+    for name, dt, arith in (("f64", "f64", "ieee"), ("f64_pair", "f64", "pair"), ("f32", "f32", "ieee"),
+                            ("bf16", "bf16", "ieee")):
+        B.set_fp64_arithmetic(arith)
+        try:
+            u, v, F = B.Grid(shape, h, dt).upload(u0), B.Grid(shape, h, dt).upload(u0), B.Grid(shape, h, dt).upload(f)
+            res = []
+            for _ in range(sweeps // EVERY):
+                res.append(B.do_reduce(B.L2, fused, [u, F], [v]))
+                B.swap(u, v)
+                B.do_all(plain, [u, F], [v], sweeps=EVERY - 1)
+                B.swap(u, v)
+            got = u.download().double().numpy()
+        finally:
+            B.set_fp64_arithmetic("ieee")
+        if dt not in oracle_runs:
+            def rnd(a):
+                return torch.from_numpy(np.ascontiguousarray(a)).to(tdt[dt]).double().numpy()
+            try:
+                O.use_library(O.build(timing=True))  # the checker's numbers, on every core
+                O.threads(avail)
+                oracle_runs[dt] = D.heat_run(O.Grid(rnd(u0), h), O.Grid(rnd(f), h), LAM, sweeps, every=EVERY)
+            finally:
+                O.use_library(None)
+        ou, ores = oracle_runs[dt]
+        err = float(np.max(np.abs(got - ou.a)) / np.max(np.abs(ou.a)))
+        rerr = max(abs(a - b) / b for a, b in zip(res, ores))
+        out[name] = {"rel_inf_error": float(f"{err:.3e}"), "residual_max_rel_error": float(f"{rerr:.3e}")}
+    return out
 
 
 # ------------------------------------------------------------------ roofline
@@ -934,10 +1025,14 @@ def main():
         dist.init("gloo")
         if dist.rank != 0:
             return
-        # a bounded sample per step: one fused and one plain sweep of the 256^3 grid
+        # a bounded sample per step: one fused and one plain sweep of the 256^3
+        # grid, the oracle's timing build on every core this process may use
+        avail, total = host_cores()
         t_all = []
+        used = 1
         for i in range(args.warmup + args.steps):
-            r = oracle_sample(args.n, 2)
+            r = oracle_sample(args.n, 2, threads=avail)
+            used = r["threads"]
             if i >= args.warmup:
                 t_all.append(r["sec"])
         sec = sum(t_all) / len(t_all)
@@ -946,7 +1041,9 @@ def main():
                 "unit": "GPoint-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
-                "cpu_baseline": {"value": round(value, 6), "unit": "GPoint-updates/s", "cores": 1, "kind": "oracle",
+                "cpu_baseline": {"value": round(value, 6), "unit": "GPoint-updates/s", "cores": used, "kind": "oracle",
+                                 "nproc": total,
+                                 "build": "gcc -O3 -march=native -fopenmp -ffp-contract=off (timing build)",
                                  "sample": "per step: 1 fused + 1 plain sweep of the 256^3 grid (of 200)"},
                 "e2e": {"value": round(value, 6), "unit": "GPoint-updates/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -1256,9 +1353,12 @@ def main():
 
     cpu = None
     if dist.rank == 0 and not args.no_cpu:
-        c = oracle_sample(args.n, EVERY)
-        cpu = {"value": round(c["value"], 6), "unit": "GPoint-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{c['sweeps']} sweeps (1 fused + 9 plain) of the 256^3 FP64 grid, {c['sec']:.1f} s"}
+        cpu = cpu_baseline_heat(args.n)
+
+    # error after the step's sweeps against the FP64 oracle, every arithmetic (64^3, outside the timed region)
+    errors = None
+    if dist.rank == 0 and not args.profile and not args.no_cpu:
+        errors = run_error_vs_oracle()
 
     if dist.rank == 0:
         line = {"metric": "GPoint-updates/s", "value": round(value, 3), "unit": "GPoint-updates/s",
@@ -1270,7 +1370,7 @@ def main():
                 "kernel_ms": {"plain_sweep": round(main_run["plain_launch_ms"], 4),
                               "fused_sweep_l2": round(main_run["fused_launch_ms"], 4)},
                 "final_residual": main_run["residuals"][-1], "variants": variants,
-                "fusion_ablation": ablation}
+                "fusion_ablation": ablation, "error_vs_oracle": errors}
         print(json.dumps(line))
 
 

@@ -472,6 +472,35 @@ gscl_status gscl_batch_tile(gscl_batch b, int32_t *tile_x, int32_t *tile_y);
 gscl_status gscl_batch_run(gscl_batch b, int32_t sweeps, int32_t use_graph, void *stream);
 
 /*
+ * Coloured batches: red-black sweeps (Section 3, stateful stencils: the
+ * colour of core element (i, j, k) is the parity of i + j + k) of many
+ * independent grid sets, every half-sweep of all of them in one launch.
+ *
+ * gscl_batch_create_colored takes ops[0 .. n_inst): one operator per
+ * instance.  They must share the structure of ops[0] (the same number of
+ * terms, each with the same offsets, grids and destination) and may differ
+ * in their weights, so each instance can carry its own factor (the SOR
+ * factor that is optimal for its own grid size, for instance).  Instance i
+ * is validated as gscl_do_colored validates one call with ops[i]: its
+ * output may also be an input (the same grid), read at offset 0 or at odd
+ * offsets, and is then updated in place.  n_out >= 1.  Other rules,
+ * ownership and the batch's device tables as gscl_batch_create.
+ *
+ * gscl_batch_run_colored applies each instance's operator at the elements
+ * of colour `color` (0 or 1), then of the other colour, half_sweeps times in
+ * all (GSCL_ERR_INVALID for another colour or half_sweeps < 1), exactly as
+ * gscl_do_colored(ops[i], ..., color, half_sweeps) on each instance alone
+ * (same point arithmetic: bit-identical results).  use_graph != 0 captures
+ * the launches once per (color, half_sweeps) in a CUDA graph and replays
+ * it.  Asynchronous on `stream`.  A coloured batch is run only this way:
+ * gscl_batch_run, gscl_batch_reduce and gscl_batch_tune reject it.
+ */
+gscl_status gscl_batch_create_colored(const gscl_stencil *ops, int32_t n_inst, const gscl_grid *in, int32_t n_in,
+                                      const gscl_grid *out, int32_t n_out, gscl_batch *out_batch);
+gscl_status gscl_batch_run_colored(gscl_batch b, int32_t color, int32_t half_sweeps, int32_t use_graph,
+                                   void *stream);
+
+/*
  * One sweep of the batch's operator (outputs written as gscl_do_reduce
  * writes them) reducing its returned value per instance into results[i]
  * (device memory, n_inst doubles).  Per-instance sums are folded in a fixed

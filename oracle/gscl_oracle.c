@@ -42,6 +42,13 @@
  *        MAXABS : max |v| (NaN if any v is NaN),
  *        L2     : sqrt of the Neumaier-compensated sum of v*v.
  *
+ * Two builds of this file.  The checker (gcc -O2 -ffp-contract=off) runs
+ * every loop in the order written above.  The timing build, used only to
+ * time the oracle as the CPU baseline (-O3 -march=native -fopenmp, still
+ * without FMA contraction), computes independent elements on several
+ * threads, plane by plane, and reduces their values in the same
+ * lexicographic order, so both builds return the same numbers.
+ *
  * Layout (the oracle's own, unrelated to the library's): each grid is a
  * dense C-order array of (nz+2hz) x (ny+2hy) x (nx+2hx) doubles, x fastest;
  * element (i,j,k) of the interior, with -h <= i < n+h, is at
@@ -50,6 +57,10 @@
 #include <math.h>
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 /* ORC_MUTANT (tests only, never set in a normal build) plants one known
  * mistake so the test suite can show that its pins detect it. */
@@ -173,7 +184,13 @@ int orc_do_all(const orc_extent *e, int n_in, const orc_grid *in, int n_out, con
                int abs_mode, double *value_out) {
   int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
   if (rc) return rc;
-  int64_t q = 0;
+  const int64_t nx = hi[0] - lo[0], ny = hi[1] - lo[1];
+  /* Elements are independent (outputs never alias inputs), so the timing
+   * build (-fopenmp) may spread the planes over threads; the values are the
+   * same in any order. */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
   for (int64_t k = lo[2]; k < hi[2]; ++k)
     for (int64_t j = lo[1]; j < hi[1]; ++j)
       for (int64_t i = lo[0]; i < hi[0]; ++i) {
@@ -182,9 +199,21 @@ int orc_do_all(const orc_extent *e, int n_in, const orc_grid *in, int n_out, con
           double r = orc_term_sum(e, in, n_terms, terms, m, v, abs_mode, i, j, k);
           out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r;
         }
-        if (value_out) value_out[q++] = v;
+        if (value_out) value_out[((k - lo[2]) * ny + (j - lo[1])) * nx + (i - lo[0])] = v;
       }
   return ORC_OK;
+}
+
+/* Threads the timing build (-fopenmp) uses from now on (n >= 1); returns the
+ * count in effect, 1 in the correctness build, which has no threads. */
+int orc_threads(int n) {
+#ifdef _OPENMP
+  if (n >= 1) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* Ordered iteration spaces (Section 3): do_i/j/k_inc visit (i-1,j,k),
@@ -297,6 +326,51 @@ static void orc_neumaier_add(orc_neumaier *a, double x) {
   a->s = t;
 }
 
+/* The reduction's running state, fed one value at a time in lexicographic
+ * order. */
+typedef struct {
+  int op;
+  double eps;
+  orc_neumaier acc;
+  double mx;
+  int saw_nan;
+  int all_within; /* logical_and of |v| <= eps (a NaN compares false) */
+} orc_reduction;
+
+static void orc_reduce_add(orc_reduction *r, double v) {
+  if (r->op == ORC_WITHIN) {
+    r->all_within = r->all_within && (fabs(v) <= r->eps);
+  } else if (r->op == ORC_SUM) {
+    orc_neumaier_add(&r->acc, v);
+  } else if (r->op == ORC_L2) {
+#if ORC_MUTANT == 8
+    orc_neumaier_add(&r->acc, fabs(v)); /* norm 1 instead of norm 2 */
+#else
+    orc_neumaier_add(&r->acc, v * v);
+#endif
+  } else {
+#if ORC_MUTANT == 6
+    if (0) r->saw_nan = 1;
+#else
+    if (isnan(v)) r->saw_nan = 1;
+#endif
+    else if (fabs(v) > r->mx) r->mx = fabs(v);
+  }
+}
+
+/* The value reduced at element (i, j, k): In_0 itself with no operator,
+ * else the operator's value, its outputs written as by orc_do_all. */
+static double orc_reduce_element(const orc_extent *e, const orc_grid *in, int n_out, const orc_out_grid *out,
+                                 int n_terms, const orc_term *terms, int64_t i, int64_t j, int64_t k) {
+  if (n_terms == 0) return orc_read(e, &in[0], i, j, k);
+  double v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, 0, i, j, k);
+  for (int m = 0; m < n_out; ++m) {
+    double r = orc_term_sum(e, in, n_terms, terms, m, v, 0, i, j, k);
+    out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r;
+  }
+  return v;
+}
+
 /* do_reduce over [lo, hi): writes the reduced value to *result.  With
  * n_terms == 0 the per-element value is In_0(p) and no output is written;
  * otherwise the operator runs as in orc_do_all (outputs included) and its
@@ -313,46 +387,32 @@ static int reduce_impl(int op, double eps, const orc_extent *e, int n_in, const 
     int rc = orc_check(e, n_in, in, n_out, n_terms, terms, lo, hi);
     if (rc) return rc;
   }
-  orc_neumaier acc = {0.0, 0.0};
-  double mx = 0.0;
-  int saw_nan = 0;
-  int all_within = 1; /* logical_and of |v| <= eps (a NaN compares false) */
+  orc_reduction red = {op, eps, {0.0, 0.0}, 0.0, 0, 1};
+#ifdef _OPENMP
+  /* timing build: every element's value (and outputs) in parallel over
+   * planes into a buffer, then the same lexicographic reduction */
+  const int64_t nx = hi[0] - lo[0], ny = hi[1] - lo[1], nz = hi[2] - lo[2];
+  const int64_t count = (nx > 0 && ny > 0 && nz > 0) ? nx * ny * nz : 0;
+  double *vals = count ? (double *)malloc((size_t)count * sizeof(double)) : NULL;
+  if (count && !vals) return ORC_BAD_ARG;
+#pragma omp parallel for schedule(static)
   for (int64_t k = lo[2]; k < hi[2]; ++k)
     for (int64_t j = lo[1]; j < hi[1]; ++j)
-      for (int64_t i = lo[0]; i < hi[0]; ++i) {
-        double v;
-        if (n_terms == 0) {
-          v = orc_read(e, &in[0], i, j, k);
-        } else {
-          v = orc_term_sum(e, in, n_terms, terms, ORC_VALUE, 0.0, 0, i, j, k);
-          for (int m = 0; m < n_out; ++m) {
-            double r = orc_term_sum(e, in, n_terms, terms, m, v, 0, i, j, k);
-            out[m].data[orc_index(e, out[m].hx, out[m].hy, out[m].hz, i, j, k)] = r;
-          }
-        }
-        if (op == ORC_WITHIN) {
-          all_within = all_within && (fabs(v) <= eps);
-        } else if (op == ORC_SUM) {
-          orc_neumaier_add(&acc, v);
-        } else if (op == ORC_L2) {
-#if ORC_MUTANT == 8
-          orc_neumaier_add(&acc, fabs(v)); /* norm 1 instead of norm 2 */
+      for (int64_t i = lo[0]; i < hi[0]; ++i)
+        vals[((k - lo[2]) * ny + (j - lo[1])) * nx + (i - lo[0])] =
+            orc_reduce_element(e, in, n_out, out, n_terms, terms, i, j, k);
+  for (int64_t q = 0; q < count; ++q) orc_reduce_add(&red, vals[q]);
+  free(vals);
 #else
-          orc_neumaier_add(&acc, v * v);
+  for (int64_t k = lo[2]; k < hi[2]; ++k)
+    for (int64_t j = lo[1]; j < hi[1]; ++j)
+      for (int64_t i = lo[0]; i < hi[0]; ++i)
+        orc_reduce_add(&red, orc_reduce_element(e, in, n_out, out, n_terms, terms, i, j, k));
 #endif
-        } else {
-#if ORC_MUTANT == 6
-          if (0) saw_nan = 1;
-#else
-          if (isnan(v)) saw_nan = 1;
-#endif
-          else if (fabs(v) > mx) mx = fabs(v);
-        }
-      }
-  if (op == ORC_WITHIN) *result = all_within ? 1.0 : 0.0;
-  else if (op == ORC_SUM) *result = acc.s + acc.c;
-  else if (op == ORC_L2) *result = sqrt(acc.s + acc.c);
-  else *result = saw_nan ? NAN : mx;
+  if (op == ORC_WITHIN) *result = red.all_within ? 1.0 : 0.0;
+  else if (op == ORC_SUM) *result = red.acc.s + red.acc.c;
+  else if (op == ORC_L2) *result = sqrt(red.acc.s + red.acc.c);
+  else *result = red.saw_nan ? NAN : red.mx;
   return ORC_OK;
 }
 

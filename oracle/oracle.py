@@ -35,18 +35,32 @@ _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
 
 
-def build(force: bool = False, mutant: int = 0) -> str:
+def build(force: bool = False, mutant: int = 0, timing: bool = False) -> str:
     """Compiles the oracle with plain gcc: -O2, no FMA contraction, no fast-math.
 
-    ``mutant`` > 0 builds a copy with one planted mistake (tests only)."""
-    path = _LIB if mutant == 0 else os.path.join(_LIB_DIR, f"liboracle_mutant{mutant}.so")
+    ``mutant`` > 0 builds a copy with one planted mistake (tests only).
+    ``timing`` builds the copy that is only timed, as the CPU baseline:
+    -O3 -march=native -fopenmp (threads set by ``threads``), still without FMA
+    contraction; it returns the checker's numbers (see the C file)."""
+    if timing:
+        path = os.path.join(_LIB_DIR, "liboracle_omp.so")
+        flags = ["-O3", "-march=native", "-fopenmp"]
+    else:
+        path = _LIB if mutant == 0 else os.path.join(_LIB_DIR, f"liboracle_mutant{mutant}.so")
+        flags = ["-O2"]
     if force or not os.path.exists(path) or os.path.getmtime(path) < os.path.getmtime(_SRC):
         os.makedirs(_LIB_DIR, exist_ok=True)
         tmp = path + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-std=c99", "-O2", "-ffp-contract=off", "-fno-fast-math",
+        subprocess.check_call(["gcc", "-std=c99", *flags, "-ffp-contract=off", "-fno-fast-math",
                                f"-DORC_MUTANT={int(mutant)}", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, path)
     return path
+
+
+def threads(n: int = 0) -> int:
+    """Sets the timing build's thread count (n >= 1) and returns the count in
+    effect (1 for the checker build)."""
+    return int(_get_lib().orc_threads(int(n)))
 
 
 class _Term(ctypes.Structure):
@@ -97,6 +111,8 @@ def _get_lib():
         lib.orc_do_colored.restype = ctypes.c_int
         lib.orc_do_diamond.argtypes = lib.orc_do_reduce.argtypes[1:-1]
         lib.orc_do_diamond.restype = ctypes.c_int
+        lib.orc_threads.argtypes = [ctypes.c_int]
+        lib.orc_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 

@@ -118,6 +118,8 @@ def lib():
         "gscl_batch_destroy": [u64],
         "gscl_batch_info": [u64, P(i32), P(i32), P(i32)],
         "gscl_batch_run": [u64, i32, i32, vp],
+        "gscl_batch_create_colored": [P(StencilC), i32, P(u64), i32, P(u64), i32, P(u64)],
+        "gscl_batch_run_colored": [u64, i32, i32, i32, vp],
         "gscl_batch_reduce": [u64, i32, vp, vp],
         "gscl_batch_tune": [u64, i32, vp, P(i32), P(i32)],
     }
@@ -541,6 +543,33 @@ class Batch:
         check(lib().gscl_batch_tune(self.handle, int(trial_sweeps), stream_ptr(stream), ctypes.byref(w),
                                     ctypes.byref(p)))
         return w.value, p.value
+
+
+class ColoredBatch(Batch):
+    """A coloured batch (gscl_batch_create_colored): red-black sweeps of many
+    instances, every half-sweep of all of them in one launch, each instance
+    with its own operator (``ops[i]``: the structure of ``ops[0]``, its own
+    weights) and updated in place."""
+
+    def __init__(self, ops, instances):
+        self.ops = [as_stencil(o) for o in ops]
+        self.instances = [(list(i), list(o)) for i, o in instances]
+        if len(self.ops) != len(self.instances):
+            raise ValueError("one operator per instance")
+        self.n_in = len(self.instances[0][0])
+        self.n_out = len(self.instances[0][1])
+        arr = (StencilC * len(self.ops))(*[o.c for o in self.ops])
+        ins = [g for i, _ in self.instances for g in i]
+        outs = [g for _, o in self.instances for g in o]
+        h = ctypes.c_uint64()
+        check(lib().gscl_batch_create_colored(arr, len(self.instances), _handles(ins), self.n_in, _handles(outs),
+                                              self.n_out, ctypes.byref(h)))
+        self.handle = h.value
+
+    def run_colored(self, color=0, half_sweeps=1, graph=False, stream=None):
+        """half_sweeps launches, the colour alternating from ``color``."""
+        check(lib().gscl_batch_run_colored(self.handle, int(color), int(half_sweeps), int(bool(graph)),
+                                           stream_ptr(stream)))
 
 
 def sync(stream=None):

@@ -6,6 +6,10 @@
 // (in[0] -> out[0] and back), so a whole sweep group can be captured once in
 // a CUDA graph and replayed.  Per-instance reductions write one partial per
 // segment and a second kernel folds each instance's segments in order.
+// Coloured batches (red-black sweeps, Section 3's stateful stencils) update
+// their instances in place, one colour per launch, and take one operator per
+// instance: the same term structure with the instance's own weights, which
+// the kernel reads from a per-instance weight table.
 #include <stdlib.h>
 #include <string.h>
 
@@ -24,6 +28,9 @@ struct Batch {
   int n_inst = 0, n_in = 0, n_out = 0, dtype = 0;
   std::vector<gscl_term> terms;
   gscl_stencil st{};
+  bool colored = false;                           // red-black batch: in place, one operator per instance
+  std::vector<std::vector<gscl_term>> inst_terms;  // coloured batches: instance i's operator
+  std::vector<gscl_stencil> inst_st;
   std::vector<gscl_grid> in_h, out_h;
   bool has_value = false;
   TileCfg cfg;
@@ -38,7 +45,9 @@ struct Batch {
   Segment *segs = nullptr;
   int32_t *cta_seg = nullptr, *inst_seg = nullptr;
   double *partials = nullptr;
-  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;  // (first table, sweeps)
+  InstWeights *wtab = nullptr;  // one weight row per instance
+  // (first table, sweeps) or, for coloured batches, (2 + first colour, half-sweeps)
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   cudaStream_t cap_stream = nullptr;
   std::mutex mu;
 };
@@ -71,23 +80,27 @@ gscl_status build(Batch *bt) {
   tabs[1].resize(n);
   std::vector<long long> work(n);
   std::vector<int64_t> nz(n);
+  std::vector<InstWeights> wrows(n);
   bt->buf_a.assign(n, nullptr);
   bt->buf_b.assign(n, nullptr);
   TileCfg cfg = bt->cfg;
   for (int i = 0; i < n; ++i) {
     Bound b;
-    if (gscl_status s = bind(&bt->st, false, &bt->in_h[(size_t)i * bt->n_in], bt->n_in,
-                             bt->n_out ? &bt->out_h[(size_t)i * bt->n_out] : nullptr, bt->n_out, nullptr, &b))
+    const gscl_stencil *op = bt->colored ? &bt->inst_st[i] : &bt->st;
+    if (gscl_status s = bind(op, false, &bt->in_h[(size_t)i * bt->n_in], bt->n_in,
+                             bt->n_out ? &bt->out_h[(size_t)i * bt->n_out] : nullptr, bt->n_out, nullptr, &b, -1, 0,
+                             bt->colored))
       return s;
     if (b.in[0].dtype != bt->dtype) return fail(GSCL_ERR_DTYPE, "instance %d has another dtype", i);
     if (b.empty) return fail(GSCL_ERR_INVALID, "instance %d has an empty interior", i);
-    if (bt->n_out && (b.in[0].halo[0] != b.out[0].halo[0] || b.in[0].halo[1] != b.out[0].halo[1] ||
-                      b.in[0].halo[2] != b.out[0].halo[2] || overlaps(b.in[0], b.out[0])))
+    if (!bt->colored && bt->n_out &&
+        (b.in[0].halo[0] != b.out[0].halo[0] || b.in[0].halo[1] != b.out[0].halo[1] ||
+         b.in[0].halo[2] != b.out[0].halo[2] || overlaps(b.in[0], b.out[0])))
       return fail(GSCL_ERR_SHAPE, "instance %d: in[0] and out[0] must be distinct grids of one layout", i);
     for (int dir = 0; dir < 2; ++dir) {
       Bound bd = b;
       if (dir == 1) {
-        if (bt->n_out < 1) break;
+        if (bt->n_out < 1 || bt->colored) break;  // coloured batches work in place: one direction
         std::swap(bd.in[0], bd.out[0]);
         for (int a = 1; a < bt->n_in; ++a)
           if (bd.in_h[a] == bd.in_h[0]) bd.in[a] = bd.in[0];
@@ -110,10 +123,17 @@ gscl_status build(Batch *bt) {
       if (dir == 0) {
         work[i] = pl.work;
         nz[i] = pl.P.inst.hi[2] - pl.P.inst.lo[2];
+        // this instance's weights in the order of the launch's term table
+        memset(&wrows[i], 0, sizeof(InstWeights));
+        for (int k = 0; k < pl.P.out_begin[pl.P.n_out]; ++k) {
+          wrows[i].wd[k] = pl.P.terms[k].wd;
+          wrows[i].wf[k] = pl.P.terms[k].wf;
+          wrows[i].wl[k] = pl.P.terms[k].wl;
+        }
       }
     }
     bt->buf_a[i] = b.in[0].buf;
-    bt->buf_b[i] = bt->n_out ? b.out[0].buf : nullptr;
+    bt->buf_b[i] = (bt->n_out && !bt->colored) ? b.out[0].buf : nullptr;
   }
   Plan &base = bt->base;
   base.batch = true;
@@ -154,7 +174,8 @@ gscl_status build(Batch *bt) {
   const size_t c_bytes = align_up(sizeof(int32_t) * (G + 1), 256);
   const size_t i_bytes = align_up(sizeof(int32_t) * (n + 1), 256);
   const size_t p_bytes = align_up(16 * segs.size(), 256);
-  const size_t need = 2 * t_bytes + s_bytes + c_bytes + i_bytes + p_bytes;
+  const size_t w_bytes = align_up(sizeof(InstWeights) * n, 256);
+  const size_t need = 2 * t_bytes + s_bytes + c_bytes + i_bytes + p_bytes + w_bytes;
   if (need > bt->dev_bytes) {
     if (bt->dev) cudaFree(bt->dev);
     bt->dev = nullptr;
@@ -170,9 +191,11 @@ gscl_status build(Batch *bt) {
   bt->cta_seg = (int32_t *)(p + 2 * t_bytes + s_bytes);
   bt->inst_seg = (int32_t *)(p + 2 * t_bytes + s_bytes + c_bytes);
   bt->partials = (double *)(p + 2 * t_bytes + s_bytes + c_bytes + i_bytes);
+  bt->wtab = (InstWeights *)(p + 2 * t_bytes + s_bytes + c_bytes + i_bytes + p_bytes);
   cudaError_t e = cudaMemcpy(bt->tab[0], tabs[0].data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && bt->n_out)
+  if (e == cudaSuccess && bt->n_out && !bt->colored)
     e = cudaMemcpy(bt->tab[1], tabs[1].data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(bt->wtab, wrows.data(), sizeof(InstWeights) * n, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(bt->segs, segs.data(), sizeof(Segment) * segs.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(bt->cta_seg, cta_seg.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(bt->inst_seg, inst_seg.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
@@ -183,6 +206,7 @@ gscl_status build(Batch *bt) {
   base.P.segs = bt->segs;
   base.P.cta_seg = bt->cta_seg;
   base.P.seg_partials = bt->partials;
+  base.P.inst_w = bt->wtab;
   bt->built = true;
   return GSCL_OK;
 }
@@ -219,6 +243,48 @@ gscl_status enqueue_sweeps(Batch *bt, int first, int sweeps, cudaStream_t stream
   return GSCL_OK;
 }
 
+// half_sweeps launches of a coloured batch, the colour alternating from `color`.
+gscl_status enqueue_colored(Batch *bt, int color, int half_sweeps, cudaStream_t stream) {
+  Plan pl = bt->base;
+  pl.P.insts = bt->tab[0];
+  for (int h = 0; h < half_sweeps; ++h) {
+    pl.P.color = (color + h) & 1;
+    if (gscl_status st = launch(pl, bt->dtype, RED_NONE, stream, nullptr)) return st;
+  }
+  return GSCL_OK;
+}
+
+// Replays (capturing it first, once) the graph of `key`'s launches, or
+// enqueues them directly.
+template <class Enqueue>
+gscl_status run_group(Batch *bt, std::pair<int, int> key, bool use_graph, cudaStream_t st, Enqueue enqueue) {
+  if (!use_graph) return enqueue(st);
+  auto it = bt->graphs.find(key);
+  if (it == bt->graphs.end()) {
+    if (!bt->cap_stream) {
+      cudaError_t e = cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
+    }
+    cudaError_t e = cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+    gscl_status s = enqueue(bt->cap_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(bt->cap_stream, &graph);
+    if (s != GSCL_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    it = bt->graphs.emplace(key, exec).first;
+  }
+  cudaError_t e = cudaGraphLaunch(it->second, st);
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "cudaGraphLaunch");
+}
+
 template <int RED>
 gscl_status finalize(Batch *bt, double *results, cudaStream_t stream) {
   const int threads = 128;
@@ -226,6 +292,68 @@ gscl_status finalize(Batch *bt, double *results, cudaStream_t stream) {
       bt->partials, bt->inst_seg, bt->n_inst, results);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "batch finalize launch");
+}
+
+// gscl_batch_create and gscl_batch_create_colored: ops holds one operator
+// (plain batches) or one per instance (coloured batches).
+gscl_status create_batch(const gscl_stencil *ops, bool colored, int32_t n_inst, const gscl_grid *in, int32_t n_in,
+                         const gscl_grid *out, int32_t n_out, gscl_batch *out_batch) {
+  if (!out_batch) return fail(GSCL_ERR_INVALID, "out_batch is required");
+  *out_batch = 0;
+  if (n_inst < 1 || n_inst > (1 << 20)) return fail(GSCL_ERR_INVALID, "n_inst = %d outside [1, 2^20]", n_inst);
+  const gscl_stencil *op = ops;
+  if (!op || !op->terms || op->n_terms < 1 || op->n_terms > kMaxTerms)
+    return fail(GSCL_ERR_INVALID, "a batch needs an operator with 1..%d terms", kMaxTerms);
+  if (n_in < 1 || n_in > kMaxIn || n_out < 0 || n_out > kMaxOut_ || !in || (n_out && !out))
+    return fail(GSCL_ERR_INVALID, "bad grid counts or arrays");
+  if (colored && n_out < 1) return fail(GSCL_ERR_INVALID, "a coloured batch needs an output");
+  std::unique_ptr<Batch> bt(new Batch());
+  bt->n_inst = n_inst;
+  bt->n_in = n_in;
+  bt->n_out = n_out;
+  bt->colored = colored;
+  bt->terms.assign(op->terms, op->terms + op->n_terms);
+  bt->st = gscl_stencil{op->n_terms, 0, bt->terms.data()};
+  if (colored) {
+    // one operator per instance, all of the first one's structure
+    bt->inst_terms.resize(n_inst);
+    bt->inst_st.resize(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+      const gscl_stencil &oi = ops[i];
+      if (!oi.terms || oi.n_terms != op->n_terms)
+        return fail(GSCL_ERR_INVALID, "instance %d: its operator must have the first one's %d terms", i, op->n_terms);
+      for (int t = 0; t < op->n_terms; ++t) {
+        const gscl_term &a = oi.terms[t], &b = op->terms[t];
+        if (a.dx != b.dx || a.dy != b.dy || a.dz != b.dz || a.in != b.in || a.coef != b.coef || a.out != b.out)
+          return fail(GSCL_ERR_INVALID, "instance %d: term %d differs from the first operator's beyond its weight",
+                      i, t);
+      }
+      bt->inst_terms[i].assign(oi.terms, oi.terms + oi.n_terms);
+      bt->inst_st[i] = gscl_stencil{oi.n_terms, 0, bt->inst_terms[i].data()};
+    }
+  }
+  bt->in_h.assign(in, in + (size_t)n_inst * n_in);
+  if (n_out) bt->out_h.assign(out, out + (size_t)n_inst * n_out);
+  for (auto &t : bt->terms)
+    if (t.out == GSCL_VALUE) bt->has_value = true;
+  // GSCL_BATCH_NARROW=1 starts the batch on the narrow tiles (the tuner
+  // chooses between the shapes by timing)
+  if (const char *e = getenv("GSCL_BATCH_NARROW")) bt->cfg.narrow = atoi(e) != 0;
+  // coloured batches of FP64 grids use the colour-compacted kernel where it
+  // exists, as gscl_do_colored does (GSCL_COLOR_COMPACT=0 turns it off)
+  if (colored) {
+    const char *e = getenv("GSCL_COLOR_COMPACT");
+    bt->cfg.compact = !(e && e[0] == '0');
+  }
+  Grid g0;
+  if (gscl_status s = lookup(bt->in_h[0], &g0)) return s;
+  bt->dtype = g0.dtype;
+  if (gscl_status s = build(bt.get())) return s;  // validates every instance
+  std::lock_guard<std::mutex> lk(g_batch_mu);
+  const uint64_t id = g_next_batch++;
+  g_batches[id].reset(bt.release());
+  *out_batch = id;
+  return GSCL_OK;
 }
 
 }  // namespace
@@ -237,35 +365,26 @@ extern "C" {
 
 gscl_status gscl_batch_create(const gscl_stencil *op, int32_t n_inst, const gscl_grid *in, int32_t n_in,
                               const gscl_grid *out, int32_t n_out, gscl_batch *out_batch) {
-  if (!out_batch) return fail(GSCL_ERR_INVALID, "out_batch is required");
-  *out_batch = 0;
-  if (!op || !op->terms || op->n_terms < 1 || op->n_terms > kMaxTerms)
-    return fail(GSCL_ERR_INVALID, "a batch needs an operator with 1..%d terms", kMaxTerms);
-  if (n_inst < 1 || n_inst > (1 << 20)) return fail(GSCL_ERR_INVALID, "n_inst = %d outside [1, 2^20]", n_inst);
-  if (n_in < 1 || n_in > kMaxIn || n_out < 0 || n_out > kMaxOut_ || !in || (n_out && !out))
-    return fail(GSCL_ERR_INVALID, "bad grid counts or arrays");
-  std::unique_ptr<Batch> bt(new Batch());
-  bt->n_inst = n_inst;
-  bt->n_in = n_in;
-  bt->n_out = n_out;
-  bt->terms.assign(op->terms, op->terms + op->n_terms);
-  bt->st = gscl_stencil{op->n_terms, 0, bt->terms.data()};
-  bt->in_h.assign(in, in + (size_t)n_inst * n_in);
-  if (n_out) bt->out_h.assign(out, out + (size_t)n_inst * n_out);
-  for (auto &t : bt->terms)
-    if (t.out == GSCL_VALUE) bt->has_value = true;
-  // GSCL_BATCH_NARROW=1 starts the batch on the narrow tiles (the tuner
-  // chooses between the shapes by timing)
-  if (const char *e = getenv("GSCL_BATCH_NARROW")) bt->cfg.narrow = atoi(e) != 0;
-  Grid g0;
-  if (gscl_status s = lookup(bt->in_h[0], &g0)) return s;
-  bt->dtype = g0.dtype;
-  if (gscl_status s = build(bt.get())) return s;  // validates every instance
-  std::lock_guard<std::mutex> lk(g_batch_mu);
-  const uint64_t id = g_next_batch++;
-  g_batches[id].reset(bt.release());
-  *out_batch = id;
-  return GSCL_OK;
+  return create_batch(op, false, n_inst, in, n_in, out, n_out, out_batch);
+}
+
+gscl_status gscl_batch_create_colored(const gscl_stencil *ops, int32_t n_inst, const gscl_grid *in, int32_t n_in,
+                                      const gscl_grid *out, int32_t n_out, gscl_batch *out_batch) {
+  return create_batch(ops, true, n_inst, in, n_in, out, n_out, out_batch);
+}
+
+gscl_status gscl_batch_run_colored(gscl_batch h, int32_t color, int32_t half_sweeps, int32_t use_graph,
+                                   void *stream) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  if (color != 0 && color != 1) return fail(GSCL_ERR_INVALID, "color must be 0 or 1, got %d", color);
+  if (half_sweeps < 1) return fail(GSCL_ERR_INVALID, "half_sweeps must be >= 1");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  if (!bt->colored) return fail(GSCL_ERR_INVALID, "not a coloured batch (gscl_batch_create_colored makes one)");
+  int first = 0;
+  if (gscl_status s = current_table(bt, &first)) return s;
+  return run_group(bt, std::make_pair(2 + color, (int)half_sweeps), use_graph != 0, (cudaStream_t)stream,
+                   [&](cudaStream_t st) { return enqueue_colored(bt, color, half_sweeps, st); });
 }
 
 gscl_status gscl_batch_destroy(gscl_batch h) {
@@ -297,10 +416,8 @@ gscl_status gscl_batch_tile(gscl_batch h, int32_t *tile_x, int32_t *tile_y) {
   Batch *bt = find_batch(h);
   if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
   std::lock_guard<std::mutex> lk(bt->mu);
-  const int vx = bt->base.narrow ? 2 : (bt->dtype == GSCL_F64 ? 2 : 4);
-  const int vy = bt->base.narrow ? 4 : 2;
-  if (tile_x) *tile_x = 32 * vx;
-  if (tile_y) *tile_y = bt->base.threads / 32 * vy;
+  if (tile_x) *tile_x = bt->base.tile_x;
+  if (tile_y) *tile_y = bt->base.tile_y;
   return GSCL_OK;
 }
 
@@ -310,38 +427,12 @@ gscl_status gscl_batch_run(gscl_batch h, int32_t sweeps, int32_t use_graph, void
   if (sweeps < 1) return fail(GSCL_ERR_INVALID, "sweeps must be >= 1");
   std::lock_guard<std::mutex> lk(bt->mu);
   if (bt->n_out < 1) return fail(GSCL_ERR_INVALID, "this batch's operator has no output to sweep");
+  if (bt->colored) return fail(GSCL_ERR_INVALID, "a coloured batch sweeps by colour (gscl_batch_run_colored)");
   int first = 0;
   if (gscl_status s = current_table(bt, &first)) return s;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (use_graph) {
-    auto key = std::make_pair(first, (int)sweeps);
-    auto it = bt->graphs.find(key);
-    if (it == bt->graphs.end()) {
-      if (!bt->cap_stream) {
-        cudaError_t e = cudaStreamCreateWithFlags(&bt->cap_stream, cudaStreamNonBlocking);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreateWithFlags");
-      }
-      cudaError_t e = cudaStreamBeginCapture(bt->cap_stream, cudaStreamCaptureModeRelaxed);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
-      gscl_status s = enqueue_sweeps(bt, first, sweeps, bt->cap_stream);
-      cudaGraph_t graph = nullptr;
-      e = cudaStreamEndCapture(bt->cap_stream, &graph);
-      if (s != GSCL_OK) {
-        if (graph) cudaGraphDestroy(graph);
-        return s;
-      }
-      if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-      cudaGraphExec_t exec = nullptr;
-      e = cudaGraphInstantiate(&exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
-      it = bt->graphs.emplace(key, exec).first;
-    }
-    cudaError_t e = cudaGraphLaunch(it->second, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-  } else {
-    if (gscl_status s = enqueue_sweeps(bt, first, sweeps, st)) return s;
-  }
+  if (gscl_status s = run_group(bt, std::make_pair(first, (int)sweeps), use_graph != 0, (cudaStream_t)stream,
+                                [&](cudaStream_t st) { return enqueue_sweeps(bt, first, sweeps, st); }))
+    return s;
   if (sweeps % 2 == 0)  // out[0] names the last sweep's result, as in gscl_do_all
     for (int i = 0; i < bt->n_inst; ++i)
       if (gscl_status s = swap_storage(bt->in_h[(size_t)i * bt->n_in], bt->out_h[(size_t)i * bt->n_out])) return s;
@@ -354,6 +445,7 @@ gscl_status gscl_batch_reduce(gscl_batch h, int32_t reduce_op, double *results, 
   if (!results) return fail(GSCL_ERR_INVALID, "results is NULL");
   std::lock_guard<std::mutex> lk(bt->mu);
   if (!bt->has_value) return fail(GSCL_ERR_INVALID, "the batch's operator returns no value");
+  if (bt->colored) return fail(GSCL_ERR_INVALID, "a coloured batch does not reduce (it updates in place)");
   int red;
   switch (reduce_op) {
     case GSCL_SUM: red = RED_SUM; break;
@@ -379,6 +471,7 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
   if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
   if (trial_sweeps < 1) return fail(GSCL_ERR_INVALID, "trial_sweeps must be >= 1");
   std::lock_guard<std::mutex> lk(bt->mu);
+  if (bt->colored) return fail(GSCL_ERR_INVALID, "coloured batches are not tuned");
   cudaStream_t st = (cudaStream_t)stream;
   const int red = bt->n_out ? RED_NONE : RED_L2;
   const TileCfg keep = bt->cfg;

@@ -200,18 +200,26 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   pl->op = cfg.generic ? OP_GENERIC : match_static(terms, n_in, n_out, &perm);
   // narrow tiles: compiled for batches of compile-time operators, FP32 / BF16
   const bool narrow = cfg.narrow && g0.dtype != GSCL_F64 && batch_capable(pl->op);
-  const int VX = narrow ? 2 : vx_for(g0.dtype);
   // colour-compacted red-black sweeps: a warp spans 64 VX columns
   const bool compact = cfg.compact && g0.dtype == GSCL_F64 && !cfg.generic && compact_capable(pl->op) && !reduce;
-  const int TX = (compact ? 64 : 32) * VX;
   // reach per input grid (coefficient reads are at the core element)
-  int rxa[kMaxIn] = {}, rya[kMaxIn] = {}, rz = 0;
+  int rxa[kMaxIn] = {}, rya[kMaxIn] = {}, rz = 0, rx_max = 0;
   for (auto &t : terms) {
     if (t.in == GSCL_VALUE) continue;
     rxa[t.in] = std::max(rxa[t.in], abs((int)t.dx));
     rya[t.in] = std::max(rya[t.in], abs((int)t.dy));
     rz = std::max(rz, abs((int)t.dz));
+    rx_max = std::max(rx_max, abs((int)t.dx));
   }
+  // vector lanes (StaticOpV): compile-time operators on FP32 / BF16 grids,
+  // G = 16 / element bytes contiguous columns per lane, 128-column tiles
+  // whose rows take 128 / G lanes (RPS row blocks per warp)
+  const int G = 16 / elem;
+  const bool vlanes = !narrow && pl->op != OP_GENERIC && (g0.dtype == GSCL_F32 || g0.dtype == GSCL_BF16) &&
+                      rx_max <= G;
+  const int VX = narrow ? 2 : (vlanes ? G : vx_for(g0.dtype));
+  const int TX = vlanes ? 128 : (compact ? 64 : 32) * VX;
+  const int RPS = vlanes ? 32 * G / 128 : 1;
   const int vec = 16 / elem;  // TMA x coordinates stay multiples of 16 bytes
   int AXa[kMaxIn], BWa[kMaxIn];
   for (int a = 0; a < n_in; ++a) {
@@ -236,11 +244,11 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   if (const char *e = getenv("GSCL_PREFETCH")) PF = nz_range > 1 ? std::max(1, std::min(6, atoi(e))) : 0;
   if (cfg.nw > 0) NW = std::min(8, cfg.nw);
   if (cfg.pf > 0 && nz_range > 1) PF = std::min(6, cfg.pf);
-  int TY = NW * VY;
+  int TY = NW * VY * RPS;
   size_t smem = 0;
   int R = 0, SEa[kMaxIn] = {}, BHa[kMaxIn] = {};
   for (;;) {
-    TY = NW * VY;
+    TY = NW * VY * RPS;
     R = 2 * rz + 1 + PF;
     size_t ring = 0;
     for (int a = 0; a < n_in; ++a) {
@@ -342,6 +350,9 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   pl->smem = smem;
   pl->narrow = narrow;
   pl->compact = compact;
+  pl->vec = vlanes;
+  pl->tile_x = TX;
+  pl->tile_y = TY;
   pl->work = (long long)P.inst.tiles_x * P.inst.tiles_y * nz_range;
   pl->max_ctas = reduce ? kMaxReduceCtas : 0x7fffffff;
   return GSCL_OK;

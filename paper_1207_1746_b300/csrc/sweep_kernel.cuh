@@ -77,6 +77,15 @@ struct Segment {
   int32_t inst, col, zoff, zlen;
 };
 
+// The term weights of one instance of a batch, in the order of the launch's
+// term table (a batch's instances share the operator's structure; coloured
+// batches give each instance its own weights, e.g. its own SOR factor).
+struct InstWeights {
+  double wd[kMaxTerms];
+  float wf[kMaxTerms];
+  float wl[kMaxTerms];  // pair arithmetic: wd - (double)wf
+};
+
 struct SweepParams {
   InstDesc inst;             // single-grid launches
   DevTerm terms[kMaxTerms];
@@ -94,6 +103,7 @@ struct SweepParams {
   int32_t zalt;       // launch a whole multiple of the tile columns (one z range per CTA)
   // batched launches: CTA b runs segments [cta_seg[b], cta_seg[b + 1])
   const InstDesc *insts;
+  const InstWeights *inst_w; // one row of weights per instance
   const Segment *segs;
   const int32_t *cta_seg;
   double *seg_partials;      // batched reduce: one (s, c) pair per segment
@@ -129,6 +139,35 @@ template <> __device__ __forceinline__ f64pair from_arith<f64pair>(Df64 x) { ret
 __device__ __forceinline__ double term_weight(const DevTerm &t, double) { return t.wd; }
 __device__ __forceinline__ float term_weight(const DevTerm &t, float) { return t.wf; }
 __device__ __forceinline__ Df64 term_weight(const DevTerm &t, Df64) { return Df64(t.wf, t.wl); }
+__device__ __forceinline__ double inst_weight(const InstWeights &w, int i, double) { return w.wd[i]; }
+__device__ __forceinline__ float inst_weight(const InstWeights &w, int i, float) { return w.wf[i]; }
+__device__ __forceinline__ Df64 inst_weight(const InstWeights &w, int i, Df64) { return Df64(w.wf[i], w.wl[i]); }
+
+// Where the operator's weights come from.  Single-grid launches read them
+// from the launch parameters.  Batched launches read the row of the
+// instance being swept, once per segment: into registers for compile-time
+// operators (N terms, constant indices), through a pointer for the
+// interpreted term list.
+template <typename A>
+struct ParamWeights {
+  __device__ __forceinline__ void load(const InstWeights *) {}
+  __device__ __forceinline__ A operator()(const SweepParams &P, int i) const { return term_weight(P.terms[i], A(0)); }
+};
+template <typename A, int N>
+struct RegWeights {
+  A v[N];
+  __device__ __forceinline__ void load(const InstWeights *w) {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = inst_weight(*w, i, A(0));
+  }
+  __device__ __forceinline__ A operator()(const SweepParams &, int i) const { return v[i]; }
+};
+template <typename A>
+struct RowWeights {
+  const InstWeights *w = nullptr;
+  __device__ __forceinline__ void load(const InstWeights *row) { w = row; }
+  __device__ __forceinline__ A operator()(const SweepParams &, int i) const { return inst_weight(*w, i, A(0)); }
+};
 
 // ------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -269,27 +308,33 @@ struct GenericOp {
   static constexpr int kMaxOut = kMaxOut_;
   static constexpr int kQueue = 1;  // no z register queue (size of the unused array)
   static constexpr int kXStep = 1;  // a thread's columns: lane + 32 e
+  static constexpr int kGroup = 1;  // columns strided by 32, not grouped (see StaticOpV)
+  static constexpr int kRowsPerSlot = 1;
+  template <typename A, bool BATCH>
+  using Weights = typename std::conditional<BATCH, RowWeights<A>, ParamWeights<A>>::type;
   __device__ static int n_out(const SweepParams &P) { return P.n_out; }
 
   template <typename T, int VX, int VY>
   __device__ static __forceinline__ void advance_queue(const SweepParams &, const T *, int, int, int, bool,
                                                        typename Arith<T>::A (&)[kQueue][VY][VX]) {}
 
-  template <typename T, int VX, int VY, int r>
-  __device__ static __forceinline__ void eval_row(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
-                                                  int lane, const typename Arith<T>::A (&)[kQueue][VY][VX],
+  template <typename T, int VX, int VY, int r, class WS>
+  __device__ static __forceinline__ void eval_row(const SweepParams &P, const WS &ws, const T *ring, int smod,
+                                                  int cslot, int row0, int lane,
+                                                  const typename Arith<T>::A (&)[kQueue][VY][VX],
                                                   typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    eval<T, VX>(P, ring, smod, cslot, row0 + r, lane, v, o);
+    eval<T, VX>(P, ws, ring, smod, cslot, row0 + r, lane, v, o);
   }
 
-  template <typename T, int VX>
-  __device__ static __forceinline__ void term(const SweepParams &P, const DevTerm &tm, const T *ring, int smod,
+  template <typename T, int VX, class WS>
+  __device__ static __forceinline__ void term(const SweepParams &P, const WS &ws, int ti, const T *ring, int smod,
                                               int row, int lane, const typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&acc)[VX]) {
     using A = typename Arith<T>::A;
     const int R = P.R;
-    const A w = term_weight(tm, A(0));
+    const DevTerm &tm = P.terms[ti];
+    const A w = ws(P, ti);
     A x[VX];
     if (tm.in < 0) {
 #pragma unroll
@@ -311,16 +356,16 @@ struct GenericOp {
     for (int e = 0; e < VX; ++e) acc[e] = fma(w, x[e], acc[e]);
   }
 
-  template <typename T, int VX>
-  __device__ static __forceinline__ void eval(const SweepParams &P, const T *ring, int smod, int, int row, int lane,
-                                              typename Arith<T>::A (&v)[VX],
+  template <typename T, int VX, class WS>
+  __device__ static __forceinline__ void eval(const SweepParams &P, const WS &ws, const T *ring, int smod, int,
+                                              int row, int lane, typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    for (int t = 0; t < P.n_value_terms; ++t) term<T, VX>(P, P.terms[t], ring, smod, row, lane, v, v);
+    for (int t = 0; t < P.n_value_terms; ++t) term<T, VX>(P, ws, t, ring, smod, row, lane, v, v);
 #pragma unroll
     for (int m = 0; m < kMaxOut; ++m)
       if (m < P.n_out)
         for (int t = P.out_begin[m]; t < P.out_begin[m + 1]; ++t)
-          term<T, VX>(P, P.terms[t], ring, smod, row, lane, v, o[m]);
+          term<T, VX>(P, ws, t, ring, smod, row, lane, v, o[m]);
   }
 };
 
@@ -336,7 +381,11 @@ struct GenericOp {
 template <class Def, int XS = 1>
 struct StaticOp {
   static constexpr int kXStep = XS;
+  static constexpr int kGroup = 1;
+  static constexpr int kRowsPerSlot = 1;
   static constexpr int kMaxOut = Def::NOUT > 0 ? Def::NOUT : 1;
+  template <typename A, bool BATCH>
+  using Weights = typename std::conditional<BATCH, RegWeights<A, Def::NT>, ParamWeights<A>>::type;
   __device__ static constexpr int n_out(const SweepParams &) { return Def::NOUT; }
 
   // reach of the terms reading input `in` (-1: every input) along `axis`
@@ -452,9 +501,9 @@ struct StaticOp {
   }
 
   // Term I at tile row row0 + r of this thread's VY rows.
-  template <typename T, int VX, int VY, int r, int I>
-  __device__ static __forceinline__ void term(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
-                                              int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+  template <typename T, int VX, int VY, int r, int I, class WS>
+  __device__ static __forceinline__ void term(const SweepParams &P, const WS &ws, const T *ring, int smod, int cslot,
+                                              int row0, int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
                                               typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX],
                                               typename Arith<T>::A (&g)[VX]) {
@@ -465,7 +514,7 @@ struct StaticOp {
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
     const int R = P.R;
-    const A w = term_weight(P.terms[I], A(0));
+    const A w = ws(P, I);
     A x[VX];
     if constexpr (t.in < 0) {
 #pragma unroll
@@ -517,22 +566,250 @@ struct StaticOp {
     }
   }
 
-  template <typename T, int VX, int VY, int r, int... I>
-  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
-                                                  int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+  template <typename T, int VX, int VY, int r, class WS, int... I>
+  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const WS &ws, const T *ring, int smod,
+                                                  int cslot, int row0, int lane,
+                                                  const typename Arith<T>::A (&zq)[kQueue][VY][VX],
                                                   typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX],
                                                   std::integer_sequence<int, I...>) {
     typename Arith<T>::A g[VX];
-    (term<T, VX, VY, r, I>(P, ring, smod, cslot, row0, lane, zq, v, o, g), ...);
+    (term<T, VX, VY, r, I>(P, ws, ring, smod, cslot, row0, lane, zq, v, o, g), ...);
   }
 
-  template <typename T, int VX, int VY, int r>
-  __device__ static __forceinline__ void eval_row(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
-                                                  int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+  template <typename T, int VX, int VY, int r, class WS>
+  __device__ static __forceinline__ void eval_row(const SweepParams &P, const WS &ws, const T *ring, int smod,
+                                                  int cslot, int row0, int lane,
+                                                  const typename Arith<T>::A (&zq)[kQueue][VY][VX],
                                                   typename Arith<T>::A (&v)[VX],
                                                   typename Arith<T>::A (&o)[kMaxOut][VX]) {
-    eval_seq<T, VX, VY, r>(P, ring, smod, cslot, row0, lane, zq, v, o, std::make_integer_sequence<int, Def::NT>{});
+    eval_seq<T, VX, VY, r>(P, ws, ring, smod, cslot, row0, lane, zq, v, o,
+                           std::make_integer_sequence<int, Def::NT>{});
+  }
+};
+
+// ---------------------------------------------------------------- vector lanes
+// Loads G contiguous elements (16 bytes) from shared memory as arithmetic
+// values; p is 16-byte aligned.  BF16 widens to FP32 by placing its bits in
+// the upper half of the word (exact).
+template <int G>
+__device__ __forceinline__ void load_group(const float *p, float (&x)[G]) {
+  static_assert(G % 4 == 0, "FP32 groups are whole float4s");
+#pragma unroll
+  for (int q = 0; q < G / 4; ++q) {
+    const float4 v = reinterpret_cast<const float4 *>(p)[q];
+    x[4 * q] = v.x;
+    x[4 * q + 1] = v.y;
+    x[4 * q + 2] = v.z;
+    x[4 * q + 3] = v.w;
+  }
+}
+template <int G>
+__device__ __forceinline__ void load_group(const __nv_bfloat16 *p, float (&x)[G]) {
+  static_assert(G % 8 == 0, "BF16 groups are whole 16-byte words");
+#pragma unroll
+  for (int q = 0; q < G / 8; ++q) {
+    const uint4 v = reinterpret_cast<const uint4 *>(p)[q];
+    const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      x[8 * q + 2 * k] = __uint_as_float(w[k] << 16);
+      x[8 * q + 2 * k + 1] = __uint_as_float(w[k] & 0xffff0000u);
+    }
+  }
+}
+
+// Stores G contiguous results (16 bytes per float4 / 8 BF16) to global
+// memory; p is 16-byte aligned.  BF16 rounds each pair with one conversion.
+template <int G>
+__device__ __forceinline__ void store_group(float *p, const float (&x)[G]) {
+#pragma unroll
+  for (int q = 0; q < G / 4; ++q)
+    reinterpret_cast<float4 *>(p)[q] = make_float4(x[4 * q], x[4 * q + 1], x[4 * q + 2], x[4 * q + 3]);
+}
+template <int G>
+__device__ __forceinline__ void store_group(__nv_bfloat16 *p, const float (&x)[G]) {
+#pragma unroll
+  for (int q = 0; q < G / 8; ++q) {
+    uint32_t w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(x[8 * q + 2 * k], x[8 * q + 2 * k + 1]);
+      w[k] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    reinterpret_cast<uint4 *>(p)[q] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// acc[e] = fma(w, x[e], acc[e]) for every element of a group; FP32 pairs go
+// through the packed two-lane FMA (each lane one fma.rn, so the bits are
+// those of the scalar FMAs).
+template <int G>
+__device__ __forceinline__ void fma_group(float w, const float (&x)[G], float (&acc)[G]) {
+#pragma unroll
+  for (int e = 0; e + 1 < G; e += 2) {
+    const float2 r = __ffma2_rn(make_float2(w, w), make_float2(x[e], x[e + 1]), make_float2(acc[e], acc[e + 1]));
+    acc[e] = r.x;
+    acc[e + 1] = r.y;
+  }
+  if constexpr (G % 2) acc[G - 1] = fmaf(w, x[G - 1], acc[G - 1]);
+}
+// acc[e] = fma(c[e], g[e], acc[e]): a coefficient run's product per element
+template <int G>
+__device__ __forceinline__ void fma_group(const float (&c)[G], const float (&g)[G], float (&acc)[G]) {
+#pragma unroll
+  for (int e = 0; e + 1 < G; e += 2) {
+    const float2 r =
+        __ffma2_rn(make_float2(c[e], c[e + 1]), make_float2(g[e], g[e + 1]), make_float2(acc[e], acc[e + 1]));
+    acc[e] = r.x;
+    acc[e + 1] = r.y;
+  }
+  if constexpr (G % 2) acc[G - 1] = fmaf(c[G - 1], g[G - 1], acc[G - 1]);
+}
+
+// Compile-time term table with vector lanes (FP32 / BF16 storage): a lane
+// owns G = 16 / sizeof(T) contiguous columns of a tile row, so every read of
+// a term's row is one 16-byte shared-memory load, the x neighbours come from
+// the same registers (plus one scalar load at the group's edge), the FMAs
+// run in FP32 pairs and the results leave as 16-byte stores.  A tile row of
+// 128 columns takes 128 / G lanes: 32 for FP32, a half-warp for BF16 (the
+// warp's two halves own the two halves of its rows, RPS = 2 row blocks per
+// warp).  Each element is evaluated with the same operations in the same
+// order as StaticOp<Def, 1>, so the two policies give bit-identical results.
+template <class Def, int G>
+struct StaticOpV {
+  using Base = StaticOp<Def, 1>;
+  static constexpr int kXStep = 1;
+  static constexpr int kGroup = G;
+  static constexpr int kLanesPerRow = 128 / G;
+  static constexpr int kRowsPerSlot = 32 / kLanesPerRow;
+  static constexpr int kMaxOut = Base::kMaxOut;
+  template <typename A, bool BATCH>
+  using Weights = typename Base::template Weights<A, BATCH>;
+  __device__ static constexpr int n_out(const SweepParams &P) { return Def::NOUT; }
+  static constexpr int RZ = Base::RZ;
+  static constexpr int ZQ = Base::ZQ;
+  static constexpr int kQueue = Base::kQueue;
+
+  __host__ __device__ static constexpr bool fits() {
+    for (int i = 0; i < Def::NT; ++i) {
+      const int dx = Def::table.t[i].dx;
+      if (dx > G || -dx > G) return false;
+    }
+    return true;
+  }
+
+  // element (row, 0) of ring input IN's box in `slot` (its tile row `row`, first core column)
+  template <int IN, typename T>
+  __device__ static __forceinline__ const T *row_ptr(const SweepParams &P, const T *ring, int slot, int row) {
+    constexpr int vec = 16 / (int)sizeof(T);
+    constexpr int AX = (Base::radius(0, IN) + vec - 1) / vec * vec;
+    constexpr int RY = Base::radius(1, IN);
+    constexpr int BW = 128 + 2 * AX;
+    return ring + P.in_base[IN] + slot * P.in_se[IN] + (row + RY) * BW + AX;
+  }
+
+  // Step start: queue rows of planes z - RZ .. z + RZ (col: this lane's first column).
+  template <typename T, int VX, int VY>
+  __device__ static __forceinline__ void advance_queue(const SweepParams &P, const T *ring, int smod, int row0,
+                                                       int col, bool first, float (&zq)[kQueue][VY][VX]) {
+    if constexpr (ZQ >= 0) {
+      const int R = P.R;
+      if (first) {
+#pragma unroll
+        for (int k = 0; k <= 2 * RZ; ++k) {
+          int sl = smod + k - RZ;
+          sl = sl >= R ? sl - R : (sl < 0 ? sl + R : sl);
+#pragma unroll
+          for (int r = 0; r < VY; ++r) load_group<G>(row_ptr<ZQ>(P, ring, sl, row0 + r) + col, zq[k][r]);
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 2 * RZ; ++k)
+#pragma unroll
+          for (int r = 0; r < VY; ++r)
+#pragma unroll
+            for (int e = 0; e < VX; ++e) zq[k][r][e] = zq[k + 1][r][e];
+        int sl = smod + RZ;
+        sl = sl >= R ? sl - R : sl;
+#pragma unroll
+        for (int r = 0; r < VY; ++r) load_group<G>(row_ptr<ZQ>(P, ring, sl, row0 + r) + col, zq[2 * RZ][r]);
+      }
+    }
+  }
+
+  // Term I at tile row row0 + r; col = this lane's first column in the tile.
+  template <typename T, int VX, int VY, int r, int I, class WS>
+  __device__ static __forceinline__ void term(const SweepParams &P, const WS &ws, const T *ring, int smod, int cslot,
+                                              int row0, int col, const float (&zq)[kQueue][VY][VX], float (&v)[VX],
+                                              float (&o)[kMaxOut][VX], float (&g)[VX]) {
+    static_assert(VX == G, "one group per lane and row");
+    const int row = row0 + r;
+    constexpr OpTerm t = Def::table.t[I];
+    const int R = P.R;
+    const float w = ws(P, I);
+    float x[G];
+    if constexpr (t.in < 0) {
+#pragma unroll
+      for (int e = 0; e < G; ++e) x[e] = v[e];
+    } else if constexpr (Base::template in_centre_ring<T>(t.in)) {
+      load_group<G>(ring + P.in_base[t.in] + cslot * P.in_se[t.in] + row * 128 + col, x);
+    } else {
+      int slot = smod + t.dz;
+      if constexpr (t.dz > 0) slot = slot >= R ? slot - R : slot;
+      if constexpr (t.dz < 0) slot = slot < 0 ? slot + R : slot;
+      const T *rp = row_ptr<t.in>(P, ring, slot, row + t.dy) + col;
+      float c[G];
+      if constexpr (t.in == ZQ && r + t.dy >= 0 && r + t.dy < VY && t.dz >= -RZ && t.dz <= RZ) {
+#pragma unroll
+        for (int e = 0; e < G; ++e) c[e] = zq[t.dz + RZ][r + t.dy][e];
+      } else {
+        load_group<G>(rp, c);
+      }
+#pragma unroll
+      for (int e = 0; e < G; ++e) {
+        const int k = e + t.dx;  // compile-time after unrolling
+        x[e] = (k >= 0 && k < G) ? c[k < 0 ? 0 : (k >= G ? G - 1 : k)] : to_arith(rp[k]);
+      }
+    }
+    if constexpr (t.coef >= 0) {
+      if constexpr (Base::run_first(I)) {
+#pragma unroll
+        for (int e = 0; e < G; ++e) g[e] = w * x[e];
+      } else {
+        fma_group<G>(w, x, g);
+      }
+      if constexpr (Base::run_last(I)) {
+        float cf[G];
+        if constexpr (Base::template in_centre_ring<T>(t.coef)) {
+          load_group<G>(ring + P.in_base[t.coef] + cslot * P.in_se[t.coef] + row * 128 + col, cf);
+        } else {
+          load_group<G>(row_ptr<t.coef>(P, ring, smod, row) + col, cf);
+        }
+        if constexpr (t.out < 0) fma_group<G>(cf, g, v);
+        else fma_group<G>(cf, g, o[t.out]);
+      }
+    } else if constexpr (t.out < 0) {
+      fma_group<G>(w, x, v);
+    } else {
+      fma_group<G>(w, x, o[t.out]);
+    }
+  }
+
+  template <typename T, int VX, int VY, int r, class WS, int... I>
+  __device__ static __forceinline__ void eval_seq(const SweepParams &P, const WS &ws, const T *ring, int smod,
+                                                  int cslot, int row0, int col, const float (&zq)[kQueue][VY][VX],
+                                                  float (&v)[VX], float (&o)[kMaxOut][VX],
+                                                  std::integer_sequence<int, I...>) {
+    float g[VX];
+    (term<T, VX, VY, r, I>(P, ws, ring, smod, cslot, row0, col, zq, v, o, g), ...);
+  }
+
+  template <typename T, int VX, int VY, int r, class WS>
+  __device__ static __forceinline__ void eval_row(const SweepParams &P, const WS &ws, const T *ring, int smod,
+                                                  int cslot, int row0, int col, const float (&zq)[kQueue][VY][VX],
+                                                  float (&v)[VX], float (&o)[kMaxOut][VX]) {
+    eval_seq<T, VX, VY, r>(P, ws, ring, smod, cslot, row0, col, zq, v, o, std::make_integer_sequence<int, Def::NT>{});
   }
 };
 
@@ -624,7 +901,9 @@ template <typename T, int VX, int VY, int RED, class Op, bool BATCH>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
   constexpr int XS = Op::kXStep;
-  constexpr int TX = 32 * XS * VX;
+  constexpr int G = Op::kGroup;           // > 1: vector lanes (StaticOpV), G contiguous columns each
+  constexpr int RPS = Op::kRowsPerSlot;   // row blocks per warp (2 when a tile row takes a half-warp)
+  constexpr int TX = G > 1 ? 128 : 32 * XS * VX;
   constexpr int NO = Op::kMaxOut;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
@@ -635,8 +914,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 
   const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
   const int NW = blockDim.x >> 5;
-  const int TY = NW * VY;
+  const int TY = NW * VY * RPS;
   const int R = P.R, rz = P.rz;
+  // vector lanes: lane = rb * (128 / G) + cg owns columns G cg .. G cg + G - 1
+  // of the rows of row block rb; the thread's first tile row
+  const int cg = G > 1 ? lane % (128 / (G > 1 ? G : 1)) : 0;
+  const int rb = G > 1 ? lane / (128 / (G > 1 ? G : 1)) : 0;
+  const int wrow0 = (wy * RPS + rb) * VY;
 
   uint64_t *cbars = bars + kMaxRing;  // the centre ring's two slots
   const bool has_c = P.cmask != 0;
@@ -654,6 +938,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   // (its outputs are this sweep's inputs).
   pdl_wait();
 
+  typename Op::template Weights<A, BATCH> ws;  // the operator's weights (per instance in batches)
   Compensated acc;
   double sq = 0.0;          // L2: plain FP64 chain of squares within one segment
   // L2 of FP32 arithmetic (FP32 / BF16 storage): squares summed on the FP32 pipe
@@ -700,6 +985,7 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
       if (kseg >= kend) break;
       const Segment sg = P.segs[kseg];
       I = &P.insts[sg.inst];
+      ws.load(P.inst_w + sg.inst);
       col = sg.col;
       zoff = sg.zoff;
       zlen = sg.zlen;
@@ -771,13 +1057,13 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     bool yok[VY];
 #pragma unroll
     for (int r = 0; r < VY; ++r) {
-      y[r] = y0 + wy * VY + r;
+      y[r] = y0 + wrow0 + r;
       yok[r] = (y[r] >= I->lo[1]) && (y[r] < I->hi[1]);
     }
     bool xok[VX];
 #pragma unroll
     for (int e = 0; e < VX; ++e) {
-      const int64_t x = x0 + lane + 32 * e;
+      const int64_t x = G > 1 ? x0 + G * cg + e : x0 + lane + 32 * e;
       xok[e] = (x >= I->lo[0]) && (x < I->hi[0]);
     }
     int smod = wslot;  // slot of the centre plane of step 0
@@ -806,8 +1092,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
         // colour-compacted sweeps: the warp's first row starts at column
         // 2 lane + p, p making (x + y + z) even for colour 0 (x0 and the
         // warp's first row y0 + wy VY differ from y0 by even amounts)
-        const int carg = XS == 1 ? lane : 2 * lane + (int)((P.color + y0 + z) & 1);
-        Op::template advance_queue<T, VX, VY>(P, ring, smod, wy * VY, lane, s == 0, zq);
+        const int carg = G > 1 ? G * cg : (XS == 1 ? lane : 2 * lane + (int)((P.color + y0 + z) & 1));
+        Op::template advance_queue<T, VX, VY>(P, ring, smod, wrow0, carg, s == 0, zq);
         static_for<VY>([&](auto rc) {
           constexpr int r = decltype(rc)::value;
           A v[VX];
@@ -818,8 +1104,29 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
 #pragma unroll
             for (int m = 0; m < NO; ++m) o[m][e] = A(0);
           }
-          Op::template eval_row<T, VX, VY, r>(P, ring, smod, cslot, wy * VY, carg, zq, v, o);
-          if constexpr (XS == 1) {
+          Op::template eval_row<T, VX, VY, r>(P, ws, ring, smod, cslot, wrow0, carg, zq, v, o);
+          if constexpr (G > 1) {
+            // vector lanes: one 16-byte store per output when the group is
+            // whole and uncoloured; element by element at ragged edges and
+            // in red-black sweeps (the group's columns alternate colours)
+            if (yok[r]) {
+#pragma unroll
+              for (int m = 0; m < NO; ++m) {
+                if (m < Op::n_out(P)) {
+                  T *dst = reinterpret_cast<T *>(I->out[m].base) + z * I->out[m].plane + y[r] * I->out[m].pitch +
+                           x0 + G * cg;
+                  if (P.color < 0 && xok[0] && xok[G - 1]) {
+                    store_group<G>(dst, o[m]);
+                  } else {
+#pragma unroll
+                    for (int e = 0; e < VX; ++e)
+                      if (xok[e] && (P.color < 0 || (int)((x0 + G * cg + e + y[r] + z) & 1) == P.color))
+                        dst[e] = from_arith<T>(o[m][e]);
+                  }
+                }
+              }
+            }
+          } else if constexpr (XS == 1) {
             // red-black colouring: a thread's columns x0 + lane + 32 e share one parity
             if (yok[r] && (P.color < 0 || (int)((x0 + lane + y[r] + z) & 1) == P.color)) {
 #pragma unroll
@@ -950,11 +1257,11 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   __threadfence();
   // last CTA: thread i folds a fixed contiguous chunk of partials, then the
   // fixed tree of block_fold combines the threads in order.
-  const int G = gridDim.x;
-  const int chunk = (G + blockDim.x - 1) / blockDim.x;
+  const int nctas = gridDim.x;
+  const int chunk = (nctas + blockDim.x - 1) / blockDim.x;
   s = 0.0;
   c = 0.0;
-  for (int b = tid * chunk; b < min(G, (tid + 1) * chunk); ++b) {
+  for (int b = tid * chunk; b < min(nctas, (tid + 1) * chunk); ++b) {
     const double ps = __ldcg(&partials[2 * b]);
     const double pc = __ldcg(&partials[2 * b + 1]);
     if (RED == RED_MAXABS) s = max_abs_bits(s, ps);
@@ -1000,6 +1307,8 @@ struct Plan {
   bool narrow = false;        // batches of FP32 / BF16 grids: 64-column tiles, 4 rows per warp
   bool pair = false;          // FP64 grids in pair arithmetic (fixed when the plan is made)
   bool compact = false;       // colour-compacted red-black sweep (XS = 2 tiles)
+  bool vec = false;           // vector lanes (StaticOpV): FP32 / BF16 compile-time operators
+  int tile_x = 0, tile_y = 0; // core elements per CTA tile
 };
 
 // Columns (TX = 32 VX) and rows (VY) per thread for each storage dtype: two
@@ -1126,17 +1435,25 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
   } else if constexpr (BATCH && !BatchCapable<Def>::value) {
     return fail(GSCL_ERR_INVALID, "no batched kernel for this operator structure");
   } else {
-    // narrow tiles (64 x 4 rows per warp, the same 8 points per thread) for
-    // batches of FP32 / BF16 grids whose widths leave 128-column tiles idle
-    if constexpr (BATCH && !IsFp64Storage<T>::value) {
-      if (pl.narrow) return launch_t<T, 2, RED, StaticOp<Def>, BATCH, 4>(pl, stream, occ);
+    if constexpr (!IsFp64Storage<T>::value) {
+      // narrow tiles (64 x 4 rows per warp, the same 8 points per thread) for
+      // batches of FP32 / BF16 grids whose widths leave 128-column tiles idle
+      if constexpr (BATCH) {
+        if (pl.narrow) return launch_t<T, 2, RED, StaticOp<Def>, BATCH, 4>(pl, stream, occ);
+      }
+      // vector lanes: 16 bytes of a row per lane (every compile-time table fits)
+      constexpr int G = 16 / (int)sizeof(T);
+      static_assert(StaticOpV<Def, G>::fits(), "x reach beyond one group");
+      if (!pl.vec) return fail(GSCL_ERR_INVALID, "FP32 / BF16 plan without vector lanes");
+      return launch_t<T, G, RED, StaticOpV<Def, G>, BATCH>(pl, stream, occ);
+    } else {
+      // colour-compacted red-black sweeps of the star family on FP64 grids
+      // (IEEE or pair arithmetic), single grids and coloured batches
+      if constexpr (RED == RED_NONE && CompactCapable<Def>::value) {
+        if (pl.compact) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
+      }
+      return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
     }
-    // colour-compacted red-black sweeps of the star family on FP64 grids
-    // (IEEE or pair arithmetic)
-    if constexpr (!BATCH && RED == RED_NONE && IsFp64Storage<T>::value && CompactCapable<Def>::value) {
-      if (pl.compact) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
-    }
-    return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
   }
 }
 

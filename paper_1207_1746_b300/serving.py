@@ -3,14 +3,15 @@ Dirichlet halo) by Jacobi iteration, stopped per request at
 ||f - A u||_2 / ||f||_2 <= tol with A u = 6u - sum6(u).
 
 Requests arrive over time; each tick the scheduler admits waiting requests
-while the HBM budget and the slot limit allow, advances every active
-request by `check_every` sweeps in one batched launch per sweep (a CUDA
-graph replays the group), measures each request's residual with one batched
-FP64-accumulated reduction, and retires the converged ones, recording their
-latency.  All arithmetic runs in the library's kernels; this module only
-schedules.
+(first come, first served) while the HBM budget and the slot limit allow,
+advances every active request by `check_every` sweeps in one batched launch
+per sweep (a CUDA graph replays the group), measures each request's residual
+with one batched FP64-accumulated reduction, and retires the converged ones,
+recording their latency.  A request whose grids alone exceed the budget is
+rejected at admission.  All arithmetic runs in the library's kernels; this
+module only schedules.
 
-Two solve modes:
+Solve modes:
   "fp64"  - plain FP64 Jacobi: u' = (sum6(u) + f) / 6, the residual fused
             into the sweep that reads u every `check_every` sweeps.
   "mixed" - mixed-precision iterative refinement: u is kept in FP64; each
@@ -20,9 +21,10 @@ Two solve modes:
   "rbsor" - red-black SOR in FP64 (the colouring of Section 3's stateful
             stencils), in place on u, with the factor that is optimal for the
             n^3 Dirichlet problem, 2 / (1 + sin(pi / (n + 1))): O(n) iterations
-            where Jacobi takes O(n^2).  Each active request runs its own
-            launches (colouring is not batched); the residual is measured
-            every `sor_check_every` iterations.
+            where Jacobi takes O(n^2).  Every half-sweep of all active
+            requests is one launch of a coloured batch, each request with its
+            own factor; the residual is measured every `sor_check_every`
+            iterations.
   "mixed_rbsor" - the refinement of "mixed" with red-black SOR in FP32 as
             the inner solver: r = f - A u in FP64, FP32 SOR on A d = r until
             ||r - A d|| <= inner_tol ||r||, u += d in FP64.
@@ -63,6 +65,9 @@ class Request:
     outer: int = 0
     rel_residual: float = math.nan
     u: np.ndarray | None = None  # final FP64 solution (when kept)
+    admit_tick: int = -1         # scheduler tick that admitted the request
+    done_tick: int = -1          # tick that retired it
+    rejected: bool = False       # needs more HBM than the whole budget
 
 
 @dataclass
@@ -108,7 +113,9 @@ class PoissonServer:
         self.waiting: list[Request] = []
         self.active: list[_Slot] = []
         self.done: list[Request] = []
+        self.rejected: list[Request] = []
         self.in_use = 0
+        self.ticks = 0
         self.t0 = time.perf_counter()
         self._batches = {}
         self.fused64 = B.Stencil(S.heat7_fused(1.0 / 6.0))   # u' = u + r/6 with r returned
@@ -128,9 +135,15 @@ class PoissonServer:
         while self.waiting and len(self.active) < self.max_active:
             req = self.waiting[0]
             need = request_bytes(req.n, self.mode)
-            if self.in_use + need > self.budget and self.active:
+            if need > self.budget:  # could never run: reject instead of blocking the queue
+                self.waiting.pop(0)
+                req.rejected = True
+                self.rejected.append(req)
+                continue
+            if self.in_use + need > self.budget:
                 break
             self.waiting.pop(0)
+            req.admit_tick = self.ticks
             self.active.append(self._start(req, need))
             self.in_use += need
 
@@ -175,6 +188,7 @@ class PoissonServer:
         if self.keep:
             req.u = slot.grids["u"].download().numpy()
         req.t_done = self.now()
+        req.done_tick = self.ticks
         slot.done = True
 
     # ------------------------------------------------------------ one tick
@@ -185,6 +199,20 @@ class PoissonServer:
             if len(self._batches) > 64:
                 self._batches.clear()
             b = B.Batch(op, instances)
+            self._batches[(key, handles)] = b
+        return b
+
+    def _colored_batch(self, key, x, rhs):
+        """Coloured batch of the active requests' SOR sweeps on grids x (in place)
+        with right-hand sides rhs, each request with its own factor."""
+        ops = [self.sor_operator(s.req.n) for s in self.active]
+        insts = [([s.grids[x], s.grids[rhs]], [s.grids[x]]) for s in self.active]
+        handles = tuple(g.handle for ins, outs in insts for g in ins + outs)
+        b = self._batches.get((key, handles))
+        if b is None:
+            if len(self._batches) > 64:
+                self._batches.clear()
+            b = B.ColoredBatch(ops, insts)
             self._batches[(key, handles)] = b
         return b
 
@@ -199,14 +227,16 @@ class PoissonServer:
         self._admit()
         if not self.active:
             return False
+        self.ticks += 1
         k = self.check_every
         res = torch.zeros(len(self.active), dtype=torch.float64, device="cuda")
         if self.mode == "rbsor":
             k = self.sor_check_every
-            for i, s in enumerate(self.active):
-                g = s.grids
-                B.do_colored(self.sor_operator(s.req.n), [g["u"], g["f"]], [g["u"]], color=0, half_sweeps=2 * k)
-                B.do_reduce(B.L2, self.resid, [g["u"], g["f"]], result=res[i:i + 1])
+            # 2k half-sweeps of every active request, one launch each, then
+            # every request's residual in one batched reduction
+            self._colored_batch("sor64", "u", "f").run_colored(0, 2 * k, graph=self.use_graph)
+            rinsts = [([s.grids["u"], s.grids["f"]], []) for s in self.active]
+            self._batch("resid64", self.resid, rinsts).reduce(B.L2, res)
             r = res.cpu().numpy()
             for s, rv in zip(self.active, r):
                 s.req.sweeps += k
@@ -215,10 +245,9 @@ class PoissonServer:
                     self._finish(s, rel)
         elif self.mode == "mixed_rbsor":
             k = self.sor_check_every
-            for i, s in enumerate(self.active):
-                g = s.grids
-                B.do_colored(self.sor_operator(s.req.n), [g["da"], g["r32"]], [g["da"]], color=0, half_sweeps=2 * k)
-                B.do_reduce(B.L2, self.resid, [g["da"], g["r32"]], result=res[i:i + 1])
+            self._colored_batch("sor32", "da", "r32").run_colored(0, 2 * k, graph=self.use_graph)
+            rinsts = [([s.grids["da"], s.grids["r32"]], []) for s in self.active]
+            self._batch("resid32", self.resid, rinsts).reduce(B.L2, res)
             r = res.cpu().numpy()
             for s, rv in zip(self.active, r):
                 s.req.sweeps += k
@@ -298,7 +327,8 @@ class PoissonServer:
             return lat[min(len(lat) - 1, int(math.ceil(p / 100.0 * len(lat))) - 1)]
 
         return {"mode": self.mode, "offered": offered, "completed": len(self.done),
-                "backlog": offered - len(self.done), "active_at_end": len(self.active),
+                "rejected": len(self.rejected),
+                "backlog": offered - len(self.done) - len(self.rejected), "active_at_end": len(self.active),
                 "elapsed_s": elapsed, "solves_per_s": len(self.done) / elapsed if elapsed > 0 else 0.0,
                 "p50_s": pct(50), "p99_s": pct(99),
                 "max_rel_residual": max((r.rel_residual for r in self.done), default=None),

@@ -131,3 +131,75 @@ def test_colored_alias_and_argument_errors():
     # odd offsets (1, 1, 1) and (-1, 0, 0) read the other colour: allowed in place
     B.do_colored([(1, 1, 1, 0, B.NONE, 0, 0.5), (-1, 0, 0, 0, B.NONE, 0, 0.5)], [gu], [gu])
     B.sync()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+@pytest.mark.parametrize("graph", [False, True])
+def test_colored_batch_equals_each_instance_alone(kernel_path, dtype, graph):
+    """A coloured batch of uneven instances, each with its own SOR factor:
+    five half-sweeps of all of them (one launch per half-sweep) give, bit for
+    bit, what gscl_do_colored gives on each instance alone, and stay within
+    tolerance of the oracle."""
+    h = (1, 1, 1)
+    sides = [(70, 21, 19), (33, 64, 12), (130, 9, 25), (5, 3, 2), (256, 17, 6)]
+    omegas = [1.05, 1.3, 1.7, 1.9, 1.55]
+    u0s = [I.random_interior(80 + k, n, h, -1.0, 1.0, halo_value=0.25) for k, n in enumerate(sides)]
+    f0s = [I.random_interior(90 + k, n, h, -1.0, 1.0) for k, n in enumerate(sides)]
+    alone = []
+    for n, w, u0, f0 in zip(sides, omegas, u0s, f0s):
+        gu, gf = B.Grid(n, h, dtype).upload(u0), B.Grid(n, h, dtype).upload(f0)
+        B.do_colored(S.poisson_sor(w), [gu, gf], [gu], color=1, half_sweeps=5)
+        alone.append(gu.download())
+    grids = [(B.Grid(n, h, dtype).upload(u0), B.Grid(n, h, dtype).upload(f0))
+             for n, u0, f0 in zip(sides, u0s, f0s)]
+    batch = B.ColoredBatch([S.poisson_sor(w) for w in omegas], [([gu, gf], [gu]) for gu, gf in grids])
+    batch.run_colored(1, 5, graph=graph)
+    for k, ((gu, _), want) in enumerate(zip(grids, alone)):
+        assert torch.equal(gu.download(), want), k
+    # the oracle, on the instance with the largest factor
+    k = 3
+    ou, of = O.Grid(as_storage(u0s[k], dtype), h), O.Grid(as_storage(f0s[k], dtype), h)
+    for s in range(5):
+        O.do_colored((1 + s) % 2, S.poisson_sor(omegas[k]), [ou, of], [ou])
+    got = grids[k][0].download().double().numpy()
+    assert np.max(np.abs(got - ou.a)) <= TOL[dtype] * 4 * max(1.0, np.max(np.abs(ou.a)))
+    # a second group continues from where the first left the grids
+    batch.run_colored(0, 2, graph=graph)
+    gu, gf = B.Grid(sides[0], h, dtype).upload(u0s[0]), B.Grid(sides[0], h, dtype).upload(f0s[0])
+    B.do_colored(S.poisson_sor(omegas[0]), [gu, gf], [gu], color=1, half_sweeps=5)
+    B.do_colored(S.poisson_sor(omegas[0]), [gu, gf], [gu], color=0, half_sweeps=2)
+    assert torch.equal(grids[0][0].download(), gu.download())
+
+
+def test_colored_batch_2d_instances():
+    """2D instances of the 5-point Jacobi operator, in place by colour."""
+    h = (1, 1, 0)
+    sides = [(150, 77, 1), (64, 300, 1), (9, 5, 1)]
+    u0s = [I.random_interior(100 + k, n, h, -1.0, 1.0, halo_value=1.0) for k, n in enumerate(sides)]
+    grids = [B.Grid(n, h, "f64", 2).upload(u0) for n, u0 in zip(sides, u0s)]
+    B.ColoredBatch([S.jacobi5_2d()] * 3, [([g], [g]) for g in grids]).run_colored(0, 4)
+    for g, n, u0 in zip(grids, sides, u0s):
+        ou = O.Grid(u0.copy(), h)
+        for s in range(4):
+            O.do_colored(s % 2, S.jacobi5_2d(), [ou], [ou])
+        assert np.max(np.abs(g.download().numpy() - ou.a)) <= 1e-14
+
+
+def test_colored_batch_argument_errors():
+    n, h = (32, 8, 8), (1, 1, 1)
+    gu, gf = B.Grid(n, h).zero(), B.Grid(n, h).zero()
+    gv, gw = B.Grid(n, h).zero(), B.Grid(n, h).zero()
+    with pytest.raises(B.GsclError) as e:          # the second operator has another structure
+        B.ColoredBatch([S.poisson_sor(1.5), S.poisson_jacobi()[:-1]], [([gu, gf], [gu]), ([gv, gw], [gv])])
+    assert e.value.status == 1
+    with pytest.raises(B.GsclError) as e:          # same-colour read of the output in place
+        B.ColoredBatch([[(1, 1, 0, 0, B.NONE, 0, 1.0)]], [([gu], [gu])])
+    assert e.value.status == 3
+    b = B.ColoredBatch([S.poisson_sor(1.5), S.poisson_sor(1.2)], [([gu, gf], [gu]), ([gv, gw], [gv])])
+    with pytest.raises(B.GsclError):
+        b.run(1)                                   # a coloured batch runs by colour only
+    with pytest.raises(B.GsclError):
+        b.run_colored(2, 1)
+    with pytest.raises(B.GsclError):
+        b.run_colored(0, 0)
+    B.sync()
