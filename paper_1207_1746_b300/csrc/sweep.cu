@@ -236,7 +236,9 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const uint32_t cmask = (compact || (g0.dtype == GSCL_F64 && !pl->pair)) ? 0u : static_centre_mask(pl->op);
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
-  const int VY = narrow ? 4 : vy_for(g0.dtype);
+  // rows per thread: vector lanes of BF16 (16 columns of a half-warp row) take
+  // one, which keeps the z register queue at 24 registers
+  const int VY = narrow ? 4 : (vlanes && elem == 2 ? 1 : vy_for(g0.dtype));
   // defaults from tile sweeps on the 256^3 heat workload (B300): FP64 4 warps,
   // FP32 / BF16 8 warps, one plane prefetched beyond the stencil's reach
   int NW = g0.dtype == GSCL_F64 ? 4 : 8, PF = nz_range > 1 ? 1 : 0;
@@ -339,10 +341,10 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   P.ctx_bytes = ctx;
   // Column-aligned launches (one z range of one tile column per CTA) let L2
   // serve the halo rows that neighbouring tiles share; they pay off where the
-  // sweep is bound by HBM (FP32 / BF16 sweeps).  FP64 sweeps and fused
-  // reductions (FP64 accumulation) are bound by the FP64 pipe and keep the
-  // even split over every resident CTA slot.
-  P.zalt = (g0.dtype == GSCL_F64 || reduce) ? 0 : 1;
+  // sweep is bound by HBM (FP32 / BF16 sweeps and reductions, whose squares
+  // are summed on the FP32 pipe).  FP64 sweeps and reductions are bound by
+  // the FP64 pipe and keep the even split over every resident CTA slot.
+  P.zalt = g0.dtype == GSCL_F64 ? 0 : 1;
   if (const char *e = getenv("GSCL_ZALT")) P.zalt = atoi(e) != 0;
   P.err = device_error_word();
   if (!P.err) return fail(GSCL_ERR_CUDA, "device error word unavailable");

@@ -257,40 +257,65 @@ __device__ __forceinline__ void combine_pair(double &s, double &c, double s2, do
   c = (c + c2) - err;
 }
 
-// Sum of squares of FP32 values on the FP32 pipe, held as the unevaluated
-// pair hi + lo (the L2 reduction of FP32 / BF16 sweeps).  Each square is
-// formed exactly as p + pe (the product and its rounding error from one
-// FMA; exact while |x| lies in [2^-50, 2^50], which the caller checks) and
-// added with Knuth's error-free TwoSum, the error going to lo.  The
-// intrinsics keep the compiler from contracting the adds into FMAs, which
-// would break the error-free steps.  renormalize() keeps |lo| within an ulp
-// of hi; the caller widens the pair into the FP64 compensated sum once per
-// z range, so the FP64 pipe sees two adds per range instead of one FMA per
-// element.  Relative error of one range's sum: about (3 + elements) 2^-48.
+// Packed two-lane FP32 subtraction (sub.rn.f32x2, sm_100 family): each lane
+// one sub.rn, like the __fadd2_rn / __fmul2_rn / __ffma2_rn intrinsics.
+__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
+  return *reinterpret_cast<const float2 *>(&d);
+}
+
+// Knuth's TwoSum on both lanes: t + err == a + b exactly, lane by lane.
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &t, float2 &err) {
+  t = __fadd2_rn(a, b);
+  const float2 bp = fsub2_rn(t, a);
+  err = __fadd2_rn(fsub2_rn(a, fsub2_rn(t, bp)), fsub2_rn(b, bp));
+}
+
+// Sum of squares of FP32 values on the FP32 pipe (the L2 reduction of FP32 /
+// BF16 sweeps), as two unevaluated pairs hi + lo, one per lane of the packed
+// two-lane instructions (even and odd elements of a group).  Each square is
+// formed exactly as p + pe (the product, and its rounding error from one
+// FMA: exact while |x| lies in [2^-50, 2^50], which the caller checks) and
+// added with Knuth's error-free TwoSum, the errors going to lo.  renormalize()
+// keeps |lo| within an ulp of hi; the pairs are folded lane to lane, across
+// the warp and into FP64 only at the end of a reduction, so the narrow FP64
+// pipe sees a few operations per warp instead of one FMA per element.  The
+// packed intrinsics and the explicit subtraction keep the compiler from
+// contracting the steps into FMAs, which would break their exactness.
+// Relative error of a sum of n squares: about (3 + n) 2^-48.
 struct SquareSum32 {
-  float hi = 0.0f, lo = 0.0f;
-  __device__ __forceinline__ void add_square(float x) {
-    const float p = __fmul_rn(x, x);
-    const float pe = __fmaf_rn(x, x, -p);
-    const float t = __fadd_rn(hi, p);
-    const float bp = __fsub_rn(t, hi);
-    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+  float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
+  __device__ __forceinline__ void add_squares(float a, float b) {
+    const float2 x = make_float2(a, b);
+    const float2 p = __fmul2_rn(x, x);
+    const float2 pe = __ffma2_rn(x, x, fsub2_rn(make_float2(0.0f, 0.0f), p));
+    float2 t, err;
+    two_sum2(hi, p, t, err);
     hi = t;
-    lo = __fadd_rn(lo, __fadd_rn(err, pe));
+    lo = __fadd2_rn(lo, __fadd2_rn(err, pe));
   }
   __device__ __forceinline__ void renormalize() {
-    const float t = __fadd_rn(hi, lo);
-    lo = __fsub_rn(lo, __fsub_rn(t, hi));
+    const float2 t = __fadd2_rn(hi, lo);
+    lo = fsub2_rn(lo, fsub2_rn(t, hi));
     hi = t;
   }
+  // adds another sum (h, l) into lane 0, after folding lane 1 into lane 0
+  __device__ __forceinline__ void fold_lanes() {
+    float2 t, err;
+    two_sum2(make_float2(hi.x, 0.0f), make_float2(hi.y, 0.0f), t, err);
+    hi = make_float2(t.x, 0.0f);
+    lo = make_float2(lo.x + lo.y + err.x, 0.0f);
+  }
+  __device__ __forceinline__ void add_sum(float h, float l) {
+    float2 t, err;
+    two_sum2(make_float2(hi.x, 0.0f), make_float2(h, 0.0f), t, err);
+    hi = make_float2(t.x, 0.0f);
+    lo = make_float2(lo.x + (l + err.x), 0.0f);
+  }
 };
-
-// |x| in [2^-50, 2^50] or x == 0: its square and the square's rounding error
-// are normal floats (NaN and infinities fail).
-__device__ __forceinline__ bool square_exact_f32(float x) {
-  const float a = fabsf(x);
-  return a <= 0x1p50f && (a >= 0x1p-50f || a == 0.0f);
-}
 
 __device__ __forceinline__ double max_abs_bits(double a, double b) {
   return __longlong_as_double(
@@ -310,6 +335,7 @@ struct GenericOp {
   static constexpr int kXStep = 1;  // a thread's columns: lane + 32 e
   static constexpr int kGroup = 1;  // columns strided by 32, not grouped (see StaticOpV)
   static constexpr int kRowsPerSlot = 1;
+  static constexpr int kTerms = kMaxTerms;
   template <typename A, bool BATCH>
   using Weights = typename std::conditional<BATCH, RowWeights<A>, ParamWeights<A>>::type;
   __device__ static int n_out(const SweepParams &P) { return P.n_out; }
@@ -383,6 +409,7 @@ struct StaticOp {
   static constexpr int kXStep = XS;
   static constexpr int kGroup = 1;
   static constexpr int kRowsPerSlot = 1;
+  static constexpr int kTerms = Def::NT;
   static constexpr int kMaxOut = Def::NOUT > 0 ? Def::NOUT : 1;
   template <typename A, bool BATCH>
   using Weights = typename std::conditional<BATCH, RegWeights<A, Def::NT>, ParamWeights<A>>::type;
@@ -683,6 +710,7 @@ struct StaticOpV {
   static constexpr int kGroup = G;
   static constexpr int kLanesPerRow = 128 / G;
   static constexpr int kRowsPerSlot = 32 / kLanesPerRow;
+  static constexpr int kTerms = Def::NT;
   static constexpr int kMaxOut = Base::kMaxOut;
   template <typename A, bool BATCH>
   using Weights = typename Base::template Weights<A, BATCH>;
@@ -890,6 +918,36 @@ __device__ __forceinline__ void block_fold(double &s, double &c, double *s_red, 
   }
 }
 
+// The CTA's L2 partial for FP32 arithmetic, valid in thread 0 as (s, c) with
+// value s - c: each warp folds its threads' square sums as FP32 pairs in a
+// fixed shuffle tree, then thread 0 widens the warps' pairs to FP64 and
+// combines them, in order, with the FP64 squares some threads took for
+// out-of-range values (folded by block_fold only when there are any).
+// (s, c) enter as the thread's FP64 part.
+__device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &c, double *s_red, int NW) {
+  const int tid = threadIdx.x, lane = tid & 31, wy = tid >> 5;
+  const bool any64 = __syncthreads_or(s != 0.0 || c != 0.0) != 0;
+  q.fold_lanes();
+  for (int off = 16; off > 0; off >>= 1) {
+    const float h = __shfl_down_sync(0xffffffffu, q.hi.x, off);
+    const float l = __shfl_down_sync(0xffffffffu, q.lo.x, off);
+    q.add_sum(h, l);
+  }
+  if (any64) block_fold<RED_L2>(s, c, s_red, NW);
+  __syncthreads();  // s_red may still be read by block_fold
+  if (lane == 0) {
+    s_red[2 * wy] = (double)q.hi.x;   // the warp's hi + lo as s - c
+    s_red[2 * wy + 1] = -(double)q.lo.x;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double fs = any64 ? s : 0.0, fc = any64 ? c : 0.0;
+    for (int w = 0; w < NW; ++w) combine_pair(fs, fc, s_red[2 * w], s_red[2 * w + 1]);
+    s = fs;
+    c = fc;
+  }
+}
+
 // Warp wy owns the VY adjacent tile rows wy VY .. wy VY + VY - 1, so the
 // y neighbour of one of its rows is the centre of the next (one shared-memory
 // load serves both).
@@ -897,8 +955,18 @@ __device__ __forceinline__ void block_fold(double &s, double &c, double *s_red, 
 // reduction goes to its own partial (per-instance results are folded by
 // batch_finalize_kernel); otherwise the CTA derives its run of (tile, plane)
 // pairs of the single grid and the last CTA folds all partials.
+// Single-grid kernels of small operators (up to 10 terms: the star / heat
+// family) in FP32 arithmetic are bound by memory and latency: they keep four
+// 8-warp CTAs per SM (at most 64 registers per thread).  Larger operators
+// (the climate operator) are held to fewer CTAs by their shared memory.
+template <typename T, bool BATCH, class Op>
+constexpr int min_ctas_per_sm() {
+  return (!BATCH && std::is_same<typename Arith<T>::A, float>::value && Op::kTerms <= 10) ? 4 : 1;
+}
+
 template <typename T, int VX, int VY, int RED, class Op, bool BATCH>
-__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams P) {
+__global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, Op>())
+    sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
   constexpr int XS = Op::kXStep;
   constexpr int G = Op::kGroup;           // > 1: vector lanes (StaticOpV), G contiguous columns each
@@ -1161,14 +1229,22 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
             for (int e = 0; e < VX; ++e)
               if (yok[r] && xok[e]) maxkey = max(maxkey, abs_key(v[e]));
           } else if constexpr (kSq32) {
-            bool exact = true;
+            // |v| <= 2^50 (NaN and infinities fail) and the row's largest |v|
+            // at least 2^-50 (or every value 0): the squares are exact in
+            // FP32 pairs; otherwise this row's squares go to the FP64 chain
+            bool small = true;
+            float m = 0.0f;
 #pragma unroll
-            for (int e = 0; e < VX; ++e) exact &= square_exact_f32(v[e]);
-            if (exact) {
+            for (int e = 0; e < VX; ++e) {
+              const float a = (yok[r] && xok[e]) ? fabsf(v[e]) : 0.0f;
+              small &= a <= 0x1p50f;
+              m = fmaxf(m, a);
+            }
+            if (small && (m >= 0x1p-50f || m == 0.0f)) {
 #pragma unroll
-              for (int e = 0; e < VX; ++e)
-                if (yok[r] && xok[e]) sq32.add_square(v[e]);
-            } else {  // huge, tiny, infinite or NaN values: FP64 squares
+              for (int e = 0; e + 1 < VX; e += 2)
+                sq32.add_squares((yok[r] && xok[e]) ? v[e] : 0.0f, (yok[r] && xok[e + 1]) ? v[e + 1] : 0.0f);
+            } else {
 #pragma unroll
               for (int e = 0; e < VX; ++e)
                 if (yok[r] && xok[e]) sq = fma((double)v[e], (double)v[e], sq);
@@ -1200,24 +1276,21 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     if (RED == RED_L2) {  // squares are non-negative: the chain's relative error is at most its length x eps
       acc.add(sq);
       sq = 0.0;
-      if constexpr (kSq32) {
-        acc.add((double)sq32.hi);
-        acc.add((double)sq32.lo);
-        sq32 = SquareSum32();
-      }
     }
     if (s_abort) break;
     if constexpr (BATCH && RED != RED_NONE) {
       // this segment's partial, in a fixed order; then start afresh
       double fs = RED == RED_MAXABS ? key_value(maxkey, A(0)) : acc.s;
       double fc = RED == RED_MAXABS ? 0.0 : acc.c;
-      block_fold<RED>(fs, fc, s_red, NW);
+      if constexpr (kSq32) cta_fold_sq32(sq32, fs, fc, s_red, NW);
+      else block_fold<RED>(fs, fc, s_red, NW);
       if (tid == 0) {
         P.seg_partials[2 * kseg] = fs;
         P.seg_partials[2 * kseg + 1] = fc;
       }
       acc = Compensated();
       maxkey = 0;
+      sq32 = SquareSum32();
     }
     if constexpr (BATCH) ++kseg;
   }
@@ -1242,7 +1315,8 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
   // ---- single grid: CTA partial, then the last CTA folds all partials
   double s = RED == RED_MAXABS ? key_value(maxkey, A(0)) : acc.s;  // widened: double bits from here on
   double c = RED == RED_MAXABS ? 0.0 : acc.c;
-  block_fold<RED>(s, c, s_red, NW);
+  if constexpr (kSq32) cta_fold_sq32(sq32, s, c, s_red, NW);
+  else block_fold<RED>(s, c, s_red, NW);
   unsigned int *ticket = reinterpret_cast<unsigned int *>(P.workspace);
   double *partials = reinterpret_cast<double *>(P.workspace + 256);
   if (tid == 0) {
@@ -1253,21 +1327,27 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
     s_last = (prev == gridDim.x - 1);
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last || wy != 0) return;
   __threadfence();
-  // last CTA: thread i folds a fixed contiguous chunk of partials, then the
-  // fixed tree of block_fold combines the threads in order.
+  // last CTA, one warp (FP64 work on B300's narrow FP64 pipe stays short):
+  // lane i folds a fixed contiguous chunk of partials, then a fixed shuffle
+  // tree combines the lanes in order.
   const int nctas = gridDim.x;
-  const int chunk = (nctas + blockDim.x - 1) / blockDim.x;
+  const int chunk = (nctas + 31) / 32;
   s = 0.0;
   c = 0.0;
-  for (int b = tid * chunk; b < min(nctas, (tid + 1) * chunk); ++b) {
+  for (int b = lane * chunk; b < min(nctas, (lane + 1) * chunk); ++b) {
     const double ps = __ldcg(&partials[2 * b]);
     const double pc = __ldcg(&partials[2 * b + 1]);
     if (RED == RED_MAXABS) s = max_abs_bits(s, ps);
     else combine_pair(s, c, ps, pc);
   }
-  block_fold<RED>(s, c, s_red, NW);
+  for (int off = 16; off > 0; off >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
+    else combine_pair(s, c, s2, c2);
+  }
   if (tid == 0) {
     double r;
     if (RED == RED_MAXABS) r = P.within >= 0.0 ? (s <= P.within ? 1.0 : 0.0) : s;  // NaN fails the test
@@ -1443,9 +1523,10 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       }
       // vector lanes: 16 bytes of a row per lane (every compile-time table fits)
       constexpr int G = 16 / (int)sizeof(T);
+      constexpr int VYV = sizeof(T) == 2 ? 1 : 2;  // rows per thread (as make_plan)
       static_assert(StaticOpV<Def, G>::fits(), "x reach beyond one group");
       if (!pl.vec) return fail(GSCL_ERR_INVALID, "FP32 / BF16 plan without vector lanes");
-      return launch_t<T, G, RED, StaticOpV<Def, G>, BATCH>(pl, stream, occ);
+      return launch_t<T, G, RED, StaticOpV<Def, G>, BATCH, VYV>(pl, stream, occ);
     } else {
       // colour-compacted red-black sweeps of the star family on FP64 grids
       // (IEEE or pair arithmetic), single grids and coloured batches
