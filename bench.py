@@ -375,7 +375,7 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
         insts.append(([B.Grid(n, h, "f32").upload(u0)], [B.Grid(n, h, "f32").upload(u0)]))
     op = B.Stencil(S.heat7(LAM, with_f=False))
     batch = B.Batch(op, insts)
-    cfg = batch.tune(trial_sweeps=3) if tune else None
+    cfg = batch.tune(trial_sweeps=10) if tune else None
     info = batch.info()
     tile = batch.tile()
     points = sum(a * b * c for a, b, c in sides)

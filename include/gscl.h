@@ -510,12 +510,13 @@ gscl_status gscl_batch_run_colored(gscl_batch b, int32_t color, int32_t half_swe
 gscl_status gscl_batch_reduce(gscl_batch b, int32_t reduce_op, double *results, void *stream);
 
 /*
- * Autotuner: times trial_sweeps sweeps (in[0] -> out[0], so in[0] is left
- * unchanged and out[0] receives one sweep) for each tile shape (warps per
- * CTA 2/4/8 x prefetched planes 1/2/3, and for FP32 / BF16 batches both the
- * default 128-column tiles and 64-column tiles with 4 rows per warp), keeps
- * the fastest and reports its warps and prefetch (gscl_batch_tile gives the
- * tile).  Synchronises `stream`.
+ * Autotuner: times two groups of trial_sweeps sweeps (in[0] -> out[0], so
+ * in[0] is left unchanged and out[0] receives one sweep) for each tile shape
+ * (warps per CTA 2/4/8 x prefetched planes 1/2/3, and for FP32 / BF16
+ * batches both the default 128-column tiles and 64-column tiles with 4 rows
+ * per warp), keeps the shape whose better group was fastest and reports its
+ * warps and prefetch (gscl_batch_tile gives the tile).  Synchronises
+ * `stream`.
  */
 gscl_status gscl_batch_tune(gscl_batch b, int32_t trial_sweeps, void *stream, int32_t *warps, int32_t *prefetch);
 

@@ -496,12 +496,19 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
       pl.P.insts = bt->tab[first];  // in[0] -> out[0] every trial: in[0] is left as it was
       if (red != RED_NONE) pl.P.seg_partials = bt->partials;
       if (launch(pl, bt->dtype, red, st, nullptr) != GSCL_OK) continue;
-      cudaEventRecord(e0, st);
-      for (int s = 0; s < trial_sweeps; ++s) launch(pl, bt->dtype, red, st, nullptr);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) break;
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
+      // the better of two timed groups: one group can catch a slow moment
+      float ms = 1e30f;
+      bool timed = true;
+      for (int rep = 0; rep < 2 && timed; ++rep) {
+        cudaEventRecord(e0, st);
+        for (int s = 0; s < trial_sweeps; ++s) launch(pl, bt->dtype, red, st, nullptr);
+        cudaEventRecord(e1, st);
+        timed = cudaEventSynchronize(e1) == cudaSuccess;
+        float t = 0.f;
+        if (timed) cudaEventElapsedTime(&t, e0, e1);
+        ms = std::min(ms, t);
+      }
+      if (!timed) break;
       if (ms < best_ms) {
         best_ms = ms;
         best = bt->cfg;

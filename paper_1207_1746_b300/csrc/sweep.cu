@@ -236,9 +236,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const uint32_t cmask = (compact || (g0.dtype == GSCL_F64 && !pl->pair)) ? 0u : static_centre_mask(pl->op);
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
-  // rows per thread: vector lanes of BF16 (16 columns of a half-warp row) take
-  // one, which keeps the z register queue at 24 registers
-  const int VY = narrow ? 4 : (vlanes && elem == 2 ? 1 : vy_for(g0.dtype));
+  const int VY = narrow ? 4 : vy_for(g0.dtype);
   // defaults from tile sweeps on the 256^3 heat workload (B300): FP64 4 warps,
   // FP32 / BF16 8 warps, one plane prefetched beyond the stencil's reach
   int NW = g0.dtype == GSCL_F64 ? 4 : 8, PF = nz_range > 1 ? 1 : 0;

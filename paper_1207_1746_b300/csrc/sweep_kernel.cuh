@@ -257,21 +257,39 @@ __device__ __forceinline__ void combine_pair(double &s, double &c, double s2, do
   c = (c + c2) - err;
 }
 
-// Packed two-lane FP32 subtraction (sub.rn.f32x2, sm_100 family): each lane
-// one sub.rn, like the __fadd2_rn / __fmul2_rn / __ffma2_rn intrinsics.
+// Packed two-lane FP32 arithmetic (the .f32x2 instructions of the sm_100
+// family), each lane one correctly rounded operation.  Written as inline PTX
+// so that the compiler can neither contract a multiply and an add into an
+// FMA nor reassociate: the error-free transformations below rely on every
+// operation being rounded on its own.
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) { return *reinterpret_cast<const unsigned long long *>(&a); }
+__device__ __forceinline__ float2 bits_f2(unsigned long long d) { return *reinterpret_cast<const float2 *>(&d); }
+__device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
 __device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
   unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;"
-      : "=l"(d)
-      : "l"(*reinterpret_cast<const unsigned long long *>(&a)), "l"(*reinterpret_cast<const unsigned long long *>(&b)));
-  return *reinterpret_cast<const float2 *>(&d);
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 fmul2_rn(float2 a, float2 b) {
+  unsigned long long d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+  return bits_f2(d);
+}
+__device__ __forceinline__ float2 ffma2_rn(float2 a, float2 b, float2 c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+  return bits_f2(d);
 }
 
 // Knuth's TwoSum on both lanes: t + err == a + b exactly, lane by lane.
 __device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &t, float2 &err) {
-  t = __fadd2_rn(a, b);
+  t = fadd2_rn(a, b);
   const float2 bp = fsub2_rn(t, a);
-  err = __fadd2_rn(fsub2_rn(a, fsub2_rn(t, bp)), fsub2_rn(b, bp));
+  err = fadd2_rn(fsub2_rn(a, fsub2_rn(t, bp)), fsub2_rn(b, bp));
 }
 
 // Sum of squares of FP32 values on the FP32 pipe (the L2 reduction of FP32 /
@@ -290,30 +308,31 @@ struct SquareSum32 {
   float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
   __device__ __forceinline__ void add_squares(float a, float b) {
     const float2 x = make_float2(a, b);
-    const float2 p = __fmul2_rn(x, x);
-    const float2 pe = __ffma2_rn(x, x, fsub2_rn(make_float2(0.0f, 0.0f), p));
+    const float2 p = fmul2_rn(x, x);
+    const float2 pe = ffma2_rn(x, x, fsub2_rn(make_float2(0.0f, 0.0f), p));
     float2 t, err;
     two_sum2(hi, p, t, err);
     hi = t;
-    lo = __fadd2_rn(lo, __fadd2_rn(err, pe));
+    lo = fadd2_rn(lo, fadd2_rn(err, pe));
   }
   __device__ __forceinline__ void renormalize() {
-    const float2 t = __fadd2_rn(hi, lo);
+    const float2 t = fadd2_rn(hi, lo);
     lo = fsub2_rn(lo, fsub2_rn(t, hi));
     hi = t;
   }
-  // adds another sum (h, l) into lane 0, after folding lane 1 into lane 0
+  // folds lane 1 into lane 0
   __device__ __forceinline__ void fold_lanes() {
     float2 t, err;
     two_sum2(make_float2(hi.x, 0.0f), make_float2(hi.y, 0.0f), t, err);
     hi = make_float2(t.x, 0.0f);
-    lo = make_float2(lo.x + lo.y + err.x, 0.0f);
+    lo = make_float2(__fadd_rn(__fadd_rn(lo.x, lo.y), err.x), 0.0f);
   }
+  // adds another sum h + l into lane 0
   __device__ __forceinline__ void add_sum(float h, float l) {
     float2 t, err;
     two_sum2(make_float2(hi.x, 0.0f), make_float2(h, 0.0f), t, err);
     hi = make_float2(t.x, 0.0f);
-    lo = make_float2(lo.x + (l + err.x), 0.0f);
+    lo = make_float2(__fadd_rn(lo.x, __fadd_rn(l, err.x)), 0.0f);
   }
 };
 
@@ -1523,10 +1542,9 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       }
       // vector lanes: 16 bytes of a row per lane (every compile-time table fits)
       constexpr int G = 16 / (int)sizeof(T);
-      constexpr int VYV = sizeof(T) == 2 ? 1 : 2;  // rows per thread (as make_plan)
       static_assert(StaticOpV<Def, G>::fits(), "x reach beyond one group");
       if (!pl.vec) return fail(GSCL_ERR_INVALID, "FP32 / BF16 plan without vector lanes");
-      return launch_t<T, G, RED, StaticOpV<Def, G>, BATCH, VYV>(pl, stream, occ);
+      return launch_t<T, G, RED, StaticOpV<Def, G>, BATCH>(pl, stream, occ);
     } else {
       // colour-compacted red-black sweeps of the star family on FP64 grids
       // (IEEE or pair arithmetic), single grids and coloured batches
