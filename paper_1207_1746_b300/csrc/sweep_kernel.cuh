@@ -257,82 +257,61 @@ __device__ __forceinline__ void combine_pair(double &s, double &c, double s2, do
   c = (c + c2) - err;
 }
 
-// Packed two-lane FP32 arithmetic (the .f32x2 instructions of the sm_100
-// family), each lane one correctly rounded operation.  Written as inline PTX
-// so that the compiler can neither contract a multiply and an add into an
-// FMA nor reassociate: the error-free transformations below rely on every
-// operation being rounded on its own.
-__device__ __forceinline__ unsigned long long f2_bits(float2 a) { return *reinterpret_cast<const unsigned long long *>(&a); }
-__device__ __forceinline__ float2 bits_f2(unsigned long long d) { return *reinterpret_cast<const float2 *>(&d); }
-__device__ __forceinline__ float2 fadd2_rn(float2 a, float2 b) {
-  unsigned long long d;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(d);
-}
-__device__ __forceinline__ float2 fsub2_rn(float2 a, float2 b) {
-  unsigned long long d;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(d);
-}
-__device__ __forceinline__ float2 fmul2_rn(float2 a, float2 b) {
-  unsigned long long d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
-  return bits_f2(d);
-}
-__device__ __forceinline__ float2 ffma2_rn(float2 a, float2 b, float2 c) {
-  unsigned long long d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
-  return bits_f2(d);
-}
-
-// Knuth's TwoSum on both lanes: t + err == a + b exactly, lane by lane.
-__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &t, float2 &err) {
-  t = fadd2_rn(a, b);
-  const float2 bp = fsub2_rn(t, a);
-  err = fadd2_rn(fsub2_rn(a, fsub2_rn(t, bp)), fsub2_rn(b, bp));
+// Knuth's TwoSum: t + err == a + b exactly.  The _rn intrinsics are never
+// contracted into FMAs, which would break the error-free steps.
+__device__ __forceinline__ void two_sum(float a, float b, float &t, float &err) {
+  t = __fadd_rn(a, b);
+  const float bp = __fsub_rn(t, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bp)), __fsub_rn(b, bp));
 }
 
 // Sum of squares of FP32 values on the FP32 pipe (the L2 reduction of FP32 /
-// BF16 sweeps), as two unevaluated pairs hi + lo, one per lane of the packed
-// two-lane instructions (even and odd elements of a group).  Each square is
-// formed exactly as p + pe (the product, and its rounding error from one
-// FMA: exact while |x| lies in [2^-50, 2^50], which the caller checks) and
-// added with Knuth's error-free TwoSum, the errors going to lo.  renormalize()
-// keeps |lo| within an ulp of hi; the pairs are folded lane to lane, across
-// the warp and into FP64 only at the end of a reduction, so the narrow FP64
-// pipe sees a few operations per warp instead of one FMA per element.  The
-// packed intrinsics and the explicit subtraction keep the compiler from
-// contracting the steps into FMAs, which would break their exactness.
-// Relative error of a sum of n squares: about (3 + n) 2^-48.
+// BF16 sweeps), as two unevaluated pairs hi + lo (even and odd elements of a
+// group, two independent chains).  Each square is formed exactly as p + pe
+// (the product, and its rounding error from one FMA: exact while |x| lies in
+// [2^-50, 2^50], which the caller checks) and added with Knuth's error-free
+// TwoSum, the errors going to lo.  renormalize() keeps |lo| within an ulp of
+// hi; the pairs are folded chain to chain, across the warp and into FP64
+// only at the end of a reduction, so the narrow FP64 pipe sees a few
+// operations per warp instead of one FMA per element.  Relative error of a
+// sum of n squares: about (3 + n) 2^-48.
 struct SquareSum32 {
-  float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
-  __device__ __forceinline__ void add_squares(float a, float b) {
-    const float2 x = make_float2(a, b);
-    const float2 p = fmul2_rn(x, x);
-    const float2 pe = ffma2_rn(x, x, fsub2_rn(make_float2(0.0f, 0.0f), p));
-    float2 t, err;
-    two_sum2(hi, p, t, err);
+  float hi0 = 0.0f, lo0 = 0.0f, hi1 = 0.0f, lo1 = 0.0f;
+  __device__ __forceinline__ static void add(float &hi, float &lo, float x) {
+    const float p = __fmul_rn(x, x);
+    const float pe = __fmaf_rn(x, x, -p);
+    float t, err;
+    two_sum(hi, p, t, err);
     hi = t;
-    lo = fadd2_rn(lo, fadd2_rn(err, pe));
+    lo = __fadd_rn(lo, __fadd_rn(err, pe));
+  }
+  __device__ __forceinline__ void add_squares(float a, float b) {
+    add(hi0, lo0, a);
+    add(hi1, lo1, b);
+  }
+  __device__ __forceinline__ static void renorm(float &hi, float &lo) {
+    const float t = __fadd_rn(hi, lo);
+    lo = __fsub_rn(lo, __fsub_rn(t, hi));
+    hi = t;
   }
   __device__ __forceinline__ void renormalize() {
-    const float2 t = fadd2_rn(hi, lo);
-    lo = fsub2_rn(lo, fsub2_rn(t, hi));
-    hi = t;
+    renorm(hi0, lo0);
+    renorm(hi1, lo1);
   }
-  // folds lane 1 into lane 0
+  // folds chain 1 into chain 0
   __device__ __forceinline__ void fold_lanes() {
-    float2 t, err;
-    two_sum2(make_float2(hi.x, 0.0f), make_float2(hi.y, 0.0f), t, err);
-    hi = make_float2(t.x, 0.0f);
-    lo = make_float2(__fadd_rn(__fadd_rn(lo.x, lo.y), err.x), 0.0f);
+    float t, err;
+    two_sum(hi0, hi1, t, err);
+    hi0 = t;
+    lo0 = __fadd_rn(__fadd_rn(lo0, lo1), err);
+    hi1 = lo1 = 0.0f;
   }
-  // adds another sum h + l into lane 0
+  // adds another sum h + l into chain 0
   __device__ __forceinline__ void add_sum(float h, float l) {
-    float2 t, err;
-    two_sum2(make_float2(hi.x, 0.0f), make_float2(h, 0.0f), t, err);
-    hi = make_float2(t.x, 0.0f);
-    lo = make_float2(__fadd_rn(lo.x, __fadd_rn(l, err.x)), 0.0f);
+    float t, err;
+    two_sum(hi0, h, t, err);
+    hi0 = t;
+    lo0 = __fadd_rn(lo0, __fadd_rn(l, err));
   }
 };
 
@@ -948,15 +927,15 @@ __device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &
   const bool any64 = __syncthreads_or(s != 0.0 || c != 0.0) != 0;
   q.fold_lanes();
   for (int off = 16; off > 0; off >>= 1) {
-    const float h = __shfl_down_sync(0xffffffffu, q.hi.x, off);
-    const float l = __shfl_down_sync(0xffffffffu, q.lo.x, off);
+    const float h = __shfl_down_sync(0xffffffffu, q.hi0, off);
+    const float l = __shfl_down_sync(0xffffffffu, q.lo0, off);
     q.add_sum(h, l);
   }
   if (any64) block_fold<RED_L2>(s, c, s_red, NW);
   __syncthreads();  // s_red may still be read by block_fold
   if (lane == 0) {
-    s_red[2 * wy] = (double)q.hi.x;   // the warp's hi + lo as s - c
-    s_red[2 * wy + 1] = -(double)q.lo.x;
+    s_red[2 * wy] = (double)q.hi0;   // the warp's hi + lo as s - c
+    s_red[2 * wy + 1] = -(double)q.lo0;
   }
   __syncthreads();
   if (tid == 0) {
@@ -975,12 +954,13 @@ __device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &
 // batch_finalize_kernel); otherwise the CTA derives its run of (tile, plane)
 // pairs of the single grid and the last CTA folds all partials.
 // Single-grid kernels of small operators (up to 10 terms: the star / heat
-// family) in FP32 arithmetic are bound by memory and latency: they keep four
+// family) on FP32 grids are bound by memory and latency: they keep four
 // 8-warp CTAs per SM (at most 64 registers per thread).  Larger operators
-// (the climate operator) are held to fewer CTAs by their shared memory.
+// (the climate operator) are held to fewer CTAs by their shared memory, and
+// BF16 vector lanes (two rows of 8 columns per thread) need more registers.
 template <typename T, bool BATCH, class Op>
 constexpr int min_ctas_per_sm() {
-  return (!BATCH && std::is_same<typename Arith<T>::A, float>::value && Op::kTerms <= 10) ? 4 : 1;
+  return (!BATCH && std::is_same<T, float>::value && Op::kTerms <= 10) ? 4 : 1;
 }
 
 template <typename T, int VX, int VY, int RED, class Op, bool BATCH>
