@@ -10,6 +10,7 @@
 // their instances in place, one colour per launch, and take one operator per
 // instance: the same term structure with the instance's own weights, which
 // the kernel reads from a per-instance weight table.
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -485,17 +486,29 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
   // tile shape: the dtype's default, and for FP32 / BF16 the narrow 64-column
   // tiles (4 rows per warp) that waste fewer lanes on narrow grids
   const int shapes = bt->dtype == GSCL_F64 ? 1 : 2;
+  // GSCL_TUNE_LOG=1 prints every trial's time to stderr
+  const char *log_env = getenv("GSCL_TUNE_LOG");
+  const bool log = log_env && log_env[0] == '1';
   for (int narrow = 0; narrow < shapes; ++narrow)
   for (int nw : nws)
     for (int pf : pfs) {
       bt->cfg = TileCfg{nw, pf, keep.generic, narrow != 0};
-      if (build(bt) != GSCL_OK) continue;  // e.g. does not fit in shared memory
+      gscl_status bs = build(bt);
+      if (bs != GSCL_OK) {  // e.g. does not fit in shared memory
+        if (log) fprintf(stderr, "gscl_batch_tune: narrow %d warps %d prefetch %d: %s\n", narrow, nw, pf,
+                         gscl_last_error());
+        continue;
+      }
       int first = 0;
       if (current_table(bt, &first) != GSCL_OK) continue;
       Plan pl = bt->base;
       pl.P.insts = bt->tab[first];  // in[0] -> out[0] every trial: in[0] is left as it was
       if (red != RED_NONE) pl.P.seg_partials = bt->partials;
-      if (launch(pl, bt->dtype, red, st, nullptr) != GSCL_OK) continue;
+      if (launch(pl, bt->dtype, red, st, nullptr) != GSCL_OK) {
+        if (log) fprintf(stderr, "gscl_batch_tune: narrow %d warps %d prefetch %d: launch failed: %s\n", narrow,
+                         nw, pf, gscl_last_error());
+        continue;
+      }
       // the better of two timed groups: one group can catch a slow moment
       float ms = 1e30f;
       bool timed = true;
@@ -509,6 +522,9 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
         ms = std::min(ms, t);
       }
       if (!timed) break;
+      if (log)
+        fprintf(stderr, "gscl_batch_tune: narrow %d warps %d prefetch %d: tile %d x %d, %d CTAs, %.4f ms per sweep\n",
+                narrow, nw, pf, bt->base.tile_x, bt->base.tile_y, bt->G, ms / trial_sweeps);
       if (ms < best_ms) {
         best_ms = ms;
         best = bt->cfg;
