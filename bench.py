@@ -202,6 +202,47 @@ def run_gpu(dtype, steps, warmup, dist, n=N_SIDE, sweeps=SWEEPS, clocks=None):
             "launches": steps * sweeps, "points": n ** 3, "residuals": residuals}
 
 
+def run_temporal(dtype, n=N_SIDE, sweeps=8, reps=5):
+    """Temporal blocking on the plain heat sweep (FP32 / BF16 storage): the
+    time per sweep of `sweeps`-sweep gscl_do_all calls with K = 1 .. 4 sweeps
+    fused per pass over HBM (GSCL_TEMPORAL), then the factor gscl_tune_sweeps
+    picks for these grids (remembered, so the variant runs use it)."""
+    import torch
+
+    from paper_1207_1746_b300 import binding as B
+    from paper_1207_1746_b300 import inputs as I
+    from paper_1207_1746_b300 import stencils as S
+
+    h, shape = (1, 1, 1), (n, n, n)
+    u0, f = I.heat3d(SEED, n)
+    u, v, F = B.Grid(shape, h, dtype).upload(u0), B.Grid(shape, h, dtype).upload(u0), B.Grid(shape, h, dtype).upload(f)
+    op = B.Stencil(S.heat7(LAM))
+    stream = torch.cuda.current_stream()
+    out = {"sweeps_per_call": sweeps}
+    old = os.environ.get("GSCL_TEMPORAL")
+    try:
+        for K in (1, 2, 3, 4):
+            os.environ["GSCL_TEMPORAL"] = str(K)
+            B.do_all(op, [u, F], [v], sweeps=sweeps)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                B.do_all(op, [u, F], [v], sweeps=sweeps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[f"k{K}_ms_per_sweep"] = round(e0.elapsed_time(e1) / (reps * sweeps), 5)
+    finally:
+        if old is None:
+            os.environ.pop("GSCL_TEMPORAL", None)
+        else:
+            os.environ["GSCL_TEMPORAL"] = old
+    out["tuned_factor"] = B.tune_sweeps(op, [u, F], [v], trial_sweeps=8)
+    out["speedup_k2_vs_k1"] = round(out["k1_ms_per_sweep"] / out["k2_ms_per_sweep"], 3)
+    B.sync()
+    return out
+
+
 def run_fusion_ablation(dtype, reps=20, n=N_SIDE):
     """Section 5.2's fused diffusion + convergence test against the two-pass
     form on the heat workload: one fused sweep returning the L2 residual of
@@ -944,6 +985,19 @@ def roofline_hbm(dtype, plain_ms, points, peaks):
             "peak_source": src}
 
 
+def variant_roofline(dtype, plain_ms, temporal, points, peaks):
+    """HBM roofline of the plain FP32 / BF16 sweeps: with K > 1 sweeps fused
+    per pass (the tuner's factor) one launch does K sweeps and moves the
+    bytes of one, so the launch time is K times the time per sweep."""
+    K = temporal.get("tuned_factor", 1) if temporal else 1
+    if K <= 1:
+        return roofline_hbm(dtype, plain_ms, points, peaks)
+    r = roofline_hbm(dtype, temporal[f"k{K}_ms_per_sweep"] * K, points, peaks)
+    r["traffic"] = None
+    r["note"] = f"{K} sweeps per launch (temporal blocking): the bytes of one sweep per launch"
+    return r
+
+
 PROFILE = False  # --profile: short runs for profilers, without the FMA microbenchmark
 
 
@@ -1308,6 +1362,7 @@ def main():
     roof = roofline_fp64(main_run["plain_launch_ms"], args.n ** 3, peaks, clocks.get("sm_mhz"), fma_tflops)
 
     variants = {}
+    temporal = {}
     if not args.no_variants:
         # FP64 storage in pair arithmetic (FP32 pairs off the FP64 pipe; within the
         # FP64 tolerance, 2^-47 instead of 2^-53 per operation)
@@ -1327,16 +1382,18 @@ def main():
             "fused_launch_ms": round(rp["fused_launch_ms"], 4), "plain_launch_ms": round(rp["plain_launch_ms"], 4),
             "final_residual": rp["residuals"][-1],
             "speedup_vs_ieee_fp64": round(t_max / tp, 3)}
-        # FP32 storage, and BF16 storage (FP32 arithmetic; a smoothing-grade precision)
+        # FP32 storage, and BF16 storage (FP32 arithmetic; a smoothing-grade precision),
+        # with the temporal factor the tuner picks for the plain sweeps
         for vdt in ("f32", "bf16"):
+            temporal[vdt] = run_temporal(vdt, args.n)
             rv = run_gpu(vdt, args.steps, args.warmup, dist, args.n, args.sweeps)
             tv = dist.max(rv["ms_total"])
             variants[vdt] = {
                 "dtype": vdt, "value": round(updates / (tv * 1e-3) / 1e9, 3), "unit": "GPoint-updates/s",
                 "ms_per_step": round(tv / args.steps, 3),
-                "roofline": roofline_hbm(vdt, rv["plain_launch_ms"], args.n ** 3, peaks),
+                "roofline": variant_roofline(vdt, rv["plain_launch_ms"], temporal[vdt], args.n ** 3, peaks),
                 "fused_launch_ms": round(rv["fused_launch_ms"], 4), "plain_launch_ms": round(rv["plain_launch_ms"], 4),
-                "final_residual": rv["residuals"][-1]}
+                "temporal_factor": temporal[vdt]["tuned_factor"], "final_residual": rv["residuals"][-1]}
 
     e2e = None
     if not args.no_e2e:
@@ -1370,7 +1427,7 @@ def main():
                 "kernel_ms": {"plain_sweep": round(main_run["plain_launch_ms"], 4),
                               "fused_sweep_l2": round(main_run["fused_launch_ms"], 4)},
                 "final_residual": main_run["residuals"][-1], "variants": variants,
-                "fusion_ablation": ablation, "error_vs_oracle": errors}
+                "fusion_ablation": ablation, "error_vs_oracle": errors, "temporal_blocking": temporal}
         print(json.dumps(line))
 
 

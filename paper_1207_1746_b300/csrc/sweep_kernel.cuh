@@ -960,7 +960,7 @@ __device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &
 // BF16 vector lanes (two rows of 8 columns per thread) need more registers.
 template <typename T, bool BATCH, class Op>
 constexpr int min_ctas_per_sm() {
-  return (!BATCH && std::is_same<T, float>::value && Op::kTerms <= 10) ? 4 : 1;
+  return (!BATCH && std::is_same<T, float>::value && Op::kTerms <= 10) ? 4 : 0;
 }
 
 template <typename T, int VX, int VY, int RED, class Op, bool BATCH>

@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "sweep_host.h"
+#include "tb2_kernel.cuh"
 #include "tb_kernel.cuh"
 
 namespace gscl {
@@ -64,10 +65,60 @@ gscl_status launch_tb_op(const Plan &pl, cudaStream_t stream) {
   return fail(GSCL_ERR_INVALID, "no temporal-blocking kernel for operator %d", pl.op);
 }
 
+// K = 2: the vector-lane kernel (tb2_kernel.cuh), one wave with programmatic
+// dependent launch like the single sweeps.
+template <typename T, class Def>
+gscl_status launch_tb2_t(const Plan &pl, cudaStream_t stream) {
+  auto kern = tb2_kernel<T, Def>;
+  constexpr size_t smem = Tb2Shape<T>::smem_bytes();
+  constexpr int kDevices = 64;
+  static std::mutex mu;
+  static int per_sm_of[kDevices] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= kDevices) return fail(GSCL_ERR_UNSUPPORTED, "device %d beyond the supported count", dev);
+  int per_sm = 0;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (!per_sm_of[dev]) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      int nb = 0;
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 256, smem);
+      if (e != cudaSuccess) return cuda_fail(e, "two-sweep kernel set-up");
+      per_sm_of[dev] = nb > 0 ? nb : 1;
+    }
+    per_sm = per_sm_of[dev];
+  }
+  const long long ctas = std::min<long long>(pl.work, (long long)sm_count() * per_sm);
+  if (ctas < 1) return GSCL_OK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ctas);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, pl.P);
+  return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "two-sweep kernel launch");
+}
+
+template <typename T>
+gscl_status launch_tb2(const Plan &pl, cudaStream_t stream) {
+  switch (pl.op) {
+    case OP_STAR7: return launch_tb2_t<T, OpStar7>(pl, stream);
+    case OP_HEAT7_RHS: return launch_tb2_t<T, OpHeat7Rhs>(pl, stream);
+    case OP_JACOBI7_RHS: return launch_tb2_t<T, OpJacobi7Rhs>(pl, stream);
+  }
+  return fail(GSCL_ERR_INVALID, "no temporal-blocking kernel for operator %d", pl.op);
+}
+
 template <typename T>
 gscl_status launch_tb_k(const Plan &pl, int K, cudaStream_t stream) {
   switch (K) {
-    case 2: return launch_tb_op<T, 2>(pl, stream);
+    case 2: return launch_tb2<T>(pl, stream);
     case 3: return launch_tb_op<T, 3>(pl, stream);
     case 4: return launch_tb_op<T, 4>(pl, stream);
   }
@@ -135,6 +186,20 @@ void tb_geometry(int K, int *TX, int *TY, int *BW0, int *BH0) {
 gscl_status make_tb_plan(const Bound &b, int K, Plan *pl) {
   if (gscl_status s = make_plan(b, false, pl, TileCfg{})) return s;
   const Grid &g = b.in[0];
+  if (K == 2) {
+    // 128 x 14 output tiles; u boxes (128 + 2 AX) x 18, f boxes 128 x 16
+    const int AX = 16 / g.elem;
+    SweepParams &P = pl->P;
+    if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[0], b.in[0], (uint32_t)(128 + 2 * AX), 18)) return s;
+    if (b.in.size() > 1)
+      if (gscl_status s = encode_tensor_map_3d(&P.inst.tmap[1], b.in[1], 128, 16)) return s;
+    P.inst.x_base = 0;
+    P.inst.y_base = 0;
+    P.inst.tiles_x = (int32_t)((g.n[0] + 127) / 128);
+    P.inst.tiles_y = (int32_t)((g.n[1] + 13) / 14);
+    pl->work = (long long)P.inst.tiles_x * P.inst.tiles_y * g.n[2];
+    return GSCL_OK;
+  }
   int TX, TY, BW0, BH0;
   if (g.dtype == GSCL_F32) tb_geometry<float>(K, &TX, &TY, &BW0, &BH0);
   else tb_geometry<__nv_bfloat16>(K, &TX, &TY, &BW0, &BH0);
