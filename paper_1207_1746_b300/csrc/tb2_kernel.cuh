@@ -76,7 +76,11 @@ __global__ void __launch_bounds__(256) tb2_kernel(const __grid_constant__ SweepP
   const int64_t nx = I.hi[0], ny = I.hi[1], nz = I.hi[2];  // the range is the whole interior
   const long long W = (long long)I.tiles_x * I.tiles_y * nz;
   const long long run_end = W * (blockIdx.x + 1) / gridDim.x;
-  uint32_t u_issued = 0, u_waited = 0, f_issued = 0, f_waited = 0;  // planes, in order, over the CTA's runs
+  // ring positions of the next run's plane 0, advanced identically in every
+  // thread; issued counts are thread 0's (it issues), waited counts each
+  // thread's own (both only drain copies after a wait gave up)
+  uint32_t u_pos = 0, f_pos = 0;
+  uint32_t u_issued = 0, u_waited = 0, f_issued = 0, f_waited = 0;
   bool ok = true;
   constexpr uint32_t u_bytes = (uint32_t)(sizeof(T) * BW * S::BH);
   constexpr uint32_t f_bytes = (uint32_t)(sizeof(T) * S::TX * S::FH);
@@ -93,7 +97,9 @@ __global__ void __launch_bounds__(256) tb2_kernel(const __grid_constant__ SweepP
     const int64_t y0 = (int64_t)(col / I.tiles_x) * S::TY;
     const int64_t zb = zoff;
     const int total = zlen + 4;  // u planes zb - 2 .. zb + zlen + 1
-    const uint32_t u0 = u_issued, f0 = f_issued;  // ring positions of this run's plane 0
+    const uint32_t u0 = u_pos, f0 = f_pos;  // ring positions of this run's plane 0
+    u_pos += (uint32_t)total;
+    if (RHS) f_pos += (uint32_t)total;
     // stage 2 of the previous run's last step read f after that step's barrier
     __syncthreads();
 
