@@ -1053,14 +1053,15 @@ def main():
                          "FMA microbenchmark (the printed numbers are not benchmark values)")
     ap.add_argument("--workload", default="heat3d",
                     choices=["heat3d", "batched", "serving", "laplace2d", "climate", "ordered", "redblack",
-                             "diamond", "program"],
+                             "diamond", "program", "temporal"],
                     help="heat3d: the 256^3 heat solve (default line); batched: 96 uneven FP32 instances; "
                          "serving: Poisson solve requests; laplace2d: 256^2 FP64 Jacobi, 100 sweeps; "
                          "climate: 8 -> 3 grid operator on 256 x 256 x 80, FP64 and FP32, 50 sweeps; "
                          "ordered: do_k_inc bidiagonal solve down 256 x 256 columns of 80; "
                          "redblack: red-black SOR on the 256^3 FP64 Poisson problem; "
                          "diamond: natural-order Gauss-Seidel (do_diamond) on 64 planes of 512^2 FP64; "
-                         "program: the 256^3 heat sweep as a run-time compiled body")
+                         "program: the 256^3 heat sweep as a run-time compiled body; "
+                         "temporal: K = 1..4 sweeps per pass (temporal blocking) on the 256^3 heat sweep, FP32 / BF16")
     args = ap.parse_args()
     if args.profile:
         global PROFILE
@@ -1327,6 +1328,23 @@ def main():
                 "fp64_pipe": out["f64"].get("fp64_pipe"), "path": out["f64"]["path"],
                 "variants": {k: {"dtype": k.split("_")[0], **v} for k, v in out.items() if k != "f64"},
                 "gpu_launches": args.steps * 10}
+        if dist.rank == 0:
+            print(json.dumps(line))
+        return
+    if args.workload == "temporal":
+        t = {dt: run_temporal(dt, args.n, reps=1 if args.profile else 5) for dt in ("f32", "bf16")}
+        k1 = dist.max(t["f32"]["k1_ms_per_sweep"])
+        best = min((t["f32"][f"k{K}_ms_per_sweep"], K) for K in (1, 2, 3, 4))
+        line = {"metric": "GPoint-updates/s", "value": round(dist.world * args.n ** 3 / (best[0] * 1e-3) / 1e9, 3),
+                "unit": "GPoint-updates/s", "n_gpus": args.gpus, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"temporal blocking: plain 3D 7-point heat sweep (lam = 1/8, RHS), "
+                                       f"{args.n}^3, 8 sweeps per gscl_do_all call, K sweeps per pass over HBM",
+                           "grid": [args.n] * 3},
+                "roofline": roofline_hbm("f32", best[0] * best[1], args.n ** 3, peaks) if best[1] == 1 else
+                variant_roofline("f32", k1, {"tuned_factor": best[1], **t["f32"]}, args.n ** 3, peaks),
+                "best_factor": best[1], "f32": t["f32"], "bf16": t["bf16"],
+                "gpu_launches": 5 * 8}
         if dist.rank == 0:
             print(json.dumps(line))
         return

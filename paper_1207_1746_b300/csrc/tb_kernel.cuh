@@ -107,7 +107,10 @@ __global__ void __launch_bounds__(256) tb_kernel(const __grid_constant__ SweepPa
     const int64_t y0 = (int64_t)(col / I.tiles_x) * S::TY;
     const int64_t zb = zoff;
     const int total = zlen + 2 * K;
-    const int slot_first = islot;
+    // ring slot of this run's first plane: every plane issued so far has been
+    // waited for, so the wait position (the same in every thread) is the issue
+    // position (thread 0's alone)
+    const int slot_first = wslot;
 
     auto issue = [&](int s) {
       const int slot = islot;
