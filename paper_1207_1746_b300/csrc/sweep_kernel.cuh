@@ -265,53 +265,58 @@ __device__ __forceinline__ void two_sum(float a, float b, float &t, float &err) 
   err = __fadd_rn(__fsub_rn(a, __fsub_rn(t, bp)), __fsub_rn(b, bp));
 }
 
+// Knuth's TwoSum on two independent lanes at once (the sm_100-family packed
+// FP32 add, each lane exactly one __fadd_rn).  Subtraction is an add of the
+// negated operand, which is exact.
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2 &t, float2 &err) {
+  t = __fadd2_rn(a, b);
+  const float2 bp = __fadd2_rn(t, neg2(a));
+  err = __fadd2_rn(__fadd2_rn(a, neg2(__fadd2_rn(t, neg2(bp)))), __fadd2_rn(b, neg2(bp)));
+}
+
 // Sum of squares of FP32 values on the FP32 pipe (the L2 reduction of FP32 /
 // BF16 sweeps), as two unevaluated pairs hi + lo (even and odd elements of a
-// group, two independent chains).  Each square is formed exactly as p + pe
-// (the product, and its rounding error from one FMA: exact while |x| lies in
-// [2^-50, 2^50], which the caller checks) and added with Knuth's error-free
-// TwoSum, the errors going to lo.  renormalize() keeps |lo| within an ulp of
-// hi; the pairs are folded chain to chain, across the warp and into FP64
-// only at the end of a reduction, so the narrow FP64 pipe sees a few
-// operations per warp instead of one FMA per element.  Relative error of a
-// sum of n squares: about (3 + n) 2^-48.
+// group, two independent chains held as the two lanes of packed registers).
+// Each square is formed exactly as p + pe (the product, and its rounding
+// error from one FMA: exact while |x| lies in [2^-50, 2^50], which the
+// caller checks) and added with Knuth's error-free TwoSum, the errors going
+// to lo.  The products are scalar, non-contractible intrinsics, and the sums
+// packed adds, so no multiply can be fused into an error-free step.
+// renormalize() keeps |lo| within an ulp of hi; the pairs are folded chain
+// to chain, across the warp and into FP64 only at the end of a reduction,
+// so the narrow FP64 pipe sees a few operations per warp instead of one FMA
+// per element.  Relative error of a sum of n squares: about (3 + n) 2^-48.
 struct SquareSum32 {
-  float hi0 = 0.0f, lo0 = 0.0f, hi1 = 0.0f, lo1 = 0.0f;
-  __device__ __forceinline__ static void add(float &hi, float &lo, float x) {
-    const float p = __fmul_rn(x, x);
-    const float pe = __fmaf_rn(x, x, -p);
-    float t, err;
-    two_sum(hi, p, t, err);
-    hi = t;
-    lo = __fadd_rn(lo, __fadd_rn(err, pe));
-  }
+  float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
   __device__ __forceinline__ void add_squares(float a, float b) {
-    add(hi0, lo0, a);
-    add(hi1, lo1, b);
-  }
-  __device__ __forceinline__ static void renorm(float &hi, float &lo) {
-    const float t = __fadd_rn(hi, lo);
-    lo = __fsub_rn(lo, __fsub_rn(t, hi));
+    const float pa = __fmul_rn(a, a), pb = __fmul_rn(b, b);
+    const float2 p = make_float2(pa, pb);
+    const float2 pe = make_float2(__fmaf_rn(a, a, -pa), __fmaf_rn(b, b, -pb));
+    float2 t, err;
+    two_sum2(hi, p, t, err);
     hi = t;
+    lo = __fadd2_rn(lo, __fadd2_rn(err, pe));
   }
   __device__ __forceinline__ void renormalize() {
-    renorm(hi0, lo0);
-    renorm(hi1, lo1);
+    const float2 t = __fadd2_rn(hi, lo);
+    lo = __fadd2_rn(lo, neg2(__fadd2_rn(t, neg2(hi))));
+    hi = t;
   }
   // folds chain 1 into chain 0
   __device__ __forceinline__ void fold_lanes() {
     float t, err;
-    two_sum(hi0, hi1, t, err);
-    hi0 = t;
-    lo0 = __fadd_rn(__fadd_rn(lo0, lo1), err);
-    hi1 = lo1 = 0.0f;
+    two_sum(hi.x, hi.y, t, err);
+    hi.x = t;
+    lo.x = __fadd_rn(__fadd_rn(lo.x, lo.y), err);
+    hi.y = lo.y = 0.0f;
   }
   // adds another sum h + l into chain 0
   __device__ __forceinline__ void add_sum(float h, float l) {
     float t, err;
-    two_sum(hi0, h, t, err);
-    hi0 = t;
-    lo0 = __fadd_rn(lo0, __fadd_rn(l, err));
+    two_sum(hi.x, h, t, err);
+    hi.x = t;
+    lo.x = __fadd_rn(lo.x, __fadd_rn(l, err));
   }
 };
 
@@ -927,15 +932,15 @@ __device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &
   const bool any64 = __syncthreads_or(s != 0.0 || c != 0.0) != 0;
   q.fold_lanes();
   for (int off = 16; off > 0; off >>= 1) {
-    const float h = __shfl_down_sync(0xffffffffu, q.hi0, off);
-    const float l = __shfl_down_sync(0xffffffffu, q.lo0, off);
+    const float h = __shfl_down_sync(0xffffffffu, q.hi.x, off);
+    const float l = __shfl_down_sync(0xffffffffu, q.lo.x, off);
     q.add_sum(h, l);
   }
   if (any64) block_fold<RED_L2>(s, c, s_red, NW);
   __syncthreads();  // s_red may still be read by block_fold
   if (lane == 0) {
-    s_red[2 * wy] = (double)q.hi0;   // the warp's hi + lo as s - c
-    s_red[2 * wy + 1] = -(double)q.lo0;
+    s_red[2 * wy] = (double)q.hi.x;   // the warp's hi + lo as s - c
+    s_red[2 * wy + 1] = -(double)q.lo.x;
   }
   __syncthreads();
   if (tid == 0) {
@@ -953,18 +958,20 @@ __device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &
 // reduction goes to its own partial (per-instance results are folded by
 // batch_finalize_kernel); otherwise the CTA derives its run of (tile, plane)
 // pairs of the single grid and the last CTA folds all partials.
-// Single-grid kernels of small operators (up to 10 terms: the star / heat
+// Single-grid sweeps of small operators (up to 10 terms: the star / heat
 // family) on FP32 grids are bound by memory and latency: they keep four
-// 8-warp CTAs per SM (at most 64 registers per thread).  Larger operators
+// 8-warp CTAs per SM (at most 64 registers per thread).  Reducing sweeps
+// carry the square-sum pairs and spill under that bound, larger operators
 // (the climate operator) are held to fewer CTAs by their shared memory, and
-// BF16 vector lanes (two rows of 8 columns per thread) need more registers.
-template <typename T, bool BATCH, class Op>
+// BF16 vector lanes (two rows of 8 columns per thread) need more registers:
+// those keep the compiler's own register target.
+template <typename T, bool BATCH, int RED, class Op>
 constexpr int min_ctas_per_sm() {
-  return (!BATCH && std::is_same<T, float>::value && Op::kTerms <= 10) ? 4 : 0;
+  return (!BATCH && RED == RED_NONE && std::is_same<T, float>::value && Op::kTerms <= 10) ? 4 : 0;
 }
 
 template <typename T, int VX, int VY, int RED, class Op, bool BATCH>
-__global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, Op>())
+__global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
     sweep_kernel(const __grid_constant__ SweepParams P) {
   using A = typename Arith<T>::A;
   constexpr int XS = Op::kXStep;
@@ -1228,25 +1235,38 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, Op>())
             for (int e = 0; e < VX; ++e)
               if (yok[r] && xok[e]) maxkey = max(maxkey, abs_key(v[e]));
           } else if constexpr (kSq32) {
-            // |v| <= 2^50 (NaN and infinities fail) and the row's largest |v|
-            // at least 2^-50 (or every value 0): the squares are exact in
-            // FP32 pairs; otherwise this row's squares go to the FP64 chain
-            bool small = true;
-            float m = 0.0f;
+            // the row's largest |v| in [2^-50, 2^50] (or every value 0): the
+            // squares are exact in FP32 pairs; otherwise (an infinity, a
+            // value out of that range) this row's squares go to the FP64
+            // chain.  fmaxf passes over NaN, which then propagates through
+            // the pair sums.  A whole group in range takes one max and one
+            // test per row, without per-element masks.
+            if (yok[r] && xok[0] && xok[VX - 1]) {
+              float m = 0.0f;
 #pragma unroll
-            for (int e = 0; e < VX; ++e) {
-              const float a = (yok[r] && xok[e]) ? fabsf(v[e]) : 0.0f;
-              small &= a <= 0x1p50f;
-              m = fmaxf(m, a);
-            }
-            if (small && (m >= 0x1p-50f || m == 0.0f)) {
+              for (int e = 0; e < VX; ++e) m = fmaxf(m, fabsf(v[e]));
+              if (m <= 0x1p50f && (m >= 0x1p-50f || m == 0.0f)) {
 #pragma unroll
-              for (int e = 0; e + 1 < VX; e += 2)
-                sq32.add_squares((yok[r] && xok[e]) ? v[e] : 0.0f, (yok[r] && xok[e + 1]) ? v[e + 1] : 0.0f);
-            } else {
+                for (int e = 0; e + 1 < VX; e += 2) sq32.add_squares(v[e], v[e + 1]);
+              } else {
 #pragma unroll
-              for (int e = 0; e < VX; ++e)
-                if (yok[r] && xok[e]) sq = fma((double)v[e], (double)v[e], sq);
+                for (int e = 0; e < VX; ++e) sq = fma((double)v[e], (double)v[e], sq);
+              }
+            } else if (yok[r]) {
+              float w[VX];
+              float m = 0.0f;
+#pragma unroll
+              for (int e = 0; e < VX; ++e) {
+                w[e] = xok[e] ? v[e] : 0.0f;
+                m = fmaxf(m, fabsf(w[e]));
+              }
+              if (m <= 0x1p50f && (m >= 0x1p-50f || m == 0.0f)) {
+#pragma unroll
+                for (int e = 0; e + 1 < VX; e += 2) sq32.add_squares(w[e], w[e + 1]);
+              } else {
+#pragma unroll
+                for (int e = 0; e < VX; ++e) sq = fma((double)w[e], (double)w[e], sq);
+              }
             }
           } else if constexpr (RED != RED_NONE) {
             double d[VX];
