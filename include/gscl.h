@@ -197,11 +197,16 @@ gscl_status gscl_swap(gscl_grid *a, gscl_grid *b);
  *  - 1 <= n_in <= GSCL_MAX_IN, 1 <= n_out <= GSCL_MAX_OUT,
  *    n_terms <= GSCL_MAX_TERMS (GSCL_ERR_UNSUPPORTED beyond).
  *  - sweeps >= 1.  sweeps > 1 repeats the operator with in[0] and out[0] as
- *    a ping-pong pair (identical layouts, GSCL_ERR_SHAPE otherwise; they
- *    must hold identical halos, which travel with their storage): sweep s
- *    reads the previous sweep's result in place of in[0].  On return out[0]
- *    names the result of the last sweep and in[0] an earlier iterate (the
- *    two handles may have exchanged storage, as by gscl_swap).
+ *    a ping-pong pair (identical layouts, GSCL_ERR_SHAPE otherwise): sweep s
+ *    reads the previous sweep's result in place of in[0], with the halo of
+ *    the grid that result went to, as single sweeps alternate.  On return
+ *    out[0] names the result of the last sweep and in[0] that of the sweep
+ *    before it (the two handles may have exchanged storage, as by
+ *    gscl_swap; halos travel with their storage, so ping-pong grids usually
+ *    carry identical halos).  Sweeps fused per launch (gscl_tune_sweeps)
+ *    give the same results, the storage each handle names included (3D
+ *    grids: when in[0] and out[0] carry identical halos; 2D grids: always);
+ *    the last launch of a call is always a single sweep.
  *  - An empty range enqueues nothing.
  */
 gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
@@ -259,14 +264,18 @@ gscl_status gscl_convert(gscl_grid dst, gscl_grid src, double alpha, int32_t acc
                          void *stream);
 
 /*
- * Autotuner for multi-sweep gscl_do_all: times K = 1 .. 4 sweeps fused per
- * pass over memory (temporal blocking; the paper's wide ghost areas,
- * Section 2, kept on chip) on these grids, trial_sweeps sweeps from in[0]
- * into out[0] per factor (in[0] is left unchanged), and records the fastest
- * for this operator structure, dtype and extent; later multi-sweep calls use
- * it (GSCL_TEMPORAL=K overrides).  Fused passes are bit-identical to single
- * sweeps.  Only the radius-1 7-point star operators with FP32 / BF16 storage
- * over the whole interior fuse; otherwise *best_factor = 1.  Synchronises.
+ * Autotuner for multi-sweep gscl_do_all: times sweeps fused per pass
+ * (temporal blocking; the paper's wide ghost areas, Section 2, kept on chip)
+ * on these grids, passes from in[0] into out[0] (in[0] is left unchanged),
+ * and records the fastest per sweep for this operator structure, dtype and
+ * extent; later multi-sweep calls use it (GSCL_TEMPORAL=K overrides, with
+ * GSCL_TEMPORAL_TILE=0..3 choosing a 2D tile shape).  Fused passes are
+ * bit-identical to single sweeps.  Candidates: the radius-1 7-point star
+ * operators with FP32 / BF16 storage over the whole interior of a 3D grid,
+ * K = 1 .. 4 (trial_sweeps sweeps each); the 2D 5-point operators over the
+ * whole interior of a one-plane grid (any storage, IEEE arithmetic for
+ * FP64), K = 1, 2, 3, 4, 6, 8, 12, 16 over four tile shapes (at least 48
+ * sweeps each).  Otherwise *best_factor = 1.  Synchronises.
  */
 gscl_status gscl_tune_sweeps(const gscl_stencil *op, const gscl_grid *in, int32_t n_in, const gscl_grid *out,
                              int32_t n_out, int32_t trial_sweeps, void *stream, int32_t *best_factor);
@@ -466,10 +475,29 @@ gscl_status gscl_batch_tile(gscl_batch b, int32_t *tile_x, int32_t *tile_y);
  * `sweeps` sweeps of every instance with in[0] / out[0] as the ping-pong
  * pair, exactly as gscl_do_all(..., sweeps) on each instance alone (same
  * point arithmetic, so bit-identical results); on return out[0] names the
- * last result.  use_graph != 0 captures the group's launches once per
- * (sweeps, starting buffer) in a CUDA graph and replays it on `stream`.
+ * last result and in[0] the one before it.  Batches of 2D grids under a
+ * 5-point operator may fuse several sweeps per launch (gscl_batch_tune,
+ * gscl_batch_set_temporal): the last launch stays a single sweep.
+ * use_graph != 0 captures the group's launches once per (sweeps, starting
+ * buffer) in a CUDA graph and replays it on `stream`.
  */
 gscl_status gscl_batch_run(gscl_batch b, int32_t sweeps, int32_t use_graph, void *stream);
+
+/*
+ * Temporal blocking of a batch (the paper's wide ghost areas, Section 2):
+ * sweeps fused per launch (1: none) and its tile (x by y core elements; 0 x
+ * 0 when nothing fuses).  gscl_batch_set_temporal sets them:
+ * sweeps_per_launch in [1, 16], tile_shape in [0, 4) naming 32 x 16,
+ * 32 x 32, 16 x 16 or 64 x 32 tiles (GSCL_ERR_INVALID otherwise).  Only
+ * batches of one-plane (2D) grids under a 5-point operator with one input
+ * and one output fuse (IEEE arithmetic for FP64 grids);
+ * sweeps_per_launch > 1 on another batch returns GSCL_ERR_UNSUPPORTED.
+ * Results are bit-identical to single sweeps.  No counterpart in the
+ * paper's API: its ghost width is a grid property, here it is a launch
+ * choice.
+ */
+gscl_status gscl_batch_temporal(gscl_batch b, int32_t *sweeps_per_launch, int32_t *tile_x, int32_t *tile_y);
+gscl_status gscl_batch_set_temporal(gscl_batch b, int32_t sweeps_per_launch, int32_t tile_shape);
 
 /*
  * Coloured batches: red-black sweeps (Section 3, stateful stencils: the
@@ -515,8 +543,11 @@ gscl_status gscl_batch_reduce(gscl_batch b, int32_t reduce_op, double *results, 
  * (warps per CTA 2/4/8 x prefetched planes 1/2/3, and for FP32 / BF16
  * batches both the default 128-column tiles and 64-column tiles with 4 rows
  * per warp), keeps the shape whose better group was fastest and reports its
- * warps and prefetch (gscl_batch_tile gives the tile).  Synchronises
- * `stream`.
+ * warps and prefetch (gscl_batch_tile gives the tile).  Batches that can
+ * fuse sweeps (gscl_batch_set_temporal) then time 1, 2, 3, 4, 6, 8, 12 and
+ * 16 sweeps per launch over the four fused tile shapes (at least 48 sweeps
+ * each) and keep the fastest per sweep (gscl_batch_temporal reports it).
+ * Synchronises `stream`.
  */
 gscl_status gscl_batch_tune(gscl_batch b, int32_t trial_sweeps, void *stream, int32_t *warps, int32_t *prefetch);
 

@@ -110,6 +110,8 @@ def lib():
         "gscl_do_reduce_program": [u64, i32, P(u64), i32, P(u64), i32, P(RangeC), P(ctypes.c_double), i32, vp,
                                    i64, vp],
         "gscl_batch_tile": [u64, P(i32), P(i32)],
+        "gscl_batch_temporal": [u64, P(i32), P(i32), P(i32)],
+        "gscl_batch_set_temporal": [u64, i32, i32],
         "gscl_set_fp64_arithmetic": [i32],
         "gscl_get_fp64_arithmetic": [],
         "gscl_do_reduce_within": [P(StencilC), P(u64), i32, P(u64), i32, P(RangeC), ctypes.c_double,
@@ -507,6 +509,7 @@ class Batch:
         check(lib().gscl_batch_create(ctypes.byref(self.op.c), len(self.instances), _handles(ins), self.n_in,
                                       _handles(outs), self.n_out, ctypes.byref(h)))
         self.handle = h.value
+        self._k = 1  # sweeps fused per launch (gscl_batch_temporal)
 
     def __del__(self):
         h = getattr(self, "handle", 0)
@@ -519,11 +522,36 @@ class Batch:
         check(lib().gscl_batch_info(self.handle, ctypes.byref(c), ctypes.byref(s), ctypes.byref(sp)))
         return {"ctas": c.value, "segments": s.value, "specialization": sp.value}
 
+    def _launches(self, sweeps):
+        """Launches gscl_batch_run takes for ``sweeps`` sweeps: fused passes
+        while more than K sweeps remain, single sweeps after, and one launch
+        more when that count and ``sweeps`` differ in parity (the library's
+        launch plan keeps them of one parity)."""
+        k, n, done = self._k, 0, 0
+        while done < sweeps:
+            done += k if (k > 1 and sweeps - done > k) else 1
+            n += 1
+        return n + (n - sweeps) % 2
+
     def run(self, sweeps, graph=False, stream=None):
         check(lib().gscl_batch_run(self.handle, int(sweeps), int(bool(graph)), stream_ptr(stream)))
-        if sweeps % 2 == 0:
+        if self._launches(int(sweeps)) % 2 == 0:  # the library exchanged in[0] / out[0] storage
             for ins, outs in self.instances:
                 ins[0].buf, outs[0].buf = outs[0].buf, ins[0].buf
+
+    def temporal(self):
+        """(sweeps per launch, tile_x, tile_y) of the batch (gscl_batch_temporal)."""
+        k, x, y = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(lib().gscl_batch_temporal(self.handle, ctypes.byref(k), ctypes.byref(x), ctypes.byref(y)))
+        self._k = k.value
+        return k.value, x.value, y.value
+
+    def set_temporal(self, sweeps_per_launch, tile_shape=0):
+        """gscl_batch_set_temporal: fuse ``sweeps_per_launch`` sweeps per launch
+        (2D batches under a 5-point operator), tiles of shape ``tile_shape``
+        (0..3: 32 x 16, 32 x 32, 16 x 16, 64 x 32)."""
+        check(lib().gscl_batch_set_temporal(self.handle, int(sweeps_per_launch), int(tile_shape)))
+        self.temporal()
 
     def reduce(self, reduce_op, results, stream=None):
         """Per-instance reduction into ``results`` (float64 CUDA tensor of n_inst)."""
@@ -542,6 +570,7 @@ class Batch:
         w, p = ctypes.c_int32(), ctypes.c_int32()
         check(lib().gscl_batch_tune(self.handle, int(trial_sweeps), stream_ptr(stream), ctypes.byref(w),
                                     ctypes.byref(p)))
+        self.temporal()
         return w.value, p.value
 
 
@@ -565,6 +594,7 @@ class ColoredBatch(Batch):
         check(lib().gscl_batch_create_colored(arr, len(self.instances), _handles(ins), self.n_in, _handles(outs),
                                               self.n_out, ctypes.byref(h)))
         self.handle = h.value
+        self._k = 1
 
     def run_colored(self, color=0, half_sweeps=1, graph=False, stream=None):
         """half_sweeps launches, the colour alternating from ``color``."""

@@ -9,7 +9,9 @@
 // Coloured batches (red-black sweeps, Section 3's stateful stencils) update
 // their instances in place, one colour per launch, and take one operator per
 // instance: the same term structure with the instance's own weights, which
-// the kernel reads from a per-instance weight table.
+// the kernel reads from a per-instance weight table.  Batches of 2D grids
+// under a 5-point operator may fuse K sweeps per launch (tb2d_kernel.cuh):
+// their launches then walk a list of (instance, tile) pairs.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -21,6 +23,7 @@
 #include <vector>
 
 #include "sweep_host.h"
+#include "tb2d_kernel.cuh"
 
 namespace gscl {
 namespace {
@@ -47,6 +50,13 @@ struct Batch {
   int32_t *cta_seg = nullptr, *inst_seg = nullptr;
   double *partials = nullptr;
   InstWeights *wtab = nullptr;  // one weight row per instance
+  // temporal blocking of 2D batches: whether every instance qualifies, the
+  // sweeps fused per launch (1: none), the tile shape and its tile list
+  bool tb_ok = false;
+  int tb_k = 1, tb_tile = 0;
+  int4 *tb_tiles = nullptr;
+  int tb_n = 0, tb_cap = 0;
+  std::vector<int64_t> nx, ny;  // instance extents (tile lists)
   // (first table, sweeps) or, for coloured batches, (2 + first colour, half-sweeps)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   cudaStream_t cap_stream = nullptr;
@@ -70,6 +80,30 @@ void drop_graphs(Batch *bt) {
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// The (instance, x0, y0) list of the 2D tiles of the batch's tile shape,
+// uploaded for fused launches (nothing when the batch does not fuse).
+gscl_status build_tb_tiles(Batch *bt) {
+  bt->tb_n = 0;
+  if (!bt->tb_ok || bt->tb_k < 2) return GSCL_OK;
+  const int TX = tb2d_tile_x(bt->tb_tile), TY = tb2d_tile_y(bt->tb_tile);
+  std::vector<int4> tiles;
+  for (int i = 0; i < bt->n_inst; ++i)
+    for (int64_t y = 0; y < bt->ny[i]; y += TY)
+      for (int64_t x = 0; x < bt->nx[i]; x += TX) tiles.push_back(make_int4(i, (int)x, (int)y, 0));
+  if ((int)tiles.size() > bt->tb_cap) {
+    if (bt->tb_tiles) cudaFree(bt->tb_tiles);
+    bt->tb_tiles = nullptr;
+    bt->tb_cap = 0;
+    cudaError_t e = cudaMalloc(&bt->tb_tiles, sizeof(int4) * tiles.size());
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc of the batch's tile list");
+    bt->tb_cap = (int)tiles.size();
+  }
+  cudaError_t e = cudaMemcpy(bt->tb_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "uploading the batch's tile list");
+  bt->tb_n = (int)tiles.size();
+  return GSCL_OK;
+}
+
 // Plans every instance in both ping-pong directions, builds the work-list
 // for one wave and uploads the tables.
 gscl_status build(Batch *bt) {
@@ -85,6 +119,9 @@ gscl_status build(Batch *bt) {
   bt->buf_a.assign(n, nullptr);
   bt->buf_b.assign(n, nullptr);
   TileCfg cfg = bt->cfg;
+  bool tb_ok = !bt->colored && bt->n_in == 1 && bt->n_out == 1;
+  bt->nx.assign(n, 0);
+  bt->ny.assign(n, 0);
   for (int i = 0; i < n; ++i) {
     Bound b;
     const gscl_stencil *op = bt->colored ? &bt->inst_st[i] : &bt->st;
@@ -122,6 +159,9 @@ gscl_status build(Batch *bt) {
       }
       tabs[dir][i] = pl.P.inst;
       if (dir == 0) {
+        tb_ok = tb_ok && tb2d_eligible(bd, pl.op);
+        bt->nx[i] = bd.in[0].n[0];
+        bt->ny[i] = bd.in[0].n[1];
         work[i] = pl.work;
         nz[i] = pl.P.inst.hi[2] - pl.P.inst.lo[2];
         // this instance's weights in the order of the launch's term table
@@ -203,6 +243,9 @@ gscl_status build(Batch *bt) {
   if (e != cudaSuccess) return cuda_fail(e, "uploading the batch tables");
   bt->G = (int)G;
   bt->S = (int)segs.size();
+  bt->tb_ok = tb_ok;
+  if (!tb_ok) bt->tb_k = 1;
+  if (gscl_status s = build_tb_tiles(bt)) return s;
   base.batch_ctas = (int)G;
   base.P.segs = bt->segs;
   base.P.cta_seg = bt->cta_seg;
@@ -235,11 +278,33 @@ gscl_status current_table(Batch *bt, int *which) {
   return GSCL_OK;
 }
 
-gscl_status enqueue_sweeps(Batch *bt, int first, int sweeps, cudaStream_t stream) {
+// Launches that `sweeps` sweeps take (tb_launch_plan).
+int batch_launches(const Batch *bt, int sweeps) { return (int)tb_launch_plan(sweeps, bt->tb_k).size(); }
+
+// One launch: a fused pass of k sweeps (k > 1) or one sweep, reading table t
+// (halo_swap as in tb2d_kernel.cuh).
+gscl_status enqueue_launch(Batch *bt, int t, int k, cudaStream_t stream, bool halo_swap = false) {
   Plan pl = bt->base;
-  for (int s = 0; s < sweeps; ++s) {
-    pl.P.insts = bt->tab[(first + s) & 1];
-    if (gscl_status st = launch(pl, bt->dtype, RED_NONE, stream, nullptr)) return st;
+  pl.P.insts = bt->tab[t];
+  if (k > 1) {
+    Tb2dArgs a{};
+    a.tiles = bt->tb_tiles;
+    a.n_tiles = bt->tb_n;
+    a.halo_swap = halo_swap ? 1 : 0;
+    a.K = k;
+    a.TX = tb2d_tile_x(bt->tb_tile);
+    a.TY = tb2d_tile_y(bt->tb_tile);
+    return launch_tb2d(pl, bt->dtype, a, stream);
+  }
+  return launch(pl, bt->dtype, RED_NONE, stream, nullptr);
+}
+
+gscl_status enqueue_sweeps(Batch *bt, int first, int sweeps, cudaStream_t stream) {
+  int L = 0, done = 0;
+  for (int k : tb_launch_plan(sweeps, bt->tb_k)) {
+    if (gscl_status st = enqueue_launch(bt, (first + L) & 1, k, stream, ((done - L) & 1) != 0)) return st;
+    done += k;
+    ++L;
   }
   return GSCL_OK;
 }
@@ -400,6 +465,7 @@ gscl_status gscl_batch_destroy(gscl_batch h) {
   drop_graphs(bt.get());
   if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
   if (bt->dev) cudaFree(bt->dev);
+  if (bt->tb_tiles) cudaFree(bt->tb_tiles);
   return GSCL_OK;
 }
 
@@ -422,6 +488,34 @@ gscl_status gscl_batch_tile(gscl_batch h, int32_t *tile_x, int32_t *tile_y) {
   return GSCL_OK;
 }
 
+gscl_status gscl_batch_temporal(gscl_batch h, int32_t *sweeps_per_launch, int32_t *tile_x, int32_t *tile_y) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  std::lock_guard<std::mutex> lk(bt->mu);
+  if (sweeps_per_launch) *sweeps_per_launch = bt->tb_k;
+  if (tile_x) *tile_x = bt->tb_k > 1 ? tb2d_tile_x(bt->tb_tile) : 0;
+  if (tile_y) *tile_y = bt->tb_k > 1 ? tb2d_tile_y(bt->tb_tile) : 0;
+  return GSCL_OK;
+}
+
+gscl_status gscl_batch_set_temporal(gscl_batch h, int32_t sweeps_per_launch, int32_t tile_shape) {
+  Batch *bt = find_batch(h);
+  if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
+  if (sweeps_per_launch < 1 || sweeps_per_launch > kTb2dMaxK)
+    return fail(GSCL_ERR_INVALID, "sweeps_per_launch = %d outside [1, %d]", sweeps_per_launch, kTb2dMaxK);
+  if (tile_shape < 0 || tile_shape >= kTb2dShapes)
+    return fail(GSCL_ERR_INVALID, "tile_shape = %d outside [0, %d)", tile_shape, kTb2dShapes);
+  std::lock_guard<std::mutex> lk(bt->mu);
+  int first = 0;
+  if (gscl_status s = current_table(bt, &first)) return s;
+  if (sweeps_per_launch > 1 && !bt->tb_ok)
+    return fail(GSCL_ERR_UNSUPPORTED, "only batches of 2D grids under a 5-point operator fuse sweeps");
+  drop_graphs(bt);
+  bt->tb_k = sweeps_per_launch;
+  bt->tb_tile = tile_shape;
+  return build_tb_tiles(bt);
+}
+
 gscl_status gscl_batch_run(gscl_batch h, int32_t sweeps, int32_t use_graph, void *stream) {
   Batch *bt = find_batch(h);
   if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
@@ -434,7 +528,7 @@ gscl_status gscl_batch_run(gscl_batch h, int32_t sweeps, int32_t use_graph, void
   if (gscl_status s = run_group(bt, std::make_pair(first, (int)sweeps), use_graph != 0, (cudaStream_t)stream,
                                 [&](cudaStream_t st) { return enqueue_sweeps(bt, first, sweeps, st); }))
     return s;
-  if (sweeps % 2 == 0)  // out[0] names the last sweep's result, as in gscl_do_all
+  if (batch_launches(bt, sweeps) % 2 == 0)  // out[0] names the last launch's result, as in gscl_do_all
     for (int i = 0; i < bt->n_inst; ++i)
       if (gscl_status s = swap_storage(bt->in_h[(size_t)i * bt->n_in], bt->out_h[(size_t)i * bt->n_out])) return s;
   return GSCL_OK;
@@ -530,10 +624,63 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
         best = bt->cfg;
       }
     }
+  bt->cfg = best;
+  const int keep_k = bt->tb_k, keep_tile = bt->tb_tile;
+  bt->tb_k = 1;
+  if (gscl_status s = build(bt)) {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return s;
+  }
+  // 2D batches: sweeps fused per launch (K = 1, 2, 3, 4, 6, 8, 12, 16) x the
+  // tile shapes, on the tuned single-sweep tiles; at least 48 sweeps per
+  // candidate (a fused launch of a small 2D batch takes microseconds)
+  if (bt->tb_ok && red == RED_NONE) {
+    int first = 0;
+    float best_sweep = 1e30f;
+    int best_k = 1, best_tile = 0;
+    const int trial = std::max((int)trial_sweeps, 48);
+    if (current_table(bt, &first) == GSCL_OK) {
+      for (int K : {1, 2, 3, 4, 6, 8, 12, 16})
+        for (int t = 0; t < (K == 1 ? 1 : kTb2dShapes); ++t) {
+          bt->tb_k = K;
+          bt->tb_tile = t;
+          if (build_tb_tiles(bt) != GSCL_OK) continue;
+          if (enqueue_launch(bt, first, K, st) != GSCL_OK) continue;  // warm-up (kernel set-up)
+          const int passes = std::max(1, trial / K);
+          float ms = 1e30f;
+          bool timed = true;
+          for (int rep = 0; rep < 2 && timed; ++rep) {
+            cudaEventRecord(e0, st);
+            for (int p = 0; p < passes; ++p) enqueue_launch(bt, first, K, st);
+            cudaEventRecord(e1, st);
+            timed = cudaEventSynchronize(e1) == cudaSuccess;
+            float tm = 0.f;
+            if (timed) cudaEventElapsedTime(&tm, e0, e1);
+            ms = std::min(ms, tm);
+          }
+          if (!timed) break;
+          const float per_sweep = ms / (passes * K);
+          if (log)
+            fprintf(stderr, "gscl_batch_tune: %d sweeps per launch, tile %d x %d: %.5f ms per sweep\n", K,
+                    tb2d_tile_x(t), tb2d_tile_y(t), per_sweep);
+          if (per_sweep < best_sweep) {
+            best_sweep = per_sweep;
+            best_k = K;
+            best_tile = t;
+          }
+        }
+    }
+    bt->tb_k = best_k;
+    bt->tb_tile = best_tile;
+  } else {
+    bt->tb_k = bt->tb_ok ? keep_k : 1;
+    bt->tb_tile = keep_tile;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  bt->cfg = best;
-  if (gscl_status s = build(bt)) return s;
+  drop_graphs(bt);
+  if (gscl_status s = build_tb_tiles(bt)) return s;
   if (warps) *warps = best.nw;
   if (prefetch) *prefetch = best.pf;
   cudaError_t e = cudaGetLastError();

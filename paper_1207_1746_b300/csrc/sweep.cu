@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "sweep_host.h"
+#include "tb2d_kernel.cuh"
 
 namespace gscl {
 
@@ -455,29 +456,37 @@ gscl_status gscl_do_all(const gscl_stencil *op, const gscl_grid *in, int32_t n_i
     if (overlaps(a, c)) return fail(GSCL_ERR_ALIAS, "multi-sweep ping-pong needs distinct in[0] and out[0]");
   }
   Grid src = b.in[0], dst = b.out[0];
-  int K = 1;
+  TbChoice tc;
+  int sop = OP_GENERIC;
   if (sweeps > 1) {
     std::vector<gscl_term> terms(op->terms, op->terms + op->n_terms);
     std::vector<int> perm;
-    K = tb_factor(b, match_static(terms, n_in, n_out, &perm), sweeps);
+    sop = match_static(terms, n_in, n_out, &perm);
+    tc = tb_choice(b, sop, sweeps);
   }
-  int launches = 0;
-  for (int done = 0; done < sweeps; ++launches) {
+  // fused passes of up to K sweeps (bit-identical to K single sweeps), the
+  // last launch a single sweep and the launch count of the parity of the
+  // sweep count (tb_launch_plan), so both handles end as after single sweeps
+  const std::vector<int> plan = tb_launch_plan(sweeps, tc.K);
+  int launches = 0, done = 0;
+  for (int k : plan) {
     b.in[0] = src;
     b.out[0] = dst;
     for (size_t a = 1; a < b.in.size(); ++a)  // another input naming the ping-pong grid follows it
       if (b.in_h[a] == b.in_h[0]) b.in[a] = src;
     Plan pl;
-    if (K > 1 && sweeps - done >= K) {
-      // K sweeps in one pass over HBM, bit-identical to K single sweeps
-      if (gscl_status st = make_tb_plan(b, K, &pl)) return st;
-      if (gscl_status st = launch_tb(pl, b.in[0].dtype, K, (cudaStream_t)stream)) return st;
-      done += K;
+    if (k > 1) {
+      TbChoice c = tc;
+      c.K = k;
+      // the input iterate `done` sits in the other grid than single sweeps put it in
+      const bool halo_swap = ((done - launches) & 1) != 0;
+      if (gscl_status st = run_tb_pass(b, sop, c, halo_swap, (cudaStream_t)stream)) return st;
     } else {
       if (gscl_status st = make_plan(b, false, &pl, TileCfg{})) return st;
       if (gscl_status st = launch(pl, b.in[0].dtype, RED_NONE, (cudaStream_t)stream, nullptr)) return st;
-      done += 1;
     }
+    done += k;
+    ++launches;
     std::swap(src, dst);
   }
   // an even number of launches leaves the result in in[0]'s storage: exchange

@@ -53,11 +53,20 @@ gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int 
 // Current arithmetic of FP64 grids (GSCL_FP64_IEEE or GSCL_FP64_PAIR); make_plan records it in the plan.
 int fp64_arith();
 
-// Temporal blocking: sweeps fused per pass for a call (1 = none), the pass
-// plan and its launch (tb.cu).
-int tb_factor(const Bound &b, int op, int sweeps);
+// Temporal blocking (tb.cu): sweeps fused per pass for a call (K = 1: none)
+// and, on 2D grids, the tile shape; one pass from in[0] into out[0]; the
+// plan and launch of the 3D kernels; the 2D kernel's launch; the tuner.
+struct TbChoice {
+  int K = 1;
+  int tile = 0;  // 2D grids: index of the tile shape (tb2d_kernel.cuh)
+};
+bool tb2d_eligible(const Bound &b, int op);
+TbChoice tb_choice(const Bound &b, int op, int sweeps);
+gscl_status run_tb_pass(const Bound &b, int op, TbChoice c, bool halo_swap, cudaStream_t stream);
 gscl_status make_tb_plan(const Bound &b, int K, Plan *pl);
 gscl_status launch_tb(const Plan &pl, int dtype, int K, cudaStream_t stream);
+struct Tb2dArgs;
+gscl_status launch_tb2d(const Plan &pl, int dtype, const Tb2dArgs &a, cudaStream_t stream);
 gscl_status tune_sweeps(const Bound &b, int op, int trial_sweeps, cudaStream_t st, int *best_out);
 
 }  // namespace gscl

@@ -347,7 +347,9 @@ def test_temporal_blocking_bitexact_with_oracle_on_integer_data(monkeypatch, whi
     storage, integer data (|u|, |f| <= 64) and lambda = 1/8: after s sweeps
     every value and every partial sum is a multiple of 2^-3s below 2^7, which
     FP32 holds exactly for s <= 4, so the GPU's blocked sweeps and the
-    oracle's one-at-a-time FP64 sweeps must agree bit for bit."""
+    oracle's one-at-a-time FP64 sweeps must agree bit for bit.  K + 1 sweeps
+    run (the last launch of a run is a single sweep), so the fused pass's
+    result u_K is the one in[0] names on return."""
     mk, lam, rhs = TEMPORAL_OPS[which]
     rng = np.random.default_rng(70 + n[0])
     u0 = int_field(rng, I.padded_shape(n, hu), 64)
@@ -356,8 +358,8 @@ def test_temporal_blocking_bitexact_with_oracle_on_integer_data(monkeypatch, whi
         monkeypatch.setenv("GSCL_TEMPORAL", str(K))
         a, b = B.Grid(n, hu, "f32").upload(u0), B.Grid(n, hu, "f32").upload(u0)
         ins = [a] + ([B.Grid(n, (0, 0, 0), "f32").upload(f)] if rhs else [])
-        B.do_all(mk(), ins, [b], sweeps=K)
-        got = b.download().double().numpy()
+        B.do_all(mk(), ins, [b], sweeps=K + 1)
+        got = a.download().double().numpy()
         want, _ = D.heat_run(O.Grid(u0.copy(), hu), O.Grid(f.copy(), (0, 0, 0)) if rhs else None, lam, K)
         assert np.array_equal(got, want.a), (K, float(np.max(np.abs(got - want.a))))
 
