@@ -54,5 +54,6 @@ gscl_status encode_tensor_map_3d(CUtensorMap *map, const Grid &g, uint32_t box_x
 
 int sm_count();
 int max_smem_per_block();
+int smem_per_sm();  // shared memory of one SM (all resident CTAs together)
 
 }  // namespace gscl

@@ -142,6 +142,13 @@ int max_smem_per_block() {
   return v;
 }
 
+int smem_per_sm() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  return v;
+}
+
 // One int per device: bit 0 = a bounded wait timed out, bit 1 = a run-time
 // compiled operator read outside its declared reach.  A __device__
 // variable exists once per device and is zero when the module loads.  Host

@@ -139,6 +139,19 @@ constexpr uint32_t centre_mask() {
   return m;
 }
 
+// IEEE FP64 sweeps are bound by the FP64 pipe: there the centre ring's extra
+// wait per step costs more than the shared memory it frees gains for an
+// operator with one centre-only input (the heat family's RHS), but an
+// operator with many (the climate operator's coefficients and tendencies)
+// frees enough for a second resident CTA.
+constexpr int kCentreFp64Min = 4;
+template <class Def>
+constexpr int centre_count() {
+  int n = 0;
+  for (int a = 0; a < Def::NIN; ++a) n += centre_only<Def>(a) ? 1 : 0;
+  return n;
+}
+
 template <class Op>
 constexpr bool op_has_value() {
   for (int i = 0; i < Op::NT; ++i)

@@ -232,9 +232,13 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   // FP64 grids: the arithmetic is fixed here, with the plan
   pl->pair = g0.dtype == GSCL_F64 && fp64_arith() == GSCL_FP64_PAIR;
   // inputs read only at the core element go to the two-slot centre ring
-  // (all but IEEE FP64; the kernel's operator tables make the same choice)
-  // (the colour-compacted kernel reads every input from the plane ring)
-  const uint32_t cmask = (compact || (g0.dtype == GSCL_F64 && !pl->pair)) ? 0u : static_centre_mask(pl->op);
+  // (IEEE FP64: only for operators with kCentreFp64Min or more such inputs;
+  // the kernel's operator tables make the same choice; the colour-compacted
+  // kernel reads every input from the plane ring)
+  const uint32_t smask = static_centre_mask(pl->op);
+  const bool ieee64 = g0.dtype == GSCL_F64 && !pl->pair;
+  const uint32_t cmask =
+      (compact || (ieee64 && __builtin_popcount(smask) < kCentreFp64Min)) ? 0u : smask;
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
   // warps per CTA (each warp owns VY rows of the tile) and planes prefetched
   const int VY = narrow ? 4 : vy_for(g0.dtype);
@@ -258,7 +262,20 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
       ring += (size_t)(centre(a) ? 2 : R) * SEa[a] * elem;
     }
     smem = kBarBytes + ring;
-    if (smem <= (size_t)smem_cap && R <= kMaxRing) break;
+    if (smem <= (size_t)smem_cap && R <= kMaxRing) {
+      // IEEE FP64 sweeps (bound by the FP64 pipe's latency at low occupancy):
+      // give up the prefetched plane when that lets a second CTA reside
+      if (ieee64 && PF > 0 && !getenv("GSCL_PREFETCH") && cfg.pf <= 0) {
+        const size_t per_sm = (size_t)smem_per_sm(), reserve = 1024;
+        size_t fewer = kBarBytes;
+        for (int a = 0; a < n_in; ++a) fewer += (size_t)(centre(a) ? 2 : R - 1) * SEa[a] * elem;
+        if (per_sm / (smem + reserve) < 2 && per_sm / (fewer + reserve) >= 2) {
+          --PF;
+          continue;
+        }
+      }
+      break;
+    }
     if (PF > 1) --PF;
     else if (NW > 1) NW /= 2;
     else return fail(GSCL_ERR_UNSUPPORTED, "operator needs %zu bytes of shared memory per CTA", smem);

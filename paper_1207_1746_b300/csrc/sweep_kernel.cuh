@@ -515,12 +515,13 @@ struct StaticOp {
   __host__ __device__ static constexpr bool run_first(int i) { return i == 0 || !same_run(i - 1, i); }
   __host__ __device__ static constexpr bool run_last(int i) { return i == Def::NT - 1 || !same_run(i, i + 1); }
 
-  // Centre ring for every storage but IEEE FP64: those sweeps are bound by
-  // the FP64 pipe, and the ring's extra wait per step costs them more than
-  // the shared memory it frees gains (the host planner makes the same choice).
+  // Centre ring for every storage, and for IEEE FP64 only for operators with
+  // kCentreFp64Min or more centre-only inputs (static_ops.h; the host planner
+  // makes the same choice).
   template <typename T>
   __host__ __device__ static constexpr bool in_centre_ring(int in) {
-    return XS == 1 && !std::is_same<T, double>::value && centre_only<Def>(in);
+    return XS == 1 && (!std::is_same<T, double>::value || centre_count<Def>() >= kCentreFp64Min) &&
+           centre_only<Def>(in);
   }
 
   // element (row, lane) of centre-ring input `in` in slot cslot

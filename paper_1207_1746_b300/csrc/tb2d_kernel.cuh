@@ -48,7 +48,7 @@ constexpr int kTb2dShapes = 4;
 __host__ __device__ constexpr int tb2d_tile_x(int i) { return i == 0 ? 32 : i == 1 ? 32 : i == 2 ? 16 : 64; }
 __host__ __device__ constexpr int tb2d_tile_y(int i) { return i == 0 ? 16 : i == 1 ? 32 : i == 2 ? 16 : 32; }
 constexpr int kTb2dMaxK = 16;
-constexpr int kTb2dThreads = 512;  // 16 warps: rows 2 (w + 16 r) and 2 (w + 16 r) + 1
+constexpr int kTb2dThreads = 512;  // 16 warps
 
 template <typename T>
 __host__ __device__ constexpr size_t tb2d_smem_bytes(int K, int TX, int TY) {
@@ -166,24 +166,27 @@ __global__ void __launch_bounds__(kTb2dThreads) tb2d_kernel(const __grid_constan
     for (int s = 1; s <= K; ++s) {
       const T *cur = (s & 1) ? buf0 : buf1;
       T *nxt = (s & 1) ? buf1 : buf0;
-      // warp wy takes the row pairs (fy, fy + 1), fy = s + 2 (wy + NWARP r):
-      // two independent FMA chains per column
-      for (int fy = s + 2 * wy; fy < FH - s; fy += 2 * NWARP) {
-        const int64_t Y = y0 - K + fy;
-        const bool row0 = Y >= 0 && Y < ny;
-        const bool row1 = fy + 1 < FH - s && Y + 1 >= 0 && Y + 1 < ny;
-        for (int fx = s + lane; fx < FW - s; fx += 32) {
-          const int64_t X = x0 - K + fx;
-          if (X < 0 || X >= nx) continue;
-          const A v0 = tb2d_point<T, Def>(cur, FW, fy, fx, w);
-          const A v1 = tb2d_point<T, Def>(cur, FW, row1 ? fy + 1 : fy, fx, w);
-          if (s < K) {
-            if (row0) nxt[fy * FW + fx] = from_arith<T>(v0);
-            if (row1) nxt[(fy + 1) * FW + fx] = from_arith<T>(v1);
-          } else {  // stage K covers exactly the tile
-            if (row0) dst[Y * dp + X] = from_arith<T>(v0);
-            if (row1) dst[(Y + 1) * dp + X] = from_arith<T>(v1);
-          }
+      // the stage's region (the tile grown by K - s cells), its points dealt
+      // to the threads in order, two per thread per round (two independent
+      // FMA chains): no lane idles on rows narrower than a warp, which
+      // matters since the FP64 pipe binds
+      const int rw = FW - 2 * s, rn = rw * (FH - 2 * s);
+      for (int i0 = tid; i0 < rn; i0 += 2 * kTb2dThreads) {
+        const int i1 = i0 + kTb2dThreads;
+        const int fy0 = s + i0 / rw, fx0 = s + i0 % rw;
+        const int fy1 = i1 < rn ? s + i1 / rw : fy0, fx1 = i1 < rn ? s + i1 % rw : fx0;
+        const int64_t Y0 = y0 - K + fy0, X0 = x0 - K + fx0, Y1 = y0 - K + fy1, X1 = x0 - K + fx1;
+        const bool in0 = X0 >= 0 && X0 < nx && Y0 >= 0 && Y0 < ny;
+        const bool in1 = i1 < rn && X1 >= 0 && X1 < nx && Y1 >= 0 && Y1 < ny;
+        if (!in0 && !in1) continue;
+        const A v0 = tb2d_point<T, Def>(cur, FW, fy0, fx0, w);
+        const A v1 = tb2d_point<T, Def>(cur, FW, fy1, fx1, w);
+        if (s < K) {
+          if (in0) nxt[fy0 * FW + fx0] = from_arith<T>(v0);
+          if (in1) nxt[fy1 * FW + fx1] = from_arith<T>(v1);
+        } else {  // stage K covers exactly the tile
+          if (in0) dst[Y0 * dp + X0] = from_arith<T>(v0);
+          if (in1) dst[Y1 * dp + X1] = from_arith<T>(v1);
         }
       }
       __syncthreads();
