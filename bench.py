@@ -398,7 +398,7 @@ def run_e2e(dtype, steps, warmup, n=N_SIDE, sweeps=SWEEPS):
 
 
 # ------------------------------------------------------------------ batched workload
-def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
+def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True, fixed_temporal=None):
     """96 independent 3D 7-point heat instances (sides uniform on 32..224 per
     axis, FP32 storage, zero 1-cell halo, lam = 1/8), `sweeps` sweeps of all
     of them per step: one launch per sweep from the batch's work-list, the
@@ -419,8 +419,11 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
     op = B.Stencil(S.heat7(LAM, with_f=False))
     batch = B.Batch(op, insts)
     cfg = batch.tune(trial_sweeps=10) if tune else None
+    if fixed_temporal:  # profiling runs: a given number of sweeps per launch instead of the tuner's
+        batch.set_temporal(fixed_temporal)
     info = batch.info()
     tile = batch.tile()
+    temporal = batch.temporal()  # sweeps per launch the tuner kept (1 or 2 for 3D batches)
     points = sum(a * b * c for a, b, c in sides)
     stream = torch.cuda.current_stream()
 
@@ -440,12 +443,20 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
     if not compare:  # profiling run: the graph replay only
         B.sync()
         return {"points": points, "ms_per_step": ms_batch, "value": sweeps * points / (ms_batch * 1e-3) / 1e9,
-                "sweep_ms": ms_batch / sweeps, "hbm_gbs": 8 * points / (ms_batch / sweeps * 1e-3) / 1e9,
+                "sweep_ms": ms_batch / sweeps, "launch_ms": ms_batch / sweeps * temporal[0],
+                "hbm_gbs": 8 * points / (ms_batch / sweeps * 1e-3) / 1e9,
                 "per_instance_loop_ms": float("nan"), "speedup_vs_loop": float("nan"), "tuned": cfg, "info": info,
-                "tile": tile,
+                "tile": tile, "temporal": temporal, "launches": batch._launches(sweeps),
                 "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
-    # one sweep of the batch alone (no graph) for the roofline
+    # the roofline's kernel: one sweep of the batch alone (no graph), or, when
+    # the tuner fuses k sweeps per launch, one such pass: run(2k + 1) is two
+    # passes and a single sweep (the last launch of a run is single)
     ms_sweep = timed(lambda: batch.run(1), 5 * steps, 2)
+    k = temporal[0]
+    ms_launch = ms_sweep
+    if k > 1:
+        ms_two_passes = timed(lambda: batch.run(2 * k + 1), 5 * steps, 2)
+        ms_launch = max(1e-6, (ms_two_passes - ms_sweep) / 2)
 
     def per_instance():
         for ins, outs in insts:
@@ -453,11 +464,11 @@ def run_batched(steps, warmup, count=96, sweeps=100, tune=True, compare=True):
 
     ms_loop = timed(per_instance, max(1, steps // 2), 1)
     B.sync()
-    nbytes = 8 * points  # FP32: u read, u' written
+    nbytes = 8 * points * k  # FP32: u read, u' written, per point-update; k updates per launch
     return {"points": points, "ms_per_step": ms_batch, "value": sweeps * points / (ms_batch * 1e-3) / 1e9,
-            "sweep_ms": ms_sweep, "hbm_gbs": nbytes / (ms_sweep * 1e-3) / 1e9,
+            "sweep_ms": ms_sweep, "launch_ms": ms_launch, "hbm_gbs": nbytes / (ms_launch * 1e-3) / 1e9,
             "per_instance_loop_ms": ms_loop, "speedup_vs_loop": ms_loop / ms_batch, "tuned": cfg, "info": info,
-            "tile": tile,
+            "tile": tile, "temporal": temporal, "launches": batch._launches(sweeps),
             "sides_min_max": [min(min(s) for s in sides), max(max(s) for s in sides)]}
 
 
@@ -1067,6 +1078,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--batch-temporal", type=int, default=None,
+                    help="batched workload: sweeps per launch to use instead of the tuner's (profiling runs)")
     ap.add_argument("--profile", action="store_true",
                     help="one short step for profilers: no warm-up, tuner, comparison runs, e2e, CPU leg or "
                          "FMA microbenchmark (the printed numbers are not benchmark values)")
@@ -1374,23 +1387,29 @@ def main():
             print(json.dumps(line))
         return
     if args.workload == "batched":
-        r = run_batched(args.steps, args.warmup, tune=not args.profile, compare=not args.profile)
+        r = run_batched(args.steps, args.warmup, tune=not args.profile, compare=not args.profile,
+                        fixed_temporal=args.batch_temporal)
         t = dist.max(r["ms_per_step"])
         line = {"metric": "GPoint-updates/s", "value": round(dist.world * 100 * r["points"] / (t * 1e-3) / 1e9, 3),
                 "unit": "GPoint-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(t, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": "batched heat3d: 96 instances, sides U{32..224} per axis (seed 4040), "
-                                       "FP32, zero halo, lam=1/8, 100 sweeps per step, one launch per sweep, "
-                                       "CUDA graph", "points": r["points"], "sides": r["sides_min_max"],
+                                       "FP32, zero halo, lam=1/8, 100 sweeps per step, the tuner's sweeps per "
+                                       "launch (1, or 2 in two-sweep passes), CUDA graph",
+                           "points": r["points"], "sides": r["sides_min_max"],
                            "l2": "working set 2 x %.2f GB > L2" % (4 * r["points"] / 1e9)},
                 "roofline": {"bound": "hbm", "achieved": round(r["hbm_gbs"], 1), "peak": peaks.get("hbm_gbs", 6400.0),
                              "unit": "GB/s", "frac": round(r["hbm_gbs"] / peaks.get("hbm_gbs", 6400.0), 4),
-                             "traffic": profile_traffic("batched_sweep")},
+                             "traffic": profile_traffic("batched_sweep" if r["temporal"][0] == 1 else
+                                                        f"batched_pass{r['temporal'][0]}"),
+                             "note": "algorithmic bytes: 8 B per point-update, the updates of one launch "
+                                     f"({r['temporal'][0]} sweep(s)) over its duration ({r['launch_ms']:.4f} ms)"},
                 "per_instance_loop_ms": round(r["per_instance_loop_ms"], 3),
                 "speedup_vs_per_instance_loop": round(r["speedup_vs_loop"], 3),
                 "tuned_warps_prefetch": r["tuned"], "tile": r["tile"], "batch": r["info"],
-                "gpu_launches": args.steps * 100}
+                "tuned_sweeps_per_launch": r["temporal"][0], "single_sweep_ms": round(r["sweep_ms"], 4),
+                "gpu_launches": args.steps * r["launches"]}
         if dist.rank == 0:
             print(json.dumps(line))
         return

@@ -488,11 +488,14 @@ gscl_status gscl_batch_run(gscl_batch b, int32_t sweeps, int32_t use_graph, void
  * sweeps fused per launch (1: none) and its tile (x by y core elements; 0 x
  * 0 when nothing fuses).  gscl_batch_set_temporal sets them:
  * sweeps_per_launch in [1, 16], tile_shape in [0, 4) naming 32 x 16,
- * 32 x 32, 16 x 16 or 64 x 32 tiles (GSCL_ERR_INVALID otherwise).  Only
- * batches of one-plane (2D) grids under a 5-point operator with one input
- * and one output fuse (IEEE arithmetic for FP64 grids);
- * sweeps_per_launch > 1 on another batch returns GSCL_ERR_UNSUPPORTED.
- * Results are bit-identical to single sweeps.  No counterpart in the
+ * 32 x 32, 16 x 16 or 64 x 32 tiles (GSCL_ERR_INVALID otherwise).  Batches
+ * of one-plane (2D) grids under a 5-point operator with one input and one
+ * output fuse up to 16 sweeps (IEEE arithmetic for FP64 grids); batches of
+ * 3D FP32 / BF16 grids under a radius-1 7-point star operator fuse two
+ * (128 x 14 tiles, tile_shape ignored; in[0] and out[0] of each instance
+ * must carry identical halos, as for gscl_do_all's fused passes).  Other
+ * requests return GSCL_ERR_UNSUPPORTED.  Results are bit-identical to
+ * single sweeps.  No counterpart in the
  * paper's API: its ghost width is a grid property, here it is a launch
  * choice.
  */
@@ -544,9 +547,10 @@ gscl_status gscl_batch_reduce(gscl_batch b, int32_t reduce_op, double *results, 
  * batches both the default 128-column tiles and 64-column tiles with 4 rows
  * per warp), keeps the shape whose better group was fastest and reports its
  * warps and prefetch (gscl_batch_tile gives the tile).  Batches that can
- * fuse sweeps (gscl_batch_set_temporal) then time 1, 2, 3, 4, 6, 8, 12 and
- * 16 sweeps per launch over the four fused tile shapes (at least 48 sweeps
- * each) and keep the fastest per sweep (gscl_batch_temporal reports it).
+ * fuse sweeps (gscl_batch_set_temporal) then time the factors (2D: 1, 2, 3,
+ * 4, 6, 8, 12 and 16 sweeps per launch over the four fused tile shapes, at
+ * least 48 sweeps each; 3D: 1 and 2, trial_sweeps sweeps each) and keep the
+ * fastest per sweep (gscl_batch_temporal reports it).
  * Synchronises `stream`.
  */
 gscl_status gscl_batch_tune(gscl_batch b, int32_t trial_sweeps, void *stream, int32_t *warps, int32_t *prefetch);

@@ -548,8 +548,9 @@ class Batch:
 
     def set_temporal(self, sweeps_per_launch, tile_shape=0):
         """gscl_batch_set_temporal: fuse ``sweeps_per_launch`` sweeps per launch
-        (2D batches under a 5-point operator), tiles of shape ``tile_shape``
-        (0..3: 32 x 16, 32 x 32, 16 x 16, 64 x 32)."""
+        (2D batches under a 5-point operator: up to 16, tiles of shape
+        ``tile_shape``, 0..3: 32 x 16, 32 x 32, 16 x 16, 64 x 32; 3D FP32 /
+        BF16 batches under a 7-point star operator: 2)."""
         check(lib().gscl_batch_set_temporal(self.handle, int(sweeps_per_launch), int(tile_shape)))
         self.temporal()
 

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "sweep_host.h"
+#include "tb2_kernel.cuh"
 #include "tb2d_kernel.cuh"
 
 namespace gscl {
@@ -57,6 +58,17 @@ struct Batch {
   int4 *tb_tiles = nullptr;
   int tb_n = 0, tb_cap = 0;
   std::vector<int64_t> nx, ny;  // instance extents (tile lists)
+  // 3D batches of the radius-1 star operators (FP32 / BF16): two-sweep
+  // passes (tb2_kernel.cuh) from their own descriptor tables (the pass's
+  // boxes) and work-list
+  bool tb3_ok = false;
+  Plan tb3_base;
+  char *tb3_dev = nullptr;
+  size_t tb3_bytes = 0;
+  InstDesc *tb3_tab[2] = {nullptr, nullptr};
+  Segment *tb3_segs = nullptr;
+  int32_t *tb3_cta = nullptr;
+  int tb3_G = 0;
   // (first table, sweeps) or, for coloured batches, (2 + first colour, half-sweeps)
   std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
   cudaStream_t cap_stream = nullptr;
@@ -104,6 +116,40 @@ gscl_status build_tb_tiles(Batch *bt) {
   return GSCL_OK;
 }
 
+// Work-list for one wave of G CTAs over instances of work[i] (tile, plane)
+// pairs each (nz[i] planes per tile column): run b = [W b / G, W (b+1) / G)
+// split at instance and column ends.
+void make_worklist(const std::vector<long long> &work, const std::vector<int64_t> &nz, long long G,
+                   std::vector<Segment> *segs, std::vector<int32_t> *cta_seg, std::vector<int32_t> *inst_seg) {
+  const int n = (int)work.size();
+  long long W = 0;
+  for (long long w : work) W += w;
+  segs->clear();
+  cta_seg->assign(G + 1, 0);
+  inst_seg->assign(n + 1, -1);
+  int inst = 0;
+  long long inst_start = 0;
+  for (long long b = 0; b < G; ++b) {
+    (*cta_seg)[b] = (int32_t)segs->size();
+    long long pos = W * b / G;
+    const long long end = W * (b + 1) / G;
+    while (pos < end) {
+      while (pos >= inst_start + work[inst]) inst_start += work[inst++];
+      if ((*inst_seg)[inst] < 0) (*inst_seg)[inst] = (int32_t)segs->size();
+      const long long local = pos - inst_start;
+      const long long col = local / nz[inst];
+      const long long zoff = local - col * nz[inst];
+      const long long len = std::min(end - pos, nz[inst] - zoff);
+      segs->push_back(Segment{inst, (int32_t)col, (int32_t)zoff, (int32_t)len});
+      pos += len;
+    }
+  }
+  (*cta_seg)[G] = (int32_t)segs->size();
+  (*inst_seg)[n] = (int32_t)segs->size();
+  for (int i = n - 1; i >= 0; --i)
+    if ((*inst_seg)[i] < 0) (*inst_seg)[i] = (*inst_seg)[i + 1];
+}
+
 // Plans every instance in both ping-pong directions, builds the work-list
 // for one wave and uploads the tables.
 gscl_status build(Batch *bt) {
@@ -120,6 +166,11 @@ gscl_status build(Batch *bt) {
   bt->buf_b.assign(n, nullptr);
   TileCfg cfg = bt->cfg;
   bool tb_ok = !bt->colored && bt->n_in == 1 && bt->n_out == 1;
+  bool tb3_ok = !bt->colored && bt->n_out == 1;
+  std::vector<InstDesc> tabs3[2];
+  tabs3[0].resize(n);
+  tabs3[1].resize(n);
+  std::vector<long long> work3(n);
   bt->nx.assign(n, 0);
   bt->ny.assign(n, 0);
   for (int i = 0; i < n; ++i) {
@@ -158,6 +209,18 @@ gscl_status build(Batch *bt) {
         return fail(GSCL_ERR_SHAPE, "instance %d plans a different tile shape", i);
       }
       tabs[dir][i] = pl.P.inst;
+      // 3D two-sweep passes: the pass's own boxes and tiles
+      tb3_ok = tb3_ok && pl.op != OP_GENERIC && tb_eligible(bd, pl.op) && !tb2d_eligible(bd, pl.op);
+      if (tb3_ok) {
+        Plan tp;
+        if (make_tb_plan(bd, 2, &tp) != GSCL_OK) {
+          tb3_ok = false;
+        } else {
+          tabs3[dir][i] = tp.P.inst;
+          if (dir == 0) work3[i] = tp.work;
+          if (i == 0 && dir == 0) bt->tb3_base = tp;
+        }
+      }
       if (dir == 0) {
         tb_ok = tb_ok && tb2d_eligible(bd, pl.op);
         bt->nx[i] = bd.in[0].n[0];
@@ -185,30 +248,9 @@ gscl_status build(Batch *bt) {
   long long W = 0;
   for (long long w : work) W += w;
   const long long G = std::max(1LL, std::min<long long>(W, (long long)sm_count() * occ));
-  // work-list: run b = [W b / G, W (b+1) / G) split at instance and column ends
   std::vector<Segment> segs;
-  std::vector<int32_t> cta_seg(G + 1), inst_seg(n + 1, -1);
-  int inst = 0;
-  long long inst_start = 0;
-  for (long long b = 0; b < G; ++b) {
-    cta_seg[b] = (int32_t)segs.size();
-    long long pos = W * b / G;
-    const long long end = W * (b + 1) / G;
-    while (pos < end) {
-      while (pos >= inst_start + work[inst]) inst_start += work[inst++];
-      if (inst_seg[inst] < 0) inst_seg[inst] = (int32_t)segs.size();
-      const long long local = pos - inst_start;
-      const long long col = local / nz[inst];
-      const long long zoff = local - col * nz[inst];
-      const long long len = std::min(end - pos, nz[inst] - zoff);
-      segs.push_back(Segment{inst, (int32_t)col, (int32_t)zoff, (int32_t)len});
-      pos += len;
-    }
-  }
-  cta_seg[G] = (int32_t)segs.size();
-  inst_seg[n] = (int32_t)segs.size();
-  for (int i = n - 1; i >= 0; --i)
-    if (inst_seg[i] < 0) inst_seg[i] = inst_seg[i + 1];
+  std::vector<int32_t> cta_seg, inst_seg;
+  make_worklist(work, nz, G, &segs, &cta_seg, &inst_seg);
   // device blob: two tables, segments, CTA and instance segment starts, partials
   const size_t t_bytes = align_up(sizeof(InstDesc) * n, 256);
   const size_t s_bytes = align_up(sizeof(Segment) * segs.size(), 256);
@@ -244,7 +286,52 @@ gscl_status build(Batch *bt) {
   bt->G = (int)G;
   bt->S = (int)segs.size();
   bt->tb_ok = tb_ok;
-  if (!tb_ok) bt->tb_k = 1;
+  bt->tb3_ok = false;
+  if (tb3_ok) {
+    // the two-sweep pass's work-list over one wave of its CTAs
+    Plan &tb = bt->tb3_base;
+    tb.batch = true;
+    int occ3 = 0;
+    if (launch_tb2_pass(tb, bt->dtype, nullptr, &occ3) == GSCL_OK) {
+      long long W3 = 0;
+      for (long long w : work3) W3 += w;
+      const long long G3 = std::max(1LL, std::min<long long>(W3, (long long)sm_count() * std::max(1, occ3)));
+      std::vector<Segment> segs3;
+      std::vector<int32_t> cta3, inst3;
+      make_worklist(work3, nz, G3, &segs3, &cta3, &inst3);
+      const size_t t3 = align_up(sizeof(InstDesc) * n, 256), s3 = align_up(sizeof(Segment) * segs3.size(), 256);
+      const size_t c3 = align_up(sizeof(int32_t) * (G3 + 1), 256);
+      const size_t need3 = 2 * t3 + s3 + c3;
+      cudaError_t e3 = cudaSuccess;
+      if (need3 > bt->tb3_bytes) {
+        if (bt->tb3_dev) cudaFree(bt->tb3_dev);
+        bt->tb3_dev = nullptr;
+        bt->tb3_bytes = 0;
+        e3 = cudaMalloc(&bt->tb3_dev, need3);
+        if (e3 == cudaSuccess) bt->tb3_bytes = need3;
+      }
+      if (e3 == cudaSuccess) {
+        bt->tb3_tab[0] = (InstDesc *)bt->tb3_dev;
+        bt->tb3_tab[1] = (InstDesc *)(bt->tb3_dev + t3);
+        bt->tb3_segs = (Segment *)(bt->tb3_dev + 2 * t3);
+        bt->tb3_cta = (int32_t *)(bt->tb3_dev + 2 * t3 + s3);
+        e3 = cudaMemcpy(bt->tb3_tab[0], tabs3[0].data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice);
+        if (e3 == cudaSuccess)
+          e3 = cudaMemcpy(bt->tb3_tab[1], tabs3[1].data(), sizeof(InstDesc) * n, cudaMemcpyHostToDevice);
+        if (e3 == cudaSuccess)
+          e3 = cudaMemcpy(bt->tb3_segs, segs3.data(), sizeof(Segment) * segs3.size(), cudaMemcpyHostToDevice);
+        if (e3 == cudaSuccess)
+          e3 = cudaMemcpy(bt->tb3_cta, cta3.data(), sizeof(int32_t) * (G3 + 1), cudaMemcpyHostToDevice);
+      }
+      if (e3 != cudaSuccess) return cuda_fail(e3, "uploading the batch's two-sweep tables");
+      bt->tb3_G = (int)G3;
+      tb.batch_ctas = (int)G3;
+      tb.P.segs = bt->tb3_segs;
+      tb.P.cta_seg = bt->tb3_cta;
+      bt->tb3_ok = true;
+    }
+  }
+  if (!tb_ok && !(bt->tb3_ok && bt->tb_k == 2)) bt->tb_k = 1;
   if (gscl_status s = build_tb_tiles(bt)) return s;
   base.batch_ctas = (int)G;
   base.P.segs = bt->segs;
@@ -284,6 +371,11 @@ int batch_launches(const Batch *bt, int sweeps) { return (int)tb_launch_plan(swe
 // One launch: a fused pass of k sweeps (k > 1) or one sweep, reading table t
 // (halo_swap as in tb2d_kernel.cuh).
 gscl_status enqueue_launch(Batch *bt, int t, int k, cudaStream_t stream, bool halo_swap = false) {
+  if (k > 1 && bt->tb3_ok) {  // a 3D batch: the two-sweep pass over its own tables
+    Plan pl = bt->tb3_base;
+    pl.P.insts = bt->tb3_tab[t];
+    return launch_tb2_pass(pl, bt->dtype, stream, nullptr);
+  }
   Plan pl = bt->base;
   pl.P.insts = bt->tab[t];
   if (k > 1) {
@@ -466,6 +558,7 @@ gscl_status gscl_batch_destroy(gscl_batch h) {
   if (bt->cap_stream) cudaStreamDestroy(bt->cap_stream);
   if (bt->dev) cudaFree(bt->dev);
   if (bt->tb_tiles) cudaFree(bt->tb_tiles);
+  if (bt->tb3_dev) cudaFree(bt->tb3_dev);
   return GSCL_OK;
 }
 
@@ -493,8 +586,9 @@ gscl_status gscl_batch_temporal(gscl_batch h, int32_t *sweeps_per_launch, int32_
   if (!bt) return fail(GSCL_ERR_STATE, "unknown or destroyed batch");
   std::lock_guard<std::mutex> lk(bt->mu);
   if (sweeps_per_launch) *sweeps_per_launch = bt->tb_k;
-  if (tile_x) *tile_x = bt->tb_k > 1 ? tb2d_tile_x(bt->tb_tile) : 0;
-  if (tile_y) *tile_y = bt->tb_k > 1 ? tb2d_tile_y(bt->tb_tile) : 0;
+  const bool d3 = bt->tb3_ok && bt->tb_k > 1;
+  if (tile_x) *tile_x = bt->tb_k > 1 ? (d3 ? Tb2Shape<float>::TX : tb2d_tile_x(bt->tb_tile)) : 0;
+  if (tile_y) *tile_y = bt->tb_k > 1 ? (d3 ? Tb2Shape<float>::TY : tb2d_tile_y(bt->tb_tile)) : 0;
   return GSCL_OK;
 }
 
@@ -508,8 +602,10 @@ gscl_status gscl_batch_set_temporal(gscl_batch h, int32_t sweeps_per_launch, int
   std::lock_guard<std::mutex> lk(bt->mu);
   int first = 0;
   if (gscl_status s = current_table(bt, &first)) return s;
-  if (sweeps_per_launch > 1 && !bt->tb_ok)
-    return fail(GSCL_ERR_UNSUPPORTED, "only batches of 2D grids under a 5-point operator fuse sweeps");
+  if (sweeps_per_launch > 1 && !bt->tb_ok && !(bt->tb3_ok && sweeps_per_launch == 2))
+    return fail(GSCL_ERR_UNSUPPORTED,
+                "batches fuse sweeps of 2D grids under a 5-point operator (up to 16) or two sweeps of 3D FP32 / "
+                "BF16 grids under a 7-point star operator");
   drop_graphs(bt);
   bt->tb_k = sweeps_per_launch;
   bt->tb_tile = tile_shape;
@@ -673,8 +769,39 @@ gscl_status gscl_batch_tune(gscl_batch h, int32_t trial_sweeps, void *stream, in
     }
     bt->tb_k = best_k;
     bt->tb_tile = best_tile;
+  } else if (bt->tb3_ok && red == RED_NONE) {
+    // 3D batches: single sweeps against two-sweep passes (trial_sweeps each)
+    int first = 0;
+    float best_sweep = 1e30f;
+    int best_k = 1;
+    if (current_table(bt, &first) == GSCL_OK) {
+      for (int K : {1, 2}) {
+        bt->tb_k = K;
+        if (enqueue_launch(bt, first, K, st) != GSCL_OK) continue;  // warm-up (kernel set-up)
+        const int passes = std::max(1, (int)trial_sweeps / K);
+        float ms = 1e30f;
+        bool timed = true;
+        for (int rep = 0; rep < 2 && timed; ++rep) {
+          cudaEventRecord(e0, st);
+          for (int p = 0; p < passes; ++p) enqueue_launch(bt, first, K, st);
+          cudaEventRecord(e1, st);
+          timed = cudaEventSynchronize(e1) == cudaSuccess;
+          float tm = 0.f;
+          if (timed) cudaEventElapsedTime(&tm, e0, e1);
+          ms = std::min(ms, tm);
+        }
+        if (!timed) break;
+        const float per_sweep = ms / (passes * K);
+        if (log) fprintf(stderr, "gscl_batch_tune: %d sweeps per launch (3D): %.5f ms per sweep\n", K, per_sweep);
+        if (per_sweep < best_sweep) {
+          best_sweep = per_sweep;
+          best_k = K;
+        }
+      }
+    }
+    bt->tb_k = best_k;
   } else {
-    bt->tb_k = bt->tb_ok ? keep_k : 1;
+    bt->tb_k = (bt->tb_ok || bt->tb3_ok) ? keep_k : 1;
     bt->tb_tile = keep_tile;
   }
   cudaEventDestroy(e0);

@@ -65,6 +65,10 @@ TbChoice tb_choice(const Bound &b, int op, int sweeps);
 gscl_status run_tb_pass(const Bound &b, int op, TbChoice c, bool halo_swap, cudaStream_t stream);
 gscl_status make_tb_plan(const Bound &b, int K, Plan *pl);
 gscl_status launch_tb(const Plan &pl, int dtype, int K, cudaStream_t stream);
+// the 3D two-sweep pass (single grids, or a batch's work-list when pl.batch);
+// occupancy_only: CTAs per SM instead of a launch
+gscl_status launch_tb2_pass(const Plan &pl, int dtype, cudaStream_t stream, int *occupancy_only);
+bool tb_eligible(const Bound &b, int op);
 struct Tb2dArgs;
 gscl_status launch_tb2d(const Plan &pl, int dtype, const Tb2dArgs &a, cudaStream_t stream);
 gscl_status tune_sweeps(const Bound &b, int op, int trial_sweeps, cudaStream_t st, int *best_out);

@@ -69,10 +69,12 @@ gscl_status launch_tb_op(const Plan &pl, cudaStream_t stream) {
 }
 
 // K = 2: the vector-lane kernel (tb2_kernel.cuh), one wave with programmatic
-// dependent launch like the single sweeps.
-template <typename T, class Def>
-gscl_status launch_tb2_t(const Plan &pl, cudaStream_t stream) {
-  auto kern = tb2_kernel<T, Def>;
+// dependent launch like the single sweeps; batches (pl.batch) launch its
+// work-list form over pl.batch_ctas CTAs.  occupancy_only: report the CTAs
+// per SM instead of launching.
+template <typename T, class Def, bool BATCH>
+gscl_status launch_tb2_t(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
+  auto kern = tb2_kernel<T, Def, BATCH>;
   constexpr size_t smem = Tb2Shape<T>::smem_bytes();
   constexpr int kDevices = 64;
   static std::mutex mu;
@@ -92,7 +94,11 @@ gscl_status launch_tb2_t(const Plan &pl, cudaStream_t stream) {
     }
     per_sm = per_sm_of[dev];
   }
-  const long long ctas = std::min<long long>(pl.work, (long long)sm_count() * per_sm);
+  if (occupancy_only) {
+    *occupancy_only = per_sm;
+    return GSCL_OK;
+  }
+  const long long ctas = BATCH ? (long long)pl.batch_ctas : std::min<long long>(pl.work, (long long)sm_count() * per_sm);
   if (ctas < 1) return GSCL_OK;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)ctas);
@@ -108,12 +114,18 @@ gscl_status launch_tb2_t(const Plan &pl, cudaStream_t stream) {
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "two-sweep kernel launch");
 }
 
+template <typename T, class Def>
+gscl_status launch_tb2_def(const Plan &pl, cudaStream_t stream, int *occupancy_only) {
+  return pl.batch ? launch_tb2_t<T, Def, true>(pl, stream, occupancy_only)
+                  : launch_tb2_t<T, Def, false>(pl, stream, occupancy_only);
+}
+
 template <typename T>
-gscl_status launch_tb2(const Plan &pl, cudaStream_t stream) {
+gscl_status launch_tb2(const Plan &pl, cudaStream_t stream, int *occupancy_only = nullptr) {
   switch (pl.op) {
-    case OP_STAR7: return launch_tb2_t<T, OpStar7>(pl, stream);
-    case OP_HEAT7_RHS: return launch_tb2_t<T, OpHeat7Rhs>(pl, stream);
-    case OP_JACOBI7_RHS: return launch_tb2_t<T, OpJacobi7Rhs>(pl, stream);
+    case OP_STAR7: return launch_tb2_def<T, OpStar7>(pl, stream, occupancy_only);
+    case OP_HEAT7_RHS: return launch_tb2_def<T, OpHeat7Rhs>(pl, stream, occupancy_only);
+    case OP_JACOBI7_RHS: return launch_tb2_def<T, OpJacobi7Rhs>(pl, stream, occupancy_only);
   }
   return fail(GSCL_ERR_INVALID, "no temporal-blocking kernel for operator %d", pl.op);
 }
@@ -205,6 +217,12 @@ int max_factor(int) {
 }
 
 }  // namespace
+
+gscl_status launch_tb2_pass(const Plan &pl, int dtype, cudaStream_t stream, int *occupancy_only) {
+  if (dtype == GSCL_F32) return launch_tb2<float>(pl, stream, occupancy_only);
+  if (dtype == GSCL_BF16) return launch_tb2<__nv_bfloat16>(pl, stream, occupancy_only);
+  return fail(GSCL_ERR_DTYPE, "two-sweep passes are for FP32 / BF16 storage");
+}
 
 gscl_status launch_tb2d(const Plan &pl, int dtype, const Tb2dArgs &a, cudaStream_t stream) {
   switch (dtype) {

@@ -45,7 +45,10 @@ struct Tb2Shape {
   static constexpr size_t smem_bytes() { return kBarBytes + sizeof(T) * (size_t)R * (SE_U + SE_F + SE_1); }
 };
 
-template <typename T, class Def>
+// BATCH: the CTA walks its segments of a batch's work-list (instance, tile
+// column, z run; P.insts holds the instances' descriptors with this kernel's
+// boxes) instead of its share of one grid's (tile, plane) pairs.
+template <typename T, class Def, bool BATCH = false>
 __global__ void __launch_bounds__(256) tb2_kernel(const __grid_constant__ SweepParams P) {
   using S = Tb2Shape<T>;
   constexpr int G = S::G, VY = S::VY, BW = S::BW, R = S::R;
@@ -72,10 +75,15 @@ __global__ void __launch_bounds__(256) tb2_kernel(const __grid_constant__ SweepP
   __syncthreads();
   pdl_wait();
 
-  const InstDesc &I = P.inst;
-  const int64_t nx = I.hi[0], ny = I.hi[1], nz = I.hi[2];  // the range is the whole interior
-  const long long W = (long long)I.tiles_x * I.tiles_y * nz;
+  const int64_t nz0 = P.inst.hi[2];
+  const long long W = BATCH ? 0 : (long long)P.inst.tiles_x * P.inst.tiles_y * nz0;
   const long long run_end = W * (blockIdx.x + 1) / gridDim.x;
+  long long pos = W * blockIdx.x / gridDim.x;
+  int sg = 0, sg_end = 0;
+  if constexpr (BATCH) {
+    sg = P.cta_seg[blockIdx.x];
+    sg_end = P.cta_seg[blockIdx.x + 1];
+  }
   // ring positions of the next run's plane 0, advanced identically in every
   // thread; issued counts are thread 0's (it issues), waited counts each
   // thread's own (both only drain copies after a wait gave up)
@@ -88,11 +96,27 @@ __global__ void __launch_bounds__(256) tb2_kernel(const __grid_constant__ SweepP
 #pragma unroll
   for (int i = 0; i < Def::NT; ++i) w[i] = P.terms[i].wf;
 
-  for (long long pos = W * blockIdx.x / gridDim.x; pos < run_end;) {
-    const long long col = pos / nz;
-    const long long zoff = pos - col * nz;
-    const int zlen = (int)min(nz - zoff, run_end - pos);
-    pos += zlen;
+  for (;;) {
+    const InstDesc *Ip;
+    long long col, zoff;
+    int zlen;
+    if constexpr (BATCH) {
+      if (sg >= sg_end) break;
+      const Segment seg = P.segs[sg++];
+      Ip = &P.insts[seg.inst];
+      col = seg.col;
+      zoff = seg.zoff;
+      zlen = seg.zlen;
+    } else {
+      if (pos >= run_end) break;
+      Ip = &P.inst;
+      col = pos / nz0;
+      zoff = pos - col * nz0;
+      zlen = (int)min(nz0 - zoff, run_end - pos);
+      pos += zlen;
+    }
+    const InstDesc &I = *Ip;
+    const int64_t nx = I.hi[0], ny = I.hi[1], nz = I.hi[2];  // the range is the whole interior
     const int64_t x0 = (int64_t)(col % I.tiles_x) * S::TX;
     const int64_t y0 = (int64_t)(col / I.tiles_x) * S::TY;
     const int64_t zb = zoff;
