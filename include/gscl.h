@@ -56,7 +56,7 @@ typedef enum gscl_status {
   GSCL_ERR_CUDA = 7,        /* a CUDA runtime or driver call failed */
   GSCL_ERR_STATE = 8,       /* destroyed or unknown handle */
   GSCL_ERR_TIMEOUT = 9,     /* a bounded device-side wait gave up (reported by gscl_sync) */
-  GSCL_ERR_UNSUPPORTED = 10 /* valid request outside what this build implements (e.g. too many terms) */
+  GSCL_ERR_UNSUPPORTED = 10 /* valid request outside what the library implements (e.g. too many terms) */
 } gscl_status;
 
 typedef enum gscl_dtype {

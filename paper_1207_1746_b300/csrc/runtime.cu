@@ -259,7 +259,7 @@ const char *gscl_status_str(gscl_status s) {
     case GSCL_ERR_CUDA: return "CUDA error";
     case GSCL_ERR_STATE: return "unknown or destroyed handle";
     case GSCL_ERR_TIMEOUT: return "device-side wait timed out";
-    case GSCL_ERR_UNSUPPORTED: return "unsupported by this build";
+    case GSCL_ERR_UNSUPPORTED: return "unsupported by this library";
   }
   return "unknown status";
 }
