@@ -146,7 +146,7 @@ constexpr uint32_t centre_mask() {
 // frees enough for a second resident CTA.
 constexpr int kCentreFp64Min = 4;
 template <class Def>
-constexpr int centre_count() {
+GSCL_HD constexpr int centre_count() {
   int n = 0;
   for (int a = 0; a < Def::NIN; ++a) n += centre_only<Def>(a) ? 1 : 0;
   return n;

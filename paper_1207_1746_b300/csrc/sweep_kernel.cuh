@@ -741,11 +741,41 @@ struct StaticOpV {
     return ring + P.in_base[IN] + slot * P.in_se[IN] + (row + RY) * BW + AX;
   }
 
+  // BF16 storage keeps the queue's rows as the packed pairs they were loaded
+  // as (G / 2 words in the first entries of each row, the rest unused) and
+  // widens an element where a term reads it, exactly as load_group does:
+  // half the queue's registers, the same values.
+  template <typename T>
+  __host__ __device__ static constexpr bool packed_queue() { return std::is_same<T, __nv_bfloat16>::value; }
+  template <typename T, int VX>
+  __device__ static __forceinline__ void queue_row(const T *p, float (&q)[VX]) {
+    if constexpr (packed_queue<T>()) {
+      static_assert(VX == 8, "BF16 vector lanes hold 8 columns (one 16-byte word)");
+      const uint4 v = *reinterpret_cast<const uint4 *>(p);
+      q[0] = __uint_as_float(v.x);
+      q[1] = __uint_as_float(v.y);
+      q[2] = __uint_as_float(v.z);
+      q[3] = __uint_as_float(v.w);
+    } else {
+      load_group<G>(p, q);
+    }
+  }
+  template <typename T, int VX>
+  __device__ static __forceinline__ float queue_elem(const float (&q)[VX], int e) {
+    if constexpr (packed_queue<T>()) {
+      const uint32_t w = __float_as_uint(q[e >> 1]);
+      return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
+    } else {
+      return q[e];
+    }
+  }
+
   // Step start: queue rows of planes z - RZ .. z + RZ (col: this lane's first column).
   template <typename T, int VX, int VY>
   __device__ static __forceinline__ void advance_queue(const SweepParams &P, const T *ring, int smod, int row0,
                                                        int col, bool first, float (&zq)[kQueue][VY][VX]) {
     if constexpr (ZQ >= 0) {
+      constexpr int used = packed_queue<T>() ? VX / 2 : VX;
       const int R = P.R;
       if (first) {
 #pragma unroll
@@ -753,7 +783,7 @@ struct StaticOpV {
           int sl = smod + k - RZ;
           sl = sl >= R ? sl - R : (sl < 0 ? sl + R : sl);
 #pragma unroll
-          for (int r = 0; r < VY; ++r) load_group<G>(row_ptr<ZQ>(P, ring, sl, row0 + r) + col, zq[k][r]);
+          for (int r = 0; r < VY; ++r) queue_row<T, VX>(row_ptr<ZQ>(P, ring, sl, row0 + r) + col, zq[k][r]);
         }
       } else {
 #pragma unroll
@@ -761,11 +791,11 @@ struct StaticOpV {
 #pragma unroll
           for (int r = 0; r < VY; ++r)
 #pragma unroll
-            for (int e = 0; e < VX; ++e) zq[k][r][e] = zq[k + 1][r][e];
+            for (int e = 0; e < used; ++e) zq[k][r][e] = zq[k + 1][r][e];
         int sl = smod + RZ;
         sl = sl >= R ? sl - R : sl;
 #pragma unroll
-        for (int r = 0; r < VY; ++r) load_group<G>(row_ptr<ZQ>(P, ring, sl, row0 + r) + col, zq[2 * RZ][r]);
+        for (int r = 0; r < VY; ++r) queue_row<T, VX>(row_ptr<ZQ>(P, ring, sl, row0 + r) + col, zq[2 * RZ][r]);
       }
     }
   }
@@ -794,7 +824,7 @@ struct StaticOpV {
       float c[G];
       if constexpr (t.in == ZQ && r + t.dy >= 0 && r + t.dy < VY && t.dz >= -RZ && t.dz <= RZ) {
 #pragma unroll
-        for (int e = 0; e < G; ++e) c[e] = zq[t.dz + RZ][r + t.dy][e];
+        for (int e = 0; e < G; ++e) c[e] = queue_elem<T, VX>(zq[t.dz + RZ][r + t.dy], e);
       } else {
         load_group<G>(rp, c);
       }
@@ -964,8 +994,8 @@ __device__ __forceinline__ void cta_fold_sq32(SquareSum32 q, double &s, double &
 // 8-warp CTAs per SM (at most 64 registers per thread).  Reducing sweeps
 // carry the square-sum pairs and spill under that bound, larger operators
 // (the climate operator) are held to fewer CTAs by their shared memory, and
-// BF16 vector lanes (two rows of 8 columns per thread) need more registers:
-// those keep the compiler's own register target.
+// BF16 vector lanes (two rows of 8 columns per thread; the z queue packed)
+// fit three CTAs per SM at the compiler's own register target: those keep it.
 template <typename T, bool BATCH, int RED, class Op>
 constexpr int min_ctas_per_sm() {
   return (!BATCH && RED == RED_NONE && std::is_same<T, float>::value && Op::kTerms <= 10) ? 4 : 0;
