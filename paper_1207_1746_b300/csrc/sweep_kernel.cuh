@@ -311,6 +311,20 @@ struct SquareSum32 {
     lo.x = __fadd_rn(__fadd_rn(lo.x, lo.y), err);
     hi.y = lo.y = 0.0f;
   }
+  // FP64 values split as v = h + e (split_double): h^2 exactly as p + pe,
+  // the cross term 2 h e rounded to a float and added with the errors;
+  // e^2 < 2^-46 h^2 is dropped.  With e = 0 (every FP64 value of at most 24
+  // significant bits, integers below 2^24 among them) this is add_squares.
+  __device__ __forceinline__ void add_split_squares(float ha, float ea, float hb, float eb) {
+    const float pa = __fmul_rn(ha, ha), pb = __fmul_rn(hb, hb);
+    const float2 p = make_float2(pa, pb);
+    const float2 pe = make_float2(__fmaf_rn(ha, ha, -pa), __fmaf_rn(hb, hb, -pb));
+    const float2 c = make_float2(__fmul_rn(__fadd_rn(ha, ha), ea), __fmul_rn(__fadd_rn(hb, hb), eb));
+    float2 t, err;
+    two_sum2(hi, p, t, err);
+    hi = t;
+    lo = __fadd2_rn(lo, __fadd2_rn(__fadd2_rn(err, pe), c));
+  }
   // adds another sum h + l into chain 0
   __device__ __forceinline__ void add_sum(float h, float l) {
     float t, err;
@@ -319,6 +333,31 @@ struct SquareSum32 {
     lo.x = __fadd_rn(lo.x, __fadd_rn(l, err));
   }
 };
+
+// FP64 values on the FP32 pipe (the L2 reduction of IEEE FP64 sweeps, whose
+// FP64 pipe binds): v = h + e with h its 24 leading significand bits (the
+// truncation, a float, exact) and e the rest rounded to a float (relative
+// error 2^-24 of a term below 2^-23 |v|), both taken apart with integer
+// operations.  In range when 2^-50 <= |v| < 2^50 (biased exponent 973 ..
+// 1072, so h, e and the squares' error terms stay representable) or v == 0;
+// other values (an infinity, a NaN, a subnormal) take the FP64 chain.
+__device__ __forceinline__ bool split_in_range(double v) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t ex = (hi >> 20) & 0x7ffu;
+  return ex - 973u < 100u || ((hi & 0x7fffffffu) | lo) == 0u;
+}
+__device__ __forceinline__ void split_double(double v, float &h, float &e) {
+  const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+  const uint32_t ex = (hi >> 20) & 0x7ffu, sign = hi & 0x80000000u;
+  // float exponent field ex - 896 (bias 1023 -> 127); 23 fraction bits: the
+  // double's top 20 and 3 more
+  const float hv = __uint_as_float(sign | ((ex - 896u) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  // the remaining 29 bits, times 2^(ex - 1075) (exponent field ex - 948)
+  const float ev = __uint_as_float(
+      __float_as_uint(__fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((ex - 948u) << 23))) | sign);
+  h = ex != 0u ? hv : 0.0f;
+  e = ex != 0u ? ev : 0.0f;
+}
 
 __device__ __forceinline__ double max_abs_bits(double a, double b) {
   return __longlong_as_double(
@@ -1048,6 +1087,7 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
   double sq = 0.0;          // L2: plain FP64 chain of squares within one segment
   // L2 of FP32 arithmetic (FP32 / BF16 storage): squares summed on the FP32 pipe
   constexpr bool kSq32 = RED == RED_L2 && std::is_same<A, float>::value;
+  constexpr bool kSq64 = RED == RED_L2 && std::is_same<A, double>::value;  // IEEE FP64 (not pairs)
   SquareSum32 sq32;
   unsigned long long maxkey = 0;
   uint32_t seq = 0;         // planes issued by this CTA (identical in every thread)
@@ -1299,6 +1339,28 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
                 for (int e = 0; e < VX; ++e) sq = fma((double)w[e], (double)w[e], sq);
               }
             }
+          } else if constexpr (kSq64) {
+            // squares on the FP32 pipe (split_double, add_split_squares) for
+            // rows whose values are all in range; otherwise the FP64 chain
+            bool in_range = true;
+            double w[VX];
+#pragma unroll
+            for (int e = 0; e < VX; ++e) {
+              w[e] = (yok[r] && xok[e]) ? v[e] : 0.0;
+              in_range &= split_in_range(w[e]);
+            }
+            if (in_range) {
+#pragma unroll
+              for (int e = 0; e + 1 < VX; e += 2) {
+                float ha, ea, hb, eb;
+                split_double(w[e], ha, ea);
+                split_double(w[e + 1], hb, eb);
+                sq32.add_split_squares(ha, ea, hb, eb);
+              }
+            } else {
+#pragma unroll
+              for (int e = 0; e < VX; ++e) sq = fma(w[e], w[e], sq);
+            }
           } else if constexpr (RED != RED_NONE) {
             double d[VX];
             widen_group<VX>(v, d);
@@ -1315,7 +1377,7 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
             }
           }
         });
-        if constexpr (kSq32) sq32.renormalize();
+        if constexpr (kSq32 || kSq64) sq32.renormalize();
       }
       smod = adv(smod);
       __syncthreads();
@@ -1332,7 +1394,7 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
       // this segment's partial, in a fixed order; then start afresh
       double fs = RED == RED_MAXABS ? key_value(maxkey, A(0)) : acc.s;
       double fc = RED == RED_MAXABS ? 0.0 : acc.c;
-      if constexpr (kSq32) cta_fold_sq32(sq32, fs, fc, s_red, NW);
+      if constexpr (kSq32 || kSq64) cta_fold_sq32(sq32, fs, fc, s_red, NW);
       else block_fold<RED>(fs, fc, s_red, NW);
       if (tid == 0) {
         P.seg_partials[2 * kseg] = fs;
@@ -1365,7 +1427,7 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
   // ---- single grid: CTA partial, then the last CTA folds all partials
   double s = RED == RED_MAXABS ? key_value(maxkey, A(0)) : acc.s;  // widened: double bits from here on
   double c = RED == RED_MAXABS ? 0.0 : acc.c;
-  if constexpr (kSq32) cta_fold_sq32(sq32, s, c, s_red, NW);
+  if constexpr (kSq32 || kSq64) cta_fold_sq32(sq32, s, c, s_red, NW);
   else block_fold<RED>(s, c, s_red, NW);
   unsigned int *ticket = reinterpret_cast<unsigned int *>(P.workspace);
   double *partials = reinterpret_cast<double *>(P.workspace + 256);
