@@ -165,6 +165,7 @@ gscl_status build(Batch *bt) {
   bt->buf_a.assign(n, nullptr);
   bt->buf_b.assign(n, nullptr);
   TileCfg cfg = bt->cfg;
+  cfg.colored = bt->colored;
   bool tb_ok = !bt->colored && bt->n_in == 1 && bt->n_out == 1;
   bool tb3_ok = !bt->colored && bt->n_out == 1;
   std::vector<InstDesc> tabs3[2];
@@ -203,7 +204,8 @@ gscl_status build(Batch *bt) {
           if (gscl_status s = make_plan(bd, bt->has_value, &pl, cfg)) return s;
         }
         bt->base = pl;
-      } else if (pl.op != bt->base.op || pl.smem != bt->base.smem || pl.threads != bt->base.threads ||
+      } else if (pl.op != bt->base.op || pl.eqw != bt->base.eqw || pl.smem != bt->base.smem ||
+                 pl.threads != bt->base.threads ||
                  pl.P.R != bt->base.P.R || memcmp(pl.P.in_bw, bt->base.P.in_bw, sizeof pl.P.in_bw) != 0 ||
                  memcmp(pl.P.in_bh, bt->base.P.in_bh, sizeof pl.P.in_bh) != 0) {
         return fail(GSCL_ERR_SHAPE, "instance %d plans a different tile shape", i);

@@ -176,4 +176,46 @@ inline uint32_t static_centre_mask(int op) {
   return 0;
 }
 
+// The axial group: six consecutive table terms reading one input at the six
+// unit offsets, without coefficient, into one destination (the star / heat
+// family's neighbour sum).  Returns the index of its first term, or -1.
+// When the six weights are bit-identical, IEEE FP64 sweeps evaluate
+// w (x+ + x-) ... as w times a tree sum of the six values, two of whose
+// additions run on the integer pipe (fp64_int.cuh): the same result within
+// a few rounding errors of the neighbour sum, and fewer FP64 operations.
+template <class Def>
+GSCL_HD constexpr int axial_group() {
+  for (int i = 0; i + 6 <= Def::NT; ++i) {
+    const OpTerm &t0 = Def::table.t[i];
+    if (t0.in < 0 || t0.coef >= 0) continue;
+    int seen = 0;
+    bool ok = true;
+    for (int k = 0; k < 6 && ok; ++k) {
+      const OpTerm &t = Def::table.t[i + k];
+      const int ax = (t.dx != 0) + (t.dy != 0) + (t.dz != 0);
+      const int mag = (t.dx < 0 ? -t.dx : t.dx) + (t.dy < 0 ? -t.dy : t.dy) + (t.dz < 0 ? -t.dz : t.dz);
+      ok = t.in == t0.in && t.coef < 0 && t.out == t0.out && ax == 1 && mag == 1;
+      if (ok) {
+        const int bit = t.dx == 1 ? 0 : t.dx == -1 ? 1 : t.dy == 1 ? 2 : t.dy == -1 ? 3 : t.dz == 1 ? 4 : 5;
+        ok = ((seen >> bit) & 1) == 0;
+        seen |= 1 << bit;
+      }
+    }
+    if (ok && seen == 63) return i;
+  }
+  return -1;
+}
+
+inline int static_axial_group(int op) {
+  switch (op) {
+    case OP_HEAT7_RHS: return axial_group<OpHeat7Rhs>();
+    case OP_STAR7: return axial_group<OpStar7>();
+    case OP_JACOBI7_RHS: return axial_group<OpJacobi7Rhs>();
+    case OP_HEAT7_RHS_FUSED: return axial_group<OpHeat7RhsFused>();
+    case OP_HEAT7_FUSED: return axial_group<OpHeat7Fused>();
+    case OP_RESIDUAL7_RHS: return axial_group<OpResidual7Rhs>();
+  }
+  return -1;
+}
+
 }  // namespace gscl

@@ -237,6 +237,18 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   // kernel reads every input from the plane ring)
   const uint32_t smask = static_centre_mask(pl->op);
   const bool ieee64 = g0.dtype == GSCL_F64 && !pl->pair;
+  // IEEE FP64 operators of the star / heat family whose six neighbour
+  // weights are bit-identical: the axial-sum evaluation (static_ops.h), not
+  // for colour sweeps (a coloured batch's instances have their own weights)
+  pl->eqw = false;
+  if (ieee64 && !compact && !cfg.colored && pl->op != OP_GENERIC && fp64_int_add()) {
+    const int ga = static_axial_group(pl->op);
+    if (ga >= 0) {
+      bool eq = true;
+      for (int k = 1; k < 6; ++k) eq = eq && memcmp(&terms[perm[ga + k]].w, &terms[perm[ga]].w, sizeof(double)) == 0;
+      pl->eqw = eq;
+    }
+  }
   const uint32_t cmask =
       (compact || (ieee64 && __builtin_popcount(smask) < kCentreFp64Min)) ? 0u : smask;
   auto centre = [&](int a) { return ((cmask >> a) & 1u) != 0; };
@@ -401,6 +413,13 @@ gscl_status launch_generic(const Plan &pl, int red, cudaStream_t stream, int *oc
 // Arithmetic of FP64 grids: IEEE FP64 (default) or pairs of FP32 numbers.
 std::atomic<int> g_fp64_arith{-1};
 
+// The axial-sum evaluation of IEEE FP64 sweeps (GSCL_FP64_INT_ADD=0 turns
+// it off: every term then takes its own FMA in table order).
+bool fp64_int_add() {
+  const char *e = getenv("GSCL_FP64_INT_ADD");
+  return !(e && e[0] == '0');
+}
+
 int fp64_arith() {
   int m = g_fp64_arith.load();
   if (m < 0) {  // first use: GSCL_FP64_ARITH=pair selects the pair arithmetic
@@ -531,6 +550,7 @@ gscl_status gscl_do_colored(const gscl_stencil *op, const gscl_grid *in, int32_t
   Plan pl;
   TileCfg cfg;
   cfg.compact = colour_compact();
+  cfg.colored = true;
   if (gscl_status s = make_plan(b, false, &pl, cfg)) return s;
   for (int h = 0; h < half_sweeps; ++h) {
     pl.P.color = (color + h) & 1;

@@ -25,6 +25,7 @@ struct TileCfg {
   bool generic = false;  // interpret the term list even if a compiled structure matches
   bool narrow = false;   // batches, FP32 / BF16: 64-column tiles with 4 rows per warp
   bool compact = false;  // red-black sweeps, IEEE FP64, star family: only the colour's elements
+  bool colored = false;  // colour sweeps (a coloured batch's instances carry their own weights)
 };
 
 bool overlaps(const Grid &a, const Grid &b);
@@ -52,6 +53,7 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg);
 gscl_status launch(const Plan &pl, int dtype, int red, cudaStream_t stream, int *occupancy_only);
 // Current arithmetic of FP64 grids (GSCL_FP64_IEEE or GSCL_FP64_PAIR); make_plan records it in the plan.
 int fp64_arith();
+bool fp64_int_add();
 
 // Temporal blocking (tb.cu): sweeps fused per pass for a call (K = 1: none)
 // and, on 2D grids, the tile shape; one pass from in[0] into out[0]; the

@@ -21,6 +21,7 @@
 #include <type_traits>
 #include <utility>
 
+#include "fp64_int.cuh"
 #include "gscl_internal.h"
 #include "pair64.cuh"
 #include "static_ops.h"
@@ -446,9 +447,17 @@ struct GenericOp {
 // The kernel passes col for the warp's first row as `lane`; row r flips its
 // low bit (the warp's rows start at an even row).  The column changes from
 // plane to plane, so there is no z register queue and no centre ring.
-template <class Def, int XS = 1>
+//
+// EQ = true (IEEE FP64 grids, XS = 1, chosen on the host when the axial
+// group's six weights are bit-identical): the group is evaluated as its
+// weight times axial_sum, w (sum of six) instead of six FMAs; two of the
+// sum's five additions run on the integer pipe, so a point of the heat
+// operator takes six FP64 operations instead of eight.
+template <class Def, int XS = 1, bool EQ = false>
 struct StaticOp {
   static constexpr int kXStep = XS;
+  static constexpr int kAxial = EQ ? axial_group<Def>() : -1;
+  static_assert(!EQ || (XS == 1 && kAxial >= 0), "the axial-sum evaluation needs an axial group and XS = 1");
   static constexpr int kGroup = 1;
   static constexpr int kRowsPerSlot = 1;
   static constexpr int kTerms = Def::NT;
@@ -570,22 +579,19 @@ struct StaticOp {
     return ring + P.in_base[in] + cslot * P.in_se[in] + row * (32 * VX) + lane;
   }
 
-  // Term I at tile row row0 + r of this thread's VY rows.
-  template <typename T, int VX, int VY, int r, int I, class WS>
-  __device__ static __forceinline__ void term(const SweepParams &P, const WS &ws, const T *ring, int smod, int cslot,
-                                              int row0, int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
-                                              typename Arith<T>::A (&v)[VX],
-                                              typename Arith<T>::A (&o)[kMaxOut][VX],
-                                              typename Arith<T>::A (&g)[VX]) {
+  // The values term I reads at tile row row0 + r of this thread's VY rows
+  // (v: the operator's value so far, for a term of the value).
+  template <typename T, int VX, int VY, int r, int I>
+  __device__ static __forceinline__ void load_x(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
+                                                int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                                const typename Arith<T>::A (&v)[VX],
+                                                typename Arith<T>::A (&x)[VX]) {
     const int row = row0 + r;
     const int col = column(lane, r);
     constexpr int ES = 32 * XS;  // element stride of a thread's columns
-    using A = typename Arith<T>::A;
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
     const int R = P.R;
-    const A w = ws(P, I);
-    A x[VX];
     if constexpr (t.in < 0) {
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = v[e];
@@ -610,6 +616,51 @@ struct StaticOp {
       const T *p = ring + P.in_base[t.in] + slot * P.in_se[t.in] + row * BW + col + toff;
 #pragma unroll
       for (int e = 0; e < VX; ++e) x[e] = to_arith(p[ES * e]);
+    }
+  }
+
+  // The axial group's six values summed as ((x+ + x-) + (y+ + y-)) + (z+ + z-)
+  // in table order of the pairs; the first two pair sums run on the integer
+  // pipe (exact IEEE additions, fp64_int.cuh), the rest on the FP64 pipe.
+  template <typename T, int VX, int VY, int r>
+  __device__ static __forceinline__ void axial_sum(const SweepParams &P, const T *ring, int smod, int cslot, int row0,
+                                                   int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                                   const typename Arith<T>::A (&v)[VX],
+                                                   typename Arith<T>::A (&x)[VX]) {
+    using A = typename Arith<T>::A;
+    A x0[VX], x1[VX], x2[VX], x3[VX], x4[VX], x5[VX];
+    load_x<T, VX, VY, r, kAxial + 0>(P, ring, smod, cslot, row0, lane, zq, v, x0);
+    load_x<T, VX, VY, r, kAxial + 1>(P, ring, smod, cslot, row0, lane, zq, v, x1);
+    load_x<T, VX, VY, r, kAxial + 2>(P, ring, smod, cslot, row0, lane, zq, v, x2);
+    load_x<T, VX, VY, r, kAxial + 3>(P, ring, smod, cslot, row0, lane, zq, v, x3);
+    load_x<T, VX, VY, r, kAxial + 4>(P, ring, smod, cslot, row0, lane, zq, v, x4);
+    load_x<T, VX, VY, r, kAxial + 5>(P, ring, smod, cslot, row0, lane, zq, v, x5);
+#pragma unroll
+    for (int e = 0; e < VX; ++e) x[e] = (fp64_add_int(x0[e], x1[e]) + fp64_add_int(x2[e], x3[e])) + (x4[e] + x5[e]);
+  }
+
+  // Term I at tile row row0 + r of this thread's VY rows.
+  template <typename T, int VX, int VY, int r, int I, class WS>
+  __device__ static __forceinline__ void term(const SweepParams &P, const WS &ws, const T *ring, int smod, int cslot,
+                                              int row0, int lane, const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                              typename Arith<T>::A (&v)[VX],
+                                              typename Arith<T>::A (&o)[kMaxOut][VX],
+                                              typename Arith<T>::A (&g)[VX]) {
+    const int row = row0 + r;
+    const int col = column(lane, r);
+    constexpr int ES = 32 * XS;  // element stride of a thread's columns
+    using A = typename Arith<T>::A;
+    constexpr OpTerm t = Def::table.t[I];
+    constexpr int vec = 16 / (int)sizeof(T);
+    if constexpr (kAxial >= 0 && I > kAxial && I < kAxial + 6) {
+      return;  // summed with the group's first term
+    }
+    const A w = ws(P, I);
+    A x[VX];
+    if constexpr (kAxial >= 0 && I == kAxial) {
+      axial_sum<T, VX, VY, r>(P, ring, smod, cslot, row0, lane, zq, v, x);
+    } else {
+      load_x<T, VX, VY, r, I>(P, ring, smod, cslot, row0, lane, zq, v, x);
     }
     if constexpr (t.coef >= 0) {
 #pragma unroll
@@ -1500,6 +1551,7 @@ struct Plan {
   bool pair = false;          // FP64 grids in pair arithmetic (fixed when the plan is made)
   bool compact = false;       // colour-compacted red-black sweep (XS = 2 tiles)
   bool vec = false;           // vector lanes (StaticOpV): FP32 / BF16 compile-time operators
+  bool eqw = false;           // IEEE FP64, equal axial weights: StaticOp<Def, 1, true>
   int tile_x = 0, tile_y = 0; // core elements per CTA tile
 };
 
@@ -1643,6 +1695,10 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       // (IEEE or pair arithmetic), single grids and coloured batches
       if constexpr (RED == RED_NONE && CompactCapable<Def>::value) {
         if (pl.compact) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
+      }
+      // equal axial weights: the neighbour sum partly on the integer pipe
+      if constexpr (std::is_same<T, double>::value && axial_group<Def>() >= 0) {
+        if (pl.eqw) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 1, true>, BATCH>(pl, stream, occ);
       }
       return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
     }

@@ -1,0 +1,206 @@
+"""IEEE FP64 sweeps of the star / heat family with equal neighbour weights.
+
+When the six axial weights are bit-identical the compiled kernel evaluates
+w * (((x+ + x-) + (y+ + y-)) + (z+ + z-)) with the first two pair sums done
+as exact IEEE additions on the integer pipe (fp64_int.cuh).  These tests pin
+that path bit for bit: with weights 2, 1, 1 every product is exact, so each
+FMA is one correctly rounded addition and numpy can restate both evaluation
+orders exactly, over data that reaches every branch of the integer adder
+(subnormals, exact cancellations, overflow to infinity, infinities, NaNs,
+signed zeros, wide exponent gaps).  GSCL_FP64_INT_ADD=0 turns the path off:
+the kernel then takes one FMA per term in table order (+x, -x, +y, -y, +z,
+-z), which the same data checks too.  The oracle-parity tests of the heat
+operators (equal weights) run through this path as well."""
+import numpy as np
+import pytest
+
+from paper_1207_1746_b300 import binding as B
+from paper_1207_1746_b300 import inputs as I
+from paper_1207_1746_b300 import stencils as S
+
+pytestmark = pytest.mark.gpu
+
+H = (1, 1, 1)
+W0, W, WF = 2.0, 1.0, 1.0
+
+
+def heat_op(w0=W0, w=W, wf=WF):
+    t = [(0, 0, 0, 0, S.NONE, 0, w0)]
+    t += [(dx, dy, dz, 0, S.NONE, 0, w) for dx, dy, dz in S.X6]
+    t.append((0, 0, 0, 1, S.NONE, 0, wf))
+    return t
+
+
+def special_field(seed, n, halo, frac=0.3):
+    """Values of every class: normals over a wide exponent range, subnormals,
+    huge values whose pair sums overflow, infinities, NaNs, signed zeros and
+    neighbours that cancel exactly."""
+    rng = np.random.default_rng(seed)
+    shape = I.padded_shape(n, halo)
+    a = rng.uniform(-1.0, 1.0, size=shape) * np.exp2(rng.integers(-60, 61, size=shape).astype(np.float64))
+    pick = rng.random(shape)
+    cls = rng.integers(0, 8, size=shape)
+    special = pick < frac
+    sub = np.frombuffer(rng.integers(1, 1 << 52, size=a.size, dtype=np.uint64).tobytes(), dtype=np.float64)
+    sub = sub.reshape(shape) * np.where(rng.random(shape) < 0.5, -1.0, 1.0)
+    vals = [sub,                                            # subnormal
+            np.where(rng.random(shape) < 0.5, -1.0, 1.0) * 1.6e308 * rng.uniform(0.7, 1.0, size=shape),  # huge
+            np.full(shape, np.inf), np.full(shape, -np.inf), np.full(shape, np.nan),
+            np.zeros(shape), np.full(shape, -0.0),
+            np.exp2(rng.integers(-1074, -1020, size=shape).astype(np.float64))]  # tiny: subnormal sums
+    for c in range(8):
+        m = special & (cls == c)
+        a[m] = vals[c][m]
+    # exact cancellations: some x+ neighbours are minus their x- partner
+    flip = rng.random(shape) < 0.05
+    a[:, :, 2:][flip[:, :, 2:]] = -a[:, :, :-2][flip[:, :, 2:]]
+    return a
+
+
+def shifted(a, n, halo, dx, dy, dz):
+    nx, ny, nz = n
+    hx, hy, hz = halo
+    return a[hz + dz:hz + dz + nz, hy + dy:hy + dy + ny, hx + dx:hx + dx + nx]
+
+
+def expected(u, f, n, axial_sum, w0=W0, w=W, wf=WF):
+    """The kernel's evaluation order restated in numpy (exact products)."""
+    c = shifted(u, n, H, 0, 0, 0)
+    nb = [shifted(u, n, H, *d) for d in S.X6]
+    fc = shifted(f, n, H, 0, 0, 0)
+    with np.errstate(all="ignore"):
+        v = 0.0 + w0 * c
+        if axial_sum:
+            s = ((nb[0] + nb[1]) + (nb[2] + nb[3])) + (nb[4] + nb[5])
+            v = v + w * s
+        else:
+            for x in nb:
+                v = v + w * x
+        v = v + wf * fc
+    return v
+
+
+def sweep(u, f, n, op):
+    gu, gf = B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)
+    go = B.Grid(n, H, "f64").upload(np.zeros(I.padded_shape(n, H)))
+    B.do_all(op, [gu, gf], [go])
+    B.sync()
+    return I.interior_view(go.download().numpy(), n, H)
+
+
+def same_bits(got, want):
+    """Bit-identical, NaNs anywhere both have one (any payload)."""
+    nan_g, nan_w = np.isnan(got), np.isnan(want)
+    ok = (nan_g == nan_w) & (nan_g | (got.view(np.uint64) == want.view(np.uint64)))
+    return ok
+
+
+@pytest.fixture
+def compiled(monkeypatch):
+    monkeypatch.delenv("GSCL_GENERIC_ONLY", raising=False)
+    monkeypatch.delenv("GSCL_FP64_ARITH", raising=False)
+    monkeypatch.delenv("GSCL_FP64_INT_ADD", raising=False)
+    return monkeypatch
+
+
+@pytest.mark.parametrize("n", [(70, 45, 23), (64, 16, 3), (5, 3, 2), (257, 33, 9)])
+@pytest.mark.parametrize("frac", [0.0, 0.3])
+def test_axial_sum_bit_exact_over_every_value_class(compiled, n, frac):
+    u = special_field(400 + n[0], n, H, frac)
+    f = special_field(401 + n[0], n, H, frac * 0.3)
+    got = sweep(u, f, n, heat_op())
+    ok = same_bits(got, expected(u, f, n, True))
+    assert ok.all(), (int((~ok).sum()), np.argwhere(~ok)[:3].tolist())
+
+
+@pytest.mark.parametrize("n", [(70, 45, 23), (5, 3, 2)])
+def test_switch_off_gives_table_order(compiled, n):
+    compiled.setenv("GSCL_FP64_INT_ADD", "0")
+    u = special_field(500 + n[0], n, H, 0.3)
+    f = special_field(501 + n[0], n, H, 0.1)
+    got = sweep(u, f, n, heat_op())
+    ok = same_bits(got, expected(u, f, n, False))
+    assert ok.all(), (int((~ok).sum()), np.argwhere(~ok)[:3].tolist())
+
+
+def test_unequal_weights_keep_table_order(compiled):
+    """One neighbour weight of 2 among weights of 1 keeps one FMA per term in
+    table order (normal data: no product overflows)."""
+    n = (70, 45, 23)
+    u = special_field(600, n, H, 0.0)
+    f = special_field(601, n, H, 0.0)
+    op = heat_op()
+    op[3] = op[3][:6] + (2.0,)
+    got = sweep(u, f, n, op)
+    v = 0.0 + W0 * shifted(u, n, H, 0, 0, 0)
+    for t in op[1:7]:
+        v = v + t[6] * shifted(u, n, H, *t[:3])
+    v = v + WF * shifted(f, n, H, 0, 0, 0)
+    assert same_bits(got, v).all()
+
+
+@pytest.mark.parametrize("lam", [0.125, 1.0 / 6.0, 0.1])
+def test_heat_within_tolerance_of_both_orders(compiled, lam):
+    """Random data, the benchmark's heat weights: the axial-sum result and the
+    table-order result differ by a few roundings of the absolute stencil
+    (each is within 7 roundings of the exact sum)."""
+    n = (96, 40, 17)
+    u = I.random_interior(700, n, H, -1.0, 1.0, halo_value=0.25)
+    f = I.random_interior(701, n, H, -1.0, 1.0)
+    op = S.heat7(lam)
+    a = sweep(u, f, n, op)
+    compiled.setenv("GSCL_FP64_INT_ADD", "0")
+    b = sweep(u, f, n, op)
+    absst = abs(1 - 6 * lam) * np.abs(shifted(u, n, H, 0, 0, 0)) + lam * np.abs(shifted(f, n, H, 0, 0, 0))
+    for d in S.X6:
+        absst = absst + lam * np.abs(shifted(u, n, H, *d))
+    assert np.all(np.abs(a - b) <= 16 * 2.0 ** -53 * absst)
+
+
+def fused_op(wc, lam):
+    """The fused heat sweep's structure (value r = sum6 + wc u + f, u' = u +
+    lam r) with weights whose products are exact."""
+    t = [(dx, dy, dz, 0, S.NONE, S.VALUE, 1.0) for dx, dy, dz in S.X6]
+    t += [(0, 0, 0, 0, S.NONE, S.VALUE, wc), (0, 0, 0, 1, S.NONE, S.VALUE, 1.0)]
+    return t + [(0, 0, 0, 0, S.NONE, 0, 1.0), (0, 0, 0, S.VALUE, S.NONE, 0, lam)]
+
+
+def test_fused_residual_sweep_bit_exact(compiled):
+    """The fused sweep with its L2 norm: the value's axial group takes the
+    same path; u' bit for bit, the norm within the reduction's tolerance."""
+    n = (70, 45, 23)
+    u = special_field(800, n, H, 0.0)
+    f = special_field(801, n, H, 0.0)
+    gu, gf = B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)
+    go = B.Grid(n, H, "f64").upload(np.zeros(I.padded_shape(n, H)))
+    res = B.do_reduce(B.L2, fused_op(-4.0, 0.125), [gu, gf], [go])
+    B.sync()
+    got = I.interior_view(go.download().numpy(), n, H)
+    c = shifted(u, n, H, 0, 0, 0)
+    nb = [shifted(u, n, H, *d) for d in S.X6]
+    r = 0.0 + (((nb[0] + nb[1]) + (nb[2] + nb[3])) + (nb[4] + nb[5]))
+    r = r + (-4.0) * c
+    r = r + shifted(f, n, H, 0, 0, 0)
+    want = (0.0 + c) + 0.125 * r
+    assert same_bits(got, want).all()
+    norm = float(np.sqrt(np.sum(r * r)))
+    assert abs(res - norm) <= 1e-12 * norm
+
+
+def test_batch_matches_single_grid(compiled):
+    """A batch of the same operator takes the same path as gscl_do_all alone."""
+    shapes = [(33, 40, 35), (64, 17, 50), (7, 5, 3)]
+    insts, singles = [], []
+    for k, n in enumerate(shapes):
+        u = special_field(900 + k, n, H, 0.1)
+        f = special_field(950 + k, n, H, 0.0)
+        gu, gf = B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)
+        go = B.Grid(n, H, "f64").upload(np.zeros(I.padded_shape(n, H)))
+        insts.append(([gu, gf], [go]))
+        singles.append(sweep(u, f, n, heat_op()))
+    bt = B.Batch(heat_op(), insts)
+    bt.run(1)
+    B.sync()
+    for (ins, outs), n, want in zip(insts, shapes, singles):
+        got = I.interior_view(outs[0].download().numpy(), n, H)
+        assert same_bits(got, want).all()
