@@ -61,26 +61,29 @@ __host__ __device__ __forceinline__ unsigned long long fp64_add_int_bits(unsigne
   mbs |= (mbs << d) != mb ? 1ull : 0ull;
   const unsigned long long m = sub ? ma - mbs : ma + mbs;  // below 2^57
   // normalise the leading bit to position 55 (lz = -1 after a carry), but
-  // not below exponent 1
+  // not below exponent 1.  One shift serves both directions: after a carry
+  // the bit shifted out is ORed back as the sticky bit; after a left shift
+  // the OR is harmless (m's bit 0 is a sticky bit that can only be set when
+  // lz <= 1, and there it leaves the rounding decision unchanged).
   int lz = fp64_int_clz(m) - 8;
   lz = lz < ea1 - 1 ? lz : ea1 - 1;
-  const unsigned long long right = (m >> 1) | (m & 1ull);
-  const unsigned long long left = m << (lz > 0 ? lz : 0);
-  const unsigned long long mn = lz < 0 ? right : left;
+  const unsigned long long mn = ((m << (lz + 1)) >> 1) | (m & 1ull);
   const int e = ea1 - lz;
-  // round to nearest, ties to even, on guard / round / sticky; the exponent
-  // field takes a carry out of the significand (and a subnormal's missing
-  // hidden bit leaves it at 0)
-  const unsigned low = (unsigned)mn & 7u;
-  unsigned long long q = mn >> 3;
-  q += (low > 4u || (low == 4u && (q & 1ull))) ? 1ull : 0ull;
+  // round to nearest, ties to even: adding 3 + lsb carries out of the three
+  // extra bits exactly when they exceed one half, or equal it with an odd
+  // lsb.  The exponent field takes a carry out of the significand (and a
+  // subnormal's missing hidden bit leaves it at 0).
+  const unsigned long long q = (mn + 3ull + ((mn >> 3) & 1ull)) >> 3;
   unsigned long long r = (ua & kSign) | (((unsigned long long)(e - 1) << 52) + q);
-  // overflow: the normalised exponent reached 2047
-  r = e >= 2047 ? (ua & kSign) | kInf : r;
   // an exact zero: +0 for opposite signs, else the common sign
   r = m == 0ull ? (sub ? 0ull : (ua & kSign)) : r;
-  // an infinity or NaN operand (it is a, the larger magnitude)
-  r = ea == 0x7ffu ? (((ua & kFrac) != 0ull || (ua ^ ub) == kSign) ? kNaN : ua) : r;
+  // overflow (the normalised exponent reached 2047) and infinite or NaN
+  // operands (a has the larger magnitude): an infinity of a's sign, or the
+  // default NaN for a NaN operand and for inf - inf
+  if (e >= 2047 || ea == 0x7ffu) {
+    const bool nan = ea == 0x7ffu && ((ua & kFrac) != 0ull || (ua ^ ub) == kSign);
+    r = nan ? kNaN : ((ua & kSign) | kInf);
+  }
   return r;
 }
 

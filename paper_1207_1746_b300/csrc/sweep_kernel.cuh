@@ -457,6 +457,18 @@ template <class Def, int XS = 1, bool EQ = false>
 struct StaticOp {
   static constexpr int kXStep = XS;
   static constexpr int kAxial = EQ ? axial_group<Def>() : -1;
+  // the group is evaluated after the last coefficient-free term of its
+  // destination's block, so the other terms accumulate while its integer
+  // additions run and one FMA follows the sum
+  __host__ __device__ static constexpr int axial_at() {
+    if (kAxial < 0) return -1;
+    int j = kAxial + 5;
+    while (j + 1 < Def::NT && Def::table.t[j + 1].out == Def::table.t[kAxial].out && Def::table.t[j + 1].coef < 0 &&
+           Def::table.t[j + 1].in >= 0)
+      ++j;
+    return j;
+  }
+  static constexpr int kAxialAt = axial_at();
   static_assert(!EQ || (XS == 1 && kAxial >= 0), "the axial-sum evaluation needs an axial group and XS = 1");
   static constexpr int kGroup = 1;
   static constexpr int kRowsPerSlot = 1;
@@ -646,22 +658,42 @@ struct StaticOp {
                                               typename Arith<T>::A (&v)[VX],
                                               typename Arith<T>::A (&o)[kMaxOut][VX],
                                               typename Arith<T>::A (&g)[VX]) {
+    using A = typename Arith<T>::A;
+    if constexpr (kAxial >= 0 && I >= kAxial && I < kAxial + 6) {
+      // the axial group: its six terms are one weighted sum at kAxialAt
+    } else {
+      term_body<T, VX, VY, r, I>(P, ws, ring, smod, cslot, row0, lane, zq, v, o, g);
+    }
+    if constexpr (kAxialAt >= 0 && I == kAxialAt) {
+      constexpr int out = Def::table.t[kAxial].out;
+      const A w = ws(P, kAxial);
+      A x[VX];
+      axial_sum<T, VX, VY, r>(P, ring, smod, cslot, row0, lane, zq, v, x);
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        if constexpr (out < 0) v[e] = fma(w, x[e], v[e]);
+        else o[out][e] = fma(w, x[e], o[out][e]);
+      }
+    }
+  }
+
+  // One term's contribution (a term outside the axial group).
+  template <typename T, int VX, int VY, int r, int I, class WS>
+  __device__ static __forceinline__ void term_body(const SweepParams &P, const WS &ws, const T *ring, int smod,
+                                                   int cslot, int row0, int lane,
+                                                   const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                                   typename Arith<T>::A (&v)[VX],
+                                                   typename Arith<T>::A (&o)[kMaxOut][VX],
+                                                   typename Arith<T>::A (&g)[VX]) {
     const int row = row0 + r;
     const int col = column(lane, r);
     constexpr int ES = 32 * XS;  // element stride of a thread's columns
     using A = typename Arith<T>::A;
     constexpr OpTerm t = Def::table.t[I];
     constexpr int vec = 16 / (int)sizeof(T);
-    if constexpr (kAxial >= 0 && I > kAxial && I < kAxial + 6) {
-      return;  // summed with the group's first term
-    }
     const A w = ws(P, I);
     A x[VX];
-    if constexpr (kAxial >= 0 && I == kAxial) {
-      axial_sum<T, VX, VY, r>(P, ring, smod, cslot, row0, lane, zq, v, x);
-    } else {
-      load_x<T, VX, VY, r, I>(P, ring, smod, cslot, row0, lane, zq, v, x);
-    }
+    load_x<T, VX, VY, r, I>(P, ring, smod, cslot, row0, lane, zq, v, x);
     if constexpr (t.coef >= 0) {
 #pragma unroll
       for (int e = 0; e < VX; ++e) g[e] = run_first(I) ? w * x[e] : fma(w, x[e], g[e]);

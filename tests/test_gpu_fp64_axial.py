@@ -2,7 +2,8 @@
 
 When the six axial weights are bit-identical the compiled kernel evaluates
 w * (((x+ + x-) + (y+ + y-)) + (z+ + z-)) with the first two pair sums done
-as exact IEEE additions on the integer pipe (fp64_int.cuh).  These tests pin
+as exact IEEE additions on the integer pipe (fp64_int.cuh), and adds it
+after the other terms of its destination.  These tests pin
 that path bit for bit: with weights 2, 1, 1 every product is exact, so each
 FMA is one correctly rounded addition and numpy can restate both evaluation
 orders exactly, over data that reaches every branch of the integer adder
@@ -71,12 +72,13 @@ def expected(u, f, n, axial_sum, w0=W0, w=W, wf=WF):
     with np.errstate(all="ignore"):
         v = 0.0 + w0 * c
         if axial_sum:
+            v = v + wf * fc
             s = ((nb[0] + nb[1]) + (nb[2] + nb[3])) + (nb[4] + nb[5])
             v = v + w * s
         else:
             for x in nb:
                 v = v + w * x
-        v = v + wf * fc
+            v = v + wf * fc
     return v
 
 
@@ -178,9 +180,9 @@ def test_fused_residual_sweep_bit_exact(compiled):
     got = I.interior_view(go.download().numpy(), n, H)
     c = shifted(u, n, H, 0, 0, 0)
     nb = [shifted(u, n, H, *d) for d in S.X6]
-    r = 0.0 + (((nb[0] + nb[1]) + (nb[2] + nb[3])) + (nb[4] + nb[5]))
-    r = r + (-4.0) * c
+    r = 0.0 + (-4.0) * c
     r = r + shifted(f, n, H, 0, 0, 0)
+    r = r + (((nb[0] + nb[1]) + (nb[2] + nb[3])) + (nb[4] + nb[5]))
     want = (0.0 + c) + 0.125 * r
     assert same_bits(got, want).all()
     norm = float(np.sqrt(np.sum(r * r)))
