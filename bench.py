@@ -1308,8 +1308,11 @@ def main():
         pts = r["points"]
         fma = B_fma()
         # a colour-compacted half-sweep evaluates the 8-FMA operator at the
-        # elements of its colour: 8 FP64-pipe operations per point and iteration
+        # elements of its colour: 8 operations per point and iteration (the
+        # algorithmic count); with equal neighbour weights two of them are
+        # additions on the integer pipe, so the FP64 pipe executes 6
         g_ops = 8 * pts / (t * 1e-3) / 1e9
+        fp64_ops = 6 if os.environ.get("GSCL_FP64_INT_ADD", "1")[:1] != "0" else 8
         gbs = 32 * pts / (t * 1e-3) / 1e9   # per half-sweep: u read, f and u' at half the points
         line = {"metric": "GPoint-updates/s", "value": round(dist.world * pts / (t * 1e-3) / 1e9, 3),
                 "unit": "GPoint-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -1327,6 +1330,9 @@ def main():
                              "traffic_note": "DRAM bytes per iteration: two half-sweeps of the ncu capture",
                              "peak_source": "measured FP64 FMA rate (gscl_fma_throughput); 8 FMAs per point "
                                             "and iteration (each colour evaluated once)",
+                             "fp64_pipe_ops_per_point": fp64_ops,
+                             "fp64_pipe_frac": (round(g_ops * fp64_ops / 8 * 2 / 1e3 / fma, 4)
+                                                if fma == fma else None),
                              "hbm_gbs": round(gbs, 1)},
                 "uncompacted_iteration_ms": round(r["uncompacted_iter_ms"], 4) if "uncompacted_iter_ms" in r else None,
                 "pair_arithmetic_iteration_ms": round(r["pair_iter_ms"], 4) if "pair_iter_ms" in r else None,

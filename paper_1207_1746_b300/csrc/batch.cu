@@ -165,7 +165,7 @@ gscl_status build(Batch *bt) {
   bt->buf_a.assign(n, nullptr);
   bt->buf_b.assign(n, nullptr);
   TileCfg cfg = bt->cfg;
-  cfg.colored = bt->colored;
+  bool any_eqw = false;  // some instance has equal axial weights (per-instance flags in the weight rows)
   bool tb_ok = !bt->colored && bt->n_in == 1 && bt->n_out == 1;
   bool tb3_ok = !bt->colored && bt->n_out == 1;
   std::vector<InstDesc> tabs3[2];
@@ -204,8 +204,7 @@ gscl_status build(Batch *bt) {
           if (gscl_status s = make_plan(bd, bt->has_value, &pl, cfg)) return s;
         }
         bt->base = pl;
-      } else if (pl.op != bt->base.op || pl.eqw != bt->base.eqw || pl.smem != bt->base.smem ||
-                 pl.threads != bt->base.threads ||
+      } else if (pl.op != bt->base.op || pl.smem != bt->base.smem || pl.threads != bt->base.threads ||
                  pl.P.R != bt->base.P.R || memcmp(pl.P.in_bw, bt->base.P.in_bw, sizeof pl.P.in_bw) != 0 ||
                  memcmp(pl.P.in_bh, bt->base.P.in_bh, sizeof pl.P.in_bh) != 0) {
         return fail(GSCL_ERR_SHAPE, "instance %d plans a different tile shape", i);
@@ -236,6 +235,8 @@ gscl_status build(Batch *bt) {
           wrows[i].wf[k] = pl.P.terms[k].wf;
           wrows[i].wl[k] = pl.P.terms[k].wl;
         }
+        wrows[i].eq = pl.eqw ? 1 : 0;
+        any_eqw = any_eqw || pl.eqw;
       }
     }
     bt->buf_a[i] = b.in[0].buf;
@@ -243,6 +244,7 @@ gscl_status build(Batch *bt) {
   }
   Plan &base = bt->base;
   base.batch = true;
+  base.eqw = any_eqw;
   // one wave of CTAs
   int occ = 0;
   const int red_probe = bt->n_out ? RED_NONE : RED_L2;

@@ -12,10 +12,11 @@
 // add or subtract the significands, normalise (a carry shifts right by one
 // position, keeping the sticky bit; a cancellation shifts left by the
 // leading-zero count, and is exact whenever it shifts by more than one),
-// round on the three extra bits with ties to even, and repack.  The code has
-// no branches: both normalisations are computed and one is selected, and the
+// round on the three extra bits with ties to even, and repack.  One shift
+// normalises in either direction, the rounding is an addition, and the
 // exponent field absorbs a rounding carry (the packed value is
-// (e - 1) * 2^52 + m with the hidden bit in m).
+// (e - 1) * 2^52 + m with the hidden bit in m); only the rare special cases
+// are a select at the end.
 //
 // It is exact for every input: subnormal operands align with exponent 1 and
 // no hidden bit, a result below the normal range keeps exponent 1 (a sum

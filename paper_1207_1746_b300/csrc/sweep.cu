@@ -238,10 +238,10 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   const uint32_t smask = static_centre_mask(pl->op);
   const bool ieee64 = g0.dtype == GSCL_F64 && !pl->pair;
   // IEEE FP64 operators of the star / heat family whose six neighbour
-  // weights are bit-identical: the axial-sum evaluation (static_ops.h), not
-  // for colour sweeps (a coloured batch's instances have their own weights)
+  // weights are bit-identical: the axial-sum evaluation (static_ops.h; a
+  // batch records this per instance)
   pl->eqw = false;
-  if (ieee64 && !compact && !cfg.colored && pl->op != OP_GENERIC && fp64_int_add()) {
+  if (ieee64 && pl->op != OP_GENERIC && fp64_int_add()) {
     const int ga = static_axial_group(pl->op);
     if (ga >= 0) {
       bool eq = true;
@@ -550,7 +550,6 @@ gscl_status gscl_do_colored(const gscl_stencil *op, const gscl_grid *in, int32_t
   Plan pl;
   TileCfg cfg;
   cfg.compact = colour_compact();
-  cfg.colored = true;
   if (gscl_status s = make_plan(b, false, &pl, cfg)) return s;
   for (int h = 0; h < half_sweeps; ++h) {
     pl.P.color = (color + h) & 1;

@@ -25,7 +25,6 @@ struct TileCfg {
   bool generic = false;  // interpret the term list even if a compiled structure matches
   bool narrow = false;   // batches, FP32 / BF16: 64-column tiles with 4 rows per warp
   bool compact = false;  // red-black sweeps, IEEE FP64, star family: only the colour's elements
-  bool colored = false;  // colour sweeps (a coloured batch's instances carry their own weights)
 };
 
 bool overlaps(const Grid &a, const Grid &b);

@@ -85,6 +85,7 @@ struct InstWeights {
   double wd[kMaxTerms];
   float wf[kMaxTerms];
   float wl[kMaxTerms];  // pair arithmetic: wd - (double)wf
+  int32_t eq;           // equal axial weights: the axial-sum evaluation (StaticOp<Def, XS, true>)
 };
 
 struct SweepParams {
@@ -153,15 +154,21 @@ template <typename A>
 struct ParamWeights {
   __device__ __forceinline__ void load(const InstWeights *) {}
   __device__ __forceinline__ A operator()(const SweepParams &P, int i) const { return term_weight(P.terms[i], A(0)); }
+  // single grids: the axial-sum kernel is launched only for equal weights
+  __device__ static constexpr bool eq() { return true; }
 };
 template <typename A, int N>
 struct RegWeights {
   A v[N];
+  bool e;
   __device__ __forceinline__ void load(const InstWeights *w) {
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = inst_weight(*w, i, A(0));
+    e = w->eq != 0;
   }
   __device__ __forceinline__ A operator()(const SweepParams &, int i) const { return v[i]; }
+  // batches: per instance (a coloured batch's instances have their own weights)
+  __device__ __forceinline__ bool eq() const { return e; }
 };
 template <typename A>
 struct RowWeights {
@@ -469,7 +476,7 @@ struct StaticOp {
     return j;
   }
   static constexpr int kAxialAt = axial_at();
-  static_assert(!EQ || (XS == 1 && kAxial >= 0), "the axial-sum evaluation needs an axial group and XS = 1");
+  static_assert(!EQ || kAxial >= 0, "the axial-sum evaluation needs an axial group");
   static constexpr int kGroup = 1;
   static constexpr int kRowsPerSlot = 1;
   static constexpr int kTerms = Def::NT;
@@ -660,11 +667,15 @@ struct StaticOp {
                                               typename Arith<T>::A (&g)[VX]) {
     using A = typename Arith<T>::A;
     if constexpr (kAxial >= 0 && I >= kAxial && I < kAxial + 6) {
-      // the axial group: its six terms are one weighted sum at kAxialAt
+      // the axial group: its six terms are one weighted sum at kAxialAt; a
+      // batch instance with unequal weights takes them in table order, as
+      // its single-grid call does
+      if (!ws.eq()) term_body<T, VX, VY, r, I>(P, ws, ring, smod, cslot, row0, lane, zq, v, o, g);
     } else {
       term_body<T, VX, VY, r, I>(P, ws, ring, smod, cslot, row0, lane, zq, v, o, g);
     }
     if constexpr (kAxialAt >= 0 && I == kAxialAt) {
+      if (!ws.eq()) return;
       constexpr int out = Def::table.t[kAxial].out;
       const A w = ws(P, kAxial);
       A x[VX];
@@ -1583,7 +1594,7 @@ struct Plan {
   bool pair = false;          // FP64 grids in pair arithmetic (fixed when the plan is made)
   bool compact = false;       // colour-compacted red-black sweep (XS = 2 tiles)
   bool vec = false;           // vector lanes (StaticOpV): FP32 / BF16 compile-time operators
-  bool eqw = false;           // IEEE FP64, equal axial weights: StaticOp<Def, 1, true>
+  bool eqw = false;           // IEEE FP64, equal axial weights: StaticOp<Def, XS, true> (batches: some instance)
   int tile_x = 0, tile_y = 0; // core elements per CTA tile
 };
 
@@ -1726,7 +1737,12 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       // colour-compacted red-black sweeps of the star family on FP64 grids
       // (IEEE or pair arithmetic), single grids and coloured batches
       if constexpr (RED == RED_NONE && CompactCapable<Def>::value) {
-        if (pl.compact) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
+        if (pl.compact) {
+          if constexpr (std::is_same<T, double>::value && axial_group<Def>() >= 0) {
+            if (pl.eqw) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2, true>, BATCH>(pl, stream, occ);
+          }
+          return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
+        }
       }
       // equal axial weights: the neighbour sum partly on the integer pipe
       if constexpr (std::is_same<T, double>::value && axial_group<Def>() >= 0) {

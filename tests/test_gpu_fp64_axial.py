@@ -206,3 +206,52 @@ def test_batch_matches_single_grid(compiled):
     for (ins, outs), n, want in zip(insts, shapes, singles):
         got = I.interior_view(outs[0].download().numpy(), n, H)
         assert same_bits(got, want).all()
+
+
+def colour_mask(n, color):
+    nx, ny, nz = n
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    return ((i + j + k) & 1) == color
+
+
+@pytest.mark.parametrize("compact", ["1", "0"])
+@pytest.mark.parametrize("n", [(70, 45, 23), (5, 3, 2)])
+def test_colored_sweep_bit_exact(compiled, compact, n):
+    """Red-black sweeps in place (the colour-compacted kernel and the
+    colour-predicated one): the colour's points take the axial-sum value of
+    the grid as it was, the other colour keeps its bits."""
+    compiled.setenv("GSCL_COLOR_COMPACT", compact)
+    u = special_field(1000 + n[0], n, H, 0.2)
+    f = special_field(1001 + n[0], n, H, 0.1)
+    gu, gf = B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)
+    cur = u.copy()
+    for color in (1, 0):
+        B.do_colored(heat_op(), [gu, gf], [gu], color=color)
+        B.sync()
+        v = expected(cur, f, n, True)
+        inner = I.interior_view(cur, n, H)
+        inner[...] = np.where(colour_mask(n, color), v, inner)
+        ok = same_bits(I.interior_view(gu.download().numpy(), n, H), inner)
+        assert ok.all(), (color, int((~ok).sum()), np.argwhere(~ok)[:3].tolist())
+
+
+def test_colored_batch_mixed_weights_equals_each_instance_alone(compiled):
+    """A coloured batch whose instances have equal and unequal neighbour
+    weights: each instance takes the evaluation its single call takes (a flag
+    per instance), bit for bit."""
+    sides = [(70, 21, 19), (33, 64, 12), (5, 3, 2)]
+    ops = [heat_op(), heat_op(), heat_op()]
+    ops[1][3] = ops[1][3][:6] + (2.0,)  # unequal: table order
+    us = [special_field(1100 + k, n, H, 0.0) for k, n in enumerate(sides)]
+    fs = [special_field(1150 + k, n, H, 0.0) for k, n in enumerate(sides)]
+    alone = []
+    for op, n, u, f in zip(ops, sides, us, fs):
+        gu, gf = B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)
+        B.do_colored(op, [gu, gf], [gu], color=0, half_sweeps=3)
+        alone.append(gu.download().numpy())
+    grids = [(B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)) for n, u, f in zip(sides, us, fs)]
+    batch = B.ColoredBatch(ops, [([gu, gf], [gu]) for gu, gf in grids])
+    batch.run_colored(0, 3)
+    B.sync()
+    for k, ((gu, _), want) in enumerate(zip(grids, alone)):
+        assert same_bits(gu.download().numpy(), want).all(), k
