@@ -206,6 +206,100 @@ GSCL_HD constexpr int axial_group() {
   return -1;
 }
 
+// Coefficient groups: consecutive terms of one coefficient run (one
+// coefficient grid, one destination) reading one input at nonzero offsets of
+// one class (the same |dx|, |dy|, |dz| up to order), four of them or two: the
+// climate operator's biharmonic rings and its vertical pair.  With the four
+// weights bit-identical a group of four is summed as (x0 + x1) + (x2 + x3)
+// with the first addition on the integer pipe; a pair whose weights are
+// opposite is differenced, x0 - x1, on the integer pipe.
+template <class Def>
+GSCL_HD constexpr int offset_class(int i) {
+  const OpTerm &t = Def::table.t[i];
+  int a = t.dx < 0 ? -t.dx : t.dx, b = t.dy < 0 ? -t.dy : t.dy, c = t.dz < 0 ? -t.dz : t.dz;
+  if (a > b) { const int x = a; a = b; b = x; }
+  if (b > c) { const int x = b; b = c; c = x; }
+  if (a > b) { const int x = a; a = b; b = x; }
+  return (a * 64 + b) * 64 + c;
+}
+template <class Def>
+GSCL_HD constexpr bool coef_link(int i, int j) {
+  const OpTerm &a = Def::table.t[i], &b = Def::table.t[j];
+  return a.in >= 0 && a.coef >= 0 && a.in == b.in && a.coef == b.coef && a.out == b.out &&
+         offset_class<Def>(i) != 0 && offset_class<Def>(i) == offset_class<Def>(j);
+}
+template <class Def>
+GSCL_HD constexpr int coef_group_len(int s) {
+  int n = 1;
+  while (s + n < Def::NT && coef_link<Def>(s, s + n)) ++n;
+  return n;
+}
+// the first term of the coefficient group holding term i, or -1
+template <class Def>
+GSCL_HD constexpr int coef_group_start(int i) {
+  if (i < 0 || i >= Def::NT) return -1;
+  int s = i;
+  while (s > 0 && coef_link<Def>(s - 1, s)) --s;
+  const int n = coef_group_len<Def>(s);
+  return (n == 2 || n == 4) ? s : -1;
+}
+template <class Def>
+GSCL_HD constexpr bool has_groups() {
+  bool any = axial_group<Def>() >= 0;
+  for (int i = 0; i < Def::NT; ++i) any = any || coef_group_start<Def>(i) >= 0;
+  return any;
+}
+// the length of the coefficient group starting at each term (0 elsewhere)
+template <int N>
+struct IntTable {
+  int v[N];
+};
+template <class Def>
+constexpr IntTable<Def::NT> coef_group_lens() {
+  IntTable<Def::NT> r{};
+  for (int i = 0; i < Def::NT; ++i) r.v[i] = coef_group_start<Def>(i) == i ? coef_group_len<Def>(i) : 0;
+  return r;
+}
+
+// Whether the weights (w[i]: table term i's weight) allow the group
+// evaluation: the axial group's six equal, every group of four equal, every
+// pair opposite; false for an operator without groups.
+template <class Def>
+bool group_weights_ok(const double *w) {
+  auto bits = [](double x) {
+    unsigned long long u = 0;
+    __builtin_memcpy(&u, &x, sizeof u);
+    return u;
+  };
+  if constexpr (!has_groups<Def>()) return false;
+  constexpr int ga = axial_group<Def>();
+  if (ga >= 0)
+    for (int k = 1; k < 6; ++k)
+      if (bits(w[ga + k]) != bits(w[ga])) return false;
+  constexpr IntTable<Def::NT> lens = coef_group_lens<Def>();
+  for (int i = 0; i < Def::NT; ++i) {
+    const int n = lens.v[i];
+    if (n == 2 && bits(w[i + 1]) != (bits(w[i]) ^ (1ull << 63))) return false;
+    if (n == 4)
+      for (int k = 1; k < 4; ++k)
+        if (bits(w[i + k]) != bits(w[i])) return false;
+  }
+  return true;
+}
+
+inline bool static_group_weights_ok(int op, const double *w) {
+  switch (op) {
+    case OP_HEAT7_RHS: return group_weights_ok<OpHeat7Rhs>(w);
+    case OP_STAR7: return group_weights_ok<OpStar7>(w);
+    case OP_JACOBI7_RHS: return group_weights_ok<OpJacobi7Rhs>(w);
+    case OP_CLIMATE: return group_weights_ok<OpClimate>(w);
+    case OP_HEAT7_RHS_FUSED: return group_weights_ok<OpHeat7RhsFused>(w);
+    case OP_HEAT7_FUSED: return group_weights_ok<OpHeat7Fused>(w);
+    case OP_RESIDUAL7_RHS: return group_weights_ok<OpResidual7Rhs>(w);
+  }
+  return false;
+}
+
 inline int static_axial_group(int op) {
   switch (op) {
     case OP_HEAT7_RHS: return axial_group<OpHeat7Rhs>();

@@ -237,17 +237,14 @@ gscl_status make_plan(const Bound &b, bool reduce, Plan *pl, TileCfg cfg) {
   // kernel reads every input from the plane ring)
   const uint32_t smask = static_centre_mask(pl->op);
   const bool ieee64 = g0.dtype == GSCL_F64 && !pl->pair;
-  // IEEE FP64 operators of the star / heat family whose six neighbour
-  // weights are bit-identical: the axial-sum evaluation (static_ops.h; a
-  // batch records this per instance)
+  // IEEE FP64 compile-time operators whose term groups have equal (pairs:
+  // opposite) weights: the group evaluation with some additions on the
+  // integer pipe (static_ops.h; a batch records this per instance)
   pl->eqw = false;
   if (ieee64 && pl->op != OP_GENERIC && fp64_int_add()) {
-    const int ga = static_axial_group(pl->op);
-    if (ga >= 0) {
-      bool eq = true;
-      for (int k = 1; k < 6; ++k) eq = eq && memcmp(&terms[perm[ga + k]].w, &terms[perm[ga]].w, sizeof(double)) == 0;
-      pl->eqw = eq;
-    }
+    double wt[kMaxTerms];
+    for (size_t i = 0; i < perm.size() && i < (size_t)kMaxTerms; ++i) wt[i] = terms[perm[i]].w;
+    pl->eqw = static_group_weights_ok(pl->op, wt);
   }
   const uint32_t cmask =
       (compact || (ieee64 && __builtin_popcount(smask) < kCentreFp64Min)) ? 0u : smask;

@@ -476,7 +476,7 @@ struct StaticOp {
     return j;
   }
   static constexpr int kAxialAt = axial_at();
-  static_assert(!EQ || kAxial >= 0, "the axial-sum evaluation needs an axial group");
+  static_assert(!EQ || has_groups<Def>(), "the group evaluation needs a term group");
   static constexpr int kGroup = 1;
   static constexpr int kRowsPerSlot = 1;
   static constexpr int kTerms = Def::NT;
@@ -658,6 +658,31 @@ struct StaticOp {
     for (int e = 0; e < VX; ++e) x[e] = (fp64_add_int(x0[e], x1[e]) + fp64_add_int(x2[e], x3[e])) + (x4[e] + x5[e]);
   }
 
+  // A coefficient group's values combined: four as (x0 + x1) + (x2 + x3), a
+  // pair as x0 - x1; the first addition (the difference) runs on the integer
+  // pipe (exact IEEE arithmetic, fp64_int.cuh).
+  template <typename T, int VX, int VY, int r, int G, int N>
+  __device__ static __forceinline__ void coef_group_sum(const SweepParams &P, const T *ring, int smod, int cslot,
+                                                        int row0, int lane,
+                                                        const typename Arith<T>::A (&zq)[kQueue][VY][VX],
+                                                        const typename Arith<T>::A (&v)[VX],
+                                                        typename Arith<T>::A (&x)[VX]) {
+    using A = typename Arith<T>::A;
+    A x0[VX], x1[VX];
+    load_x<T, VX, VY, r, G + 0>(P, ring, smod, cslot, row0, lane, zq, v, x0);
+    load_x<T, VX, VY, r, G + 1>(P, ring, smod, cslot, row0, lane, zq, v, x1);
+    if constexpr (N == 2) {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = fp64_add_int(x0[e], -x1[e]);
+    } else {
+      A x2[VX], x3[VX];
+      load_x<T, VX, VY, r, G + 2>(P, ring, smod, cslot, row0, lane, zq, v, x2);
+      load_x<T, VX, VY, r, G + 3>(P, ring, smod, cslot, row0, lane, zq, v, x3);
+#pragma unroll
+      for (int e = 0; e < VX; ++e) x[e] = fp64_add_int(x0[e], x1[e]) + (x2[e] + x3[e]);
+    }
+  }
+
   // Term I at tile row row0 + r of this thread's VY rows.
   template <typename T, int VX, int VY, int r, int I, class WS>
   __device__ static __forceinline__ void term(const SweepParams &P, const WS &ws, const T *ring, int smod, int cslot,
@@ -666,7 +691,20 @@ struct StaticOp {
                                               typename Arith<T>::A (&o)[kMaxOut][VX],
                                               typename Arith<T>::A (&g)[VX]) {
     using A = typename Arith<T>::A;
-    if constexpr (kAxial >= 0 && I >= kAxial && I < kAxial + 6) {
+    constexpr int cg = EQ ? coef_group_start<Def>(I) : -1;
+    if constexpr (cg >= 0) {
+      // a coefficient group: one weighted sum (or difference) at its first
+      // term; a batch instance whose weights do not allow it takes the terms
+      // one by one, as its single-grid call does
+      if (!ws.eq()) {
+        term_body<T, VX, VY, r, I>(P, ws, ring, smod, cslot, row0, lane, zq, v, o, g);
+      } else if constexpr (I == cg) {
+        constexpr int n = coef_group_len<Def>(cg);
+        A x[VX];
+        coef_group_sum<T, VX, VY, r, cg, n>(P, ring, smod, cslot, row0, lane, zq, v, x);
+        accumulate<T, VX, r, cg, cg + n - 1>(P, ring, smod, cslot, row0, lane, ws(P, cg), x, v, o, g);
+      }
+    } else if constexpr (kAxial >= 0 && I >= kAxial && I < kAxial + 6) {
       // the axial group: its six terms are one weighted sum at kAxialAt; a
       // batch instance with unequal weights takes them in table order, as
       // its single-grid call does
@@ -696,19 +734,32 @@ struct StaticOp {
                                                    typename Arith<T>::A (&v)[VX],
                                                    typename Arith<T>::A (&o)[kMaxOut][VX],
                                                    typename Arith<T>::A (&g)[VX]) {
-    const int row = row0 + r;
-    const int col = column(lane, r);
-    constexpr int ES = 32 * XS;  // element stride of a thread's columns
     using A = typename Arith<T>::A;
-    constexpr OpTerm t = Def::table.t[I];
-    constexpr int vec = 16 / (int)sizeof(T);
     const A w = ws(P, I);
     A x[VX];
     load_x<T, VX, VY, r, I>(P, ring, smod, cslot, row0, lane, zq, v, x);
+    accumulate<T, VX, r, I, I>(P, ring, smod, cslot, row0, lane, w, x, v, o, g);
+  }
+
+  // w x added for table terms IF .. IL (one term, or a group summed into x):
+  // into the run's sum g (then times the coefficient at the run's last
+  // term), or into the destination.
+  template <typename T, int VX, int r, int IF, int IL>
+  __device__ static __forceinline__ void accumulate(const SweepParams &P, const T *ring, int smod, int cslot,
+                                                    int row0, int lane, typename Arith<T>::A w,
+                                                    const typename Arith<T>::A (&x)[VX],
+                                                    typename Arith<T>::A (&v)[VX],
+                                                    typename Arith<T>::A (&o)[kMaxOut][VX],
+                                                    typename Arith<T>::A (&g)[VX]) {
+    const int row = row0 + r;
+    const int col = column(lane, r);
+    constexpr int ES = 32 * XS;  // element stride of a thread's columns
+    constexpr OpTerm t = Def::table.t[IL];
+    constexpr int vec = 16 / (int)sizeof(T);
     if constexpr (t.coef >= 0) {
 #pragma unroll
-      for (int e = 0; e < VX; ++e) g[e] = run_first(I) ? w * x[e] : fma(w, x[e], g[e]);
-      if constexpr (run_last(I)) {
+      for (int e = 0; e < VX; ++e) g[e] = run_first(IF) ? w * x[e] : fma(w, x[e], g[e]);
+      if constexpr (run_last(IL)) {
         constexpr int RXc = radius(0, t.coef), RYc = radius(1, t.coef);
         constexpr int AXc = (RXc + vec - 1) / vec * vec;
         constexpr int BWc = ES * VX + 2 * AXc;
@@ -1738,14 +1789,14 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       // (IEEE or pair arithmetic), single grids and coloured batches
       if constexpr (RED == RED_NONE && CompactCapable<Def>::value) {
         if (pl.compact) {
-          if constexpr (std::is_same<T, double>::value && axial_group<Def>() >= 0) {
+          if constexpr (std::is_same<T, double>::value && has_groups<Def>()) {
             if (pl.eqw) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2, true>, BATCH>(pl, stream, occ);
           }
           return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
         }
       }
       // equal axial weights: the neighbour sum partly on the integer pipe
-      if constexpr (std::is_same<T, double>::value && axial_group<Def>() >= 0) {
+      if constexpr (std::is_same<T, double>::value && has_groups<Def>()) {
         if (pl.eqw) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 1, true>, BATCH>(pl, stream, occ);
       }
       return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);

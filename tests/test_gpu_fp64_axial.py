@@ -255,3 +255,66 @@ def test_colored_batch_mixed_weights_equals_each_instance_alone(compiled):
     B.sync()
     for k, ((gu, _), want) in enumerate(zip(grids, alone)):
         assert same_bits(gu.download().numpy(), want).all(), k
+
+
+HC = (2, 2, 1)
+BIH = ([((0, 0), 20.0)] + [((a, b), -8.0) for a, b in ((1, 0), (-1, 0), (0, 1), (0, -1))]
+       + [((a, b), 2.0) for a, b in ((1, 1), (1, -1), (-1, 1), (-1, -1))]
+       + [((a, b), 1.0) for a, b in ((2, 0), (-2, 0), (0, 2), (0, -2))])
+
+
+def climate_expected(q, kap, w, t, n, groups):
+    """The climate operator (dt = dz = 1) in the kernel's order, with exact
+    products (kappa and w powers of two): per output, the unit term, the
+    biharmonic run times kappa (its rings of four summed as (x0 + x1) +
+    (x2 + x3) when grouped), the vertical pair times w (differenced when
+    grouped), the tendency."""
+    outs = []
+    kc, wc = shifted(kap, n, HC, 0, 0, 0), shifted(w, n, HC, 0, 0, 0)
+    with np.errstate(all="ignore"):
+        for m in range(3):
+            def x(dx, dy, dz=0):
+                return shifted(q[m], n, HC, dx, dy, dz)
+            v = 0.0 + x(0, 0)
+            g = -BIH[0][1] * x(0, 0)
+            for k in (1, 5, 9):
+                ring = BIH[k:k + 4]
+                if groups:
+                    s = (x(*ring[0][0]) + x(*ring[1][0])) + (x(*ring[2][0]) + x(*ring[3][0]))
+                    g = g + (-ring[0][1]) * s
+                else:
+                    for off, c in ring:
+                        g = g + (-c) * x(*off)
+            v = v + kc * g
+            if groups:
+                g2 = -0.5 * (x(0, 0, 1) - x(0, 0, -1))
+            else:
+                g2 = -0.5 * x(0, 0, 1)
+                g2 = g2 + 0.5 * x(0, 0, -1)
+            v = v + wc * g2
+            outs.append(v + shifted(t[m], n, HC, 0, 0, 0))
+    return outs
+
+
+@pytest.mark.parametrize("int_add", ["1", "0"])
+@pytest.mark.parametrize("n", [(70, 45, 9), (5, 3, 2)])
+def test_climate_groups_bit_exact(compiled, int_add, n):
+    """The 8 -> 3 climate operator: its biharmonic rings of four equal
+    weights summed with one integer-pipe addition each and its vertical pair
+    differenced on the integer pipe (GSCL_FP64_INT_ADD=0: one FMA per term),
+    bit for bit against numpy in the same order."""
+    compiled.setenv("GSCL_FP64_INT_ADD", int_add)
+    rng = np.random.default_rng(1200 + n[0])
+    shape = I.padded_shape(n, HC)
+    q = [special_field(1210 + m, n, HC, 0.0) for m in range(3)]
+    t = [special_field(1220 + m, n, HC, 0.0) for m in range(3)]
+    kap = np.exp2(rng.integers(-10, -2, size=shape).astype(np.float64))
+    w = np.where(rng.random(shape) < 0.5, -1.0, 1.0) * np.exp2(rng.integers(-6, 0, size=shape).astype(np.float64))
+    ins = [B.Grid(n, HC, "f64").upload(a) for a in (q[0], q[1], q[2], kap, w, t[0], t[1], t[2])]
+    outs = [B.Grid(n, HC, "f64").upload(np.zeros(shape)) for _ in range(3)]
+    B.do_all(S.climate(), ins, outs)
+    B.sync()
+    want = climate_expected(q, kap, w, t, n, int_add == "1")
+    for m in range(3):
+        ok = same_bits(I.interior_view(outs[m].download().numpy(), n, HC), want[m])
+        assert ok.all(), (m, int((~ok).sum()), np.argwhere(~ok)[:3].tolist())
