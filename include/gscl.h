@@ -96,7 +96,15 @@ typedef uint64_t gscl_grid; /* 0 is never a valid handle */
  * so a term of an output may use it: that is how two operators share one
  * scan (the paper's fuse(), Section 5.2).  Terms may be given in any order;
  * the sum over an output's terms is evaluated in an unspecified order with
- * fused multiply-adds in the grids' arithmetic type.
+ * fused multiply-adds in the grids' arithmetic type.  On IEEE FP64 grids,
+ * terms that differ only in the sign pattern of their offset (one input, one
+ * coefficient, one destination; the six neighbours of a 7-point star, the
+ * rings of a biharmonic) and have equal weights (a pair: opposite weights)
+ * may be summed first and weighted once: w * (x1 + x2 + ...).  Every
+ * addition is an IEEE binary64 addition rounded to nearest (some of them are
+ * computed on the integer pipe, with identical results), so the value differs
+ * from the term-by-term sum only by rounding.  The environment variable
+ * GSCL_FP64_INT_ADD=0 keeps one fused multiply-add per term.
  */
 typedef struct gscl_term {
   int8_t dx, dy, dz;
