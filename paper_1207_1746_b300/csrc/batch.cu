@@ -165,7 +165,7 @@ gscl_status build(Batch *bt) {
   bt->buf_a.assign(n, nullptr);
   bt->buf_b.assign(n, nullptr);
   TileCfg cfg = bt->cfg;
-  bool any_eqw = false;  // some instance has equal axial weights (per-instance flags in the weight rows)
+  bool any_eqw = false, all_eqw = true;  // instances allowing the group evaluation (flags in the weight rows)
   bool tb_ok = !bt->colored && bt->n_in == 1 && bt->n_out == 1;
   bool tb3_ok = !bt->colored && bt->n_out == 1;
   std::vector<InstDesc> tabs3[2];
@@ -237,6 +237,7 @@ gscl_status build(Batch *bt) {
         }
         wrows[i].eq = pl.eqw ? 1 : 0;
         any_eqw = any_eqw || pl.eqw;
+        all_eqw = all_eqw && pl.eqw;
       }
     }
     bt->buf_a[i] = b.in[0].buf;
@@ -245,6 +246,7 @@ gscl_status build(Batch *bt) {
   Plan &base = bt->base;
   base.batch = true;
   base.eqw = any_eqw;
+  base.eq_mixed = any_eqw && !all_eqw;
   // one wave of CTAs
   int occ = 0;
   const int red_probe = bt->n_out ? RED_NONE : RED_L2;

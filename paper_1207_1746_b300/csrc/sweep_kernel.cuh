@@ -157,18 +157,23 @@ struct ParamWeights {
   // single grids: the axial-sum kernel is launched only for equal weights
   __device__ static constexpr bool eq() { return true; }
 };
-template <typename A, int N>
+template <typename A, int N, bool DYN = false>
 struct RegWeights {
   A v[N];
   bool e;
   __device__ __forceinline__ void load(const InstWeights *w) {
 #pragma unroll
     for (int i = 0; i < N; ++i) v[i] = inst_weight(*w, i, A(0));
-    e = w->eq != 0;
+    if constexpr (DYN) e = w->eq != 0;
   }
   __device__ __forceinline__ A operator()(const SweepParams &, int i) const { return v[i]; }
-  // batches: per instance (a coloured batch's instances have their own weights)
-  __device__ __forceinline__ bool eq() const { return e; }
+  // the group evaluation: per instance (DYN: a coloured batch mixing
+  // instances whose weights allow it and instances whose weights do not),
+  // else for every instance of the batch
+  __device__ __forceinline__ bool eq() const {
+    if constexpr (DYN) return e;
+    else return true;
+  }
 };
 template <typename A>
 struct RowWeights {
@@ -460,7 +465,7 @@ struct GenericOp {
 // weight times axial_sum, w (sum of six) instead of six FMAs; two of the
 // sum's five additions run on the integer pipe, so a point of the heat
 // operator takes six FP64 operations instead of eight.
-template <class Def, int XS = 1, bool EQ = false>
+template <class Def, int XS = 1, bool EQ = false, bool DYN = false>
 struct StaticOp {
   static constexpr int kXStep = XS;
   static constexpr int kAxial = EQ ? axial_group<Def>() : -1;
@@ -482,7 +487,7 @@ struct StaticOp {
   static constexpr int kTerms = Def::NT;
   static constexpr int kMaxOut = Def::NOUT > 0 ? Def::NOUT : 1;
   template <typename A, bool BATCH>
-  using Weights = typename std::conditional<BATCH, RegWeights<A, Def::NT>, ParamWeights<A>>::type;
+  using Weights = typename std::conditional<BATCH, RegWeights<A, Def::NT, DYN>, ParamWeights<A>>::type;
   __device__ static constexpr int n_out(const SweepParams &) { return Def::NOUT; }
 
   // reach of the terms reading input `in` (-1: every input) along `axis`
@@ -1645,7 +1650,8 @@ struct Plan {
   bool pair = false;          // FP64 grids in pair arithmetic (fixed when the plan is made)
   bool compact = false;       // colour-compacted red-black sweep (XS = 2 tiles)
   bool vec = false;           // vector lanes (StaticOpV): FP32 / BF16 compile-time operators
-  bool eqw = false;           // IEEE FP64, equal axial weights: StaticOp<Def, XS, true> (batches: some instance)
+  bool eqw = false;           // IEEE FP64 group evaluation: StaticOp<Def, XS, true> (batches: some instance)
+  bool eq_mixed = false;      // batches: only some instances allow it (a flag per instance)
   int tile_x = 0, tile_y = 0; // core elements per CTA tile
 };
 
@@ -1790,6 +1796,10 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       if constexpr (RED == RED_NONE && CompactCapable<Def>::value) {
         if (pl.compact) {
           if constexpr (std::is_same<T, double>::value && has_groups<Def>()) {
+            if constexpr (BATCH) {
+              if (pl.eqw && pl.eq_mixed)
+                return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2, true, true>, BATCH>(pl, stream, occ);
+            }
             if (pl.eqw) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2, true>, BATCH>(pl, stream, occ);
           }
           return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 2>, BATCH>(pl, stream, occ);
@@ -1797,6 +1807,10 @@ gscl_status launch_op(const Plan &pl, cudaStream_t stream, int *occ) {
       }
       // equal axial weights: the neighbour sum partly on the integer pipe
       if constexpr (std::is_same<T, double>::value && has_groups<Def>()) {
+        if constexpr (BATCH) {
+          if (pl.eqw && pl.eq_mixed)
+            return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 1, true, true>, BATCH>(pl, stream, occ);
+        }
         if (pl.eqw) return launch_t<T, VxOf<T>::value, RED, StaticOp<Def, 1, true>, BATCH>(pl, stream, occ);
       }
       return launch_t<T, VxOf<T>::value, RED, StaticOp<Def>, BATCH>(pl, stream, occ);
