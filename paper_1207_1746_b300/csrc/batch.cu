@@ -451,8 +451,8 @@ gscl_status run_group(Batch *bt, std::pair<int, int> key, bool use_graph, cudaSt
 
 template <int RED>
 gscl_status finalize(Batch *bt, double *results, cudaStream_t stream) {
-  const int threads = 128;
-  batch_finalize_kernel<RED><<<(bt->n_inst + threads - 1) / threads, threads, 0, stream>>>(
+  const int threads = 128, per_block = threads / 32;  // one warp per instance
+  batch_finalize_kernel<RED><<<(bt->n_inst + per_block - 1) / per_block, threads, 0, stream>>>(
       bt->partials, bt->inst_seg, bt->n_inst, results);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? GSCL_OK : cuda_fail(e, "batch finalize launch");

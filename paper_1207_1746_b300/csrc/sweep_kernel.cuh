@@ -1621,19 +1621,33 @@ __global__ void __launch_bounds__(256, min_ctas_per_sm<T, BATCH, RED, Op>())
 }
 
 // Per-instance results of a batched reduce: instance i's segments are the
-// contiguous range [inst_seg[i], inst_seg[i + 1]) of the work-list; folded
-// in order (deterministic for a given work-list).
+// contiguous range [inst_seg[i], inst_seg[i + 1]) of the work-list.  One
+// warp per instance: lane l folds the l-th of 32 equal contiguous chunks in
+// order, then the lanes combine in a fixed shuffle tree (deterministic for a
+// given work-list).  One thread per instance had made the fold a dependent
+// chain of FP64 TwoSums as long as the instance's segment count, which on
+// the FP64 pipe's latency took as long as the sweep for a large instance.
 template <int RED>
 __global__ void batch_finalize_kernel(const double *seg_partials, const int32_t *inst_seg, int n_inst,
                                       double *results) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n_inst) return;
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n_inst) return;  // the whole warp
+  const int k0 = inst_seg[i], n = inst_seg[i + 1] - k0;
+  const int chunk = (n + 31) / 32;
+  const int b = min(n, lane * chunk), e = min(n, b + chunk);
   double s = 0.0, c = 0.0;
-  for (int k = inst_seg[i]; k < inst_seg[i + 1]; ++k) {
+  for (int k = k0 + b; k < k0 + e; ++k) {
     if (RED == RED_MAXABS) s = max_abs_bits(s, seg_partials[2 * k]);
     else combine_pair(s, c, seg_partials[2 * k], seg_partials[2 * k + 1]);
   }
-  results[i] = RED == RED_MAXABS ? s : (RED == RED_L2 ? sqrt(s - c) : s - c);
+  for (int off = 16; off > 0; off >>= 1) {
+    const double s2 = __shfl_down_sync(0xffffffffu, s, off);
+    const double c2 = __shfl_down_sync(0xffffffffu, c, off);
+    if (RED == RED_MAXABS) s = max_abs_bits(s, s2);
+    else combine_pair(s, c, s2, c2);
+  }
+  if (lane == 0) results[i] = RED == RED_MAXABS ? s : (RED == RED_L2 ? sqrt(s - c) : s - c);
 }
 
 // ---------------------------------------------------------------- launching
