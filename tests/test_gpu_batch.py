@@ -165,3 +165,32 @@ def test_batch_rejects_mismatched_instances():
     e2 = B.Grid((8, 8, 8), (1, 1, 1))
     with pytest.raises(B.GsclError):
         B.Batch(S.heat7(0.125, with_f=False), [([c], [d]), ([a], [e2])])
+
+
+@pytest.mark.parametrize("red", [B.L2, B.SUM, B.MAXABS])
+def test_batch_reduce_of_large_instances_is_deterministic(red):
+    """Instances large enough to spread over hundreds of work-list segments
+    (one warp per instance folds them: fixed chunks per lane, then a fixed
+    shuffle tree): two reductions give the same bits, and each agrees with
+    gscl_do_reduce on the instance alone (MAXABS exactly)."""
+    sides = [(256, 64, 64), (130, 90, 40), (33, 40, 35)]
+    insts = []
+    for k, n in enumerate(sides):
+        u0 = I.random_interior(1300 + k, n, H, -1.0, 1.0)
+        f0 = I.random_interior(1310 + k, n, H, -1.0, 1.0)
+        insts.append(([B.Grid(n, H).upload(u0), B.Grid(n, H).upload(f0)], []))
+    bt = B.Batch(S.residual7(), insts)
+    a = torch.zeros(len(sides), dtype=torch.float64, device="cuda")
+    b = torch.zeros(len(sides), dtype=torch.float64, device="cuda")
+    bt.reduce(red, a)
+    bt.reduce(red, b)
+    assert torch.equal(a, b)
+    for k, ((ins, _), n) in enumerate(zip(insts, sides)):
+        want = B.do_reduce(red, S.residual7(), ins)
+        got = a[k].item()
+        if red == B.MAXABS:
+            assert got == want
+        elif red == B.L2:
+            assert abs(got - want) <= 1e-12 * abs(want)
+        else:  # the sum of |terms| bounds the rounding: 8 terms of at most 6 in size per point
+            assert abs(got - want) <= 1e-13 * 13.0 * n[0] * n[1] * n[2]
