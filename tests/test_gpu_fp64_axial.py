@@ -318,3 +318,38 @@ def test_climate_groups_bit_exact(compiled, int_add, n):
     for m in range(3):
         ok = same_bits(I.interior_view(outs[m].download().numpy(), n, HC), want[m])
         assert ok.all(), (m, int((~ok).sum()), np.argwhere(~ok)[:3].tolist())
+
+
+def fma0(w, x):
+    """fma(w, x, +0) for a power of two w: the rounded product (numpy rounds
+    to nearest even, keeping the sign of a product that underflows to zero),
+    and +0 where x is a zero."""
+    with np.errstate(all="ignore"):
+        p = w * x
+    return np.where(x == 0.0, 0.0, p)
+
+
+@pytest.mark.parametrize("w0", [0.25, 1.0, -0.5, 2.0 ** -600])
+@pytest.mark.parametrize("n", [(70, 45, 23), (5, 3, 2)])
+def test_power_of_two_first_term_bit_exact(compiled, w0, n):
+    """A first weight that is a power of two of magnitude at most 1 (the heat
+    sweep's 1 - 6 lam = 1/4): the chain opens with fma(w0, u, +0), whose bits
+    include products that underflow into subnormals or to a signed zero; a
+    batch gives the same bits."""
+    u = special_field(1400 + n[0], n, H, 0.3)
+    f = special_field(1401 + n[0], n, H, 0.1)
+    op = heat_op(w0=w0)
+    got = sweep(u, f, n, op)
+    c = shifted(u, n, H, 0, 0, 0)
+    nb = [shifted(u, n, H, *d) for d in S.X6]
+    with np.errstate(all="ignore"):
+        v = fma0(w0, c)
+        v = v + WF * shifted(f, n, H, 0, 0, 0)
+        v = v + W * (((nb[0] + nb[1]) + (nb[2] + nb[3])) + (nb[4] + nb[5]))
+    ok = same_bits(got, v)
+    assert ok.all(), (int((~ok).sum()), np.argwhere(~ok)[:3].tolist())
+    gu, gf = B.Grid(n, H, "f64").upload(u), B.Grid(n, H, "f64").upload(f)
+    go = B.Grid(n, H, "f64").upload(np.zeros(I.padded_shape(n, H)))
+    B.Batch(op, [([gu, gf], [go])]).run(1)
+    B.sync()
+    assert same_bits(I.interior_view(go.download().numpy(), n, H), got).all()
